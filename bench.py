@@ -1,0 +1,347 @@
+"""Benchmark: exact QFT on 27 qubits (complex64 ket, fused passes) through
+the C-ABI library, in amplitude-gate updates per second.
+
+One step = the whole hot path over one ket: the 391-gate QFT (H, controlled
+phases, qubit-reversal swaps) applied to a seeded Gaussian 27-qubit ket by
+the fused SIMT passes, followed by the FP64 norm reduction of the result.
+updates/s = gates x 2^n / step time. The ket (1 GiB) is larger than L2, so
+no flush is needed between steps.
+
+Also reported on the same box: the plain per-gate FP64 (complex128) path on
+the same circuit (the in-run GPU baseline), the 30-qubit 5x6 grid random
+circuit (10 layers) on the fused complex64 path, the roofline of the fused
+pass kernel against the measured HBM copy bandwidth, the end-to-end number
+with host buffers, and the FP64 CPU oracle on a bounded sample.
+
+--impl reference times the CPU oracle instead (the oracle is the reference
+for this build: there is no reference implementation to install).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_QUBITS = 27
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-extras", action="store_true", help="skip the per-gate FP64, grid and CPU legs")
+    return ap.parse_args()
+
+
+def dist_init(n):
+    if n <= 1:
+        return 0, 1
+    import torch.distributed as dist
+    dist.init_process_group("nccl")
+    return dist.get_rank(), dist.get_world_size()
+
+
+# ------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------ CPU oracle
+
+def oracle_sample(n_gates=16, n=N_QUBITS, seed=0):
+    """The FP64 CPU oracle on the first n_gates gates of the 27-qubit QFT
+    (single thread), in updates/s."""
+    import oracle
+    from paper_2304_14969_gb300 import workloads as W
+    g = W.qft_circuit(n)[:n_gates]
+    x = W.gaussian_state(n, seed)
+    oracle.lib()
+    t0 = time.perf_counter()
+    oracle.apply_circuit(x, g)
+    dt = time.perf_counter() - t0
+    return len(g) * (1 << n) / dt, dt, len(g)
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    vals, secs = [], []
+    for i in range(args.warmup + args.steps):
+        v, dt, ng = oracle_sample(n_gates=4)
+        if i >= args.warmup:
+            vals.append(v)
+            secs.append(dt)
+    value = float(np.median(vals))
+    line = {
+        "impl": "reference", "metric": "amplitude-gate updates/s", "value": value, "unit": "updates/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * float(np.median(secs)), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "qft27_gaussian", "n_qubits": N_QUBITS, "gates": 391,
+                   "sample": "first 4 gates of the 27-qubit QFT per step"},
+        "cpu_baseline": {"value": value, "unit": "updates/s", "cores": 1, "kind": "oracle",
+                         "sample": "first 4 gates of the 27-qubit QFT per step, FP64, one thread"},
+        "e2e": {"value": value, "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+# ------------------------------------------------------------ GPU legs
+
+def traffic_from_profiles(kernel):
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p))
+        e = d.get(kernel)
+        if not e:
+            return None
+        src = os.path.join(ROOT, "paper_2304_14969_gb300", "csrc", e["source"])
+        import hashlib
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        return e["bytes_per_launch"] if h == e.get("source_sha") else None
+    except Exception:
+        return None
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    if args.warmup < 3:
+        args.warmup = 3
+    import torch
+    rank, world = dist_init(args.gpus)
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    from paper_2304_14969_gb300 import build, qsim as Q
+    from paper_2304_14969_gb300 import workloads as W
+    build.build()
+    Q.lib()
+    n = N_QUBITS
+    N = 1 << n
+    gates = W.qft_circuit(n)
+    ng = len(gates)
+    circ = Q.Circuit(n, gates)
+    stream = torch.cuda.Stream()
+    sp = stream.cuda_stream
+    # ket in a torch-owned device buffer, wrapped by the library
+    x = W.gaussian_state(n, rank)
+    x64 = torch.from_numpy(x.astype(np.complex64))
+    host_in = torch.empty(N, dtype=torch.complex64).pin_memory()
+    host_in.copy_(x64)
+    host_out = torch.empty(N, dtype=torch.complex64).pin_memory()
+    dev = torch.empty(N, dtype=torch.complex64, device="cuda")
+    st = Q.State(n, Q.QSIM_C64, stream=sp, dev_ptr=dev.data_ptr())
+    plan = Q.Plan(circ, dtype=Q.QSIM_C64)
+    info = plan.info()
+    import ctypes as C
+    nrm = C.c_double()
+
+    def step():
+        plan.execute(st)
+        Q.qsim_norm(st.h, C.byref(nrm))   # FP64 norm of the result (syncs)
+
+    Q.qsim_upload(st.h, C.c_void_p(host_in.data_ptr()))
+    for _ in range(args.warmup):
+        step()
+    # ---- timed region: K steps, events on the library's stream
+    with torch.cuda.stream(stream):
+        torch.cuda.synchronize()
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        clocks = ClockSampler(local)
+        clocks.start()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+               torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for k in range(args.steps):
+            ev[k][0].record(stream)
+            plan.execute(st)
+            ev[k][1].record(stream)
+            Q.qsim_norm(st.h, C.byref(nrm))
+            ev[k][2].record(stream)
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+    step_ms = [a.elapsed_time(c) for a, b, c in ev]
+    pass_ms = [a.elapsed_time(b) for a, b, c in ev]
+    total_ms = sum(step_ms)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * ng * N / (ms_per_step * 1e-3)
+    npass = info["passes"]
+    launch_ms = float(np.mean(pass_ms)) / npass
+    alg_bytes = 2 * 8 * N                   # one read + one write of the ket per pass
+    achieved = alg_bytes / (launch_ms * 1e-3) / 1e9
+    peaks = {}
+    pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pp):
+        peaks = json.load(open(pp))
+    peak = peaks.get("hbm_gbs", 6800.0)
+
+    # ---- end to end through the public API with pinned host buffers
+    e2e_ms = []
+    for k in range(max(3, min(args.steps, 5))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Q.qsim_upload(st.h, C.c_void_p(host_in.data_ptr()))
+        plan.execute(st)
+        Q.qsim_download(st.h, C.c_void_p(host_out.data_ptr()))
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_val = world * ng * N / (float(np.median(e2e_ms)) * 1e-3)
+
+    extras = {}
+    if rank == 0 and not args.no_extras:
+        extras = extra_legs(Q, W, C, torch, circ, x, n, ng)
+    if rank != 0:
+        return
+    cpu = {}
+    if not args.no_extras:
+        v, dt, k = oracle_sample()
+        cpu = {"value": v, "unit": "updates/s", "cores": 1, "kind": "oracle",
+               "sample": f"first {k} gates of the 27-qubit QFT on a Gaussian ket, FP64, one thread ({dt:.1f} s)"}
+    line = {
+        "metric": "amplitude-gate updates/s", "value": value, "unit": "updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "qft27_gaussian_c64_fused", "n_qubits": n, "gates": ng, "passes": npass,
+                   "tile_qubits": info["tile_qubits"], "ket_bytes": 8 * N, "l2": "ket (1 GiB) larger than L2",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic_from_profiles("k_fused_pass"),
+                     "kernel": "k_fused_pass", "alg_bytes_per_launch": alg_bytes,
+                     "launch_ms": launch_ms, "peak_source": "measured hbm_gbs" if peaks else "fallback"},
+        "e2e": {"value": e2e_val, "unit": "updates/s", "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 8 * N},
+        "gpu_launches": args.steps * (npass + 2),
+        "clocks": clk,
+        "cpu_baseline": cpu,
+        "norm_check": nrm.value,
+    }
+    line.update(extras)
+    if "per_gate_fp64" in extras:
+        line["speedup_vs_per_gate_fp64"] = extras["per_gate_fp64"]["ms"] / float(np.mean(pass_ms))
+    print(json.dumps(line))
+    st.close()
+
+
+def extra_legs(Q, W, C, torch, circ, x, n, ng):
+    out = {}
+    N = 1 << n
+    # plain per-gate FP64 path on the same circuit
+    s128 = Q.State(n, Q.QSIM_C128)
+    s128.upload(x)
+    o = Q.qsim_run_opts(mode=0, relabel_swaps=1)
+    Q.qsim_run_circuit(s128.h, circ.ptr(), C.byref(o))
+    Q.qsim_synchronize(s128.h)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Q.qsim_upload(s128.h, x.ctypes.data_as(C.c_void_p))
+    Q.qsim_synchronize(s128.h)
+    t0 = time.perf_counter()
+    Q.qsim_run_circuit(s128.h, circ.ptr(), C.byref(o))
+    Q.qsim_synchronize(s128.h)
+    pg = time.perf_counter() - t0
+    out["per_gate_fp64"] = {"updates_per_s": ng * N / pg, "ms": pg * 1e3, "dtype": "c128"}
+    s128.close()
+    # fused c128
+    s = Q.State(n, Q.QSIM_C128)
+    s.upload(x)
+    p = Q.Plan(circ, dtype=Q.QSIM_C128)
+    p.execute(s)
+    Q.qsim_synchronize(s.h)
+    t0 = time.perf_counter()
+    for _ in range(3):
+        p.execute(s)
+    Q.qsim_synchronize(s.h)
+    f128 = (time.perf_counter() - t0) / 3
+    out["fused_fp64"] = {"updates_per_s": ng * N / f128, "ms": f128 * 1e3, "dtype": "c128",
+                         "passes": p.info()["passes"]}
+    s.close()
+    # grid random circuit, 5x6, 10 layers, complex64 fused
+    g = W.grid_rcs_circuit(5, 6, 10, seed=0)
+    gc = Q.Circuit(30, g)
+    gp = Q.Plan(gc, dtype=Q.QSIM_C64)
+    sg = Q.State(30, Q.QSIM_C64)
+    gp.execute(sg)
+    Q.qsim_synchronize(sg.h)
+    t0 = time.perf_counter()
+    for _ in range(3):
+        gp.execute(sg)
+    Q.qsim_synchronize(sg.h)
+    tg = (time.perf_counter() - t0) / 3
+    gi = gp.info()
+    out["grid30_c64_fused"] = {"updates_per_s": len(g) * (1 << 30) / tg, "ms": tg * 1e3, "passes": gi["passes"],
+                               "hbm_gbs": gi["passes"] * 2 * 8 * (1 << 30) / tg / 1e9}
+    sg.close()
+    return out
+
+
+if __name__ == "__main__":
+    main()

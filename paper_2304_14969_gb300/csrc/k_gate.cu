@@ -1,0 +1,329 @@
+// Per-gate kernels: one HBM pass per gate (the plain baseline path).
+//
+// Sec. II of arXiv 2304.14969: a gate on k qubits updates every group of
+// 2^k amplitudes whose indices differ only in those qubits. Work items are
+// numbered densely and expanded to amplitude indices by inserting the
+// gate's qubit bits (zeros) at their positions, so no thread idles on an
+// index the gate does not touch. Consecutive work items map to consecutive
+// amplitudes in every stream, which keeps loads coalesced; complex64 pairs
+// are moved as 16-byte vectors when the lowest qubit is untouched.
+#include <algorithm>
+#include <cmath>
+#include <cuda_runtime.h>
+
+#include "qsim_internal.h"
+
+namespace qs {
+
+template <typename R> struct Vec2;
+template <> struct Vec2<float> { using T = float2; };
+template <> struct Vec2<double> { using T = double2; };
+
+template <typename R> struct M2 { R re[4], im[4]; };
+template <typename R> struct M4 { R re[16], im[16]; };
+
+__device__ __forceinline__ uint64_t expand_bits(uint64_t w, const InsSpec &ins)
+{
+#pragma unroll
+    for (int j = 0; j < 12; j++) {
+        if (j < ins.npos) {
+            int p = ins.pos[j];
+            uint64_t lo = w & ((1ull << p) - 1);
+            w = ((w >> p) << (p + 1)) | lo;
+        }
+    }
+    return w;
+}
+
+int default_grid(uint64_t work, int threads)
+{
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 152;
+    }
+    uint64_t blocks = (work + threads - 1) / threads;
+    uint64_t cap = (uint64_t)sms * 16;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    return (int)blocks;
+}
+
+template <typename R>
+__device__ __forceinline__ void cmul_acc(R &ore, R &oim, R ure, R uim, R xre, R xim)
+{
+    ore = fma(ure, xre, ore);
+    ore = fma(-uim, xim, ore);
+    oim = fma(ure, xim, oim);
+    oim = fma(uim, xre, oim);
+}
+
+// One-qubit gate. Each work item is one pair (i, i | tbit).
+template <typename R>
+__global__ void k_gate1(typename Vec2<R>::T *__restrict__ a, uint64_t nwork, InsSpec ins,
+                        uint64_t setmask, uint64_t tbit, M2<R> u)
+{
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nwork; w += stride) {
+        uint64_t i0 = expand_bits(w, ins) | setmask, i1 = i0 | tbit;
+        auto x = a[i0], y = a[i1];
+        R r0 = 0, m0 = 0, r1 = 0, m1 = 0;
+        cmul_acc(r0, m0, u.re[0], u.im[0], x.x, x.y);
+        cmul_acc(r0, m0, u.re[1], u.im[1], y.x, y.y);
+        cmul_acc(r1, m1, u.re[2], u.im[2], x.x, x.y);
+        cmul_acc(r1, m1, u.re[3], u.im[3], y.x, y.y);
+        x.x = r0; x.y = m0; y.x = r1; y.y = m1;
+        a[i0] = x;
+        a[i1] = y;
+    }
+}
+
+// complex64 variant: each work item covers two neighbouring pairs (bit 0 of
+// the index is untouched by the gate), moved as float4.
+__global__ void k_gate1_c64v(float4 *__restrict__ a4, uint64_t nwork, InsSpec ins, uint64_t setmask,
+                             uint64_t tbit, M2<float> u)
+{
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nwork; w += stride) {
+        uint64_t i0 = expand_bits(w << 1, ins) | setmask, i1 = i0 | tbit;
+        float4 x = a4[i0 >> 1], y = a4[i1 >> 1];
+        float4 o0 = make_float4(0, 0, 0, 0), o1 = o0;
+        cmul_acc(o0.x, o0.y, u.re[0], u.im[0], x.x, x.y);
+        cmul_acc(o0.x, o0.y, u.re[1], u.im[1], y.x, y.y);
+        cmul_acc(o0.z, o0.w, u.re[0], u.im[0], x.z, x.w);
+        cmul_acc(o0.z, o0.w, u.re[1], u.im[1], y.z, y.w);
+        cmul_acc(o1.x, o1.y, u.re[2], u.im[2], x.x, x.y);
+        cmul_acc(o1.x, o1.y, u.re[3], u.im[3], y.x, y.y);
+        cmul_acc(o1.z, o1.w, u.re[2], u.im[2], x.z, x.w);
+        cmul_acc(o1.z, o1.w, u.re[3], u.im[3], y.z, y.w);
+        a4[i0 >> 1] = o0;
+        a4[i1 >> 1] = o1;
+    }
+}
+
+// Dense two-qubit gate: each work item is one quad.
+template <typename R>
+__global__ void k_gate2(typename Vec2<R>::T *__restrict__ a, uint64_t nwork, InsSpec ins, uint64_t b0,
+                        uint64_t b1, M4<R> u)
+{
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nwork; w += stride) {
+        uint64_t base = expand_bits(w, ins);
+        uint64_t idx[4] = {base, base | b0, base | b1, base | b0 | b1};
+        R xr[4], xi[4];
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+            auto v = a[idx[c]];
+            xr[c] = v.x;
+            xi[c] = v.y;
+        }
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            R orr = 0, oi = 0;
+#pragma unroll
+            for (int c = 0; c < 4; c++) cmul_acc(orr, oi, u.re[r * 4 + c], u.im[r * 4 + c], xr[c], xi[c]);
+            typename Vec2<R>::T o;
+            o.x = orr;
+            o.y = oi;
+            a[idx[r]] = o;
+        }
+    }
+}
+
+// Controlled phase: multiplies the amplitudes with both bits set.
+template <typename R>
+__global__ void k_cphase(typename Vec2<R>::T *__restrict__ a, uint64_t nwork, InsSpec ins, uint64_t both,
+                         R cr, R ci)
+{
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nwork; w += stride) {
+        uint64_t i = expand_bits(w, ins) | both;
+        auto v = a[i];
+        R re = v.x * cr - v.y * ci;
+        R im = v.x * ci + v.y * cr;
+        v.x = re;
+        v.y = im;
+        a[i] = v;
+    }
+}
+
+template <typename R>
+__global__ void k_swap(typename Vec2<R>::T *__restrict__ a, uint64_t nwork, InsSpec ins, uint64_t ba,
+                       uint64_t bb)
+{
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nwork; w += stride) {
+        uint64_t i = expand_bits(w, ins);
+        auto x = a[i | ba], y = a[i | bb];
+        a[i | ba] = y;
+        a[i | bb] = x;
+    }
+}
+
+template <typename R>
+__global__ void k_set_basis(typename Vec2<R>::T *__restrict__ a, uint64_t N, uint64_t x)
+{
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+        typename Vec2<R>::T v;
+        v.x = (i == x) ? R(1) : R(0);
+        v.y = 0;
+        a[i] = v;
+    }
+}
+
+template <typename R>
+__global__ void k_scale(typename Vec2<R>::T *__restrict__ a, uint64_t N, R f)
+{
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+        auto v = a[i];
+        v.x *= f;
+        v.y *= f;
+        a[i] = v;
+    }
+}
+
+// dst[perm(i)] = src[i] where bit q of i moves to bit new_of_old[q].
+struct PermSpec { int n; int to[40]; };
+
+template <typename R>
+__global__ void k_permute(const typename Vec2<R>::T *__restrict__ src, typename Vec2<R>::T *__restrict__ dst,
+                          uint64_t N, PermSpec ps)
+{
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+        uint64_t j = 0;
+        for (int q = 0; q < ps.n; q++) j |= ((i >> q) & 1ull) << ps.to[q];
+        dst[j] = src[i];
+    }
+}
+
+// ------------------------------------------------------------ launchers
+
+static InsSpec make_ins(std::vector<int> pos)
+{
+    std::sort(pos.begin(), pos.end());
+    InsSpec s;
+    s.npos = (int)pos.size();
+    for (int j = 0; j < s.npos; j++) s.pos[j] = pos[j];
+    return s;
+}
+
+template <typename R> static M2<R> to_m2(const cd u[4])
+{
+    M2<R> m;
+    for (int k = 0; k < 4; k++) { m.re[k] = (R)u[k].real(); m.im[k] = (R)u[k].imag(); }
+    return m;
+}
+
+template <typename R> static M4<R> to_m4(const cd u[16])
+{
+    M4<R> m;
+    for (int k = 0; k < 16; k++) { m.re[k] = (R)u[k].real(); m.im[k] = (R)u[k].imag(); }
+    return m;
+}
+
+static const int kThreads = 256;
+
+cudaError_t launch_gate1(qsim_state *s, const cd u[4], int t, uint64_t cmask, uint64_t cval)
+{
+    std::vector<int> pos{t};
+    for (int q = 0; q < s->n; q++)
+        if (cmask & bit(q)) pos.push_back(q);
+    InsSpec ins = make_ins(pos);
+    uint64_t nwork = s->N() >> ins.npos;
+    bool low_free = (ins.pos[0] != 0);
+    if (s->dt == QSIM_C64) {
+        if (low_free && nwork >= 2) {
+            uint64_t nw = nwork / 2;
+            k_gate1_c64v<<<default_grid(nw, kThreads), kThreads, 0, s->stream>>>(
+                (float4 *)s->amps, nw, ins, cval, bit(t), to_m2<float>(u));
+        } else {
+            k_gate1<float><<<default_grid(nwork, kThreads), kThreads, 0, s->stream>>>(
+                (float2 *)s->amps, nwork, ins, cval, bit(t), to_m2<float>(u));
+        }
+    } else {
+        k_gate1<double><<<default_grid(nwork, kThreads), kThreads, 0, s->stream>>>(
+            (double2 *)s->amps, nwork, ins, cval, bit(t), to_m2<double>(u));
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gate2(qsim_state *s, const cd u[16], int q0, int q1)
+{
+    InsSpec ins = make_ins({q0, q1});
+    uint64_t nwork = s->N() >> 2;
+    if (s->dt == QSIM_C64)
+        k_gate2<float><<<default_grid(nwork, kThreads), kThreads, 0, s->stream>>>(
+            (float2 *)s->amps, nwork, ins, bit(q0), bit(q1), to_m4<float>(u));
+    else
+        k_gate2<double><<<default_grid(nwork, kThreads), kThreads, 0, s->stream>>>(
+            (double2 *)s->amps, nwork, ins, bit(q0), bit(q1), to_m4<double>(u));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cphase(qsim_state *s, int q0, int q1, double theta)
+{
+    InsSpec ins = make_ins({q0, q1});
+    uint64_t nwork = s->N() >> 2;
+    double c = std::cos(theta), sn = std::sin(theta);
+    if (s->dt == QSIM_C64)
+        k_cphase<float><<<default_grid(nwork, kThreads), kThreads, 0, s->stream>>>(
+            (float2 *)s->amps, nwork, ins, bit(q0) | bit(q1), (float)c, (float)sn);
+    else
+        k_cphase<double><<<default_grid(nwork, kThreads), kThreads, 0, s->stream>>>(
+            (double2 *)s->amps, nwork, ins, bit(q0) | bit(q1), c, sn);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_swap(qsim_state *s, int q0, int q1)
+{
+    InsSpec ins = make_ins({q0, q1});
+    uint64_t nwork = s->N() >> 2;
+    if (s->dt == QSIM_C64)
+        k_swap<float><<<default_grid(nwork, kThreads), kThreads, 0, s->stream>>>(
+            (float2 *)s->amps, nwork, ins, bit(q0), bit(q1));
+    else
+        k_swap<double><<<default_grid(nwork, kThreads), kThreads, 0, s->stream>>>(
+            (double2 *)s->amps, nwork, ins, bit(q0), bit(q1));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_basis(qsim_state *s, uint64_t x)
+{
+    uint64_t N = s->N();
+    if (s->dt == QSIM_C64)
+        k_set_basis<float><<<default_grid(N, kThreads), kThreads, 0, s->stream>>>((float2 *)s->amps, N, x);
+    else
+        k_set_basis<double><<<default_grid(N, kThreads), kThreads, 0, s->stream>>>((double2 *)s->amps, N, x);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scale(void *amps, qsim_dtype dt, uint64_t N, double f, cudaStream_t st)
+{
+    if (dt == QSIM_C64)
+        k_scale<float><<<default_grid(N, kThreads), kThreads, 0, st>>>((float2 *)amps, N, (float)f);
+    else
+        k_scale<double><<<default_grid(N, kThreads), kThreads, 0, st>>>((double2 *)amps, N, f);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_permute(const void *src, void *dst, qsim_dtype dt, int n, const int *new_of_old,
+                           cudaStream_t st)
+{
+    PermSpec ps;
+    ps.n = n;
+    for (int q = 0; q < n; q++) ps.to[q] = new_of_old[q];
+    uint64_t N = 1ull << n;
+    if (dt == QSIM_C64)
+        k_permute<float><<<default_grid(N, kThreads), kThreads, 0, st>>>((const float2 *)src, (float2 *)dst, N, ps);
+    else
+        k_permute<double><<<default_grid(N, kThreads), kThreads, 0, st>>>((const double2 *)src, (double2 *)dst, N,
+                                                                         ps);
+    return cudaGetLastError();
+}
+
+}  // namespace qs

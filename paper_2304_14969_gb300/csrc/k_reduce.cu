@@ -1,0 +1,442 @@
+// FP64 reductions over a ket: norm, P(q = 1), inner product, Bloch vectors,
+// probabilities.
+//
+// Sec. III.A (arXiv 2304.14969) needs the reduced one-qubit state rho_q of
+// each checked qubit, i.e. r = (<X_q>, <Y_q>, <Z_q>), and a normalised ket;
+// Eq. (fid_exact) needs <psi_approx|psi_exact>. All cross-element sums are
+// carried in FP64. For complex64 kets each thread first sums runs of 8
+// terms in FP32 (the products of FP32 amplitudes are FP32 numbers anyway)
+// and adds each run to an FP64 accumulator; this keeps the FP64 pipe, which
+// is narrow on this part, off the critical path while the sum itself stays
+// FP64. complex128 kets are summed in FP64 throughout.
+//
+// Each kernel writes one row of M partial sums per CTA; a one-CTA kernel
+// adds the rows in FP64 and the result is copied to pinned host memory.
+#include <algorithm>
+#include <cuda_runtime.h>
+
+#include "qsim_internal.h"
+
+namespace qs {
+
+static const int kRedThreads = 256;
+static const int kMaxRedBlocks = 152 * 8;
+
+template <typename R> struct V2T;
+template <> struct V2T<float> { using T = float2; };
+template <> struct V2T<double> { using T = double2; };
+
+template <int M>
+__device__ __forceinline__ void block_write(double (&acc)[M], double *__restrict__ partial)
+{
+    __shared__ double sh[M][kRedThreads / 32];
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int m = 0; m < M; m++) {
+        double v = acc[m];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) sh[m][wid] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < M) {
+        double v = 0;
+        for (int w = 0; w < kRedThreads / 32; w++) v += sh[threadIdx.x][w];
+        partial[(size_t)blockIdx.x * M + threadIdx.x] = v;
+    }
+}
+
+template <int M>
+__global__ void k_red_final(const double *__restrict__ partial, int rows, double *__restrict__ out)
+{
+    // one CTA; thread m sums column m in FP64 (rows is small)
+    for (int m = threadIdx.x; m < M; m += blockDim.x) {
+        double s = 0;
+        for (int r = 0; r < rows; r++) s += partial[(size_t)r * M + m];
+        out[m] = s;
+    }
+}
+
+// ---- norm: sum |psi_i|^2
+template <typename R>
+__global__ void k_red_norm(const typename V2T<R>::T *__restrict__ a, uint64_t N, double *partial)
+{
+    double acc[1] = {0};
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x * 8;
+    for (uint64_t base = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) * 8; base < N; base += stride) {
+        R run = 0;
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            if (base + j < N) {
+                auto v = a[base + j];
+                run = fma(v.x, v.x, run);
+                run = fma(v.y, v.y, run);
+            }
+        }
+        acc[0] += (double)run;
+    }
+    block_write<1>(acc, partial);
+}
+
+// ---- P(q = 1): partial[0] = sum over bit q = 1, partial[1] = total
+template <typename R>
+__global__ void k_red_prob1(const typename V2T<R>::T *__restrict__ a, uint64_t N, uint64_t qb, double *partial)
+{
+    double acc[2] = {0, 0};
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x * 8;
+    for (uint64_t base = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) * 8; base < N; base += stride) {
+        R one = 0, all = 0;
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            uint64_t i = base + j;
+            if (i < N) {
+                auto v = a[i];
+                R p = v.x * v.x + v.y * v.y;
+                all += p;
+                one += (i & qb) ? p : R(0);
+            }
+        }
+        acc[0] += (double)one;
+        acc[1] += (double)all;
+    }
+    block_write<2>(acc, partial);
+}
+
+// ---- <a|b> = sum conj(a_i) b_i
+template <typename R>
+__global__ void k_red_inner(const typename V2T<R>::T *__restrict__ a, const typename V2T<R>::T *__restrict__ b,
+                            uint64_t N, double *partial)
+{
+    double acc[2] = {0, 0};
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x * 8;
+    for (uint64_t base = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) * 8; base < N; base += stride) {
+        R re = 0, im = 0;
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            if (base + j < N) {
+                auto x = a[base + j];
+                auto y = b[base + j];
+                re = fma(x.x, y.x, re);
+                re = fma(x.y, y.y, re);
+                im = fma(x.x, y.y, im);
+                im = fma(-x.y, y.x, im);
+            }
+        }
+        acc[0] += (double)re;
+        acc[1] += (double)im;
+    }
+    block_write<2>(acc, partial);
+}
+
+// ---- Bloch sums of one qubit over pairs (a = bit 0, b = bit 1):
+// partial = [sum |a|^2, sum |b|^2, Re sum conj(a) b, Im sum conj(a) b]
+template <typename R>
+__global__ void k_red_bloch(const typename V2T<R>::T *__restrict__ a, uint64_t npairs, int q, double *partial)
+{
+    double acc[4] = {0, 0, 0, 0};
+    uint64_t qb = 1ull << q, lomask = qb - 1;
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x * 4;
+    for (uint64_t base = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4; base < npairs; base += stride) {
+        R s0 = 0, s1 = 0, sr = 0, si = 0;
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            uint64_t w = base + j;
+            if (w < npairs) {
+                uint64_t i0 = ((w & ~lomask) << 1) | (w & lomask);
+                auto x = a[i0];
+                auto y = a[i0 | qb];
+                s0 = fma(x.x, x.x, fma(x.y, x.y, s0));
+                s1 = fma(y.x, y.x, fma(y.y, y.y, s1));
+                sr = fma(x.x, y.x, fma(x.y, y.y, sr));
+                si = fma(x.x, y.y, fma(-x.y, y.x, si));
+            }
+        }
+        acc[0] += (double)s0;
+        acc[1] += (double)s1;
+        acc[2] += (double)sr;
+        acc[3] += (double)si;
+    }
+    block_write<4>(acc, partial);
+}
+
+// ---- Bloch sums of several qubits in one pass. Each CTA iteration stages a
+// tile of 2^t amplitudes whose index bits are the physical qubits tq[0..t-1]
+// (tq[0..c-1] = 0..c-1, so every tile row is a contiguous run), then for
+// each tile qubit j accumulates [sum_{bit 1} |psi|^2, Re S_j, Im S_j] and, for
+// j == 0 only, the total sum |psi|^2. Output row per CTA: 1 + 3t doubles.
+static const int kTileRow = 1 + 3 * 16;   // partial row of the tiled Bloch pass
+
+struct TileSpec {
+    int n, t, c;
+    int tq[16];       // tile qubits, tq[0..c-1] = 0..c-1, rest ascending
+    InsSpec ins;      // high tile qubits to insert when expanding a tile id
+};
+
+__device__ __forceinline__ uint64_t tile_expand(uint64_t w, const InsSpec &ins)
+{
+    for (int j = 0; j < ins.npos; j++) {
+        int p = ins.pos[j];
+        uint64_t lo = w & ((1ull << p) - 1);
+        w = ((w >> p) << (p + 1)) | lo;
+    }
+    return w;
+}
+
+template <typename R>
+__global__ void k_red_bloch_tile(const typename V2T<R>::T *__restrict__ a, TileSpec ts, double *partial)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    typename V2T<R>::T *tile = (typename V2T<R>::T *)smraw;
+    const int t = ts.t, c = ts.c;
+    const uint64_t T = 1ull << t, runs = T >> c, runlen = 1ull << c;
+    const uint64_t ntiles = 1ull << (ts.n - t);
+    __shared__ double bacc[kTileRow];
+    for (int m = threadIdx.x; m < kTileRow; m += blockDim.x) bacc[m] = 0;
+    double tot = 0;
+
+    for (uint64_t tid = blockIdx.x; tid < ntiles; tid += gridDim.x) {
+        // tile base: insert zeros at the high tile qubits, after the low c bits
+        uint64_t base = tile_expand(tid << c, ts.ins);
+        __syncthreads();
+        for (uint64_t e = threadIdx.x; e < T; e += blockDim.x) {
+            uint64_t run = e >> c, off = e & (runlen - 1);
+            uint64_t idx = base | off;
+            for (int j = c; j < t; j++)
+                if ((run >> (j - c)) & 1) idx |= 1ull << ts.tq[j];
+            tile[e] = a[idx];
+        }
+        __syncthreads();
+        // total |psi|^2
+        {
+            R run = 0;
+            for (uint64_t e = threadIdx.x; e < T; e += blockDim.x) {
+                auto v = tile[e];
+                run = fma(v.x, v.x, fma(v.y, v.y, run));
+            }
+            tot += (double)run;
+        }
+        for (int j = 0; j < t; j++) {
+            R s1 = 0, sr = 0, si = 0;
+            uint64_t jb = 1ull << j, lom = jb - 1;
+            for (uint64_t w = threadIdx.x; w < T / 2; w += blockDim.x) {
+                uint64_t e0 = ((w & ~lom) << 1) | (w & lom);
+                auto x = tile[e0];
+                auto y = tile[e0 | jb];
+                s1 = fma(y.x, y.x, fma(y.y, y.y, s1));
+                sr = fma(x.x, y.x, fma(x.y, y.y, sr));
+                si = fma(x.x, y.y, fma(-x.y, y.x, si));
+            }
+            double d1 = s1, dr = sr, di = si;
+            for (int o = 16; o > 0; o >>= 1) {
+                d1 += __shfl_down_sync(0xffffffffu, d1, o);
+                dr += __shfl_down_sync(0xffffffffu, dr, o);
+                di += __shfl_down_sync(0xffffffffu, di, o);
+            }
+            if ((threadIdx.x & 31) == 0) {
+                atomicAdd(&bacc[1 + 3 * j], d1);
+                atomicAdd(&bacc[2 + 3 * j], dr);
+                atomicAdd(&bacc[3 + 3 * j], di);
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) tot += __shfl_down_sync(0xffffffffu, tot, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&bacc[0], tot);
+    __syncthreads();
+    for (int m = threadIdx.x; m < kTileRow; m += blockDim.x) partial[(size_t)blockIdx.x * kTileRow + m] = bacc[m];
+}
+
+template <typename R>
+__global__ void k_probs(const typename V2T<R>::T *__restrict__ a, uint64_t N, double *__restrict__ out)
+{
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+        auto v = a[i];
+        double re = v.x, im = v.y;
+        out[i] = re * re + im * im;
+    }
+}
+
+// ------------------------------------------------------------- host side
+
+qsim_status ensure_scratch(Scratch &sc, size_t doubles)
+{
+    if (sc.cap >= doubles) return QSIM_OK;
+    free_scratch(sc);
+    QS_CUDA(cudaMalloc(&sc.d, doubles * sizeof(double)));
+    QS_CUDA(cudaMallocHost(&sc.h, 64 * sizeof(double)));
+    sc.cap = doubles;
+    return QSIM_OK;
+}
+
+void free_scratch(Scratch &sc)
+{
+    if (sc.d) cudaFree(sc.d);
+    if (sc.h) cudaFreeHost(sc.h);
+    sc.d = nullptr;
+    sc.h = nullptr;
+    sc.cap = 0;
+}
+
+static int red_blocks(uint64_t items)
+{
+    uint64_t b = (items + kRedThreads - 1) / kRedThreads;
+    return (int)std::max<uint64_t>(1, std::min<uint64_t>(b, kMaxRedBlocks));
+}
+
+// Final FP64 combine of `rows` x M partials into red.h[0..M-1] (syncs).
+template <int M>
+static qsim_status finish(qsim_state *s, int rows)
+{
+    double *dout = s->red.d + (size_t)kMaxRedBlocks * 64;
+    k_red_final<M><<<1, 64, 0, s->stream>>>(s->red.d, rows, dout);
+    QS_CUDA(cudaGetLastError());
+    QS_CUDA(cudaMemcpyAsync(s->red.h, dout, M * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    QS_CUDA(cudaStreamSynchronize(s->stream));
+    return QSIM_OK;
+}
+
+static qsim_status ensure_red(qsim_state *s)
+{
+    return ensure_scratch(s->red, (size_t)kMaxRedBlocks * 64 + 64);
+}
+
+qsim_status reduce_norm(qsim_state *s, double *out)
+{
+    QS_TRY(ensure_red(s));
+    uint64_t N = s->N();
+    int blocks = red_blocks((N + 7) / 8);
+    if (s->dt == QSIM_C64)
+        k_red_norm<float><<<blocks, kRedThreads, 0, s->stream>>>((const float2 *)s->amps, N, s->red.d);
+    else
+        k_red_norm<double><<<blocks, kRedThreads, 0, s->stream>>>((const double2 *)s->amps, N, s->red.d);
+    QS_CUDA(cudaGetLastError());
+    QS_TRY(finish<1>(s, blocks));
+    *out = s->red.h[0];
+    return QSIM_OK;
+}
+
+qsim_status reduce_prob1(qsim_state *s, int q, double *p1, double *total)
+{
+    QS_TRY(ensure_red(s));
+    uint64_t N = s->N();
+    int blocks = red_blocks((N + 7) / 8);
+    if (s->dt == QSIM_C64)
+        k_red_prob1<float><<<blocks, kRedThreads, 0, s->stream>>>((const float2 *)s->amps, N, bit(q), s->red.d);
+    else
+        k_red_prob1<double><<<blocks, kRedThreads, 0, s->stream>>>((const double2 *)s->amps, N, bit(q), s->red.d);
+    QS_CUDA(cudaGetLastError());
+    QS_TRY(finish<2>(s, blocks));
+    *p1 = s->red.h[0];
+    *total = s->red.h[1];
+    return QSIM_OK;
+}
+
+qsim_status reduce_inner(qsim_state *a, qsim_state *b, double out[2])
+{
+    QS_TRY(ensure_red(a));
+    uint64_t N = a->N();
+    int blocks = red_blocks((N + 7) / 8);
+    if (a->stream != b->stream) QS_CUDA(cudaStreamSynchronize(b->stream));
+    if (a->dt == QSIM_C64)
+        k_red_inner<float><<<blocks, kRedThreads, 0, a->stream>>>((const float2 *)a->amps, (const float2 *)b->amps, N,
+                                                                  a->red.d);
+    else
+        k_red_inner<double><<<blocks, kRedThreads, 0, a->stream>>>((const double2 *)a->amps,
+                                                                   (const double2 *)b->amps, N, a->red.d);
+    QS_CUDA(cudaGetLastError());
+    QS_TRY(finish<2>(a, blocks));
+    out[0] = a->red.h[0];
+    out[1] = a->red.h[1];
+    return QSIM_OK;
+}
+
+qsim_status reduce_bloch(qsim_state *s, int q, double out4[4])
+{
+    QS_TRY(ensure_red(s));
+    uint64_t np = s->N() / 2;
+    int blocks = red_blocks((np + 3) / 4);
+    if (s->dt == QSIM_C64)
+        k_red_bloch<float><<<blocks, kRedThreads, 0, s->stream>>>((const float2 *)s->amps, np, q, s->red.d);
+    else
+        k_red_bloch<double><<<blocks, kRedThreads, 0, s->stream>>>((const double2 *)s->amps, np, q, s->red.d);
+    QS_CUDA(cudaGetLastError());
+    QS_TRY(finish<4>(s, blocks));
+    for (int k = 0; k < 4; k++) out4[k] = s->red.h[k];
+    return QSIM_OK;
+}
+
+// Bloch sums of every physical qubit: sums[4q..4q+3] = [sum_{bit0}|psi|^2,
+// sum_{bit1}|psi|^2, Re S_q, Im S_q]. One tiled pass covers the t tile
+// qubits; the low c qubits ride along in every pass.
+qsim_status reduce_bloch_all(qsim_state *s, double *sums)
+{
+    const int n = s->n;
+    int t = std::min(n, s->dt == QSIM_C64 ? 12 : 11);
+    int c = std::min(t, 4);
+    std::vector<int> done(n, 0);
+    int next_high = c;
+    QS_TRY(ensure_red(s));
+    while (true) {
+        TileSpec ts;
+        ts.n = n;
+        ts.t = t;
+        ts.c = c;
+        for (int j = 0; j < c; j++) ts.tq[j] = j;
+        int h = 0;
+        std::vector<int> high;
+        for (int q = next_high; q < n && h < t - c; q++) {
+            high.push_back(q);
+            h++;
+        }
+        // pad with already-covered qubits when fewer remain (keeps t fixed)
+        for (int q = n - 1; (int)high.size() < t - c && q >= c; q--)
+            if (std::find(high.begin(), high.end(), q) == high.end()) high.push_back(q);
+        std::sort(high.begin(), high.end());
+        for (int j = 0; j < t - c; j++) ts.tq[c + j] = high[j];
+        ts.ins.npos = t - c;
+        for (int j = 0; j < t - c; j++) ts.ins.pos[j] = high[j];
+        uint64_t ntiles = 1ull << (n - t);
+        int blocks = (int)std::min<uint64_t>(ntiles, kMaxRedBlocks);
+        size_t smem = ((size_t)1 << t) * (s->dt == QSIM_C64 ? 8 : 16);
+        if (s->dt == QSIM_C64) {
+            cudaFuncSetAttribute(k_red_bloch_tile<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            k_red_bloch_tile<float><<<blocks, kRedThreads, smem, s->stream>>>((const float2 *)s->amps, ts, s->red.d);
+        } else {
+            cudaFuncSetAttribute(k_red_bloch_tile<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            k_red_bloch_tile<double><<<blocks, kRedThreads, smem, s->stream>>>((const double2 *)s->amps, ts,
+                                                                              s->red.d);
+        }
+        QS_CUDA(cudaGetLastError());
+        QS_TRY(finish<kTileRow>(s, blocks));
+        double hbuf[kTileRow];
+        for (int m = 0; m < kTileRow; m++) hbuf[m] = s->red.h[m];
+        double total = hbuf[0];
+        for (int j = 0; j < t; j++) {
+            int q = ts.tq[j];
+            if (done[q]) continue;
+            double one = hbuf[1 + 3 * j];
+            sums[4 * q + 0] = total - one;
+            sums[4 * q + 1] = one;
+            sums[4 * q + 2] = hbuf[2 + 3 * j];
+            sums[4 * q + 3] = hbuf[3 + 3 * j];
+            done[q] = 1;
+        }
+        next_high += t - c;
+        bool all = true;
+        for (int q = 0; q < n; q++) all = all && done[q];
+        if (all) break;
+    }
+    return QSIM_OK;
+}
+
+qsim_status probs_to_device(qsim_state *s, double *d_out)
+{
+    uint64_t N = s->N();
+    if (s->dt == QSIM_C64)
+        k_probs<float><<<default_grid(N, 256), 256, 0, s->stream>>>((const float2 *)s->amps, N, d_out);
+    else
+        k_probs<double><<<default_grid(N, 256), 256, 0, s->stream>>>((const double2 *)s->amps, N, d_out);
+    QS_CUDA(cudaGetLastError());
+    return QSIM_OK;
+}
+
+}  // namespace qs

@@ -1,0 +1,107 @@
+// Fused execution plans: the host planner's output and the device-side
+// descriptors of one fused pass.
+//
+// A pass streams the ket through the SMs once: each CTA owns a tile of 2^t
+// amplitudes whose index bits are the c lowest physical qubits (contiguous
+// runs in HBM) plus t - c chosen high qubits. The tile is spread over the
+// CTA as 2^RB registers per thread x 32 lanes x 2^W warps; a "phase" assigns
+// tile bits to register, lane and warp bits, and gates act on register bits
+// only. Changing phase is one transpose through shared memory.
+#pragma once
+
+#include <vector>
+
+#include "qsim_internal.h"
+
+namespace qs {
+
+enum FOpKind : int32_t {
+    FO_G1 = 1,     // dense 2x2 on register bit j0; cf[coef .. +8): u00,u01,u10,u11 (re,im)
+    FO_G1R = 2,    // real 2x2 on j0; cf[coef .. +4)
+    FO_G1X = 3,    // anti-diagonal 2x2 on j0: out0 = u01*b, out1 = u10*a; cf[coef .. +4)
+    FO_G2 = 4,     // dense 4x4 on (j0 = bit 0, j1 = bit 1); cf[coef .. +32)
+    FO_G2M = 5,    // monomial 4x4: out[r] = ph[r] * in[perm[r]]; aux = perm packed 2 bits each; cf: 8
+    FO_DIAGR = 6,  // amplitudes with register bits j0 and j1 set *= cf[coef .. +2)
+    FO_LINR = 7,   // amplitudes with register bit j0 set *= exp(2 pi i turns), turns =
+                   //   tw[coef] + (aux >= 0 ? tw[aux + threadIdx.x] : 0) + ext sum of lin aux2
+    FO_XPOSE = 8,  // transpose through shared memory to map aux
+    FO_SCALE = 9   // every register amplitude *= cf[coef .. +2)
+};
+
+struct FOp {
+    int32_t kind, j0, j1, coef, aux, aux2;
+};
+
+static const int kMaxRB = 5;
+static const int kMaxW = 6;
+static const int kMaxTile = 16;
+
+// Phase map: tile bit of each register, lane and warp bit, plus the tile
+// index and physical offset of each register element x (bit r of x is
+// register bit r).
+struct FMap {
+    int8_t reg[kMaxRB];
+    int8_t lane[5];
+    int8_t warp[kMaxW];
+    int8_t pad[16 - kMaxRB - 5 - kMaxW + 16];
+    uint32_t treg[1 << kMaxRB];
+    uint64_t preg[1 << kMaxRB];
+};
+
+struct FPassDev {
+    int n, t, c, RB, W;
+    int hq[kMaxTile];        // physical bit of tile bit c + j
+    InsSpec ins;             // sorted hq for tile-id expansion
+    int nops;
+    const FOp *ops;
+    const float *cf;         // complex64 coefficients
+    const double *cd;        // complex128 coefficients (same layout)
+    const uint64_t *tw;      // phase turns (2^64 = one turn) and per-thread tables
+    const FMap *maps;
+    int map0;                // load map
+    int nlin;
+    const int32_t *lin_off;  // ext partner list of lin l: [lin_off[l], lin_off[l+1])
+    const int32_t *ext_bit;
+    const uint64_t *ext_tw;
+};
+
+// Host-side plan
+struct PlanPass {
+    FPassDev dev;            // pointers filled at upload
+    int op_begin, op_end;    // into ops
+    int map_begin;           // into maps
+    int lin_begin, nlin;     // into lin_off
+    int ndense;
+};
+
+struct PlanStep {
+    int kind;                // 0 fused pass, 1 per-gate gate (physical qubits), 2 global phase
+    int pass;                // kind 0
+    qsim_gate gate;          // kind 1 (physical qubits, matrix in mats)
+    std::vector<cd> mat;     // kind 1: 2x2 or 4x4
+    cd phase;                // kind 2
+};
+
+struct CircuitPlanner;
+
+}  // namespace qs
+
+struct qsim_plan {
+    int n = 0;
+    qsim_dtype dt = QSIM_C64;
+    int t = 0, c = 0, RB = 0;
+    std::vector<qs::PlanStep> steps;
+    std::vector<qs::PlanPass> passes;
+    std::vector<int> final_l2p;
+    // host arrays
+    std::vector<qs::FOp> ops;
+    std::vector<double> coef;
+    std::vector<uint64_t> tw;
+    std::vector<qs::FMap> maps;
+    std::vector<int32_t> lin_off, ext_bit;
+    std::vector<uint64_t> ext_tw;
+    // device copies
+    void *dmem = nullptr;
+    size_t dbytes = 0;
+    int64_t ngates = 0, ndense = 0, nswaps = 0, npergate = 0;
+};

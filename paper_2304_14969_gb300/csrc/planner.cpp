@@ -1,0 +1,609 @@
+// Fusion planner: turns a circuit into fused passes over the ket.
+//
+// Table I of arXiv 2304.14969 lists the ideas this planner builds on:
+// gates "coalesced ... with a single traversal", SWAP as a constant-cost
+// qubit relabel, and controlled-phase gates "buffered and commuted" rather
+// than applied one by one. Concretely:
+//
+//  * Every gate is classified once (FP64 host matrices). Diagonal gates
+//    (CP, phase, Z/S/T, RZ, controlled diagonals) never move data: they are
+//    decomposed into a global phase, linear terms theta*b_q and pair terms
+//    theta*b_q*b_r, and kept "pending". A pending term commutes with every
+//    gate that does not densely act on its qubits, so it is flushed only
+//    right before the next dense gate on one of its qubits, where it costs
+//    one multiply per amplitude on chip.
+//  * Dense gates (1 qubit, or 2 qubits incl. singly-controlled 1-qubit
+//    gates) are grouped into passes by a commutation-aware sweep: a pass
+//    owns a tile of t qubits (the c lowest physical qubits plus high qubits
+//    added greedily in circuit order while room remains); a gate runs in
+//    the pass when all its qubits are in the tile and no earlier unrun gate
+//    shares a qubit with it.
+//  * Inside a pass, gates act on RB register bits of each thread; a new
+//    "phase" (one transpose through shared memory) brings the next gates'
+//    qubits into registers.
+//  * Gates with two or more controls, and pending terms left at the end,
+//    run through the per-gate kernels.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+
+#include "plan.h"
+
+namespace qs {
+
+qsim_status validate_circuit(const qsim_circuit *c);
+
+namespace {
+
+const double kTiny = 1e-14;
+
+uint64_t to_turns(double theta)
+{
+    long double f = (long double)theta / (2.0L * 3.14159265358979323846264338327950288L);
+    f -= std::floor(f);
+    long double x = f * 18446744073709551616.0L;
+    if (x >= 18446744073709551615.0L) return 0;
+    return (uint64_t)x;
+}
+
+struct Term {
+    int a, b;      // physical bits; b = -1 for a linear term
+    double th;
+};
+
+struct Item {
+    int kind = 0;            // 0 dense, 1 diagonal, 2 barrier
+    int nq = 0;
+    int q[2] = {0, 0};       // physical bits; dense: q[0] = matrix bit 0
+    cd m[16];
+    std::vector<Term> terms; // diagonal
+    cd gphase = 1.0;         // diagonal
+    qsim_gate gate{};        // barrier (physical qubits)
+    std::vector<cd> bmat;
+};
+
+bool is_diag(const cd *m, int d)
+{
+    for (int r = 0; r < d; r++)
+        for (int c = 0; c < d; c++)
+            if (r != c && std::abs(m[r * d + c]) > kTiny) return false;
+    for (int r = 0; r < d; r++)
+        if (std::abs(std::abs(m[r * d + r]) - 1.0) > 1e-12) return false;
+    return true;
+}
+
+void add_term(Item &it, int a, int b, double th)
+{
+    // terms that vanish modulo one turn are dropped
+    if (std::fabs(std::remainder(th, 2.0 * M_PI)) < 1e-15) return;
+    it.terms.push_back({a, b, th});
+}
+
+// Diagonal of phases alpha[idx] on qubits q (q[0] = bit 0) -> terms.
+void diag_terms(const cd *m, int nq, const int *q, Item &it)
+{
+    if (nq == 1) {
+        double a0 = std::arg(m[0]), a1 = std::arg(m[3]);
+        it.gphase *= std::polar(1.0, a0);
+        add_term(it, q[0], -1, a1 - a0);
+    } else {
+        double a[4];
+        for (int k = 0; k < 4; k++) a[k] = std::arg(m[k * 4 + k]);
+        it.gphase *= std::polar(1.0, a[0]);
+        add_term(it, q[0], -1, a[1] - a[0]);
+        add_term(it, q[1], -1, a[2] - a[0]);
+        add_term(it, q[0], q[1], a[3] - a[1] - a[2] + a[0]);
+    }
+}
+
+// ------------------------------------------------------------ pass builder
+
+struct Builder {
+    qsim_plan &P;
+    int n, t, c, RB, W, NT;
+    std::vector<Term> pending;
+    cd gphase = 1.0;
+
+    Builder(qsim_plan &p, int n_, int t_, int c_, int rb) : P(p), n(n_), t(t_), c(c_), RB(rb)
+    {
+        W = t - RB - 5;
+        NT = 1 << (t - RB);
+    }
+
+    int add_coef(const cd *v, int count, bool realonly = false)
+    {
+        int off = (int)P.coef.size();
+        for (int i = 0; i < count; i++) {
+            P.coef.push_back(v[i].real());
+            if (!realonly) P.coef.push_back(v[i].imag());
+        }
+        return off;
+    }
+
+    // -------- per-pass state
+    std::vector<int> tq;         // tau bit -> physical
+    std::vector<int> tau_of;     // physical -> tau bit or -1
+    int reg[kMaxRB], lane[5], warp[kMaxW];
+    int cur_map = -1;
+    int lin_count = 0;
+    PlanPass *pass = nullptr;
+
+    int reg_of_tau(int tb) const
+    {
+        for (int r = 0; r < RB; r++)
+            if (reg[r] == tb) return r;
+        return -1;
+    }
+
+    int push_map()
+    {
+        FMap m;
+        memset(&m, 0, sizeof m);
+        for (int r = 0; r < RB; r++) m.reg[r] = (int8_t)reg[r];
+        for (int l = 0; l < 5; l++) m.lane[l] = (int8_t)lane[l];
+        for (int w = 0; w < W; w++) m.warp[w] = (int8_t)warp[w];
+        for (int x = 0; x < (1 << RB); x++) {
+            uint32_t tt = 0;
+            uint64_t pp = 0;
+            for (int r = 0; r < RB; r++)
+                if ((x >> r) & 1) {
+                    tt |= 1u << reg[r];
+                    pp |= 1ull << tq[reg[r]];
+                }
+            m.treg[x] = tt;
+            m.preg[x] = pp;
+        }
+        P.maps.push_back(m);
+        return (int)P.maps.size() - 1 - pass->map_begin;
+    }
+
+    // Chooses lanes and warps for the tau bits not in registers. load_store:
+    // lanes are the 5 lowest tau bits (coalesced HBM access).
+    void assign_lanes(bool load_store)
+    {
+        std::vector<int> rest;
+        for (int b = 0; b < t; b++)
+            if (reg_of_tau(b) < 0) rest.push_back(b);
+        std::vector<int> ln;
+        if (load_store) {
+            for (int l = 0; l < 5; l++) ln.push_back(l);
+        } else {
+            // cover residues mod 4 (shared-memory swizzle folds bit groups of 4)
+            for (int r = 0; r < 4 && (int)ln.size() < 5; r++)
+                for (int b : rest)
+                    if (b % 4 == r && std::find(ln.begin(), ln.end(), b) == ln.end()) {
+                        ln.push_back(b);
+                        break;
+                    }
+            for (int b : rest)
+                if ((int)ln.size() < 5 && std::find(ln.begin(), ln.end(), b) == ln.end()) ln.push_back(b);
+        }
+        int w = 0;
+        for (int l = 0; l < 5; l++) lane[l] = ln[l];
+        for (int b : rest)
+            if (std::find(ln.begin(), ln.end(), b) == ln.end()) warp[w++] = b;
+    }
+
+    void emit(int kind, int j0, int j1, int coef, int aux, int aux2)
+    {
+        P.ops.push_back(FOp{kind, j0, j1, coef, aux, aux2});
+    }
+
+    // Register set for a new phase starting at dense op i of `ops`.
+    void choose_regs(const std::vector<std::vector<int>> &opt, size_t i, bool exclude_low)
+    {
+        std::vector<int> S;
+        for (size_t j = i; j < opt.size(); j++) {
+            std::vector<int> U = S;
+            bool bad = false;
+            for (int b : opt[j]) {
+                if (exclude_low && b < 5) bad = true;
+                if (std::find(U.begin(), U.end(), b) == U.end()) U.push_back(b);
+            }
+            if (bad || (int)U.size() > RB) break;
+            S = U;
+        }
+        // pad: bits needed soonest by later ops, then the highest tau bits
+        for (size_t j = i; j < opt.size() && (int)S.size() < RB; j++)
+            for (int b : opt[j])
+                if ((int)S.size() < RB && !(exclude_low && b < 5) && std::find(S.begin(), S.end(), b) == S.end())
+                    S.push_back(b);
+        for (int b = t - 1; b >= 0 && (int)S.size() < RB; b--)
+            if (!(exclude_low && b < 5) && std::find(S.begin(), S.end(), b) == S.end()) S.push_back(b);
+        for (int r = 0; r < RB; r++) reg[r] = S[r];
+    }
+
+    // Flushes pending terms touching any physical qubit of `phys` (all in
+    // registers now) into DIAGR / LINR ops.
+    void flush_for(const std::vector<int> &phys)
+    {
+        std::map<std::pair<int, int>, double> diagr;
+        struct Lin { double th0 = 0; std::vector<std::pair<int, double>> tile, ext; };
+        std::map<int, Lin> lins;
+        std::vector<Term> keep;
+        auto touches = [&](int q) { return std::find(phys.begin(), phys.end(), q) != phys.end(); };
+        for (const Term &tm : pending) {
+            if (!touches(tm.a) && !(tm.b >= 0 && touches(tm.b))) {
+                keep.push_back(tm);
+                continue;
+            }
+            int a = tm.a, b = tm.b;
+            if (b >= 0 && !touches(a)) std::swap(a, b);  // a is touched
+            int ra = reg_of_tau(tau_of[a]);
+            if (b < 0) {
+                lins[ra].th0 += tm.th;
+                continue;
+            }
+            int tb = tau_of[b];
+            int rb = tb >= 0 ? reg_of_tau(tb) : -1;
+            if (rb >= 0) {
+                diagr[{std::min(ra, rb), std::max(ra, rb)}] += tm.th;
+            } else if (tb >= 0) {
+                lins[ra].tile.push_back({tb, tm.th});
+            } else {
+                lins[ra].ext.push_back({b, tm.th});
+            }
+        }
+        pending.swap(keep);
+        for (auto &kv : diagr) {
+            cd ph = std::polar(1.0, kv.second);
+            emit(FO_DIAGR, kv.first.first, kv.first.second, add_coef(&ph, 1), 0, 0);
+        }
+        for (auto &kv : lins) {
+            Lin &L = kv.second;
+            int c0 = (int)P.tw.size();
+            P.tw.push_back(to_turns(L.th0));
+            int taux = -1;
+            if (!L.tile.empty()) {
+                taux = (int)P.tw.size();
+                for (int tid = 0; tid < NT; tid++) {
+                    int ln = tid & 31, wp = tid >> 5;
+                    uint32_t tt = 0;
+                    for (int l = 0; l < 5; l++)
+                        if ((ln >> l) & 1) tt |= 1u << lane[l];
+                    for (int w = 0; w < W; w++)
+                        if ((wp >> w) & 1) tt |= 1u << warp[w];
+                    uint64_t s = 0;
+                    for (auto &pt : L.tile)
+                        if ((tt >> pt.first) & 1) s += to_turns(pt.second);
+                    P.tw.push_back(s);
+                }
+            }
+            int li = lin_count++;
+            for (auto &pe : L.ext) {
+                P.ext_bit.push_back(pe.first);
+                P.ext_tw.push_back(to_turns(pe.second));
+            }
+            P.lin_off.push_back((int32_t)P.ext_bit.size());
+            emit(FO_LINR, kv.first, 0, c0, taux, li);
+        }
+    }
+
+    void emit_dense(const Item &it)
+    {
+        if (it.nq == 1) {
+            int r = reg_of_tau(tau_of[it.q[0]]);
+            const cd *m = it.m;
+            bool real = true;
+            for (int k = 0; k < 4; k++) real = real && std::abs(m[k].imag()) < 1e-15;
+            if (std::abs(m[0]) < kTiny && std::abs(m[3]) < kTiny) {
+                cd v[2] = {m[1], m[2]};
+                emit(FO_G1X, r, 0, add_coef(v, 2), 0, 0);
+            } else if (real) {
+                emit(FO_G1R, r, 0, add_coef(m, 4, true), 0, 0);
+            } else {
+                emit(FO_G1, r, 0, add_coef(m, 4), 0, 0);
+            }
+            return;
+        }
+        int r0 = reg_of_tau(tau_of[it.q[0]]), r1 = reg_of_tau(tau_of[it.q[1]]);
+        // monomial?
+        int perm[4];
+        cd ph[4];
+        bool mono = true;
+        for (int r = 0; r < 4 && mono; r++) {
+            int cnt = 0;
+            for (int col = 0; col < 4; col++)
+                if (std::abs(it.m[r * 4 + col]) > kTiny) {
+                    cnt++;
+                    perm[r] = col;
+                    ph[r] = it.m[r * 4 + col];
+                }
+            mono = (cnt == 1);
+        }
+        if (mono) {
+            int packed = perm[0] | (perm[1] << 2) | (perm[2] << 4) | (perm[3] << 6);
+            emit(FO_G2M, r0, r1, add_coef(ph, 4), packed, 0);
+        } else {
+            emit(FO_G2, r0, r1, add_coef(it.m, 16), 0, 0);
+        }
+    }
+
+    // Builds one fused pass over tile `tile_phys` (c low + high bits) from the
+    // in-order list of executed items.
+    void build_pass(const std::vector<int> &high, const std::vector<const Item *> &exec)
+    {
+        P.passes.emplace_back();
+        pass = &P.passes.back();
+        pass->op_begin = (int)P.ops.size();
+        pass->map_begin = (int)P.maps.size();
+        pass->lin_begin = (int)P.lin_off.size();
+        P.lin_off.push_back((int32_t)P.ext_bit.size());
+        lin_count = 0;
+        tq.assign(t, 0);
+        tau_of.assign(n, -1);
+        for (int b = 0; b < c; b++) tq[b] = b;
+        for (int j = 0; j < t - c; j++) tq[c + j] = high[j];
+        for (int b = 0; b < t; b++) tau_of[tq[b]] = b;
+
+        std::vector<std::vector<int>> opt;  // tau bits of each dense op
+        for (const Item *it : exec)
+            if (it->kind == 0) {
+                std::vector<int> v;
+                for (int k = 0; k < it->nq; k++) v.push_back(tau_of[it->q[k]]);
+                opt.push_back(v);
+            }
+        // phase 0 (load): lanes = tau 0..4, registers exclude them
+        choose_regs(opt, 0, true);
+        assign_lanes(true);
+        pass->dev.map0 = push_map();
+        size_t di = 0;
+        int ndense = 0;
+        for (const Item *it : exec) {
+            if (it->kind == 1) {
+                for (const Term &tm : it->terms) pending.push_back(tm);
+                gphase *= it->gphase;
+                continue;
+            }
+            bool in_regs = true;
+            for (int k = 0; k < it->nq; k++) in_regs = in_regs && reg_of_tau(tau_of[it->q[k]]) >= 0;
+            if (!in_regs) {
+                choose_regs(opt, di, false);
+                assign_lanes(false);
+                emit(FO_XPOSE, 0, 0, 0, push_map(), 0);
+            }
+            std::vector<int> ph(it->q, it->q + it->nq);
+            flush_for(ph);
+            emit_dense(*it);
+            di++;
+            ndense++;
+        }
+        // store: lanes = tau 0..4 and no register on them
+        bool store_ok = true;
+        for (int r = 0; r < RB; r++) store_ok = store_ok && reg[r] >= 5;
+        for (int l = 0; l < 5; l++) store_ok = store_ok && lane[l] == l;
+        if (!store_ok) {
+            std::vector<std::vector<int>> none;
+            choose_regs(none, 0, true);
+            assign_lanes(true);
+            emit(FO_XPOSE, 0, 0, 0, push_map(), 0);
+        }
+        pass->op_end = (int)P.ops.size();
+        pass->nlin = lin_count;
+        pass->ndense = ndense;
+        FPassDev &d = pass->dev;
+        memset(&d, 0, sizeof d);
+        d.n = n;
+        d.t = t;
+        d.c = c;
+        d.RB = RB;
+        d.W = W;
+        for (int j = 0; j < t - c; j++) d.hq[j] = high[j];
+        std::vector<int> s(high.begin(), high.end());
+        std::sort(s.begin(), s.end());
+        d.ins.npos = (int)s.size();
+        for (size_t j = 0; j < s.size(); j++) d.ins.pos[j] = s[j];
+        d.nops = pass->op_end - pass->op_begin;
+        d.nlin = lin_count;
+        d.map0 = 0;
+    }
+};
+
+}  // namespace
+
+qsim_status plan_build(const qsim_circuit *cir, qsim_dtype dt, const qsim_run_opts *opts, qsim_plan *P)
+{
+    const int n = cir->n;
+    qsim_run_opts o{};
+    if (opts) o = *opts;
+    int RB = 4;
+    int t = o.tile_qubits ? o.tile_qubits : (dt == QSIM_C64 ? 13 : 12);
+    int c = 5;
+    if (o.low_qubits && o.low_qubits != 5) return fail(QSIM_E_UNSUPPORTED, "low_qubits must be 5 (warp lanes)");
+    if (t > n) t = n;
+    if (t < RB + 5) return fail(QSIM_E_UNSUPPORTED, "fused path needs n >= %d", RB + 5);
+    if (t - RB - 5 > kMaxW || t > kMaxTile) return fail(QSIM_E_INVAL, "tile_qubits %d too large", t);
+    if (t - c > 12) return fail(QSIM_E_INVAL, "tile_qubits %d too large", t);
+    P->n = n;
+    P->dt = dt;
+    P->t = t;
+    P->c = c;
+    P->RB = RB;
+    P->ngates = cir->ngates;
+    bool relabel = opts ? (o.relabel_swaps != 0 || o.mode == QSIM_MODE_FUSED) : true;
+
+    // ---- classify gates into items (physical bits after relabels)
+    std::vector<int> l2p(n);
+    for (int q = 0; q < n; q++) l2p[q] = q;
+    std::vector<Item> items;
+    items.reserve(cir->ngates);
+    for (int k = 0; k < cir->ngates; k++) {
+        const qsim_gate &g = cir->gates[k];
+        cd m[16];
+        int d = gate_matrix(g, cir->matrices, cir->nmatrix_doubles, m);
+        Item it;
+        if (g.kind == QSIM_G_SWAP && relabel) {
+            std::swap(l2p[g.q0], l2p[g.q1]);
+            P->nswaps++;
+            continue;
+        }
+        if (d == 2 && g.ncontrols >= 2) {
+            it.kind = 2;
+            it.gate = g;
+            it.gate.q0 = l2p[g.q0];
+            for (int j = 0; j < g.ncontrols; j++) it.gate.controls[j] = l2p[g.controls[j]];
+            it.bmat.assign(m, m + 4);
+            items.push_back(it);
+            continue;
+        }
+        if (d == 2 && g.ncontrols == 1) {
+            // 4x4 on (target = bit 0, control = bit 1)
+            cd M[16];
+            for (int z = 0; z < 16; z++) M[z] = 0.0;
+            int cv = (int)(g.control_values & 1);
+            for (int bc = 0; bc < 2; bc++)
+                for (int r = 0; r < 2; r++)
+                    for (int col = 0; col < 2; col++)
+                        M[(r + 2 * bc) * 4 + (col + 2 * bc)] = (bc == cv) ? m[r * 2 + col] : cd(r == col ? 1.0 : 0.0);
+            memcpy(m, M, sizeof M);
+            d = 4;
+            it.q[0] = l2p[g.q0];
+            it.q[1] = l2p[g.controls[0]];
+        } else if (d == 2) {
+            it.q[0] = l2p[g.q0];
+        } else {
+            it.q[0] = l2p[g.q0];
+            it.q[1] = l2p[g.q1];
+        }
+        it.nq = d == 2 ? 1 : 2;
+        if (is_diag(m, d)) {
+            it.kind = 1;
+            diag_terms(m, it.nq, it.q, it);
+        } else {
+            it.kind = 0;
+            for (int z = 0; z < d * d; z++) it.m[z] = m[z];
+        }
+        items.push_back(it);
+    }
+    P->final_l2p = l2p;
+
+    // ---- passes
+    Builder B(*P, n, t, c, RB);
+    std::vector<const Item *> rem;
+    for (auto &it : items) rem.push_back(&it);
+    auto item_qubits = [](const Item *it, std::vector<int> &v) {
+        v.clear();
+        if (it->kind == 2) {
+            v.push_back(it->gate.q0);
+            for (int j = 0; j < it->gate.ncontrols; j++) v.push_back(it->gate.controls[j]);
+        } else if (it->kind == 1) {
+            for (const Term &tm : it->terms) {
+                if (std::find(v.begin(), v.end(), tm.a) == v.end()) v.push_back(tm.a);
+                if (tm.b >= 0 && std::find(v.begin(), v.end(), tm.b) == v.end()) v.push_back(tm.b);
+            }
+        } else {
+            for (int k = 0; k < it->nq; k++) v.push_back(it->q[k]);
+        }
+    };
+    auto flush_all_pergate = [&]() {
+        for (const Term &tm : B.pending) {
+            PlanStep st;
+            st.kind = 1;
+            memset(&st.gate, 0, sizeof st.gate);
+            if (tm.b < 0) {
+                st.gate.kind = QSIM_G_PHASE;
+                st.gate.q0 = tm.a;
+                st.mat = {1.0, 0.0, 0.0, std::polar(1.0, tm.th)};
+            } else {
+                st.gate.kind = QSIM_G_CP;
+                st.gate.q0 = tm.a;
+                st.gate.q1 = tm.b;
+                st.gate.params[0] = tm.th;
+            }
+            P->steps.push_back(st);
+            P->npergate++;
+        }
+        B.pending.clear();
+    };
+    std::vector<int> qv;
+    while (!rem.empty()) {
+        // grow the tile in circuit order
+        std::vector<int> tile;  // high qubits
+        std::vector<char> in_tile(n, 0), blocked(n, 0);
+        for (int b = 0; b < c; b++) in_tile[b] = 1;
+        std::vector<const Item *> exec, left;
+        int ndense = 0;
+        for (const Item *it : rem) {
+            item_qubits(it, qv);
+            bool blk = false;
+            for (int q : qv) blk = blk || blocked[q];
+            if (!blk && it->kind == 1) {
+                exec.push_back(it);
+                continue;
+            }
+            if (!blk && it->kind == 0) {
+                int need = 0;
+                for (int q : qv) need += !in_tile[q];
+                if ((int)tile.size() + need <= t - c) {
+                    for (int q : qv)
+                        if (!in_tile[q]) {
+                            in_tile[q] = 1;
+                            tile.push_back(q);
+                        }
+                    exec.push_back(it);
+                    ndense++;
+                    continue;
+                }
+            }
+            for (int q : qv) blocked[q] = 1;
+            left.push_back(it);
+        }
+        if (ndense == 0) {
+            // only diagonal items and barriers remain runnable: fold the
+            // diagonal ones, then run the first barrier per gate
+            for (const Item *it : exec) {
+                for (const Term &tm : it->terms) B.pending.push_back(tm);
+                B.gphase *= it->gphase;
+            }
+            if (left.empty()) {
+                rem.clear();
+                break;
+            }
+            const Item *bar = left.front();
+            flush_all_pergate();
+            PlanStep st;
+            st.kind = 1;
+            st.gate = bar->gate;
+            st.mat = bar->bmat;
+            P->steps.push_back(st);
+            P->npergate++;
+            left.erase(left.begin());
+            rem = left;
+            continue;
+        }
+        // fill the tile with unused high qubits
+        for (int q = n - 1; q >= c && (int)tile.size() < t - c; q--)
+            if (!in_tile[q]) {
+                in_tile[q] = 1;
+                tile.push_back(q);
+            }
+        std::sort(tile.begin(), tile.end());
+        B.build_pass(tile, exec);
+        PlanStep st;
+        st.kind = 0;
+        st.pass = (int)P->passes.size() - 1;
+        P->steps.push_back(st);
+        P->ndense += ndense;
+        rem = left;
+    }
+    // global phase: into the last fused pass, else a per-gate step
+    if (std::abs(B.gphase - cd(1.0)) > 1e-15) {
+        if (!P->passes.empty() && P->steps.back().kind == 0) {
+            PlanPass &ps = P->passes.back();
+            cd g = B.gphase;
+            P->ops.push_back(FOp{FO_SCALE, 0, 0, B.add_coef(&g, 1), 0, 0});
+            ps.op_end = (int)P->ops.size();
+            ps.dev.nops = ps.op_end - ps.op_begin;
+        } else {
+            PlanStep st;
+            st.kind = 2;
+            st.phase = B.gphase;
+            P->steps.push_back(st);
+        }
+    }
+    flush_all_pergate();
+    return QSIM_OK;
+}
+
+}  // namespace qs

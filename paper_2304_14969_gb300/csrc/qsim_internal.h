@@ -1,0 +1,104 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <complex>
+#include <string>
+#include <vector>
+
+#include "../../include/qsim.h"
+
+namespace qs {
+
+// ------------------------------------------------------------ errors
+qsim_status fail(qsim_status st, const char *fmt, ...);
+qsim_status cuda_fail(cudaError_t e, const char *what);
+void clear_error();
+const char *g_last_error_cstr();
+
+#define QS_CUDA(expr)                                              \
+    do {                                                           \
+        cudaError_t _e = (expr);                                   \
+        if (_e != cudaSuccess) return ::qs::cuda_fail(_e, #expr);  \
+    } while (0)
+
+#define QS_TRY(expr)                                \
+    do {                                            \
+        qsim_status _s = (expr);                    \
+        if (_s != QSIM_OK) return _s;               \
+    } while (0)
+
+// ------------------------------------------------------- host matrices
+using cd = std::complex<double>;
+
+// Matrix of a named gate kind in FP64 (2x2 or 4x4, row-major). Returns the
+// dimension, 0 for an unknown kind. pool: matrix pool of the circuit.
+int gate_matrix(const qsim_gate &g, const double *pool, int64_t pool_len, cd *m);
+bool gate_is_two_qubit_kind(int kind);
+// Validates a gate against n qubits; returns QSIM_OK or QSIM_E_INVAL (with
+// the error message set).
+qsim_status validate_gate(const qsim_gate &g, int n, const double *pool, int64_t pool_len);
+// True when the gate's matrix is diagonal (phase-only) in its qubits.
+bool gate_is_diagonal(const qsim_gate &g);
+
+// ------------------------------------------------------- device state
+struct Scratch {
+    double *d = nullptr;     // device partials
+    double *h = nullptr;     // pinned host results
+    size_t cap = 0;          // doubles in d
+};
+
+}  // namespace qs
+
+struct qsim_state {
+    int n = 0;
+    qsim_dtype dt = QSIM_C64;
+    cudaStream_t stream = nullptr;
+    void *amps = nullptr;
+    bool owned = false;
+    int device = 0;
+    std::vector<int> l2p;    // logical qubit -> physical bit
+    qs::Scratch red;
+    size_t amp_bytes() const { return (size_t)(dt == QSIM_C64 ? 8 : 16) << n; }
+    uint64_t N() const { return (uint64_t)1 << n; }
+};
+
+namespace qs {
+
+// Bit positions are physical unless stated otherwise.
+struct InsSpec {
+    int npos = 0;
+    int pos[12] = {0};  // ascending
+};
+
+// ------------------------------------------------------ kernel launchers
+// (all stream-ordered, no sync; return cuda errors)
+cudaError_t launch_gate1(qsim_state *s, const cd u[4], int t, uint64_t cmask, uint64_t cval);
+cudaError_t launch_gate2(qsim_state *s, const cd u[16], int q0, int q1);
+cudaError_t launch_cphase(qsim_state *s, int q0, int q1, double theta);
+cudaError_t launch_swap(qsim_state *s, int q0, int q1);
+cudaError_t launch_fused_simt(qsim_state *s, int k, const int *phys, const cd *u);
+cudaError_t launch_set_basis(qsim_state *s, uint64_t x_phys);
+cudaError_t launch_scale(void *amps, qsim_dtype dt, uint64_t N, double f, cudaStream_t st);
+cudaError_t launch_permute(const void *src, void *dst, qsim_dtype dt, int n, const int *new_of_old,
+                           cudaStream_t st);
+
+// Reductions (write FP64 results into s->red.h after a stream sync).
+qsim_status reduce_norm(qsim_state *s, double *out);
+qsim_status reduce_prob1(qsim_state *s, int phys_q, double *p1, double *total);
+qsim_status reduce_inner(qsim_state *a, qsim_state *b, double out[2]);
+qsim_status reduce_bloch(qsim_state *s, int phys_q, double out4[4]);
+qsim_status reduce_bloch_all(qsim_state *s, double *sums /* 4 per physical qubit */);
+qsim_status probs_to_device(qsim_state *s, double *d_out);
+
+// Generic device buffers ("raw" kets used by approx mode).
+qsim_status ensure_scratch(Scratch &sc, size_t doubles);
+void free_scratch(Scratch &sc);
+
+// Helpers
+inline uint64_t bit(int q) { return (uint64_t)1 << q; }
+int default_grid(uint64_t work, int threads);
+
+}  // namespace qs

@@ -1,0 +1,262 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle
+on the same seeded inputs.
+
+Tolerances (state infidelity 1 - |<a|b>|^2 / (<a|a><b|b>)): <= 1e-12 for
+complex128 kets, <= 1e-6 for complex64 kets; probabilities and reductions
+within the rounding of the ket's precision; index order exact."""
+import ctypes as C
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2304_14969_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL_INF = {0: 1e-6, 1: 1e-12}
+
+
+@pytest.fixture(scope="module")
+def Q():
+    from paper_2304_14969_gb300 import build, qsim
+    build.build()
+    qsim.lib()
+    return qsim
+
+
+def infid(a, b):
+    a = np.asarray(a, dtype=np.complex128)
+    b = np.asarray(b, dtype=np.complex128)
+    ov = np.vdot(a, b)
+    return 1.0 - abs(ov) ** 2 / (np.vdot(a, a).real * np.vdot(b, b).real)
+
+
+def run_gpu(Q, n, gates, psi0, dt, mode=0, relabel=0, tile=0):
+    st = Q.State(n, dt)
+    st.upload(psi0)
+    st.run(Q.Circuit(n, gates), mode=mode, relabel=relabel, tile=tile)
+    out = st.download()
+    st.close()
+    return out
+
+
+# ------------------------------------------------------------ per-gate path
+
+@pytest.mark.parametrize("dt", [0, 1])
+@pytest.mark.parametrize("n,seed", [(1, 0), (2, 1), (5, 2), (11, 3)])
+def test_per_gate_every_kind_vs_oracle(Q, dt, n, seed):
+    g = W.random_1q_circuit(n, 120, seed)
+    x = W.gaussian_state(n, seed)
+    ref = oracle.apply_circuit(x, g)
+    for relabel in (0, 1):
+        y = run_gpu(Q, n, g, x, dt, relabel=relabel)
+        assert infid(y, ref) <= TOL_INF[dt]
+        tol = 1e-12 if dt else 5e-6
+        assert np.max(np.abs(y - ref)) <= tol
+
+
+@pytest.mark.parametrize("dt", [0, 1])
+def test_per_gate_every_position(Q, dt):
+    n = 8
+    x = W.gaussian_state(n, 5)
+    g = []
+    for t in range(n):
+        g.append(W.Gate("u3", (t,), (0.3 + t, 0.2, 1.1)))
+        for c in range(n):
+            if c != t:
+                g.append(W.Gate("cp", (c, t), (0.1 * (c + 1),)))
+                g.append(W.Gate("x", (t,), (), (c,), ((c + t) % 2,)))
+                g.append(W.Gate("fsim", (c, t), (0.4, 0.3 * c)))
+    ref = oracle.apply_circuit(x, g)
+    assert infid(run_gpu(Q, n, g, x, dt), ref) <= TOL_INF[dt]
+
+
+@pytest.mark.parametrize("kind", ["basis", "gauss"])
+def test_qft16_complex128_per_gate(Q, kind):
+    """16-qubit QFT, complex128, per-gate path (144 operations)."""
+    n = 16
+    for seed in range(3):
+        x = W.basis_state(n, W.basis_index(n, seed)) if kind == "basis" else W.gaussian_state(n, seed)
+        g = W.qft_circuit(n)
+        ref = oracle.apply_circuit(x, g)
+        y = run_gpu(Q, n, g, x, 1)
+        assert infid(y, ref) <= 1e-12
+        assert np.max(np.abs(y - ref)) <= 1e-13
+        if kind == "basis":
+            p = np.abs(y) ** 2
+            assert np.max(np.abs(p - 2.0 ** -n)) <= 2 * np.finfo(float).eps * 2.0 ** -n * len(g)
+
+
+# ------------------------------------------------------------- fused path
+
+@pytest.mark.parametrize("dt", [0, 1])
+@pytest.mark.parametrize("n", [9, 10, 13, 14, 17, 20])
+def test_fused_qft_vs_oracle(Q, dt, n):
+    x = W.gaussian_state(n, 40 + n)
+    g = W.qft_circuit(n)
+    ref = oracle.apply_circuit(x, g)
+    y = run_gpu(Q, n, g, x, dt, mode=1)
+    assert infid(y, ref) <= TOL_INF[dt]
+    assert np.max(np.abs(y - ref)) <= (1e-13 if dt else 2e-6 * 2 ** (-n / 2) * 50)
+
+
+@pytest.mark.parametrize("dt", [0, 1])
+@pytest.mark.parametrize("n,seed", [(9, 1), (12, 2), (15, 3)])
+def test_fused_every_kind_vs_oracle(Q, dt, n, seed):
+    g = W.random_1q_circuit(n, 300, seed)
+    x = W.gaussian_state(n, seed)
+    ref = oracle.apply_circuit(x, g)
+    y = run_gpu(Q, n, g, x, dt, mode=1)
+    assert infid(y, ref) <= TOL_INF[dt]
+
+
+@pytest.mark.parametrize("rows,cols,layers", [(3, 4, 10), (4, 6, 6)])
+def test_fused_grid_vs_oracle(Q, rows, cols, layers):
+    n = rows * cols
+    g = W.grid_rcs_circuit(rows, cols, layers, seed=7)
+    x = W.basis_state(n, 0)
+    ref = oracle.apply_circuit(x, g)
+    for dt in (0, 1):
+        y = run_gpu(Q, n, g, x, dt, mode=1)
+        assert infid(y, ref) <= TOL_INF[dt]
+    y = run_gpu(Q, n, g, x, 1, mode=0)
+    assert infid(y, ref) <= 1e-12
+
+
+def test_fused_tile_sizes(Q):
+    n = 16
+    x = W.gaussian_state(n, 3)
+    g = W.random_1q_circuit(n, 200, 9)
+    ref = oracle.apply_circuit(x, g)
+    for tile in (9, 11, 13, 14):
+        assert infid(run_gpu(Q, n, g, x, 0, mode=1, tile=tile), ref) <= 1e-6
+
+
+# --------------------------------------------------------- full-size QFT
+
+def sampled_error(Q, st, x, n, idx):
+    y = st.download()
+    num = den = 0.0
+    for j in idx:
+        r = oracle.dft_sample(x, j)
+        num += abs(y[j] - r) ** 2
+        den += abs(r) ** 2
+    return y, num / den
+
+
+def test_qft27_full_size_sampled(Q):
+    """27 qubits, the benchmark's launch configuration: complex64 fused and
+    complex128 per-gate, sampled outputs against Eq. (dft) evaluated one by
+    one, plus norm preservation at full size."""
+    n = 27
+    x = W.gaussian_state(n, 0)
+    idx = [0, 1, 12345, (1 << n) - 1, 98765432]
+    circ = Q.Circuit(n, W.qft_circuit(n))
+    st = Q.State(n, 0)
+    st.upload(x)
+    plan = Q.Plan(circ, dtype=0)
+    plan.execute(st)
+    assert abs(st.norm() - 1.0) < 1e-5
+    y, err = sampled_error(Q, st, x, n, idx)
+    assert err <= 1e-6
+    st.close()
+    st = Q.State(n, 1)
+    st.upload(x)
+    st.run(circ, mode=0, relabel=1)
+    y, err = sampled_error(Q, st, x, n, idx)
+    assert err <= 1e-12
+    assert abs(st.norm() - 1.0) < 1e-12
+    st.close()
+
+
+# ------------------------------------------------------------- reductions
+
+@pytest.mark.parametrize("dt", [0, 1])
+def test_reductions_vs_oracle(Q, dt):
+    n = 14
+    x = W.gaussian_state(n, 21)
+    g = W.random_1q_circuit(n, 60, 4) + [W.Gate("swap", (0, 9)), W.Gate("swap", (3, 13))]
+    ref = oracle.apply_circuit(x, g)
+    st = Q.State(n, dt)
+    st.upload(x)
+    st.run(Q.Circuit(n, g), mode=0, relabel=1)
+    assert not np.array_equal(st.qubit_map(), np.arange(n))   # a permuted layout
+    tol = 1e-13 if dt else 2e-6
+    assert abs(st.norm() - oracle.norm2(ref)) <= tol
+    p = st.probs()
+    assert np.max(np.abs(p - oracle.probs(ref))) <= (1e-15 if dt else 1e-7)
+    assert int(np.argmax(p)) == int(np.argmax(oracle.probs(ref)))
+    for q in range(n):
+        assert abs(st.prob1(q) - oracle.prob1(ref, q)) <= tol
+        assert np.max(np.abs(st.bloch(q) - oracle.bloch(ref, q))) <= tol
+    allr = st.bloch_all()
+    for q in range(n):
+        assert np.max(np.abs(allr[q] - oracle.bloch(ref, q))) <= tol
+    other = Q.State(n, dt)
+    z = W.gaussian_state(n, 22)
+    other.upload(z)
+    ip = st.inner(other)
+    assert abs(ip - oracle.inner(ref, z)) <= tol
+    st.close()
+    other.close()
+
+
+def test_bloch_all_large(Q):
+    n = 22
+    x = W.gaussian_state(n, 2)
+    st = Q.State(n, 0)
+    st.upload(x)
+    r = st.bloch_all()
+    for q in (0, 5, 11, 17, 21):
+        assert np.max(np.abs(r[q] - oracle.bloch(x, q))) <= 2e-6
+    st.close()
+
+
+# ------------------------------------------------------------ fused blocks
+
+@pytest.mark.parametrize("dt", [0, 1])
+@pytest.mark.parametrize("k", [1, 2, 3, 5, 7])
+def test_apply_fused_native(Q, dt, k):
+    n = 12
+    x = W.gaussian_state(n, 3)
+    rng = np.random.default_rng(k)
+    qs = [int(v) for v in rng.choice(n, size=k, replace=False)]
+    U = W.random_unitary(k, 10 + k)
+    ref = oracle.apply_kq(x, qs, U)
+    st = Q.State(n, dt)
+    st.upload(x)
+    qa = (C.c_int * k)(*qs)
+    u = np.ascontiguousarray(U.ravel().view(np.float64))
+    Q.qsim_apply_fused(st.h, k, qa, u.ctypes.data_as(C.c_void_p), Q.QSIM_PREC_NATIVE)
+    y = st.download()
+    assert infid(y, ref) <= TOL_INF[dt]
+    st.close()
+
+
+# --------------------------------------------------------------- edges
+
+def test_edge_cases_and_errors(Q):
+    st = Q.State(1, 1)
+    Q.qsim_set_basis(st.h, 1)
+    assert np.allclose(st.download(), [0, 1])
+    h = Q.u2(np.array([[1, 1], [1, -1]]) / math.sqrt(2))
+    Q.qsim_apply_gate(st.h, h.ctypes.data_as(C.c_void_p), 0, None, 0, 0)
+    assert np.allclose(st.download(), [2 ** -0.5, -(2 ** -0.5)])
+    before = st.download()
+    with pytest.raises(Q.QsimError) as e:
+        Q.qsim_apply_gate(st.h, h.ctypes.data_as(C.c_void_p), 1, None, 0, 0)
+    assert e.value.status == 1
+    with pytest.raises(Q.QsimError):
+        Q.qsim_set_basis(st.h, 2)
+    assert np.array_equal(st.download(), before)
+    st.close()
+    # a wrapped torch-owned buffer
+    torch = pytest.importorskip("torch")
+    t = torch.zeros(1 << 6, dtype=torch.complex64, device="cuda")
+    t[5] = 1.0
+    w = Q.State(6, 0, dev_ptr=t.data_ptr())
+    assert abs(w.prob1(0) - 1.0) < 1e-7 and abs(w.prob1(1)) < 1e-7
+    w.close()
+    del t
