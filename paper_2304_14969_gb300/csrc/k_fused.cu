@@ -198,7 +198,6 @@ __device__ __forceinline__ void op_g2m(V (&v)[NR], const R *__restrict__ u, int 
         QS_CASE2(4, 0, CALL) QS_CASE2(4, 1, CALL) QS_CASE2(4, 2, CALL) QS_CASE2(4, 3, CALL)                  \
     }
 
-static const int kMaxLin = 256;
 
 template <typename R, int RB, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB) k_fused_pass(typename FV<R>::T *__restrict__ a, FPassDev P)
@@ -207,7 +206,9 @@ __global__ void __launch_bounds__(NT, MINB) k_fused_pass(typename FV<R>::T *__re
     constexpr int NR = 1 << RB;
     extern __shared__ __align__(16) unsigned char smraw[];
     V *sm = (V *)smraw;
-    __shared__ uint64_t E[kMaxLin];
+    // per-CTA sums of the LINR ops' partners outside the tile (nlin entries
+    // after the 2^t-element transpose buffer)
+    uint64_t *E = (uint64_t *)(smraw + ((size_t)sizeof(V) << P.t));
     __shared__ int s_hq[kMaxTile], s_pos[12];
     if (threadIdx.x < kMaxTile) s_hq[threadIdx.x] = P.hq[threadIdx.x];
     if (threadIdx.x < 12) s_pos[threadIdx.x] = P.ins.pos[threadIdx.x];
@@ -381,7 +382,8 @@ template <typename R, int NT, int MINB>
 cudaError_t launch_pass_t(void *amps, const FPassDev &d, cudaStream_t st)
 {
     using V = typename FV<R>::T;
-    size_t smem = (size_t)sizeof(V) << d.t;
+    size_t smem = ((size_t)sizeof(V) << d.t) + (size_t)d.nlin * sizeof(uint64_t);
+    if (smem > 200 * 1024) return cudaErrorInvalidValue;
     auto kern = k_fused_pass<R, 4, NT, MINB>;
     static bool attr = false;
     if (!attr) {
