@@ -435,7 +435,8 @@ void orc_sdrp_project(cplx *psi, int n, int q, const double r[3])
  * |0...0>); every qubit starts in its own subsystem.
  *
  * Subsystem bookkeeping is membership only: a two-qubit gate (or a
- * controlled one-qubit gate) merges the subsystems of its qubits; after it,
+ * controlled one-qubit gate) merges the subsystems of its qubits, except a
+ * SWAP, which only exchanges the two qubits' memberships; after a merge,
  * every qubit of the merged subsystem is checked in ascending global id,
  * one after the other, while that subsystem still holds two or more
  * qubits. A check computes r and eps = (1 - |r|)/2; eps <= p/2 rounds
@@ -461,6 +462,13 @@ int orc_sdrp_run(cplx *psi, int n, const orc_gate *g, int ng, double p, double t
     for (int k = 0; k < ng; k++) {
         const orc_gate *gk = &g[k];
         if (orc_apply_gate(psi, n, gk)) return -1;
+        if (gk->kind == OG_SWAP) {
+            /* a SWAP entangles nothing: the two qubits trade subsystems */
+            int t = sys[gk->q[0]];
+            sys[gk->q[0]] = sys[gk->q[1]];
+            sys[gk->q[1]] = t;
+            continue;
+        }
         int two = 0, a = -1, b = -1;
         cplx m[16];
         int d = orc_gate_matrix(gk, m);

@@ -1,0 +1,461 @@
+// Approximate mode: SDRP rounding on a factorised ket (arXiv 2304.14969,
+// Sec. II.A and Sec. III.A-B).
+//
+// The ket is kept as a tensor product of subsystem kets (Sec. II.A, "as
+// factorized as possible"); every subsystem lives in its own device buffer
+// with local bit b holding global qubit qs[b]. A two-qubit gate spanning two
+// subsystems first composes them (Kronecker product); a SWAP is a relabel
+// (Table I). After every entangling gate the qubits of the touched subsystem
+// are checked in ascending global id: the Bloch sums of all its qubits come
+// from one tiled FP64 reduction, a one-thread kernel forms
+// r = (<X>, <Y>, <Z>), eps = (1 - |r|)/2 (step 2) and picks the first
+// candidate with eps <= p/2 (SDRP rounding, Eq. sdrp) or eps <= tau (exact
+// separation); that qubit is projected onto the dominant Schmidt branch
+// |phi> (steps 2-4 collapse to <phi|_q applied to the subsystem, then an
+// FP64 renormalisation) and becomes a one-qubit subsystem holding |phi>.
+// F <- F (1 - eps) for each rounding (Eq. fid_model). Candidates after the
+// rounded one are checked again on the new, smaller subsystem.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <memory>
+
+#include "qsim_internal.h"
+
+namespace qs {
+
+qsim_status validate_circuit(const qsim_circuit *c);
+
+template <typename R> struct AV;
+template <> struct AV<float> { using T = float2; };
+template <> struct AV<double> { using T = double2; };
+
+// C[ia + (ib << ma)] = A[ia] * B[ib]
+template <typename R>
+__global__ void k_kron(const typename AV<R>::T *__restrict__ A, int ma, const typename AV<R>::T *__restrict__ B,
+                       uint64_t nb, typename AV<R>::T *__restrict__ Cc)
+{
+    uint64_t total = nb << ma, stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
+        auto a = A[i & ((1ull << ma) - 1)];
+        auto b = B[i >> ma];
+        typename AV<R>::T o;
+        o.x = a.x * b.x - a.y * b.y;
+        o.y = a.x * b.y + a.y * b.x;
+        Cc[i] = o;
+    }
+}
+
+// dst[j] = conj(f0) src[j with bit b = 0] + conj(f1) src[j with bit b = 1]
+template <typename R>
+__global__ void k_project(const typename AV<R>::T *__restrict__ src, int b, uint64_t nout, double f0r, double f0i,
+                          double f1r, double f1i, typename AV<R>::T *__restrict__ dst)
+{
+    const R c0r = (R)f0r, c0i = (R)-f0i, c1r = (R)f1r, c1i = (R)-f1i;
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x, lo = (1ull << b) - 1;
+    for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nout; j += stride) {
+        uint64_t i0 = ((j & ~lo) << 1) | (j & lo);
+        auto x = src[i0], y = src[i0 | (1ull << b)];
+        typename AV<R>::T o;
+        o.x = c0r * x.x - c0i * x.y + c1r * y.x - c1i * y.y;
+        o.y = c0r * x.y + c0i * x.x + c1r * y.y + c1i * y.x;
+        dst[j] = o;
+    }
+}
+
+template <typename R>
+__global__ void k_put2(typename AV<R>::T *__restrict__ d, double a0r, double a0i, double a1r, double a1i)
+{
+    d[0].x = (R)a0r;
+    d[0].y = (R)a0i;
+    d[1].x = (R)a1r;
+    d[1].y = (R)a1i;
+}
+
+struct Decide {
+    int32_t first;       // index into the candidate list of the first acted-on qubit, or ncand
+    int32_t action;      // 1 rounded, 2 exact, 0 none
+    int32_t examined;
+    int32_t pad;
+    double eps[64];
+    double r[64][3];
+    double phi[4];       // |phi> of the acted-on qubit (re0, im0, re1, im1)
+};
+
+// Sec. III.A step 2 in FP64 on the device: for candidates in order, r from
+// the Bloch sums, eps = (1 - |r|)/2, stop at the first eps <= p/2 (round) or
+// eps <= tau (exact separation). |phi> = (cos(th/2), e^{i ph} sin(th/2)),
+// th = acos(r_z/|r|), ph = atan2(r_y, r_x); +z when |r| < 1e-15.
+__global__ void k_decide(const double *__restrict__ sums, const int *__restrict__ cand, int ncand, double p,
+                         double tau, Decide *__restrict__ out)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    out->first = ncand;
+    out->action = 0;
+    int k = 0;
+    for (; k < ncand; k++) {
+        const double *s = sums + 4 * cand[k];
+        double tr = s[0] + s[1];
+        double r0 = 2.0 * s[2] / tr, r1 = 2.0 * s[3] / tr, r2 = (s[0] - s[1]) / tr;
+        double len = sqrt(r0 * r0 + r1 * r1 + r2 * r2);
+        double eps = (1.0 - len) / 2.0;
+        out->eps[k] = eps;
+        out->r[k][0] = r0;
+        out->r[k][1] = r1;
+        out->r[k][2] = r2;
+        int act = eps <= p / 2.0 ? 1 : (eps <= tau ? 2 : 0);
+        if (act) {
+            double th = 0.0, ph = 0.0;
+            if (len >= 1e-15) {
+                double cz = fmin(1.0, fmax(-1.0, r2 / len));
+                th = acos(cz);
+                ph = atan2(r1, r0);
+            }
+            double ch = cos(th / 2.0), sh = sin(th / 2.0);
+            out->phi[0] = ch;
+            out->phi[1] = 0.0;
+            out->phi[2] = cos(ph) * sh;
+            out->phi[3] = sin(ph) * sh;
+            out->first = k;
+            out->action = act;
+            k++;
+            break;
+        }
+    }
+    out->examined = k;
+}
+
+namespace {
+
+struct Sub {
+    std::vector<int> qs;   // local bit -> global qubit
+    void *d = nullptr;
+    size_t bytes = 0;
+};
+
+struct Run {
+    int n = 0;
+    qsim_dtype dt = QSIM_C64;
+    cudaStream_t st = nullptr;
+    size_t es = 8;
+    double budget = 0;
+    size_t cur = 0, peak = 0;
+    std::vector<std::unique_ptr<Sub>> subs;
+    std::vector<int> sys_of;  // global qubit -> index in subs
+    Scratch sc;
+    double *d_sums = nullptr;
+    int *d_cand = nullptr;
+    Decide *d_dec = nullptr, *h_dec = nullptr;
+    int64_t bloch_passes = 0;
+
+    ~Run()
+    {
+        cudaStreamSynchronize(st);
+        for (auto &s : subs)
+            if (s && s->d) cudaFree(s->d);
+        if (d_sums) cudaFree(d_sums);
+        if (d_cand) cudaFree(d_cand);
+        if (d_dec) cudaFree(d_dec);
+        if (h_dec) cudaFreeHost(h_dec);
+        free_scratch(sc);
+    }
+
+    qsim_status alloc(Sub &s, int m)
+    {
+        s.bytes = es << m;
+        QS_CUDA(cudaMallocAsync(&s.d, s.bytes, st));
+        cur += s.bytes;
+        peak = std::max(peak, cur);
+        return QSIM_OK;
+    }
+    void release(Sub &s)
+    {
+        if (s.d) cudaFreeAsync(s.d, st);
+        cur -= s.bytes;
+        s.d = nullptr;
+        s.bytes = 0;
+    }
+
+    qsim_state view(Sub &s)
+    {
+        qsim_state v;
+        v.n = (int)s.qs.size();
+        v.dt = dt;
+        v.stream = st;
+        v.amps = s.d;
+        v.owned = false;
+        v.l2p.resize(v.n);
+        for (int b = 0; b < v.n; b++) v.l2p[b] = b;
+        return v;
+    }
+
+    int local(const Sub &s, int q) const
+    {
+        for (size_t b = 0; b < s.qs.size(); b++)
+            if (s.qs[b] == q) return (int)b;
+        return -1;
+    }
+
+    // merge subsystem j into i (i keeps its low bits)
+    qsim_status compose(int i, int j)
+    {
+        Sub &A = *subs[i], &B = *subs[j];
+        int ma = (int)A.qs.size(), mb = (int)B.qs.size();
+        size_t nb = es << (ma + mb);
+        if ((double)(cur + nb) > budget) return fail(QSIM_E_BUDGET, "composing %d+%d qubits exceeds the budget", ma, mb);
+        Sub C;
+        C.qs = A.qs;
+        C.qs.insert(C.qs.end(), B.qs.begin(), B.qs.end());
+        QS_TRY(alloc(C, ma + mb));
+        uint64_t total = 1ull << (ma + mb);
+        int grid = default_grid(total, 256);
+        if (dt == QSIM_C64)
+            k_kron<float><<<grid, 256, 0, st>>>((const float2 *)A.d, ma, (const float2 *)B.d, 1ull << mb, (float2 *)C.d);
+        else
+            k_kron<double><<<grid, 256, 0, st>>>((const double2 *)A.d, ma, (const double2 *)B.d, 1ull << mb,
+                                                 (double2 *)C.d);
+        QS_CUDA(cudaGetLastError());
+        release(A);
+        release(B);
+        A = C;
+        C.d = nullptr;
+        for (int q : A.qs) sys_of[q] = i;
+        subs[j].reset();
+        return QSIM_OK;
+    }
+
+    // projects qubit at local bit b of subsystem i onto phi and splits it off
+    qsim_status split(int i, int b, const double phi[4])
+    {
+        Sub &S = *subs[i];
+        int m = (int)S.qs.size();
+        int q = S.qs[b];
+        Sub R;
+        R.qs = S.qs;
+        R.qs.erase(R.qs.begin() + b);
+        QS_TRY(alloc(R, m - 1));
+        uint64_t nout = 1ull << (m - 1);
+        int grid = default_grid(nout, 256);
+        if (dt == QSIM_C64)
+            k_project<float><<<grid, 256, 0, st>>>((const float2 *)S.d, b, nout, phi[0], phi[1], phi[2], phi[3],
+                                                  (float2 *)R.d);
+        else
+            k_project<double><<<grid, 256, 0, st>>>((const double2 *)S.d, b, nout, phi[0], phi[1], phi[2], phi[3],
+                                                   (double2 *)R.d);
+        QS_CUDA(cudaGetLastError());
+        release(S);
+        S = R;
+        R.d = nullptr;
+        // renormalise by the computed FP64 norm (Sec. III.A step 3)
+        qsim_state v = view(S);
+        v.red = sc;
+        double nrm = 0;
+        qsim_status stt = reduce_norm(&v, &nrm);
+        sc = v.red;
+        v.red = Scratch();
+        QS_TRY(stt);
+        if (!(nrm > 0)) return fail(QSIM_E_CUDA, "projected ket has zero norm");
+        QS_CUDA(launch_scale(S.d, dt, 1ull << (m - 1), 1.0 / std::sqrt(nrm), st));
+        // the new one-qubit factor
+        auto F = std::make_unique<Sub>();
+        F->qs = {q};
+        QS_TRY(alloc(*F, 1));
+        if (dt == QSIM_C64) k_put2<float><<<1, 1, 0, st>>>((float2 *)F->d, phi[0], phi[1], phi[2], phi[3]);
+        else k_put2<double><<<1, 1, 0, st>>>((double2 *)F->d, phi[0], phi[1], phi[2], phi[3]);
+        QS_CUDA(cudaGetLastError());
+        subs.push_back(std::move(F));
+        sys_of[q] = (int)subs.size() - 1;
+        return QSIM_OK;
+    }
+};
+
+}  // namespace
+}  // namespace qs
+
+using namespace qs;
+
+extern "C" qsim_status qsim_approx_run(const qsim_circuit *c, double p, const qsim_approx_opts *opts,
+                                       qsim_approx_result *res)
+{
+    clear_error();
+    QS_TRY(validate_circuit(c));
+    if (!res) return fail(QSIM_E_INVAL, "result is NULL");
+    if (!(p >= 0.0 && p <= 1.0)) return fail(QSIM_E_INVAL, "p=%g outside [0, 1]", p);
+    qsim_approx_opts o{};
+    if (opts) o = *opts;
+    if (o.dtype != QSIM_C64 && o.dtype != QSIM_C128) return fail(QSIM_E_INVAL, "unknown dtype");
+    if (o.schedule == QSIM_SCHED_MLP) return fail(QSIM_E_UNSUPPORTED, "MLP schedule is not available in this build");
+    if (o.schedule == QSIM_SCHED_FORCED && o.nforce > 0 && !o.force) return fail(QSIM_E_INVAL, "force is NULL");
+    if (o.state_out && c->n > 30) return fail(QSIM_E_INVAL, "state_out needs n <= 30");
+    memset(res, 0, sizeof *res);
+    res->budget_gate = -1;
+    auto t0 = std::chrono::steady_clock::now();
+
+    Run R;
+    R.n = c->n;
+    R.dt = (qsim_dtype)o.dtype;
+    R.es = R.dt == QSIM_C64 ? 8 : 16;
+    R.st = (cudaStream_t)o.stream;
+    R.budget = o.budget_bytes > 0 ? o.budget_bytes : 64.0 * (1ull << 30);
+    double tau = o.tau > 0 ? o.tau : (R.dt == QSIM_C64 ? 1e-6 : 1e-13);
+    const int n = c->n;
+    R.sys_of.resize(n);
+    QS_CUDA(cudaMalloc(&R.d_sums, 4 * sizeof(double) * 64));
+    QS_CUDA(cudaMalloc(&R.d_cand, sizeof(int) * 64));
+    QS_CUDA(cudaMalloc(&R.d_dec, sizeof(Decide)));
+    QS_CUDA(cudaMallocHost(&R.h_dec, sizeof(Decide)));
+    for (int q = 0; q < n; q++) {
+        auto s = std::make_unique<Sub>();
+        s->qs = {q};
+        QS_TRY(R.alloc(*s, 1));
+        if (R.dt == QSIM_C64) k_put2<float><<<1, 1, 0, R.st>>>((float2 *)s->d, 1, 0, 0, 0);
+        else k_put2<double><<<1, 1, 0, R.st>>>((double2 *)s->d, 1, 0, 0, 0);
+        R.subs.push_back(std::move(s));
+        R.sys_of[q] = q;
+    }
+    QS_CUDA(cudaGetLastError());
+
+    double F = 1.0;
+    int64_t nlog = 0, nround = 0, nexact = 0, nchecks = 0;
+    int maxsub = 1, fpos = 0;
+    qsim_status status = QSIM_OK;
+    for (int k = 0; k < c->ngates && status == QSIM_OK; k++) {
+        const qsim_gate &g = c->gates[k];
+        cd m[16];
+        int d = gate_matrix(g, c->matrices, c->nmatrix_doubles, m);
+        if (g.kind == QSIM_G_SWAP) {
+            int a = g.q0, b = g.q1, ia = R.sys_of[a], ib = R.sys_of[b];
+            Sub &A = *R.subs[ia], &B = *R.subs[ib];
+            A.qs[R.local(A, a)] = -1;
+            B.qs[R.local(B, b)] = a;
+            A.qs[R.local(A, -1)] = b;
+            R.sys_of[a] = ib;
+            R.sys_of[b] = ia;
+            continue;
+        }
+        std::vector<int> touched;
+        touched.push_back(g.q0);
+        if (d == 4) touched.push_back(g.q1);
+        for (int j = 0; j < g.ncontrols; j++) touched.push_back(g.controls[j]);
+        int si = R.sys_of[touched[0]];
+        for (size_t j = 1; j < touched.size() && status == QSIM_OK; j++) {
+            int sj = R.sys_of[touched[j]];
+            if (sj != si) {
+                status = R.compose(si, sj);
+                if (status == QSIM_E_BUDGET) res->budget_gate = k;
+            }
+        }
+        if (status != QSIM_OK) break;
+        Sub &S = *R.subs[si];
+        maxsub = std::max(maxsub, (int)S.qs.size());
+        qsim_state v = R.view(S);
+        if (d == 2) {
+            uint64_t cmask = 0, cval = 0;
+            for (int j = 0; j < g.ncontrols; j++) {
+                uint64_t bb = bit(R.local(S, g.controls[j]));
+                cmask |= bb;
+                if ((g.control_values >> j) & 1) cval |= bb;
+            }
+            QS_CUDA(launch_gate1(&v, m, R.local(S, g.q0), cmask, cval));
+        } else if (g.kind == QSIM_G_CP) {
+            QS_CUDA(launch_cphase(&v, R.local(S, g.q0), R.local(S, g.q1), g.params[0]));
+        } else {
+            QS_CUDA(launch_gate2(&v, m, R.local(S, g.q0), R.local(S, g.q1)));
+        }
+        if (touched.size() < 2) continue;
+
+        // ---- checks (Sec. III.A) on the touched subsystem
+        std::vector<int> cand;
+        if (o.schedule == QSIM_SCHED_FORCED) {
+            while (fpos < o.nforce && o.force[2 * fpos] == k) cand.push_back(o.force[2 * fpos++ + 1]);
+        } else {
+            cand = R.subs[si]->qs;
+            std::sort(cand.begin(), cand.end());
+        }
+        size_t ci = 0;
+        while (ci < cand.size()) {
+            // skip candidates whose subsystem is a single qubit now
+            int q = cand[ci];
+            Sub &Sq = *R.subs[R.sys_of[q]];
+            if (Sq.qs.size() < 2) {
+                ci++;
+                continue;
+            }
+            int sidx = R.sys_of[q];
+            // the run of following candidates in the same subsystem
+            std::vector<int> loc;
+            size_t cj = ci;
+            while (cj < cand.size() && R.sys_of[cand[cj]] == sidx && loc.size() < 64) loc.push_back(R.local(Sq, cand[cj++]));
+            int passes = 0;
+            QS_TRY(bloch_sums_device(Sq.d, R.dt, (int)Sq.qs.size(), R.st, R.sc, R.d_sums, &passes));
+            R.bloch_passes += passes;
+            QS_CUDA(cudaMemcpyAsync(R.d_cand, loc.data(), sizeof(int) * loc.size(), cudaMemcpyHostToDevice, R.st));
+            k_decide<<<1, 1, 0, R.st>>>(R.d_sums, R.d_cand, (int)loc.size(), p, tau, R.d_dec);
+            QS_CUDA(cudaGetLastError());
+            QS_CUDA(cudaMemcpyAsync(R.h_dec, R.d_dec, sizeof(Decide), cudaMemcpyDeviceToHost, R.st));
+            QS_CUDA(cudaStreamSynchronize(R.st));
+            const Decide &D = *R.h_dec;
+            for (int e = 0; e < D.examined; e++) {
+                int qq = cand[ci + e];
+                int act = (e == D.first) ? D.action : 0;
+                if (o.log && nlog < o.log_cap) {
+                    qsim_decision &L = o.log[nlog];
+                    L.gate = k;
+                    L.qubit = qq;
+                    L.action = act;
+                    L.reserved = 0;
+                    L.eps = D.eps[e];
+                    for (int z = 0; z < 3; z++) L.r[z] = D.r[e][z];
+                }
+                nlog++;
+                nchecks++;
+            }
+            if (D.action == 0) {
+                ci += D.examined;
+                continue;
+            }
+            double phi[4] = {D.phi[0], D.phi[1], D.phi[2], D.phi[3]};
+            int qa = cand[ci + D.first];
+            if (D.action == 1) {
+                F *= (1.0 - D.eps[D.first]);
+                nround++;
+            } else {
+                nexact++;
+            }
+            QS_TRY(R.split(sidx, R.local(Sq, qa), phi));
+            ci += D.examined;
+        }
+    }
+    res->fidelity_model = F;
+    res->n_rounds = nround;
+    res->n_exact = nexact;
+    res->n_checks = nchecks;
+    res->n_bloch_passes = R.bloch_passes;
+    res->peak_bytes = (int64_t)R.peak;
+    res->n_log = nlog;
+    res->max_subsystem_qubits = maxsub;
+    if (status != QSIM_OK) {
+        res->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        return status;
+    }
+    // ---- expand the factors into the full ket (validation, Eq. fid_exact)
+    if (o.state_out) {
+        std::vector<int> live;
+        for (size_t i = 0; i < R.subs.size(); i++)
+            if (R.subs[i]) live.push_back((int)i);
+        R.budget = 1e300;
+        for (size_t j = 1; j < live.size(); j++) QS_TRY(R.compose(live[0], live[j]));
+        Sub &A = *R.subs[live[0]];
+        std::vector<int> to(n);
+        for (int b = 0; b < n; b++) to[b] = A.qs[b];
+        void *tmp = nullptr;
+        QS_CUDA(cudaMallocAsync(&tmp, A.bytes, R.st));
+        QS_CUDA(launch_permute(A.d, tmp, R.dt, n, to.data(), R.st));
+        QS_CUDA(cudaMemcpyAsync(o.state_out, tmp, A.bytes, cudaMemcpyDeviceToHost, R.st));
+        cudaFreeAsync(tmp, R.st);
+    }
+    QS_CUDA(cudaStreamSynchronize(R.st));
+    res->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return QSIM_OK;
+}

@@ -200,142 +200,163 @@ __device__ __forceinline__ void op_g2m(V (&v)[NR], const R *__restrict__ u, int 
 
 
 template <typename R, int RB, int NT, int MINB>
-__global__ void __launch_bounds__(NT, MINB) k_fused_pass(typename FV<R>::T *__restrict__ a, FPassDev P)
+__global__ void __launch_bounds__(NT, MINB) k_fused_pass(typename FV<R>::T *__restrict__ a, FPassDev P,
+                                                         uint64_t ntiles)
 {
     using V = typename FV<R>::T;
     constexpr int NR = 1 << RB;
     extern __shared__ __align__(16) unsigned char smraw[];
     V *sm = (V *)smraw;
-    // per-CTA sums of the LINR ops' partners outside the tile (nlin entries
-    // after the 2^t-element transpose buffer)
-    uint64_t *E = (uint64_t *)(smraw + ((size_t)sizeof(V) << P.t));
+    const size_t tile_bytes = (size_t)sizeof(V) << P.t;
+    // per-CTA sums of the LINR ops' partners outside the tile
+    uint64_t *E = (uint64_t *)(smraw + tile_bytes);
+    // the pass's constant block (ops, coefficients, turns, maps, partners)
+    unsigned char *stg = smraw + tile_bytes + (((size_t)P.nlin * 8 + 15) & ~(size_t)15);
     __shared__ int s_hq[kMaxTile], s_pos[12];
-    if (threadIdx.x < kMaxTile) s_hq[threadIdx.x] = P.hq[threadIdx.x];
-    if (threadIdx.x < 12) s_pos[threadIdx.x] = P.ins.pos[threadIdx.x];
-    __syncthreads();
-    const R *cf;
-    if constexpr (sizeof(R) == 4) cf = (const R *)P.cf;
-    else cf = (const R *)P.cd;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    {
+        const int4 *src = (const int4 *)P.stage;
+        int4 *dst = (int4 *)stg;
+        for (int i = tid; i < P.stage_bytes / 16; i += blockDim.x) dst[i] = src[i];
+        if (tid < kMaxTile) s_hq[tid] = P.hq[tid];
+        if (tid < 12) s_pos[tid] = P.ins.pos[tid];
+    }
+    const uint64_t *tw = (const uint64_t *)(stg + P.off_tw);
+    const R *cf = (const R *)(stg + P.off_cf);
+    const FOp *ops = (const FOp *)(stg + P.off_ops);
+    const FMap *maps = (const FMap *)(stg + P.off_maps);
+    const int32_t *lin_off = (const int32_t *)(stg + P.off_lin);
+    const int32_t *ext_bit = (const int32_t *)(stg + P.off_eb);
+    const uint64_t *ext_tw = (const uint64_t *)(stg + P.off_et);
     const int c = P.c;
-    // tile base: the CTA id fills the non-tile bits
-    uint64_t base = (uint64_t)blockIdx.x << c;
-    for (int j = 0; j < P.ins.npos; j++) {
-        int p = s_pos[j];
-        base = ((base >> p) << (p + 1)) | (base & ((1ull << p) - 1));
-    }
-    for (int l = tid; l < P.nlin; l += blockDim.x) {
-        uint64_t s = 0;
-        for (int e = P.lin_off[l]; e < P.lin_off[l + 1]; e++)
-            if ((base >> P.ext_bit[e]) & 1) s += P.ext_tw[e];
-        E[l] = s;
-    }
-    auto tau_phys = [&](int tb) -> int { return tb < c ? tb : s_hq[tb - c]; };
-    const FMap *mp = &P.maps[P.map0];
-    uint32_t tthr = 0;
-    uint64_t pthr = 0;
-    auto thread_bits = [&]() {
-        tthr = 0;
-        pthr = 0;
-#pragma unroll
-        for (int l = 0; l < 5; l++)
-            if ((lane >> l) & 1) {
-                tthr |= 1u << mp->lane[l];
-                pthr |= 1ull << tau_phys(mp->lane[l]);
-            }
-        for (int w = 0; w < P.W; w++)
-            if ((warp >> w) & 1) {
-                tthr |= 1u << mp->warp[w];
-                pthr |= 1ull << tau_phys(mp->warp[w]);
-            }
-    };
-    thread_bits();
-    V v[NR];
-    {
-        const V *src = a + (base | pthr);
-#pragma unroll
-        for (int x = 0; x < NR; x++) v[x] = src[mp->preg[x]];
-    }
-    __syncthreads();
 
-    for (int i = 0; i < P.nops; i++) {
-        const FOp op = P.ops[i];
-        const R *u = cf + op.coef;
-        switch (op.kind) {
-        case FO_G1: {
+    for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        __syncthreads();   // staging done / previous tile finished with E and sm
+        uint64_t base = tile << c;
+        for (int j = 0; j < P.ins.npos; j++) {
+            int p = s_pos[j];
+            base = ((base >> p) << (p + 1)) | (base & ((1ull << p) - 1));
+        }
+        for (int l = tid; l < P.nlin; l += blockDim.x) {
+            uint64_t sacc = 0;
+            for (int e = lin_off[l]; e < lin_off[l + 1]; e++)
+                if ((base >> ext_bit[e]) & 1) sacc += ext_tw[e];
+            E[l] = sacc;
+        }
+        const FMap *mp = &maps[0];
+        uint32_t tthr = 0;
+        uint64_t pthr = 0;
+        auto thread_bits = [&]() {
+            tthr = 0;
+            pthr = 0;
+#pragma unroll
+            for (int l = 0; l < 5; l++)
+                if ((lane >> l) & 1) {
+                    int tb = mp->lane[l];
+                    tthr |= 1u << tb;
+                    pthr |= 1ull << (tb < c ? tb : s_hq[tb - c]);
+                }
+            for (int w = 0; w < P.W; w++)
+                if ((warp >> w) & 1) {
+                    int tb = mp->warp[w];
+                    tthr |= 1u << tb;
+                    pthr |= 1ull << (tb < c ? tb : s_hq[tb - c]);
+                }
+        };
+        thread_bits();
+        V v[NR];
+        {
+            const V *src = a + (base | pthr);
+#pragma unroll
+            for (int x = 0; x < NR; x++) v[x] = src[mp->preg[x]];
+        }
+        __syncthreads();   // E ready
+
+        for (int i = 0; i < P.nops; i++) {
+            const FOp op = ops[i];
+            const R *u = cf + op.coef;
+            switch (op.kind) {
+            case FO_G1: {
 #define QS_C(J) op_g1<J>(v, u)
-            QS_SWITCH1(op.j0, QS_C)
+                QS_SWITCH1(op.j0, QS_C)
 #undef QS_C
-            break;
-        }
-        case FO_G1R: {
+                break;
+            }
+            case FO_G1R: {
 #define QS_C(J) op_g1r<J>(v, u)
-            QS_SWITCH1(op.j0, QS_C)
+                QS_SWITCH1(op.j0, QS_C)
 #undef QS_C
-            break;
-        }
-        case FO_G1X: {
+                break;
+            }
+            case FO_G1X: {
 #define QS_C(J) op_g1x<J>(v, u)
-            QS_SWITCH1(op.j0, QS_C)
+                QS_SWITCH1(op.j0, QS_C)
 #undef QS_C
-            break;
-        }
-        case FO_G2: {
+                break;
+            }
+            case FO_G2: {
+                // dense 4x4 ops are planned only for kernels with <= 16 registers
+                // of amplitudes per thread (register pressure)
+                if constexpr (RB <= 4) {
 #define QS_C(A, B) op_g2<A, B>(v, u)
-            QS_SWITCH2(op.j0 * 8 + op.j1, QS_C)
+                    QS_SWITCH2(op.j0 * 8 + op.j1, QS_C)
 #undef QS_C
-            break;
-        }
-        case FO_G2M: {
+                }
+                break;
+            }
+            case FO_G2M: {
 #define QS_C(A, B) op_g2m<A, B>(v, u, op.aux)
-            QS_SWITCH2(op.j0 * 8 + op.j1, QS_C)
+                QS_SWITCH2(op.j0 * 8 + op.j1, QS_C)
 #undef QS_C
-            break;
-        }
-        case FO_DIAGR: {
-            const R cr = u[0], ci = u[1];
-            int jj = op.j0 * 8 + op.j1;
+                break;
+            }
+            case FO_DIAGR: {
+                const R cr = u[0], ci = u[1];
+                int jj = op.j0 * 8 + op.j1;
 #define QS_C(A, B) op_diagr<A, B>(v, cr, ci)
-            QS_SWITCH2(jj, QS_C)
+                QS_SWITCH2(jj, QS_C)
 #undef QS_C
-            break;
-        }
-        case FO_LINR: {
-            uint64_t tt = P.tw[op.coef] + E[op.aux2];
-            if (op.aux >= 0) tt += P.tw[op.aux + tid];
-            R s, cc;
-            tsincos(tt, s, cc);
-#define QS_C(J) op_lin<J>(v, cc, s)
-            QS_SWITCH1(op.j0, QS_C)
+                break;
+            }
+            case FO_LINR: {
+                uint64_t tt = tw[op.coef] + E[op.aux2];
+                if (op.aux >= 0) tt += tw[op.aux + tid];
+                R sn, cs;
+                tsincos(tt, sn, cs);
+#define QS_C(J) op_lin<J>(v, cs, sn)
+                QS_SWITCH1(op.j0, QS_C)
 #undef QS_C
-            break;
-        }
-        case FO_SCALE: {
-            const R cr = u[0], ci = u[1];
+                break;
+            }
+            case FO_SCALE: {
+                const R cr = u[0], ci = u[1];
 #pragma unroll
-            for (int x = 0; x < NR; x++) v[x] = cmul(v[x], cr, ci);
-            break;
-        }
-        case FO_XPOSE: {
+                for (int x = 0; x < NR; x++) v[x] = cmul(v[x], cr, ci);
+                break;
+            }
+            case FO_XPOSE: {
+                uint32_t sw = swz(tthr, (V *)nullptr);
 #pragma unroll
-            for (int x = 0; x < NR; x++) sm[swz(tthr | mp->treg[x], (V *)nullptr)] = v[x];
-            __syncthreads();
-            mp = &P.maps[op.aux];
-            thread_bits();
+                for (int x = 0; x < NR; x++) sm[sw ^ mp->tsw[x]] = v[x];
+                __syncthreads();
+                mp = &maps[op.aux];
+                thread_bits();
+                sw = swz(tthr, (V *)nullptr);
 #pragma unroll
-            for (int x = 0; x < NR; x++) v[x] = sm[swz(tthr | mp->treg[x], (V *)nullptr)];
-            __syncthreads();
-            break;
+                for (int x = 0; x < NR; x++) v[x] = sm[sw ^ mp->tsw[x]];
+                __syncthreads();
+                break;
+            }
+            default:
+                break;
+            }
         }
-        default:
-            break;
-        }
-    }
-    {
-        V *dst = a + (base | pthr);
+        {
+            V *dst = a + (base | pthr);
 #pragma unroll
-        for (int x = 0; x < NR; x++) dst[mp->preg[x]] = v[x];
+            for (int x = 0; x < NR; x++) dst[mp->preg[x]] = v[x];
+        }
     }
 }
 
@@ -354,45 +375,54 @@ size_t push_bytes(std::vector<unsigned char> &buf, const std::vector<T> &v)
 
 qsim_status plan_upload(qsim_plan *P)
 {
-    std::vector<float> cf(P->coef.begin(), P->coef.end());
     std::vector<unsigned char> buf;
-    size_t o_ops = push_bytes(buf, P->ops), o_cf = push_bytes(buf, cf), o_cd = push_bytes(buf, P->coef),
-           o_tw = push_bytes(buf, P->tw), o_maps = push_bytes(buf, P->maps), o_lin = push_bytes(buf, P->lin_off),
-           o_eb = push_bytes(buf, P->ext_bit), o_et = push_bytes(buf, P->ext_tw);
+    std::vector<size_t> offs;
+    for (PlanPass &ps : P->passes) {
+        size_t off = (buf.size() + 255) & ~(size_t)255;
+        buf.resize(off + ps.stage.size());
+        if (!ps.stage.empty()) memcpy(buf.data() + off, ps.stage.data(), ps.stage.size());
+        offs.push_back(off);
+    }
     if (buf.empty()) buf.resize(256);
     QS_CUDA(cudaMalloc(&P->dmem, buf.size()));
     P->dbytes = buf.size();
     QS_CUDA(cudaMemcpy(P->dmem, buf.data(), buf.size(), cudaMemcpyHostToDevice));
-    unsigned char *d = (unsigned char *)P->dmem;
-    for (PlanPass &ps : P->passes) {
-        FPassDev &x = ps.dev;
-        x.ops = (const FOp *)(d + o_ops) + ps.op_begin;
-        x.cf = (const float *)(d + o_cf);
-        x.cd = (const double *)(d + o_cd);
-        x.tw = (const uint64_t *)(d + o_tw);
-        x.maps = (const FMap *)(d + o_maps) + ps.map_begin;
-        x.lin_off = (const int32_t *)(d + o_lin) + ps.lin_begin;
-        x.ext_bit = (const int32_t *)(d + o_eb);
-        x.ext_tw = (const uint64_t *)(d + o_et);
-    }
+    for (size_t i = 0; i < P->passes.size(); i++)
+        P->passes[i].dev.stage = (const unsigned char *)P->dmem + offs[i];
     return QSIM_OK;
 }
 
-template <typename R, int NT, int MINB>
+int num_sms()
+{
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 152;
+    }
+    return sms;
+}
+
+template <typename R, int RB, int NT, int MINB>
 cudaError_t launch_pass_t(void *amps, const FPassDev &d, cudaStream_t st)
 {
     using V = typename FV<R>::T;
-    size_t smem = ((size_t)sizeof(V) << d.t) + (size_t)d.nlin * sizeof(uint64_t);
-    if (smem > 200 * 1024) return cudaErrorInvalidValue;
-    auto kern = k_fused_pass<R, 4, NT, MINB>;
+    size_t smem = ((size_t)sizeof(V) << d.t) + (((size_t)d.nlin * 8 + 15) & ~(size_t)15) + d.stage_bytes;
+    if (smem > 220 * 1024) return cudaErrorInvalidValue;
+    auto kern = k_fused_pass<R, RB, NT, MINB>;
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
         attr = true;
     }
     uint64_t ntiles = 1ull << (d.n - d.t);
     int threads = 1 << (d.t - d.RB);
-    kern<<<(unsigned)ntiles, threads, smem, st>>>((V *)amps, d);
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
+    if (occ < 1) occ = 1;
+    uint64_t grid = std::min<uint64_t>(ntiles, (uint64_t)num_sms() * occ);
+    kern<<<(unsigned)grid, threads, smem, st>>>((V *)amps, d, ntiles);
     return cudaGetLastError();
 }
 
@@ -400,13 +430,11 @@ cudaError_t launch_pass_t(void *amps, const FPassDev &d, cudaStream_t st)
 
 cudaError_t launch_fused_pass(qsim_state *s, const FPassDev &d)
 {
-    int threads = 1 << (d.t - d.RB);
     if (s->dt == QSIM_C64) {
-        if (threads > 512) return launch_pass_t<float, 1024, 1>(s->amps, d, s->stream);
-        return launch_pass_t<float, 512, 1>(s->amps, d, s->stream);
+        if (d.RB == 5) return launch_pass_t<float, 5, 256, 2>(s->amps, d, s->stream);
+        return launch_pass_t<float, 4, 512, 1>(s->amps, d, s->stream);
     }
-    if (threads > 256) return launch_pass_t<double, 512, 1>(s->amps, d, s->stream);
-    return launch_pass_t<double, 256, 1>(s->amps, d, s->stream);
+    return launch_pass_t<double, 4, 256, 1>(s->amps, d, s->stream);
 }
 
 }  // namespace qs

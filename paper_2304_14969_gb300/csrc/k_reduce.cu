@@ -364,30 +364,41 @@ qsim_status reduce_bloch(qsim_state *s, int q, double out4[4])
     return QSIM_OK;
 }
 
-// Bloch sums of every physical qubit: sums[4q..4q+3] = [sum_{bit0}|psi|^2,
-// sum_{bit1}|psi|^2, Re S_q, Im S_q]. One tiled pass covers the t tile
-// qubits; the low c qubits ride along in every pass.
-qsim_status reduce_bloch_all(qsim_state *s, double *sums)
+// Writes, for every tile qubit j of a finished tiled pass, the four sums
+// [sum_{bit0}|psi|^2, sum_{bit1}|psi|^2, Re S, Im S] of qubit tq[j] into
+// out[4*tq[j] ..] (device), from the FP64 combine of the partial rows.
+__global__ void k_bloch_scatter(const double *__restrict__ comb, TileSpec ts, int first_new, double *__restrict__ out)
 {
-    const int n = s->n;
-    int t = std::min(n, s->dt == QSIM_C64 ? 12 : 11);
+    int j = threadIdx.x;
+    if (j >= ts.t) return;
+    int q = ts.tq[j];
+    if (q < first_new && j >= ts.c) return;   // covered by an earlier pass
+    double total = comb[0], one = comb[1 + 3 * j];
+    out[4 * q + 0] = total - one;
+    out[4 * q + 1] = one;
+    out[4 * q + 2] = comb[2 + 3 * j];
+    out[4 * q + 3] = comb[3 + 3 * j];
+}
+
+// Bloch sums of all n qubits of a ket into d_out[4n] (device), without a
+// host sync: ceil((n - c)/(t - c)) tiled passes, each covering the c low
+// qubits and t - c new high qubits.
+qsim_status bloch_sums_device(const void *amps, qsim_dtype dt, int n, cudaStream_t stream, Scratch &sc,
+                              double *d_out, int *passes)
+{
+    int t = std::min(n, dt == QSIM_C64 ? 12 : 11);
     int c = std::min(t, 4);
-    std::vector<int> done(n, 0);
-    int next_high = c;
-    QS_TRY(ensure_red(s));
+    QS_TRY(ensure_scratch(sc, (size_t)kMaxRedBlocks * 64 + 64));
+    int next_high = c, np = 0;
     while (true) {
         TileSpec ts;
         ts.n = n;
         ts.t = t;
         ts.c = c;
         for (int j = 0; j < c; j++) ts.tq[j] = j;
-        int h = 0;
         std::vector<int> high;
-        for (int q = next_high; q < n && h < t - c; q++) {
-            high.push_back(q);
-            h++;
-        }
-        // pad with already-covered qubits when fewer remain (keeps t fixed)
+        for (int q = next_high; q < n && (int)high.size() < t - c; q++) high.push_back(q);
+        int first_new = next_high;
         for (int q = n - 1; (int)high.size() < t - c && q >= c; q--)
             if (std::find(high.begin(), high.end(), q) == high.end()) high.push_back(q);
         std::sort(high.begin(), high.end());
@@ -396,36 +407,38 @@ qsim_status reduce_bloch_all(qsim_state *s, double *sums)
         for (int j = 0; j < t - c; j++) ts.ins.pos[j] = high[j];
         uint64_t ntiles = 1ull << (n - t);
         int blocks = (int)std::min<uint64_t>(ntiles, kMaxRedBlocks);
-        size_t smem = ((size_t)1 << t) * (s->dt == QSIM_C64 ? 8 : 16);
-        if (s->dt == QSIM_C64) {
-            cudaFuncSetAttribute(k_red_bloch_tile<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            k_red_bloch_tile<float><<<blocks, kRedThreads, smem, s->stream>>>((const float2 *)s->amps, ts, s->red.d);
-        } else {
-            cudaFuncSetAttribute(k_red_bloch_tile<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            k_red_bloch_tile<double><<<blocks, kRedThreads, smem, s->stream>>>((const double2 *)s->amps, ts,
-                                                                              s->red.d);
-        }
+        size_t smem = ((size_t)1 << t) * (dt == QSIM_C64 ? 8 : 16);
+        if (dt == QSIM_C64)
+            k_red_bloch_tile<float><<<blocks, kRedThreads, smem, stream>>>((const float2 *)amps, ts, sc.d);
+        else
+            k_red_bloch_tile<double><<<blocks, kRedThreads, smem, stream>>>((const double2 *)amps, ts, sc.d);
         QS_CUDA(cudaGetLastError());
-        QS_TRY(finish<kTileRow>(s, blocks));
-        double hbuf[kTileRow];
-        for (int m = 0; m < kTileRow; m++) hbuf[m] = s->red.h[m];
-        double total = hbuf[0];
-        for (int j = 0; j < t; j++) {
-            int q = ts.tq[j];
-            if (done[q]) continue;
-            double one = hbuf[1 + 3 * j];
-            sums[4 * q + 0] = total - one;
-            sums[4 * q + 1] = one;
-            sums[4 * q + 2] = hbuf[2 + 3 * j];
-            sums[4 * q + 3] = hbuf[3 + 3 * j];
-            done[q] = 1;
-        }
+        double *comb = sc.d + (size_t)kMaxRedBlocks * 64;
+        k_red_final<kTileRow><<<1, 64, 0, stream>>>(sc.d, blocks, comb);
+        k_bloch_scatter<<<1, 32, 0, stream>>>(comb, ts, np == 0 ? 0 : first_new, d_out);
+        QS_CUDA(cudaGetLastError());
+        np++;
         next_high += t - c;
-        bool all = true;
-        for (int q = 0; q < n; q++) all = all && done[q];
-        if (all) break;
+        if (next_high >= n || t == n) break;
     }
+    if (passes) *passes = np;
     return QSIM_OK;
+}
+
+// Host copy of the per-physical-qubit Bloch sums (synchronises).
+qsim_status reduce_bloch_all(qsim_state *s, double *sums)
+{
+    QS_TRY(ensure_red(s));
+    double *d = nullptr;
+    QS_CUDA(cudaMallocAsync((void **)&d, 4 * sizeof(double) * s->n, s->stream));
+    qsim_status st = bloch_sums_device(s->amps, s->dt, s->n, s->stream, s->red, d, nullptr);
+    if (st == QSIM_OK) {
+        cudaError_t e = cudaMemcpyAsync(sums, d, 4 * sizeof(double) * s->n, cudaMemcpyDeviceToHost, s->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+        if (e != cudaSuccess) st = cuda_fail(e, "bloch sums");
+    }
+    cudaFreeAsync(d, s->stream);
+    return st;
 }
 
 qsim_status probs_to_device(qsim_state *s, double *d_out)

@@ -6,11 +6,6 @@ using namespace qs;
 
 extern "C" {
 
-qsim_status qsim_approx_run(const qsim_circuit *, double, const qsim_approx_opts *, qsim_approx_result *)
-{
-    return fail(QSIM_E_UNSUPPORTED, "approximate mode is not available in this build");
-}
-
 qsim_status qsim_batch_create(const qsim_circuit *const *, int, const qsim_batch_opts *, qsim_batch **out)
 {
     if (out) *out = nullptr;

@@ -45,33 +45,30 @@ struct FMap {
     int8_t warp[kMaxW];
     int8_t pad[16 - kMaxRB - 5 - kMaxW + 16];
     uint32_t treg[1 << kMaxRB];
+    uint32_t tsw[1 << kMaxRB];   // swizzled shared-memory slot of treg[x] (linear over XOR)
     uint64_t preg[1 << kMaxRB];
 };
 
 struct FPassDev {
     int n, t, c, RB, W;
+    // pass-local constant block staged into shared memory by every CTA:
+    // counts and the byte offset of each array inside the block
+    int nops, ncoef, ntw, nmaps, nlin, next;
+    int off_tw, off_cf, off_ops, off_maps, off_lin, off_eb, off_et, stage_bytes;
+    const unsigned char *stage;  // the block in global memory
     int hq[kMaxTile];        // physical bit of tile bit c + j
     InsSpec ins;             // sorted hq for tile-id expansion
-    int nops;
-    const FOp *ops;
-    const float *cf;         // complex64 coefficients
-    const double *cd;        // complex128 coefficients (same layout)
-    const uint64_t *tw;      // phase turns (2^64 = one turn) and per-thread tables
-    const FMap *maps;
-    int map0;                // load map
-    int nlin;
-    const int32_t *lin_off;  // ext partner list of lin l: [lin_off[l], lin_off[l+1])
-    const int32_t *ext_bit;
-    const uint64_t *ext_tw;
 };
 
 // Host-side plan
 struct PlanPass {
-    FPassDev dev;            // pointers filled at upload
+    FPassDev dev;            // stage pointer filled at upload
     int op_begin, op_end;    // into ops
-    int map_begin;           // into maps
-    int lin_begin, nlin;     // into lin_off
+    int map_begin, map_end;  // into maps
+    int lin_begin, nlin;     // into lin_off (nlin + 1 entries, rebased to ext_begin)
+    int coef_begin, coef_end, tw_begin, tw_end, ext_begin, ext_end;
     int ndense;
+    std::vector<unsigned char> stage;  // host image of the staged block
 };
 
 struct PlanStep {

@@ -97,15 +97,24 @@ void diag_terms(const cd *m, int nq, const int *q, Item &it)
     }
 }
 
+// Shared-memory slot of tile index t: the low bank bits are XORed with the
+// higher bit groups (linear over XOR, so slot(a ^ b) = slot(a) ^ slot(b)).
+uint32_t swz_host(uint32_t t, qsim_dtype dt)
+{
+    if (dt == QSIM_C64) return t ^ (((t >> 4) ^ (t >> 8) ^ (t >> 12)) & 15u);
+    return t ^ (((t >> 3) ^ (t >> 6) ^ (t >> 9) ^ (t >> 12)) & 7u);
+}
+
 // ------------------------------------------------------------ pass builder
 
 struct Builder {
     qsim_plan &P;
+    qsim_dtype dt;
     int n, t, c, RB, W, NT;
     std::vector<Term> pending;
     cd gphase = 1.0;
 
-    Builder(qsim_plan &p, int n_, int t_, int c_, int rb) : P(p), n(n_), t(t_), c(c_), RB(rb)
+    Builder(qsim_plan &p, qsim_dtype d, int n_, int t_, int c_, int rb) : P(p), dt(d), n(n_), t(t_), c(c_), RB(rb)
     {
         W = t - RB - 5;
         NT = 1 << (t - RB);
@@ -152,6 +161,7 @@ struct Builder {
                     pp |= 1ull << tq[reg[r]];
                 }
             m.treg[x] = tt;
+            m.tsw[x] = swz_host(tt, dt);
             m.preg[x] = pp;
         }
         P.maps.push_back(m);
@@ -329,6 +339,9 @@ struct Builder {
         pass->op_begin = (int)P.ops.size();
         pass->map_begin = (int)P.maps.size();
         pass->lin_begin = (int)P.lin_off.size();
+        pass->coef_begin = (int)P.coef.size();
+        pass->tw_begin = (int)P.tw.size();
+        pass->ext_begin = (int)P.ext_bit.size();
         P.lin_off.push_back((int32_t)P.ext_bit.size());
         lin_count = 0;
         tq.assign(t, 0);
@@ -347,7 +360,7 @@ struct Builder {
         // phase 0 (load): lanes = tau 0..4, registers exclude them
         choose_regs(opt, 0, true);
         assign_lanes(true);
-        pass->dev.map0 = push_map();
+        push_map();   // map 0: the load map
         size_t di = 0;
         int ndense = 0;
         for (const Item *it : exec) {
@@ -380,6 +393,7 @@ struct Builder {
             emit(FO_XPOSE, 0, 0, 0, push_map(), 0);
         }
         pass->op_end = (int)P.ops.size();
+        pass->map_end = (int)P.maps.size();
         pass->nlin = lin_count;
         pass->ndense = ndense;
         FPassDev &d = pass->dev;
@@ -394,9 +408,56 @@ struct Builder {
         std::sort(s.begin(), s.end());
         d.ins.npos = (int)s.size();
         for (size_t j = 0; j < s.size(); j++) d.ins.pos[j] = s[j];
-        d.nops = pass->op_end - pass->op_begin;
-        d.nlin = lin_count;
-        d.map0 = 0;
+    }
+
+    // Host image of a pass's constant block (ops with offsets rebased to
+    // the block, coefficients in the ket's precision, phase turns, maps and
+    // partner lists), staged into shared memory by every CTA.
+    void finalize(PlanPass &ps)
+    {
+        FPassDev &d = ps.dev;
+        d.nops = ps.op_end - ps.op_begin;
+        d.ncoef = ps.coef_end - ps.coef_begin;
+        d.ntw = ps.tw_end - ps.tw_begin;
+        d.nmaps = ps.map_end - ps.map_begin;
+        d.nlin = ps.nlin;
+        d.next = ps.ext_end - ps.ext_begin;
+        const size_t rs = dt == QSIM_C64 ? 4 : 8;
+        auto al = [](size_t x) { return (x + 15) & ~(size_t)15; };
+        size_t o = 0;
+        d.off_tw = (int)o; o = al(o + 8 * (size_t)d.ntw);
+        d.off_cf = (int)o; o = al(o + rs * (size_t)d.ncoef);
+        d.off_ops = (int)o; o = al(o + sizeof(FOp) * (size_t)d.nops);
+        d.off_maps = (int)o; o = al(o + sizeof(FMap) * (size_t)d.nmaps);
+        d.off_lin = (int)o; o = al(o + 4 * (size_t)(d.nlin + 1));
+        d.off_eb = (int)o; o = al(o + 4 * (size_t)d.next);
+        d.off_et = (int)o; o = al(o + 8 * (size_t)d.next);
+        d.stage_bytes = (int)o;
+        ps.stage.assign(o, 0);
+        unsigned char *b = ps.stage.data();
+        memcpy(b + d.off_tw, P.tw.data() + ps.tw_begin, 8 * (size_t)d.ntw);
+        for (int i = 0; i < d.ncoef; i++) {
+            double v = P.coef[ps.coef_begin + i];
+            if (rs == 4) { float f = (float)v; memcpy(b + d.off_cf + 4 * i, &f, 4); }
+            else memcpy(b + d.off_cf + 8 * i, &v, 8);
+        }
+        for (int i = 0; i < d.nops; i++) {
+            FOp op = P.ops[ps.op_begin + i];
+            if (op.kind == FO_LINR) {
+                op.coef -= ps.tw_begin;
+                if (op.aux >= 0) op.aux -= ps.tw_begin;
+            } else if (op.kind != FO_XPOSE) {
+                op.coef -= ps.coef_begin;
+            }
+            memcpy(b + d.off_ops + sizeof(FOp) * i, &op, sizeof(FOp));
+        }
+        memcpy(b + d.off_maps, P.maps.data() + ps.map_begin, sizeof(FMap) * (size_t)d.nmaps);
+        for (int i = 0; i <= d.nlin; i++) {
+            int32_t v = P.lin_off[ps.lin_begin + i] - ps.ext_begin;
+            memcpy(b + d.off_lin + 4 * i, &v, 4);
+        }
+        memcpy(b + d.off_eb, P.ext_bit.data() + ps.ext_begin, 4 * (size_t)d.next);
+        memcpy(b + d.off_et, P.ext_tw.data() + ps.ext_begin, 8 * (size_t)d.next);
     }
 };
 
@@ -407,12 +468,13 @@ qsim_status plan_build(const qsim_circuit *cir, qsim_dtype dt, const qsim_run_op
     const int n = cir->n;
     qsim_run_opts o{};
     if (opts) o = *opts;
-    int RB = 4;
-    int t = o.tile_qubits ? o.tile_qubits : (dt == QSIM_C64 ? 13 : 12);
+    int t = o.tile_qubits ? o.tile_qubits : 13;
     int c = 5;
     if (o.low_qubits && o.low_qubits != 5) return fail(QSIM_E_UNSUPPORTED, "low_qubits must be 5 (warp lanes)");
     if (t > n) t = n;
-    if (t < RB + 5) return fail(QSIM_E_UNSUPPORTED, "fused path needs n >= %d", RB + 5);
+    // registers per thread: 2^5 amplitudes for complex64, 2^4 for complex128
+    int RB = std::min(dt == QSIM_C64 ? 5 : 4, t - 5);
+    if (RB < 4) return fail(QSIM_E_UNSUPPORTED, "fused path needs n >= 9");
     if (t - RB - 5 > kMaxW || t > kMaxTile) return fail(QSIM_E_INVAL, "tile_qubits %d too large", t);
     if (t - c > 12) return fail(QSIM_E_INVAL, "tile_qubits %d too large", t);
     P->n = n;
@@ -478,8 +540,27 @@ qsim_status plan_build(const qsim_circuit *cir, qsim_dtype dt, const qsim_run_op
     }
     P->final_l2p = l2p;
 
+    // complex64 plans with a dense (non-monomial) two-qubit gate use 16
+    // amplitude registers per thread: the 4x4 product needs the headroom
+    if (RB == 5) {
+        for (const Item &it : items) {
+            if (it.kind != 0 || it.nq != 2) continue;
+            bool mono = true;
+            for (int r = 0; r < 4 && mono; r++) {
+                int cnt = 0;
+                for (int col = 0; col < 4; col++) cnt += std::abs(it.m[r * 4 + col]) > kTiny;
+                mono = (cnt == 1);
+            }
+            if (!mono) {
+                RB = 4;
+                break;
+            }
+        }
+        P->RB = RB;
+    }
+
     // ---- passes
-    Builder B(*P, n, t, c, RB);
+    Builder B(*P, dt, n, t, c, RB);
     std::vector<const Item *> rem;
     for (auto &it : items) rem.push_back(&it);
     auto item_qubits = [](const Item *it, std::vector<int> &v) {
@@ -594,7 +675,6 @@ qsim_status plan_build(const qsim_circuit *cir, qsim_dtype dt, const qsim_run_op
             cd g = B.gphase;
             P->ops.push_back(FOp{FO_SCALE, 0, 0, B.add_coef(&g, 1), 0, 0});
             ps.op_end = (int)P->ops.size();
-            ps.dev.nops = ps.op_end - ps.op_begin;
         } else {
             PlanStep st;
             st.kind = 2;
@@ -603,6 +683,15 @@ qsim_status plan_build(const qsim_circuit *cir, qsim_dtype dt, const qsim_run_op
         }
     }
     flush_all_pergate();
+    for (size_t i = 0; i < P->passes.size(); i++) {
+        // coefficient / turn / partner ranges end where the next pass begins
+        PlanPass &ps = P->passes[i];
+        bool last = (i + 1 == P->passes.size());
+        ps.coef_end = last ? (int)P->coef.size() : P->passes[i + 1].coef_begin;
+        ps.tw_end = last ? (int)P->tw.size() : P->passes[i + 1].tw_begin;
+        ps.ext_end = last ? (int)P->ext_bit.size() : P->passes[i + 1].ext_begin;
+        B.finalize(ps);
+    }
     return QSIM_OK;
 }
 

@@ -1,0 +1,134 @@
+"""GPU parity of the approximate (SDRP) mode, Sec. III.A-B: the factorised
+GPU run against the oracle's full-state-vector run of the same algorithm.
+
+complex128: identical decision log, F within 1e-12, expanded state within
+infidelity 1e-10 of the oracle's. complex64: decisions may differ only where
+the oracle's eps lies within 1e-5 of p/2 (a tie in FP32); such cases are
+checked by replaying the GPU's checks through the oracle."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2304_14969_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def Q():
+    from paper_2304_14969_gb300 import build, qsim
+    build.build()
+    qsim.lib()
+    return qsim
+
+
+def gpu_approx(Q, n, gates, p, dt, tau, want_state=True, budget=0.0, force=None):
+    circ = Q.Circuit(n, gates)
+    cap = 64 * len(gates) + 64
+    log = (Q.qsim_decision * cap)()
+    out = np.zeros(1 << n, dtype=np.complex64 if dt == 0 else np.complex128) if want_state else None
+    o = Q.qsim_approx_opts()
+    o.dtype = dt
+    o.tau = tau
+    o.budget_bytes = budget
+    o.log = log
+    o.log_cap = cap
+    if force is not None:
+        f = np.ascontiguousarray(np.asarray(force, dtype=np.int32).reshape(-1))
+        o.schedule = Q.QSIM_SCHED_FORCED
+        o.force = f.ctypes.data_as(C.POINTER(C.c_int32))
+        o.nforce = len(f) // 2
+    if want_state:
+        o.state_out = out.ctypes.data_as(C.c_void_p)
+    r = Q.qsim_approx_result()
+    st = Q.lib().qsim_approx_run(circ.ptr(), float(p), C.byref(o), C.byref(r))
+    entries = [(log[i].gate, log[i].qubit, log[i].action, log[i].eps) for i in range(min(r.n_log, cap))]
+    return st, r, entries, out
+
+
+def fid(a, b):
+    a = a.astype(np.complex128)
+    b = b.astype(np.complex128)
+    return abs(np.vdot(a, b)) ** 2 / (np.vdot(a, a).real * np.vdot(b, b).real)
+
+
+@pytest.mark.parametrize("p", [0.0, 0.1, 0.3, 1.0])
+@pytest.mark.parametrize("rows,cols,layers", [(3, 4, 6), (2, 5, 8)])
+def test_approx_c128_matches_oracle(Q, p, rows, cols, layers):
+    n = rows * cols
+    g = W.grid_rcs_circuit(rows, cols, layers, seed=3)
+    tau = 1e-13
+    st, r, log, psi = gpu_approx(Q, n, g, p, 1, tau)
+    assert st == 0
+    opsi, oF, onr, olog = oracle.sdrp_run(n, g, p, tau)
+    assert [(e[0], e[1], e[2]) for e in log] == [(int(a), int(b), int(c)) for a, b, c in
+                                                 zip(olog["gate"], olog["qubit"], olog["action"])]
+    assert np.max(np.abs(np.array([e[3] for e in log]) - olog["eps"])) < 1e-10
+    assert abs(r.fidelity_model - oF) < 1e-12
+    assert r.n_rounds == onr
+    assert fid(psi, opsi) > 1 - 1e-10
+    if p == 0.0:
+        assert r.fidelity_model == 1.0
+
+
+@pytest.mark.parametrize("p", [0.05, 0.2, 0.5])
+def test_approx_paper_family_c128(Q, p):
+    """The paper's own random family (U3 + C/A-Pauli couplers, ABCDCDAB)."""
+    rows, cols = 3, 4
+    n = rows * cols
+    g = W.paper_random_circuit(rows, cols, 5, seed=11)
+    st, r, log, psi = gpu_approx(Q, n, g, p, 1, 1e-13)
+    assert st == 0
+    opsi, oF, onr, olog = oracle.sdrp_run(n, g, p, 1e-13)
+    assert len(log) == len(olog)
+    assert abs(r.fidelity_model - oF) < 1e-12
+    assert fid(psi, opsi) > 1 - 1e-10
+
+
+@pytest.mark.parametrize("p", [0.1, 0.4])
+def test_approx_c64_with_ties(Q, p):
+    rows, cols = 4, 5
+    n = rows * cols
+    g = W.grid_rcs_circuit(rows, cols, 6, seed=5)
+    tau = 1e-6
+    st, r, log, psi = gpu_approx(Q, n, g, p, 0, tau)
+    assert st == 0
+    force = [(e[0], e[1]) for e in log]
+    opsi, oF, onr, olog = oracle.sdrp_run(n, g, p, tau, force=force)
+    mism = [i for i, e in enumerate(log) if e[2] != olog["action"][i]]
+    for i in mism:   # only ties near the threshold may differ
+        assert abs(olog["eps"][i] - p / 2) < 1e-5 or abs(olog["eps"][i] - tau) < 1e-5
+    if not mism:
+        assert abs(r.fidelity_model - oF) < 1e-5
+        assert fid(psi, opsi) > 1 - 1e-5
+
+
+def test_single_rounding_model_is_exact(Q):
+    """F model equals F_exact when exactly one rounding happened (Sec. III.B)."""
+    n = 5
+    g = [W.Gate("u3", (q,), (0.2 + 0.1 * q, 0.3, 0.1)) for q in range(n)]
+    g += [W.Gate("x", (1,), (), (0,), (1,))]
+    g += [W.Gate("u3", (q,), (1.1, 0.4 * q, 0.2)) for q in range(n)]
+    st, r, log, psi = gpu_approx(Q, n, g, 0.2, 1, 1e-13)
+    assert st == 0 and r.n_rounds == 1
+    exact = oracle.apply_circuit(W.basis_state(n, 0), g)
+    assert abs(r.fidelity_model - fid(psi, exact)) < 1e-12
+
+
+def test_budget_error(Q):
+    g = W.grid_rcs_circuit(4, 5, 6, seed=2)
+    st, r, log, psi = gpu_approx(Q, 20, g, 0.0, 0, 1e-6, want_state=False, budget=2.0 ** 12)
+    assert st == 5            # QSIM_E_BUDGET
+    assert r.budget_gate >= 0
+
+
+def test_54_qubit_grid_runs(Q):
+    """6x9 grid, 7 layers: the approximate run completes within a 64 GiB
+    budget at a moderate p; F stays in (0, 1] (no exact state exists)."""
+    g = W.grid_rcs_circuit(6, 9, 7, seed=0)
+    st, r, log, _ = gpu_approx(Q, 54, g, 0.3, 0, 1e-6, want_state=False, budget=64.0 * 2 ** 30)
+    assert st == 0
+    assert 0 < r.fidelity_model <= 1
+    assert r.max_subsystem_qubits <= 33
