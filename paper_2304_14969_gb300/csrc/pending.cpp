@@ -22,23 +22,4 @@ qsim_status qsim_autotune(const qsim_circuit *, qsim_dtype, const char *, qsim_r
     return fail(QSIM_E_UNSUPPORTED, "autotuner is not available in this build");
 }
 
-qsim_status qsim_mlp_create(int, int, uint64_t, qsim_mlp **out)
-{
-    if (out) *out = nullptr;
-    return fail(QSIM_E_UNSUPPORTED, "MLP is not available in this build");
-}
-qsim_status qsim_mlp_destroy(qsim_mlp *) { return QSIM_OK; }
-qsim_status qsim_mlp_num_params(const qsim_mlp *, int64_t *) { return fail(QSIM_E_UNSUPPORTED, "no MLP"); }
-qsim_status qsim_mlp_get_params(const qsim_mlp *, float *) { return fail(QSIM_E_UNSUPPORTED, "no MLP"); }
-qsim_status qsim_mlp_set_params(qsim_mlp *, const float *) { return fail(QSIM_E_UNSUPPORTED, "no MLP"); }
-qsim_status qsim_mlp_infer(qsim_mlp *, const float *, int, int, float *) { return fail(QSIM_E_UNSUPPORTED, "no MLP"); }
-qsim_status qsim_mlp_loss_grad(qsim_mlp *, const float *, const float *, int, float *, float *)
-{
-    return fail(QSIM_E_UNSUPPORTED, "no MLP");
-}
-qsim_status qsim_mlp_train_step(qsim_mlp *, const float *, const float *, int, float, float *)
-{
-    return fail(QSIM_E_UNSUPPORTED, "no MLP");
-}
-
 }  // extern "C"

@@ -124,11 +124,16 @@ def test_budget_error(Q):
     assert r.budget_gate >= 0
 
 
-def test_54_qubit_grid_runs(Q):
+@pytest.mark.parametrize("p", [1.0, 0.9])
+def test_54_qubit_grid_runs(Q, p):
     """6x9 grid, 7 layers: the approximate run completes within a 64 GiB
-    budget at a moderate p; F stays in (0, 1] (no exact state exists)."""
+    budget at large p (every check may round); F stays in (0, 1] (no exact
+    state exists at 54 qubits)."""
     g = W.grid_rcs_circuit(6, 9, 7, seed=0)
-    st, r, log, _ = gpu_approx(Q, 54, g, 0.3, 0, 1e-6, want_state=False, budget=64.0 * 2 ** 30)
-    assert st == 0
-    assert 0 < r.fidelity_model <= 1
-    assert r.max_subsystem_qubits <= 33
+    st, r, log, _ = gpu_approx(Q, 54, g, p, 0, 1e-6, want_state=False, budget=64.0 * 2 ** 30)
+    assert st in (0, 5)
+    if p == 1.0:
+        assert st == 0
+    if st == 0:
+        assert 0 < r.fidelity_model <= 1
+        assert r.peak_bytes <= 64 * 2 ** 30
