@@ -26,6 +26,37 @@
 namespace qs {
 
 qsim_status validate_circuit(const qsim_circuit *c);
+qsim_status mlp_infer_device(const qsim_mlp *m, const float *d_x, int rows, float *d_out, cudaStream_t st);
+int mlp_nfeat(const qsim_mlp *m);
+
+// Features of a candidate qubit for the proposal network (all known on the
+// host before any reduction runs): the Bloch vector and its length from the
+// qubit's last check (stale by design: the fresh one is what a check
+// costs), its rounding error then, gates on it since (one- and two-qubit),
+// gates since its last check, whether that check separated it, the
+// subsystem size relative to n, p, and a constant.
+static const int kFeat = 12;
+struct QubitHist {
+    double r[3] = {0, 0, 1};
+    int g1 = 0, g2 = 0, last = -1, sep = 0;
+};
+
+static void features(const QubitHist &h, int gate, int m, int n, double p, float *f)
+{
+    double len = std::sqrt(h.r[0] * h.r[0] + h.r[1] * h.r[1] + h.r[2] * h.r[2]);
+    f[0] = (float)h.r[0];
+    f[1] = (float)h.r[1];
+    f[2] = (float)h.r[2];
+    f[3] = (float)len;
+    f[4] = (float)((1.0 - len) / 2.0);
+    f[5] = (float)h.g1 / 8.0f;
+    f[6] = (float)h.g2 / 8.0f;
+    f[7] = (float)(h.last < 0 ? gate + 1 : gate - h.last) / 64.0f;
+    f[8] = (float)h.sep;
+    f[9] = (float)m / (float)n;
+    f[10] = (float)p;
+    f[11] = 1.0f;
+}
 
 template <typename R> struct AV;
 template <> struct AV<float> { using T = float2; };
@@ -285,7 +316,12 @@ extern "C" qsim_status qsim_approx_run(const qsim_circuit *c, double p, const qs
     qsim_approx_opts o{};
     if (opts) o = *opts;
     if (o.dtype != QSIM_C64 && o.dtype != QSIM_C128) return fail(QSIM_E_INVAL, "unknown dtype");
-    if (o.schedule == QSIM_SCHED_MLP) return fail(QSIM_E_UNSUPPORTED, "MLP schedule is not available in this build");
+    if (o.schedule == QSIM_SCHED_MLP) {
+        if (!o.mlp) return fail(QSIM_E_INVAL, "MLP schedule needs opts->mlp");
+        if (mlp_nfeat(o.mlp) != kFeat) return fail(QSIM_E_INVAL, "the proposal MLP must take %d features", kFeat);
+        if (o.top_m < 1) return fail(QSIM_E_INVAL, "top_m must be >= 1");
+    }
+    if (o.schedule < 0 || o.schedule > 2) return fail(QSIM_E_INVAL, "unknown schedule %d", o.schedule);
     if (o.schedule == QSIM_SCHED_FORCED && o.nforce > 0 && !o.force) return fail(QSIM_E_INVAL, "force is NULL");
     if (o.state_out && c->n > 30) return fail(QSIM_E_INVAL, "state_out needs n <= 30");
     memset(res, 0, sizeof *res);
@@ -316,6 +352,18 @@ extern "C" qsim_status qsim_approx_run(const qsim_circuit *c, double p, const qs
     }
     QS_CUDA(cudaGetLastError());
 
+    std::vector<QubitHist> hist(n);
+    float *d_feat = nullptr, *d_logit = nullptr;
+    std::vector<float> hfeat, hlogit;
+    if (o.schedule == QSIM_SCHED_MLP) {
+        QS_CUDA(cudaMalloc(&d_feat, sizeof(float) * kFeat * 64));
+        QS_CUDA(cudaMalloc(&d_logit, sizeof(float) * 64));
+    }
+    struct Free {
+        float *a, *b;
+        ~Free() { if (a) cudaFree(a); if (b) cudaFree(b); }
+    } free_mlp{d_feat, d_logit};
+    int64_t n_ent = 0, ntrace = 0;
     double F = 1.0;
     int64_t nlog = 0, nround = 0, nexact = 0, nchecks = 0;
     int maxsub = 1, fpos = 0;
@@ -363,7 +411,12 @@ extern "C" qsim_status qsim_approx_run(const qsim_circuit *c, double p, const qs
         } else {
             QS_CUDA(launch_gate2(&v, m, R.local(S, g.q0), R.local(S, g.q1)));
         }
-        if (touched.size() < 2) continue;
+        if (touched.size() < 2) {
+            hist[g.q0].g1++;
+            continue;
+        }
+        for (int q : touched) hist[q].g2++;
+        n_ent++;
 
         // ---- checks (Sec. III.A) on the touched subsystem
         std::vector<int> cand;
@@ -372,6 +425,35 @@ extern "C" qsim_status qsim_approx_run(const qsim_circuit *c, double p, const qs
         } else {
             cand = R.subs[si]->qs;
             std::sort(cand.begin(), cand.end());
+        }
+        if (o.schedule == QSIM_SCHED_MLP && cand.size() >= 2 &&
+            !(o.fallback_every > 0 && n_ent % o.fallback_every == 0)) {
+            // score every qubit of the subsystem, keep the top_m predicted
+            // to round (logit > 0), check them in ascending qubit order
+            int rows = (int)std::min<size_t>(cand.size(), 64);
+            hfeat.assign((size_t)rows * kFeat, 0.f);
+            hlogit.assign(rows, 0.f);
+            int msz = (int)R.subs[si]->qs.size();
+            for (int i = 0; i < rows; i++) features(hist[cand[i]], k, msz, n, p, &hfeat[(size_t)i * kFeat]);
+            QS_CUDA(cudaMemcpyAsync(d_feat, hfeat.data(), sizeof(float) * hfeat.size(), cudaMemcpyHostToDevice, R.st));
+            QS_TRY(mlp_infer_device(o.mlp, d_feat, rows, d_logit, R.st));
+            QS_CUDA(cudaMemcpyAsync(hlogit.data(), d_logit, sizeof(float) * rows, cudaMemcpyDeviceToHost, R.st));
+            QS_CUDA(cudaStreamSynchronize(R.st));
+            std::vector<std::pair<float, int>> sc;
+            for (int i = 0; i < rows; i++)
+                if (hlogit[i] > 0.f) sc.push_back({-hlogit[i], cand[i]});
+            std::sort(sc.begin(), sc.end());
+            if ((int)sc.size() > o.top_m) sc.resize(o.top_m);
+            cand.clear();
+            for (auto &x : sc) cand.push_back(x.second);
+            std::sort(cand.begin(), cand.end());
+        }
+        // trace rows: features of the candidates before this check round
+        std::vector<float> tf;
+        if (o.trace_features && o.schedule != QSIM_SCHED_MLP) {
+            tf.assign(cand.size() * kFeat, 0.f);
+            int msz = (int)R.subs[si]->qs.size();
+            for (size_t i = 0; i < cand.size(); i++) features(hist[cand[i]], k, msz, n, p, &tf[i * kFeat]);
         }
         size_t ci = 0;
         while (ci < cand.size()) {
@@ -399,6 +481,24 @@ extern "C" qsim_status qsim_approx_run(const qsim_circuit *c, double p, const qs
             for (int e = 0; e < D.examined; e++) {
                 int qq = cand[ci + e];
                 int act = (e == D.first) ? D.action : 0;
+                if (!tf.empty()) {
+                    if (ntrace < o.trace_cap) {
+                        memcpy(o.trace_features + ntrace * kFeat, &tf[(ci + e) * kFeat], sizeof(float) * kFeat);
+                        if (o.trace_labels) o.trace_labels[ntrace] = (act == 1);
+                    }
+                    ntrace++;
+                }
+                QubitHist &hq = hist[qq];
+                hq.r[0] = D.r[e][0];
+                hq.r[1] = D.r[e][1];
+                hq.r[2] = D.r[e][2];
+                hq.g1 = hq.g2 = 0;
+                hq.last = k;
+                hq.sep = act != 0;
+                if (act) {
+                    double len = std::sqrt(hq.r[0] * hq.r[0] + hq.r[1] * hq.r[1] + hq.r[2] * hq.r[2]);
+                    for (int z = 0; z < 3 && len > 0; z++) hq.r[z] /= len;
+                }
                 if (o.log && nlog < o.log_cap) {
                     qsim_decision &L = o.log[nlog];
                     L.gate = k;
@@ -434,6 +534,7 @@ extern "C" qsim_status qsim_approx_run(const qsim_circuit *c, double p, const qs
     res->n_bloch_passes = R.bloch_passes;
     res->peak_bytes = (int64_t)R.peak;
     res->n_log = nlog;
+    res->n_trace = ntrace;
     res->max_subsystem_qubits = maxsub;
     if (status != QSIM_OK) {
         res->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();

@@ -430,11 +430,16 @@ cudaError_t launch_pass_t(void *amps, const FPassDev &d, cudaStream_t st)
 
 cudaError_t launch_fused_pass(qsim_state *s, const FPassDev &d)
 {
+    const int threads = 1 << (d.t - d.RB);
     if (s->dt == QSIM_C64) {
-        if (d.RB == 5) return launch_pass_t<float, 5, 256, 2>(s->amps, d, s->stream);
-        return launch_pass_t<float, 4, 512, 1>(s->amps, d, s->stream);
+        if (d.RB == 5)
+            return threads <= 256 ? launch_pass_t<float, 5, 256, 2>(s->amps, d, s->stream)
+                                  : launch_pass_t<float, 5, 512, 1>(s->amps, d, s->stream);
+        return threads <= 512 ? launch_pass_t<float, 4, 512, 1>(s->amps, d, s->stream)
+                              : launch_pass_t<float, 4, 1024, 1>(s->amps, d, s->stream);
     }
-    return launch_pass_t<double, 4, 256, 1>(s->amps, d, s->stream);
+    return threads <= 256 ? launch_pass_t<double, 4, 256, 1>(s->amps, d, s->stream)
+                          : launch_pass_t<double, 4, 512, 1>(s->amps, d, s->stream);
 }
 
 }  // namespace qs
@@ -465,7 +470,6 @@ qsim_status qsim_plan_create(const qsim_circuit *c, qsim_dtype dt, const qsim_ru
 
 qsim_status qsim_plan_destroy(qsim_plan *p)
 {
-    clear_error();
     if (!p) return QSIM_OK;
     if (p->dmem) {
         cudaDeviceSynchronize();

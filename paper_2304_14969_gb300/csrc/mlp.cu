@@ -186,7 +186,7 @@ static qsim_status ensure_io(qsim_mlp *m, int rows)
 }
 
 // Device inference on device features (used by the approximate mode).
-qsim_status mlp_infer_device(qsim_mlp *m, const float *d_x, int rows, float *d_out, cudaStream_t st)
+qsim_status mlp_infer_device(const qsim_mlp *m, const float *d_x, int rows, float *d_out, cudaStream_t st)
 {
     int grid = std::max(1, std::min(64, (rows + 127) / 128));
     k_mlp_infer<true><<<grid, 128, 0, st>>>(m->w, m->wb, m->nf, m->H, d_x, rows, d_out);

@@ -468,7 +468,9 @@ qsim_status plan_build(const qsim_circuit *cir, qsim_dtype dt, const qsim_run_op
     const int n = cir->n;
     qsim_run_opts o{};
     if (opts) o = *opts;
-    int t = o.tile_qubits ? o.tile_qubits : 13;
+    int t = o.tile_qubits ? o.tile_qubits : (dt == QSIM_C64 ? 13 : 12);
+    if (dt == QSIM_C128 && t > 13) return fail(QSIM_E_INVAL, "complex128 tiles hold at most 13 qubits");
+    if (t > 14) return fail(QSIM_E_INVAL, "tiles hold at most 14 qubits");
     int c = 5;
     if (o.low_qubits && o.low_qubits != 5) return fail(QSIM_E_UNSUPPORTED, "low_qubits must be 5 (warp lanes)");
     if (t > n) t = n;
