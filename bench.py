@@ -196,16 +196,27 @@ def main():
     host_out = torch.empty(N, dtype=torch.complex64).pin_memory()
     dev = torch.empty(N, dtype=torch.complex64, device="cuda")
     st = Q.State(n, Q.QSIM_C64, stream=sp, dev_ptr=dev.data_ptr())
-    plan = Q.Plan(circ, dtype=Q.QSIM_C64)
-    info = plan.info()
     import ctypes as C
+    Q.qsim_upload(st.h, C.c_void_p(host_in.data_ptr()))
+    # The QFT leaves the ket bit-reversed (its swaps are relabels, Table I);
+    # a second plan starts from that layout, so consecutive steps alternate
+    # between the two plans and no step moves data for the relabel.
+    plans = [Q.Plan(circ, dtype=Q.QSIM_C64, state=st)]
+    plans[0].execute(st)
+    plans.append(Q.Plan(circ, dtype=Q.QSIM_C64, state=st))
+    plans[1].execute(st)
+    info = plans[0].info()
     nrm = C.c_double()
+    turn = [0]
+
+    def run_plan():
+        plans[turn[0]].execute(st)
+        turn[0] ^= 1
 
     def step():
-        plan.execute(st)
+        run_plan()
         Q.qsim_norm(st.h, C.byref(nrm))   # FP64 norm of the result (syncs)
 
-    Q.qsim_upload(st.h, C.c_void_p(host_in.data_ptr()))
     for _ in range(args.warmup):
         step()
     # ---- timed region: K steps, events on the library's stream
@@ -220,7 +231,7 @@ def main():
                torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
         for k in range(args.steps):
             ev[k][0].record(stream)
-            plan.execute(st)
+            run_plan()
             ev[k][1].record(stream)
             Q.qsim_norm(st.h, C.byref(nrm))
             ev[k][2].record(stream)
@@ -252,7 +263,7 @@ def main():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         Q.qsim_upload(st.h, C.c_void_p(host_in.data_ptr()))
-        plan.execute(st)
+        plans[0].execute(st)
         Q.qsim_download(st.h, C.c_void_p(host_out.data_ptr()))
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e_val = world * ng * N / (float(np.median(e2e_ms)) * 1e-3)

@@ -198,11 +198,18 @@ qsim_status qsim_run_circuit(qsim_state *s, const qsim_circuit *c, const qsim_ru
  * gates applied to 2^t-amplitude tiles on chip. */
 qsim_status qsim_plan_create(const qsim_circuit *c, qsim_dtype dt, const qsim_run_opts *opts,
                              qsim_plan **out);
+/* As qsim_plan_create, for the dtype of s and starting from s's current
+ * qubit map, so that a ket left permuted by earlier SWAP relabels is used
+ * in place (no data movement before the first pass). */
+qsim_status qsim_plan_create_for_state(const qsim_circuit *c, const qsim_state *s, const qsim_run_opts *opts,
+                                       qsim_plan **out);
 qsim_status qsim_plan_destroy(qsim_plan *p);
 /* info[0] passes, info[1] gates, info[2] dense blocks, info[3] swaps
  * folded into the map, info[4] tile qubits, info[5] low qubits. */
 qsim_status qsim_plan_info(const qsim_plan *p, int64_t info[8]);
-/* Executes the plan on s (stream-ordered, no host sync). */
+/* Executes the plan on s (stream-ordered, no host sync). If s's qubit map is
+ * not the plan's starting map, the amplitudes are first permuted to it (one
+ * extra read+write of the ket). */
 qsim_status qsim_plan_execute(qsim_state *s, const qsim_plan *p);
 
 /* ------------------------------------------------------ reductions */

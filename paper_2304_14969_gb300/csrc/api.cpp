@@ -51,8 +51,11 @@ qsim_status make_state(int n, qsim_dtype dt, void *stream, qsim_state **out)
     return QSIM_OK;
 }
 
+}  // namespace
+
+namespace qs {
 // Moves the amplitudes so that physical bit p ends up at new_pos[p].
-qsim_status permute_inplace(qsim_state *s, const std::vector<int> &new_pos)
+qsim_status permute_state(qsim_state *s, const std::vector<int> &new_pos)
 {
     void *tmp = nullptr;
     cudaError_t e = cudaMallocAsync(&tmp, s->amp_bytes(), s->stream);
@@ -64,7 +67,9 @@ qsim_status permute_inplace(qsim_state *s, const std::vector<int> &new_pos)
     if (e != cudaSuccess) return cuda_fail(e, "permute");
     return QSIM_OK;
 }
+}  // namespace qs
 
+namespace {
 }  // namespace
 
 extern "C" {
@@ -183,7 +188,7 @@ qsim_status qsim_materialize(qsim_state *s)
     if (is_identity(s)) return QSIM_OK;
     std::vector<int> to(s->n);
     for (int L = 0; L < s->n; L++) to[s->l2p[L]] = L;
-    QS_TRY(permute_inplace(s, to));
+    QS_TRY(permute_state(s, to));
     for (int q = 0; q < s->n; q++) s->l2p[q] = q;
     return QSIM_OK;
 }

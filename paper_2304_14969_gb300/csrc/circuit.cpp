@@ -69,8 +69,14 @@ qsim_status qsim_run_circuit(qsim_state *s, const qsim_circuit *c, const qsim_ru
         return QSIM_OK;
     }
     if (o.mode != QSIM_MODE_FUSED) return fail(QSIM_E_INVAL, "unknown mode %d", o.mode);
+    if (c->n < 9) {
+        // tiles need at least 9 qubits; smaller kets run gate by gate
+        for (int k = 0; k < c->ngates; k++)
+            QS_TRY(apply_one_gate(s, c->gates[k], c->matrices, c->nmatrix_doubles, true));
+        return QSIM_OK;
+    }
     qsim_plan *p = nullptr;
-    QS_TRY(qsim_plan_create(c, s->dt, &o, &p));
+    QS_TRY(qsim_plan_create_for_state(c, s, &o, &p));
     qsim_status st = qsim_plan_execute(s, p);
     qsim_plan_destroy(p);
     return st;

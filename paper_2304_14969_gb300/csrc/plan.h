@@ -16,20 +16,26 @@
 namespace qs {
 
 enum FOpKind : int32_t {
-    FO_G1 = 1,     // dense 2x2 on register bit j0; cf[coef .. +8): u00,u01,u10,u11 (re,im)
-    FO_G1R = 2,    // real 2x2 on j0; cf[coef .. +4)
-    FO_G1X = 3,    // anti-diagonal 2x2 on j0: out0 = u01*b, out1 = u10*a; cf[coef .. +4)
+    // FO_G1F: dense 2x2 on register bit j0, preceded by the phase prefactor
+    // of the amplitudes with bit j0 set (deferred diagonal terms). j1 = matrix
+    // form (0 none / pure phase, 1 real 2x2, 2 complex 2x2, 3 anti-diagonal).
+    // The prefactor of register element x is
+    //   cf[aux4] * (aux >= 0 ? cf[aux + 2 tid] : 1) * (aux2 >= 0 ? Ec[aux2] : 1) * cf[aux3 + 2 xr]
+    // with xr = x without bit j0 (aux3 table of 2^(RB-1) complex entries for
+    // partners among the other register bits) and Ec[l] a per-tile factor
+    // from partners outside the tile.
+    FO_G1F = 1,
     FO_G2 = 4,     // dense 4x4 on (j0 = bit 0, j1 = bit 1); cf[coef .. +32)
     FO_G2M = 5,    // monomial 4x4: out[r] = ph[r] * in[perm[r]]; aux = perm packed 2 bits each; cf: 8
-    FO_DIAGR = 6,  // amplitudes with register bits j0 and j1 set *= cf[coef .. +2)
-    FO_LINR = 7,   // amplitudes with register bit j0 set *= exp(2 pi i turns), turns =
-                   //   tw[coef] + (aux >= 0 ? tw[aux + threadIdx.x] : 0) + ext sum of lin aux2
     FO_XPOSE = 8,  // transpose through shared memory to map aux
     FO_SCALE = 9   // every register amplitude *= cf[coef .. +2)
 };
 
+// u form of FO_G1F (j1)
+enum { U_NONE = 0, U_REAL = 1, U_CPLX = 2, U_ANTI = 3 };
+
 struct FOp {
-    int32_t kind, j0, j1, coef, aux, aux2;
+    int32_t kind, j0, j1, coef, aux, aux2, aux3, aux4;
 };
 
 static const int kMaxRB = 5;
@@ -89,7 +95,7 @@ struct qsim_plan {
     int t = 0, c = 0, RB = 0;
     std::vector<qs::PlanStep> steps;
     std::vector<qs::PlanPass> passes;
-    std::vector<int> final_l2p;
+    std::vector<int> start_l2p, final_l2p;
     // host arrays
     std::vector<qs::FOp> ops;
     std::vector<double> coef;

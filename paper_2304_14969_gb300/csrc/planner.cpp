@@ -176,7 +176,11 @@ struct Builder {
         for (int b = 0; b < t; b++)
             if (reg_of_tau(b) < 0) rest.push_back(b);
         std::vector<int> ln;
-        if (load_store) {
+        bool low_free = true;
+        for (int r = 0; r < RB; r++) low_free = low_free && reg[r] >= 5;
+        if (load_store || low_free) {
+            // lanes on the 5 lowest tile bits: coalesced HBM access, and a
+            // phase that can store without another transpose
             for (int l = 0; l < 5; l++) ln.push_back(l);
         } else {
             // cover residues mod 4 (shared-memory swizzle folds bit groups of 4)
@@ -197,7 +201,7 @@ struct Builder {
 
     void emit(int kind, int j0, int j1, int coef, int aux, int aux2)
     {
-        P.ops.push_back(FOp{kind, j0, j1, coef, aux, aux2});
+        P.ops.push_back(FOp{kind, j0, j1, coef, aux, aux2, 0, 0});
     }
 
     // Register set for a new phase starting at dense op i of `ops`.
@@ -224,13 +228,20 @@ struct Builder {
         for (int r = 0; r < RB; r++) reg[r] = S[r];
     }
 
-    // Flushes pending terms touching any physical qubit of `phys` (all in
-    // registers now) into DIAGR / LINR ops.
-    void flush_for(const std::vector<int> &phys)
+    // Takes the pending terms touching any physical qubit of `phys` (all in
+    // registers now) and returns, per register bit, the prefactor of the
+    // amplitudes with that bit set: a constant angle, partners among the
+    // other register bits, partners on lane/warp bits and partners outside
+    // the tile. A pair term between two op qubits goes to the first one.
+    struct Pre {
+        double th0 = 0;
+        std::map<int, double> regp;                  // other register bit -> angle
+        std::vector<std::pair<int, double>> tile;    // tau bit (lane/warp) -> angle
+        std::vector<std::pair<int, double>> ext;     // physical bit outside the tile -> angle
+    };
+    std::map<int, Pre> take_pending(const std::vector<int> &phys)
     {
-        std::map<std::pair<int, int>, double> diagr;
-        struct Lin { double th0 = 0; std::vector<std::pair<int, double>> tile, ext; };
-        std::map<int, Lin> lins;
+        std::map<int, Pre> pre;
         std::vector<Term> keep;
         auto touches = [&](int q) { return std::find(phys.begin(), phys.end(), q) != phys.end(); };
         for (const Term &tm : pending) {
@@ -239,78 +250,101 @@ struct Builder {
                 continue;
             }
             int a = tm.a, b = tm.b;
-            if (b >= 0 && !touches(a)) std::swap(a, b);  // a is touched
+            if (b >= 0 && !touches(a)) std::swap(a, b);  // a is an op qubit
             int ra = reg_of_tau(tau_of[a]);
+            Pre &P0 = pre[ra];
             if (b < 0) {
-                lins[ra].th0 += tm.th;
+                P0.th0 += tm.th;
                 continue;
             }
             int tb = tau_of[b];
             int rb = tb >= 0 ? reg_of_tau(tb) : -1;
-            if (rb >= 0) {
-                diagr[{std::min(ra, rb), std::max(ra, rb)}] += tm.th;
-            } else if (tb >= 0) {
-                lins[ra].tile.push_back({tb, tm.th});
-            } else {
-                lins[ra].ext.push_back({b, tm.th});
-            }
+            if (rb >= 0) P0.regp[rb] += tm.th;
+            else if (tb >= 0) P0.tile.push_back({tb, tm.th});
+            else P0.ext.push_back({b, tm.th});
         }
         pending.swap(keep);
-        for (auto &kv : diagr) {
-            cd ph = std::polar(1.0, kv.second);
-            emit(FO_DIAGR, kv.first.first, kv.first.second, add_coef(&ph, 1), 0, 0);
-        }
-        for (auto &kv : lins) {
-            Lin &L = kv.second;
-            int c0 = (int)P.tw.size();
-            P.tw.push_back(to_turns(L.th0));
-            int taux = -1;
-            if (!L.tile.empty()) {
-                taux = (int)P.tw.size();
-                for (int tid = 0; tid < NT; tid++) {
-                    int ln = tid & 31, wp = tid >> 5;
-                    uint32_t tt = 0;
-                    for (int l = 0; l < 5; l++)
-                        if ((ln >> l) & 1) tt |= 1u << lane[l];
-                    for (int w = 0; w < W; w++)
-                        if ((wp >> w) & 1) tt |= 1u << warp[w];
-                    uint64_t s = 0;
-                    for (auto &pt : L.tile)
-                        if ((tt >> pt.first) & 1) s += to_turns(pt.second);
-                    P.tw.push_back(s);
-                }
+        return pre;
+    }
+
+    // Emits a FO_G1F op on register bit r with prefactor `pr` and matrix form
+    // uform (U_NONE for a pure phase op), matrix coefficients at ucoef.
+    void emit_g1f(int r, const Pre &pr, int uform, int ucoef)
+    {
+        cd c0 = std::polar(1.0, pr.th0);
+        int oc0 = add_coef(&c0, 1);
+        int taux = -1, laux = -1, daux = -1;
+        if (!pr.tile.empty()) {
+            std::vector<cd> tab(NT);
+            for (int tid = 0; tid < NT; tid++) {
+                int ln = tid & 31, wp = tid >> 5;
+                uint32_t tt = 0;
+                for (int l = 0; l < 5; l++)
+                    if ((ln >> l) & 1) tt |= 1u << lane[l];
+                for (int w = 0; w < W; w++)
+                    if ((wp >> w) & 1) tt |= 1u << warp[w];
+                double ang = 0;
+                for (auto &pt : pr.tile)
+                    if ((tt >> pt.first) & 1) ang += pt.second;
+                tab[tid] = std::polar(1.0, ang);
             }
-            int li = lin_count++;
-            for (auto &pe : L.ext) {
+            taux = add_coef(tab.data(), NT);
+        }
+        if (!pr.ext.empty()) {
+            laux = lin_count++;
+            for (auto &pe : pr.ext) {
                 P.ext_bit.push_back(pe.first);
                 P.ext_tw.push_back(to_turns(pe.second));
             }
             P.lin_off.push_back((int32_t)P.ext_bit.size());
-            emit(FO_LINR, kv.first, 0, c0, taux, li);
         }
+        {
+            // register-partner table over x without bit r
+            int half = 1 << (RB - 1);
+            std::vector<cd> tab(half);
+            for (int xr = 0; xr < half; xr++) {
+                int x = ((xr >> r) << (r + 1)) | (xr & ((1 << r) - 1));
+                double ang = 0;
+                for (auto &kv : pr.regp)
+                    if ((x >> kv.first) & 1) ang += kv.second;
+                tab[xr] = std::polar(1.0, ang);
+            }
+            daux = add_coef(tab.data(), half);
+        }
+        P.ops.push_back(FOp{FO_G1F, r, uform, ucoef, taux, laux, daux, oc0});
     }
 
     void emit_dense(const Item &it)
     {
+        std::vector<int> ph(it.q, it.q + it.nq);
+        std::map<int, Pre> pre = take_pending(ph);
         if (it.nq == 1) {
             int r = reg_of_tau(tau_of[it.q[0]]);
             const cd *m = it.m;
             bool real = true;
             for (int k = 0; k < 4; k++) real = real && std::abs(m[k].imag()) < 1e-15;
+            int uform, uc;
             if (std::abs(m[0]) < kTiny && std::abs(m[3]) < kTiny) {
                 cd v[2] = {m[1], m[2]};
-                emit(FO_G1X, r, 0, add_coef(v, 2), 0, 0);
+                uform = U_ANTI;
+                uc = add_coef(v, 2);
             } else if (real) {
-                emit(FO_G1R, r, 0, add_coef(m, 4, true), 0, 0);
+                uform = U_REAL;
+                uc = add_coef(m, 4, true);
             } else {
-                emit(FO_G1, r, 0, add_coef(m, 4), 0, 0);
+                uform = U_CPLX;
+                uc = add_coef(m, 4);
             }
+            Pre none;
+            auto f = pre.find(r);
+            emit_g1f(r, f != pre.end() ? f->second : none, uform, uc);
             return;
         }
         int r0 = reg_of_tau(tau_of[it.q[0]]), r1 = reg_of_tau(tau_of[it.q[1]]);
+        for (auto &kv : pre) emit_g1f(kv.first, kv.second, U_NONE, 0);
         // monomial?
         int perm[4];
-        cd ph[4];
+        cd phv[4];
         bool mono = true;
         for (int r = 0; r < 4 && mono; r++) {
             int cnt = 0;
@@ -318,15 +352,15 @@ struct Builder {
                 if (std::abs(it.m[r * 4 + col]) > kTiny) {
                     cnt++;
                     perm[r] = col;
-                    ph[r] = it.m[r * 4 + col];
+                    phv[r] = it.m[r * 4 + col];
                 }
             mono = (cnt == 1);
         }
         if (mono) {
             int packed = perm[0] | (perm[1] << 2) | (perm[2] << 4) | (perm[3] << 6);
-            emit(FO_G2M, r0, r1, add_coef(ph, 4), packed, 0);
+            P.ops.push_back(FOp{FO_G2M, r0, r1, add_coef(phv, 4), packed, 0, 0, 0});
         } else {
-            emit(FO_G2, r0, r1, add_coef(it.m, 16), 0, 0);
+            P.ops.push_back(FOp{FO_G2, r0, r1, add_coef(it.m, 16), 0, 0, 0, 0});
         }
     }
 
@@ -376,8 +410,6 @@ struct Builder {
                 assign_lanes(false);
                 emit(FO_XPOSE, 0, 0, 0, push_map(), 0);
             }
-            std::vector<int> ph(it->q, it->q + it->nq);
-            flush_for(ph);
             emit_dense(*it);
             di++;
             ndense++;
@@ -443,9 +475,11 @@ struct Builder {
         }
         for (int i = 0; i < d.nops; i++) {
             FOp op = P.ops[ps.op_begin + i];
-            if (op.kind == FO_LINR) {
-                op.coef -= ps.tw_begin;
-                if (op.aux >= 0) op.aux -= ps.tw_begin;
+            if (op.kind == FO_G1F) {
+                if (op.j1 != U_NONE) op.coef -= ps.coef_begin;
+                if (op.aux >= 0) op.aux -= ps.coef_begin;
+                op.aux3 -= ps.coef_begin;
+                op.aux4 -= ps.coef_begin;
             } else if (op.kind != FO_XPOSE) {
                 op.coef -= ps.coef_begin;
             }
@@ -463,7 +497,8 @@ struct Builder {
 
 }  // namespace
 
-qsim_status plan_build(const qsim_circuit *cir, qsim_dtype dt, const qsim_run_opts *opts, qsim_plan *P)
+qsim_status plan_build(const qsim_circuit *cir, qsim_dtype dt, const qsim_run_opts *opts, const int *start_l2p,
+                       qsim_plan *P)
 {
     const int n = cir->n;
     qsim_run_opts o{};
@@ -489,7 +524,8 @@ qsim_status plan_build(const qsim_circuit *cir, qsim_dtype dt, const qsim_run_op
 
     // ---- classify gates into items (physical bits after relabels)
     std::vector<int> l2p(n);
-    for (int q = 0; q < n; q++) l2p[q] = q;
+    for (int q = 0; q < n; q++) l2p[q] = start_l2p ? start_l2p[q] : q;
+    P->start_l2p = l2p;
     std::vector<Item> items;
     items.reserve(cir->ngates);
     for (int k = 0; k < cir->ngates; k++) {
@@ -675,7 +711,7 @@ qsim_status plan_build(const qsim_circuit *cir, qsim_dtype dt, const qsim_run_op
         if (!P->passes.empty() && P->steps.back().kind == 0) {
             PlanPass &ps = P->passes.back();
             cd g = B.gphase;
-            P->ops.push_back(FOp{FO_SCALE, 0, 0, B.add_coef(&g, 1), 0, 0});
+            P->ops.push_back(FOp{FO_SCALE, 0, 0, B.add_coef(&g, 1), 0, 0, 0, 0});
             ps.op_end = (int)P->ops.size();
         } else {
             PlanStep st;

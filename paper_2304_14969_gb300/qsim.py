@@ -107,6 +107,7 @@ def _sig(L):
         "qsim_apply_fused": [P, i32, P, P, i32],
         "qsim_run_circuit": [P, P, P],
         "qsim_plan_create": [P, i32, P, pp],
+        "qsim_plan_create_for_state": [P, P, P, pp],
         "qsim_plan_destroy": [P],
         "qsim_plan_info": [P, P],
         "qsim_plan_execute": [P, P],
@@ -177,7 +178,7 @@ def _wrap(name):
 for _n in ["qsim_create", "qsim_wrap", "qsim_destroy", "qsim_set_basis", "qsim_upload", "qsim_download",
            "qsim_device_ptr", "qsim_qubit_map", "qsim_materialize", "qsim_synchronize", "qsim_apply_gate",
            "qsim_apply_cphase", "qsim_apply_2q", "qsim_apply_swap", "qsim_apply_fused", "qsim_run_circuit",
-           "qsim_plan_create", "qsim_plan_destroy", "qsim_plan_info", "qsim_plan_execute", "qsim_norm",
+           "qsim_plan_create", "qsim_plan_create_for_state", "qsim_plan_destroy", "qsim_plan_info", "qsim_plan_execute", "qsim_norm",
            "qsim_renormalize", "qsim_measure_prob", "qsim_probs", "qsim_inner_product", "qsim_bloch",
            "qsim_bloch_all", "qsim_approx_run", "qsim_batch_create", "qsim_batch_destroy", "qsim_batch_upload",
            "qsim_batch_reset", "qsim_batch_run", "qsim_batch_download", "qsim_batch_info", "qsim_autotune",
@@ -315,11 +316,16 @@ class State:
 
 
 class Plan:
-    def __init__(self, circ: Circuit, dtype=QSIM_C64, prec=QSIM_PREC_NATIVE, tile=0):
+    """Fused plan; with `state` it starts from that state's current qubit map."""
+
+    def __init__(self, circ: Circuit, dtype=QSIM_C64, prec=QSIM_PREC_NATIVE, tile=0, state=None):
         self.circ = circ
         o = qsim_run_opts(mode=QSIM_MODE_FUSED, prec=prec, tile_qubits=tile, relabel_swaps=1)
         h = C.c_void_p()
-        qsim_plan_create(circ.ptr(), dtype, C.byref(o), C.byref(h))
+        if state is None:
+            qsim_plan_create(circ.ptr(), dtype, C.byref(o), C.byref(h))
+        else:
+            qsim_plan_create_for_state(circ.ptr(), state.h, C.byref(o), C.byref(h))
         self.h = h
 
     def info(self):
