@@ -115,6 +115,12 @@ cudaError_t launch_pass_t(void *amps, const FPassDev &d, cudaStream_t st)
 
 }  // namespace
 
+qsim_status plan_upload_ext(qsim_plan *P)
+{
+    if (P->dmem || P->passes.empty()) return QSIM_OK;
+    return plan_upload(P);
+}
+
 cudaError_t launch_fused_pass(qsim_state *s, const FPassDev &d)
 {
     const int threads = 1 << (d.t - d.RB);
