@@ -79,18 +79,6 @@ qsim_status plan_upload(qsim_plan *P)
     return QSIM_OK;
 }
 
-int num_sms()
-{
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 152;
-    }
-    return sms;
-}
-
 template <typename R, int RB, int NT, int MINB>
 cudaError_t launch_pass_t(void *amps, const FPassDev &d, cudaStream_t st)
 {

@@ -35,6 +35,18 @@ __device__ __forceinline__ uint64_t expand_bits(uint64_t w, const InsSpec &ins)
     return w;
 }
 
+int num_sms()
+{
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 152;
+    }
+    return sms;
+}
+
 int default_grid(uint64_t work, int threads)
 {
     static int sms = 0;

@@ -102,5 +102,6 @@ void free_scratch(Scratch &sc);
 // Helpers
 inline uint64_t bit(int q) { return (uint64_t)1 << q; }
 int default_grid(uint64_t work, int threads);
+int num_sms();
 
 }  // namespace qs

@@ -107,3 +107,11 @@ def test_multi_controlled_gate_becomes_per_gate_step(Q):
     g += [W.Gate("rz", (3,), (0.3,))]
     info = plan_info(Q, 10, g)
     assert info["per_gate_steps"] >= 2
+
+
+def test_library_has_no_unresolved_internal_symbols(Q):
+    """Every internal (qs::) function the library calls is defined in it."""
+    import subprocess
+    lib = os.path.join(ROOT, "paper_2304_14969_gb300", "libqsim.so")
+    out = subprocess.run(["nm", "-D", "--undefined-only", lib], capture_output=True, text=True).stdout
+    assert "_ZN2qs" not in out, [l for l in out.splitlines() if "_ZN2qs" in l]
