@@ -233,6 +233,21 @@ qsim_status qsim_probs(qsim_state *s, double *host_out);
  * out[1] = im. */
 qsim_status qsim_inner_product(qsim_state *a, qsim_state *b, double out[2]);
 
+/* <a|b> = sum_i conj(a_i) b_i in FP64 for callers that cannot let the library
+ * allocate device memory (the paper has no counterpart: this is a service
+ * variant of qsim_inner_product). a_dev and b_dev are device arrays of 2^n
+ * interleaved complex numbers of dt in the same qubit order, 1 <= n <= 36;
+ * out is host memory (out[0] = re, out[1] = im). Partial sums live in one
+ * fixed 16.4 KB __device__ array of the library, so the call performs no
+ * cudaMalloc, cudaFree or other allocation; it synchronises `stream`
+ * (cudaStream_t, NULL = legacy default). The first call on a device looks up
+ * that array's address (cudaGetSymbolAddress) with the device current; make
+ * that first call before any stream capture. All calls share the array:
+ * calls whose kernels overlap on the GPU race. n outside [1, 36] returns
+ * QSIM_E_INVAL. */
+qsim_status qsim_inner_product_noalloc(const void *a_dev, const void *b_dev, int n, qsim_dtype dt, void *stream,
+                                       double out[2]);
+
 /* Sec. III.A step 1: Bloch vector r = (<X_q>, <Y_q>, <Z_q>) of the reduced
  * state of `qubit`, normalised by the state's norm, FP64. */
 qsim_status qsim_bloch(qsim_state *s, int qubit, double r[3]);

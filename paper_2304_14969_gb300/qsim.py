@@ -116,6 +116,7 @@ def _sig(L):
         "qsim_measure_prob": [P, i32, P],
         "qsim_probs": [P, P],
         "qsim_inner_product": [P, P, P],
+        "qsim_inner_product_noalloc": [P, P, i32, i32, P, P],
         "qsim_bloch": [P, i32, P],
         "qsim_bloch_all": [P, P],
         "qsim_approx_run": [P, f64, P, P],
@@ -179,7 +180,8 @@ for _n in ["qsim_create", "qsim_wrap", "qsim_destroy", "qsim_set_basis", "qsim_u
            "qsim_device_ptr", "qsim_qubit_map", "qsim_materialize", "qsim_synchronize", "qsim_apply_gate",
            "qsim_apply_cphase", "qsim_apply_2q", "qsim_apply_swap", "qsim_apply_fused", "qsim_run_circuit",
            "qsim_plan_create", "qsim_plan_create_for_state", "qsim_plan_destroy", "qsim_plan_info", "qsim_plan_execute", "qsim_norm",
-           "qsim_renormalize", "qsim_measure_prob", "qsim_probs", "qsim_inner_product", "qsim_bloch",
+           "qsim_renormalize", "qsim_measure_prob", "qsim_probs", "qsim_inner_product",
+           "qsim_inner_product_noalloc", "qsim_bloch",
            "qsim_bloch_all", "qsim_approx_run", "qsim_batch_create", "qsim_batch_destroy", "qsim_batch_upload",
            "qsim_batch_reset", "qsim_batch_run", "qsim_batch_download", "qsim_batch_info", "qsim_autotune",
            "qsim_mlp_create", "qsim_mlp_destroy", "qsim_mlp_num_params", "qsim_mlp_get_params",
