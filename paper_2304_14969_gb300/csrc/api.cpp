@@ -291,7 +291,7 @@ qsim_status qsim_apply_fused(qsim_state *s, int k, const int *qubits, const doub
         return QSIM_OK;
     }
     if (prec != QSIM_PREC_3XTF32 && prec != QSIM_PREC_BF16X3) return fail(QSIM_E_INVAL, "unknown prec %d", prec);
-    return fail(QSIM_E_UNSUPPORTED, "tensor-core fused blocks are not available in this build");
+    return apply_fused_tc(s, k, phys, m.data(), prec);
 }
 
 // ------------------------------------------------------- reductions

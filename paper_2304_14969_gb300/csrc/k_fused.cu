@@ -19,6 +19,7 @@ namespace qs {
 qsim_status plan_build(const qsim_circuit *cir, qsim_dtype dt, const qsim_run_opts *opts, const int *start_l2p,
                        qsim_plan *P);
 qsim_status permute_state(qsim_state *s, const std::vector<int> &new_pos);
+qsim_status plan_build_tc(const qsim_circuit *cir, const qsim_run_opts *opts, const int *start_l2p, qsim_plan *P);
 qsim_status validate_circuit(const qsim_circuit *c);
 qsim_status apply_one_gate(qsim_state *s, const qsim_gate &g, const double *pool, int64_t pool_len, bool relabel);
 
@@ -70,12 +71,22 @@ qsim_status plan_upload(qsim_plan *P)
         if (!ps.stage.empty()) memcpy(buf.data() + off, ps.stage.data(), ps.stage.size());
         offs.push_back(off);
     }
+    P->tc_off.clear();
+    for (auto &A : P->tc_A) {
+        size_t off = (buf.size() + 255) & ~(size_t)255;
+        buf.resize(off + A.size());
+        memcpy(buf.data() + off, A.data(), A.size());
+        P->tc_off.push_back(off);
+    }
+    size_t err_off = (buf.size() + 255) & ~(size_t)255;
+    buf.resize(err_off + 256, 0);
     if (buf.empty()) buf.resize(256);
     QS_CUDA(cudaMalloc(&P->dmem, buf.size()));
     P->dbytes = buf.size();
     QS_CUDA(cudaMemcpy(P->dmem, buf.data(), buf.size(), cudaMemcpyHostToDevice));
     for (size_t i = 0; i < P->passes.size(); i++)
         P->passes[i].dev.stage = (const unsigned char *)P->dmem + offs[i];
+    P->d_err = (int *)((unsigned char *)P->dmem + err_off);
     return QSIM_OK;
 }
 
@@ -136,10 +147,15 @@ static qsim_status plan_create_impl(const qsim_circuit *c, qsim_dtype dt, const 
     *out = nullptr;
     QS_TRY(validate_circuit(c));
     if (dt != QSIM_C64 && dt != QSIM_C128) return fail(QSIM_E_INVAL, "unknown dtype");
-    if (opts && opts->prec != QSIM_PREC_NATIVE)
-        return fail(QSIM_E_UNSUPPORTED, "tensor-core fused plans are not available in this build");
     qsim_plan *P = new qsim_plan();
-    qsim_status st = plan_build(c, dt, opts, start, P);
+    qsim_status st;
+    if (opts && opts->prec != QSIM_PREC_NATIVE) {
+        if (opts->prec != QSIM_PREC_3XTF32 && opts->prec != QSIM_PREC_BF16X3) st = fail(QSIM_E_INVAL, "unknown prec");
+        else if (dt != QSIM_C64) st = fail(QSIM_E_UNSUPPORTED, "tensor-core plans take complex64 kets");
+        else st = plan_build_tc(c, opts, start, P);
+    } else {
+        st = plan_build(c, dt, opts, start, P);
+    }
     if (st != QSIM_OK) {
         delete P;
         return st;
@@ -178,7 +194,7 @@ qsim_status qsim_plan_info(const qsim_plan *p, int64_t info[8])
 {
     clear_error();
     if (!p || !info) return fail(QSIM_E_INVAL, "NULL argument");
-    info[0] = (int64_t)p->passes.size();
+    info[0] = (int64_t)(p->passes.size() + p->tc_spec.size());
     info[1] = p->ngates;
     info[2] = p->ndense;
     info[3] = p->nswaps;
@@ -196,7 +212,7 @@ qsim_status qsim_plan_execute(qsim_state *s, const qsim_plan *p)
     clear_error();
     if (!s || !s->amps || !p) return fail(QSIM_E_INVAL, "NULL argument");
     if (p->n != s->n || p->dt != s->dt) return fail(QSIM_E_INVAL, "plan and state differ in n or dtype");
-    if (!p->dmem && !p->passes.empty()) QS_TRY(plan_upload(const_cast<qsim_plan *>(p)));
+    if (!p->dmem && (!p->passes.empty() || !p->tc_A.empty())) QS_TRY(plan_upload(const_cast<qsim_plan *>(p)));
     if (s->l2p != p->start_l2p) {
         // move logical qubit L from physical bit s->l2p[L] to p->start_l2p[L]
         std::vector<int> to(s->n);
@@ -219,12 +235,22 @@ qsim_status qsim_plan_execute(qsim_state *s, const qsim_plan *p)
                 }
                 QS_CUDA(launch_gate1(s, st.mat.data(), g.q0, cmask, cval));
             }
+        } else if (st.kind == 3) {
+            QS_CUDA(tc_launch(s, p->tc_spec[st.pass], (const unsigned char *)p->dmem + p->tc_off[st.pass],
+                              (qsim_prec)p->prec, p->d_err));
         } else {
             cd m[4] = {st.phase, 0.0, 0.0, st.phase};
             QS_CUDA(launch_gate1(s, m, 0, 0, 0));
         }
     }
     s->l2p = p->final_l2p;
+    if (!p->tc_spec.empty()) {
+        // tensor-core plans report a bounded MMA wait that gave up (synchronises)
+        int herr = 0;
+        QS_CUDA(cudaMemcpyAsync(&herr, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+        QS_CUDA(cudaStreamSynchronize(s->stream));
+        if (herr) return fail(QSIM_E_TIMEOUT, "tensor-core block: MMA completion wait gave up");
+    }
     return QSIM_OK;
 }
 

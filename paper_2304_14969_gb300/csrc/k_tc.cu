@@ -1,0 +1,359 @@
+// Dense k-qubit block on the 5th-generation tensor cores (tcgen05), k <= 6.
+//
+// Table I of arXiv 2304.14969 ("coalesced gates ... single traversal"):
+// a run of gates fused into one 2^k x 2^k unitary U is a dense contraction
+// of U with the ket viewed as a (2^k) x (2^n / 2^k) matrix of groups. With
+// the real embedding
+//     [Re y]   [Re U  -Im U] [Re x]
+//     [Im y] = [Im U   Re U] [Im x]
+// interleaved as rows 2r + {re, im}, the product is a real GEMM
+// D (128 x N) = A (128 x 128) * B (128 x N) for k = 6; blocks with k < 6 are
+// padded with identity qubits (U (x) I), so every block uses M = K = 128.
+//
+// Precision: the 3-product split x = x_hi + x_lo of both operands
+// (a_hi b_hi + a_hi b_lo + a_lo b_hi, FP32 accumulation in TMEM), with
+// TF32 parts (kind::tf32) or BF16 parts (kind::f16 with BF16 inputs).
+//
+// One CTA = one warpgroup (128 threads). A (hi, lo) is staged once per CTA
+// in shared memory in the canonical K-major no-swizzle layout (8-row x
+// 16-byte core matrices, K-adjacent core matrices 128 B apart). Per
+// iteration the CTA gathers N groups, splits them into B_hi / B_lo (same
+// layout, rows = groups), one thread issues the 3 x K/kstep MMAs into a
+// 128 x N FP32 accumulator in TMEM and commits to an mbarrier, every thread
+// waits (bounded), each warp reads its 32 TMEM lanes (rows), the tile goes
+// through shared memory and back to HBM coalesced.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+
+#include "qsim_internal.h"
+
+namespace qs {
+
+static const int kTcThreads = 128;
+static const int kTcRows = 128;   // M = K
+static const long long kTcSpin = 1ll << 26;
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// byte offset of element (row, k) in the canonical K-major no-swizzle layout
+__host__ __device__ __forceinline__ uint32_t canon_off(int row, int k, int es)
+{
+    const int per = 16 / es;                       // elements per core-matrix row
+    const uint32_t sbo = (uint32_t)(kTcRows / per) * 128u;
+    return (uint32_t)(row >> 3) * sbo + (uint32_t)(k / per) * 128u + (uint32_t)(row & 7) * 16u +
+           (uint32_t)(k % per) * (uint32_t)es;
+}
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;   // descriptor version of this architecture; no swizzle, base offset 0
+    return d;
+}
+
+__device__ __forceinline__ void mma_issue(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accum, int kind_tf32)
+{
+    if (kind_tf32)
+        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                     "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+                     "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum));
+    else
+        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+                     "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum));
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity)
+{
+    for (long long it = 0; it < kTcSpin; it++) {
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.b32 %0, 1, 0, p;\n\t}\n"
+                     : "=r"(done)
+                     : "r"(mbar), "r"(parity)
+                     : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+template <int ES>
+__device__ __forceinline__ void split_store(unsigned char *hi, unsigned char *lo, uint32_t off, float x)
+{
+    if constexpr (ES == 4) {
+        uint32_t h;
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+        float hf = __uint_as_float(h);
+        *(uint32_t *)(hi + off) = h;
+        *(float *)(lo + off) = x - hf;
+    } else {
+        __nv_bfloat16 h = __float2bfloat16_rn(x);
+        float hf = __bfloat162float(h);
+        *(__nv_bfloat16 *)(hi + off) = h;
+        *(__nv_bfloat16 *)(lo + off) = __float2bfloat16_rn(x - hf);
+    }
+}
+
+// PREC: 1 = 3xTF32 (ES 4, N 64), 2 = BF16x3 (ES 2, N 128)
+template <int PREC>
+__global__ void __launch_bounds__(kTcThreads, 1) k_tc_block(float2 *__restrict__ a, uint64_t ngroups, TcSpec ts,
+                                                            const unsigned char *__restrict__ Ag, int *err)
+{
+    constexpr int ES = PREC == 1 ? 4 : 2;
+    constexpr int N = PREC == 1 ? 64 : 128;
+    constexpr int KSTEP = PREC == 1 ? 8 : 16;          // K per instruction
+    constexpr uint32_t A_BYTES = kTcRows * kTcRows * ES;
+    constexpr uint32_t B_BYTES = N * kTcRows * ES;
+    constexpr int SROW = kTcRows + 2;                  // padded staging row (floats)
+    constexpr uint32_t SBO = (uint32_t)(kTcRows / (16 / ES)) * 128u;
+    extern __shared__ __align__(1024) unsigned char sm[];
+    unsigned char *Ahi = sm, *Alo = sm + A_BYTES, *Bhi = sm + 2 * A_BYTES, *Blo = Bhi + B_BYTES;
+    float *stage = (float *)Bhi;                       // D staging reuses the B region
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_fail;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    // A (hi, lo) arrives in its final byte layout
+    {
+        const int4 *src = (const int4 *)Ag;
+        int4 *dst = (int4 *)Ahi;
+        for (uint32_t i = tid; i < 2 * A_BYTES / 16; i += kTcThreads) dst[i] = src[i];
+    }
+    if (tid == 0) {
+        s_fail = 0;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar)));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_base)),
+                     "r"((uint32_t)N));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tmem_base;
+    const uint32_t idesc = (1u << 4) | ((PREC == 1 ? 2u : 1u) << 7) | ((PREC == 1 ? 2u : 1u) << 10) |
+                           ((uint32_t)(N >> 3) << 17) | ((uint32_t)(kTcRows >> 4) << 24);
+    uint32_t phase = 0;
+
+    for (uint64_t g0 = (uint64_t)blockIdx.x * N; g0 < ngroups; g0 += (uint64_t)gridDim.x * N) {
+        // ---- gather N groups (rows of B) and split them
+        for (int e = tid; e < N * 64; e += kTcThreads) {
+            const int nn = e % N, l = e / N;
+            const uint64_t g = g0 + nn;
+            float2 v = make_float2(0.f, 0.f);
+            if (g < ngroups) {
+                uint64_t base = g;
+                for (int j = 0; j < 6; j++) {
+                    int p = ts.ins.pos[j];
+                    base = ((base >> p) << (p + 1)) | (base & ((1ull << p) - 1));
+                }
+                uint64_t idx = base;
+#pragma unroll
+                for (int b = 0; b < 6; b++)
+                    if ((l >> b) & 1) idx |= 1ull << ts.q[b];
+                v = a[idx];
+            }
+            split_store<ES>(Bhi, Blo, canon_off(nn, 2 * l, ES), v.x);
+            split_store<ES>(Bhi, Blo, canon_off(nn, 2 * l + 1, ES), v.y);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        // ---- D = A_hi B_hi + A_hi B_lo + A_lo B_hi
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t ah = smem_addr(Ahi), al = smem_addr(Alo), bh = smem_addr(Bhi), bl = smem_addr(Blo);
+            uint32_t accum = 0;
+            for (int part = 0; part < 3; part++) {
+                const uint32_t abase = part == 2 ? al : ah, bbase = part == 1 ? bl : bh;
+                for (int kk = 0; kk < kTcRows / KSTEP; kk++) {
+                    const uint32_t koff = (uint32_t)kk * 256u;   // two K-adjacent core matrices per step
+                    mma_issue(tmem, smem_desc(abase + koff, 128u, SBO), smem_desc(bbase + koff, 128u, SBO), idesc,
+                              accum, PREC == 1);
+                    accum = 1;
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_addr(&mbar)));
+        }
+        if (!mbar_wait(smem_addr(&mbar), phase)) {
+            s_fail = 1;
+            atomicExch(err, 1);
+        }
+        phase ^= 1;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        __syncthreads();
+        if (s_fail) break;
+        // ---- TMEM -> registers -> staging (row m = this thread's lane)
+        const int m = warp * 32 + lane;
+#pragma unroll 1
+        for (int c0 = 0; c0 < N; c0 += 32) {
+            uint32_t r[32];
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+                "%13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
+                "[%32];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                  "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                  "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int j = 0; j < 32; j++) stage[(c0 + j) * SROW + m] = __uint_as_float(r[j]);
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
+        // ---- write the N groups back
+        for (int e = tid; e < N * 64; e += kTcThreads) {
+            const int nn = e % N, l = e / N;
+            const uint64_t g = g0 + nn;
+            if (g >= ngroups) continue;
+            uint64_t base = g;
+            for (int j = 0; j < 6; j++) {
+                int p = ts.ins.pos[j];
+                base = ((base >> p) << (p + 1)) | (base & ((1ull << p) - 1));
+            }
+            uint64_t idx = base;
+#pragma unroll
+            for (int b = 0; b < 6; b++)
+                if ((l >> b) & 1) idx |= 1ull << ts.q[b];
+            a[idx] = make_float2(stage[nn * SROW + 2 * l], stage[nn * SROW + 2 * l + 1]);
+        }
+        __syncthreads();   // staging (B region) free for the next gather
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)N));
+}
+
+// Host side: pads the block to 6 qubits (identity on the highest unused
+// qubits, which keeps the low qubits outside the block so consecutive groups
+// are consecutive amplitudes), forms A = [[Re U, -Im U], [Im U, Re U]]
+// interleaved, and splits it into hi / lo parts in the kernel's byte layout.
+qsim_status tc_build(int n, int k, const int *phys, const cd *u, qsim_prec prec, std::vector<unsigned char> &A,
+                     TcSpec &ts)
+{
+    if (k > 6) return fail(QSIM_E_UNSUPPORTED, "tensor-core blocks take k <= 6 (M = 128)");
+    if (n < 6) return fail(QSIM_E_UNSUPPORTED, "tensor-core blocks need n >= 6");
+    int q[6];
+    uint64_t used = 0;
+    for (int b = 0; b < k; b++) {
+        q[b] = phys[b];
+        used |= bit(phys[b]);
+    }
+    int kk = k;
+    for (int p = n - 1; p >= 0 && kk < 6; p--)
+        if (!(used & bit(p))) {
+            q[kk++] = p;
+            used |= bit(p);
+        }
+    const int D = 1 << k;
+    const int es = prec == QSIM_PREC_3XTF32 ? 4 : 2;
+    const size_t abytes = (size_t)kTcRows * kTcRows * es;
+    A.assign(2 * abytes, 0);
+    for (int r = 0; r < 64; r++)
+        for (int c = 0; c < 64; c++) {
+            cd v = ((r >> k) == (c >> k)) ? u[(r & (D - 1)) * D + (c & (D - 1))] : cd(0.0);
+            double e[2][2] = {{v.real(), -v.imag()}, {v.imag(), v.real()}};
+            for (int ri = 0; ri < 2; ri++)
+                for (int ci = 0; ci < 2; ci++) {
+                    int row = 2 * r + ri, col = 2 * c + ci;
+                    float x = (float)e[ri][ci];
+                    uint32_t off = canon_off(row, col, es);
+                    if (es == 4) {
+                        // TF32 hi part: keep 10 mantissa bits, round half away from zero
+                        uint32_t bits;
+                        memcpy(&bits, &x, 4);
+                        uint32_t h = (bits + 0x1000u) & 0xFFFFE000u;
+                        float hf;
+                        memcpy(&hf, &h, 4);
+                        float lo = x - hf;
+                        memcpy(A.data() + off, &h, 4);
+                        memcpy(A.data() + abytes + off, &lo, 4);
+                    } else {
+                        __nv_bfloat16 h = __float2bfloat16_rn(x);
+                        float hf = __bfloat162float(h);
+                        __nv_bfloat16 lo = __float2bfloat16_rn(x - hf);
+                        memcpy(A.data() + off, &h, 2);
+                        memcpy(A.data() + abytes + off, &lo, 2);
+                    }
+                }
+        }
+    std::vector<int> pos(q, q + 6);
+    std::sort(pos.begin(), pos.end());
+    for (int b = 0; b < 6; b++) ts.q[b] = q[b];
+    ts.ins.npos = 6;
+    for (int b = 0; b < 6; b++) ts.ins.pos[b] = pos[b];
+    return QSIM_OK;
+}
+
+// Launches one block (stream-ordered; the kernel raises *derr if an MMA
+// completion wait gave up).
+cudaError_t tc_launch(qsim_state *s, const TcSpec &ts, const unsigned char *dA, qsim_prec prec, int *derr)
+{
+    const uint64_t ngroups = s->N() >> 6;
+    if (prec == QSIM_PREC_3XTF32) {
+        const int N = 64;
+        size_t smem = 2 * (size_t)kTcRows * kTcRows * 4 +
+                      std::max<size_t>(2 * (size_t)N * kTcRows * 4, (size_t)N * (kTcRows + 2) * 4);
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(k_tc_block<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            attr = true;
+        }
+        int grid = (int)std::min<uint64_t>((ngroups + N - 1) / N, (uint64_t)num_sms());
+        k_tc_block<1><<<grid, kTcThreads, smem, s->stream>>>((float2 *)s->amps, ngroups, ts, dA, derr);
+    } else {
+        const int N = 128;
+        size_t smem = 2 * (size_t)kTcRows * kTcRows * 2 +
+                      std::max<size_t>(2 * (size_t)N * kTcRows * 2, (size_t)N * (kTcRows + 2) * 4);
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(k_tc_block<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            attr = true;
+        }
+        int grid = (int)std::min<uint64_t>((ngroups + N - 1) / N, (uint64_t)num_sms());
+        k_tc_block<2><<<grid, kTcThreads, smem, s->stream>>>((float2 *)s->amps, ngroups, ts, dA, derr);
+    }
+    return cudaGetLastError();
+}
+
+qsim_status apply_fused_tc(qsim_state *s, int k, const int *phys, const cd *u, qsim_prec prec)
+{
+    if (s->dt != QSIM_C64) return fail(QSIM_E_UNSUPPORTED, "tensor-core blocks take complex64 kets");
+    std::vector<unsigned char> A;
+    TcSpec ts;
+    QS_TRY(tc_build(s->n, k, phys, u, prec, A, ts));
+    unsigned char *dA = nullptr;
+    int *derr = nullptr;
+    QS_CUDA(cudaMallocAsync((void **)&dA, A.size(), s->stream));
+    QS_CUDA(cudaMallocAsync((void **)&derr, sizeof(int), s->stream));
+    QS_CUDA(cudaMemsetAsync(derr, 0, sizeof(int), s->stream));
+    QS_CUDA(cudaMemcpyAsync(dA, A.data(), A.size(), cudaMemcpyHostToDevice, s->stream));
+    cudaError_t e = tc_launch(s, ts, dA, prec, derr);
+    int herr = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    cudaFreeAsync(dA, s->stream);
+    cudaFreeAsync(derr, s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "tensor-core block");
+    if (herr) return fail(QSIM_E_TIMEOUT, "tensor-core block: MMA completion wait gave up");
+    return QSIM_OK;
+}
+
+}  // namespace qs

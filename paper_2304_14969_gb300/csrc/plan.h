@@ -78,7 +78,8 @@ struct PlanPass {
 };
 
 struct PlanStep {
-    int kind;                // 0 fused pass, 1 per-gate gate (physical qubits), 2 global phase
+    int kind;                // 0 fused pass, 1 per-gate gate (physical qubits), 2 global phase,
+                             // 3 tensor-core block (pass = index into tc_spec)
     int pass;                // kind 0
     qsim_gate gate;          // kind 1 (physical qubits, matrix in mats)
     std::vector<cd> mat;     // kind 1: 2x2 or 4x4
@@ -103,6 +104,12 @@ struct qsim_plan {
     std::vector<qs::FMap> maps;
     std::vector<int32_t> lin_off, ext_bit;
     std::vector<uint64_t> ext_tw;
+    // tensor-core blocks
+    int prec = QSIM_PREC_NATIVE;
+    std::vector<qs::TcSpec> tc_spec;
+    std::vector<std::vector<unsigned char>> tc_A;
+    std::vector<size_t> tc_off;
+    int *d_err = nullptr;
     // device copies
     void *dmem = nullptr;
     size_t dbytes = 0;

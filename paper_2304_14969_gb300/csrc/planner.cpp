@@ -734,3 +734,130 @@ qsim_status plan_build(const qsim_circuit *cir, qsim_dtype dt, const qsim_run_op
 }
 
 }  // namespace qs
+
+namespace qs {
+
+// Tensor-core plans: the circuit is fused into dense blocks of at most 6
+// qubits by the same commutation-aware sweep as the fused passes (a gate
+// joins the current block when its qubits fit and no earlier gate left for
+// later shares a qubit with it). Each block's unitary is the FP64 product of
+// its gates embedded in the block's qubits (new qubits join as higher
+// block bits); SWAPs are relabels. Every block is one pass of the tensor-core
+// kernel.
+qsim_status plan_build_tc(const qsim_circuit *cir, const qsim_run_opts *opts, const int *start_l2p, qsim_plan *P)
+{
+    const int n = cir->n;
+    if (n < 6) return fail(QSIM_E_UNSUPPORTED, "tensor-core plans need n >= 6");
+    P->n = n;
+    P->dt = QSIM_C64;
+    P->prec = opts->prec;
+    P->ngates = cir->ngates;
+    std::vector<int> l2p(n);
+    for (int q = 0; q < n; q++) l2p[q] = start_l2p ? start_l2p[q] : q;
+    P->start_l2p = l2p;
+    struct G {
+        std::vector<int> q;      // physical qubits, local bit j <-> q[j]
+        std::vector<cd> m;       // 2^|q| x 2^|q|
+    };
+    std::vector<G> gates;
+    for (int k = 0; k < cir->ngates; k++) {
+        const qsim_gate &g = cir->gates[k];
+        if (g.kind == QSIM_G_SWAP) {
+            std::swap(l2p[g.q0], l2p[g.q1]);
+            P->nswaps++;
+            continue;
+        }
+        cd m[16];
+        int d = gate_matrix(g, cir->matrices, cir->nmatrix_doubles, m);
+        G x;
+        if (d == 4) {
+            x.q = {l2p[g.q0], l2p[g.q1]};
+            x.m.assign(m, m + 16);
+        } else {
+            x.q = {l2p[g.q0]};
+            for (int j = 0; j < g.ncontrols; j++) x.q.push_back(l2p[g.controls[j]]);
+            int dim = 1 << x.q.size();
+            x.m.assign((size_t)dim * dim, 0.0);
+            int want = 0;
+            for (int j = 0; j < g.ncontrols; j++) want |= (int)((g.control_values >> j) & 1) << j;
+            for (int r = 0; r < dim; r++)
+                for (int c = 0; c < dim; c++) {
+                    if ((r >> 1) != (c >> 1)) continue;
+                    x.m[(size_t)r * dim + c] = ((r >> 1) == want) ? m[(r & 1) * 2 + (c & 1)]
+                                                                 : cd((r & 1) == (c & 1) ? 1.0 : 0.0);
+                }
+        }
+        gates.push_back(std::move(x));
+    }
+    P->final_l2p = l2p;
+    std::vector<const G *> rem;
+    for (auto &g : gates) rem.push_back(&g);
+    while (!rem.empty()) {
+        std::vector<int> Q;
+        std::vector<cd> U(1, 1.0);
+        std::vector<char> blocked(n, 0);
+        std::vector<const G *> left;
+        int ng = 0;
+        for (const G *g : rem) {
+            bool blk = false;
+            for (int q : g->q) blk = blk || blocked[q];
+            std::vector<int> nq = Q;
+            for (int q : g->q)
+                if (std::find(nq.begin(), nq.end(), q) == nq.end()) nq.push_back(q);
+            if (blk || nq.size() > 6) {
+                for (int q : g->q) blocked[q] = 1;
+                left.push_back(g);
+                continue;
+            }
+            // extend U to nq (new qubits are higher bits: U <- I (x) U)
+            int od = 1 << Q.size(), nd = 1 << nq.size();
+            if (nd != od) {
+                std::vector<cd> V((size_t)nd * nd, 0.0);
+                for (int r = 0; r < nd; r++)
+                    for (int c = 0; c < nd; c++)
+                        if ((r / od) == (c / od)) V[(size_t)r * nd + c] = U[(size_t)(r % od) * od + (c % od)];
+                U.swap(V);
+                Q = nq;
+            }
+            // embed the gate and left-multiply
+            std::vector<int> pos(g->q.size());
+            for (size_t j = 0; j < g->q.size(); j++)
+                pos[j] = (int)(std::find(Q.begin(), Q.end(), g->q[j]) - Q.begin());
+            int gmask = 0;
+            for (int p : pos) gmask |= 1 << p;
+            int gd = 1 << g->q.size();
+            auto loc = [&](int r) {
+                int l = 0;
+                for (size_t j = 0; j < pos.size(); j++) l |= ((r >> pos[j]) & 1) << j;
+                return l;
+            };
+            std::vector<cd> Gm((size_t)nd * nd, 0.0);
+            for (int r = 0; r < nd; r++)
+                for (int c = 0; c < nd; c++)
+                    if ((r & ~gmask) == (c & ~gmask)) Gm[(size_t)r * nd + c] = g->m[(size_t)loc(r) * gd + loc(c)];
+            std::vector<cd> W((size_t)nd * nd, 0.0);
+            for (int r = 0; r < nd; r++)
+                for (int x = 0; x < nd; x++) {
+                    cd a = Gm[(size_t)r * nd + x];
+                    if (a == cd(0.0)) continue;
+                    for (int c = 0; c < nd; c++) W[(size_t)r * nd + c] += a * U[(size_t)x * nd + c];
+                }
+            U.swap(W);
+            ng++;
+        }
+        TcSpec ts;
+        std::vector<unsigned char> A;
+        QS_TRY(tc_build(n, (int)Q.size(), Q.data(), U.data(), (qsim_prec)opts->prec, A, ts));
+        P->tc_spec.push_back(ts);
+        P->tc_A.push_back(std::move(A));
+        PlanStep st;
+        st.kind = 3;
+        st.pass = (int)P->tc_spec.size() - 1;
+        P->steps.push_back(st);
+        P->ndense += ng;
+        rem = left;
+    }
+    return QSIM_OK;
+}
+
+}  // namespace qs

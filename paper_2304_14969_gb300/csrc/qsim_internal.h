@@ -73,6 +73,16 @@ struct InsSpec {
     int pos[12] = {0};  // ascending
 };
 
+// Tensor-core block (k <= 6, padded to 6): physical bit of block bit b and
+// the sorted block qubits for group expansion.
+struct TcSpec {
+    int q[6];
+    InsSpec ins;
+};
+qsim_status tc_build(int n, int k, const int *phys, const cd *u, qsim_prec prec, std::vector<unsigned char> &A,
+                     TcSpec &ts);
+cudaError_t tc_launch(qsim_state *s, const TcSpec &ts, const unsigned char *dA, qsim_prec prec, int *derr);
+
 // ------------------------------------------------------ kernel launchers
 // (all stream-ordered, no sync; return cuda errors)
 cudaError_t launch_gate1(qsim_state *s, const cd u[4], int t, uint64_t cmask, uint64_t cval);
@@ -80,6 +90,7 @@ cudaError_t launch_gate2(qsim_state *s, const cd u[16], int q0, int q1);
 cudaError_t launch_cphase(qsim_state *s, int q0, int q1, double theta);
 cudaError_t launch_swap(qsim_state *s, int q0, int q1);
 cudaError_t launch_fused_simt(qsim_state *s, int k, const int *phys, const cd *u);
+qsim_status apply_fused_tc(qsim_state *s, int k, const int *phys, const cd *u, qsim_prec prec);
 cudaError_t launch_set_basis(qsim_state *s, uint64_t x_phys);
 cudaError_t launch_scale(void *amps, qsim_dtype dt, uint64_t N, double f, cudaStream_t st);
 cudaError_t launch_permute(const void *src, void *dst, qsim_dtype dt, int n, const int *new_of_old,

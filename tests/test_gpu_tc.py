@@ -1,0 +1,81 @@
+"""Tensor-core dense blocks (tcgen05, 3xTF32 and BF16x3 splits with FP32
+accumulation) against the FP64 oracle's k-qubit block application.
+Tolerance: state infidelity <= 1e-6 (complex64 ket)."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2304_14969_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def Q():
+    from paper_2304_14969_gb300 import build, qsim
+    build.build()
+    qsim.lib()
+    return qsim
+
+
+def infid(a, b):
+    a = a.astype(np.complex128)
+    b = b.astype(np.complex128)
+    return 1 - abs(np.vdot(a, b)) ** 2 / (np.vdot(a, a).real * np.vdot(b, b).real)
+
+
+def apply(Q, n, qs, U, prec, x):
+    st = Q.State(n, 0)
+    st.upload(x)
+    k = len(qs)
+    qa = (C.c_int * k)(*qs)
+    u = np.ascontiguousarray(np.asarray(U, dtype=np.complex128).ravel().view(np.float64))
+    Q.qsim_apply_fused(st.h, k, qa, u.ctypes.data_as(C.c_void_p), prec)
+    y = st.download()
+    st.close()
+    return y
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("n,qs", [(6, [0, 1, 2, 3, 4, 5]), (8, [2, 7, 0, 5, 3, 6]), (12, [11, 3, 8, 5, 9, 1]),
+                                  (16, [4, 15, 9]), (18, [0]), (20, [19, 18, 17, 16, 2, 10])])
+def test_tc_block_vs_oracle(Q, prec, n, qs):
+    x = W.gaussian_state(n, n)
+    U = W.random_unitary(len(qs), 7 + n)
+    ref = oracle.apply_kq(x, qs, U)
+    y = apply(Q, n, qs, U, prec, x)
+    assert infid(y, ref) <= 1e-6
+    assert np.max(np.abs(y - ref)) <= 2e-5 * np.max(np.abs(ref)) + 1e-7
+
+
+def test_tc_block_rejects_k7_and_c128(Q):
+    st = Q.State(10, 1)
+    qa = (C.c_int * 2)(0, 1)
+    u = np.ascontiguousarray(np.eye(4, dtype=np.complex128).ravel().view(np.float64))
+    with pytest.raises(Q.QsimError) as e:
+        Q.qsim_apply_fused(st.h, 2, qa, u.ctypes.data_as(C.c_void_p), 2)
+    assert e.value.status == 6
+    st.close()
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("which", ["grid", "random", "qft"])
+def test_tc_plan_vs_oracle(Q, prec, which):
+    """Whole circuits fused into <= 6-qubit blocks on the tensor cores."""
+    if which == "grid":
+        n, g, x = 20, W.grid_rcs_circuit(4, 5, 8, seed=2), W.basis_state(20, 0)
+    elif which == "random":
+        n = 14
+        g, x = W.random_1q_circuit(n, 200, 5), W.gaussian_state(n, 5)
+    else:
+        n = 16
+        g, x = W.qft_circuit(n), W.gaussian_state(n, 6)
+    ref = oracle.apply_circuit(x, g)
+    st = Q.State(n, 0)
+    st.upload(x)
+    st.run(Q.Circuit(n, g), mode=1, prec=prec, relabel=1)
+    y = st.download()
+    st.close()
+    assert infid(y, ref) <= 1e-6
