@@ -41,6 +41,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip the per-gate FP64, grid and CPU legs")
+    ap.add_argument("--workload", default="qft27",
+                    help="qft27 (default, fused SIMT passes) or grid<n>_tc (n-qubit grid circuit on tensor-core "
+                         "blocks, BF16x3), used for small profiling captures")
     return ap.parse_args()
 
 
@@ -173,6 +176,9 @@ def main():
         return
     if args.warmup < 3:
         args.warmup = 3
+    if args.workload != "qft27":
+        run_grid_tc(args)
+        return
     import torch
     rank, world = dist_init(args.gpus)
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -302,6 +308,57 @@ def main():
     st.close()
 
 
+def time_plan(Q, C, plan, st, reps):
+    """Device time of plan executions (events on the ket's stream)."""
+    import torch
+    s = torch.cuda.Stream()
+    a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    plan.execute(st)
+    Q.qsim_synchronize(st.h)
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(reps):
+        plan.execute(st)
+    z.record()
+    Q.qsim_synchronize(st.h)
+    torch.cuda.synchronize()
+    return a.elapsed_time(z) / reps
+
+
+def run_grid_tc(args):
+    """Grid circuit on tensor-core blocks (profiling workload)."""
+    import ctypes as C
+    import torch
+    from paper_2304_14969_gb300 import build, qsim as Q
+    from paper_2304_14969_gb300 import workloads as W
+    build.build()
+    Q.lib()
+    n = int(args.workload[4:].split("_")[0])
+    rows, cols = W.grid_shape(n)
+    g = W.grid_rcs_circuit(rows, cols, 10, seed=0, n=n)
+    circ = Q.Circuit(n, g)
+    st = Q.State(n, Q.QSIM_C64)
+    plan = Q.Plan(circ, dtype=Q.QSIM_C64, prec=Q.QSIM_PREC_BF16X3)
+    for _ in range(args.warmup):
+        Q.qsim_set_basis(st.h, 0)
+        plan.execute(st)
+    Q.qsim_synchronize(st.h)
+    ms = 0.0
+    for _ in range(args.steps):
+        Q.qsim_set_basis(st.h, 0)
+        ms += time_plan(Q, C, plan, st, 1)
+    ms /= args.steps
+    nb = plan.info()["passes"]
+    N = 1 << n
+    print(json.dumps({"metric": "amplitude-gate updates/s", "value": len(g) * N / (ms * 1e-3), "unit": "updates/s",
+                      "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                      "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                      "data": "synthetic",
+                      "config": {"workload": f"grid{n}_c64_tc_bf16x3", "n_qubits": n, "gates": len(g), "blocks": nb},
+                      "roofline": {"bound": "hbm", "kernel": "k_tc_block",
+                                   "achieved": 2 * 8 * N / (ms / nb * 1e-3) / 1e9}}))
+
+
 def extra_legs(Q, W, C, torch, circ, x, n, ng):
     out = {}
     N = 1 << n
@@ -350,7 +407,43 @@ def extra_legs(Q, W, C, torch, circ, x, n, ng):
     gi = gp.info()
     out["grid30_c64_fused"] = {"updates_per_s": len(g) * (1 << 30) / tg, "ms": tg * 1e3, "passes": gi["passes"],
                                "hbm_gbs": gi["passes"] * 2 * 8 * (1 << 30) / tg / 1e9}
+    # the same circuit on tensor-core blocks (BF16x3 and 3xTF32 splits)
+    peaks = {}
+    pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pp):
+        peaks = json.load(open(pp))
+    for prec, name in ((Q.QSIM_PREC_BF16X3, "bf16x3"), (Q.QSIM_PREC_3XTF32, "3xtf32")):
+        tp = Q.Plan(gc, dtype=Q.QSIM_C64, prec=prec)
+        st2 = Q.State(30, Q.QSIM_C64)
+        ms = time_plan(Q, C, tp, st2, 3)
+        nb = tp.info()["passes"]
+        achieved = 2 * 8 * (1 << 30) / (ms / nb * 1e-3) / 1e9
+        # agreement with the SIMT result from |0...0> (both complex64)
+        Q.qsim_set_basis(sg.h, 0)
+        gp.execute(sg)
+        Q.qsim_set_basis(st2.h, 0)
+        tp.execute(st2)
+        ip = (C.c_double * 2)()
+        Q.qsim_inner_product(sg.h, st2.h, ip)
+        out[f"grid30_c64_tc_{name}"] = {
+            "updates_per_s": len(g) * (1 << 30) / (ms * 1e-3), "ms": ms, "blocks": nb,
+            "kernel": "k_tc_block", "hbm_gbs_per_block": achieved,
+            "frac_of_hbm": achieved / peaks.get("hbm_gbs", 6800.0),
+            "infidelity_vs_simt": 1.0 - (ip[0] ** 2 + ip[1] ** 2)}
+        st2.close()
     sg.close()
+    # the plain per-gate FP64 path on the grid circuit (one run)
+    s128 = Q.State(30, Q.QSIM_C128)
+    o = Q.qsim_run_opts(mode=0, relabel_swaps=1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Q.qsim_run_circuit(s128.h, gc.ptr(), C.byref(o))
+    Q.qsim_synchronize(s128.h)
+    pg = time.perf_counter() - t0
+    out["grid30_per_gate_fp64"] = {"updates_per_s": len(g) * (1 << 30) / pg, "ms": pg * 1e3, "dtype": "c128"}
+    best = min(out[k]["ms"] for k in out if k.startswith("grid30_c64"))
+    out["grid30_speedup_vs_per_gate_fp64"] = pg * 1e3 / best
+    s128.close()
     return out
 
 
