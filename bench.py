@@ -425,11 +425,14 @@ def extra_legs(Q, W, C, torch, circ, x, n, ng):
         tp.execute(st2)
         ip = (C.c_double * 2)()
         Q.qsim_inner_product(sg.h, st2.h, ip)
+        na, nb2 = C.c_double(), C.c_double()
+        Q.qsim_norm(sg.h, C.byref(na))
+        Q.qsim_norm(st2.h, C.byref(nb2))
         out[f"grid30_c64_tc_{name}"] = {
             "updates_per_s": len(g) * (1 << 30) / (ms * 1e-3), "ms": ms, "blocks": nb,
             "kernel": "k_tc_block", "hbm_gbs_per_block": achieved,
             "frac_of_hbm": achieved / peaks.get("hbm_gbs", 6800.0),
-            "infidelity_vs_simt": 1.0 - (ip[0] ** 2 + ip[1] ** 2)}
+            "infidelity_vs_simt": 1.0 - (ip[0] ** 2 + ip[1] ** 2) / (na.value * nb2.value)}
         st2.close()
     sg.close()
     # the plain per-gate FP64 path on the grid circuit (one run)

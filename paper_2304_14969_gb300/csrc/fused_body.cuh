@@ -39,13 +39,13 @@ __device__ __forceinline__ V cmul(V a, R br, R bi)
 // ---- register ops (J: register bit, compile time)
 
 // Dense 2x2 on register bit J (form UF) after multiplying every amplitude
-// with bit J set by its prefactor f * D[xr] (xr = register index without
-// bit J). UF: U_NONE pure phase, U_REAL 4 reals, U_CPLX 4 complex, U_ANTI
-// anti-diagonal (2 complex).
-template <int J, int UF, int NR, typename V, typename R>
+// with bit J set by its prefactor (PR: none, D[xr], or f * D[xr]; xr =
+// register index without bit J). UF: U_NONE pure phase, U_REAL 4 reals,
+// U_CPLX 4 complex, U_ANTI anti-diagonal (2 complex), U_HAD (p + q, p - q).
+template <int J, int UF, int PR, int NR, typename V, typename R>
 __device__ __forceinline__ void op_g1f(V (&v)[NR], const R *__restrict__ u, R fr, R fi, const R *__restrict__ D)
 {
-    if constexpr ((1 << J) < NR) {
+    if constexpr ((1 << J) < NR && !(UF == U_NONE && PR == PRE_NONE)) {
         R a0 = 0, a1 = 0, b0 = 0, b1 = 0, c0 = 0, c1 = 0, d0 = 0, d1 = 0;
         if constexpr (UF == U_REAL) {
             a0 = u[0]; b0 = u[1]; c0 = u[2]; d0 = u[3];
@@ -58,11 +58,23 @@ __device__ __forceinline__ void op_g1f(V (&v)[NR], const R *__restrict__ u, R fr
         for (int x = 0; x < NR; x++) {
             if (x & (1 << J)) continue;
             const int xr = ((x >> (J + 1)) << J) | (x & ((1 << J) - 1));
-            const R dr = D[2 * xr], di = D[2 * xr + 1];
-            const R er = fr * dr - fi * di, ei = fr * di + fi * dr;
-            V p = v[x], q = cmul(v[x | (1 << J)], er, ei);
+            V p = v[x], q = v[x | (1 << J)];
+            if constexpr (PR == PRE_D) {
+                q = cmul(q, D[2 * xr], D[2 * xr + 1]);
+            } else if constexpr (PR == PRE_FD) {
+                const R dr = D[2 * xr], di = D[2 * xr + 1];
+                q = cmul(q, fr * dr - fi * di, fr * di + fi * dr);
+            }
             if constexpr (UF == U_NONE) {
                 v[x | (1 << J)] = q;
+            } else if constexpr (UF == U_HAD) {
+                V o0, o1;
+                o0.x = p.x + q.x;
+                o0.y = p.y + q.y;
+                o1.x = p.x - q.x;
+                o1.y = p.y - q.y;
+                v[x] = o0;
+                v[x | (1 << J)] = o1;
             } else if constexpr (UF == U_REAL) {
                 V o0, o1;
                 o0.x = a0 * p.x + b0 * q.x;
@@ -148,17 +160,83 @@ __device__ __forceinline__ void op_g2m(V (&v)[NR], const R *__restrict__ u, int 
         break;
 #define QS_SWITCH1(j, CALL) \
     switch (j) { QS_CASE1(0, CALL) QS_CASE1(1, CALL) QS_CASE1(2, CALL) QS_CASE1(3, CALL) QS_CASE1(4, CALL) }
-#define QS_CASEF(J, U, CALL) \
-    case J * 4 + U:          \
-        CALL(J, U);          \
-        break;
-#define QS_SWITCHF(j, CALL)                                                                                  \
-    switch (j) {                                                                                             \
-        QS_CASEF(0, 0, CALL) QS_CASEF(0, 1, CALL) QS_CASEF(0, 2, CALL) QS_CASEF(0, 3, CALL)                  \
-        QS_CASEF(1, 0, CALL) QS_CASEF(1, 1, CALL) QS_CASEF(1, 2, CALL) QS_CASEF(1, 3, CALL)                  \
-        QS_CASEF(2, 0, CALL) QS_CASEF(2, 1, CALL) QS_CASEF(2, 2, CALL) QS_CASEF(2, 3, CALL)                  \
-        QS_CASEF(3, 0, CALL) QS_CASEF(3, 1, CALL) QS_CASEF(3, 2, CALL) QS_CASEF(3, 3, CALL)                  \
-        QS_CASEF(4, 0, CALL) QS_CASEF(4, 1, CALL) QS_CASEF(4, 2, CALL) QS_CASEF(4, 3, CALL)                  \
+#define QS_SWITCHG(j, CALL) \
+    switch (j) { \
+    case 0: CALL(0, 0, 0); break; \
+    case 1: CALL(0, 0, 1); break; \
+    case 2: CALL(0, 0, 2); break; \
+    case 3: CALL(0, 1, 0); break; \
+    case 4: CALL(0, 1, 1); break; \
+    case 5: CALL(0, 1, 2); break; \
+    case 6: CALL(0, 2, 0); break; \
+    case 7: CALL(0, 2, 1); break; \
+    case 8: CALL(0, 2, 2); break; \
+    case 9: CALL(0, 3, 0); break; \
+    case 10: CALL(0, 3, 1); break; \
+    case 11: CALL(0, 3, 2); break; \
+    case 12: CALL(0, 4, 0); break; \
+    case 13: CALL(0, 4, 1); break; \
+    case 14: CALL(0, 4, 2); break; \
+    case 16: CALL(1, 0, 0); break; \
+    case 17: CALL(1, 0, 1); break; \
+    case 18: CALL(1, 0, 2); break; \
+    case 19: CALL(1, 1, 0); break; \
+    case 20: CALL(1, 1, 1); break; \
+    case 21: CALL(1, 1, 2); break; \
+    case 22: CALL(1, 2, 0); break; \
+    case 23: CALL(1, 2, 1); break; \
+    case 24: CALL(1, 2, 2); break; \
+    case 25: CALL(1, 3, 0); break; \
+    case 26: CALL(1, 3, 1); break; \
+    case 27: CALL(1, 3, 2); break; \
+    case 28: CALL(1, 4, 0); break; \
+    case 29: CALL(1, 4, 1); break; \
+    case 30: CALL(1, 4, 2); break; \
+    case 32: CALL(2, 0, 0); break; \
+    case 33: CALL(2, 0, 1); break; \
+    case 34: CALL(2, 0, 2); break; \
+    case 35: CALL(2, 1, 0); break; \
+    case 36: CALL(2, 1, 1); break; \
+    case 37: CALL(2, 1, 2); break; \
+    case 38: CALL(2, 2, 0); break; \
+    case 39: CALL(2, 2, 1); break; \
+    case 40: CALL(2, 2, 2); break; \
+    case 41: CALL(2, 3, 0); break; \
+    case 42: CALL(2, 3, 1); break; \
+    case 43: CALL(2, 3, 2); break; \
+    case 44: CALL(2, 4, 0); break; \
+    case 45: CALL(2, 4, 1); break; \
+    case 46: CALL(2, 4, 2); break; \
+    case 48: CALL(3, 0, 0); break; \
+    case 49: CALL(3, 0, 1); break; \
+    case 50: CALL(3, 0, 2); break; \
+    case 51: CALL(3, 1, 0); break; \
+    case 52: CALL(3, 1, 1); break; \
+    case 53: CALL(3, 1, 2); break; \
+    case 54: CALL(3, 2, 0); break; \
+    case 55: CALL(3, 2, 1); break; \
+    case 56: CALL(3, 2, 2); break; \
+    case 57: CALL(3, 3, 0); break; \
+    case 58: CALL(3, 3, 1); break; \
+    case 59: CALL(3, 3, 2); break; \
+    case 60: CALL(3, 4, 0); break; \
+    case 61: CALL(3, 4, 1); break; \
+    case 62: CALL(3, 4, 2); break; \
+    case 64: CALL(4, 0, 0); break; \
+    case 65: CALL(4, 0, 1); break; \
+    case 66: CALL(4, 0, 2); break; \
+    case 67: CALL(4, 1, 0); break; \
+    case 68: CALL(4, 1, 1); break; \
+    case 69: CALL(4, 1, 2); break; \
+    case 70: CALL(4, 2, 0); break; \
+    case 71: CALL(4, 2, 1); break; \
+    case 72: CALL(4, 2, 2); break; \
+    case 73: CALL(4, 3, 0); break; \
+    case 74: CALL(4, 3, 1); break; \
+    case 75: CALL(4, 3, 2); break; \
+    case 76: CALL(4, 4, 0); break; \
+    case 77: CALL(4, 4, 1); break; \
+    case 78: CALL(4, 4, 2); break; \
     }
 #define QS_CASE2(A, B, CALL) \
     case A * 8 + B:          \
@@ -246,23 +324,37 @@ __device__ __forceinline__ void fused_tile(typename FV<R>::T *__restrict__ a, co
             if (!active && op.kind != FO_XPOSE) continue;
             switch (op.kind) {
             case FO_G1F: {
-                R fr = cf[op.aux4], fi = cf[op.aux4 + 1];
-                if (op.aux >= 0) {
-                    const R tr = cf[op.aux + 2 * tid], ti = cf[op.aux + 2 * tid + 1];
-                    const R xr = fr * tr - fi * ti;
-                    fi = fr * ti + fi * tr;
-                    fr = xr;
+                const int uf = op.j1 & 15, pr = op.j1 >> 4;
+                R fr = 1, fi = 0;
+                if (pr == PRE_FD) {
+                    fr = cf[op.aux4];
+                    fi = cf[op.aux4 + 1];
+                    if (op.aux >= 0) {
+                        const R tr = cf[op.aux + 2 * tid], ti = cf[op.aux + 2 * tid + 1];
+                        const R xr = fr * tr - fi * ti;
+                        fi = fr * ti + fi * tr;
+                        fr = xr;
+                    }
+                    if (op.aux2 >= 0) {
+                        const R er = E[2 * op.aux2], ei = E[2 * op.aux2 + 1];
+                        const R xr = fr * er - fi * ei;
+                        fi = fr * ei + fi * er;
+                        fr = xr;
+                    }
                 }
-                if (op.aux2 >= 0) {
-                    const R er = E[2 * op.aux2], ei = E[2 * op.aux2 + 1];
-                    const R xr = fr * er - fi * ei;
-                    fi = fr * ei + fi * er;
-                    fr = xr;
-                }
-                const R *D = cf + op.aux3;
-#define QS_C(J, UF) op_g1f<J, UF>(v, u, fr, fi, D)
-                QS_SWITCHF(op.j0 * 4 + op.j1, QS_C)
+                const R *D = cf + (op.aux3 >= 0 ? op.aux3 : 0);
+#define QS_C(J, UF, PR) op_g1f<J, UF, PR>(v, u, fr, fi, D)
+                QS_SWITCHG(op.j0 * 16 + uf * 3 + pr, QS_C)
 #undef QS_C
+                break;
+            }
+            case FO_RSCALE: {
+                const R sc = u[0];
+#pragma unroll
+                for (int x = 0; x < NR; x++) {
+                    v[x].x *= sc;
+                    v[x].y *= sc;
+                }
                 break;
             }
             case FO_G2: {

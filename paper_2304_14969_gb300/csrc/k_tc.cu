@@ -84,30 +84,33 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity)
     return false;
 }
 
+// Splits the pair (re, im) into hi and lo parts and stores each part as
+// one paired store (the two K-adjacent elements of a row).
 template <int ES>
-__device__ __forceinline__ void split_store(unsigned char *hi, unsigned char *lo, uint32_t off, float x)
+__device__ __forceinline__ void split_store2(unsigned char *hi, unsigned char *lo, uint32_t off, float2 x)
 {
     if constexpr (ES == 4) {
-        uint32_t h;
-        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
-        float hf = __uint_as_float(h);
-        *(uint32_t *)(hi + off) = h;
-        *(float *)(lo + off) = x - hf;
+        uint32_t h0, h1;
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h0) : "f"(x.x));
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h1) : "f"(x.y));
+        *(uint2 *)(hi + off) = make_uint2(h0, h1);
+        *(float2 *)(lo + off) = make_float2(x.x - __uint_as_float(h0), x.y - __uint_as_float(h1));
     } else {
-        __nv_bfloat16 h = __float2bfloat16_rn(x);
-        float hf = __bfloat162float(h);
-        *(__nv_bfloat16 *)(hi + off) = h;
-        *(__nv_bfloat16 *)(lo + off) = __float2bfloat16_rn(x - hf);
+        __nv_bfloat162 h = __floats2bfloat162_rn(x.x, x.y);
+        float2 hf = __bfloat1622float2(h);
+        *(__nv_bfloat162 *)(hi + off) = h;
+        *(__nv_bfloat162 *)(lo + off) = __floats2bfloat162_rn(x.x - hf.x, x.y - hf.y);
     }
 }
 
-// PREC: 1 = 3xTF32 (ES 4, N 64), 2 = BF16x3 (ES 2, N 128)
+// PREC: 1 = 3xTF32 (ES 4), 2 = BF16x3 (ES 2); N = 64 groups per iteration
+// (BF16x3 fits two CTAs per SM)
 template <int PREC>
-__global__ void __launch_bounds__(kTcThreads, 1) k_tc_block(float2 *__restrict__ a, uint64_t ngroups, TcSpec ts,
+__global__ void __launch_bounds__(kTcThreads, PREC == 1 ? 1 : 2) k_tc_block(float2 *__restrict__ a, uint64_t ngroups, TcSpec ts,
                                                             const unsigned char *__restrict__ Ag, int *err)
 {
     constexpr int ES = PREC == 1 ? 4 : 2;
-    constexpr int N = PREC == 1 ? 64 : 128;
+    constexpr int N = 64;
     constexpr int KSTEP = PREC == 1 ? 8 : 16;          // K per instruction
     constexpr uint32_t A_BYTES = kTcRows * kTcRows * ES;
     constexpr uint32_t B_BYTES = N * kTcRows * ES;
@@ -119,7 +122,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_block(float2 *__restrict__
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_base;
     __shared__ int s_fail;
+    __shared__ uint64_t s_spread[64];   // physical offset of block index l
+    __shared__ int s_pos[6];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid < 64) {
+        uint64_t o = 0;
+#pragma unroll
+        for (int b = 0; b < 6; b++)
+            if ((tid >> b) & 1) o |= 1ull << ts.q[b];
+        s_spread[tid] = o;
+    }
+    if (tid < 6) s_pos[tid] = ts.ins.pos[tid];
 
     // A (hi, lo) arrives in its final byte layout
     {
@@ -147,25 +160,33 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_block(float2 *__restrict__
     uint32_t phase = 0;
 
     for (uint64_t g0 = (uint64_t)blockIdx.x * N; g0 < ngroups; g0 += (uint64_t)gridDim.x * N) {
-        // ---- gather N groups (rows of B) and split them
-        for (int e = tid; e < N * 64; e += kTcThreads) {
-            const int nn = e % N, l = e / N;
-            const uint64_t g = g0 + nn;
-            float2 v = make_float2(0.f, 0.f);
-            if (g < ngroups) {
-                uint64_t base = g;
-                for (int j = 0; j < 6; j++) {
-                    int p = ts.ins.pos[j];
-                    base = ((base >> p) << (p + 1)) | (base & ((1ull << p) - 1));
-                }
-                uint64_t idx = base;
+        // ---- gather N groups (rows of B) and split them; thread owns group
+        // row nn = tid % N and block elements l = tid / N + j * (threads / N)
+        const int nn = tid % N;
+        const uint64_t g = g0 + nn;
+        const bool gok = g < ngroups;
+        uint64_t base = g;
 #pragma unroll
-                for (int b = 0; b < 6; b++)
-                    if ((l >> b) & 1) idx |= 1ull << ts.q[b];
-                v = a[idx];
-            }
-            split_store<ES>(Bhi, Blo, canon_off(nn, 2 * l, ES), v.x);
-            split_store<ES>(Bhi, Blo, canon_off(nn, 2 * l + 1, ES), v.y);
+        for (int j = 0; j < 6; j++) {
+            const int p = s_pos[j];
+            base = ((base >> p) << (p + 1)) | (base & ((1ull << p) - 1));
+        }
+        const uint32_t rowoff = (uint32_t)(nn >> 3) * SBO + (uint32_t)(nn & 7) * 16u;
+        constexpr int LPER = 64 / (kTcThreads / N);   // block elements per thread
+        const int l0 = tid / N;
+        float2 vin[LPER];
+        // all loads first: LPER independent 8-byte loads in flight per thread
+#pragma unroll
+        for (int j = 0; j < LPER; j++) {
+            const int l = l0 + j * (kTcThreads / N);
+            vin[j] = gok ? a[base | s_spread[l]] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int j = 0; j < LPER; j++) {
+            const int l = l0 + j * (kTcThreads / N);
+            // (re, im) of element l are K-adjacent: one paired store per part
+            split_store2<ES>(Bhi, Blo, rowoff + (uint32_t)((2 * l) / (16 / ES)) * 128u +
+                                           (uint32_t)((2 * l) % (16 / ES)) * ES, vin[j]);
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
@@ -216,21 +237,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_block(float2 *__restrict__
         }
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncthreads();
-        // ---- write the N groups back
-        for (int e = tid; e < N * 64; e += kTcThreads) {
-            const int nn = e % N, l = e / N;
-            const uint64_t g = g0 + nn;
-            if (g >= ngroups) continue;
-            uint64_t base = g;
-            for (int j = 0; j < 6; j++) {
-                int p = ts.ins.pos[j];
-                base = ((base >> p) << (p + 1)) | (base & ((1ull << p) - 1));
-            }
-            uint64_t idx = base;
+        // ---- write the N groups back (same thread -> group ownership)
+        if (gok) {
 #pragma unroll
-            for (int b = 0; b < 6; b++)
-                if ((l >> b) & 1) idx |= 1ull << ts.q[b];
-            a[idx] = make_float2(stage[nn * SROW + 2 * l], stage[nn * SROW + 2 * l + 1]);
+            for (int j = 0; j < LPER; j++) {
+                const int l = l0 + j * (kTcThreads / N);
+                a[base | s_spread[l]] = *(const float2 *)&stage[nn * SROW + 2 * l];
+            }
         }
         __syncthreads();   // staging (B region) free for the next gather
     }
@@ -319,7 +332,7 @@ cudaError_t tc_launch(qsim_state *s, const TcSpec &ts, const unsigned char *dA, 
         int grid = (int)std::min<uint64_t>((ngroups + N - 1) / N, (uint64_t)num_sms());
         k_tc_block<1><<<grid, kTcThreads, smem, s->stream>>>((float2 *)s->amps, ngroups, ts, dA, derr);
     } else {
-        const int N = 128;
+        const int N = 64;
         size_t smem = 2 * (size_t)kTcRows * kTcRows * 2 +
                       std::max<size_t>(2 * (size_t)N * kTcRows * 2, (size_t)N * (kTcRows + 2) * 4);
         static bool attr = false;
@@ -327,7 +340,9 @@ cudaError_t tc_launch(qsim_state *s, const TcSpec &ts, const unsigned char *dA, 
             cudaFuncSetAttribute(k_tc_block<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             attr = true;
         }
-        int grid = (int)std::min<uint64_t>((ngroups + N - 1) / N, (uint64_t)num_sms());
+        int occ = 1;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tc_block<2>, kTcThreads, smem);
+        int grid = (int)std::min<uint64_t>((ngroups + N - 1) / N, (uint64_t)num_sms() * std::max(1, occ));
         k_tc_block<2><<<grid, kTcThreads, smem, s->stream>>>((float2 *)s->amps, ngroups, ts, dA, derr);
     }
     return cudaGetLastError();

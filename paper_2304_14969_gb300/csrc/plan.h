@@ -28,11 +28,18 @@ enum FOpKind : int32_t {
     FO_G2 = 4,     // dense 4x4 on (j0 = bit 0, j1 = bit 1); cf[coef .. +32)
     FO_G2M = 5,    // monomial 4x4: out[r] = ph[r] * in[perm[r]]; aux = perm packed 2 bits each; cf: 8
     FO_XPOSE = 8,  // transpose through shared memory to map aux
-    FO_SCALE = 9   // every register amplitude *= cf[coef .. +2)
+    FO_SCALE = 9,  // every register amplitude *= cf[coef .. +2)
+    FO_RSCALE = 10 // every register amplitude *= the real cf[coef]
 };
 
-// u form of FO_G1F (j1)
-enum { U_NONE = 0, U_REAL = 1, U_CPLX = 2, U_ANTI = 3 };
+// j1 of FO_G1F = uform | (pre << 4).
+// uform: U_NONE pure phase, U_REAL 4 reals, U_CPLX 4 complex, U_ANTI
+// anti-diagonal (2 complex), U_HAD unnormalised Hadamard butterfly
+// (p + q, p - q); the pass's product of the dropped scales is applied once by
+// a FO_RSCALE op. pre: PRE_NONE no prefactor, PRE_D prefactor D[xr] (a
+// constant table), PRE_FD prefactor f * D[xr] (per-thread f).
+enum { U_NONE = 0, U_REAL = 1, U_CPLX = 2, U_ANTI = 3, U_HAD = 4 };
+enum { PRE_NONE = 0, PRE_D = 1, PRE_FD = 2 };
 
 struct FOp {
     int32_t kind, j0, j1, coef, aux, aux2, aux3, aux4;

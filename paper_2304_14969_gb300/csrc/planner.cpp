@@ -136,6 +136,7 @@ struct Builder {
     int reg[kMaxRB], lane[5], warp[kMaxW];
     int cur_map = -1;
     int lin_count = 0;
+    double pass_scale = 1.0;
     PlanPass *pass = nullptr;
 
     int reg_of_tau(int tb) const
@@ -271,7 +272,12 @@ struct Builder {
     // uform (U_NONE for a pure phase op), matrix coefficients at ucoef.
     void emit_g1f(int r, const Pre &pr, int uform, int ucoef)
     {
-        cd c0 = std::polar(1.0, pr.th0);
+        const bool has_f = !pr.tile.empty() || !pr.ext.empty();
+        const bool has_d = !pr.regp.empty();
+        const cd c0 = std::polar(1.0, pr.th0);
+        const bool has_c = std::abs(c0 - cd(1.0)) > 1e-15;
+        int pre = !has_f && !has_d && !has_c ? PRE_NONE : (!has_f ? PRE_D : PRE_FD);
+        if (uform == U_NONE && pre == PRE_NONE) return;   // nothing to do
         int oc0 = add_coef(&c0, 1);
         int taux = -1, laux = -1, daux = -1;
         if (!pr.tile.empty()) {
@@ -298,20 +304,20 @@ struct Builder {
             }
             P.lin_off.push_back((int32_t)P.ext_bit.size());
         }
-        {
-            // register-partner table over x without bit r
+        if (pre != PRE_NONE) {
+            // register-partner table over x without bit r; PRE_D folds c0 in
             int half = 1 << (RB - 1);
             std::vector<cd> tab(half);
             for (int xr = 0; xr < half; xr++) {
                 int x = ((xr >> r) << (r + 1)) | (xr & ((1 << r) - 1));
-                double ang = 0;
+                double ang = pre == PRE_D ? pr.th0 : 0.0;
                 for (auto &kv : pr.regp)
                     if ((x >> kv.first) & 1) ang += kv.second;
                 tab[xr] = std::polar(1.0, ang);
             }
             daux = add_coef(tab.data(), half);
         }
-        P.ops.push_back(FOp{FO_G1F, r, uform, ucoef, taux, laux, daux, oc0});
+        P.ops.push_back(FOp{FO_G1F, r, uform | (pre << 4), ucoef, taux, laux, daux, oc0});
     }
 
     void emit_dense(const Item &it)
@@ -324,7 +330,13 @@ struct Builder {
             bool real = true;
             for (int k = 0; k < 4; k++) real = real && std::abs(m[k].imag()) < 1e-15;
             int uform, uc;
-            if (std::abs(m[0]) < kTiny && std::abs(m[3]) < kTiny) {
+            if (real && std::abs(m[0] - m[1]) < 1e-15 && std::abs(m[0] - m[2]) < 1e-15 &&
+                std::abs(m[0] + m[3]) < 1e-15 && std::abs(m[0]) > kTiny) {
+                // a * [[1, 1], [1, -1]]: unnormalised butterfly, a applied once per pass
+                uform = U_HAD;
+                uc = 0;
+                pass_scale *= m[0].real();
+            } else if (std::abs(m[0]) < kTiny && std::abs(m[3]) < kTiny) {
                 cd v[2] = {m[1], m[2]};
                 uform = U_ANTI;
                 uc = add_coef(v, 2);
@@ -373,6 +385,7 @@ struct Builder {
         pass->op_begin = (int)P.ops.size();
         pass->map_begin = (int)P.maps.size();
         pass->lin_begin = (int)P.lin_off.size();
+        pass_scale = 1.0;
         pass->coef_begin = (int)P.coef.size();
         pass->tw_begin = (int)P.tw.size();
         pass->ext_begin = (int)P.ext_bit.size();
@@ -413,6 +426,10 @@ struct Builder {
             emit_dense(*it);
             di++;
             ndense++;
+        }
+        if (pass_scale != 1.0) {
+            cd sc(pass_scale, 0.0);
+            P.ops.push_back(FOp{FO_RSCALE, 0, 0, add_coef(&sc, 1, true), 0, 0, 0, 0});
         }
         // store: lanes = tau 0..4 and no register on them
         bool store_ok = true;
@@ -476,9 +493,10 @@ struct Builder {
         for (int i = 0; i < d.nops; i++) {
             FOp op = P.ops[ps.op_begin + i];
             if (op.kind == FO_G1F) {
-                if (op.j1 != U_NONE) op.coef -= ps.coef_begin;
+                int uf = op.j1 & 15;
+                if (uf != U_NONE && uf != U_HAD) op.coef -= ps.coef_begin;
                 if (op.aux >= 0) op.aux -= ps.coef_begin;
-                op.aux3 -= ps.coef_begin;
+                if (op.aux3 >= 0) op.aux3 -= ps.coef_begin;
                 op.aux4 -= ps.coef_begin;
             } else if (op.kind != FO_XPOSE) {
                 op.coef -= ps.coef_begin;
