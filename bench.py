@@ -447,7 +447,74 @@ def extra_legs(Q, W, C, torch, circ, x, n, ng):
     best = min(out[k]["ms"] for k in out if k.startswith("grid30_c64"))
     out["grid30_speedup_vs_per_gate_fp64"] = pg * 1e3 / best
     s128.close()
+    out["batch512"] = batch_leg(Q, W, C)
+    out["approx54"] = approx_leg(Q, W)
     return out
+
+
+def batch_leg(Q, W, C):
+    """512 seeded circuits (n ~ U{10..24}, depth ~ U{4..20}, QFT / grid 50/50)
+    in one persistent launch replayed from a CUDA graph; tile widths from the
+    autotuner (one representative circuit per qubit count)."""
+    import tempfile
+    specs = W.batch_circuits(512, seed=0)
+    circs = [Q.Circuit(sp["n"], sp["gates"]) for sp in specs]
+    with tempfile.TemporaryDirectory() as d:
+        cache = os.path.join(d, "tune.jsonl")
+        tuned = {}
+        for sp, c in zip(specs, circs):
+            if sp["n"] in tuned or sp["kind"] != "grid":
+                continue
+            best = Q.qsim_run_opts()
+            sec = C.c_double()
+            Q.qsim_autotune(c.ptr(), Q.QSIM_C64, cache.encode(), C.byref(best), C.byref(sec))
+            tuned[sp["n"]] = best.tile_qubits
+        arr = (C.POINTER(Q.qsim_circuit) * len(circs))(*[C.pointer(c.c) for c in circs])
+        o = Q.qsim_batch_opts(use_graph=1, tune_cache=cache.encode())
+        h = C.c_void_p()
+        Q.qsim_batch_create(C.cast(arr, C.c_void_p), len(circs), C.byref(o), C.byref(h))
+    info = np.zeros(8, dtype=np.int64)
+    Q.qsim_batch_info(h, info.ctypes.data_as(C.c_void_p))
+    secs, lat = [], np.zeros(len(circs))
+    for r in range(5):
+        Q.qsim_batch_reset(h)
+        sec = C.c_double()
+        Q.qsim_batch_run(h, C.byref(sec), lat.ctypes.data_as(C.c_void_p))
+        if r >= 2:
+            secs.append(sec.value)
+    Q.qsim_batch_destroy(h)
+    t = float(np.median(secs))
+    upd = sum(len(sp["gates"]) * (1 << sp["n"]) for sp in specs)
+    return {"circuits": len(specs), "seconds": t, "circuits_per_s": len(specs) / t, "updates_per_s": upd / t,
+            "latency_p50_ms": float(np.percentile(lat, 50)) * 1e3,
+            "latency_p99_ms": float(np.percentile(lat, 99)) * 1e3, "work_items": int(info[1]),
+            "ctas": int(info[2]), "arena_bytes": int(info[3]), "graph": bool(info[6]),
+            "tuned_tiles": {str(k): v for k, v in sorted(tuned.items())}}
+
+
+def approx_leg(Q, W, budget_gib=16.0, layers=7, time_cap_s=30.0):
+    """The paper's Fig. 3 protocol on the 54-qubit 6x9 grid circuit (7
+    layers): p from 1 downward in steps of 0.025 until the memory budget is
+    exceeded (or one run exceeds the time cap); F model of the last
+    completed run."""
+    g = W.grid_rcs_circuit(6, 9, layers, seed=0)
+    runs = []
+    p = 1.0
+    while p > -1e-9:
+        try:
+            r, _, _, _ = Q.approx_run(54, g, round(p, 3), budget=budget_gib * 2 ** 30)
+        except Q.QsimError as e:
+            runs.append({"p": round(p, 3), "status": "budget" if e.status == 5 else str(e)})
+            break
+        runs.append({"p": round(p, 3), "F": r.fidelity_model, "seconds": r.seconds, "rounds": r.n_rounds,
+                     "peak_gib": r.peak_bytes / 2 ** 30, "max_subsystem_qubits": r.max_subsystem_qubits,
+                     "bloch_passes": r.n_bloch_passes})
+        if r.seconds > time_cap_s:
+            break
+        p -= 0.025
+    done = [x for x in runs if "F" in x]
+    return {"qubits": 54, "layers": layers, "budget_gib": budget_gib, "min_p": done[-1]["p"] if done else None,
+            "F_at_min_p": done[-1]["F"] if done else None, "runs": runs}
 
 
 if __name__ == "__main__":

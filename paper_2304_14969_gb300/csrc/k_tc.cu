@@ -159,34 +159,50 @@ __global__ void __launch_bounds__(kTcThreads, PREC == 1 ? 1 : 2) k_tc_block(floa
                            ((uint32_t)(N >> 3) << 17) | ((uint32_t)(kTcRows >> 4) << 24);
     uint32_t phase = 0;
 
-    for (uint64_t g0 = (uint64_t)blockIdx.x * N; g0 < ngroups; g0 += (uint64_t)gridDim.x * N) {
-        // ---- gather N groups (rows of B) and split them; thread owns group
-        // row nn = tid % N and block elements l = tid / N + j * (threads / N)
-        const int nn = tid % N;
-        const uint64_t g = g0 + nn;
-        const bool gok = g < ngroups;
+    // Thread -> work ownership: group row nn = tid % N of each iteration and
+    // block elements l = l0 + j * (threads / N). The loads of iteration i+1
+    // are issued right after iteration i's operands are stored, so they are
+    // in flight during i's MMAs, TMEM reads and write-back.
+    const int nn = tid % N;
+    constexpr int LPER = 64 / (kTcThreads / N);
+    const int l0 = tid / N;
+    const uint32_t rowoff = (uint32_t)(nn >> 3) * SBO + (uint32_t)(nn & 7) * 16u;
+    auto group_base = [&](uint64_t g) {
         uint64_t base = g;
 #pragma unroll
         for (int j = 0; j < 6; j++) {
             const int p = s_pos[j];
             base = ((base >> p) << (p + 1)) | (base & ((1ull << p) - 1));
         }
-        const uint32_t rowoff = (uint32_t)(nn >> 3) * SBO + (uint32_t)(nn & 7) * 16u;
-        constexpr int LPER = 64 / (kTcThreads / N);   // block elements per thread
-        const int l0 = tid / N;
-        float2 vin[LPER];
-        // all loads first: LPER independent 8-byte loads in flight per thread
+        return base;
+    };
+    const uint64_t gstride = (uint64_t)gridDim.x * N;
+    float2 vin[LPER];
+    uint64_t g0 = (uint64_t)blockIdx.x * N;
+    uint64_t base = group_base(g0 + nn);
+    bool gok = g0 + nn < ngroups;
+#pragma unroll
+    for (int j = 0; j < LPER; j++)
+        vin[j] = gok ? a[base | s_spread[l0 + j * (kTcThreads / N)]] : make_float2(0.f, 0.f);
+
+    for (; g0 < ngroups; g0 += gstride) {
+        // ---- split the loaded groups into the B operands
 #pragma unroll
         for (int j = 0; j < LPER; j++) {
             const int l = l0 + j * (kTcThreads / N);
-            vin[j] = gok ? a[base | s_spread[l]] : make_float2(0.f, 0.f);
-        }
-#pragma unroll
-        for (int j = 0; j < LPER; j++) {
-            const int l = l0 + j * (kTcThreads / N);
-            // (re, im) of element l are K-adjacent: one paired store per part
             split_store2<ES>(Bhi, Blo, rowoff + (uint32_t)((2 * l) / (16 / ES)) * 128u +
                                            (uint32_t)((2 * l) % (16 / ES)) * ES, vin[j]);
+        }
+        // ---- prefetch the next iteration's groups
+        const uint64_t cur_base = base;
+        const bool cur_ok = gok;
+        {
+            const uint64_t gn = g0 + gstride + nn;
+            gok = gn < ngroups;
+            base = gok ? group_base(gn) : 0;
+#pragma unroll
+            for (int j = 0; j < LPER; j++)
+                vin[j] = gok ? a[base | s_spread[l0 + j * (kTcThreads / N)]] : make_float2(0.f, 0.f);
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
@@ -238,11 +254,11 @@ __global__ void __launch_bounds__(kTcThreads, PREC == 1 ? 1 : 2) k_tc_block(floa
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncthreads();
         // ---- write the N groups back (same thread -> group ownership)
-        if (gok) {
+        if (cur_ok) {
 #pragma unroll
             for (int j = 0; j < LPER; j++) {
                 const int l = l0 + j * (kTcThreads / N);
-                a[base | s_spread[l]] = *(const float2 *)&stage[nn * SROW + 2 * l];
+                a[cur_base | s_spread[l]] = *(const float2 *)&stage[nn * SROW + 2 * l];
             }
         }
         __syncthreads();   // staging (B region) free for the next gather

@@ -355,3 +355,45 @@ class Plan:
 def u2(m) -> np.ndarray:
     """2x2 complex -> 8 doubles (re/im interleaved, row-major)."""
     return np.ascontiguousarray(np.asarray(m, dtype=np.complex128).ravel().view(np.float64))
+
+
+def approx_run(n, gates, p, dtype=QSIM_C64, tau=0.0, budget=0.0, schedule=QSIM_SCHED_EXHAUSTIVE, mlp=None,
+               top_m=4, fallback_every=0, want_state=False, trace_cap=0, log_cap=0):
+    """qsim_approx_run on a list of workloads.Gate; returns (result, state or
+    None, (features, labels) or None, decisions list)."""
+    circ = Circuit(n, gates)
+    o = qsim_approx_opts()
+    o.dtype = dtype
+    o.tau = tau
+    o.budget_bytes = budget
+    o.schedule = schedule
+    o.top_m = top_m
+    o.fallback_every = fallback_every
+    if mlp is not None:
+        o.mlp = mlp
+    state = None
+    if want_state:
+        state = np.zeros(1 << n, dtype=np.complex64 if dtype == QSIM_C64 else np.complex128)
+        o.state_out = state.ctypes.data_as(C.c_void_p)
+    feats = labels = None
+    if trace_cap:
+        feats = np.zeros((trace_cap, 12), dtype=np.float32)
+        labels = np.zeros(trace_cap, dtype=np.int32)
+        o.trace_features = feats.ctypes.data_as(C.POINTER(C.c_float))
+        o.trace_labels = labels.ctypes.data_as(C.POINTER(C.c_int32))
+        o.trace_cap = trace_cap
+    log = None
+    if log_cap:
+        log = (qsim_decision * log_cap)()
+        o.log = log
+        o.log_cap = log_cap
+    r = qsim_approx_result()
+    qsim_approx_run(circ.ptr(), float(p), C.byref(o), C.byref(r))
+    tr = None
+    if trace_cap:
+        k = min(r.n_trace, trace_cap)
+        tr = (feats[:k].copy(), labels[:k].copy())
+    dec = []
+    if log_cap:
+        dec = [(log[i].gate, log[i].qubit, log[i].action, log[i].eps) for i in range(min(r.n_log, log_cap))]
+    return r, state, tr, dec

@@ -82,3 +82,49 @@ def test_training_lowers_loss(Q):
             first = loss.value
     assert loss.value < 0.5 * first
     Q.qsim_mlp_destroy(h)
+
+
+def test_mlp_schedule_gain_over_exhaustive(Q):
+    """Train the proposal MLP on traces of the exhaustive approximate mode
+    (20-qubit grid circuits, several p), then run held-out circuits with the
+    MLP schedule (check only qubits it predicts to round, exhaustive round
+    every 8 entangling gates) and with the exhaustive schedule at the same p.
+    The gain is fewer Bloch reductions; the fidelity cost is judged by the
+    exhaustive run and the exact state."""
+    import oracle
+    from paper_2304_14969_gb300 import workloads as W
+    rows, cols = 4, 5
+    n = rows * cols
+    X, Y = [], []
+    for seed in range(6):
+        g = W.grid_rcs_circuit(rows, cols, 6, seed=100 + seed)
+        for p in (0.2, 0.35, 0.5):
+            r, _, (f, l), _ = Q.approx_run(n, g, p, trace_cap=20000)
+            X.append(f)
+            Y.append(l)
+    X = np.concatenate(X).astype(np.float32)
+    Y = np.concatenate(Y).astype(np.float32)
+    assert len(X) > 500 and 0.02 < Y.mean() < 0.98
+    h = C.c_void_p()
+    Q.qsim_mlp_create(12, 64, 7, C.byref(h))
+    loss = C.c_float()
+    for it in range(400):
+        Q.qsim_mlp_train_step(h, fptr(X), fptr(Y), len(X), C.c_float(3e-3), C.byref(loss))
+    logits = np.zeros(len(X), dtype=np.float32)
+    Q.qsim_mlp_infer(h, fptr(X), len(X), 1, fptr(logits))
+    acc = np.mean((logits > 0) == (Y > 0.5))
+    assert acc > 0.85, acc
+    passes = {"exh": 0, "mlp": 0}
+    fid = {"exh": [], "mlp": []}
+    for seed in range(3):
+        g = W.grid_rcs_circuit(rows, cols, 6, seed=900 + seed)
+        exact = oracle.apply_circuit(W.basis_state(n, 0), g)
+        for name, kw in (("exh", {}), ("mlp", {"schedule": Q.QSIM_SCHED_MLP, "mlp": h, "top_m": 4,
+                                                "fallback_every": 8})):
+            r, psi, _, _ = Q.approx_run(n, g, 0.35, want_state=True, **kw)
+            passes[name] += r.n_bloch_passes
+            psi = psi.astype(np.complex128)
+            fid[name].append(abs(np.vdot(psi, exact)) ** 2 / np.vdot(psi, psi).real)
+    assert passes["mlp"] < 0.8 * passes["exh"], passes
+    assert np.mean(fid["mlp"]) >= np.mean(fid["exh"]) - 0.05, fid
+    Q.qsim_mlp_destroy(h)
