@@ -392,6 +392,48 @@ def extra_legs(Q, W, C, torch, circ, x, n, ng):
     out["fused_fp64"] = {"updates_per_s": ng * N / f128, "ms": f128 * 1e3, "dtype": "c128",
                          "passes": p.info()["passes"]}
     s.close()
+    # the same QFT on tensor-core blocks (deferred phases as per-group
+    # pre-diagonals), agreement with the fused SIMT result
+    peaks = {}
+    pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pp):
+        peaks = json.load(open(pp))
+    sref = Q.State(n, Q.QSIM_C64)
+    sref.upload(x)
+    Q.Plan(circ, dtype=Q.QSIM_C64, state=sref).execute(sref)
+    for prec, name in ((Q.QSIM_PREC_BF16X3, "bf16x3"), (Q.QSIM_PREC_3XTF32, "3xtf32")):
+        stc = Q.State(n, Q.QSIM_C64)
+        stc.upload(x)
+        tp = Q.Plan(circ, dtype=Q.QSIM_C64, prec=prec, state=stc)
+        tp.execute(stc)
+        ip = (C.c_double * 2)()
+        na, nb = C.c_double(), C.c_double()
+        Q.qsim_inner_product(sref.h, stc.h, ip)
+        Q.qsim_norm(sref.h, C.byref(na))
+        Q.qsim_norm(stc.h, C.byref(nb))
+        # timing: alternate the two layouts as in the main leg
+        tps = [Q.Plan(circ, dtype=Q.QSIM_C64, prec=prec, state=stc)]
+        tps[0].execute(stc)
+        tps.append(Q.Plan(circ, dtype=Q.QSIM_C64, prec=prec, state=stc))
+        tps[1].execute(stc)
+        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        Q.qsim_synchronize(stc.h)
+        torch.cuda.synchronize()
+        a.record()
+        for r in range(6):
+            tps[r % 2].execute(stc)
+        z.record()
+        Q.qsim_synchronize(stc.h)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(z) / 6
+        nbk = tps[0].info()["passes"]
+        achieved = 2 * 8 * N / (ms / nbk * 1e-3) / 1e9
+        out[f"qft27_c64_tc_{name}"] = {"updates_per_s": ng * N / (ms * 1e-3), "ms": ms, "blocks": nbk,
+                                       "kernel": "k_tc_block", "hbm_gbs_per_block": achieved,
+                                       "frac_of_hbm": achieved / peaks.get("hbm_gbs", 6800.0),
+                                       "infidelity_vs_simt": 1.0 - (ip[0] ** 2 + ip[1] ** 2) / (na.value * nb.value)}
+        stc.close()
+    sref.close()
     # grid random circuit, 5x6, 10 layers, complex64 fused
     g = W.grid_rcs_circuit(5, 6, 10, seed=0)
     gc = Q.Circuit(30, g)
@@ -448,7 +490,8 @@ def extra_legs(Q, W, C, torch, circ, x, n, ng):
     out["grid30_speedup_vs_per_gate_fp64"] = pg * 1e3 / best
     s128.close()
     out["batch512"] = batch_leg(Q, W, C)
-    out["approx54"] = approx_leg(Q, W)
+    out["approx54_grid"] = approx_leg(Q, W, W.grid_rcs_circuit(6, 9, 7, seed=0))
+    out["approx54_paper_family"] = approx_leg(Q, W, W.paper_random_circuit(6, 9, 7, seed=0))
     return out
 
 
@@ -492,12 +535,10 @@ def batch_leg(Q, W, C):
             "tuned_tiles": {str(k): v for k, v in sorted(tuned.items())}}
 
 
-def approx_leg(Q, W, budget_gib=16.0, layers=7, time_cap_s=30.0):
-    """The paper's Fig. 3 protocol on the 54-qubit 6x9 grid circuit (7
-    layers): p from 1 downward in steps of 0.025 until the memory budget is
-    exceeded (or one run exceeds the time cap); F model of the last
-    completed run."""
-    g = W.grid_rcs_circuit(6, 9, layers, seed=0)
+def approx_leg(Q, W, g, budget_gib=64.0, time_cap_s=40.0):
+    """The paper's Fig. 3 protocol on a 54-qubit, 7-layer circuit: p from 1
+    downward in steps of 0.025 until the memory budget is exceeded (or one run
+    exceeds the time cap); F model of the last completed run."""
     runs = []
     p = 1.0
     while p > -1e-9:
@@ -513,7 +554,7 @@ def approx_leg(Q, W, budget_gib=16.0, layers=7, time_cap_s=30.0):
             break
         p -= 0.025
     done = [x for x in runs if "F" in x]
-    return {"qubits": 54, "layers": layers, "budget_gib": budget_gib, "min_p": done[-1]["p"] if done else None,
+    return {"qubits": 54, "layers": 7, "budget_gib": budget_gib, "min_p": done[-1]["p"] if done else None,
             "F_at_min_p": done[-1]["F"] if done else None, "runs": runs}
 
 

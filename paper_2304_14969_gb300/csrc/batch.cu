@@ -36,6 +36,7 @@ struct BatchItem {
 };
 
 static const int kBatchThreads = 256;
+static const int kChunk = 8;
 static const size_t kBatchTile = (size_t)8 << 13;   // complex64 tile of 13 qubits
 
 __device__ __forceinline__ unsigned long long gtimer()
@@ -59,10 +60,17 @@ __global__ void __launch_bounds__(kBatchThreads, 2)
     unsigned char *stg = smraw + stage_off;
     int cur = -1;
     (void)max_lin16;
+    // items are taken in chunks of kChunk consecutive ones (consecutive
+    // items mostly share a pass, so its constants are staged once per chunk)
+    int chunk_at = 0, chunk_end = 0;
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) {
-            int it = (int)atomicAdd(head, 1u);
+            if (chunk_at >= chunk_end) {
+                chunk_at = (int)atomicAdd(head, 1u) * kChunk;
+                chunk_end = min(chunk_at + kChunk, nitems);
+            }
+            int it = chunk_at < nitems ? chunk_at++ : nitems;
             int bad = *(volatile int *)err;
             if (!bad && it < nitems) {
                 BatchItem b = items[it];

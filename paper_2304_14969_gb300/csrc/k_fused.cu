@@ -78,6 +78,20 @@ qsim_status plan_upload(qsim_plan *P)
         memcpy(buf.data() + off, A.data(), A.size());
         P->tc_off.push_back(off);
     }
+    // pre-diagonal partner lists of the tensor-core blocks
+    std::vector<size_t> pd_o(P->tc_A.size(), 0), pd_b(P->tc_A.size(), 0), pd_t(P->tc_A.size(), 0);
+    auto put = [&](const void *src, size_t bytes) {
+        size_t off = (buf.size() + 15) & ~(size_t)15;
+        buf.resize(off + std::max<size_t>(bytes, 16));
+        if (bytes) memcpy(buf.data() + off, src, bytes);
+        return off;
+    };
+    for (size_t i = 0; i < P->tc_A.size(); i++) {
+        if (P->tc_pd_off[i].empty()) continue;
+        pd_o[i] = put(P->tc_pd_off[i].data(), 4 * P->tc_pd_off[i].size());
+        pd_b[i] = put(P->tc_pd_bit[i].data(), 4 * P->tc_pd_bit[i].size());
+        pd_t[i] = put(P->tc_pd_tw[i].data(), 8 * P->tc_pd_tw[i].size());
+    }
     size_t err_off = (buf.size() + 255) & ~(size_t)255;
     buf.resize(err_off + 256, 0);
     if (buf.empty()) buf.resize(256);
@@ -87,6 +101,19 @@ qsim_status plan_upload(qsim_plan *P)
     for (size_t i = 0; i < P->passes.size(); i++)
         P->passes[i].dev.stage = (const unsigned char *)P->dmem + offs[i];
     P->d_err = (int *)((unsigned char *)P->dmem + err_off);
+    for (size_t i = 0; i < P->tc_A.size(); i++) {
+        TcSpec &ts = P->tc_spec[i];
+        if (P->tc_pd_off[i].empty()) {
+            ts.pd_off = nullptr;
+            ts.pd_bit = nullptr;
+            ts.pd_tw = nullptr;
+        } else {
+            unsigned char *d = (unsigned char *)P->dmem;
+            ts.pd_off = (const int32_t *)(d + pd_o[i]);
+            ts.pd_bit = (const int32_t *)(d + pd_b[i]);
+            ts.pd_tw = (const uint64_t *)(d + pd_t[i]);
+        }
+    }
     return QSIM_OK;
 }
 

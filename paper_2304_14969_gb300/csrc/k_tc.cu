@@ -36,6 +36,8 @@ static const int kTcThreads = 128;
 static const int kTcRows = 128;   // M = K
 static const long long kTcSpin = 1ll << 26;
 
+__host__ __device__ constexpr int ctz_const(int j) { return (j & 1) ? 0 : 1 + ctz_const(j >> 1); }
+
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 // byte offset of element (row, k) in the canonical K-major no-swizzle layout
@@ -186,7 +188,47 @@ __global__ void __launch_bounds__(kTcThreads, PREC == 1 ? 1 : 2) k_tc_block(floa
         vin[j] = gok ? a[base | s_spread[l0 + j * (kTcThreads / N)]] : make_float2(0.f, 0.f);
 
     for (; g0 < ngroups; g0 += gstride) {
-        // ---- split the loaded groups into the B operands
+        // ---- deferred phases of this group (pre-diagonal), then split the
+        // loaded groups into the B operands
+        if (ts.pd_off) {
+            // per block bit b: e_b = exp(2 pi i T_b(group)); element factor is
+            // the product of e_b over the set bits of l = l0 + j * step
+            float er[6], ei[6];
+#pragma unroll
+            for (int b = 0; b < 6; b++) {
+                uint64_t tt = 0;
+                for (int e = ts.pd_off[b]; e < ts.pd_off[b + 1]; e++)
+                    if ((base >> ts.pd_bit[e]) & 1) tt += ts.pd_tw[e];
+                float f = (float)(int64_t)tt * 5.42101086242752217e-20f;
+                sincospif(2.0f * f, &ei[b], &er[b]);
+            }
+            constexpr int STEP = kTcThreads / N;
+            // factors for the low log2(STEP) bits come from l0, the rest from j
+            float br = 1.f, bi = 0.f;
+#pragma unroll
+            for (int b = 0; b < 6; b++)
+                if ((1 << b) < STEP && ((l0 >> b) & 1)) {
+                    const float xr = br * er[b] - bi * ei[b];
+                    bi = br * ei[b] + bi * er[b];
+                    br = xr;
+                }
+            constexpr int SH = STEP == 1 ? 0 : (STEP == 2 ? 1 : 2);
+            float fr[LPER], fi[LPER];
+            fr[0] = br;
+            fi[0] = bi;
+            // f[j] = f[j without its lowest set bit] * e[that bit]
+#pragma unroll
+            for (int j = 1; j < LPER; j++) {
+                const int low = ctz_const(j), prev = j & (j - 1);
+                fr[j] = fr[prev] * er[SH + low] - fi[prev] * ei[SH + low];
+                fi[j] = fr[prev] * ei[SH + low] + fi[prev] * er[SH + low];
+            }
+#pragma unroll
+            for (int j = 0; j < LPER; j++) {
+                const float2 x = vin[j];
+                vin[j] = make_float2(x.x * fr[j] - x.y * fi[j], x.x * fi[j] + x.y * fr[j]);
+            }
+        }
 #pragma unroll
         for (int j = 0; j < LPER; j++) {
             const int l = l0 + j * (kTcThreads / N);
@@ -328,6 +370,9 @@ qsim_status tc_build(int n, int k, const int *phys, const cd *u, qsim_prec prec,
     for (int b = 0; b < 6; b++) ts.q[b] = q[b];
     ts.ins.npos = 6;
     for (int b = 0; b < 6; b++) ts.ins.pos[b] = pos[b];
+    ts.pd_off = nullptr;
+    ts.pd_bit = nullptr;
+    ts.pd_tw = nullptr;
     return QSIM_OK;
 }
 

@@ -115,6 +115,8 @@ struct qsim_plan {
     int prec = QSIM_PREC_NATIVE;
     std::vector<qs::TcSpec> tc_spec;
     std::vector<std::vector<unsigned char>> tc_A;
+    std::vector<std::vector<int32_t>> tc_pd_off, tc_pd_bit;   // pre-diagonal partner lists per block
+    std::vector<std::vector<uint64_t>> tc_pd_tw;
     std::vector<size_t> tc_off;
     int *d_err = nullptr;
     // device copies

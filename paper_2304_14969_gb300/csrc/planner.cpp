@@ -513,38 +513,16 @@ struct Builder {
     }
 };
 
-}  // namespace
-
-qsim_status plan_build(const qsim_circuit *cir, qsim_dtype dt, const qsim_run_opts *opts, const int *start_l2p,
-                       qsim_plan *P)
+// Classifies every gate (FP64 host matrices, physical qubits after SWAP
+// relabels): dense one/two-qubit items, diagonal items as phase terms, and
+// barriers (gates with two or more controls).
+void classify_gates(const qsim_circuit *cir, const int *start_l2p, bool relabel, std::vector<Item> &items,
+                    std::vector<int> &final_l2p, int64_t &nswaps)
 {
     const int n = cir->n;
-    qsim_run_opts o{};
-    if (opts) o = *opts;
-    int t = o.tile_qubits ? o.tile_qubits : (dt == QSIM_C64 ? 13 : 12);
-    if (dt == QSIM_C128 && t > 13) return fail(QSIM_E_INVAL, "complex128 tiles hold at most 13 qubits");
-    if (t > 14) return fail(QSIM_E_INVAL, "tiles hold at most 14 qubits");
-    int c = 5;
-    if (o.low_qubits && o.low_qubits != 5) return fail(QSIM_E_UNSUPPORTED, "low_qubits must be 5 (warp lanes)");
-    if (t > n) t = n;
-    // registers per thread: 2^5 amplitudes for complex64, 2^4 for complex128
-    int RB = std::min(dt == QSIM_C64 ? 5 : 4, t - 5);
-    if (RB < 4) return fail(QSIM_E_UNSUPPORTED, "fused path needs n >= 9");
-    if (t - RB - 5 > kMaxW || t > kMaxTile) return fail(QSIM_E_INVAL, "tile_qubits %d too large", t);
-    if (t - c > 12) return fail(QSIM_E_INVAL, "tile_qubits %d too large", t);
-    P->n = n;
-    P->dt = dt;
-    P->t = t;
-    P->c = c;
-    P->RB = RB;
-    P->ngates = cir->ngates;
-    bool relabel = opts ? (o.relabel_swaps != 0 || o.mode == QSIM_MODE_FUSED) : true;
-
-    // ---- classify gates into items (physical bits after relabels)
     std::vector<int> l2p(n);
     for (int q = 0; q < n; q++) l2p[q] = start_l2p ? start_l2p[q] : q;
-    P->start_l2p = l2p;
-    std::vector<Item> items;
+    items.clear();
     items.reserve(cir->ngates);
     for (int k = 0; k < cir->ngates; k++) {
         const qsim_gate &g = cir->gates[k];
@@ -553,7 +531,7 @@ qsim_status plan_build(const qsim_circuit *cir, qsim_dtype dt, const qsim_run_op
         Item it;
         if (g.kind == QSIM_G_SWAP && relabel) {
             std::swap(l2p[g.q0], l2p[g.q1]);
-            P->nswaps++;
+            nswaps++;
             continue;
         }
         if (d == 2 && g.ncontrols >= 2) {
@@ -594,7 +572,44 @@ qsim_status plan_build(const qsim_circuit *cir, qsim_dtype dt, const qsim_run_op
         }
         items.push_back(it);
     }
-    P->final_l2p = l2p;
+    final_l2p = l2p;
+}
+
+}  // namespace
+
+qsim_status plan_build(const qsim_circuit *cir, qsim_dtype dt, const qsim_run_opts *opts, const int *start_l2p,
+                       qsim_plan *P)
+{
+    const int n = cir->n;
+    qsim_run_opts o{};
+    if (opts) o = *opts;
+    int t = o.tile_qubits ? o.tile_qubits : (dt == QSIM_C64 ? 13 : 12);
+    if (dt == QSIM_C128 && t > 13) return fail(QSIM_E_INVAL, "complex128 tiles hold at most 13 qubits");
+    if (t > 14) return fail(QSIM_E_INVAL, "tiles hold at most 14 qubits");
+    int c = 5;
+    if (o.low_qubits && o.low_qubits != 5) return fail(QSIM_E_UNSUPPORTED, "low_qubits must be 5 (warp lanes)");
+    if (t > n) t = n;
+    // registers per thread: 2^5 amplitudes for complex64, 2^4 for complex128
+    int RB = std::min(dt == QSIM_C64 ? 5 : 4, t - 5);
+    if (RB < 4) return fail(QSIM_E_UNSUPPORTED, "fused path needs n >= 9");
+    if (t - RB - 5 > kMaxW || t > kMaxTile) return fail(QSIM_E_INVAL, "tile_qubits %d too large", t);
+    if (t - c > 12) return fail(QSIM_E_INVAL, "tile_qubits %d too large", t);
+    P->n = n;
+    P->dt = dt;
+    P->t = t;
+    P->c = c;
+    P->RB = RB;
+    P->ngates = cir->ngates;
+    bool relabel = opts ? (o.relabel_swaps != 0 || o.mode == QSIM_MODE_FUSED) : true;
+
+    // ---- classify gates into items (physical bits after relabels)
+    std::vector<Item> items;
+    {
+        std::vector<int> l2p(n);
+        for (int q = 0; q < n; q++) l2p[q] = start_l2p ? start_l2p[q] : q;
+        P->start_l2p = l2p;
+    }
+    classify_gates(cir, start_l2p, relabel, items, P->final_l2p, P->nswaps);
 
     // complex64 plans with a dense (non-monomial) two-qubit gate use 16
     // amplitude registers per thread: the 4x4 product needs the headroom
@@ -755,13 +770,18 @@ qsim_status plan_build(const qsim_circuit *cir, qsim_dtype dt, const qsim_run_op
 
 namespace qs {
 
-// Tensor-core plans: the circuit is fused into dense blocks of at most 6
-// qubits by the same commutation-aware sweep as the fused passes (a gate
-// joins the current block when its qubits fit and no earlier gate left for
-// later shares a qubit with it). Each block's unitary is the FP64 product of
-// its gates embedded in the block's qubits (new qubits join as higher
-// block bits); SWAPs are relabels. Every block is one pass of the tensor-core
-// kernel.
+// Tensor-core plans: dense gates are fused into blocks of at most 6 qubits
+// by the commutation-aware sweep of the fused passes (a gate joins the
+// current block when its qubits fit and no earlier gate left for later
+// shares a qubit with it). Diagonal gates never block: as in the fused
+// passes they become pending phase terms and are applied right before the
+// next dense gate on one of their qubits. There a term whose qubits are both
+// in the block is folded into the block's FP64 unitary; a term pairing a
+// block qubit q with an outside qubit o becomes part of the block's
+// pre-diagonal (applied per group at gather time, o read from the group's
+// index) when no earlier gate of the block acted on q (so the term may move
+// to the block's start), and o is then kept out of the block. SWAPs are
+// relabels. Every block is one pass of the tensor-core kernel.
 qsim_status plan_build_tc(const qsim_circuit *cir, const qsim_run_opts *opts, const int *start_l2p, qsim_plan *P)
 {
     const int n = cir->n;
@@ -770,64 +790,107 @@ qsim_status plan_build_tc(const qsim_circuit *cir, const qsim_run_opts *opts, co
     P->dt = QSIM_C64;
     P->prec = opts->prec;
     P->ngates = cir->ngates;
-    std::vector<int> l2p(n);
-    for (int q = 0; q < n; q++) l2p[q] = start_l2p ? start_l2p[q] : q;
-    P->start_l2p = l2p;
-    struct G {
-        std::vector<int> q;      // physical qubits, local bit j <-> q[j]
-        std::vector<cd> m;       // 2^|q| x 2^|q|
-    };
-    std::vector<G> gates;
-    for (int k = 0; k < cir->ngates; k++) {
-        const qsim_gate &g = cir->gates[k];
-        if (g.kind == QSIM_G_SWAP) {
-            std::swap(l2p[g.q0], l2p[g.q1]);
-            P->nswaps++;
-            continue;
-        }
-        cd m[16];
-        int d = gate_matrix(g, cir->matrices, cir->nmatrix_doubles, m);
-        G x;
-        if (d == 4) {
-            x.q = {l2p[g.q0], l2p[g.q1]};
-            x.m.assign(m, m + 16);
-        } else {
-            x.q = {l2p[g.q0]};
-            for (int j = 0; j < g.ncontrols; j++) x.q.push_back(l2p[g.controls[j]]);
-            int dim = 1 << x.q.size();
-            x.m.assign((size_t)dim * dim, 0.0);
-            int want = 0;
-            for (int j = 0; j < g.ncontrols; j++) want |= (int)((g.control_values >> j) & 1) << j;
-            for (int r = 0; r < dim; r++)
-                for (int c = 0; c < dim; c++) {
-                    if ((r >> 1) != (c >> 1)) continue;
-                    x.m[(size_t)r * dim + c] = ((r >> 1) == want) ? m[(r & 1) * 2 + (c & 1)]
-                                                                 : cd((r & 1) == (c & 1) ? 1.0 : 0.0);
-                }
-        }
-        gates.push_back(std::move(x));
+    {
+        std::vector<int> l2p(n);
+        for (int q = 0; q < n; q++) l2p[q] = start_l2p ? start_l2p[q] : q;
+        P->start_l2p = l2p;
     }
-    P->final_l2p = l2p;
-    std::vector<const G *> rem;
-    for (auto &g : gates) rem.push_back(&g);
+    std::vector<Item> items;
+    classify_gates(cir, start_l2p, true, items, P->final_l2p, P->nswaps);
+    std::vector<Term> pending;
+    cd gphase = 1.0;
+    auto item_qubits = [](const Item *it, std::vector<int> &v) {
+        v.clear();
+        if (it->kind == 2) {
+            v.push_back(it->gate.q0);
+            for (int j = 0; j < it->gate.ncontrols; j++) v.push_back(it->gate.controls[j]);
+        } else if (it->kind == 1) {
+            for (const Term &tm : it->terms) {
+                if (std::find(v.begin(), v.end(), tm.a) == v.end()) v.push_back(tm.a);
+                if (tm.b >= 0 && std::find(v.begin(), v.end(), tm.b) == v.end()) v.push_back(tm.b);
+            }
+        } else {
+            for (int k = 0; k < it->nq; k++) v.push_back(it->q[k]);
+        }
+    };
+    auto flush_pergate = [&]() {
+        for (const Term &tm : pending) {
+            PlanStep st;
+            st.kind = 1;
+            memset(&st.gate, 0, sizeof st.gate);
+            if (tm.b < 0) {
+                st.gate.kind = QSIM_G_PHASE;
+                st.gate.q0 = tm.a;
+                st.mat = {1.0, 0.0, 0.0, std::polar(1.0, tm.th)};
+            } else {
+                st.gate.kind = QSIM_G_CP;
+                st.gate.q0 = tm.a;
+                st.gate.q1 = tm.b;
+                st.gate.params[0] = tm.th;
+            }
+            P->steps.push_back(st);
+            P->npergate++;
+        }
+        pending.clear();
+    };
+    std::vector<const Item *> rem;
+    for (auto &it : items) rem.push_back(&it);
+    std::vector<int> qv;
     while (!rem.empty()) {
-        std::vector<int> Q;
+        std::vector<int> Q;                   // block qubits, block bit b <-> Q[b]
         std::vector<cd> U(1, 1.0);
-        std::vector<char> blocked(n, 0);
-        std::vector<const G *> left;
+        std::vector<char> blocked(n, 0), touched(n, 0), outside(n, 0);
+        std::vector<std::pair<int, std::pair<int, double>>> pre;   // (block qubit, (outside qubit, angle))
+        std::vector<const Item *> left;
         int ng = 0;
-        for (const G *g : rem) {
+        for (const Item *it : rem) {
+            item_qubits(it, qv);
             bool blk = false;
-            for (int q : g->q) blk = blk || blocked[q];
-            std::vector<int> nq = Q;
-            for (int q : g->q)
-                if (std::find(nq.begin(), nq.end(), q) == nq.end()) nq.push_back(q);
-            if (blk || nq.size() > 6) {
-                for (int q : g->q) blocked[q] = 1;
-                left.push_back(g);
+            for (int q : qv) blk = blk || blocked[q];
+            if (!blk && it->kind == 1) {
+                for (const Term &tm : it->terms) pending.push_back(tm);
+                gphase *= it->gphase;
                 continue;
             }
-            // extend U to nq (new qubits are higher bits: U <- I (x) U)
+            bool fits = !blk && it->kind == 0;
+            std::vector<int> nq = Q;
+            if (fits) {
+                for (int q : qv) {
+                    if (outside[q]) fits = false;
+                    if (std::find(nq.begin(), nq.end(), q) == nq.end()) nq.push_back(q);
+                }
+                if (nq.size() > 6) fits = false;
+            }
+            // pending terms this gate must see first
+            std::vector<Term> keep, fold, hoist;
+            if (fits) {
+                auto in_op = [&](int q) { return std::find(qv.begin(), qv.end(), q) != qv.end(); };
+                auto in_blk = [&](int q) { return std::find(nq.begin(), nq.end(), q) != nq.end(); };
+                for (const Term &tm : pending) {
+                    bool t = in_op(tm.a) || (tm.b >= 0 && in_op(tm.b));
+                    if (!t) {
+                        keep.push_back(tm);
+                        continue;
+                    }
+                    if (tm.b < 0 || (in_blk(tm.a) && in_blk(tm.b))) {
+                        fold.push_back(tm);
+                        continue;
+                    }
+                    int q = in_blk(tm.a) ? tm.a : tm.b;
+                    if (touched[q]) {
+                        fits = false;
+                        break;
+                    }
+                    hoist.push_back(tm);
+                }
+            }
+            if (!fits) {
+                for (int q : qv) blocked[q] = 1;
+                left.push_back(it);
+                continue;
+            }
+            pending.swap(keep);
+            // extend U to nq (new qubits become higher block bits)
             int od = 1 << Q.size(), nd = 1 << nq.size();
             if (nd != od) {
                 std::vector<cd> V((size_t)nd * nd, 0.0);
@@ -837,37 +900,94 @@ qsim_status plan_build_tc(const qsim_circuit *cir, const qsim_run_opts *opts, co
                 U.swap(V);
                 Q = nq;
             }
-            // embed the gate and left-multiply
-            std::vector<int> pos(g->q.size());
-            for (size_t j = 0; j < g->q.size(); j++)
-                pos[j] = (int)(std::find(Q.begin(), Q.end(), g->q[j]) - Q.begin());
-            int gmask = 0;
-            for (int p : pos) gmask |= 1 << p;
-            int gd = 1 << g->q.size();
+            auto bpos = [&](int q) { return (int)(std::find(Q.begin(), Q.end(), q) - Q.begin()); };
+            // folded terms: a diagonal on the block, applied now
+            if (!fold.empty()) {
+                for (int r = 0; r < nd; r++) {
+                    double ang = 0;
+                    for (const Term &tm : fold) {
+                        bool ba = (r >> bpos(tm.a)) & 1;
+                        bool bb = tm.b < 0 ? true : (bool)((r >> bpos(tm.b)) & 1);
+                        if (ba && bb) ang += tm.th;
+                    }
+                    cd f = std::polar(1.0, ang);
+                    for (int c = 0; c < nd; c++) U[(size_t)r * nd + c] *= f;
+                }
+            }
+            for (const Term &tm : hoist) {
+                int q = std::find(Q.begin(), Q.end(), tm.a) != Q.end() ? tm.a : tm.b;
+                int o = q == tm.a ? tm.b : tm.a;
+                pre.push_back({q, {o, tm.th}});
+                outside[o] = 1;
+            }
+            // the gate
+            int gd = 1 << it->nq, gmask = 0;
+            int pos[2];
+            for (int k = 0; k < it->nq; k++) {
+                pos[k] = bpos(it->q[k]);
+                gmask |= 1 << pos[k];
+            }
             auto loc = [&](int r) {
                 int l = 0;
-                for (size_t j = 0; j < pos.size(); j++) l |= ((r >> pos[j]) & 1) << j;
+                for (int k = 0; k < it->nq; k++) l |= ((r >> pos[k]) & 1) << k;
                 return l;
             };
-            std::vector<cd> Gm((size_t)nd * nd, 0.0);
-            for (int r = 0; r < nd; r++)
-                for (int c = 0; c < nd; c++)
-                    if ((r & ~gmask) == (c & ~gmask)) Gm[(size_t)r * nd + c] = g->m[(size_t)loc(r) * gd + loc(c)];
             std::vector<cd> W((size_t)nd * nd, 0.0);
             for (int r = 0; r < nd; r++)
                 for (int x = 0; x < nd; x++) {
-                    cd a = Gm[(size_t)r * nd + x];
+                    if ((r & ~gmask) != (x & ~gmask)) continue;
+                    cd a = it->m[loc(r) * gd + loc(x)];
                     if (a == cd(0.0)) continue;
                     for (int c = 0; c < nd; c++) W[(size_t)r * nd + c] += a * U[(size_t)x * nd + c];
                 }
             U.swap(W);
+            for (int k = 0; k < it->nq; k++) touched[it->q[k]] = 1;
             ng++;
+        }
+        if (ng == 0) {
+            if (left.empty()) {
+                rem.clear();
+                break;
+            }
+            // a barrier heads the remaining gates: flush, then run it per gate
+            const Item *bar = left.front();
+            flush_pergate();
+            PlanStep st;
+            st.kind = 1;
+            st.gate = bar->gate;
+            st.mat = bar->bmat;
+            P->steps.push_back(st);
+            P->npergate++;
+            left.erase(left.begin());
+            rem = left;
+            continue;
+        }
+        // the global phase gathered so far rides on this block
+        if (std::abs(gphase - cd(1.0)) > 1e-15) {
+            for (auto &x : U) x *= gphase;
+            gphase = 1.0;
         }
         TcSpec ts;
         std::vector<unsigned char> A;
         QS_TRY(tc_build(n, (int)Q.size(), Q.data(), U.data(), (qsim_prec)opts->prec, A, ts));
+        // pre-diagonal partner lists per block bit (tc_build keeps Q's order)
+        std::vector<int32_t> off(7, 0), pb;
+        std::vector<uint64_t> ptw;
+        for (int b = 0; b < 6; b++) {
+            off[b] = (int32_t)pb.size();
+            if (b < (int)Q.size())
+                for (auto &x : pre)
+                    if (x.first == Q[b]) {
+                        pb.push_back(x.second.first);
+                        ptw.push_back(to_turns(x.second.second));
+                    }
+        }
+        off[6] = (int32_t)pb.size();
         P->tc_spec.push_back(ts);
         P->tc_A.push_back(std::move(A));
+        P->tc_pd_off.push_back(pre.empty() ? std::vector<int32_t>() : off);
+        P->tc_pd_bit.push_back(pb);
+        P->tc_pd_tw.push_back(ptw);
         PlanStep st;
         st.kind = 3;
         st.pass = (int)P->tc_spec.size() - 1;
@@ -875,6 +995,13 @@ qsim_status plan_build_tc(const qsim_circuit *cir, const qsim_run_opts *opts, co
         P->ndense += ng;
         rem = left;
     }
+    if (std::abs(gphase - cd(1.0)) > 1e-15) {
+        PlanStep st;
+        st.kind = 2;
+        st.phase = gphase;
+        P->steps.push_back(st);
+    }
+    flush_pergate();
     return QSIM_OK;
 }
 

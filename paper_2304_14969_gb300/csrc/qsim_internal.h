@@ -78,6 +78,13 @@ struct InsSpec {
 struct TcSpec {
     int q[6];
     InsSpec ins;
+    // optional pre-diagonal: the amplitude with block index l in the group
+    // whose outside bits are G is multiplied by exp(2 pi i sum_b l_b T_b(G))
+    // with T_b(G) = sum of pd_tw[e] over e in [pd_off[b], pd_off[b+1]) with
+    // bit pd_bit[e] of G set (device arrays, NULL when there is none)
+    const int32_t *pd_off;
+    const int32_t *pd_bit;
+    const uint64_t *pd_tw;
 };
 qsim_status tc_build(int n, int k, const int *phys, const cd *u, qsim_prec prec, std::vector<unsigned char> &A,
                      TcSpec &ts);

@@ -79,3 +79,23 @@ def test_tc_plan_vs_oracle(Q, prec, which):
     y = st.download()
     st.close()
     assert infid(y, ref) <= 1e-6
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_tc_qft27_full_size_sampled(Q, prec):
+    """27-qubit QFT on tensor-core blocks (controlled phases deferred into
+    per-group pre-diagonals): sampled outputs against Eq. (dft) evaluated
+    one by one; relative squared error <= 1e-6."""
+    n = 27
+    x = W.gaussian_state(n, 0)
+    st = Q.State(n, 0)
+    st.upload(x)
+    st.run(Q.Circuit(n, W.qft_circuit(n)), mode=1, prec=prec, relabel=1)
+    y = st.download()
+    st.close()
+    num = den = 0.0
+    for j in [0, 3, 77777, (1 << n) - 5]:
+        r = oracle.dft_sample(x, j)
+        num += abs(y[j] - r) ** 2
+        den += abs(r) ** 2
+    assert num / den <= 1e-6
