@@ -967,6 +967,43 @@ qsim_status plan_build_tc(const qsim_circuit *cir, const qsim_run_opts *opts, co
             for (auto &x : U) x *= gphase;
             gphase = 1.0;
         }
+        // pad the block to six qubits here (the kernel reads a pre-diagonal
+        // partner's bit from the group index, where padded bits are 0):
+        // highest free qubits that are no partner first, then partners,
+        // whose terms then act inside the block as a diagonal before U
+        {
+            std::vector<int> pad;
+            for (int pass = 0; pass < 2; pass++)
+                for (int p = n - 1; p >= 0 && Q.size() + pad.size() < 6; p--)
+                    if (std::find(Q.begin(), Q.end(), p) == Q.end() &&
+                        std::find(pad.begin(), pad.end(), p) == pad.end() && (bool)outside[p] == (pass == 1))
+                        pad.push_back(p);
+            int od = 1 << Q.size();
+            Q.insert(Q.end(), pad.begin(), pad.end());
+            int nd = 1 << Q.size();
+            if (nd != od) {
+                std::vector<cd> V((size_t)nd * nd, 0.0);
+                for (int r = 0; r < nd; r++)
+                    for (int c = 0; c < nd; c++)
+                        if ((r / od) == (c / od)) V[(size_t)r * nd + c] = U[(size_t)(r % od) * od + (c % od)];
+                U.swap(V);
+            }
+            auto bpos = [&](int q) { return (int)(std::find(Q.begin(), Q.end(), q) - Q.begin()); };
+            std::vector<std::pair<int, std::pair<int, double>>> rest;
+            for (auto &x : pre) {
+                int o = x.second.first;
+                if (std::find(pad.begin(), pad.end(), o) == pad.end()) {
+                    rest.push_back(x);
+                    continue;
+                }
+                int ba = bpos(x.first), bb = bpos(o);
+                cd f = std::polar(1.0, x.second.second);
+                for (int c = 0; c < nd; c++)
+                    if (((c >> ba) & 1) && ((c >> bb) & 1))
+                        for (int r = 0; r < nd; r++) U[(size_t)r * nd + c] *= f;
+            }
+            pre.swap(rest);
+        }
         TcSpec ts;
         std::vector<unsigned char> A;
         QS_TRY(tc_build(n, (int)Q.size(), Q.data(), U.data(), (qsim_prec)opts->prec, A, ts));

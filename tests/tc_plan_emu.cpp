@@ -1,0 +1,157 @@
+// Host-side check of the tensor-core block planner (test infrastructure).
+//
+// Links the library's host planner with a stand-in for tc_build that keeps
+// each block's qubits and complex matrix instead of packing split operands
+// for the MMA, then applies the plan's steps to a ket on the CPU with the
+// semantics the block kernel has: per-group pre-diagonal phases read from
+// the group base index (where the block's own bits, padding included, are
+// 0), then the 2^k x 2^k matrix on the block qubits. Per-gate steps and the
+// global phase are applied as plain matrix-vector updates.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+
+#include "plan.h"
+
+namespace qs {
+qsim_status plan_build_tc(const qsim_circuit *, const qsim_run_opts *, const int *, qsim_plan *);
+
+struct EmuBlock {
+    int k;
+    int q[6];
+    std::vector<cd> U;
+};
+static std::vector<EmuBlock> g_blocks;
+
+qsim_status tc_build(int n, int k, const int *phys, const cd *u, qsim_prec, std::vector<unsigned char> &, TcSpec &ts)
+{
+    EmuBlock b;
+    b.k = k;
+    uint64_t used = 0;
+    for (int j = 0; j < k; j++) {
+        b.q[j] = phys[j];
+        used |= 1ull << phys[j];
+    }
+    int kk = k;
+    for (int p = n - 1; p >= 0 && kk < 6; p--)
+        if (!((used >> p) & 1)) {
+            b.q[kk++] = p;
+            used |= 1ull << p;
+        }
+    b.U.assign(u, u + (size_t)(1 << k) * (1 << k));
+    for (int j = 0; j < 6; j++) ts.q[j] = b.q[j];
+    g_blocks.push_back(b);
+    return QSIM_OK;
+}
+}  // namespace qs
+
+using namespace qs;
+
+// psi_io: 2^n interleaved complex doubles in logical order (in and out).
+// start_l2p: logical -> physical map the plan starts from (NULL = identity).
+// info[0..2]: blocks, per-gate steps, qubits tc_build padded (0 when the
+// planner pads every block itself).
+extern "C" int emu_tc_run(const qsim_circuit *c, int prec, const int *start_l2p, double *psi_io, int64_t info[3])
+{
+    g_blocks.clear();
+    qsim_run_opts o;
+    memset(&o, 0, sizeof o);
+    o.mode = QSIM_MODE_FUSED;
+    o.prec = prec;
+    o.relabel_swaps = 1;
+    qsim_plan P;
+    qsim_status st = plan_build_tc(c, &o, start_l2p, &P);
+    if (st != QSIM_OK) return (int)st;
+    const int n = c->n;
+    const uint64_t N = 1ull << n;
+    std::vector<cd> a(N), b(N);
+    for (uint64_t i = 0; i < N; i++) {
+        uint64_t j = 0;
+        for (int q = 0; q < n; q++)
+            if ((i >> q) & 1) j |= 1ull << P.start_l2p[q];
+        a[j] = cd(psi_io[2 * i], psi_io[2 * i + 1]);
+    }
+    int64_t npergate = 0, padded = 0;
+    for (const PlanStep &s : P.steps) {
+        if (s.kind == 3) {
+            const EmuBlock &B = g_blocks[s.pass];
+            padded += 6 - B.k;
+            uint64_t m6 = 0;
+            for (int x = 0; x < 6; x++) m6 |= 1ull << B.q[x];
+            const std::vector<int32_t> &off = P.tc_pd_off[s.pass];
+            const std::vector<int32_t> &pb = P.tc_pd_bit[s.pass];
+            const std::vector<uint64_t> &tw = P.tc_pd_tw[s.pass];
+            const int D = 1 << B.k;
+            std::vector<cd> v(D), w(D);
+            for (uint64_t base = 0; base < N; base++) {
+                if (base & m6) continue;
+                for (int hi = 0; hi < 64 / D; hi++) {
+                    for (int l = 0; l < D; l++) {
+                        int row = l | (hi * D);
+                        uint64_t idx = base;
+                        for (int x = 0; x < 6; x++)
+                            if ((row >> x) & 1) idx |= 1ull << B.q[x];
+                        cd f = a[idx];
+                        if (!off.empty())
+                            for (int bb = 0; bb < 6; bb++)
+                                if ((row >> bb) & 1)
+                                    for (int z = off[bb]; z < off[bb + 1]; z++)
+                                        if ((base >> pb[z]) & 1)
+                                            f *= std::polar(1.0, (double)tw[z] * (2.0 * M_PI / 18446744073709551616.0));
+                        v[l] = f;
+                    }
+                    for (int r = 0; r < D; r++) {
+                        w[r] = 0.0;
+                        for (int cc = 0; cc < D; cc++) w[r] += B.U[(size_t)r * D + cc] * v[cc];
+                    }
+                    for (int l = 0; l < D; l++) {
+                        int row = l | (hi * D);
+                        uint64_t idx = base;
+                        for (int x = 0; x < 6; x++)
+                            if ((row >> x) & 1) idx |= 1ull << B.q[x];
+                        a[idx] = w[l];
+                    }
+                }
+            }
+        } else if (s.kind == 1) {
+            npergate++;
+            const qsim_gate &g = s.gate;
+            if (g.kind == QSIM_G_CP) {
+                cd f = std::polar(1.0, g.params[0]);
+                for (uint64_t i = 0; i < N; i++)
+                    if (((i >> g.q0) & 1) && ((i >> g.q1) & 1)) a[i] *= f;
+            } else {
+                uint64_t cm = 0, cv = 0;
+                for (int j = 0; j < g.ncontrols; j++) {
+                    cm |= 1ull << g.controls[j];
+                    if ((g.control_values >> j) & 1) cv |= 1ull << g.controls[j];
+                }
+                for (uint64_t i = 0; i < N; i++) {
+                    if (((i >> g.q0) & 1) || (i & cm) != cv) continue;
+                    uint64_t j = i | (1ull << g.q0);
+                    cd x = a[i], y = a[j];
+                    a[i] = s.mat[0] * x + s.mat[1] * y;
+                    a[j] = s.mat[2] * x + s.mat[3] * y;
+                }
+            }
+        } else if (s.kind == 2) {
+            for (cd &x : a) x *= s.phase;
+        } else {
+            return 100 + s.kind;
+        }
+    }
+    for (uint64_t i = 0; i < N; i++) {
+        uint64_t j = 0;
+        for (int q = 0; q < n; q++)
+            if ((i >> q) & 1) j |= 1ull << P.final_l2p[q];
+        b[i] = a[j];
+    }
+    for (uint64_t i = 0; i < N; i++) {
+        psi_io[2 * i] = b[i].real();
+        psi_io[2 * i + 1] = b[i].imag();
+    }
+    info[0] = (int64_t)g_blocks.size();
+    info[1] = npergate;
+    info[2] = padded;
+    return 0;
+}

@@ -1,0 +1,106 @@
+"""Host-side check of the tensor-core block planner (no GPU).
+
+The planner groups a circuit into <= 6-qubit dense blocks, defers diagonal
+gates (controlled phases, Z/S/T/phase, the diagonal part of fSim) into the
+next block that needs them, either folded into the block matrix or, for a
+term whose partner qubit stays outside, as a per-group phase read from the
+group index, and relabels SWAPs (Table I). tests/tc_plan_emu.cpp applies the
+resulting steps on the CPU exactly as the block kernel interprets them; the
+result must equal the FP64 oracle's state for the same circuit."""
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2304_14969_gb300 import qsim as Q
+from paper_2304_14969_gb300 import workloads as W
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+CSRC = os.path.join(ROOT, "paper_2304_14969_gb300", "csrc")
+CUDA = os.environ.get("CUDA_HOME", "/usr/local/cuda")
+
+
+@pytest.fixture(scope="module")
+def emu():
+    out = os.path.join(HERE, "_build", "libtcemu.so")
+    os.makedirs(os.path.dirname(out), exist_ok=True)
+    srcs = [os.path.join(HERE, "tc_plan_emu.cpp"), os.path.join(CSRC, "planner.cpp"), os.path.join(CSRC, "gates.cpp")]
+    cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-I", os.path.join(ROOT, "include"), "-I", CSRC,
+           "-I", os.path.join(CUDA, "include"), "-o", out] + srcs + \
+          ["-L", os.path.join(CUDA, "lib64"), "-lcudart", "-Wl,-rpath," + os.path.join(CUDA, "lib64")]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        pytest.fail("building the planner emulator failed:\n" + r.stderr[-3000:])
+    lib = C.CDLL(out)
+    lib.emu_tc_run.restype = C.c_int
+    return lib
+
+
+def run(lib, n, gates, x, start=None, prec=1):
+    c = Q.Circuit(n, gates)
+    y = np.ascontiguousarray(x.astype(np.complex128)).copy()
+    info = (C.c_int64 * 3)()
+    sp = (C.c_int * n)(*start) if start is not None else None
+    rc = lib.emu_tc_run(c.ptr(), prec, sp, y.ctypes.data_as(C.c_void_p), info)
+    assert rc == 0, rc
+    return y, list(info)
+
+
+def infid(y, ref):
+    return 1 - abs(np.vdot(ref, y)) ** 2 / (np.vdot(ref, ref).real * np.vdot(y, y).real)
+
+
+CASES = {
+    "grid20": lambda: (20, W.grid_rcs_circuit(4, 5, 8, seed=2), W.basis_state(20, 0)),
+    "paper16": lambda: (16, W.paper_random_circuit(4, 4, 6, seed=3), W.gaussian_state(16, 3)),
+    "random14": lambda: (14, W.random_1q_circuit(14, 200, 5), W.gaussian_state(14, 5)),
+    "random10": lambda: (10, W.random_1q_circuit(10, 300, 11), W.gaussian_state(10, 11)),
+    "qft16": lambda: (16, W.qft_circuit(16), W.gaussian_state(16, 6)),
+    "iqft12": lambda: (12, W.inverse_circuit(W.qft_circuit(12)), W.gaussian_state(12, 2)),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_tc_plan_matches_oracle(emu, name):
+    n, g, x = CASES[name]()
+    ref = oracle.apply_circuit(x, g)
+    y, info = run(emu, n, g, x)
+    assert info[0] >= 1
+    assert infid(y, ref) <= 1e-12
+    assert np.max(np.abs(y - ref)) <= 1e-12
+
+
+@pytest.mark.parametrize("name", ["qft16", "random14", "grid20"])
+def test_tc_plan_from_permuted_map(emu, name):
+    """Plans start from a state's current qubit map (bit-reversed after an
+    odd number of QFTs with relabelled SWAPs)."""
+    n, g, x = CASES[name]()
+    ref = oracle.apply_circuit(x, g)
+    rng = np.random.default_rng(n)
+    for start in (list(range(n))[::-1], [int(v) for v in rng.permutation(n)]):
+        y, _ = run(emu, n, g, x, start=start)
+        assert infid(y, ref) <= 1e-12
+
+
+def test_tc_plan_qft_block_count(emu):
+    """QFT-16: controlled phases deferred into the Hadamards' blocks; the
+    whole transform takes three six-qubit blocks and no per-gate step."""
+    n, g, x = CASES["qft16"]()
+    _, info = run(emu, n, g, x)
+    assert info[0] == 3 and info[1] == 0
+
+
+@pytest.mark.parametrize("n", [6, 7, 8, 9])
+def test_tc_plan_padding_with_partner_qubits(emu, n):
+    """Blocks of fewer than six qubits are padded with free qubits; in a small
+    QFT the only free ones are often partners of the block's deferred phases,
+    which then act inside the block rather than from the group index."""
+    g, x = W.qft_circuit(n), W.gaussian_state(n, n)
+    ref = oracle.apply_circuit(x, g)
+    y, info = run(emu, n, g, x)
+    assert infid(y, ref) <= 1e-12
+    assert np.max(np.abs(y - ref)) <= 1e-12
