@@ -86,11 +86,18 @@ qsim_status plan_upload(qsim_plan *P)
         if (bytes) memcpy(buf.data() + off, src, bytes);
         return off;
     };
+    const bool pipe = !P->tc_A.empty() && tc_pipe_eligible(P->n, (qsim_prec)P->prec);
+    std::vector<size_t> gt(P->tc_A.size(), 0);
     for (size_t i = 0; i < P->tc_A.size(); i++) {
         if (P->tc_pd_off[i].empty()) continue;
         pd_o[i] = put(P->tc_pd_off[i].data(), 4 * P->tc_pd_off[i].size());
         pd_b[i] = put(P->tc_pd_bit[i].data(), 4 * P->tc_pd_bit[i].size());
         pd_t[i] = put(P->tc_pd_tw[i].data(), 8 * P->tc_pd_tw[i].size());
+        if (pipe) {
+            std::vector<uint64_t> g;
+            tc_pipe_gturn(P->n, P->tc_spec[i], P->tc_pd_off[i], P->tc_pd_bit[i], P->tc_pd_tw[i], g);
+            gt[i] = put(g.data(), 8 * g.size());
+        }
     }
     size_t err_off = (buf.size() + 255) & ~(size_t)255;
     buf.resize(err_off + 256, 0);
@@ -112,6 +119,14 @@ qsim_status plan_upload(qsim_plan *P)
             ts.pd_off = (const int32_t *)(d + pd_o[i]);
             ts.pd_bit = (const int32_t *)(d + pd_b[i]);
             ts.pd_tw = (const uint64_t *)(d + pd_t[i]);
+        }
+    }
+    P->tc_pipe.clear();
+    if (pipe) {
+        P->tc_pipe.resize(P->tc_A.size());
+        for (size_t i = 0; i < P->tc_A.size(); i++) {
+            const uint64_t *g = P->tc_pd_off[i].empty() ? nullptr : (const uint64_t *)((unsigned char *)P->dmem + gt[i]);
+            QS_TRY(tc_pipe_prepare(P->n, P->tc_spec[i], g, P->tc_pipe[i]));
         }
     }
     return QSIM_OK;
@@ -263,8 +278,11 @@ qsim_status qsim_plan_execute(qsim_state *s, const qsim_plan *p)
                 QS_CUDA(launch_gate1(s, st.mat.data(), g.q0, cmask, cval));
             }
         } else if (st.kind == 3) {
-            QS_CUDA(tc_launch(s, p->tc_spec[st.pass], (const unsigned char *)p->dmem + p->tc_off[st.pass],
-                              (qsim_prec)p->prec, p->d_err));
+            const unsigned char *dU = (const unsigned char *)p->dmem + p->tc_off[st.pass];
+            if (!p->tc_pipe.empty())
+                QS_CUDA(tc_pipe_launch(s, p->tc_pipe[st.pass], dU, p->d_err));
+            else
+                QS_CUDA(tc_launch(s, p->tc_spec[st.pass], dU, (qsim_prec)p->prec, p->d_err));
         } else {
             cd m[4] = {st.phase, 0.0, 0.0, st.phase};
             QS_CUDA(launch_gate1(s, m, 0, 0, 0));

@@ -29,63 +29,11 @@
 #include <cstring>
 
 #include "qsim_internal.h"
+#include "tc_ptx.cuh"
 
 namespace qs {
 
 static const int kTcThreads = 128;
-static const int kTcRows = 128;   // M = K
-static const long long kTcSpin = 1ll << 26;
-
-__host__ __device__ constexpr int ctz_const(int j) { return (j & 1) ? 0 : 1 + ctz_const(j >> 1); }
-
-__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-// byte offset of element (row, k) in the canonical K-major no-swizzle layout
-__host__ __device__ __forceinline__ uint32_t canon_off(int row, int k, int es)
-{
-    const int per = 16 / es;                       // elements per core-matrix row
-    const uint32_t sbo = (uint32_t)(kTcRows / per) * 128u;
-    return (uint32_t)(row >> 3) * sbo + (uint32_t)(k / per) * 128u + (uint32_t)(row & 7) * 16u +
-           (uint32_t)(k % per) * (uint32_t)es;
-}
-
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
-{
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-    d |= (uint64_t)1 << 46;   // descriptor version of this architecture; no swizzle, base offset 0
-    return d;
-}
-
-__device__ __forceinline__ void mma_issue(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                          uint32_t accum, int kind_tf32)
-{
-    if (kind_tf32)
-        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                     "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
-                     "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum));
-    else
-        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
-                     "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum));
-}
-
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity)
-{
-    for (long long it = 0; it < kTcSpin; it++) {
-        uint32_t done;
-        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                     "selp.b32 %0, 1, 0, p;\n\t}\n"
-                     : "=r"(done)
-                     : "r"(mbar), "r"(parity)
-                     : "memory");
-        if (done) return true;
-    }
-    return false;
-}
-
 // Splits the pair (re, im) into hi and lo parts and stores each part as
 // one paired store (the two K-adjacent elements of a row).
 template <int ES>
@@ -279,17 +227,8 @@ __global__ void __launch_bounds__(kTcThreads, PREC == 1 ? 1 : 2) k_tc_block(floa
         for (int c0 = 0; c0 < N; c0 += 32) {
             uint32_t r[32];
             const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
-                "%13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
-                "[%32];"
-                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                  "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-                  "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-                  "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-                : "r"(taddr));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            tmem_ld32(taddr, r);
+            tmem_wait_ld();
 #pragma unroll
             for (int j = 0; j < 32; j++) stage[(c0 + j) * SROW + m] = __uint_as_float(r[j]);
         }
@@ -421,7 +360,14 @@ qsim_status apply_fused_tc(qsim_state *s, int k, const int *phys, const cd *u, q
     QS_CUDA(cudaMallocAsync((void **)&derr, sizeof(int), s->stream));
     QS_CUDA(cudaMemsetAsync(derr, 0, sizeof(int), s->stream));
     QS_CUDA(cudaMemcpyAsync(dA, A.data(), A.size(), cudaMemcpyHostToDevice, s->stream));
-    cudaError_t e = tc_launch(s, ts, dA, prec, derr);
+    cudaError_t e;
+    if (tc_pipe_eligible(s->n, prec)) {
+        TcPipeHost H;
+        qsim_status st = tc_pipe_prepare(s->n, ts, nullptr, H);
+        e = st == QSIM_OK ? tc_pipe_launch(s, H, dA, derr) : cudaErrorInvalidValue;
+    } else {
+        e = tc_launch(s, ts, dA, prec, derr);
+    }
     int herr = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);

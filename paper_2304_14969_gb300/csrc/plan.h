@@ -118,6 +118,7 @@ struct qsim_plan {
     std::vector<std::vector<int32_t>> tc_pd_off, tc_pd_bit;   // pre-diagonal partner lists per block
     std::vector<std::vector<uint64_t>> tc_pd_tw;
     std::vector<size_t> tc_off;
+    std::vector<qs::TcPipeHost> tc_pipe;                       // pipelined kernel geometry (BF16x3, n >= 13)
     int *d_err = nullptr;
     // device copies
     void *dmem = nullptr;

@@ -90,6 +90,38 @@ qsim_status tc_build(int n, int k, const int *phys, const cd *u, qsim_prec prec,
                      TcSpec &ts);
 cudaError_t tc_launch(qsim_state *s, const TcSpec &ts, const unsigned char *dA, qsim_prec prec, int *derr);
 
+// Pipelined BF16x3 block kernel (n >= 13): tile geometry and tables, built
+// on the host per block (k_tc_pipe.cu).
+struct TcPipeArgs {
+    uint64_t ntiles;
+    int tpos[13];            // tile qubits, ascending (tile index bits go to the other positions)
+    int dim_lo[5];           // lowest qubit of each tensor dimension
+    int dim_bits[5];         // qubits covered by each tensor dimension (coordinate width)
+    int nload;               // boxes per tile
+    int xoff[4];             // coordinate offset along dimension 4 of box v
+    uint32_t box_bytes;
+    uint16_t posL[64];       // in-stage element index of block index l
+    uint16_t posG[128];      // in-stage element index of group g
+    uint64_t spL[64];        // amplitude offset of block index l
+    uint64_t spG[128];       // amplitude offset of group g
+    const int32_t *pd_off;   // deferred phases (as in TcSpec), NULL if none
+    const int32_t *pd_bit;
+    const uint64_t *pd_tw;
+    const uint64_t *gturn;   // [128][6] turns contributed by the group bits, NULL if none
+};
+struct TcPipeHost {
+    TcPipeArgs args;
+    int rank;
+    uint64_t gdim[5], gstr[4];
+    uint32_t box[5], estr[5];
+    int freeq[7];
+};
+bool tc_pipe_eligible(int n, qsim_prec prec);
+qsim_status tc_pipe_prepare(int n, const TcSpec &ts, const uint64_t *gturn_dev, TcPipeHost &H);
+void tc_pipe_gturn(int n, const TcSpec &ts, const std::vector<int32_t> &off, const std::vector<int32_t> &pbit,
+                   const std::vector<uint64_t> &tw, std::vector<uint64_t> &out);
+cudaError_t tc_pipe_launch(qsim_state *s, const TcPipeHost &H, const unsigned char *dU, int *derr);
+
 // ------------------------------------------------------ kernel launchers
 // (all stream-ordered, no sync; return cuda errors)
 cudaError_t launch_gate1(qsim_state *s, const cd u[4], int t, uint64_t cmask, uint64_t cval);

@@ -1,0 +1,140 @@
+// Host-side geometry of the pipelined tensor-core block kernel
+// (k_tc_pipe.cu): which qubits form a tile, how a 5-D TMA tensor map
+// covers it, and the index tables the kernel uses. Plain C++ so that the
+// CPU tests can check it.
+#include <algorithm>
+#include <cstring>
+
+#include "qsim_internal.h"
+
+namespace qs {
+
+bool tc_pipe_eligible(int n, qsim_prec prec) { return prec == QSIM_PREC_BF16X3 && n >= 13; }
+
+// Tile geometry of a block: tile qubits T = the block's 6 qubits and the 7
+// lowest qubits outside it; the tensor map views the ket as up to 5
+// dimensions, each a run of consecutive qubits of T (at most 8 per
+// dimension) plus the non-tile qubits above it, so a box is exactly the
+// tile's amplitudes with the tile base's bits as coordinates. Runs beyond
+// the fifth become extra boxes along dimension 4.
+qsim_status tc_pipe_prepare(int n, const TcSpec &ts, const uint64_t *gturn_dev, TcPipeHost &H)
+{
+    if (n < 13 || n > 36) return fail(QSIM_E_UNSUPPORTED, "pipelined tensor-core blocks need 13 <= n <= 36");
+    uint64_t blk = 0;
+    for (int b = 0; b < 6; b++) blk |= bit(ts.q[b]);
+    std::vector<int> freeq;
+    for (int p = 0; p < n && (int)freeq.size() < 7; p++)
+        if (!(blk & bit(p))) freeq.push_back(p);
+    std::vector<int> T;
+    for (int p = 0; p < n; p++)
+        if ((blk & bit(p)) || std::find(freeq.begin(), freeq.end(), p) != freeq.end()) T.push_back(p);
+    // chunks of consecutive tile qubits, at most 8 each
+    std::vector<std::pair<int, int>> ch;   // (first qubit, length)
+    for (int p : T) {
+        if (!ch.empty() && ch.back().first + ch.back().second == p && ch.back().second < 8)
+            ch.back().second++;
+        else
+            ch.push_back({p, 1});
+    }
+    int nd = std::min<int>((int)ch.size(), 5);
+    TcPipeArgs &A = H.args;
+    memset(&A, 0, sizeof A);
+    A.ntiles = 1ull << (n - 13);
+    for (int j = 0; j < 13; j++) A.tpos[j] = T[j];
+    uint64_t gdim[5], gstr[4];
+    uint32_t box[5], estr[5] = {1, 1, 1, 1, 1};
+    int boxbits = 0;
+    for (int d = 0; d < 5; d++) {
+        if (d < nd) {
+            const int lo = ch[d].first;
+            const int hi = (d + 1 < nd) ? ch[d + 1].first : n;
+            A.dim_lo[d] = lo;
+            A.dim_bits[d] = hi - lo;
+            gdim[d] = 1ull << (hi - lo);
+            box[d] = 1u << ch[d].second;
+            boxbits += ch[d].second;
+        } else {
+            A.dim_lo[d] = n;
+            A.dim_bits[d] = 0;
+            gdim[d] = 1;
+            box[d] = 1;
+        }
+        if (d >= 1) gstr[d - 1] = (d < nd) ? (uint64_t)8 << A.dim_lo[d] : (uint64_t)8 << n;
+    }
+    // extra boxes enumerate the qubits of chunks 5.. (inside dimension 4)
+    std::vector<int> xq;
+    for (size_t c = 5; c < ch.size(); c++)
+        for (int i = 0; i < ch[c].second; i++) xq.push_back(ch[c].first + i);
+    if ((int)xq.size() > 2 || boxbits + (int)xq.size() != 13)
+        return fail(QSIM_E_UNSUPPORTED, "tensor-core tile geometry not covered (%d extra qubits)", (int)xq.size());
+    A.nload = 1 << xq.size();
+    for (int v = 0; v < A.nload; v++) {
+        int off = 0;
+        for (size_t i = 0; i < xq.size(); i++)
+            if ((v >> i) & 1) off |= 1 << (xq[i] - A.dim_lo[4]);
+        A.xoff[v] = off;
+    }
+    A.box_bytes = (uint32_t)(8u << boxbits);
+    auto rank = [&](int q) { return (int)(std::find(T.begin(), T.end(), q) - T.begin()); };
+    for (int l = 0; l < 64; l++) {
+        int r = 0;
+        uint64_t o = 0;
+        for (int b = 0; b < 6; b++)
+            if ((l >> b) & 1) {
+                r |= 1 << rank(ts.q[b]);
+                o |= bit(ts.q[b]);
+            }
+        A.posL[l] = (uint16_t)r;
+        A.spL[l] = o;
+    }
+    for (int g = 0; g < 128; g++) {
+        int r = 0;
+        uint64_t o = 0;
+        for (int f = 0; f < 7; f++)
+            if ((g >> f) & 1) {
+                r |= 1 << rank(freeq[f]);
+                o |= bit(freeq[f]);
+            }
+        A.posG[g] = (uint16_t)r;
+        A.spG[g] = o;
+    }
+    A.pd_off = ts.pd_off;
+    A.pd_bit = ts.pd_bit;
+    A.pd_tw = ts.pd_tw;
+    A.gturn = gturn_dev;
+    H.rank = 5;
+    for (int d = 0; d < 5; d++) {
+        H.gdim[d] = gdim[d];
+        H.box[d] = box[d];
+        H.estr[d] = estr[d];
+        if (d < 4) H.gstr[d] = gstr[d];
+    }
+    for (int f = 0; f < 7; f++) H.freeq[f] = freeq[f];
+    return QSIM_OK;
+}
+
+// Host table of the deferred phases' group terms: gturn[g][b] = sum of the
+// turns of block bit b's partners that are group bits of g.
+void tc_pipe_gturn(int n, const TcSpec &ts, const std::vector<int32_t> &off, const std::vector<int32_t> &pbit,
+                   const std::vector<uint64_t> &tw, std::vector<uint64_t> &out)
+{
+    uint64_t blk = 0;
+    for (int b = 0; b < 6; b++) blk |= bit(ts.q[b]);
+    std::vector<int> freeq;
+    for (int p = 0; p < n && (int)freeq.size() < 7; p++)
+        if (!(blk & bit(p))) freeq.push_back(p);
+    out.assign(128 * 6, 0);
+    for (int g = 0; g < 128; g++) {
+        uint64_t o = 0;
+        for (int f = 0; f < 7; f++)
+            if ((g >> f) & 1) o |= bit(freeq[f]);
+        for (int b = 0; b < 6; b++) {
+            uint64_t t = 0;
+            for (int e = off[b]; e < off[b + 1]; e++)
+                if ((o >> pbit[e]) & 1) t += tw[e];
+            out[g * 6 + b] = t;
+        }
+    }
+}
+
+}  // namespace qs

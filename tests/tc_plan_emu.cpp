@@ -155,3 +155,40 @@ extern "C" int emu_tc_run(const qsim_circuit *c, int prec, const int *start_l2p,
     info[2] = padded;
     return 0;
 }
+
+// Tile geometry of the pipelined tensor-core kernel for block qubits q6:
+// dims[0..4] lowest qubit, dims[5..9] coordinate bits, dims[10..14] box
+// extents, dims[15..19] global extents, dims[20..23] byte strides of
+// dimensions 1..4, dims[24] boxes per tile, dims[25..28] dimension-4
+// offsets of the boxes, dims[29] box bytes; tpos[13] tile qubits.
+extern "C" int emu_tc_geometry(int n, const int *q6, int64_t *dims, int *tpos, int *posL, int *posG, uint64_t *spL,
+                               uint64_t *spG)
+{
+    TcSpec ts;
+    memset(&ts, 0, sizeof ts);
+    for (int b = 0; b < 6; b++) ts.q[b] = q6[b];
+    TcPipeHost H;
+    qsim_status st = tc_pipe_prepare(n, ts, nullptr, H);
+    if (st != QSIM_OK) return (int)st;
+    const TcPipeArgs &A = H.args;
+    for (int d = 0; d < 5; d++) {
+        dims[d] = A.dim_lo[d];
+        dims[5 + d] = A.dim_bits[d];
+        dims[10 + d] = H.box[d];
+        dims[15 + d] = (int64_t)H.gdim[d];
+        if (d < 4) dims[20 + d] = (int64_t)H.gstr[d];
+    }
+    dims[24] = A.nload;
+    for (int v = 0; v < 4; v++) dims[25 + v] = A.xoff[v];
+    dims[29] = A.box_bytes;
+    for (int j = 0; j < 13; j++) tpos[j] = A.tpos[j];
+    for (int l = 0; l < 64; l++) {
+        posL[l] = A.posL[l];
+        spL[l] = A.spL[l];
+    }
+    for (int g = 0; g < 128; g++) {
+        posG[g] = A.posG[g];
+        spG[g] = A.spG[g];
+    }
+    return 0;
+}

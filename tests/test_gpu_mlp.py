@@ -86,12 +86,15 @@ def test_training_lowers_loss(Q):
 
 def test_mlp_schedule_gain_over_exhaustive(Q):
     """Train the proposal MLP on traces of the exhaustive approximate mode
-    (20-qubit grid circuits, p in the range where checks both round and keep:
-    with fSim(pi/2, pi/6) couplers eps clusters just below 0.38), then run
+    (20-qubit 4x5 grid circuits, 6 layers, p from 0.5 to 0.9), then run
     held-out circuits with the MLP schedule (check only qubits it predicts to
-    round, exhaustive round every 8 entangling gates) and with the exhaustive
-    schedule at the same p. The gain is fewer Bloch reductions; the fidelity
-    cost is judged against the exhaustive run with the exact state."""
+    round, top 4; exhaustive round every 8 entangling gates) and with the
+    exhaustive schedule at the same p. With fSim(pi/2, pi/6) couplers the
+    checks round selectively for p in about [0.6, 0.72] and almost always
+    above; the gain is measured where the choice matters (p = 0.6, 0.7):
+    fewer Bloch reductions, while still finding a fair share of the
+    roundings, at no fidelity cost against the exact state (a missed
+    rounding keeps more of the state, it costs memory, not fidelity)."""
     import oracle
     from paper_2304_14969_gb300 import workloads as W
     rows, cols = 4, 5
@@ -99,7 +102,7 @@ def test_mlp_schedule_gain_over_exhaustive(Q):
     X, Y = [], []
     for seed in range(6):
         g = W.grid_rcs_circuit(rows, cols, 6, seed=100 + seed)
-        for p in (0.70, 0.72, 0.74, 0.76, 0.78, 0.80):
+        for p in (0.5, 0.6, 0.66, 0.7, 0.72, 0.74, 0.76, 0.78, 0.8, 0.85, 0.9):
             r, _, (f, l), _ = Q.approx_run(n, g, p, trace_cap=20000)
             X.append(f)
             Y.append(l)
@@ -116,17 +119,25 @@ def test_mlp_schedule_gain_over_exhaustive(Q):
     acc = np.mean((logits > 0) == (Y > 0.5))
     base = max(Y.mean(), 1 - Y.mean())
     assert acc >= base, (acc, base)       # at least as good as the majority class
-    passes = {"exh": 0, "mlp": 0}
-    fid = {"exh": [], "mlp": []}
+    exact = []
     for seed in range(3):
         g = W.grid_rcs_circuit(rows, cols, 6, seed=900 + seed)
-        exact = oracle.apply_circuit(W.basis_state(n, 0), g)
+        exact.append((g, oracle.apply_circuit(W.basis_state(n, 0), g)))
+    for p in (0.6, 0.7):
+        out = {}
         for name, kw in (("exh", {}), ("mlp", {"schedule": Q.QSIM_SCHED_MLP, "mlp": h, "top_m": 4,
                                                 "fallback_every": 8})):
-            r, psi, _, _ = Q.approx_run(n, g, 0.74, want_state=True, **kw)
-            passes[name] += r.n_bloch_passes
-            psi = psi.astype(np.complex128)
-            fid[name].append(abs(np.vdot(psi, exact)) ** 2 / np.vdot(psi, psi).real)
-    assert passes["mlp"] < 0.8 * passes["exh"], passes
-    assert np.mean(fid["mlp"]) >= np.mean(fid["exh"]) - 0.05, fid
+            passes = rounds = 0
+            fid = []
+            for g, ex in exact:
+                r, psi, _, _ = Q.approx_run(n, g, p, want_state=True, **kw)
+                passes += r.n_bloch_passes
+                rounds += r.n_rounds
+                psi = psi.astype(np.complex128)
+                fid.append(abs(np.vdot(psi, ex)) ** 2 / np.vdot(psi, psi).real)
+            out[name] = (passes, rounds, float(np.mean(fid)))
+        (pe, re_, fe), (pm, rm, fm) = out["exh"], out["mlp"]
+        assert pm <= 0.7 * pe, (p, out)
+        assert rm >= 0.4 * re_, (p, out)
+        assert fm >= fe - 0.05, (p, out)
     Q.qsim_mlp_destroy(h)

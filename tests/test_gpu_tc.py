@@ -40,7 +40,12 @@ def apply(Q, n, qs, U, prec, x):
 
 @pytest.mark.parametrize("prec", [1, 2])
 @pytest.mark.parametrize("n,qs", [(6, [0, 1, 2, 3, 4, 5]), (8, [2, 7, 0, 5, 3, 6]), (12, [11, 3, 8, 5, 9, 1]),
-                                  (16, [4, 15, 9]), (18, [0]), (20, [19, 18, 17, 16, 2, 10])])
+                                  (16, [4, 15, 9]), (18, [0]), (20, [19, 18, 17, 16, 2, 10]),
+                                  # n >= 13 (BF16x3: TMA-fed pipelined kernel): low block, two to four
+                                  # boxes per tile, block on the top qubits
+                                  (13, [0, 1, 2, 3, 4, 5]), (14, [8, 10, 12, 3, 1, 13]),
+                                  (22, [7, 9, 11, 13, 15, 17]), (21, [20, 14, 9, 7, 3, 11]),
+                                  (19, [18, 17, 16, 15, 14, 13])])
 def test_tc_block_vs_oracle(Q, prec, n, qs):
     x = W.gaussian_state(n, n)
     U = W.random_unitary(len(qs), 7 + n)

@@ -28,7 +28,8 @@ CUDA = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 def emu():
     out = os.path.join(HERE, "_build", "libtcemu.so")
     os.makedirs(os.path.dirname(out), exist_ok=True)
-    srcs = [os.path.join(HERE, "tc_plan_emu.cpp"), os.path.join(CSRC, "planner.cpp"), os.path.join(CSRC, "gates.cpp")]
+    srcs = [os.path.join(HERE, "tc_plan_emu.cpp"), os.path.join(CSRC, "planner.cpp"), os.path.join(CSRC, "gates.cpp"),
+            os.path.join(CSRC, "tc_geom.cpp")]
     cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-I", os.path.join(ROOT, "include"), "-I", CSRC,
            "-I", os.path.join(CUDA, "include"), "-o", out] + srcs + \
           ["-L", os.path.join(CUDA, "lib64"), "-lcudart", "-Wl,-rpath," + os.path.join(CUDA, "lib64")]
@@ -104,3 +105,70 @@ def test_tc_plan_padding_with_partner_qubits(emu, n):
     y, info = run(emu, n, g, x)
     assert infid(y, ref) <= 1e-12
     assert np.max(np.abs(y - ref)) <= 1e-12
+
+
+def tile_base(tpos, t):
+    base = t
+    for p in tpos:
+        base = ((base >> p) << (p + 1)) | (base & ((1 << p) - 1))
+    return base
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_tc_pipe_tile_geometry(emu, seed):
+    """The pipelined tensor-core kernel loads a tile (the block's 6 qubits and
+    the 7 lowest others) with up to four 5-D TMA boxes. Replaying the box
+    semantics (element (i0..i4) of box v sits at sum_d (c_d + i_d) * stride_d,
+    c_4 shifted by the box's offset; the boxes land one after another in
+    shared memory, dimension 0 fastest) must give every amplitude of the tile
+    exactly once, at the in-stage index posL[l] | posG[g] the kernel reads,
+    with all coordinates inside the tensor."""
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(13, 31))
+    if seed % 4 == 0:
+        q6 = sorted(int(v) for v in rng.choice(n, 6, replace=False))
+    elif seed % 4 == 1:
+        q6 = [int(v) for v in rng.choice(np.arange(0, n, 2), 6, replace=False)]
+    elif seed % 4 == 2:
+        q6 = [n - 1 - i for i in range(6)]
+    else:
+        q6 = [int(v) for v in rng.choice(n, 6, replace=False)]
+    dims = (C.c_int64 * 30)()
+    tpos = (C.c_int * 13)()
+    posL, posG = (C.c_int * 64)(), (C.c_int * 128)()
+    spL, spG = (C.c_uint64 * 64)(), (C.c_uint64 * 128)()
+    rc = emu.emu_tc_geometry(n, (C.c_int * 6)(*q6), dims, tpos, posL, posG, spL, spG)
+    assert rc == 0
+    d = list(dims)
+    lo, bits, box, gdim, gstr = d[0:5], d[5:10], d[10:15], d[15:20], d[20:24]
+    nload, xoff, box_bytes = d[24], d[25:29], d[29]
+    tp = list(tpos)
+    assert sorted(tp) == tp and set(q6) <= set(tp)
+    free = [p for p in range(n) if p not in q6][:7]
+    assert sorted(set(q6) | set(free)) == tp
+    strides = [8] + gstr          # bytes; dimension 0 is contiguous
+    for k in range(1, 5):          # dense, non-overlapping dimensions
+        assert strides[k] == strides[k - 1] * gdim[k - 1]
+        assert strides[k] % 16 == 0 and strides[k] < 2 ** 40
+    assert all(1 <= b <= 256 for b in box) and box[0] * 8 % 16 == 0
+    assert box_bytes == 8 * int(np.prod(box)) and box_bytes * nload == 65536
+    ntiles = 1 << (n - 13)
+    for t in {0, ntiles - 1, int(rng.integers(0, ntiles))}:
+        base = tile_base(tp, t)
+        assert all(not (base >> p) & 1 for p in tp)
+        c = [(base >> lo[k]) & ((1 << bits[k]) - 1) for k in range(5)]
+        stage = np.full(8192, -1, dtype=np.int64)
+        for v in range(nload):
+            cc = list(c)
+            cc[4] += xoff[v]
+            for k in range(5):
+                assert 0 <= cc[k] and cc[k] + box[k] <= gdim[k]
+            idx = np.zeros(1, dtype=np.int64)
+            for k in range(5):       # box elements, dimension 0 fastest
+                off = (cc[k] + np.arange(box[k], dtype=np.int64)) * (strides[k] // 8)
+                idx = (idx[None, :] + off[:, None]).reshape(-1)
+            stage[v * (box_bytes // 8):(v + 1) * (box_bytes // 8)] = idx
+        want = np.array([base + spL[l] + spG[g] for g in range(128) for l in range(64)], dtype=np.int64)
+        pos = np.array([posL[l] | posG[g] for g in range(128) for l in range(64)])
+        assert np.array_equal(np.sort(pos), np.arange(8192))
+        assert np.array_equal(stage[pos], want)
