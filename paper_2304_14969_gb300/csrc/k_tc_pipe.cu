@@ -70,9 +70,9 @@ __global__ void __launch_bounds__(kPThreads, 1)
 {
     extern __shared__ unsigned char sm_dyn[];
     unsigned char *smb = (unsigned char *)(((uintptr_t)sm_dyn + 1023) & ~(uintptr_t)1023);
-    unsigned char *Us = smb;                              // U^T operand: hi [0, 32K), lo [32K, 64K)
-    unsigned char *St = smb + kPU;                        // stages 0 and 1
-    __shared__ __align__(8) uint64_t bar_full[2], bar_opr[2], bar_mma[2], bar_accf[2];
+    unsigned char *Us = smb;                              // U operand (N x K): hi [0, 32K), lo [32K, 64K)
+    unsigned char *St = smb + kPU;                        // raw stages 0 and 1
+    __shared__ __align__(8) uint64_t bar_full[2], bar_sfree[2], bar_aready[2], bar_mma[2], bar_accf[2];
     __shared__ uint32_t s_tmem;
     __shared__ int s_abort;
     __shared__ uint16_t s_posL[64];
@@ -97,7 +97,8 @@ __global__ void __launch_bounds__(kPThreads, 1)
         s_abort = 0;
         for (int s = 0; s < 2; s++) {
             mbar_init(smem_addr(&bar_full[s]), 1);
-            mbar_init(smem_addr(&bar_opr[s]), kPConv);
+            mbar_init(smem_addr(&bar_sfree[s]), kPConv);
+            mbar_init(smem_addr(&bar_aready[s]), kPConv);
             mbar_init(smem_addr(&bar_mma[s]), 1);
             mbar_init(smem_addr(&bar_accf[s]), kPConv);
         }
@@ -105,13 +106,15 @@ __global__ void __launch_bounds__(kPThreads, 1)
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&s_tmem)),
-                     "r"(256u));
+                     "r"(512u));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
+    // TMEM columns: accumulators [0, 128) and [128, 256); A operands (hi, lo:
+    // 64 + 64 columns, BF16 pairs) [256, 384) and [384, 512)
     const uint32_t tmem = s_tmem;
     volatile int *abort_flag = &s_abort;
     auto give_up = [&]() {
@@ -122,12 +125,14 @@ __global__ void __launch_bounds__(kPThreads, 1)
     const uint64_t J = P.ntiles > blockIdx.x ? (P.ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
 
     if (warp == 0) {
-        // ---------------- TMA producer
+        // ---------------- TMA producer: stage s is reloaded once the
+        // converters have read the tile two before
         if (lane == 0) {
             uint64_t issued = 0;
             for (uint64_t j = 0; j < J && !*abort_flag; j++) {
                 const int s = (int)(j & 1);
-                if (j >= 2 && !mbar_wait_or_abort(smem_addr(&bar_mma[s]), (uint32_t)(((j - 2) >> 1) & 1), abort_flag)) {
+                if (j >= 2 &&
+                    !mbar_wait_or_abort(smem_addr(&bar_sfree[s]), (uint32_t)(((j - 2) >> 1) & 1), abort_flag)) {
                     give_up();
                     break;
                 }
@@ -147,35 +152,36 @@ __global__ void __launch_bounds__(kPThreads, 1)
                 mbar_wait(smem_addr(&bar_full[j & 1]), (uint32_t)((j >> 1) & 1));
         }
     } else if (warp == 1) {
-        // ---------------- MMA issue
+        // ---------------- MMA issue: D[g][n] = sum_k A[g][k] U[n][k], A in TMEM
         if (lane == 0) {
             const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(128 >> 3) << 17) |
                                    ((uint32_t)(128 >> 4) << 24);
             const uint32_t SBO = 2048u;
             uint64_t issued = 0;
             for (uint64_t j = 0; j < J && !*abort_flag; j++) {
-                const int s = (int)(j & 1), b = (int)(j & 1);
-                if (!mbar_wait_or_abort(smem_addr(&bar_opr[s]), (uint32_t)((j >> 1) & 1), abort_flag)) {
+                const int b = (int)(j & 1);
+                if (!mbar_wait_or_abort(smem_addr(&bar_aready[b]), (uint32_t)((j >> 1) & 1), abort_flag)) {
                     give_up();
                     break;
                 }
-                if (j >= 2 && !mbar_wait_or_abort(smem_addr(&bar_accf[b]), (uint32_t)(((j - 2) >> 1) & 1), abort_flag)) {
+                if (j >= 2 &&
+                    !mbar_wait_or_abort(smem_addr(&bar_accf[b]), (uint32_t)(((j - 2) >> 1) & 1), abort_flag)) {
                     give_up();
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 const uint32_t d = tmem + (uint32_t)b * 128u;
-                const uint32_t sh = smem_addr(St + (size_t)s * kPStage), sl = sh + kPHalf;
+                const uint32_t ah = tmem + 256u + (uint32_t)b * 128u, al = ah + 64u;
                 const uint32_t uh = smem_addr(Us), ul = uh + kPHalf;
                 uint32_t accum = 0;
 #pragma unroll 1
                 for (int part = 0; part < 3; part++) {
-                    const uint32_t abase = part == 2 ? sl : sh, bbase = part == 1 ? ul : uh;
+                    const uint32_t abase = part == 2 ? al : ah, bbase = part == 1 ? ul : uh;
 #pragma unroll
                     for (int kk = 0; kk < 8; kk++) {
-                        const uint32_t koff = (uint32_t)kk * 256u;
-                        mma_issue(d, smem_desc(abase + koff, 128u, SBO), smem_desc(bbase + koff, 128u, SBO), idesc,
-                                  accum, 0);
+                        // K step of 16 BF16 = 8 TMEM columns of A, two core matrices of U
+                        mma_issue_tmem_a(d, abase + (uint32_t)kk * 8u, smem_desc(bbase + (uint32_t)kk * 256u, 128u, SBO),
+                                         idesc, accum);
                         accum = 1;
                     }
                 }
@@ -186,28 +192,20 @@ __global__ void __launch_bounds__(kPThreads, 1)
             if (issued) mbar_wait(smem_addr(&bar_mma[(issued - 1) & 1]), (uint32_t)(((issued - 1) >> 1) & 1));
         }
     } else {
-        // ---------------- convert + write back (warps 2..9)
+        // ---------------- convert + write back (warps 2..9). A thread owns one
+        // group (its TMEM lane) and half of its 64 amplitudes.
         const int ct = tid - 64, cw = ct >> 5;
-        const int lq = lane >> 3;                          // l & 3 of this thread's elements
-        const int ga = 16 * cw + (lane & 7), gb = ga + 8;  // this thread's two groups (convert)
-        uint32_t offL[16];                                 // raw byte offset of l = 4m + lq
-#pragma unroll
-        for (int m = 0; m < 16; m++) offL[m] = 8u * s_posL[4 * m + lq];
-        const uint32_t offGa = 8u * P.posG[ga], offGb = 8u * P.posG[gb];
-        // operand byte offset of (g, l): (g >> 3) * SBO + (l >> 2) * 128 + (g & 7) * 16 + (l & 3) * 4
-        const uint32_t wa = (uint32_t)(ga >> 3) * 2048u + (uint32_t)(ga & 7) * 16u + (uint32_t)lq * 4u;
-        const uint32_t wb = wa + 2048u;
-        // write-back: TMEM lane quarter of this warp, column half
         const int quarter = warp & 3, half = cw >> 2;
-        const int ge = 32 * quarter + lane;
-        const uint64_t spGe = P.spG[ge];
+        const int g = 32 * quarter + lane;
+        const uint32_t lane_off = (uint32_t)(32 * quarter) << 16;
+        const uint32_t offG = 8u * P.posG[g];
+        const uint64_t spG = P.spG[g];
 
         for (uint64_t j = 0; j <= J; j++) {
             if (j < J) {
-                const int s = (int)(j & 1);
-                // base turns of the deferred phases for this tile (published by
-                // the barrier below)
+                const int s = (int)(j & 1), b = (int)(j & 1);
                 if (has_pd && ct < 6) {
+                    // base turns of the deferred phases (published by the barrier below)
                     const uint64_t base = tile_base(P, blockIdx.x + j * gridDim.x);
                     uint64_t tt = 0;
                     for (int e = P.pd_off[ct]; e < P.pd_off[ct + 1]; e++)
@@ -220,63 +218,51 @@ __global__ void __launch_bounds__(kPThreads, 1)
                     give_up();
                     break;
                 }
-                unsigned char *stage = St + (size_t)s * kPStage;
-                float2 va[16], vb[16];
+                const unsigned char *stage = St + (size_t)s * kPStage + offG;
+                float2 v[32];
 #pragma unroll
-                for (int m = 0; m < 16; m++) {
-                    va[m] = *(const float2 *)(stage + offGa + offL[m]);
-                    vb[m] = *(const float2 *)(stage + offGb + offL[m]);
-                }
+                for (int i = 0; i < 32; i++) v[i] = *(const float2 *)(stage + 8u * s_posL[32 * half + i]);
+                mbar_arrive(smem_addr(&bar_sfree[s]));   // the stage may be reloaded
                 if (has_pd) {
-                    // factor of (g, l) = prod_b e_b(g)^(l_b); l = 4m + lq
+                    // factor of (g, l) = prod_b e_b(g)^(l_b), l = 32 half + i
+                    float er[6], ei[6];
 #pragma unroll
-                    for (int h = 0; h < 2; h++) {
-                        const int g = h ? gb : ga;
-                        float er[6], ei[6];
+                    for (int bb = 0; bb < 6; bb++) turns_sincos(s_bt[bb] + s_gturn[g * 6 + bb], ei[bb], er[bb]);
+                    float fr = half ? er[5] : 1.f, fi = half ? ei[5] : 0.f;
+                    float tr[32], ti[32];
+                    tr[0] = fr;
+                    ti[0] = fi;
 #pragma unroll
-                        for (int b = 0; b < 6; b++) turns_sincos(s_bt[b] + s_gturn[g * 6 + b], ei[b], er[b]);
-                        float fr[16], fi[16];
-                        fr[0] = 1.f;
-                        fi[0] = 0.f;
-                        if (lq & 1) {
-                            fr[0] = er[0];
-                            fi[0] = ei[0];
-                        }
-                        if (lq & 2) {
-                            const float xr = fr[0] * er[1] - fi[0] * ei[1];
-                            fi[0] = fr[0] * ei[1] + fi[0] * er[1];
-                            fr[0] = xr;
-                        }
+                    for (int i = 1; i < 32; i++) {
+                        const int low = ctz_const(i), prev = i & (i - 1);
+                        tr[i] = tr[prev] * er[low] - ti[prev] * ei[low];
+                        ti[i] = tr[prev] * ei[low] + ti[prev] * er[low];
+                    }
 #pragma unroll
-                        for (int m = 1; m < 16; m++) {
-                            const int low = ctz_const(m), prev = m & (m - 1);
-                            fr[m] = fr[prev] * er[2 + low] - fi[prev] * ei[2 + low];
-                            fi[m] = fr[prev] * ei[2 + low] + fi[prev] * er[2 + low];
-                        }
-#pragma unroll
-                        for (int m = 0; m < 16; m++) {
-                            float2 &x = h ? vb[m] : va[m];
-                            const float xr = x.x * fr[m] - x.y * fi[m];
-                            x.y = x.x * fi[m] + x.y * fr[m];
-                            x.x = xr;
-                        }
+                    for (int i = 0; i < 32; i++) {
+                        const float xr = v[i].x * tr[i] - v[i].y * ti[i];
+                        v[i].y = v[i].x * ti[i] + v[i].y * tr[i];
+                        v[i].x = xr;
                     }
                 }
-                named_bar_sync(1, kPConv);   // every raw element of the stage has been read
+                // BF16 hi / lo split into the A operand of accumulator b (the MMAs
+                // of tile j - 2, the last reader of these columns, completed
+                // before this thread wrote that tile back)
+                uint32_t hi[32], lo[32];
 #pragma unroll
-                for (int m = 0; m < 16; m++) {
-#pragma unroll
-                    for (int h = 0; h < 2; h++) {
-                        const float2 x = h ? vb[m] : va[m];
-                        const uint32_t off = (h ? wb : wa) + (uint32_t)m * 128u;
-                        const __nv_bfloat162 hi = __floats2bfloat162_rn(x.x, x.y);
-                        const float2 hf = __bfloat1622float2(hi);
-                        *(__nv_bfloat162 *)(stage + off) = hi;
-                        *(__nv_bfloat162 *)(stage + kPHalf + off) = __floats2bfloat162_rn(x.x - hf.x, x.y - hf.y);
-                    }
+                for (int i = 0; i < 32; i++) {
+                    const __nv_bfloat162 h = __floats2bfloat162_rn(v[i].x, v[i].y);
+                    const float2 hf = __bfloat1622float2(h);
+                    const __nv_bfloat162 l2 = __floats2bfloat162_rn(v[i].x - hf.x, v[i].y - hf.y);
+                    hi[i] = *(const uint32_t *)&h;
+                    lo[i] = *(const uint32_t *)&l2;
                 }
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                mbar_arrive(smem_addr(&bar_opr[s]));
+                const uint32_t acol = tmem + lane_off + 256u + (uint32_t)b * 128u + (uint32_t)(32 * half);
+                tmem_st32(acol, hi);
+                tmem_st32(acol + 64u, lo);
+                tmem_wait_st();
+                asm volatile("tcgen05.fence::before_thread_sync;");
+                mbar_arrive(smem_addr(&bar_aready[b]));
             }
             if (j >= 1) {
                 // write back tile j - 1
@@ -289,12 +275,11 @@ __global__ void __launch_bounds__(kPThreads, 1)
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 const uint64_t base = tile_base(P, blockIdx.x + jj * gridDim.x);
-                float2 *dstg = a + (base + spGe);
+                float2 *dstg = a + (base + spG);
 #pragma unroll 1
                 for (int c0 = 0; c0 < 64; c0 += 32) {
                     uint32_t r[32];
-                    tmem_ld32(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)b * 128u + (uint32_t)(64 * half + c0),
-                              r);
+                    tmem_ld32(tmem + lane_off + (uint32_t)b * 128u + (uint32_t)(64 * half + c0), r);
                     tmem_wait_ld();
                     const int l0 = 32 * half + c0 / 2;
 #pragma unroll
@@ -311,7 +296,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (warp == 1) {
         __syncwarp();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256u));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u));
     }
 }
 
