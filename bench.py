@@ -207,9 +207,11 @@ def main():
     # The QFT leaves the ket bit-reversed (its swaps are relabels, Table I);
     # a second plan starts from that layout, so consecutive steps alternate
     # between the two plans and no step moves data for the relabel.
-    plans = [Q.Plan(circ, dtype=Q.QSIM_C64, state=st)]
+    # Fused blocks of <= 6 qubits on the tensor cores (BF16x3 split, FP32
+    # accumulation in TMEM, controlled phases deferred into per-group phases).
+    plans = [Q.Plan(circ, dtype=Q.QSIM_C64, prec=Q.QSIM_PREC_BF16X3, state=st)]
     plans[0].execute(st)
-    plans.append(Q.Plan(circ, dtype=Q.QSIM_C64, state=st))
+    plans.append(Q.Plan(circ, dtype=Q.QSIM_C64, prec=Q.QSIM_PREC_BF16X3, state=st))
     plans[1].execute(st)
     info = plans[0].info()
     nrm = C.c_double()
@@ -288,12 +290,13 @@ def main():
         "metric": "amplitude-gate updates/s", "value": value, "unit": "updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "qft27_gaussian_c64_fused", "n_qubits": n, "gates": ng, "passes": npass,
-                   "tile_qubits": info["tile_qubits"], "ket_bytes": 8 * N, "l2": "ket (1 GiB) larger than L2",
+        "config": {"workload": "qft27_gaussian_c64_tc_bf16x3", "n_qubits": n, "gates": ng, "blocks": npass,
+                   "path": "fused <=6-qubit blocks on tensor cores (BF16x3 split, FP32 accumulation)",
+                   "ket_bytes": 8 * N, "l2": "ket (1 GiB) larger than L2",
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic_from_profiles("k_fused_pass"),
-                     "kernel": "k_fused_pass", "alg_bytes_per_launch": alg_bytes,
+                     "frac": achieved / peak, "traffic": traffic_from_profiles("k_tc_pipe"),
+                     "kernel": "k_tc_pipe", "alg_bytes_per_launch": alg_bytes,
                      "launch_ms": launch_ms, "peak_source": "measured hbm_gbs" if peaks else "fallback"},
         "e2e": {"value": e2e_val, "unit": "updates/s", "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 8 * N},
         "gpu_launches": args.steps * (npass + 2),
@@ -326,36 +329,51 @@ def time_plan(Q, C, plan, st, reps):
 
 
 def run_grid_tc(args):
-    """Grid circuit on tensor-core blocks (profiling workload)."""
+    """Grid circuit or QFT on tensor-core blocks (profiling workload)."""
     import ctypes as C
     import torch
     from paper_2304_14969_gb300 import build, qsim as Q
     from paper_2304_14969_gb300 import workloads as W
     build.build()
     Q.lib()
-    n = int(args.workload[4:].split("_")[0])
-    rows, cols = W.grid_shape(n)
-    g = W.grid_rcs_circuit(rows, cols, 10, seed=0, n=n)
+    fam = "qft" if args.workload.startswith("qft") else "grid"
+    n = int(args.workload[len(fam):].split("_")[0])
+    if fam == "grid":
+        rows, cols = W.grid_shape(n)
+        g = W.grid_rcs_circuit(rows, cols, 10, seed=0, n=n)
+    else:
+        g = W.qft_circuit(n)
     circ = Q.Circuit(n, g)
     st = Q.State(n, Q.QSIM_C64)
-    plan = Q.Plan(circ, dtype=Q.QSIM_C64, prec=Q.QSIM_PREC_BF16X3)
+    # plans for both qubit maps the state alternates between (a QFT with
+    # relabelled swaps leaves the ket bit-reversed), so no step permutes
+    plans = [Q.Plan(circ, dtype=Q.QSIM_C64, prec=Q.QSIM_PREC_BF16X3, state=st)]
+    plans[0].execute(st)
+    plans.append(Q.Plan(circ, dtype=Q.QSIM_C64, prec=Q.QSIM_PREC_BF16X3, state=st))
+    k = 1
     for _ in range(args.warmup):
-        Q.qsim_set_basis(st.h, 0)
-        plan.execute(st)
+        plans[k % 2].execute(st)
+        k += 1
     Q.qsim_synchronize(st.h)
-    ms = 0.0
+    import torch
+    a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record()
     for _ in range(args.steps):
-        Q.qsim_set_basis(st.h, 0)
-        ms += time_plan(Q, C, plan, st, 1)
-    ms /= args.steps
-    nb = plan.info()["passes"]
+        plans[k % 2].execute(st)
+        k += 1
+    z.record()
+    Q.qsim_synchronize(st.h)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(z) / args.steps
+    nb = plans[0].info()["passes"]
     N = 1 << n
     print(json.dumps({"metric": "amplitude-gate updates/s", "value": len(g) * N / (ms * 1e-3), "unit": "updates/s",
                       "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                       "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                       "data": "synthetic",
-                      "config": {"workload": f"grid{n}_c64_tc_bf16x3", "n_qubits": n, "gates": len(g), "blocks": nb},
-                      "roofline": {"bound": "hbm", "kernel": "k_tc_block",
+                      "config": {"workload": f"{fam}{n}_c64_tc_bf16x3", "n_qubits": n, "gates": len(g), "blocks": nb},
+                      "roofline": {"bound": "hbm", "kernel": "k_tc_pipe",
                                    "achieved": 2 * 8 * N / (ms / nb * 1e-3) / 1e9}}))
 
 
@@ -392,6 +410,27 @@ def extra_legs(Q, W, C, torch, circ, x, n, ng):
     out["fused_fp64"] = {"updates_per_s": ng * N / f128, "ms": f128 * 1e3, "dtype": "c128",
                          "passes": p.info()["passes"]}
     s.close()
+    # the same QFT as fused SIMT passes (complex64, 2^13-amplitude tiles)
+    ssim = Q.State(n, Q.QSIM_C64)
+    ssim.upload(x)
+    sps = [Q.Plan(circ, dtype=Q.QSIM_C64, state=ssim)]
+    sps[0].execute(ssim)
+    sps.append(Q.Plan(circ, dtype=Q.QSIM_C64, state=ssim))
+    sps[1].execute(ssim)
+    a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    Q.qsim_synchronize(ssim.h)
+    torch.cuda.synchronize()
+    a.record()
+    for r in range(10):
+        sps[r % 2].execute(ssim)
+    z.record()
+    Q.qsim_synchronize(ssim.h)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(z) / 10
+    npp = sps[0].info()["passes"]
+    out["qft27_c64_fused_simt"] = {"updates_per_s": ng * N / (ms * 1e-3), "ms": ms, "passes": npp,
+                                   "kernel": "k_fused_pass", "hbm_gbs_per_pass": 2 * 8 * N / (ms / npp * 1e-3) / 1e9}
+    ssim.close()
     # the same QFT on tensor-core blocks (deferred phases as per-group
     # pre-diagonals), agreement with the fused SIMT result
     peaks = {}
@@ -429,7 +468,7 @@ def extra_legs(Q, W, C, torch, circ, x, n, ng):
         nbk = tps[0].info()["passes"]
         achieved = 2 * 8 * N / (ms / nbk * 1e-3) / 1e9
         out[f"qft27_c64_tc_{name}"] = {"updates_per_s": ng * N / (ms * 1e-3), "ms": ms, "blocks": nbk,
-                                       "kernel": "k_tc_block", "hbm_gbs_per_block": achieved,
+                                       "kernel": "k_tc_pipe" if name == "bf16x3" else "k_tc_block", "hbm_gbs_per_block": achieved,
                                        "frac_of_hbm": achieved / peaks.get("hbm_gbs", 6800.0),
                                        "infidelity_vs_simt": 1.0 - (ip[0] ** 2 + ip[1] ** 2) / (na.value * nb.value)}
         stc.close()
@@ -472,7 +511,7 @@ def extra_legs(Q, W, C, torch, circ, x, n, ng):
         Q.qsim_norm(st2.h, C.byref(nb2))
         out[f"grid30_c64_tc_{name}"] = {
             "updates_per_s": len(g) * (1 << 30) / (ms * 1e-3), "ms": ms, "blocks": nb,
-            "kernel": "k_tc_block", "hbm_gbs_per_block": achieved,
+            "kernel": "k_tc_pipe" if name == "bf16x3" else "k_tc_block", "hbm_gbs_per_block": achieved,
             "frac_of_hbm": achieved / peaks.get("hbm_gbs", 6800.0),
             "infidelity_vs_simt": 1.0 - (ip[0] ** 2 + ip[1] ** 2) / (na.value * nb2.value)}
         st2.close()

@@ -114,6 +114,8 @@ qsim_status qsim_destroy(qsim_state *s)
     if (s->stream) cudaStreamSynchronize(s->stream);
     else cudaDeviceSynchronize();
     if (s->owned && s->amps) cudaFree(s->amps);
+    if (s->d_err) cudaFree(s->d_err);
+    if (s->h_err) cudaFreeHost(s->h_err);
     free_scratch(s->red);
     delete s;
     return QSIM_OK;
@@ -146,8 +148,9 @@ qsim_status qsim_download(qsim_state *s, void *host_amps)
     if (!host_amps) return fail(QSIM_E_INVAL, "host_amps is NULL");
     if (is_identity(s)) {
         QS_CUDA(cudaMemcpyAsync(host_amps, s->amps, s->amp_bytes(), cudaMemcpyDeviceToHost, s->stream));
+        err_fetch(s);
         QS_CUDA(cudaStreamSynchronize(s->stream));
-        return QSIM_OK;
+        return err_check(s);
     }
     // physical bit p holds logical qubit L with l2p[L] = p; logical order puts it at bit L
     std::vector<int> to(s->n);
@@ -159,8 +162,9 @@ qsim_status qsim_download(qsim_state *s, void *host_amps)
         e = cudaMemcpyAsync(host_amps, tmp, s->amp_bytes(), cudaMemcpyDeviceToHost, s->stream);
     cudaFreeAsync(tmp, s->stream);
     if (e != cudaSuccess) return cuda_fail(e, "download");
+    err_fetch(s);
     QS_CUDA(cudaStreamSynchronize(s->stream));
-    return QSIM_OK;
+    return err_check(s);
 }
 
 qsim_status qsim_device_ptr(const qsim_state *s, void **dev_amps)
@@ -197,8 +201,9 @@ qsim_status qsim_synchronize(qsim_state *s)
 {
     clear_error();
     QS_TRY(check_state(s));
+    err_fetch(s);
     QS_CUDA(cudaStreamSynchronize(s->stream));
-    return QSIM_OK;
+    return err_check(s);
 }
 
 // ------------------------------------------------------------ gates
@@ -352,8 +357,9 @@ qsim_status qsim_probs(qsim_state *s, double *host_out)
     }
     cudaFreeAsync(d, s->stream);
     if (st != QSIM_OK) return st;
+    err_fetch(s);
     QS_CUDA(cudaStreamSynchronize(s->stream));
-    return QSIM_OK;
+    return err_check(s);
 }
 
 qsim_status qsim_inner_product(qsim_state *a, qsim_state *b, double out[2])
@@ -407,3 +413,30 @@ qsim_status qsim_bloch_all(qsim_state *s, double *r)
 const char *qsim_version(void) { return "qsim-gb300 0.1 (sm_103a)"; }
 
 }  // extern "C"
+
+namespace qs {
+
+qsim_status err_ensure(qsim_state *s)
+{
+    if (s->d_err) return QSIM_OK;
+    QS_CUDA(cudaMalloc((void **)&s->d_err, sizeof(int)));
+    QS_CUDA(cudaMallocHost((void **)&s->h_err, sizeof(int)));
+    *s->h_err = 0;
+    QS_CUDA(cudaMemsetAsync(s->d_err, 0, sizeof(int), s->stream));
+    return QSIM_OK;
+}
+
+void err_fetch(qsim_state *s)
+{
+    if (s->d_err) cudaMemcpyAsync(s->h_err, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
+}
+
+qsim_status err_check(qsim_state *s)
+{
+    if (!s->h_err || !*s->h_err) return QSIM_OK;
+    *s->h_err = 0;
+    cudaMemsetAsync(s->d_err, 0, sizeof(int), s->stream);
+    return fail(QSIM_E_TIMEOUT, "tensor-core block: a bounded wait in the MMA pipeline gave up (result invalid)");
+}
+
+}  // namespace qs

@@ -94,20 +94,17 @@ qsim_status plan_upload(qsim_plan *P)
         pd_b[i] = put(P->tc_pd_bit[i].data(), 4 * P->tc_pd_bit[i].size());
         pd_t[i] = put(P->tc_pd_tw[i].data(), 8 * P->tc_pd_tw[i].size());
         if (pipe) {
-            std::vector<uint64_t> g;
-            tc_pipe_gturn(P->n, P->tc_spec[i], P->tc_pd_off[i], P->tc_pd_bit[i], P->tc_pd_tw[i], g);
-            gt[i] = put(g.data(), 8 * g.size());
+            std::vector<unsigned char> tb;
+            tc_pipe_tables(P->n, P->tc_spec[i], P->tc_pd_off[i], P->tc_pd_bit[i], P->tc_pd_tw[i], tb);
+            gt[i] = put(tb.data(), tb.size());
         }
     }
-    size_t err_off = (buf.size() + 255) & ~(size_t)255;
-    buf.resize(err_off + 256, 0);
     if (buf.empty()) buf.resize(256);
     QS_CUDA(cudaMalloc(&P->dmem, buf.size()));
     P->dbytes = buf.size();
     QS_CUDA(cudaMemcpy(P->dmem, buf.data(), buf.size(), cudaMemcpyHostToDevice));
     for (size_t i = 0; i < P->passes.size(); i++)
         P->passes[i].dev.stage = (const unsigned char *)P->dmem + offs[i];
-    P->d_err = (int *)((unsigned char *)P->dmem + err_off);
     for (size_t i = 0; i < P->tc_A.size(); i++) {
         TcSpec &ts = P->tc_spec[i];
         if (P->tc_pd_off[i].empty()) {
@@ -125,7 +122,7 @@ qsim_status plan_upload(qsim_plan *P)
     if (pipe) {
         P->tc_pipe.resize(P->tc_A.size());
         for (size_t i = 0; i < P->tc_A.size(); i++) {
-            const uint64_t *g = P->tc_pd_off[i].empty() ? nullptr : (const uint64_t *)((unsigned char *)P->dmem + gt[i]);
+            const void *g = P->tc_pd_off[i].empty() ? nullptr : (const void *)((unsigned char *)P->dmem + gt[i]);
             QS_TRY(tc_pipe_prepare(P->n, P->tc_spec[i], g, P->tc_pipe[i]));
         }
     }
@@ -279,23 +276,19 @@ qsim_status qsim_plan_execute(qsim_state *s, const qsim_plan *p)
             }
         } else if (st.kind == 3) {
             const unsigned char *dU = (const unsigned char *)p->dmem + p->tc_off[st.pass];
+            QS_TRY(err_ensure(s));
             if (!p->tc_pipe.empty())
-                QS_CUDA(tc_pipe_launch(s, p->tc_pipe[st.pass], dU, p->d_err));
+                QS_CUDA(tc_pipe_launch(s, p->tc_pipe[st.pass], dU, s->d_err));
             else
-                QS_CUDA(tc_launch(s, p->tc_spec[st.pass], dU, (qsim_prec)p->prec, p->d_err));
+                QS_CUDA(tc_launch(s, p->tc_spec[st.pass], dU, (qsim_prec)p->prec, s->d_err));
         } else {
             cd m[4] = {st.phase, 0.0, 0.0, st.phase};
             QS_CUDA(launch_gate1(s, m, 0, 0, 0));
         }
     }
     s->l2p = p->final_l2p;
-    if (!p->tc_spec.empty()) {
-        // tensor-core plans report a bounded MMA wait that gave up (synchronises)
-        int herr = 0;
-        QS_CUDA(cudaMemcpyAsync(&herr, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
-        QS_CUDA(cudaStreamSynchronize(s->stream));
-        if (herr) return fail(QSIM_E_TIMEOUT, "tensor-core block: MMA completion wait gave up");
-    }
+    // tensor-core blocks report a bounded wait that gave up through the
+    // state's error word, read at the next call that synchronises
     return QSIM_OK;
 }
 

@@ -290,8 +290,9 @@ static qsim_status finish(qsim_state *s, int rows)
     k_red_final<M><<<1, 64, 0, s->stream>>>(s->red.d, rows, dout);
     QS_CUDA(cudaGetLastError());
     QS_CUDA(cudaMemcpyAsync(s->red.h, dout, M * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    err_fetch(s);
     QS_CUDA(cudaStreamSynchronize(s->stream));
-    return QSIM_OK;
+    return err_check(s);
 }
 
 static qsim_status ensure_red(qsim_state *s)

@@ -147,8 +147,10 @@ __global__ void __launch_bounds__(kTcThreads, PREC == 1 ? 1 : 2) k_tc_block(floa
                 uint64_t tt = 0;
                 for (int e = ts.pd_off[b]; e < ts.pd_off[b + 1]; e++)
                     if ((base >> ts.pd_bit[e]) & 1) tt += ts.pd_tw[e];
-                float f = (float)(int64_t)tt * 5.42101086242752217e-20f;
-                sincospif(2.0f * f, &ei[b], &er[b]);
+                float f = (float)(int64_t)tt * 5.42101086242752217e-20f, sn, cs;
+                sincospif(2.0f * f, &sn, &cs);
+                ei[b] = sn;
+                er[b] = cs;
             }
             constexpr int STEP = kTcThreads / N;
             // factors for the low log2(STEP) bits come from l0, the rest from j
@@ -164,12 +166,15 @@ __global__ void __launch_bounds__(kTcThreads, PREC == 1 ? 1 : 2) k_tc_block(floa
             float fr[LPER], fi[LPER];
             fr[0] = br;
             fi[0] = bi;
-            // f[j] = f[j without its lowest set bit] * e[that bit]
+            // f[m + 2^bb] = f[m] * e[SH + bb] (constant indices: registers, not local memory)
+            constexpr int LB = LPER == 64 ? 6 : LPER == 32 ? 5 : LPER == 16 ? 4 : 3;
 #pragma unroll
-            for (int j = 1; j < LPER; j++) {
-                const int low = ctz_const(j), prev = j & (j - 1);
-                fr[j] = fr[prev] * er[SH + low] - fi[prev] * ei[SH + low];
-                fi[j] = fr[prev] * ei[SH + low] + fi[prev] * er[SH + low];
+            for (int bb = 0; bb < LB; bb++) {
+#pragma unroll
+                for (int m = 0; m < (1 << bb); m++) {
+                    fr[m + (1 << bb)] = fr[m] * er[SH + bb] - fi[m] * ei[SH + bb];
+                    fi[m + (1 << bb)] = fr[m] * ei[SH + bb] + fi[m] * er[SH + bb];
+                }
             }
 #pragma unroll
             for (int j = 0; j < LPER; j++) {

@@ -12,12 +12,13 @@
 //            U[2l'+ri'][k], S the tile (M = 128 groups, K = 128) and U the
 //            real-embedded block (N = 128), into one of two 128-column TMEM
 //            accumulators;
-//   warps 2..9 = convert (read the raw tile from its stage, apply the
-//            deferred per-group phases, write its BF16 hi / lo split in
-//            place as the MMA's A operand) and write back (each thread owns
-//            one TMEM lane = one group and 32 of its amplitudes, stored to
-//            HBM directly: lanes are consecutive groups, so stores are
-//            coalesced when the low qubits are outside the block).
+//   warps 2..17 = convert: read the raw tile from its stage (and release
+//            the stage at once), apply the deferred per-group phases, write
+//            the BF16 hi / lo split into TMEM as the MMA's A operand;
+//   warps 18..21 = write back: each thread owns one TMEM lane = one group
+//            and stores its 64 amplitudes to HBM directly (lanes are
+//            consecutive groups, so stores are coalesced when the low
+//            qubits are outside the block).
 //
 // Stage s is reloaded once the MMAs that read it have completed; TMEM
 // accumulator b is reused once the write-back of the tile before has read
@@ -39,8 +40,11 @@ namespace qs {
 
 namespace {
 
-constexpr int kPThreads = 320;
-constexpr int kPConv = 256;                  // converter / write-back threads (warps 2..9)
+constexpr int kPConvWarps = 16;              // converter warps (2 .. 17)
+constexpr int kPConv = 32 * kPConvWarps;
+constexpr int kPEpiWarps = 4;                // write-back warps (18 .. 21), one per TMEM lane quarter
+constexpr int kPEpi = 32 * kPEpiWarps;
+constexpr int kPThreads = 64 + kPConv + kPEpi;
 constexpr uint32_t kPStage = 65536;          // one tile of complex64
 constexpr uint32_t kPHalf = 32768;           // hi or lo BF16 operand of a tile (128 x 128)
 constexpr uint32_t kPU = 65536;              // U hi + lo
@@ -77,17 +81,20 @@ __global__ void __launch_bounds__(kPThreads, 1)
     __shared__ int s_abort;
     __shared__ uint16_t s_posL[64];
     __shared__ uint64_t s_spL[64];
-    __shared__ uint64_t s_bt[6];
-    __shared__ uint64_t s_gturn[128 * 6];
+    __shared__ uint64_t s_tturn[6 * 24];
+    __shared__ float2 s_gfac[128 * 6];
+    __shared__ float2 s_E[4][6];             // tile factors of the deferred phases (tile j in slot j & 3)
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const bool has_pd = P.pd_off != nullptr;
+    const bool has_pd = P.gfac != nullptr;
     for (int i = tid; i < 64; i += kPThreads) {
         s_posL[i] = P.posL[i];
         s_spL[i] = P.spL[i];
     }
-    if (has_pd)
-        for (int i = tid; i < 128 * 6; i += kPThreads) s_gturn[i] = P.gturn[i];
+    if (has_pd) {
+        for (int i = tid; i < 128 * 6; i += kPThreads) s_gfac[i] = P.gfac[i];
+        for (int i = tid; i < 6 * 24; i += kPThreads) s_tturn[i] = P.tturn[i];
+    }
     {
         const int4 *src = (const int4 *)Ug;
         int4 *dst = (int4 *)Us;
@@ -96,11 +103,13 @@ __global__ void __launch_bounds__(kPThreads, 1)
     if (tid == 0) {
         s_abort = 0;
         for (int s = 0; s < 2; s++) {
-            mbar_init(smem_addr(&bar_full[s]), 1);
+            // with deferred phases the producer arrives a second time once the
+            // tile factors are written
+            mbar_init(smem_addr(&bar_full[s]), has_pd ? 2 : 1);
             mbar_init(smem_addr(&bar_sfree[s]), kPConv);
             mbar_init(smem_addr(&bar_aready[s]), kPConv);
             mbar_init(smem_addr(&bar_mma[s]), 1);
-            mbar_init(smem_addr(&bar_accf[s]), kPConv);
+            mbar_init(smem_addr(&bar_accf[s]), kPEpi);
         }
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
@@ -125,32 +134,50 @@ __global__ void __launch_bounds__(kPThreads, 1)
     const uint64_t J = P.ntiles > blockIdx.x ? (P.ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
 
     if (warp == 0) {
-        // ---------------- TMA producer: stage s is reloaded once the
+        // ---------------- TMA producer (lane 0) and tile factors of the
+        // deferred phases (lanes 0..5): stage s is reloaded once the
         // converters have read the tile two before
-        if (lane == 0) {
-            uint64_t issued = 0;
-            for (uint64_t j = 0; j < J && !*abort_flag; j++) {
-                const int s = (int)(j & 1);
-                if (j >= 2 &&
-                    !mbar_wait_or_abort(smem_addr(&bar_sfree[s]), (uint32_t)(((j - 2) >> 1) & 1), abort_flag)) {
-                    give_up();
-                    break;
-                }
-                const uint64_t base = tile_base(P, blockIdx.x + j * gridDim.x);
+        uint64_t issued = 0;
+        for (uint64_t j = 0; j < J; j++) {
+            const int s = (int)(j & 1);
+            int stop = 0;
+            if (lane == 0) {
+                const bool ok = j < 2 ||
+                                mbar_wait_or_abort(smem_addr(&bar_sfree[s]), (uint32_t)(((j - 2) >> 1) & 1), abort_flag);
+                if (!ok) give_up();
+                stop = !ok || *abort_flag;
+            }
+            if (__shfl_sync(0xffffffffu, stop, 0)) break;
+            const uint64_t t = blockIdx.x + j * gridDim.x;
+            const uint32_t fb = smem_addr(&bar_full[s]);
+            if (lane == 0) {
+                const uint64_t base = tile_base(P, t);
                 int c[5];
 #pragma unroll
                 for (int d = 0; d < 5; d++) c[d] = (int)((base >> P.dim_lo[d]) & ((1ull << P.dim_bits[d]) - 1));
-                const uint32_t fb = smem_addr(&bar_full[s]);
                 mbar_arrive_expect_tx(fb, P.box_bytes * (uint32_t)P.nload);
                 const uint32_t dst = smem_addr(St + (size_t)s * kPStage);
                 for (int v = 0; v < P.nload; v++)
                     tma_load_5d(dst + (uint32_t)v * P.box_bytes, &tmap, fb, c[0], c[1], c[2], c[3], c[4] + P.xoff[v]);
-                issued = j + 1;
             }
-            // loads still in flight (only after an abort) land before the CTA exits
+            if (has_pd) {
+                if (lane < 6) {
+                    uint64_t tt = 0;
+                    for (int i = 0; i < P.ntb; i++)
+                        if ((t >> i) & 1) tt += s_tturn[lane * 24 + i];
+                    float sn, cs;
+                    turns_sincos(tt, sn, cs);
+                    s_E[j & 3][lane] = make_float2(cs, sn);
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(fb);
+            }
+            issued = j + 1;
+        }
+        // loads still in flight (only after an abort) land before the CTA exits
+        if (lane == 0)
             for (uint64_t j = issued >= 2 ? issued - 2 : 0; j < issued; j++)
                 mbar_wait(smem_addr(&bar_full[j & 1]), (uint32_t)((j >> 1) & 1));
-        }
     } else if (warp == 1) {
         // ---------------- MMA issue: D[g][n] = sum_k A[g][k] U[n][k], A in TMEM
         if (lane == 0) {
@@ -191,104 +218,125 @@ __global__ void __launch_bounds__(kPThreads, 1)
             }
             if (issued) mbar_wait(smem_addr(&bar_mma[(issued - 1) & 1]), (uint32_t)(((issued - 1) >> 1) & 1));
         }
-    } else {
-        // ---------------- convert + write back (warps 2..9). A thread owns one
-        // group (its TMEM lane) and half of its 64 amplitudes.
+    } else if (warp < 2 + kPConvWarps) {
+        // ---------------- convert (warps 2..17). A thread owns one group (its
+        // TMEM lane) and 16 of its 64 amplitudes, l = 16 part + i. The stage
+        // is released as soon as it has been read: with two stages, the time
+        // a landed tile waits to be read is what bounds the load pipeline.
         const int ct = tid - 64, cw = ct >> 5;
-        const int quarter = warp & 3, half = cw >> 2;
+        const int quarter = warp & 3, part = cw >> 2;
         const int g = 32 * quarter + lane;
         const uint32_t lane_off = (uint32_t)(32 * quarter) << 16;
         const uint32_t offG = 8u * P.posG[g];
-        const uint64_t spG = P.spG[g];
 
-        for (uint64_t j = 0; j <= J; j++) {
-            if (j < J) {
-                const int s = (int)(j & 1), b = (int)(j & 1);
-                if (has_pd && ct < 6) {
-                    // base turns of the deferred phases (published by the barrier below)
-                    const uint64_t base = tile_base(P, blockIdx.x + j * gridDim.x);
-                    uint64_t tt = 0;
-                    for (int e = P.pd_off[ct]; e < P.pd_off[ct + 1]; e++)
-                        if ((base >> P.pd_bit[e]) & 1) tt += P.pd_tw[e];
-                    s_bt[ct] = tt;
-                }
-                const bool ok = mbar_wait_or_abort(smem_addr(&bar_full[s]), (uint32_t)((j >> 1) & 1), abort_flag);
-                // one decision for all converter threads (none may be left at a barrier)
-                if (named_bar_or(1, kPConv, !ok || *abort_flag)) {
-                    give_up();
-                    break;
-                }
-                const unsigned char *stage = St + (size_t)s * kPStage + offG;
-                float2 v[32];
-#pragma unroll
-                for (int i = 0; i < 32; i++) v[i] = *(const float2 *)(stage + 8u * s_posL[32 * half + i]);
-                mbar_arrive(smem_addr(&bar_sfree[s]));   // the stage may be reloaded
-                if (has_pd) {
-                    // factor of (g, l) = prod_b e_b(g)^(l_b), l = 32 half + i
-                    float er[6], ei[6];
-#pragma unroll
-                    for (int bb = 0; bb < 6; bb++) turns_sincos(s_bt[bb] + s_gturn[g * 6 + bb], ei[bb], er[bb]);
-                    float fr = half ? er[5] : 1.f, fi = half ? ei[5] : 0.f;
-                    float tr[32], ti[32];
-                    tr[0] = fr;
-                    ti[0] = fi;
-#pragma unroll
-                    for (int i = 1; i < 32; i++) {
-                        const int low = ctz_const(i), prev = i & (i - 1);
-                        tr[i] = tr[prev] * er[low] - ti[prev] * ei[low];
-                        ti[i] = tr[prev] * ei[low] + ti[prev] * er[low];
-                    }
-#pragma unroll
-                    for (int i = 0; i < 32; i++) {
-                        const float xr = v[i].x * tr[i] - v[i].y * ti[i];
-                        v[i].y = v[i].x * ti[i] + v[i].y * tr[i];
-                        v[i].x = xr;
-                    }
-                }
-                // BF16 hi / lo split into the A operand of accumulator b (the MMAs
-                // of tile j - 2, the last reader of these columns, completed
-                // before this thread wrote that tile back)
-                uint32_t hi[32], lo[32];
-#pragma unroll
-                for (int i = 0; i < 32; i++) {
-                    const __nv_bfloat162 h = __floats2bfloat162_rn(v[i].x, v[i].y);
-                    const float2 hf = __bfloat1622float2(h);
-                    const __nv_bfloat162 l2 = __floats2bfloat162_rn(v[i].x - hf.x, v[i].y - hf.y);
-                    hi[i] = *(const uint32_t *)&h;
-                    lo[i] = *(const uint32_t *)&l2;
-                }
-                const uint32_t acol = tmem + lane_off + 256u + (uint32_t)b * 128u + (uint32_t)(32 * half);
-                tmem_st32(acol, hi);
-                tmem_st32(acol + 64u, lo);
-                tmem_wait_st();
-                asm volatile("tcgen05.fence::before_thread_sync;");
-                mbar_arrive(smem_addr(&bar_aready[b]));
+        for (uint64_t j = 0; j < J; j++) {
+            const int s = (int)(j & 1), b = (int)(j & 1);
+            const bool ok = mbar_wait_or_abort(smem_addr(&bar_full[s]), (uint32_t)((j >> 1) & 1), abort_flag);
+            // one decision for all converter threads (none may be left at a barrier)
+            if (named_bar_or(1, kPConv, !ok || *abort_flag)) {
+                give_up();
+                break;
             }
-            if (j >= 1) {
-                // write back tile j - 1
-                const uint64_t jj = j - 1;
-                const int b = (int)(jj & 1);
-                const bool ok = mbar_wait_or_abort(smem_addr(&bar_mma[b]), (uint32_t)((jj >> 1) & 1), abort_flag);
-                if (named_bar_or(1, kPConv, !ok || *abort_flag)) {
+            const unsigned char *stage = St + (size_t)s * kPStage + offG;
+            float2 v[16];
+#pragma unroll
+            for (int i = 0; i < 16; i++) v[i] = *(const float2 *)(stage + 8u * s_posL[16 * part + i]);
+            mbar_arrive(smem_addr(&bar_sfree[s]));   // the stage may be reloaded
+            if (has_pd) {
+                // factor of (g, l) = prod_b e_b(g)^(l_b), e_b(g) = E_b(tile) G_b(g);
+                // bits 4, 5 of l from part, 0..3 from i
+                float er[6], ei[6];
+#pragma unroll
+                for (int bb = 0; bb < 6; bb++) {
+                    const float2 E = s_E[j & 3][bb], G = s_gfac[g * 6 + bb];
+                    er[bb] = E.x * G.x - E.y * G.y;
+                    ei[bb] = E.x * G.y + E.y * G.x;
+                }
+                float fr = 1.f, fi = 0.f;
+                if (part & 1) {
+                    fr = er[4];
+                    fi = ei[4];
+                }
+                if (part & 2) {
+                    const float xr = fr * er[5] - fi * ei[5];
+                    fi = fr * ei[5] + fi * er[5];
+                    fr = xr;
+                }
+                float tr[16], ti[16];
+                tr[0] = fr;
+                ti[0] = fi;
+                // tr[m + 2^bb] = tr[m] e_bb (constant indices: the factors stay in registers)
+#pragma unroll
+                for (int bb = 0; bb < 4; bb++) {
+#pragma unroll
+                    for (int m = 0; m < (1 << bb); m++) {
+                        tr[m + (1 << bb)] = tr[m] * er[bb] - ti[m] * ei[bb];
+                        ti[m + (1 << bb)] = tr[m] * ei[bb] + ti[m] * er[bb];
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < 16; i++) {
+                    const float xr = v[i].x * tr[i] - v[i].y * ti[i];
+                    v[i].y = v[i].x * ti[i] + v[i].y * tr[i];
+                    v[i].x = xr;
+                }
+            }
+            // BF16 hi / lo split into A operand b (TMEM)
+            uint32_t hi[16], lo[16];
+#pragma unroll
+            for (int i = 0; i < 16; i++) {
+                const __nv_bfloat162 h = __floats2bfloat162_rn(v[i].x, v[i].y);
+                const float2 hf = __bfloat1622float2(h);
+                const __nv_bfloat162 l2 = __floats2bfloat162_rn(v[i].x - hf.x, v[i].y - hf.y);
+                hi[i] = *(const uint32_t *)&h;
+                lo[i] = *(const uint32_t *)&l2;
+            }
+            if (j >= 2) {
+                // A operand b was last read by the MMAs of tile j - 2
+                const bool ok2 =
+                    mbar_wait_or_abort(smem_addr(&bar_mma[b]), (uint32_t)(((j - 2) >> 1) & 1), abort_flag);
+                if (named_bar_or(1, kPConv, !ok2 || *abort_flag)) {
                     give_up();
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;");
-                const uint64_t base = tile_base(P, blockIdx.x + jj * gridDim.x);
-                float2 *dstg = a + (base + spG);
-#pragma unroll 1
-                for (int c0 = 0; c0 < 64; c0 += 32) {
-                    uint32_t r[32];
-                    tmem_ld32(tmem + lane_off + (uint32_t)b * 128u + (uint32_t)(64 * half + c0), r);
-                    tmem_wait_ld();
-                    const int l0 = 32 * half + c0 / 2;
-#pragma unroll
-                    for (int i = 0; i < 16; i++)
-                        dstg[s_spL[l0 + i]] = make_float2(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1]));
-                }
-                asm volatile("tcgen05.fence::before_thread_sync;");
-                mbar_arrive(smem_addr(&bar_accf[b]));
             }
+            const uint32_t acol = tmem + lane_off + 256u + (uint32_t)b * 128u + (uint32_t)(16 * part);
+            tmem_st16(acol, hi);
+            tmem_st16(acol + 64u, lo);
+            tmem_wait_st();
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            mbar_arrive(smem_addr(&bar_aready[b]));
+        }
+    } else {
+        // ---------------- write back (warps 18..21): TMEM lane = group,
+        // accumulator columns 2l + {re, im}; 32 amplitudes per pass
+        const int quarter = warp & 3;
+        const int g = 32 * quarter + lane;
+        const uint32_t lane_off = (uint32_t)(32 * quarter) << 16;
+        const uint64_t spG = P.spG[g];
+        for (uint64_t j = 0; j < J; j++) {
+            const int b = (int)(j & 1);
+            const bool ok = mbar_wait_or_abort(smem_addr(&bar_mma[b]), (uint32_t)((j >> 1) & 1), abort_flag);
+            if (named_bar_or(2, kPEpi, !ok || *abort_flag)) {
+                give_up();
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint64_t base = tile_base(P, blockIdx.x + j * gridDim.x);
+            float2 *dstg = a + (base + spG);
+#pragma unroll 1
+            for (int c0 = 0; c0 < 128; c0 += 32) {
+                uint32_t r[32];
+                tmem_ld32(tmem + lane_off + (uint32_t)b * 128u + (uint32_t)c0, r);
+                tmem_wait_ld();
+                const int l0 = c0 / 2;
+#pragma unroll
+                for (int i = 0; i < 16; i++)
+                    dstg[s_spL[l0 + i]] = make_float2(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1]));
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            mbar_arrive(smem_addr(&bar_accf[b]));
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");

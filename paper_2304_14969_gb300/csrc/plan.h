@@ -119,7 +119,6 @@ struct qsim_plan {
     std::vector<std::vector<uint64_t>> tc_pd_tw;
     std::vector<size_t> tc_off;
     std::vector<qs::TcPipeHost> tc_pipe;                       // pipelined kernel geometry (BF16x3, n >= 13)
-    int *d_err = nullptr;
     // device copies
     void *dmem = nullptr;
     size_t dbytes = 0;

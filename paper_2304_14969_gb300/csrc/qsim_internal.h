@@ -61,6 +61,11 @@ struct qsim_state {
     int device = 0;
     std::vector<int> l2p;    // logical qubit -> physical bit
     qs::Scratch red;
+    // error word of kernels that report asynchronously (tensor-core blocks:
+    // an MMA completion wait that gave up); device word + pinned host copy,
+    // allocated on first use, read at the next call that synchronises
+    int *d_err = nullptr;
+    int *h_err = nullptr;
     size_t amp_bytes() const { return (size_t)(dt == QSIM_C64 ? 8 : 16) << n; }
     uint64_t N() const { return (uint64_t)1 << n; }
 };
@@ -104,10 +109,12 @@ struct TcPipeArgs {
     uint16_t posG[128];      // in-stage element index of group g
     uint64_t spL[64];        // amplitude offset of block index l
     uint64_t spG[128];       // amplitude offset of group g
-    const int32_t *pd_off;   // deferred phases (as in TcSpec), NULL if none
-    const int32_t *pd_bit;
-    const uint64_t *pd_tw;
-    const uint64_t *gturn;   // [128][6] turns contributed by the group bits, NULL if none
+    int ntb;                 // tile-index bits (n - 13)
+    // deferred phases (NULL if none): exp(2 pi i T_b) of block bit b for a
+    // group is the product of a tile factor, from the turns tturn[b][i] of
+    // the tile-index bits i, and the group factor gfac[g][b]
+    const uint64_t *tturn;   // [6][24]
+    const float2 *gfac;      // [128][6]
 };
 struct TcPipeHost {
     TcPipeArgs args;
@@ -117,10 +124,19 @@ struct TcPipeHost {
     int freeq[7];
 };
 bool tc_pipe_eligible(int n, qsim_prec prec);
-qsim_status tc_pipe_prepare(int n, const TcSpec &ts, const uint64_t *gturn_dev, TcPipeHost &H);
-void tc_pipe_gturn(int n, const TcSpec &ts, const std::vector<int32_t> &off, const std::vector<int32_t> &pbit,
-                   const std::vector<uint64_t> &tw, std::vector<uint64_t> &out);
+qsim_status tc_pipe_prepare(int n, const TcSpec &ts, const void *pd_tables_dev, TcPipeHost &H);
+// Deferred-phase tables of a block (tturn then gfac, kTcPipeTableBytes).
+const size_t kTcPipeTableBytes = 6 * 24 * 8 + 128 * 6 * 8;
+void tc_pipe_tables(int n, const TcSpec &ts, const std::vector<int32_t> &off, const std::vector<int32_t> &pbit,
+                    const std::vector<uint64_t> &tw, std::vector<unsigned char> &out);
 cudaError_t tc_pipe_launch(qsim_state *s, const TcPipeHost &H, const unsigned char *dU, int *derr);
+
+// Asynchronous error word of a state (see qsim_state): ensure allocates it,
+// fetch enqueues its copy to the host (before a synchronisation), check
+// reports and clears it (after the synchronisation).
+qsim_status err_ensure(qsim_state *s);
+void err_fetch(qsim_state *s);
+qsim_status err_check(qsim_state *s);
 
 // ------------------------------------------------------ kernel launchers
 // (all stream-ordered, no sync; return cuda errors)

@@ -3,6 +3,7 @@
 // covers it, and the index tables the kernel uses. Plain C++ so that the
 // CPU tests can check it.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 
 #include "qsim_internal.h"
@@ -17,7 +18,7 @@ bool tc_pipe_eligible(int n, qsim_prec prec) { return prec == QSIM_PREC_BF16X3 &
 // dimension) plus the non-tile qubits above it, so a box is exactly the
 // tile's amplitudes with the tile base's bits as coordinates. Runs beyond
 // the fifth become extra boxes along dimension 4.
-qsim_status tc_pipe_prepare(int n, const TcSpec &ts, const uint64_t *gturn_dev, TcPipeHost &H)
+qsim_status tc_pipe_prepare(int n, const TcSpec &ts, const void *pd_tables_dev, TcPipeHost &H)
 {
     if (n < 13 || n > 36) return fail(QSIM_E_UNSUPPORTED, "pipelined tensor-core blocks need 13 <= n <= 36");
     uint64_t blk = 0;
@@ -98,10 +99,9 @@ qsim_status tc_pipe_prepare(int n, const TcSpec &ts, const uint64_t *gturn_dev, 
         A.posG[g] = (uint16_t)r;
         A.spG[g] = o;
     }
-    A.pd_off = ts.pd_off;
-    A.pd_bit = ts.pd_bit;
-    A.pd_tw = ts.pd_tw;
-    A.gturn = gturn_dev;
+    A.ntb = n - 13;
+    A.tturn = pd_tables_dev ? (const uint64_t *)pd_tables_dev : nullptr;
+    A.gfac = pd_tables_dev ? (const float2 *)((const unsigned char *)pd_tables_dev + 6 * 24 * 8) : nullptr;
     H.rank = 5;
     for (int d = 0; d < 5; d++) {
         H.gdim[d] = gdim[d];
@@ -113,28 +113,45 @@ qsim_status tc_pipe_prepare(int n, const TcSpec &ts, const uint64_t *gturn_dev, 
     return QSIM_OK;
 }
 
-// Host table of the deferred phases' group terms: gturn[g][b] = sum of the
-// turns of block bit b's partners that are group bits of g.
-void tc_pipe_gturn(int n, const TcSpec &ts, const std::vector<int32_t> &off, const std::vector<int32_t> &pbit,
-                   const std::vector<uint64_t> &tw, std::vector<uint64_t> &out)
+// Deferred-phase tables of a block: T_b(amplitude index) = sum of tw[e] over
+// the partners pbit[e] of block bit b whose bit is set; the partners are
+// outside the block, so each is either a tile-index bit or a group bit.
+// tturn[b][i] sums the partners at the i-th non-tile qubit; gfac[g][b] =
+// exp(2 pi i (sum of the partners among g's bits)), in double, rounded.
+void tc_pipe_tables(int n, const TcSpec &ts, const std::vector<int32_t> &off, const std::vector<int32_t> &pbit,
+                    const std::vector<uint64_t> &tw, std::vector<unsigned char> &out)
 {
     uint64_t blk = 0;
     for (int b = 0; b < 6; b++) blk |= bit(ts.q[b]);
     std::vector<int> freeq;
     for (int p = 0; p < n && (int)freeq.size() < 7; p++)
         if (!(blk & bit(p))) freeq.push_back(p);
-    out.assign(128 * 6, 0);
-    for (int g = 0; g < 128; g++) {
-        uint64_t o = 0;
-        for (int f = 0; f < 7; f++)
-            if ((g >> f) & 1) o |= bit(freeq[f]);
-        for (int b = 0; b < 6; b++) {
+    uint64_t tmask = blk;
+    for (int f : freeq) tmask |= bit(f);
+    std::vector<int> tbit;   // i-th tile-index bit -> qubit
+    for (int p = 0; p < n; p++)
+        if (!(tmask & bit(p))) tbit.push_back(p);
+    std::vector<uint64_t> tturn(6 * 24, 0);
+    std::vector<float> gfac(128 * 6 * 2, 0.f);
+    for (int b = 0; b < 6; b++) {
+        for (size_t i = 0; i < tbit.size(); i++)
+            for (int e = off[b]; e < off[b + 1]; e++)
+                if (pbit[e] == tbit[i]) tturn[b * 24 + i] += tw[e];
+        for (int g = 0; g < 128; g++) {
+            uint64_t o = 0;
+            for (int f = 0; f < 7; f++)
+                if ((g >> f) & 1) o |= bit(freeq[f]);
             uint64_t t = 0;
             for (int e = off[b]; e < off[b + 1]; e++)
                 if ((o >> pbit[e]) & 1) t += tw[e];
-            out[g * 6 + b] = t;
+            const double ang = 2.0 * 3.14159265358979323846 * ((double)t / 18446744073709551616.0);
+            gfac[(g * 6 + b) * 2] = (float)std::cos(ang);
+            gfac[(g * 6 + b) * 2 + 1] = (float)std::sin(ang);
         }
     }
+    out.resize(kTcPipeTableBytes);
+    memcpy(out.data(), tturn.data(), 6 * 24 * 8);
+    memcpy(out.data() + 6 * 24 * 8, gfac.data(), 128 * 6 * 8);
 }
 
 }  // namespace qs

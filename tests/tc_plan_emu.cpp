@@ -192,3 +192,20 @@ extern "C" int emu_tc_geometry(int n, const int *q6, int64_t *dims, int *tpos, i
     }
     return 0;
 }
+
+// Deferred-phase tables of the pipelined kernel for block qubits q6 and
+// partner lists (off[7], pbit, tw): out = tturn[6][24] (uint64) followed by
+// gfac[128][6] (float2).
+extern "C" int emu_tc_tables(int n, const int *q6, const int32_t *off, const int32_t *pbit, const uint64_t *tw,
+                             unsigned char *out)
+{
+    TcSpec ts;
+    memset(&ts, 0, sizeof ts);
+    for (int b = 0; b < 6; b++) ts.q[b] = q6[b];
+    std::vector<int32_t> o(off, off + 7), pb(pbit, pbit + off[6]);
+    std::vector<uint64_t> t(tw, tw + off[6]);
+    std::vector<unsigned char> blob;
+    tc_pipe_tables(n, ts, o, pb, t, blob);
+    memcpy(out, blob.data(), blob.size());
+    return (int)blob.size();
+}

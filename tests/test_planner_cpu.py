@@ -172,3 +172,42 @@ def test_tc_pipe_tile_geometry(emu, seed):
         pos = np.array([posL[l] | posG[g] for g in range(128) for l in range(64)])
         assert np.array_equal(np.sort(pos), np.arange(8192))
         assert np.array_equal(stage[pos], want)
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_tc_pipe_phase_tables(emu, seed):
+    """Deferred phases in the pipelined kernel: block bit b of the amplitude
+    with index x is multiplied by exp(2 pi i T_b(x)), T_b(x) = sum of the
+    turns of b's partners whose bit is set in x. The kernel forms it as
+    (tile factor from tturn[b][tile-index bits]) x gfac[g][b]; for random
+    partner lists and amplitudes that product must equal the direct sum."""
+    rng = np.random.default_rng(100 + seed)
+    n = int(rng.integers(13, 29))
+    q6 = [int(v) for v in rng.choice(n, 6, replace=False)]
+    outside = [p for p in range(n) if p not in q6]
+    off, pbit, tw = [0], [], []
+    for b in range(6):
+        k = int(rng.integers(0, min(12, len(outside)) + 1))
+        for p in rng.choice(outside, k, replace=False):
+            pbit.append(int(p))
+            tw.append(int(rng.integers(0, 2 ** 63)) * 2 + int(rng.integers(0, 2)))
+        off.append(len(pbit))
+    out = np.zeros(6 * 24 * 8 + 128 * 6 * 8, dtype=np.uint8)
+    rc = emu.emu_tc_tables(n, (C.c_int * 6)(*q6), (C.c_int32 * 7)(*off), (C.c_int32 * max(1, len(pbit)))(*pbit),
+                           (C.c_uint64 * max(1, len(tw)))(*tw), out.ctypes.data_as(C.c_void_p))
+    assert rc == out.size
+    tturn = out[:6 * 24 * 8].view(np.uint64).reshape(6, 24)
+    gfac = out[6 * 24 * 8:].view(np.float32).reshape(128, 6, 2)
+    free = [p for p in range(n) if p not in q6][:7]
+    tile = sorted(q6 + free)
+    tbits = [p for p in range(n) if p not in tile]
+    for _ in range(20):
+        t = int(rng.integers(0, 1 << (n - 13)))
+        gi = int(rng.integers(0, 128))
+        x = sum(1 << tbits[i] for i in range(n - 13) if (t >> i) & 1)
+        x |= sum(1 << free[f] for f in range(7) if (gi >> f) & 1)
+        for b in range(6):
+            direct = sum(tw[e] for e in range(off[b], off[b + 1]) if (x >> pbit[e]) & 1) % 2 ** 64
+            tt = sum(int(tturn[b, i]) for i in range(n - 13) if (t >> i) & 1) % 2 ** 64
+            f = np.exp(2j * np.pi * tt / 2 ** 64) * complex(gfac[gi, b, 0], gfac[gi, b, 1])
+            assert abs(f - np.exp(2j * np.pi * direct / 2 ** 64)) < 1e-6
