@@ -265,11 +265,29 @@ qsim_status tc_build(int n, int k, const int *phys, const cd *u, qsim_prec prec,
 {
     if (k > 6) return fail(QSIM_E_UNSUPPORTED, "tensor-core blocks take k <= 6 (M = 128)");
     if (n < 6) return fail(QSIM_E_UNSUPPORTED, "tensor-core blocks need n >= 6");
+    // block bits in ascending qubit order (u permuted to match): the
+    // block's low qubits are then its low index bits
     int q[6];
     uint64_t used = 0;
+    int order[6];
+    for (int b = 0; b < k; b++) order[b] = b;
+    std::sort(order, order + k, [&](int x, int y) { return phys[x] < phys[y]; });
     for (int b = 0; b < k; b++) {
-        q[b] = phys[b];
+        q[b] = phys[order[b]];
         used |= bit(phys[b]);
+    }
+    std::vector<cd> us((size_t)(1 << k) << k);
+    {
+        const int D = 1 << k;
+        auto old_index = [&](int r) {
+            int o = 0;
+            for (int j = 0; j < k; j++)
+                if ((r >> j) & 1) o |= 1 << order[j];
+            return o;
+        };
+        for (int r = 0; r < D; r++)
+            for (int c = 0; c < D; c++) us[(size_t)r * D + c] = u[(size_t)old_index(r) * D + old_index(c)];
+        u = us.data();
     }
     int kk = k;
     for (int p = n - 1; p >= 0 && kk < 6; p--)

@@ -228,6 +228,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
         const int g = 32 * quarter + lane;
         const uint32_t lane_off = (uint32_t)(32 * quarter) << 16;
         const uint32_t offG = 8u * P.posG[g];
+        const int rot = P.rot_bits ? (lane >> (4 - P.rot_bits)) & ((1 << P.rot_bits) - 1) : 0;
 
         for (uint64_t j = 0; j < J; j++) {
             const int s = (int)(j & 1), b = (int)(j & 1);
@@ -239,9 +240,27 @@ __global__ void __launch_bounds__(kPThreads, 1)
             }
             const unsigned char *stage = St + (size_t)s * kPStage + offG;
             float2 v[16];
+            // Block qubits among qubits 0..3 (block bits 0..rot_bits-1) would put
+            // the 16 lanes of a half-warp on one bank: each lane reads its
+            // amplitudes in an order XOR-rotated by its own lane bits, so every
+            // read instruction covers 16 distinct banks; v[] is put back in
+            // order below.
 #pragma unroll
-            for (int i = 0; i < 16; i++) v[i] = *(const float2 *)(stage + 8u * s_posL[16 * part + i]);
+            for (int i = 0; i < 16; i++) v[i] = *(const float2 *)(stage + 8u * s_posL[16 * part + (i ^ rot)]);
             mbar_arrive(smem_addr(&bar_sfree[s]));   // the stage may be reloaded
+#pragma unroll
+            for (int bb = 0; bb < 4; bb++) {
+                if (bb < P.rot_bits) {
+                    const bool sw = (rot >> bb) & 1;
+#pragma unroll
+                    for (int i = 0; i < 16; i++)
+                        if (!(i & (1 << bb))) {
+                            const float2 x = v[i], y = v[i | (1 << bb)];
+                            v[i] = sw ? y : x;
+                            v[i | (1 << bb)] = sw ? x : y;
+                        }
+                }
+            }
             if (has_pd) {
                 // factor of (g, l) = prod_b e_b(g)^(l_b), e_b(g) = E_b(tile) G_b(g);
                 // bits 4, 5 of l from part, 0..3 from i
@@ -331,9 +350,18 @@ __global__ void __launch_bounds__(kPThreads, 1)
                 tmem_ld32(tmem + lane_off + (uint32_t)b * 128u + (uint32_t)c0, r);
                 tmem_wait_ld();
                 const int l0 = c0 / 2;
+                if (P.vec2) {
+                    // amplitudes l, l + 1 adjacent: one 16-byte store per pair
 #pragma unroll
-                for (int i = 0; i < 16; i++)
-                    dstg[s_spL[l0 + i]] = make_float2(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1]));
+                    for (int i = 0; i < 16; i += 2)
+                        *(float4 *)(dstg + s_spL[l0 + i]) =
+                            make_float4(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1]),
+                                        __uint_as_float(r[2 * i + 2]), __uint_as_float(r[2 * i + 3]));
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 16; i++)
+                        dstg[s_spL[l0 + i]] = make_float2(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1]));
+                }
             }
             asm volatile("tcgen05.fence::before_thread_sync;");
             mbar_arrive(smem_addr(&bar_accf[b]));

@@ -1007,14 +1007,14 @@ qsim_status plan_build_tc(const qsim_circuit *cir, const qsim_run_opts *opts, co
         TcSpec ts;
         std::vector<unsigned char> A;
         QS_TRY(tc_build(n, (int)Q.size(), Q.data(), U.data(), (qsim_prec)opts->prec, A, ts));
-        // pre-diagonal partner lists per block bit (tc_build keeps Q's order)
+        // pre-diagonal partner lists per block bit, in tc_build's bit order
         std::vector<int32_t> off(7, 0), pb;
         std::vector<uint64_t> ptw;
         for (int b = 0; b < 6; b++) {
             off[b] = (int32_t)pb.size();
             if (b < (int)Q.size())
                 for (auto &x : pre)
-                    if (x.first == Q[b]) {
+                    if (x.first == ts.q[b]) {
                         pb.push_back(x.second.first);
                         ptw.push_back(to_turns(x.second.second));
                     }

@@ -110,6 +110,8 @@ struct TcPipeArgs {
     uint64_t spL[64];        // amplitude offset of block index l
     uint64_t spG[128];       // amplitude offset of group g
     int ntb;                 // tile-index bits (n - 13)
+    int rot_bits;            // block qubits among qubits 0..3 (= block index bits 0..rot_bits-1)
+    int vec2;                // qubit 0 is block bit 0: amplitudes l, l + 1 (l even) are adjacent
     // deferred phases (NULL if none): exp(2 pi i T_b) of block bit b for a
     // group is the product of a tile factor, from the turns tturn[b][i] of
     // the tile-index bits i, and the group factor gfac[g][b]

@@ -100,6 +100,13 @@ qsim_status tc_pipe_prepare(int n, const TcSpec &ts, const void *pd_tables_dev, 
         A.spG[g] = o;
     }
     A.ntb = n - 13;
+    // tile qubits 0..3 are the in-stage bits 0..3 (the tile holds qubits
+    // 0..3: each is a block qubit or one of the lowest outside ones)
+    A.rot_bits = 0;
+    for (int b = 0; b < 6; b++) A.rot_bits += ts.q[b] < 4;
+    for (int b = 0; b < A.rot_bits; b++)
+        if (ts.q[b] >= 4) return fail(QSIM_E_UNSUPPORTED, "tensor-core block bits not in ascending qubit order");
+    A.vec2 = ts.q[0] == 0;
     A.tturn = pd_tables_dev ? (const uint64_t *)pd_tables_dev : nullptr;
     A.gfac = pd_tables_dev ? (const float2 *)((const unsigned char *)pd_tables_dev + 6 * 24 * 8) : nullptr;
     H.rank = 5;

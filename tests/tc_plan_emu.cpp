@@ -160,7 +160,9 @@ extern "C" int emu_tc_run(const qsim_circuit *c, int prec, const int *start_l2p,
 // dims[0..4] lowest qubit, dims[5..9] coordinate bits, dims[10..14] box
 // extents, dims[15..19] global extents, dims[20..23] byte strides of
 // dimensions 1..4, dims[24] boxes per tile, dims[25..28] dimension-4
-// offsets of the boxes, dims[29] box bytes; tpos[13] tile qubits.
+// offsets of the boxes, dims[29] box bytes, dims[30] rotated low block bits,
+// dims[31] paired stores; tpos[13] tile qubits. q6 ascending (as tc_build
+// orders a block).
 extern "C" int emu_tc_geometry(int n, const int *q6, int64_t *dims, int *tpos, int *posL, int *posG, uint64_t *spL,
                                uint64_t *spG)
 {
@@ -181,6 +183,8 @@ extern "C" int emu_tc_geometry(int n, const int *q6, int64_t *dims, int *tpos, i
     dims[24] = A.nload;
     for (int v = 0; v < 4; v++) dims[25 + v] = A.xoff[v];
     dims[29] = A.box_bytes;
+    dims[30] = A.rot_bits;
+    dims[31] = A.vec2;
     for (int j = 0; j < 13; j++) tpos[j] = A.tpos[j];
     for (int l = 0; l < 64; l++) {
         posL[l] = A.posL[l];

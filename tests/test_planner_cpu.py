@@ -133,7 +133,8 @@ def test_tc_pipe_tile_geometry(emu, seed):
         q6 = [n - 1 - i for i in range(6)]
     else:
         q6 = [int(v) for v in rng.choice(n, 6, replace=False)]
-    dims = (C.c_int64 * 30)()
+    q6 = sorted(q6)                # tc_build orders block bits by qubit
+    dims = (C.c_int64 * 32)()
     tpos = (C.c_int * 13)()
     posL, posG = (C.c_int * 64)(), (C.c_int * 128)()
     spL, spG = (C.c_uint64 * 64)(), (C.c_uint64 * 128)()
@@ -172,6 +173,23 @@ def test_tc_pipe_tile_geometry(emu, seed):
         pos = np.array([posL[l] | posG[g] for g in range(128) for l in range(64)])
         assert np.array_equal(np.sort(pos), np.arange(8192))
         assert np.array_equal(stage[pos], want)
+    # converter reads: lane (group g = 32 quarter + lane) reads block index
+    # 16 part + (i ^ rot(lane)) at instruction i; each half-warp's 16 lanes
+    # must hit 16 distinct 8-byte slots of a 128-byte bank row
+    rot_bits, vec2 = d[30], d[31]
+    assert rot_bits == sum(q < 4 for q in q6) and vec2 == (q6[0] == 0)
+    for quarter in range(4):
+        for part in range(4):
+            for i in range(16):
+                for hw in range(2):
+                    slots = set()
+                    for lane in range(16 * hw, 16 * hw + 16):
+                        rot = (lane >> (4 - rot_bits)) & ((1 << rot_bits) - 1) if rot_bits else 0
+                        g, l = 32 * quarter + lane, 16 * part + (i ^ rot)
+                        slots.add((posG[g] | posL[l]) % 16)
+                    assert len(slots) == 16, (q6, quarter, part, i, hw)
+    if vec2:
+        assert all(spL[l + 1] == spL[l] + 1 for l in range(0, 64, 2))
 
 
 @pytest.mark.parametrize("seed", range(12))
