@@ -42,8 +42,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip the per-gate FP64, grid and CPU legs")
     ap.add_argument("--workload", default="qft27",
-                    help="qft27 (default, fused SIMT passes) or grid<n>_tc (n-qubit grid circuit on tensor-core "
-                         "blocks, BF16x3), used for small profiling captures")
+                    help="qft27 (default: the 27-qubit QFT on tensor-core blocks) or {qft,grid}<n>_{tc,simt} (one "
+                         "circuit on tensor-core blocks or fused SIMT passes; profiling workloads)")
     return ap.parse_args()
 
 
@@ -329,7 +329,8 @@ def time_plan(Q, C, plan, st, reps):
 
 
 def run_grid_tc(args):
-    """Grid circuit or QFT on tensor-core blocks (profiling workload)."""
+    """One grid circuit or QFT on tensor-core blocks or fused SIMT passes
+    (profiling workload)."""
     import ctypes as C
     import torch
     from paper_2304_14969_gb300 import build, qsim as Q
@@ -338,6 +339,8 @@ def run_grid_tc(args):
     Q.lib()
     fam = "qft" if args.workload.startswith("qft") else "grid"
     n = int(args.workload[len(fam):].split("_")[0])
+    simt = args.workload.endswith("_simt")
+    prec_kw = {} if simt else {"prec": Q.QSIM_PREC_BF16X3}
     if fam == "grid":
         rows, cols = W.grid_shape(n)
         g = W.grid_rcs_circuit(rows, cols, 10, seed=0, n=n)
@@ -347,9 +350,9 @@ def run_grid_tc(args):
     st = Q.State(n, Q.QSIM_C64)
     # plans for both qubit maps the state alternates between (a QFT with
     # relabelled swaps leaves the ket bit-reversed), so no step permutes
-    plans = [Q.Plan(circ, dtype=Q.QSIM_C64, prec=Q.QSIM_PREC_BF16X3, state=st)]
+    plans = [Q.Plan(circ, dtype=Q.QSIM_C64, state=st, **prec_kw)]
     plans[0].execute(st)
-    plans.append(Q.Plan(circ, dtype=Q.QSIM_C64, prec=Q.QSIM_PREC_BF16X3, state=st))
+    plans.append(Q.Plan(circ, dtype=Q.QSIM_C64, state=st, **prec_kw))
     k = 1
     for _ in range(args.warmup):
         plans[k % 2].execute(st)
@@ -372,8 +375,9 @@ def run_grid_tc(args):
                       "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                       "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                       "data": "synthetic",
-                      "config": {"workload": f"{fam}{n}_c64_tc_bf16x3", "n_qubits": n, "gates": len(g), "blocks": nb},
-                      "roofline": {"bound": "hbm", "kernel": "k_tc_pipe",
+                      "config": {"workload": f"{fam}{n}_c64_" + ("fused_simt" if simt else "tc_bf16x3"),
+                                 "n_qubits": n, "gates": len(g), "launches_per_step": nb},
+                      "roofline": {"bound": "hbm", "kernel": "k_fused_pass" if simt else "k_tc_pipe",
                                    "achieved": 2 * 8 * N / (ms / nb * 1e-3) / 1e9}}))
 
 

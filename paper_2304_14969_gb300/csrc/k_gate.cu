@@ -9,6 +9,7 @@
 // are moved as 16-byte vectors when the lowest qubit is untouched.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <cuda_runtime.h>
 
 #include "qsim_internal.h"
@@ -199,17 +200,58 @@ __global__ void k_scale(typename Vec2<R>::T *__restrict__ a, uint64_t N, R f)
 }
 
 // dst[perm(i)] = src[i] where bit q of i moves to bit new_of_old[q].
-struct PermSpec { int n; int to[40]; };
+// Qubit permutation (relabel materialised in memory), tiled: a tile is the
+// 2^s amplitudes spanned by S = qubits 0..4, the source qubits that move
+// to positions 0..4, and further low qubits up to s = min(n, 10). It is
+// read with consecutive threads on source qubits 0..4 and written with
+// consecutive threads on destination qubits 0..4 (both coalesced) through
+// a shared-memory tile whose index e (compressed over S) is stored at
+// e ^ ((e >> 5) & 31): conflict-free for reads, and for writes whenever
+// the lanes' source bits fold onto distinct low bits (e.g. bit reversal).
+struct PermTile {
+    int s;               // tile qubits
+    int nrest;           // other qubits
+    int rest[40];        // their source positions, ascending
+    int rest_to[40];     // their destination positions
+    uint64_t srcLo[32], srcHi[32];   // source offset of tile index e: low 5 / high bits of e
+    uint64_t dstLo[32], dstHi[32];   // destination offset of destination tile index f
+    uint16_t eLo[32], eHi[32];       // tile index e of destination tile index f
+};
 
 template <typename R>
-__global__ void k_permute(const typename Vec2<R>::T *__restrict__ src, typename Vec2<R>::T *__restrict__ dst,
-                          uint64_t N, PermSpec ps)
+__global__ void __launch_bounds__(256) k_permute(const typename Vec2<R>::T *__restrict__ src,
+                                                 typename Vec2<R>::T *__restrict__ dst, uint64_t ntiles,
+                                                 const __grid_constant__ PermTile P)
 {
-    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
-        uint64_t j = 0;
-        for (int q = 0; q < ps.n; q++) j |= ((i >> q) & 1ull) << ps.to[q];
-        dst[j] = src[i];
+    using V = typename Vec2<R>::T;
+    __shared__ V tile[1024];
+    __shared__ uint64_t sLo[32], sHi[32], dLo[32], dHi[32];
+    __shared__ uint16_t eLo[32], eHi[32];
+    if (threadIdx.x < 32) {
+        sLo[threadIdx.x] = P.srcLo[threadIdx.x];
+        sHi[threadIdx.x] = P.srcHi[threadIdx.x];
+        dLo[threadIdx.x] = P.dstLo[threadIdx.x];
+        dHi[threadIdx.x] = P.dstHi[threadIdx.x];
+        eLo[threadIdx.x] = P.eLo[threadIdx.x];
+        eHi[threadIdx.x] = P.eHi[threadIdx.x];
+    }
+    __syncthreads();
+    const uint32_t T = 1u << P.s;
+    for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        uint64_t sb = 0, db = 0;
+        for (int i = 0; i < P.nrest; i++)
+            if ((t >> i) & 1) {
+                sb |= 1ull << P.rest[i];
+                db |= 1ull << P.rest_to[i];
+            }
+        for (uint32_t e = threadIdx.x; e < T; e += blockDim.x)
+            tile[e ^ ((e >> 5) & 31)] = src[sb | sLo[e & 31] | sHi[e >> 5]];
+        __syncthreads();
+        for (uint32_t f = threadIdx.x; f < T; f += blockDim.x) {
+            const uint32_t e = eLo[f & 31] | eHi[f >> 5];
+            dst[db | dLo[f & 31] | dHi[f >> 5]] = tile[e ^ ((e >> 5) & 31)];
+        }
+        __syncthreads();
     }
 }
 
@@ -326,15 +368,66 @@ cudaError_t launch_scale(void *amps, qsim_dtype dt, uint64_t N, double f, cudaSt
 cudaError_t launch_permute(const void *src, void *dst, qsim_dtype dt, int n, const int *new_of_old,
                            cudaStream_t st)
 {
-    PermSpec ps;
-    ps.n = n;
-    for (int q = 0; q < n; q++) ps.to[q] = new_of_old[q];
-    uint64_t N = 1ull << n;
+    // S: qubits 0..4, the source qubits moving to 0..4, then low qubits up to s
+    std::vector<int> S;
+    auto add = [&](int q) {
+        if (q < n && std::find(S.begin(), S.end(), q) == S.end()) S.push_back(q);
+    };
+    for (int q = 0; q < std::min(n, 5); q++) add(q);
+    for (int q = 0; q < n; q++)
+        if (new_of_old[q] < 5) add(q);
+    const int s = std::min(n, 10);
+    for (int q = 0; q < n && (int)S.size() < s; q++) add(q);
+    if ((int)S.size() > 10) return cudaErrorInvalidValue;
+    std::sort(S.begin(), S.end());
+    PermTile P;
+    memset(&P, 0, sizeof P);
+    P.s = (int)S.size();
+    for (int q = 0; q < n; q++)
+        if (std::find(S.begin(), S.end(), q) == S.end()) {
+            P.rest[P.nrest] = q;
+            P.rest_to[P.nrest++] = new_of_old[q];
+        }
+    // destination tile qubits, ascending; f indexes them
+    std::vector<int> D;
+    for (int q : S) D.push_back(new_of_old[q]);
+    std::sort(D.begin(), D.end());
+    auto src_off = [&](uint32_t e) {
+        uint64_t o = 0;
+        for (int j = 0; j < P.s; j++)
+            if ((e >> j) & 1) o |= 1ull << S[j];
+        return o;
+    };
+    auto dst_off = [&](uint32_t f) {
+        uint64_t o = 0;
+        for (int j = 0; j < P.s; j++)
+            if ((f >> j) & 1) o |= 1ull << D[j];
+        return o;
+    };
+    auto e_of_f = [&](uint32_t f) {
+        uint32_t e = 0;
+        for (int j = 0; j < P.s; j++)
+            if ((f >> j) & 1) {
+                // destination qubit D[j] holds source qubit S[i] with new_of_old[S[i]] == D[j]
+                for (int i = 0; i < P.s; i++)
+                    if (new_of_old[S[i]] == D[j]) e |= 1u << i;
+            }
+        return e;
+    };
+    for (uint32_t x = 0; x < 32; x++) {
+        P.srcLo[x] = src_off(x);
+        P.srcHi[x] = src_off(x << 5);
+        P.dstLo[x] = dst_off(x);
+        P.dstHi[x] = dst_off(x << 5);
+        P.eLo[x] = (uint16_t)e_of_f(x);
+        P.eHi[x] = (uint16_t)e_of_f(x << 5);
+    }
+    const uint64_t ntiles = 1ull << (n - P.s);
+    const int grid = (int)std::min<uint64_t>(ntiles, (uint64_t)num_sms() * 8);
     if (dt == QSIM_C64)
-        k_permute<float><<<default_grid(N, kThreads), kThreads, 0, st>>>((const float2 *)src, (float2 *)dst, N, ps);
+        k_permute<float><<<grid, 256, 0, st>>>((const float2 *)src, (float2 *)dst, ntiles, P);
     else
-        k_permute<double><<<default_grid(N, kThreads), kThreads, 0, st>>>((const double2 *)src, (double2 *)dst, N,
-                                                                         ps);
+        k_permute<double><<<grid, 256, 0, st>>>((const double2 *)src, (double2 *)dst, ntiles, P);
     return cudaGetLastError();
 }
 

@@ -46,13 +46,24 @@ __device__ __forceinline__ void block_write(double (&acc)[M], double *__restrict
 }
 
 template <int M>
-__global__ void k_red_final(const double *__restrict__ partial, int rows, double *__restrict__ out)
+__global__ void __launch_bounds__(256) k_red_final(const double *__restrict__ partial, int rows,
+                                                   double *__restrict__ out)
 {
-    // one CTA; thread m sums column m in FP64 (rows is small)
-    for (int m = threadIdx.x; m < M; m += blockDim.x) {
-        double s = 0;
-        for (int r = 0; r < rows; r++) s += partial[(size_t)r * M + m];
-        out[m] = s;
+    // one CTA of 256 threads; per column m each thread adds every 256th row,
+    // then a warp-shuffle and shared-memory tree adds the 256 sums (FP64)
+    __shared__ double sh[8];
+    for (int m = 0; m < M; m++) {
+        double v = 0;
+        for (int r = threadIdx.x; r < rows; r += blockDim.x) v += partial[(size_t)r * M + m];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += sh[w];
+            out[m] = t;
+        }
+        __syncthreads();
     }
 }
 
@@ -61,18 +72,40 @@ template <typename R>
 __global__ void k_red_norm(const typename V2T<R>::T *__restrict__ a, uint64_t N, double *partial)
 {
     double acc[1] = {0};
-    uint64_t stride = (uint64_t)gridDim.x * blockDim.x * 8;
-    for (uint64_t base = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) * 8; base < N; base += stride) {
-        R run = 0;
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (uint64_t)gridDim.x * blockDim.x;
+    if constexpr (sizeof(R) == 4) {
+        // 16-byte loads, consecutive lanes on consecutive amplitude pairs;
+        // runs of 8 terms in FP32 (four loads in flight per thread)
+        const float4 *a4 = (const float4 *)a;
+        const uint64_t N4 = N / 2;
+        uint64_t i = tid;
+        for (; i + 3 * nt < N4; i += 4 * nt) {
+            float4 v[4];
 #pragma unroll
-        for (int j = 0; j < 8; j++) {
-            if (base + j < N) {
-                auto v = a[base + j];
-                run = fma(v.x, v.x, run);
-                run = fma(v.y, v.y, run);
+            for (int j = 0; j < 4; j++) v[j] = a4[i + j * nt];
+            float run = 0;
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                run = fmaf(v[j].x, v[j].x, run);
+                run = fmaf(v[j].y, v[j].y, run);
+                run = fmaf(v[j].z, v[j].z, run);
+                run = fmaf(v[j].w, v[j].w, run);
             }
+            acc[0] += (double)run;
         }
-        acc[0] += (double)run;
+        for (; i < N4; i += nt) {
+            const float4 v = a4[i];
+            acc[0] += (double)(v.x * v.x + v.y * v.y + v.z * v.z + v.w * v.w);
+        }
+        if ((N & 1) && tid == 0) {
+            const auto v = a[N - 1];
+            acc[0] += (double)v.x * v.x + (double)v.y * v.y;
+        }
+    } else {
+        for (uint64_t i = tid; i < N; i += nt) {
+            const auto v = a[i];
+            acc[0] += v.x * v.x + v.y * v.y;
+        }
     }
     block_write<1>(acc, partial);
 }
@@ -287,7 +320,7 @@ template <int M>
 static qsim_status finish(qsim_state *s, int rows)
 {
     double *dout = s->red.d + (size_t)kMaxRedBlocks * 64;
-    k_red_final<M><<<1, 64, 0, s->stream>>>(s->red.d, rows, dout);
+    k_red_final<M><<<1, 256, 0, s->stream>>>(s->red.d, rows, dout);
     QS_CUDA(cudaGetLastError());
     QS_CUDA(cudaMemcpyAsync(s->red.h, dout, M * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
     err_fetch(s);
@@ -415,7 +448,7 @@ qsim_status bloch_sums_device(const void *amps, qsim_dtype dt, int n, cudaStream
             k_red_bloch_tile<double><<<blocks, kRedThreads, smem, stream>>>((const double2 *)amps, ts, sc.d);
         QS_CUDA(cudaGetLastError());
         double *comb = sc.d + (size_t)kMaxRedBlocks * 64;
-        k_red_final<kTileRow><<<1, 64, 0, stream>>>(sc.d, blocks, comb);
+        k_red_final<kTileRow><<<1, 256, 0, stream>>>(sc.d, blocks, comb);
         k_bloch_scatter<<<1, 32, 0, stream>>>(comb, ts, np == 0 ? 0 : first_new, d_out);
         QS_CUDA(cudaGetLastError());
         np++;

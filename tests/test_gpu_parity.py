@@ -260,3 +260,29 @@ def test_edge_cases_and_errors(Q):
     assert abs(w.prob1(0) - 1.0) < 1e-7 and abs(w.prob1(1)) < 1e-7
     w.close()
     del t
+
+
+@pytest.mark.parametrize("dt", [0, 1])
+@pytest.mark.parametrize("n", [1, 3, 5, 7, 11, 16, 21])
+def test_relabel_download_is_exact_permutation(Q, dt, n):
+    """SWAPs applied as qubit relabels (Table I) leave the amplitudes in
+    place; downloading in logical order moves them with the tiled permute.
+    No arithmetic happens, so the result equals the oracle's SWAP circuit
+    bit for bit (also a full bit reversal)."""
+    rng = np.random.default_rng(100 + n)
+    x = W.gaussian_state(n, n)
+    x = x.astype(np.complex64 if dt == 0 else np.complex128).astype(np.complex128)
+    for case in range(2):
+        if n < 2:
+            g = []
+        elif case == 0:
+            g = [W.Gate("swap", (q, n - 1 - q)) for q in range(n // 2)]
+        else:
+            g = [W.Gate("swap", tuple(int(v) for v in rng.choice(n, 2, replace=False))) for _ in range(3 * n)]
+        ref = oracle.apply_circuit(x, g)
+        st = Q.State(n, dt)
+        st.upload(x)
+        st.run(Q.Circuit(n, g), mode=0, relabel=1)
+        y = st.download().astype(np.complex128)
+        st.close()
+        assert np.array_equal(y, ref)
