@@ -435,6 +435,40 @@ def extra_legs(Q, W, C, torch, circ, x, n, ng):
     out["qft27_c64_fused_simt"] = {"updates_per_s": ng * N / (ms * 1e-3), "ms": ms, "passes": npp,
                                    "kernel": "k_fused_pass", "hbm_gbs_per_pass": 2 * 8 * N / (ms / npp * 1e-3) / 1e9}
     ssim.close()
+    # larger QFTs on tensor-core blocks (complex64, 8 GiB and 64 GiB kets,
+    # basis-state input prepared on the device)
+    for nn in (30, 33):
+        try:
+            cc = Q.Circuit(nn, W.qft_circuit(nn))
+            sb = Q.State(nn, Q.QSIM_C64)
+            Q.qsim_set_basis(sb.h, 1)
+            bps = [Q.Plan(cc, dtype=Q.QSIM_C64, prec=Q.QSIM_PREC_BF16X3, state=sb)]
+            bps[0].execute(sb)
+            bps.append(Q.Plan(cc, dtype=Q.QSIM_C64, prec=Q.QSIM_PREC_BF16X3, state=sb))
+            bps[1].execute(sb)
+            reps = 6 if nn == 30 else 2
+            a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            Q.qsim_synchronize(sb.h)
+            torch.cuda.synchronize()
+            a.record()
+            for r in range(reps):
+                bps[r % 2].execute(sb)
+            z.record()
+            Q.qsim_synchronize(sb.h)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(z) / reps
+            nb_ = bps[0].info()["passes"]
+            nrm = C.c_double()
+            Q.qsim_norm(sb.h, C.byref(nrm))
+            ngg = len(cc.gates)
+            out[f"qft{nn}_c64_tc_bf16x3"] = {
+                "updates_per_s": ngg * (1 << nn) / (ms * 1e-3), "ms": ms, "blocks": nb_, "kernel": "k_tc_pipe",
+                "hbm_gbs_per_block": 2 * 8 * (1 << nn) / (ms / nb_ * 1e-3) / 1e9,
+                "ket_gib": 8 * (1 << nn) / 2 ** 30, "norm": nrm.value}
+            sb.close()
+            del bps
+        except Exception as e:   # e.g. not enough device memory on a smaller part
+            out[f"qft{nn}_c64_tc_bf16x3"] = {"error": str(e)[:200]}
     # the same QFT on tensor-core blocks (deferred phases as per-group
     # pre-diagonals), agreement with the fused SIMT result
     peaks = {}
@@ -533,8 +567,15 @@ def extra_legs(Q, W, C, torch, circ, x, n, ng):
     out["grid30_speedup_vs_per_gate_fp64"] = pg * 1e3 / best
     s128.close()
     out["batch512"] = batch_leg(Q, W, C)
-    out["approx54_grid"] = approx_leg(Q, W, W.grid_rcs_circuit(6, 9, 7, seed=0))
-    out["approx54_paper_family"] = approx_leg(Q, W, W.paper_random_circuit(6, 9, 7, seed=0))
+    out["approx54_grid"] = approx_leg(Q, W, W.grid_rcs_circuit(6, 9, 7, seed=0), budget_gib=80.0)
+    pf = W.paper_random_circuit(6, 9, 7, seed=0)
+    out["approx54_paper_family"] = approx_leg(Q, W, pf, budget_gib=80.0)
+    out["approx54_paper_family_full_hbm"] = approx_leg(Q, W, pf, budget_gib=240.0, p_start=0.45, time_cap_s=60.0)
+    # the same sweep with the learned proposal schedule (MLP trained here on
+    # exhaustive-mode traces of 20-qubit circuits of the same family)
+    h = train_proposal_mlp(Q, W, C)
+    out["approx54_paper_family_mlp"] = approx_leg(Q, W, pf, budget_gib=80.0, mlp=h)
+    Q.qsim_mlp_destroy(h)
     return out
 
 
@@ -578,15 +619,20 @@ def batch_leg(Q, W, C):
             "tuned_tiles": {str(k): v for k, v in sorted(tuned.items())}}
 
 
-def approx_leg(Q, W, g, budget_gib=64.0, time_cap_s=40.0):
-    """The paper's Fig. 3 protocol on a 54-qubit, 7-layer circuit: p from 1
-    downward in steps of 0.025 until the memory budget is exceeded (or one run
-    exceeds the time cap); F model of the last completed run."""
+def approx_leg(Q, W, g, budget_gib=80.0, time_cap_s=40.0, p_start=1.0, mlp=None):
+    """The paper's Fig. 3 protocol on a 54-qubit, 7-layer circuit: p from
+    p_start downward in steps of 0.025 until the memory budget is exceeded
+    (or one run exceeds the time cap); F model of the last completed run.
+    With mlp, the learned proposal schedule (top 4; exhaustive every 8
+    entangling gates and on subsystems of 20 qubits or more) replaces the
+    exhaustive checks."""
     runs = []
-    p = 1.0
+    p = p_start
+    kw = {} if mlp is None else {"schedule": Q.QSIM_SCHED_MLP, "mlp": mlp, "top_m": 4, "fallback_every": 8,
+                                 "exhaustive_from": 20}
     while p > -1e-9:
         try:
-            r, _, _, _ = Q.approx_run(54, g, round(p, 3), budget=budget_gib * 2 ** 30)
+            r, _, _, _ = Q.approx_run(54, g, round(p, 3), budget=budget_gib * 2 ** 30, **kw)
         except Q.QsimError as e:
             runs.append({"p": round(p, 3), "status": "budget" if e.status == 5 else str(e)})
             break
@@ -597,8 +643,33 @@ def approx_leg(Q, W, g, budget_gib=64.0, time_cap_s=40.0):
             break
         p -= 0.025
     done = [x for x in runs if "F" in x]
-    return {"qubits": 54, "layers": 7, "budget_gib": budget_gib, "min_p": done[-1]["p"] if done else None,
-            "F_at_min_p": done[-1]["F"] if done else None, "runs": runs}
+    return {"qubits": 54, "layers": 7, "budget_gib": budget_gib,
+            "schedule": "exhaustive" if mlp is None else "mlp top-4; exhaustive every 8 gates and from 20 qubits",
+            "min_p": done[-1]["p"] if done else None, "F_at_min_p": done[-1]["F"] if done else None,
+            "seconds_total": sum(x["seconds"] for x in done),
+            "bloch_passes_total": sum(x["bloch_passes"] for x in done), "runs": runs}
+
+
+def train_proposal_mlp(Q, W, C):
+    """Proposal MLP (12 -> 64 -> 64 -> 1) trained on the GPU on traces of the
+    exhaustive approximate mode: 4x5 paper-family circuits (U3 + C/A Pauli),
+    7 layers, p from 0.3 to 0.7."""
+    X, Y = [], []
+    for seed in range(6):
+        g = W.paper_random_circuit(4, 5, 7, seed=200 + seed)
+        for p in (0.3, 0.35, 0.4, 0.45, 0.5, 0.55, 0.6, 0.65, 0.7):
+            _, _, (f, l), _ = Q.approx_run(20, g, p, trace_cap=20000)
+            X.append(f)
+            Y.append(l)
+    X = np.ascontiguousarray(np.concatenate(X), dtype=np.float32)
+    Y = np.ascontiguousarray(np.concatenate(Y), dtype=np.float32)
+    h = C.c_void_p()
+    Q.qsim_mlp_create(12, 64, 7, C.byref(h))
+    loss = C.c_float()
+    fp = lambda a: a.ctypes.data_as(C.POINTER(C.c_float))
+    for _ in range(400):
+        Q.qsim_mlp_train_step(h, fp(X), fp(Y), len(X), C.c_float(3e-3), C.byref(loss))
+    return h
 
 
 if __name__ == "__main__":

@@ -154,8 +154,20 @@ qsim_status qsim_qubit_map(const qsim_state *s, int32_t *l2p);
  * read+write pass per permutation cycle group; no-op if already identity). */
 qsim_status qsim_materialize(qsim_state *s);
 
-/* Waits for all work queued on the state's stream. */
+/* Waits for all work queued on the state's stream. Kernels that report
+ * errors asynchronously (a bounded wait inside a tensor-core block that
+ * gave up) are reported here, and by every other call that synchronises
+ * the stream (reductions, downloads), as QSIM_E_TIMEOUT; the report clears
+ * the error and the state stays usable (its amplitudes are then invalid). */
 qsim_status qsim_synchronize(qsim_state *s);
+
+/* Self-test of that failure path (the paper has no counterpart): queues on
+ * s's stream one CTA that waits on an mbarrier no thread ever arrives at,
+ * with the bounded wait the tensor-core kernels use but a limit of limit_ns
+ * nanoseconds of device time (1e3 .. 1e10). The wait gives up and sets s's
+ * asynchronous error word; nothing else is touched (s's amplitudes stay
+ * valid). Returns QSIM_E_INVAL for a limit outside the range. */
+qsim_status qsim_selftest_wait_timeout(qsim_state *s, int64_t limit_ns);
 
 /* --------------------------------------------------- per-gate path */
 
@@ -283,6 +295,9 @@ typedef struct {
     int32_t top_m;              /* MLP schedule: candidates per gate */
     int32_t fallback_every;     /* MLP schedule: exhaustive check every this many
                                    two-qubit gates (0: never) */
+    int32_t exhaustive_from;    /* MLP schedule: a subsystem of at least this many
+                                   qubits is checked exhaustively (memory is what a
+                                   missed rounding costs; 0: never) */
     const qsim_mlp *mlp;        /* MLP schedule */
     const int32_t *force;       /* forced schedule: nforce (gate, qubit) pairs, host */
     int32_t nforce;

@@ -427,7 +427,8 @@ extern "C" qsim_status qsim_approx_run(const qsim_circuit *c, double p, const qs
             std::sort(cand.begin(), cand.end());
         }
         if (o.schedule == QSIM_SCHED_MLP && cand.size() >= 2 &&
-            !(o.fallback_every > 0 && n_ent % o.fallback_every == 0)) {
+            !(o.fallback_every > 0 && n_ent % o.fallback_every == 0) &&
+            !(o.exhaustive_from > 0 && (int)cand.size() >= o.exhaustive_from)) {
             // score every qubit of the subsystem, keep the top_m predicted
             // to round (logit > 0), check them in ascending qubit order
             int rows = (int)std::min<size_t>(cand.size(), 64);

@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(kBatchThreads, 2)
     k_batch(float2 *__restrict__ arena, const FPassDev *__restrict__ passes, const uint64_t *__restrict__ amp_off,
             const BatchItem *__restrict__ items, int nitems, unsigned *__restrict__ head, unsigned *done,
             const unsigned *__restrict__ need, unsigned long long *t0, unsigned long long *t1, int *err,
-            long long spin_limit, int max_lin16, int stage_off)
+            long long wait_limit_ns, int max_lin16, int stage_off)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ int s_item, s_bad;
@@ -75,9 +75,9 @@ __global__ void __launch_bounds__(kBatchThreads, 2)
             if (!bad && it < nitems) {
                 BatchItem b = items[it];
                 if (b.prev >= 0) {
-                    long long spins = 0;
+                    const unsigned long long w0 = gtimer();
                     while (*(volatile unsigned *)&done[b.prev] < need[b.prev]) {
-                        if (++spins > spin_limit || *(volatile int *)err) {
+                        if (gtimer() - w0 > (unsigned long long)wait_limit_ns || *(volatile int *)err) {
                             atomicExch(err, 1);
                             bad = 1;
                             break;
@@ -215,10 +215,10 @@ static qsim_status batch_launch(qsim_batch *b)
     QS_CUDA(cudaMemsetAsync(b->dts, 0xff, sizeof(unsigned long long) * b->count, b->st));
     QS_CUDA(cudaMemsetAsync(b->dts + b->count, 0, sizeof(unsigned long long) * b->count, b->st));
     QS_CUDA(cudaMemsetAsync(b->derr, 0, sizeof(int), b->st));
-    long long spin_limit = 20000000;   // ~2 s of 100 ns sleeps
+    const long long wait_limit_ns = 2000000000;   // 2 s of device time per wait
     k_batch<<<b->grid, kBatchThreads, b->smem, b->st>>>(b->arena, b->d_passes, b->d_off, b->d_items, b->nitems,
                                                        b->dcnt, b->dcnt + 1, b->d_need, b->dts, b->dts + b->count,
-                                                       b->derr, spin_limit, 0, b->stage_off);
+                                                       b->derr, wait_limit_ns, 0, b->stage_off);
     QS_CUDA(cudaGetLastError());
     return QSIM_OK;
 }

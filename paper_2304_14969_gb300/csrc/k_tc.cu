@@ -401,4 +401,32 @@ qsim_status apply_fused_tc(qsim_state *s, int k, const int *phys, const cd *u, q
     return QSIM_OK;
 }
 
+// One CTA waits on an mbarrier that no thread arrives at (its phase 0 never
+// completes), through the same bounded wait as the block kernels; when the
+// wait gives up it sets the error word.
+__global__ void k_wait_selftest(int *err, unsigned long long limit_ns)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(smem_addr(&bar), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !mbar_wait(smem_addr(&bar), 0, limit_ns)) atomicExch(err, 1);
+}
+
 }  // namespace qs
+
+using namespace qs;
+
+extern "C" qsim_status qsim_selftest_wait_timeout(qsim_state *s, int64_t limit_ns)
+{
+    clear_error();
+    if (!s) return fail(QSIM_E_INVAL, "NULL state");
+    if (limit_ns < 1000 || limit_ns > 10000000000ll)
+        return fail(QSIM_E_INVAL, "limit_ns=%lld outside [1e3, 1e10]", (long long)limit_ns);
+    QS_TRY(err_ensure(s));
+    k_wait_selftest<<<1, 32, 0, s->stream>>>(s->d_err, (unsigned long long)limit_ns);
+    QS_CUDA(cudaGetLastError());
+    return QSIM_OK;
+}

@@ -10,7 +10,17 @@
 namespace qs {
 
 static const int kTcRows = 128;   // M = K
-static const long long kTcSpin = 1ll << 26;
+// Waits give up after this much device time (%globaltimer, ns): long
+// enough for any legitimate wait in these kernels, short enough to keep
+// the GPU responsive and report an error instead.
+static const unsigned long long kTcWaitNs = 4000000000ull;
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -56,18 +66,27 @@ __device__ __forceinline__ void mma_issue_tmem_a(uint32_t tmem_d, uint32_t tmem_
                  "r"(tmem_a), "l"(bdesc), "r"(idesc), "r"(accum));
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity)
+__device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t parity)
 {
-    for (long long it = 0; it < kTcSpin; it++) {
-        uint32_t done;
-        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                     "selp.b32 %0, 1, 0, p;\n\t}\n"
-                     : "=r"(done)
-                     : "r"(mbar), "r"(parity)
-                     : "memory");
-        if (done) return true;
+    uint32_t done;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.b32 %0, 1, 0, p;\n\t}\n"
+                 : "=r"(done)
+                 : "r"(mbar), "r"(parity)
+                 : "memory");
+    return done != 0;
+}
+
+// Waits for the phase with the given parity to complete; gives up (false)
+// after limit_ns of device time.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, unsigned long long limit_ns = kTcWaitNs)
+{
+    if (mbar_try_wait(mbar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+        if (mbar_try_wait(mbar, parity)) return true;
+        if (global_ns() - t0 > limit_ns) return false;
     }
-    return false;
 }
 
 __device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count)
@@ -88,19 +107,15 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t mbar, uint32_t by
 }
 
 // Bounded wait that also gives up early once *abort is set by another role.
-__device__ __forceinline__ bool mbar_wait_or_abort(uint32_t mbar, uint32_t parity, const volatile int *abort)
+__device__ __forceinline__ bool mbar_wait_or_abort(uint32_t mbar, uint32_t parity, const volatile int *abort,
+                                                   unsigned long long limit_ns = kTcWaitNs)
 {
-    for (long long it = 0; it < kTcSpin; it++) {
-        uint32_t done;
-        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                     "selp.b32 %0, 1, 0, p;\n\t}\n"
-                     : "=r"(done)
-                     : "r"(mbar), "r"(parity)
-                     : "memory");
-        if (done) return true;
-        if ((it & 255) == 255 && *abort) return false;
+    if (mbar_try_wait(mbar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+        if (mbar_try_wait(mbar, parity)) return true;
+        if (*abort || global_ns() - t0 > limit_ns) return false;
     }
-    return false;
 }
 
 // 5-D tiled TMA load of one box into shared memory, completion counted in

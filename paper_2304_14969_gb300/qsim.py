@@ -63,7 +63,7 @@ class qsim_decision(C.Structure):
 class qsim_approx_opts(C.Structure):
     _fields_ = [("budget_bytes", C.c_double), ("tau", C.c_double), ("dtype", C.c_int32),
                 ("schedule", C.c_int32), ("top_m", C.c_int32), ("fallback_every", C.c_int32),
-                ("mlp", C.c_void_p), ("force", C.POINTER(C.c_int32)), ("nforce", C.c_int32),
+                ("exhaustive_from", C.c_int32), ("mlp", C.c_void_p), ("force", C.POINTER(C.c_int32)), ("nforce", C.c_int32),
                 ("log_cap", C.c_int32), ("log", C.POINTER(qsim_decision)), ("state_out", C.c_void_p),
                 ("trace_features", C.POINTER(C.c_float)), ("trace_labels", C.POINTER(C.c_int32)),
                 ("trace_cap", C.c_int64), ("stream", C.c_void_p)]
@@ -100,6 +100,7 @@ def _sig(L):
         "qsim_qubit_map": [P, P],
         "qsim_materialize": [P],
         "qsim_synchronize": [P],
+        "qsim_selftest_wait_timeout": [P, C.c_int64],
         "qsim_apply_gate": [P, P, i32, P, i32, u64],
         "qsim_apply_cphase": [P, i32, i32, f64],
         "qsim_apply_2q": [P, P, i32, i32],
@@ -177,7 +178,8 @@ def _wrap(name):
 
 
 for _n in ["qsim_create", "qsim_wrap", "qsim_destroy", "qsim_set_basis", "qsim_upload", "qsim_download",
-           "qsim_device_ptr", "qsim_qubit_map", "qsim_materialize", "qsim_synchronize", "qsim_apply_gate",
+           "qsim_device_ptr", "qsim_qubit_map", "qsim_materialize", "qsim_synchronize", "qsim_selftest_wait_timeout",
+           "qsim_apply_gate",
            "qsim_apply_cphase", "qsim_apply_2q", "qsim_apply_swap", "qsim_apply_fused", "qsim_run_circuit",
            "qsim_plan_create", "qsim_plan_create_for_state", "qsim_plan_destroy", "qsim_plan_info", "qsim_plan_execute", "qsim_norm",
            "qsim_renormalize", "qsim_measure_prob", "qsim_probs", "qsim_inner_product",
@@ -358,7 +360,7 @@ def u2(m) -> np.ndarray:
 
 
 def approx_run(n, gates, p, dtype=QSIM_C64, tau=0.0, budget=0.0, schedule=QSIM_SCHED_EXHAUSTIVE, mlp=None,
-               top_m=4, fallback_every=0, want_state=False, trace_cap=0, log_cap=0):
+               top_m=4, fallback_every=0, exhaustive_from=0, want_state=False, trace_cap=0, log_cap=0):
     """qsim_approx_run on a list of workloads.Gate; returns (result, state or
     None, (features, labels) or None, decisions list)."""
     circ = Circuit(n, gates)
@@ -369,6 +371,7 @@ def approx_run(n, gates, p, dtype=QSIM_C64, tau=0.0, budget=0.0, schedule=QSIM_S
     o.schedule = schedule
     o.top_m = top_m
     o.fallback_every = fallback_every
+    o.exhaustive_from = exhaustive_from
     if mlp is not None:
         o.mlp = mlp
     state = None
