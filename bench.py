@@ -567,6 +567,7 @@ def extra_legs(Q, W, C, torch, circ, x, n, ng):
     out["grid30_speedup_vs_per_gate_fp64"] = pg * 1e3 / best
     s128.close()
     out["batch512"] = batch_leg(Q, W, C)
+    out["batch512_tc"] = batch_leg(Q, W, C, path=2)
     out["approx54_grid"] = approx_leg(Q, W, W.grid_rcs_circuit(6, 9, 7, seed=0), budget_gib=80.0)
     pf = W.paper_random_circuit(6, 9, 7, seed=0)
     out["approx54_paper_family"] = approx_leg(Q, W, pf, budget_gib=80.0)
@@ -579,10 +580,13 @@ def extra_legs(Q, W, C, torch, circ, x, n, ng):
     return out
 
 
-def batch_leg(Q, W, C):
+def batch_leg(Q, W, C, path=0):
     """512 seeded circuits (n ~ U{10..24}, depth ~ U{4..20}, QFT / grid 50/50)
-    in one persistent launch replayed from a CUDA graph; tile widths from the
-    autotuner (one representative circuit per qubit count)."""
+    replayed from a CUDA graph: a persistent launch for the circuits on fused
+    SIMT passes, grouped launches per block round for those on tensor-core
+    blocks. path 0: per qubit count the autotuner's choice (tile width, or
+    tensor cores; one representative circuit timed alone per qubit count);
+    path 2: tensor cores for every circuit with n >= 13."""
     import tempfile
     specs = W.batch_circuits(512, seed=0)
     circs = [Q.Circuit(sp["n"], sp["gates"]) for sp in specs]
@@ -595,9 +599,9 @@ def batch_leg(Q, W, C):
             best = Q.qsim_run_opts()
             sec = C.c_double()
             Q.qsim_autotune(c.ptr(), Q.QSIM_C64, cache.encode(), C.byref(best), C.byref(sec))
-            tuned[sp["n"]] = best.tile_qubits
+            tuned[sp["n"]] = "tc" if best.prec == Q.QSIM_PREC_BF16X3 else best.tile_qubits
         arr = (C.POINTER(Q.qsim_circuit) * len(circs))(*[C.pointer(c.c) for c in circs])
-        o = Q.qsim_batch_opts(use_graph=1, tune_cache=cache.encode())
+        o = Q.qsim_batch_opts(use_graph=1, path=path, tune_cache=cache.encode())
         h = C.c_void_p()
         Q.qsim_batch_create(C.cast(arr, C.c_void_p), len(circs), C.byref(o), C.byref(h))
     info = np.zeros(8, dtype=np.int64)
@@ -616,6 +620,7 @@ def batch_leg(Q, W, C):
             "latency_p50_ms": float(np.percentile(lat, 50)) * 1e3,
             "latency_p99_ms": float(np.percentile(lat, 99)) * 1e3, "work_items": int(info[1]),
             "ctas": int(info[2]), "arena_bytes": int(info[3]), "graph": bool(info[6]),
+            "tensor_core_circuits": int(info[7]),
             "tuned_tiles": {str(k): v for k, v in sorted(tuned.items())}}
 
 

@@ -341,13 +341,20 @@ typedef struct {
     int32_t low_qubits;         /* 0: autotuned */
     int32_t ctas;               /* persistent CTAs (0: one per SM x occupancy) */
     int32_t use_graph;          /* 1: launch through a captured CUDA graph */
+    int32_t path;               /* per circuit: 0 autotuned (tensor-core blocks for a qubit count
+                                   whose fastest tune-cache entry is a tensor-core plan, else
+                                   fused SIMT passes), 1 fused SIMT passes only, 2 tensor-core
+                                   blocks (BF16x3) for every circuit with n >= 13 */
     const char *tune_cache;     /* JSON file of autotuner results, may be NULL */
     void *stream;
 } qsim_batch_opts;
 
 /* Plans count circuits (complex64), allocates one device arena holding all
- * their kets, each initialised to |0...0>, and prepares one persistent
- * launch (captured in a CUDA graph when use_graph = 1). */
+ * their kets, each initialised to |0...0>, and prepares the launch (captured
+ * in a CUDA graph when use_graph = 1): one persistent launch runs every
+ * circuit planned as fused SIMT passes; circuits planned as tensor-core
+ * blocks (see path) run as one grouped launch per block round, each CTA a
+ * range of tiles of one block, concurrently with it on a second stream. */
 qsim_status qsim_batch_create(const qsim_circuit *const *cs, int count, const qsim_batch_opts *opts,
                               qsim_batch **out);
 qsim_status qsim_batch_destroy(qsim_batch *b);
@@ -364,9 +371,12 @@ qsim_status qsim_batch_download(qsim_batch *b, int i, void *host_amps);
 /* info[0] circuits, info[1] work items, info[2] ctas, info[3] arena bytes. */
 qsim_status qsim_batch_info(const qsim_batch *b, int64_t info[8]);
 
-/* Autotuner: times candidate (tile_qubits, low_qubits, prec) settings for
- * the circuit on a scratch state of its size and returns the fastest in
- * best_opts; appends the result to the JSON file tune_cache if not NULL. */
+/* Autotuner: times the circuit on a scratch state of its size as fused SIMT
+ * passes with every tile width (10 .. 14 qubits) and, for complex64 with
+ * n >= 13, as tensor-core blocks (BF16x3); returns the fastest in best_opts
+ * (prec QSIM_PREC_BF16X3 for the tensor-core plan) and appends one JSON
+ * line per candidate to tune_cache if not NULL ("path": "tc" marks the
+ * tensor-core plan; qsim_batch_create reads the file). */
 qsim_status qsim_autotune(const qsim_circuit *c, qsim_dtype dt, const char *tune_cache,
                           qsim_run_opts *best_opts, double *best_seconds);
 

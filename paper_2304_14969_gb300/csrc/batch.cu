@@ -27,6 +27,7 @@ namespace qs {
 qsim_status permute_state(qsim_state *s, const std::vector<int> &new_pos);
 qsim_status plan_build(const qsim_circuit *cir, qsim_dtype dt, const qsim_run_opts *opts, const int *start_l2p,
                        qsim_plan *P);
+qsim_status plan_build_tc(const qsim_circuit *cir, const qsim_run_opts *opts, const int *start_l2p, qsim_plan *P);
 qsim_status validate_circuit(const qsim_circuit *c);
 int num_sms();
 
@@ -162,6 +163,32 @@ static int cached_tile(const char *path, int n)
     return tile;
 }
 
+// True if the fastest complex64 tune-cache entry for n is a tensor-core
+// plan ("path": "tc").
+static bool cached_tc(const char *path, int n)
+{
+    if (!path) return false;
+    std::ifstream f(path);
+    if (!f) return false;
+    std::string line;
+    double best = 1e300;
+    bool tc = false;
+    while (std::getline(f, line)) {
+        int ln = -1, ldt = -1;
+        double ms = 0;
+        const char *s = line.c_str();
+        const char *p;
+        if ((p = strstr(s, "\"n\":"))) ln = atoi(p + 4);
+        if ((p = strstr(s, "\"dtype\":"))) ldt = atoi(p + 8);
+        if ((p = strstr(s, "\"ms\":"))) ms = atof(p + 5);
+        if (ln == n && ldt == 0 && ms > 0 && ms < best) {
+            best = ms;
+            tc = strstr(s, "\"path\": \"tc\"") != nullptr;
+        }
+    }
+    return tc;
+}
+
 }  // namespace qs
 
 using namespace qs;
@@ -192,6 +219,14 @@ struct qsim_batch {
     int stage_off = 0;
     bool dirty = false;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
+    // circuits on tensor-core blocks: descriptors, work entries per round
+    int ntc = 0;
+    void *tc_mem = nullptr;
+    TcBatchDesc *d_desc = nullptr;
+    TcWork *d_work = nullptr;
+    std::vector<int> round_off, round_cnt;
+    cudaStream_t st2 = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
 };
 
 static void batch_free(qsim_batch *b)
@@ -200,8 +235,12 @@ static void batch_free(qsim_batch *b)
     if (b->st) cudaStreamSynchronize(b->st);
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
     if (b->graph) cudaGraphDestroy(b->graph);
-    for (void *p : {(void *)b->arena, b->dtab, (void *)b->dcnt, (void *)b->dts, (void *)b->derr})
+    if (b->st2) cudaStreamSynchronize(b->st2);
+    for (void *p : {(void *)b->arena, b->dtab, (void *)b->dcnt, (void *)b->dts, (void *)b->derr, b->tc_mem})
         if (p) cudaFree(p);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->join) cudaEventDestroy(b->join);
+    if (b->st2) cudaStreamDestroy(b->st2);
     for (qsim_plan *p : b->plans) qsim_plan_destroy(p);
     if (b->e0) cudaEventDestroy(b->e0);
     if (b->e1) cudaEventDestroy(b->e1);
@@ -216,10 +255,23 @@ static qsim_status batch_launch(qsim_batch *b)
     QS_CUDA(cudaMemsetAsync(b->dts + b->count, 0, sizeof(unsigned long long) * b->count, b->st));
     QS_CUDA(cudaMemsetAsync(b->derr, 0, sizeof(int), b->st));
     const long long wait_limit_ns = 2000000000;   // 2 s of device time per wait
-    k_batch<<<b->grid, kBatchThreads, b->smem, b->st>>>(b->arena, b->d_passes, b->d_off, b->d_items, b->nitems,
-                                                       b->dcnt, b->dcnt + 1, b->d_need, b->dts, b->dts + b->count,
-                                                       b->derr, wait_limit_ns, 0, b->stage_off);
-    QS_CUDA(cudaGetLastError());
+    if (!b->round_cnt.empty()) {
+        // tensor-core circuits: one grouped launch per block round on a second
+        // stream, concurrent with the persistent SIMT launch
+        QS_CUDA(cudaEventRecord(b->fork, b->st));
+        QS_CUDA(cudaStreamWaitEvent(b->st2, b->fork, 0));
+        for (size_t r = 0; r < b->round_cnt.size(); r++)
+            QS_CUDA(tc_pipe_launch_grouped(b->d_desc, b->d_work + b->round_off[r], b->round_cnt[r], b->dts,
+                                           b->dts + b->count, b->derr, b->st2));
+        QS_CUDA(cudaEventRecord(b->join, b->st2));
+    }
+    if (b->nitems > 0) {
+        k_batch<<<b->grid, kBatchThreads, b->smem, b->st>>>(b->arena, b->d_passes, b->d_off, b->d_items, b->nitems,
+                                                           b->dcnt, b->dcnt + 1, b->d_need, b->dts, b->dts + b->count,
+                                                           b->derr, wait_limit_ns, 0, b->stage_off);
+        QS_CUDA(cudaGetLastError());
+    }
+    if (!b->round_cnt.empty()) QS_CUDA(cudaStreamWaitEvent(b->st, b->join, 0));
     return QSIM_OK;
 }
 
@@ -263,6 +315,27 @@ qsim_status qsim_batch_create(const qsim_circuit *const *cs, int count, const qs
         ro.relabel_swaps = 1;
         ro.tile_qubits = t;
         qsim_plan *P = nullptr;
+        // tensor-core blocks (BF16x3) when asked for or autotuned, if the plan
+        // is blocks only; otherwise fused SIMT passes
+        const bool want_tc = c && c->n >= 13 && (o.path == 2 || (o.path == 0 && cached_tc(o.tune_cache, c->n)));
+        if (st == QSIM_OK && want_tc) {
+            qsim_run_opts to{};
+            to.mode = QSIM_MODE_FUSED;
+            to.relabel_swaps = 1;
+            to.prec = QSIM_PREC_BF16X3;
+            P = new qsim_plan();
+            bool ok = plan_build_tc(c, &to, nullptr, P) == QSIM_OK;
+            for (const PlanStep &s2 : P->steps) ok = ok && s2.kind == 3;
+            if (ok) {
+                b->plans.push_back(P);
+                b->n.push_back(c->n);
+                b->ntc++;
+                continue;
+            }
+            delete P;
+            P = nullptr;
+            clear_error();
+        }
         if (st == QSIM_OK) {
             P = new qsim_plan();
             st = plan_build(c, QSIM_C64, &ro, nullptr, P);
@@ -368,6 +441,92 @@ qsim_status qsim_batch_create(const qsim_circuit *const *cs, int count, const qs
     b->d_items = (BatchItem *)(d + o_it);
     b->d_off = (uint64_t *)(d + o_of);
     b->d_need = (unsigned *)(d + o_ne);
+    // ---- tensor-core circuits: per block a descriptor (tensor map over the
+    // circuit's ket, geometry, U, deferred-phase tables); work entries of at
+    // most kTcChunk tiles, grouped by block round
+    if (b->ntc > 0) {
+        const uint64_t kTcChunk = 16;
+        std::vector<std::pair<int, int>> blocks;   // (circuit, block)
+        int rounds_tc = 0;
+        for (int i = 0; i < count; i++)
+            if (b->plans[i]->passes.empty() && !b->plans[i]->tc_A.empty()) {
+                for (int j = 0; j < (int)b->plans[i]->tc_A.size(); j++) blocks.push_back({i, j});
+                rounds_tc = std::max(rounds_tc, (int)b->plans[i]->tc_A.size());
+            }
+        const size_t nb = blocks.size();
+        const size_t o_desc = 0, o_u = (nb * sizeof(TcBatchDesc) + 255) & ~(size_t)255;
+        size_t o_tab = o_u + nb * 65536, o_work;
+        std::vector<size_t> tab_off(nb, 0);
+        for (size_t k = 0; k < nb; k++) {
+            const qsim_plan *Pk = b->plans[blocks[k].first];
+            if (!Pk->tc_pd_off[blocks[k].second].empty()) {
+                tab_off[k] = o_tab;
+                o_tab += (kTcPipeTableBytes + 255) & ~(size_t)255;
+            }
+        }
+        std::vector<std::vector<int>> desc_of(count);
+        for (size_t k = 0; k < nb; k++) desc_of[blocks[k].first].push_back((int)k);
+        std::vector<TcWork> works;
+        for (int r = 0; r < rounds_tc; r++) {
+            b->round_off.push_back((int)works.size());
+            for (int i = 0; i < count; i++) {
+                if (r >= (int)desc_of[i].size()) continue;
+                const uint64_t ntiles = 1ull << (b->n[i] - 13);
+                for (uint64_t t0 = 0; t0 < ntiles; t0 += kTcChunk)
+                    works.push_back(TcWork{desc_of[i][r], 0, t0, std::min(kTcChunk, ntiles - t0)});
+            }
+            b->round_cnt.push_back((int)works.size() - b->round_off.back());
+        }
+        o_work = (o_tab + 255) & ~(size_t)255;
+        const size_t tot_tc = o_work + works.size() * sizeof(TcWork) + 256;
+        e = cudaMalloc(&b->tc_mem, tot_tc);
+        if (e != cudaSuccess) {
+            batch_free(b);
+            return cuda_fail(e, "batch tensor-core tables");
+        }
+        unsigned char *dm = (unsigned char *)b->tc_mem;
+        std::vector<unsigned char> hm(tot_tc, 0);
+        std::vector<TcBatchDesc> descs(nb);
+        for (size_t k = 0; k < nb; k++) {
+            const int i = blocks[k].first, j = blocks[k].second;
+            const qsim_plan *Pk = b->plans[i];
+            if (Pk->tc_A[j].size() != 65536) {
+                batch_free(b);
+                return fail(QSIM_E_UNSUPPORTED, "unexpected tensor-core operand size");
+            }
+            memcpy(hm.data() + o_u + k * 65536, Pk->tc_A[j].data(), 65536);
+            const void *tabs = nullptr;
+            if (tab_off[k]) {
+                std::vector<unsigned char> tb;
+                tc_pipe_tables(b->n[i], Pk->tc_spec[j], Pk->tc_pd_off[j], Pk->tc_pd_bit[j], Pk->tc_pd_tw[j], tb);
+                memcpy(hm.data() + tab_off[k], tb.data(), tb.size());
+                tabs = dm + tab_off[k];
+            }
+            TcPipeHost H;
+            qsim_status st = tc_pipe_prepare(b->n[i], Pk->tc_spec[j], tabs, H);
+            if (st == QSIM_OK) st = tc_pipe_encode(H, b->arena + b->amp_off[i], descs[k].tmap);
+            if (st != QSIM_OK) {
+                batch_free(b);
+                return st;
+            }
+            descs[k].args = H.args;
+            descs[k].U = dm + o_u + k * 65536;
+            descs[k].amps = b->arena + b->amp_off[i];
+            descs[k].circ = i;
+        }
+        memcpy(hm.data() + o_desc, descs.data(), nb * sizeof(TcBatchDesc));
+        memcpy(hm.data() + o_work, works.data(), works.size() * sizeof(TcWork));
+        e = cudaMemcpy(b->tc_mem, hm.data(), tot_tc, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->st2, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            batch_free(b);
+            return cuda_fail(e, "batch tensor-core setup");
+        }
+        b->d_desc = (TcBatchDesc *)(dm + o_desc);
+        b->d_work = (TcWork *)(dm + o_work);
+    }
     // ---- launch shape
     size_t lin_bytes = ((size_t)max_lin * 16 + 15) & ~(size_t)15;
     b->stage_off = (int)(kBatchTile + lin_bytes);
@@ -382,7 +541,7 @@ qsim_status qsim_batch_create(const qsim_circuit *const *cs, int count, const qs
     if (occ < 1) occ = 1;
     int ctas = num_sms() * occ;
     if (o.ctas > 0) ctas = std::min(ctas, o.ctas);
-    b->grid = std::max(1, std::min(ctas, b->nitems));
+    b->grid = std::max(1, std::min(ctas, std::max(1, b->nitems)));
     // ---- kets at |0...0>
     k_batch_reset<<<num_sms() * 4, 256, 0, b->st>>>(b->arena, b->total_amps, b->d_off, count);
     k_batch_ones<<<(count + 255) / 256, 256, 0, b->st>>>(b->arena, b->d_off, count);
@@ -493,7 +652,7 @@ qsim_status qsim_batch_info(const qsim_batch *b, int64_t info[8])
     info[4] = b->npasses;
     info[5] = (int64_t)b->smem;
     info[6] = b->gexec ? 1 : 0;
-    info[7] = 0;
+    info[7] = b->ntc;
     return QSIM_OK;
 }
 
@@ -559,6 +718,49 @@ qsim_status qsim_autotune(const qsim_circuit *c, qsim_dtype dt, const char *tune
             best_t = t;
         }
     }
+    // complex64 with n >= 13: the same circuit as tensor-core blocks (BF16x3)
+    bool best_tc = false;
+    if (st == QSIM_OK && dt == QSIM_C64 && c->n >= 13) {
+        qsim_run_opts o{};
+        o.mode = QSIM_MODE_FUSED;
+        o.relabel_swaps = 1;
+        o.prec = QSIM_PREC_BF16X3;
+        float tot = 0;
+        bool ok = true;
+        for (int r = 0; r < 4 && st == QSIM_OK; r++) {
+            qsim_plan *p = nullptr;
+            if (qsim_plan_create_for_state(c, s, &o, &p) != QSIM_OK) {
+                ok = false;
+                break;
+            }
+            cudaEventRecord(a, s->stream);
+            st = qsim_plan_execute(s, p);
+            cudaEventRecord(z, s->stream);
+            cudaEventSynchronize(z);
+            if (st == QSIM_OK) st = qsim_synchronize(s);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, a, z);
+            if (r > 0) tot += ms;
+            qsim_plan_destroy(p);
+        }
+        if (!ok) {
+            clear_error();
+        } else if (st == QSIM_OK) {
+            double avg = tot / 3.0;
+            if (tune_cache) {
+                FILE *f = fopen(tune_cache, "a");
+                if (f) {
+                    fprintf(f, "{\"n\": %d, \"dtype\": %d, \"gates\": %d, \"tile\": 0, \"path\": \"tc\", \"ms\": %.6f}\n",
+                            c->n, (int)dt, c->ngates, avg);
+                    fclose(f);
+                }
+            }
+            if (avg < best) {
+                best = avg;
+                best_tc = true;
+            }
+        }
+    }
     cudaEventDestroy(a);
     cudaEventDestroy(z);
     qsim_destroy(s);
@@ -567,7 +769,8 @@ qsim_status qsim_autotune(const qsim_circuit *c, qsim_dtype dt, const char *tune
         memset(best_opts, 0, sizeof *best_opts);
         best_opts->mode = QSIM_MODE_FUSED;
         best_opts->relabel_swaps = 1;
-        best_opts->tile_qubits = best_t;
+        best_opts->tile_qubits = best_tc ? 0 : best_t;
+        best_opts->prec = best_tc ? QSIM_PREC_BF16X3 : QSIM_PREC_NATIVE;
     }
     if (best_seconds) *best_seconds = best * 1e-3;
     return QSIM_OK;

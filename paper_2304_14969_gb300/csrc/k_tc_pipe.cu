@@ -68,11 +68,34 @@ __device__ __forceinline__ void turns_sincos(uint64_t tt, float &s, float &c)
     sincospif(2.0f * f, &s, &c);
 }
 
+// G = false: one block over one ket, CTAs stride over its tiles (the
+// tensor map, geometry, ket and U come as parameters). G = true: grouped
+// (batched circuits): CTA i takes work entry i, a range of tiles of the
+// block that descs[works[i].desc] describes, and stamps the circuit's first
+// load and last store with %globaltimer.
+template <bool G>
 __global__ void __launch_bounds__(kPThreads, 1)
-    k_tc_pipe(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ TcPipeArgs P, float2 *__restrict__ a,
-              const unsigned char *__restrict__ Ug, int *err)
+    k_tc_pipe(const __grid_constant__ CUtensorMap tmap_param, const __grid_constant__ TcPipeArgs P_param,
+              float2 *__restrict__ a_param, const unsigned char *__restrict__ Ug_param, int *err,
+              const TcBatchDesc *__restrict__ descs, const TcWork *__restrict__ works, unsigned long long *t0s,
+              unsigned long long *t1s)
 {
     extern __shared__ unsigned char sm_dyn[];
+    __shared__ __align__(16) TcPipeArgs s_P;
+    const TcBatchDesc *desc = G ? &descs[works[blockIdx.x].desc] : nullptr;
+    {
+        const uint64_t *src = (const uint64_t *)(G ? &desc->args : &P_param);
+        uint64_t *dst = (uint64_t *)&s_P;
+        for (int i = threadIdx.x; i < (int)(sizeof(TcPipeArgs) / 8); i += blockDim.x) dst[i] = src[i];
+    }
+    __syncthreads();
+    const TcPipeArgs &P = s_P;
+    const void *tmap = G ? (const void *)desc->tmap : (const void *)&tmap_param;
+    float2 *__restrict__ a = G ? desc->amps : a_param;
+    const unsigned char *__restrict__ Ug = G ? desc->U : Ug_param;
+    const uint64_t wtile0 = G ? works[blockIdx.x].tile0 : 0, wntiles = G ? works[blockIdx.x].ntiles : 0;
+    // tile of this CTA's j-th iteration
+    auto tile_of = [&](uint64_t j) -> uint64_t { return G ? wtile0 + j : blockIdx.x + j * gridDim.x; };
     unsigned char *smb = (unsigned char *)(((uintptr_t)sm_dyn + 1023) & ~(uintptr_t)1023);
     unsigned char *Us = smb;                              // U operand (N x K): hi [0, 32K), lo [32K, 64K)
     unsigned char *St = smb + kPU;                        // raw stages 0 and 1
@@ -130,8 +153,9 @@ __global__ void __launch_bounds__(kPThreads, 1)
         *abort_flag = 1;
         atomicExch(err, 1);
     };
-    // tiles of this CTA: blockIdx.x + j * gridDim.x, j < J
-    const uint64_t J = P.ntiles > blockIdx.x ? (P.ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+    // number of tiles of this CTA
+    const uint64_t J = G ? wntiles : (P.ntiles > blockIdx.x ? (P.ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0);
+    if (G && tid == 0 && J > 0) atomicMin(&t0s[desc->circ], global_ns());
 
     if (warp == 0) {
         // ---------------- TMA producer (lane 0) and tile factors of the
@@ -148,7 +172,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
                 stop = !ok || *abort_flag;
             }
             if (__shfl_sync(0xffffffffu, stop, 0)) break;
-            const uint64_t t = blockIdx.x + j * gridDim.x;
+            const uint64_t t = tile_of(j);
             const uint32_t fb = smem_addr(&bar_full[s]);
             if (lane == 0) {
                 const uint64_t base = tile_base(P, t);
@@ -158,7 +182,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
                 mbar_arrive_expect_tx(fb, P.box_bytes * (uint32_t)P.nload);
                 const uint32_t dst = smem_addr(St + (size_t)s * kPStage);
                 for (int v = 0; v < P.nload; v++)
-                    tma_load_5d(dst + (uint32_t)v * P.box_bytes, &tmap, fb, c[0], c[1], c[2], c[3], c[4] + P.xoff[v]);
+                    tma_load_5d(dst + (uint32_t)v * P.box_bytes, tmap, fb, c[0], c[1], c[2], c[3], c[4] + P.xoff[v]);
             }
             if (has_pd) {
                 if (lane < 6) {
@@ -342,7 +366,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;");
-            const uint64_t base = tile_base(P, blockIdx.x + j * gridDim.x);
+            const uint64_t base = tile_base(P, tile_of(j));
             float2 *dstg = a + (base + spG);
 #pragma unroll 1
             for (int c0 = 0; c0 < 128; c0 += 32) {
@@ -365,6 +389,10 @@ __global__ void __launch_bounds__(kPThreads, 1)
             }
             asm volatile("tcgen05.fence::before_thread_sync;");
             mbar_arrive(smem_addr(&bar_accf[b]));
+        }
+        if (G) {
+            named_bar_sync(2, kPEpi);
+            if (warp == 2 + kPConvWarps && lane == 0 && J > 0) atomicMax(&t1s[desc->circ], global_ns());
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -397,23 +425,51 @@ EncodeTiledFn encode_fn()
 
 }  // namespace
 
-cudaError_t tc_pipe_launch(qsim_state *s, const TcPipeHost &H, const unsigned char *dU, int *derr)
+qsim_status tc_pipe_encode(const TcPipeHost &H, void *amps, unsigned char tmap[128])
 {
     EncodeTiledFn enc = encode_fn();
-    if (!enc) return cudaErrorNotSupported;
+    if (!enc) return fail(QSIM_E_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
     alignas(64) CUtensorMap tm;
-    CUresult r = enc(&tm, CU_TENSOR_MAP_DATA_TYPE_INT64, (cuuint32_t)H.rank, s->amps, (const cuuint64_t *)H.gdim,
+    CUresult r = enc(&tm, CU_TENSOR_MAP_DATA_TYPE_INT64, (cuuint32_t)H.rank, amps, (const cuuint64_t *)H.gdim,
                      (const cuuint64_t *)H.gstr, (const cuuint32_t *)H.box, (const cuuint32_t *)H.estr,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_tc_pipe, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPSmem);
-        attr = true;
-    }
+    if (r != CUDA_SUCCESS) return fail(QSIM_E_CUDA, "tensor map encoding failed (CUresult %d)", (int)r);
+    static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
+    memcpy(tmap, &tm, 128);
+    return QSIM_OK;
+}
+
+static void tc_pipe_attrs()
+{
+    static std::once_flag once;
+    std::call_once(once, []() {
+        cudaFuncSetAttribute(k_tc_pipe<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPSmem);
+        cudaFuncSetAttribute(k_tc_pipe<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPSmem);
+    });
+}
+
+cudaError_t tc_pipe_launch(qsim_state *s, const TcPipeHost &H, const unsigned char *dU, int *derr)
+{
+    alignas(64) CUtensorMap tm;
+    if (tc_pipe_encode(H, s->amps, (unsigned char *)&tm) != QSIM_OK) return cudaErrorInvalidValue;
+    tc_pipe_attrs();
     const int grid = (int)std::min<uint64_t>(H.args.ntiles, (uint64_t)num_sms());
-    k_tc_pipe<<<grid, kPThreads, kPSmem, s->stream>>>(tm, H.args, (float2 *)s->amps, dU, derr);
+    k_tc_pipe<false><<<grid, kPThreads, kPSmem, s->stream>>>(tm, H.args, (float2 *)s->amps, dU, derr, nullptr, nullptr,
+                                                              nullptr, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t tc_pipe_launch_grouped(const TcBatchDesc *descs, const TcWork *works, int nwork, unsigned long long *t0,
+                                   unsigned long long *t1, int *err, cudaStream_t st)
+{
+    if (nwork <= 0) return cudaSuccess;
+    tc_pipe_attrs();
+    alignas(64) CUtensorMap tm;
+    memset(&tm, 0, sizeof tm);
+    TcPipeArgs none;
+    memset(&none, 0, sizeof none);
+    k_tc_pipe<true><<<nwork, kPThreads, kPSmem, st>>>(tm, none, nullptr, nullptr, err, descs, works, t0, t1);
     return cudaGetLastError();
 }
 

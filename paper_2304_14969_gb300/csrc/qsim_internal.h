@@ -133,6 +133,23 @@ void tc_pipe_tables(int n, const TcSpec &ts, const std::vector<int32_t> &off, co
                     const std::vector<uint64_t> &tw, std::vector<unsigned char> &out);
 cudaError_t tc_pipe_launch(qsim_state *s, const TcPipeHost &H, const unsigned char *dU, int *derr);
 
+// Grouped launches of the pipelined kernel (batched circuits): one CTA per
+// work entry = a range of tiles of one block of one circuit.
+struct alignas(64) TcBatchDesc {
+    unsigned char tmap[128];     // tensor map of the block over the circuit's ket
+    TcPipeArgs args;
+    const unsigned char *U;      // BF16 hi / lo operand of the block (64 KB, device)
+    float2 *amps;                // the circuit's ket (device)
+    int circ;                    // circuit index (latency stamps)
+};
+struct TcWork {
+    int32_t desc, pad;
+    uint64_t tile0, ntiles;
+};
+qsim_status tc_pipe_encode(const TcPipeHost &H, void *amps, unsigned char tmap[128]);
+cudaError_t tc_pipe_launch_grouped(const TcBatchDesc *descs, const TcWork *works, int nwork, unsigned long long *t0,
+                                   unsigned long long *t1, int *err, cudaStream_t st);
+
 // Asynchronous error word of a state (see qsim_state): ensure allocates it,
 // fetch enqueues its copy to the host (before a synchronisation), check
 // reports and clears it (after the synchronisation).

@@ -78,7 +78,7 @@ class qsim_approx_result(C.Structure):
 
 class qsim_batch_opts(C.Structure):
     _fields_ = [("tile_qubits", C.c_int32), ("low_qubits", C.c_int32), ("ctas", C.c_int32),
-                ("use_graph", C.c_int32), ("tune_cache", C.c_char_p), ("stream", C.c_void_p)]
+                ("use_graph", C.c_int32), ("path", C.c_int32), ("tune_cache", C.c_char_p), ("stream", C.c_void_p)]
 
 
 _lib = None

@@ -29,23 +29,29 @@ def infid(a, b):
     return 1 - abs(np.vdot(a, b)) ** 2 / (np.vdot(a, a).real * np.vdot(b, b).real)
 
 
-def make_batch(Q, specs, use_graph=1, cache=None, tile=0):
+def make_batch(Q, specs, use_graph=1, cache=None, tile=0, path=0):
     circs = [Q.Circuit(s["n"], s["gates"]) for s in specs]
     arr = (C.POINTER(Q.qsim_circuit) * len(circs))(*[C.pointer(c.c) for c in circs])
-    o = Q.qsim_batch_opts(use_graph=use_graph, tile_qubits=tile,
+    o = Q.qsim_batch_opts(use_graph=use_graph, tile_qubits=tile, path=path,
                           tune_cache=cache.encode() if cache else None)
     h = C.c_void_p()
     Q.qsim_batch_create(C.cast(arr, C.c_void_p), len(circs), C.byref(o), C.byref(h))
     return h, circs
 
 
+@pytest.mark.parametrize("path", [1, 2])
 @pytest.mark.parametrize("use_graph", [0, 1])
-def test_batch_matches_oracle(Q, use_graph):
+def test_batch_matches_oracle(Q, use_graph, path):
+    """path 1: every circuit as fused SIMT passes in the persistent launch;
+    path 2: circuits with n >= 13 as tensor-core blocks (grouped launches per
+    block round, concurrent with the SIMT launch for the smaller ones)."""
     specs = W.batch_circuits(12, seed=3, nmin=10, nmax=17, dmin=2, dmax=8)
-    h, circs = make_batch(Q, specs, use_graph)
+    h, circs = make_batch(Q, specs, use_graph, path=path)
     info = np.zeros(8, dtype=np.int64)
     Q.qsim_batch_info(h, info.ctypes.data_as(C.c_void_p))
-    assert info[0] == 12 and info[1] >= 12
+    ntc = sum(s["n"] >= 13 for s in specs)
+    assert info[0] == 12 and info[7] == (ntc if path == 2 else 0)
+    assert 0 < ntc < 12
     # Gaussian inputs for even circuits, |0...0> for odd ones
     inputs = []
     Q.qsim_batch_reset(h)
@@ -80,9 +86,11 @@ def test_autotune_and_cache(Q):
     with tempfile.TemporaryDirectory() as d:
         path = os.path.join(d, "tune.jsonl")
         Q.qsim_autotune(c.ptr(), 0, path.encode(), C.byref(best), C.byref(secs))
-        assert 10 <= best.tile_qubits <= 14 and secs.value > 0
+        assert secs.value > 0
+        # the fastest candidate: a SIMT tile width, or the tensor-core plan
+        assert (10 <= best.tile_qubits <= 14 and best.prec == 0) or (best.tile_qubits == 0 and best.prec == 2)
         lines = open(path).read().strip().splitlines()
-        assert len(lines) >= 4
+        assert len(lines) >= 5 and sum('"path": "tc"' in x for x in lines) == 1
         specs = [{"n": 16, "gates": g, "kind": "qft"}]
         h, circs = make_batch(Q, specs, cache=path)
         Q.qsim_batch_run(h, None, None)
