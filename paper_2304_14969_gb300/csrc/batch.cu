@@ -137,7 +137,8 @@ qsim_status plan_upload_ext(qsim_plan *P);
 cudaError_t launch_fused_pass(qsim_state *s, const FPassDev &d);
 
 // Tile choice per qubit count from the tuner's JSON-lines cache: the
-// fastest complex64 entry for that n; 0 if none.
+// complex64 entry for that n with the lowest batch cost (sm_ms, else ms);
+// 0 if none.
 static int cached_tile(const char *path, int n)
 {
     if (!path) return 0;
@@ -155,6 +156,7 @@ static int cached_tile(const char *path, int n)
         if ((p = strstr(s, "\"tile\":"))) lt = atoi(p + 7);
         if ((p = strstr(s, "\"dtype\":"))) ldt = atoi(p + 8);
         if ((p = strstr(s, "\"ms\":"))) ms = atof(p + 5);
+        if ((p = strstr(s, "\"sm_ms\":"))) ms = atof(p + 8);   // batch cost when recorded
         if (ln == n && ldt == 0 && lt > 0 && ms < best) {
             best = ms;
             tile = lt;
@@ -163,8 +165,8 @@ static int cached_tile(const char *path, int n)
     return tile;
 }
 
-// True if the fastest complex64 tune-cache entry for n is a tensor-core
-// plan ("path": "tc").
+// True if the complex64 tune-cache entry for n with the lowest batch cost
+// (sm_ms, else ms) is a tensor-core plan ("path": "tc").
 static bool cached_tc(const char *path, int n)
 {
     if (!path) return false;
@@ -181,6 +183,7 @@ static bool cached_tc(const char *path, int n)
         if ((p = strstr(s, "\"n\":"))) ln = atoi(p + 4);
         if ((p = strstr(s, "\"dtype\":"))) ldt = atoi(p + 8);
         if ((p = strstr(s, "\"ms\":"))) ms = atof(p + 5);
+        if ((p = strstr(s, "\"sm_ms\":"))) ms = atof(p + 8);
         if (ln == n && ldt == 0 && ms > 0 && ms < best) {
             best = ms;
             tc = strstr(s, "\"path\": \"tc\"") != nullptr;
@@ -708,8 +711,14 @@ qsim_status qsim_autotune(const qsim_circuit *c, qsim_dtype dt, const char *tune
         if (tune_cache) {
             FILE *f = fopen(tune_cache, "a");
             if (f) {
-                fprintf(f, "{\"n\": %d, \"dtype\": %d, \"gates\": %d, \"tile\": %d, \"ms\": %.6f}\n", c->n, (int)dt,
-                        c->ngates, t, avg);
+                // sm_ms: the time weighted by the share of the GPU's CTA slots the
+                // plan's launches occupy (persistent CTAs, two per SM for
+                // complex64, one for complex128): what a batch of such circuits
+                // pays per circuit, running side by side
+                const double slots = (double)num_sms() * (dt == QSIM_C64 ? 2 : 1);
+                const double share = std::min(1.0, (double)(1ull << (c->n - t)) / slots);
+                fprintf(f, "{\"n\": %d, \"dtype\": %d, \"gates\": %d, \"tile\": %d, \"ms\": %.6f, \"sm_ms\": %.6f}\n",
+                        c->n, (int)dt, c->ngates, t, avg, avg * share);
                 fclose(f);
             }
         }
@@ -750,8 +759,12 @@ qsim_status qsim_autotune(const qsim_circuit *c, qsim_dtype dt, const char *tune
             if (tune_cache) {
                 FILE *f = fopen(tune_cache, "a");
                 if (f) {
-                    fprintf(f, "{\"n\": %d, \"dtype\": %d, \"gates\": %d, \"tile\": 0, \"path\": \"tc\", \"ms\": %.6f}\n",
-                            c->n, (int)dt, c->ngates, avg);
+                    // one CTA per SM, one tile of 2^13 amplitudes per CTA at most
+                    const double share = std::min(1.0, (double)(1ull << (c->n - 13)) / (double)num_sms());
+                    fprintf(f,
+                            "{\"n\": %d, \"dtype\": %d, \"gates\": %d, \"tile\": 0, \"path\": \"tc\", \"ms\": %.6f, "
+                            "\"sm_ms\": %.6f}\n",
+                            c->n, (int)dt, c->ngates, avg, avg * share);
                     fclose(f);
                 }
             }
