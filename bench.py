@@ -621,7 +621,7 @@ def batch_leg(Q, W, C, path=0):
             "latency_p99_ms": float(np.percentile(lat, 99)) * 1e3, "work_items": int(info[1]),
             "ctas": int(info[2]), "arena_bytes": int(info[3]), "graph": bool(info[6]),
             "tensor_core_circuits": int(info[7]),
-            "tuned_tiles": {str(k): v for k, v in sorted(tuned.items())}}
+            "fastest_alone": {str(k): v for k, v in sorted(tuned.items())}}
 
 
 def approx_leg(Q, W, g, budget_gib=80.0, time_cap_s=40.0, p_start=1.0, mlp=None):

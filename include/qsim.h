@@ -375,11 +375,11 @@ qsim_status qsim_batch_info(const qsim_batch *b, int64_t info[8]);
  * passes with every tile width (10 .. 14 qubits) and, for complex64 with
  * n >= 13, as tensor-core blocks (BF16x3); returns the fastest in best_opts
  * (prec QSIM_PREC_BF16X3 for the tensor-core plan) and appends one JSON
- * line per candidate to tune_cache if not NULL: its time ("ms") and its
- * batch cost ("sm_ms": the time weighted by the share of the GPU's CTA
- * slots the plan's launches occupy, what the circuit costs when many run
- * side by side); "path": "tc" marks the tensor-core plan.
- * qsim_batch_create ranks a qubit count's candidates by batch cost. */
+ * line per candidate to tune_cache if not NULL: its time alone ("ms") and,
+ * for complex64, its batch cost ("sm_ms": device time per circuit of a
+ * batch of copies of the circuit that fills the GPU, run through the batch
+ * runner); "path": "tc" marks the tensor-core plan. qsim_batch_create
+ * ranks a qubit count's candidates by batch cost. */
 qsim_status qsim_autotune(const qsim_circuit *c, qsim_dtype dt, const char *tune_cache,
                           qsim_run_opts *best_opts, double *best_seconds);
 

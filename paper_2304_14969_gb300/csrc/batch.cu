@@ -659,6 +659,41 @@ qsim_status qsim_batch_info(const qsim_batch *b, int64_t info[8])
     return QSIM_OK;
 }
 
+}  // extern "C"
+
+// Batch cost of one setting: device time per circuit of a batch of R copies
+// of c (R large enough to occupy every SM a few times over), run through
+// the batch runner itself; negative if the setting cannot be batched.
+static double batch_cost_ms(const qsim_circuit *c, int path, int tile)
+{
+    const int t = path == 2 ? 13 : tile;
+    const uint64_t tiles = 1ull << std::max(0, c->n - t);
+    uint64_t R = (4ull * (uint64_t)num_sms() * 2 + tiles - 1) / tiles;
+    R = std::max<uint64_t>(1, std::min<uint64_t>(R, 512));
+    while (R > 1 && (R << c->n) * 8 > (2ull << 30)) R--;
+    std::vector<const qsim_circuit *> cs((size_t)R, c);
+    qsim_batch_opts o{};
+    o.use_graph = 1;
+    o.path = path;
+    o.tile_qubits = path == 2 ? 0 : tile;
+    qsim_batch *b = nullptr;
+    if (qsim_batch_create(cs.data(), (int)R, &o, &b) != QSIM_OK) {
+        clear_error();
+        return -1;
+    }
+    double sec = 0;
+    bool ok = qsim_batch_run(b, nullptr, nullptr) == QSIM_OK && qsim_batch_reset(b) == QSIM_OK &&
+              qsim_batch_run(b, &sec, nullptr) == QSIM_OK;
+    qsim_batch_destroy(b);
+    if (!ok) {
+        clear_error();
+        return -1;
+    }
+    return sec * 1e3 / (double)R;
+}
+
+extern "C" {
+
 qsim_status qsim_autotune(const qsim_circuit *c, qsim_dtype dt, const char *tune_cache, qsim_run_opts *best_opts,
                           double *best_seconds)
 {
@@ -711,14 +746,15 @@ qsim_status qsim_autotune(const qsim_circuit *c, qsim_dtype dt, const char *tune
         if (tune_cache) {
             FILE *f = fopen(tune_cache, "a");
             if (f) {
-                // sm_ms: the time weighted by the share of the GPU's CTA slots the
-                // plan's launches occupy (persistent CTAs, two per SM for
-                // complex64, one for complex128): what a batch of such circuits
-                // pays per circuit, running side by side
-                const double slots = (double)num_sms() * (dt == QSIM_C64 ? 2 : 1);
-                const double share = std::min(1.0, (double)(1ull << (c->n - t)) / slots);
-                fprintf(f, "{\"n\": %d, \"dtype\": %d, \"gates\": %d, \"tile\": %d, \"ms\": %.6f, \"sm_ms\": %.6f}\n",
-                        c->n, (int)dt, c->ngates, t, avg, avg * share);
+                // sm_ms: device time per circuit when a batch of copies runs
+                // side by side (complex64 tiles the batch runner takes)
+                const double bc = dt == QSIM_C64 && t <= 13 ? batch_cost_ms(c, 1, t) : -1.0;
+                if (bc > 0)
+                    fprintf(f, "{\"n\": %d, \"dtype\": %d, \"gates\": %d, \"tile\": %d, \"ms\": %.6f, \"sm_ms\": %.6f}\n",
+                            c->n, (int)dt, c->ngates, t, avg, bc);
+                else
+                    fprintf(f, "{\"n\": %d, \"dtype\": %d, \"gates\": %d, \"tile\": %d, \"ms\": %.6f}\n", c->n,
+                            (int)dt, c->ngates, t, avg);
                 fclose(f);
             }
         }
@@ -759,12 +795,15 @@ qsim_status qsim_autotune(const qsim_circuit *c, qsim_dtype dt, const char *tune
             if (tune_cache) {
                 FILE *f = fopen(tune_cache, "a");
                 if (f) {
-                    // one CTA per SM, one tile of 2^13 amplitudes per CTA at most
-                    const double share = std::min(1.0, (double)(1ull << (c->n - 13)) / (double)num_sms());
-                    fprintf(f,
-                            "{\"n\": %d, \"dtype\": %d, \"gates\": %d, \"tile\": 0, \"path\": \"tc\", \"ms\": %.6f, "
-                            "\"sm_ms\": %.6f}\n",
-                            c->n, (int)dt, c->ngates, avg, avg * share);
+                    const double bc = batch_cost_ms(c, 2, 0);
+                    if (bc > 0)
+                        fprintf(f,
+                                "{\"n\": %d, \"dtype\": %d, \"gates\": %d, \"tile\": 0, \"path\": \"tc\", \"ms\": %.6f, "
+                                "\"sm_ms\": %.6f}\n",
+                                c->n, (int)dt, c->ngates, avg, bc);
+                    else
+                        fprintf(f, "{\"n\": %d, \"dtype\": %d, \"gates\": %d, \"tile\": 0, \"path\": \"tc\", \"ms\": %.6f}\n",
+                                c->n, (int)dt, c->ngates, avg);
                     fclose(f);
                 }
             }
