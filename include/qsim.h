@@ -223,6 +223,12 @@ qsim_status qsim_plan_info(const qsim_plan *p, int64_t info[8]);
  * not the plan's starting map, the amplitudes are first permuted to it (one
  * extra read+write of the ket). */
 qsim_status qsim_plan_execute(qsim_state *s, const qsim_plan *p);
+/* Executes the plan and returns the FP64 sum of |psi_i|^2 of the result in
+ * *norm (synchronises), as qsim_plan_execute then qsim_norm. When the plan
+ * ends with a tensor-core block the sum is taken by that block's write-back
+ * (FP32 runs of 16 squares, FP64 accumulation) instead of a separate read
+ * of the ket. */
+qsim_status qsim_plan_execute_norm(qsim_state *s, const qsim_plan *p, double *norm);
 
 /* ------------------------------------------------------ reductions */
 

@@ -246,9 +246,11 @@ qsim_status qsim_plan_info(const qsim_plan *p, int64_t info[8])
     return QSIM_OK;
 }
 
-qsim_status qsim_plan_execute(qsim_state *s, const qsim_plan *p)
+// Executes p on s; when norm_dev is not NULL and the last step is a
+// pipelined tensor-core block, that block adds the sum of |psi_i|^2 of its
+// output to *norm_dev.
+static qsim_status plan_execute_impl(qsim_state *s, const qsim_plan *p, double *norm_dev)
 {
-    clear_error();
     if (!s || !s->amps || !p) return fail(QSIM_E_INVAL, "NULL argument");
     if (p->n != s->n || p->dt != s->dt) return fail(QSIM_E_INVAL, "plan and state differ in n or dtype");
     if (!p->dmem && (!p->passes.empty() || !p->tc_A.empty())) QS_TRY(plan_upload(const_cast<qsim_plan *>(p)));
@@ -259,7 +261,8 @@ qsim_status qsim_plan_execute(qsim_state *s, const qsim_plan *p)
         QS_TRY(permute_state(s, to));
         s->l2p = p->start_l2p;
     }
-    for (const PlanStep &st : p->steps) {
+    for (size_t k = 0; k < p->steps.size(); k++) {
+        const PlanStep &st = p->steps[k];
         if (st.kind == 0) {
             QS_CUDA(launch_fused_pass(s, p->passes[st.pass].dev));
         } else if (st.kind == 1) {
@@ -278,7 +281,8 @@ qsim_status qsim_plan_execute(qsim_state *s, const qsim_plan *p)
             const unsigned char *dU = (const unsigned char *)p->dmem + p->tc_off[st.pass];
             QS_TRY(err_ensure(s));
             if (!p->tc_pipe.empty())
-                QS_CUDA(tc_pipe_launch(s, p->tc_pipe[st.pass], dU, s->d_err));
+                QS_CUDA(tc_pipe_launch(s, p->tc_pipe[st.pass], dU, s->d_err,
+                                       k + 1 == p->steps.size() ? norm_dev : nullptr));
             else
                 QS_CUDA(tc_launch(s, p->tc_spec[st.pass], dU, (qsim_prec)p->prec, s->d_err));
         } else {
@@ -289,6 +293,33 @@ qsim_status qsim_plan_execute(qsim_state *s, const qsim_plan *p)
     s->l2p = p->final_l2p;
     // tensor-core blocks report a bounded wait that gave up through the
     // state's error word, read at the next call that synchronises
+    return QSIM_OK;
+}
+
+qsim_status qsim_plan_execute(qsim_state *s, const qsim_plan *p)
+{
+    clear_error();
+    return plan_execute_impl(s, p, nullptr);
+}
+
+qsim_status qsim_plan_execute_norm(qsim_state *s, const qsim_plan *p, double *norm)
+{
+    clear_error();
+    if (!norm) return fail(QSIM_E_INVAL, "norm is NULL");
+    const bool fused = p && !p->steps.empty() && p->steps.back().kind == 3 && !p->tc_pipe.empty() &&
+                       s && s->dt == QSIM_C64;
+    if (!fused) {
+        QS_TRY(plan_execute_impl(s, p, nullptr));
+        return qsim_norm(s, norm);
+    }
+    QS_TRY(ensure_scratch(s->red, 64));
+    QS_CUDA(cudaMemsetAsync(s->red.d, 0, sizeof(double), s->stream));
+    QS_TRY(plan_execute_impl(s, p, s->red.d));
+    QS_CUDA(cudaMemcpyAsync(s->red.h, s->red.d, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    err_fetch(s);
+    QS_CUDA(cudaStreamSynchronize(s->stream));
+    QS_TRY(err_check(s));
+    *norm = s->red.h[0];
     return QSIM_OK;
 }
 

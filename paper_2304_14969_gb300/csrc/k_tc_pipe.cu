@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
     k_tc_pipe(const __grid_constant__ CUtensorMap tmap_param, const __grid_constant__ TcPipeArgs P_param,
               float2 *__restrict__ a_param, const unsigned char *__restrict__ Ug_param, int *err,
               const TcBatchDesc *__restrict__ descs, const TcWork *__restrict__ works, unsigned long long *t0s,
-              unsigned long long *t1s)
+              unsigned long long *t1s, double *norm_out)
 {
     extern __shared__ unsigned char sm_dyn[];
     __shared__ __align__(16) TcPipeArgs s_P;
@@ -253,6 +253,10 @@ __global__ void __launch_bounds__(kPThreads, 1)
         const uint32_t lane_off = (uint32_t)(32 * quarter) << 16;
         const uint32_t offG = 8u * P.posG[g];
         const int rot = P.rot_bits ? (lane >> (4 - P.rot_bits)) & ((1 << P.rot_bits) - 1) : 0;
+        // in-stage byte offsets of this thread's reads (the same for every tile)
+        uint32_t offL[16];
+#pragma unroll
+        for (int i = 0; i < 16; i++) offL[i] = offG + 8u * s_posL[16 * part + (i ^ rot)];
 
         for (uint64_t j = 0; j < J; j++) {
             const int s = (int)(j & 1), b = (int)(j & 1);
@@ -262,7 +266,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
                 give_up();
                 break;
             }
-            const unsigned char *stage = St + (size_t)s * kPStage + offG;
+            const unsigned char *stage = St + (size_t)s * kPStage;
             float2 v[16];
             // Block qubits among qubits 0..3 (block bits 0..rot_bits-1) would put
             // the 16 lanes of a half-warp on one bank: each lane reads its
@@ -270,7 +274,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
             // read instruction covers 16 distinct banks; v[] is put back in
             // order below.
 #pragma unroll
-            for (int i = 0; i < 16; i++) v[i] = *(const float2 *)(stage + 8u * s_posL[16 * part + (i ^ rot)]);
+            for (int i = 0; i < 16; i++) v[i] = *(const float2 *)(stage + offL[i]);
             mbar_arrive(smem_addr(&bar_sfree[s]));   // the stage may be reloaded
 #pragma unroll
             for (int bb = 0; bb < 4; bb++) {
@@ -358,6 +362,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
         const int g = 32 * quarter + lane;
         const uint32_t lane_off = (uint32_t)(32 * quarter) << 16;
         const uint64_t spG = P.spG[g];
+        double nacc = 0;   // sum of |amplitude|^2 written (norm_out): FP32 runs of 16, FP64 across runs
         for (uint64_t j = 0; j < J; j++) {
             const int b = (int)(j & 1);
             const bool ok = mbar_wait_or_abort(smem_addr(&bar_mma[b]), (uint32_t)((j >> 1) & 1), abort_flag);
@@ -373,6 +378,12 @@ __global__ void __launch_bounds__(kPThreads, 1)
                 uint32_t r[32];
                 tmem_ld32(tmem + lane_off + (uint32_t)b * 128u + (uint32_t)c0, r);
                 tmem_wait_ld();
+                if (norm_out) {
+                    float run = 0.f;
+#pragma unroll
+                    for (int i = 0; i < 32; i++) run = fmaf(__uint_as_float(r[i]), __uint_as_float(r[i]), run);
+                    nacc += (double)run;
+                }
                 const int l0 = c0 / 2;
                 if (P.vec2) {
                     // amplitudes l, l + 1 adjacent: one 16-byte store per pair
@@ -389,6 +400,11 @@ __global__ void __launch_bounds__(kPThreads, 1)
             }
             asm volatile("tcgen05.fence::before_thread_sync;");
             mbar_arrive(smem_addr(&bar_accf[b]));
+        }
+        if (norm_out) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) nacc += __shfl_down_sync(0xffffffffu, nacc, o);
+            if (lane == 0) atomicAdd(norm_out, nacc);
         }
         if (G) {
             named_bar_sync(2, kPEpi);
@@ -449,14 +465,14 @@ static void tc_pipe_attrs()
     });
 }
 
-cudaError_t tc_pipe_launch(qsim_state *s, const TcPipeHost &H, const unsigned char *dU, int *derr)
+cudaError_t tc_pipe_launch(qsim_state *s, const TcPipeHost &H, const unsigned char *dU, int *derr, double *norm_out)
 {
     alignas(64) CUtensorMap tm;
     if (tc_pipe_encode(H, s->amps, (unsigned char *)&tm) != QSIM_OK) return cudaErrorInvalidValue;
     tc_pipe_attrs();
     const int grid = (int)std::min<uint64_t>(H.args.ntiles, (uint64_t)num_sms());
     k_tc_pipe<false><<<grid, kPThreads, kPSmem, s->stream>>>(tm, H.args, (float2 *)s->amps, dU, derr, nullptr, nullptr,
-                                                              nullptr, nullptr);
+                                                              nullptr, nullptr, norm_out);
     return cudaGetLastError();
 }
 
@@ -469,7 +485,7 @@ cudaError_t tc_pipe_launch_grouped(const TcBatchDesc *descs, const TcWork *works
     memset(&tm, 0, sizeof tm);
     TcPipeArgs none;
     memset(&none, 0, sizeof none);
-    k_tc_pipe<true><<<nwork, kPThreads, kPSmem, st>>>(tm, none, nullptr, nullptr, err, descs, works, t0, t1);
+    k_tc_pipe<true><<<nwork, kPThreads, kPSmem, st>>>(tm, none, nullptr, nullptr, err, descs, works, t0, t1, nullptr);
     return cudaGetLastError();
 }
 

@@ -131,7 +131,10 @@ qsim_status tc_pipe_prepare(int n, const TcSpec &ts, const void *pd_tables_dev, 
 const size_t kTcPipeTableBytes = 6 * 24 * 8 + 128 * 6 * 8;
 void tc_pipe_tables(int n, const TcSpec &ts, const std::vector<int32_t> &off, const std::vector<int32_t> &pbit,
                     const std::vector<uint64_t> &tw, std::vector<unsigned char> &out);
-cudaError_t tc_pipe_launch(qsim_state *s, const TcPipeHost &H, const unsigned char *dU, int *derr);
+// norm_out (device, optional): the kernel adds the sum of |amplitude|^2 of
+// everything it writes (FP64 accumulation); the caller zeroes it first.
+cudaError_t tc_pipe_launch(qsim_state *s, const TcPipeHost &H, const unsigned char *dU, int *derr,
+                           double *norm_out = nullptr);
 
 // Grouped launches of the pipelined kernel (batched circuits): one CTA per
 // work entry = a range of tiles of one block of one circuit.

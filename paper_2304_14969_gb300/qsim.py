@@ -100,6 +100,7 @@ def _sig(L):
         "qsim_qubit_map": [P, P],
         "qsim_materialize": [P],
         "qsim_synchronize": [P],
+        "qsim_plan_execute_norm": [P, P, P],
         "qsim_selftest_wait_timeout": [P, C.c_int64],
         "qsim_apply_gate": [P, P, i32, P, i32, u64],
         "qsim_apply_cphase": [P, i32, i32, f64],
@@ -178,7 +179,7 @@ def _wrap(name):
 
 
 for _n in ["qsim_create", "qsim_wrap", "qsim_destroy", "qsim_set_basis", "qsim_upload", "qsim_download",
-           "qsim_device_ptr", "qsim_qubit_map", "qsim_materialize", "qsim_synchronize", "qsim_selftest_wait_timeout",
+           "qsim_device_ptr", "qsim_qubit_map", "qsim_materialize", "qsim_synchronize", "qsim_selftest_wait_timeout", "qsim_plan_execute_norm",
            "qsim_apply_gate",
            "qsim_apply_cphase", "qsim_apply_2q", "qsim_apply_swap", "qsim_apply_fused", "qsim_run_circuit",
            "qsim_plan_create", "qsim_plan_create_for_state", "qsim_plan_destroy", "qsim_plan_info", "qsim_plan_execute", "qsim_norm",
@@ -341,6 +342,12 @@ class Plan:
 
     def execute(self, st: State):
         qsim_plan_execute(st.h, self.h)
+
+    def execute_norm(self, st: State) -> float:
+        """Executes the plan and returns the FP64 sum of |psi_i|^2 of the result."""
+        x = C.c_double()
+        qsim_plan_execute_norm(st.h, self.h, C.byref(x))
+        return x.value
 
     def close(self):
         if self.h:

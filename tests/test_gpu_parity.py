@@ -147,9 +147,9 @@ def sampled_error(Q, st, x, n, idx):
 
 
 def test_qft27_full_size_sampled(Q):
-    """27 qubits, the benchmark's launch configuration: complex64 fused and
-    complex128 per-gate, sampled outputs against Eq. (dft) evaluated one by
-    one, plus norm preservation at full size."""
+    """27 qubits: complex64 fused, complex128 per-gate and complex128 fused,
+    sampled outputs against Eq. (dft) evaluated one by one, plus norm
+    preservation at full size."""
     n = 27
     x = W.gaussian_state(n, 0)
     idx = [0, 1, 12345, (1 << n) - 1, 98765432]
@@ -165,6 +165,14 @@ def test_qft27_full_size_sampled(Q):
     st = Q.State(n, 1)
     st.upload(x)
     st.run(circ, mode=0, relabel=1)
+    y, err = sampled_error(Q, st, x, n, idx)
+    assert err <= 1e-12
+    assert abs(st.norm() - 1.0) < 1e-12
+    st.close()
+    # complex128 fused passes (deferred phases in FP64 turns)
+    st = Q.State(n, 1)
+    st.upload(x)
+    Q.Plan(circ, dtype=1).execute(st)
     y, err = sampled_error(Q, st, x, n, idx)
     assert err <= 1e-12
     assert abs(st.norm() - 1.0) < 1e-12

@@ -125,3 +125,26 @@ def test_tc_qft30_basis_closed_form(Q):
     ref = np.exp(2j * np.pi * ((x * ks) % N).astype(np.float64) / N) / np.sqrt(N)
     got = y[ks].astype(np.complex128)
     assert np.sum(np.abs(got - ref) ** 2) / np.sum(np.abs(ref) ** 2) <= 1e-6
+
+
+@pytest.mark.parametrize("which", ["qft16", "grid20", "simt_qft16"])
+def test_plan_execute_norm(Q, which):
+    """qsim_plan_execute_norm: the norm taken by the last tensor-core block's
+    write-back equals a separate FP64 norm of the result (same ket, FP32 runs
+    summed in FP64, different order); plans that do not end with a
+    tensor-core block fall back to the separate reduction."""
+    if which.endswith("qft16"):
+        n, g = 16, W.qft_circuit(16)
+    else:
+        n, g = 20, W.grid_rcs_circuit(4, 5, 8, seed=4)
+    x = W.gaussian_state(n, 9)
+    st = Q.State(n, 0)
+    st.upload(x)
+    plan = Q.Plan(Q.Circuit(n, g), dtype=0, state=st, **({} if which.startswith("simt") else {"prec": 2}))
+    nf = plan.execute_norm(st)
+    ns = st.norm()
+    assert abs(nf - ns) <= 1e-6 * ns
+    assert abs(nf - 1.0) <= 1e-5
+    ref = oracle.apply_circuit(x, g)
+    assert infid(st.download(), ref) <= 1e-6
+    st.close()
