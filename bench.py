@@ -125,6 +125,15 @@ def oracle_sample(n_gates=16, n=N_QUBITS, seed=0):
     return len(g) * (1 << n) / dt, dt, len(g)
 
 
+def main_config(world, blocks=5):
+    """The workload both arms report (the 27-qubit QFT on a Gaussian
+    complex64 ket, on tensor-core blocks in this implementation)."""
+    return {"workload": "qft27_gaussian_c64_tc_bf16x3", "n_qubits": N_QUBITS, "gates": 391, "blocks": blocks,
+            "path": "fused <=6-qubit blocks on tensor cores (BF16x3 split, FP32 accumulation)",
+            "ket_bytes": 8 << N_QUBITS, "l2": "ket (1 GiB) larger than L2",
+            "parallelism": "replicas" if world > 1 else "single"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -141,8 +150,7 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * float(np.median(secs)), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "qft27_gaussian", "n_qubits": N_QUBITS, "gates": 391,
-                   "sample": "first 4 gates of the 27-qubit QFT per step"},
+        "config": dict(main_config(1), sample="first 4 gates of the 27-qubit QFT per step (FP64 oracle)"),
         "cpu_baseline": {"value": value, "unit": "updates/s", "cores": 1, "kind": "oracle",
                          "sample": "first 4 gates of the 27-qubit QFT per step, FP64, one thread"},
         "e2e": {"value": value, "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -297,10 +305,7 @@ def main():
         "metric": "amplitude-gate updates/s", "value": value, "unit": "updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "qft27_gaussian_c64_tc_bf16x3", "n_qubits": n, "gates": ng, "blocks": npass,
-                   "path": "fused <=6-qubit blocks on tensor cores (BF16x3 split, FP32 accumulation)",
-                   "ket_bytes": 8 * N, "l2": "ket (1 GiB) larger than L2",
-                   "parallelism": "replicas" if world > 1 else "single"},
+        "config": main_config(world, npass),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic_from_profiles("k_tc_pipe"),
                      "kernel": "k_tc_pipe", "alg_bytes_per_launch": alg_bytes,
