@@ -48,11 +48,33 @@ def parse():
 
 
 def dist_init(n):
+    """N > 1: one process per GPU under torchrun (NCCL; gloo where no CUDA
+    device is present). The GPUs run independent replicas: no data-path
+    collective, only the barrier and the max of the step times."""
     if n <= 1:
         return 0, 1
+    import torch
     import torch.distributed as dist
-    dist.init_process_group("nccl")
+    dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     return dist.get_rank(), dist.get_world_size()
+
+
+def max_over_ranks(x, world):
+    """The largest value of x over all ranks (the job's time is its slowest
+    replica's)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, units_per_rank, ms_per_step):
+    """Whole-job throughput: every replica processes units_per_rank per step."""
+    return world * units_per_rank / (ms_per_step * 1e-3)
 
 
 # ------------------------------------------------------------- clocks
@@ -262,14 +284,9 @@ def main():
         kz.record(stream)
         torch.cuda.synchronize()
     pass_ms = [ka.elapsed_time(kz) / kt]
-    total_ms = sum(step_ms)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), world)
     ms_per_step = total_ms / args.steps
-    value = world * ng * N / (ms_per_step * 1e-3)
+    value = job_value(world, ng * N, ms_per_step)
     npass = info["passes"]
     launch_ms = float(np.mean(pass_ms)) / npass
     alg_bytes = 2 * 8 * N                   # one read + one write of the ket per pass
@@ -289,7 +306,7 @@ def main():
         plans[0].execute(st)
         Q.qsim_download(st.h, C.c_void_p(host_out.data_ptr()))
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    e2e_val = world * ng * N / (float(np.median(e2e_ms)) * 1e-3)
+    e2e_val = job_value(world, ng * N, max_over_ranks(float(np.median(e2e_ms)), world))
 
     extras = {}
     if rank == 0 and not args.no_extras:
