@@ -595,6 +595,7 @@ def extra_legs(Q, W, C, torch, circ, x, n, ng):
     best = min(out[k]["ms"] for k in out if k.startswith("grid30_c64"))
     out["grid30_speedup_vs_per_gate_fp64"] = pg * 1e3 / best
     s128.close()
+    out["rows"] = rows_leg(Q, W, C, torch)
     out["batch512"] = batch_leg(Q, W, C)
     out["batch512_tc"] = batch_leg(Q, W, C, path=2)
     out["approx54_grid"] = approx_leg(Q, W, W.grid_rcs_circuit(6, 9, 7, seed=0), budget_gib=80.0)
@@ -606,6 +607,89 @@ def extra_legs(Q, W, C, torch, circ, x, n, ng):
     h = train_proposal_mlp(Q, W, C)
     out["approx54_paper_family_mlp"] = approx_leg(Q, W, pf, budget_gib=80.0, mlp=h)
     Q.qsim_mlp_destroy(h)
+    return out
+
+
+def rows_leg(Q, W, C, torch, n=27):
+    """Each remaining hot-path row on its own, on a 27-qubit complex64 ket
+    (1 GiB, larger than L2): device time per call with CUDA events (reductions
+    include their host synchronisation), algorithmic bytes, GB/s and the
+    fraction of the measured HBM peak; MLP inference / training latency."""
+    peaks = {}
+    pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pp):
+        peaks = json.load(open(pp))
+    peak = peaks.get("hbm_gbs", 6800.0)
+    N = 1 << n
+    B = 8
+    st = Q.State(n, Q.QSIM_C64)
+    Q.qsim_set_basis(st.h, 12345)
+    other = Q.State(n, Q.QSIM_C64)
+    Q.qsim_set_basis(other.h, 12345)
+    h = np.ascontiguousarray(np.array([1, 0, 1, 0, 1, 0, -1, 0], dtype=np.float64) / np.sqrt(2))
+    x = np.ascontiguousarray(np.array([0, 0, 1, 0, 1, 0, 0, 0], dtype=np.float64))
+    fsim = np.zeros((4, 4), dtype=np.complex128)
+    fsim[0, 0] = 1
+    fsim[1, 2] = fsim[2, 1] = -1j
+    fsim[3, 3] = np.exp(-1j * np.pi / 6)
+    f2 = np.ascontiguousarray(fsim.ravel().view(np.float64))
+    ctl = (C.c_int * 1)(5)
+    r3 = (C.c_double * (3 * n))()
+    ip = (C.c_double * 2)()
+    d = C.c_double()
+
+    def timed(fn, reps=10):
+        fn()
+        Q.qsim_synchronize(st.h)
+        torch.cuda.synchronize()
+        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        z.record()
+        Q.qsim_synchronize(st.h)
+        torch.cuda.synchronize()
+        return a.elapsed_time(z) / reps
+
+    cases = [
+        ("A2 1-qubit gate (H, qubit 20)", lambda: Q.qsim_apply_gate(st.h, h.ctypes.data_as(C.c_void_p), 20, None, 0, 0),
+         2 * B * N),
+        ("A2 controlled X (control 5, target 20)",
+         lambda: Q.qsim_apply_gate(st.h, x.ctypes.data_as(C.c_void_p), 20, ctl, 1, 1), 2 * B * N // 2),
+        ("A3 controlled phase (qubits 3, 22)", lambda: Q.qsim_apply_cphase(st.h, 3, 22, 0.3), 2 * B * N // 4),
+        ("A4 dense 2-qubit fSim (qubits 7, 19)", lambda: Q.qsim_apply_2q(st.h, f2.ctypes.data_as(C.c_void_p), 7, 19),
+         2 * B * N),
+        ("A8 FP64 norm", lambda: Q.qsim_norm(st.h, C.byref(d)), B * N),
+        ("A9 P(q = 1), qubit 11", lambda: Q.qsim_measure_prob(st.h, 11, C.byref(d)), B * N),
+        ("A10 FP64 inner product", lambda: Q.qsim_inner_product(st.h, other.h, ip), 2 * B * N),
+    ]
+    out = {}
+    for name, fn, by in cases:
+        ms = timed(fn)
+        out[name] = {"ms": ms, "bytes": by, "gbs": by / (ms * 1e-3) / 1e9, "frac_of_hbm": by / (ms * 1e-3) / 1e9 / peak}
+    # A11: Bloch vectors of all 27 qubits (tiled passes over the ket)
+    ms = timed(lambda: Q.qsim_bloch_all(st.h, r3), reps=3)
+    out["A11 Bloch vectors, all 27 qubits"] = {"ms": ms}
+    st.close()
+    other.close()
+    # A19 / A20: proposal MLP (12 -> 64 -> 64 -> 1)
+    hm = C.c_void_p()
+    Q.qsim_mlp_create(12, 64, 1, C.byref(hm))
+    fp = lambda a: a.ctypes.data_as(C.POINTER(C.c_float))
+    X = np.ascontiguousarray(np.random.default_rng(0).normal(size=(10000, 12)), dtype=np.float32)
+    Y = np.ascontiguousarray((X[:, 0] > 0).astype(np.float32))
+    lg = np.zeros(10000, dtype=np.float32)
+    loss = C.c_float()
+    t0 = time.perf_counter()
+    for _ in range(50):
+        Q.qsim_mlp_infer(hm, fp(X), 64, 1, fp(lg))
+    out["A19 MLP inference, 64 candidates (BF16 weights), host call"] = {"us": (time.perf_counter() - t0) / 50 * 1e6}
+    t0 = time.perf_counter()
+    for _ in range(20):
+        Q.qsim_mlp_train_step(hm, fp(X), fp(Y), 10000, C.c_float(3e-3), C.byref(loss))
+    out["A20 MLP training step, 10000 rows (fwd + bwd + Adam), host call"] = {
+        "ms": (time.perf_counter() - t0) / 20 * 1e3}
+    Q.qsim_mlp_destroy(hm)
     return out
 
 

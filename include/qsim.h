@@ -193,8 +193,10 @@ qsim_status qsim_apply_swap(qsim_state *s, int q0, int q1, int relabel);
 /* Fused block: U of size 2^k x 2^k (k <= 7; host, 2*4^k doubles, re/im,
  * row-major) applied on qubits[0..k-1], where qubits[b] is bit b of U's
  * row/column index (Table I "coalesced gates with a single traversal").
- * prec selects SIMT (NATIVE) or the tensor-core split precisions; the
- * tensor-core forms need a complex64 state and 5 <= k <= 7. */
+ * prec selects SIMT (NATIVE, k <= 7) or the tensor-core split precisions;
+ * the tensor-core forms need a complex64 state, n >= 6 and k <= 6 (smaller
+ * blocks are padded with identity qubits); k = 7 returns
+ * QSIM_E_UNSUPPORTED. */
 qsim_status qsim_apply_fused(qsim_state *s, int k, const int *qubits, const double *u,
                              qsim_prec prec);
 

@@ -98,11 +98,10 @@ __global__ void k_gate1(typename Vec2<R>::T *__restrict__ a, uint64_t nwork, Ins
 __global__ void k_gate1_c64v(float4 *__restrict__ a4, uint64_t nwork, InsSpec ins, uint64_t setmask,
                              uint64_t tbit, M2<float> u)
 {
-    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nwork; w += stride) {
-        uint64_t i0 = expand_bits(w << 1, ins) | setmask, i1 = i0 | tbit;
-        float4 x = a4[i0 >> 1], y = a4[i1 >> 1];
-        float4 o0 = make_float4(0, 0, 0, 0), o1 = o0;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    auto apply = [&](float4 x, float4 y, float4 &o0, float4 &o1) {
+        o0 = make_float4(0, 0, 0, 0);
+        o1 = o0;
         cmul_acc(o0.x, o0.y, u.re[0], u.im[0], x.x, x.y);
         cmul_acc(o0.x, o0.y, u.re[1], u.im[1], y.x, y.y);
         cmul_acc(o0.z, o0.w, u.re[0], u.im[0], x.z, x.w);
@@ -111,6 +110,30 @@ __global__ void k_gate1_c64v(float4 *__restrict__ a4, uint64_t nwork, InsSpec in
         cmul_acc(o1.x, o1.y, u.re[3], u.im[3], y.x, y.y);
         cmul_acc(o1.z, o1.w, u.re[2], u.im[2], x.z, x.w);
         cmul_acc(o1.z, o1.w, u.re[3], u.im[3], y.z, y.w);
+    };
+    uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    // four work items per iteration: eight 16-byte loads in flight per thread
+    for (; w + 3 * stride < nwork; w += 4 * stride) {
+        uint64_t i0[4];
+        float4 x[4], y[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            i0[k] = expand_bits((w + k * stride) << 1, ins) | setmask;
+            x[k] = a4[i0[k] >> 1];
+            y[k] = a4[(i0[k] | tbit) >> 1];
+        }
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            float4 o0, o1;
+            apply(x[k], y[k], o0, o1);
+            a4[i0[k] >> 1] = o0;
+            a4[(i0[k] | tbit) >> 1] = o1;
+        }
+    }
+    for (; w < nwork; w += stride) {
+        const uint64_t i0 = expand_bits(w << 1, ins) | setmask, i1 = i0 | tbit;
+        float4 o0, o1;
+        apply(a4[i0 >> 1], a4[i1 >> 1], o0, o1);
         a4[i0 >> 1] = o0;
         a4[i1 >> 1] = o1;
     }
@@ -159,6 +182,34 @@ __global__ void k_cphase(typename Vec2<R>::T *__restrict__ a, uint64_t nwork, In
         v.x = re;
         v.y = im;
         a[i] = v;
+    }
+}
+
+// complex64, neither qubit is qubit 0: each work item is an adjacent pair
+// of affected amplitudes (one 16-byte access), four items in flight; ins
+// holds qubit 0 as well as the two qubits.
+__global__ void k_cphase_c64v(float4 *__restrict__ a4, uint64_t nwork, InsSpec ins, uint64_t both, float cr,
+                              float ci)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    auto rot = [&](float4 v) {
+        return make_float4(v.x * cr - v.y * ci, v.x * ci + v.y * cr, v.z * cr - v.w * ci, v.z * ci + v.w * cr);
+    };
+    uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; w + 3 * stride < nwork; w += 4 * stride) {
+        uint64_t i[4];
+        float4 v[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            i[k] = (expand_bits(w + k * stride, ins) | both) >> 1;
+            v[k] = a4[i[k]];
+        }
+#pragma unroll
+        for (int k = 0; k < 4; k++) a4[i[k]] = rot(v[k]);
+    }
+    for (; w < nwork; w += stride) {
+        const uint64_t i = (expand_bits(w, ins) | both) >> 1;
+        a4[i] = rot(a4[i]);
     }
 }
 
@@ -324,7 +375,13 @@ cudaError_t launch_cphase(qsim_state *s, int q0, int q1, double theta)
     InsSpec ins = make_ins({q0, q1});
     uint64_t nwork = s->N() >> 2;
     double c = std::cos(theta), sn = std::sin(theta);
-    if (s->dt == QSIM_C64)
+    if (s->dt == QSIM_C64 && q0 != 0 && q1 != 0 && nwork >= 2) {
+        // ins also holds qubit 0 so that work items enumerate pairs (2i, 2i+1)
+        InsSpec ins0 = make_ins({0, q0, q1});
+        const uint64_t nw = s->N() >> 3;
+        k_cphase_c64v<<<default_grid(nw, kThreads), kThreads, 0, s->stream>>>(
+            (float4 *)s->amps, nw, ins0, bit(q0) | bit(q1), (float)c, (float)sn);
+    } else if (s->dt == QSIM_C64)
         k_cphase<float><<<default_grid(nwork, kThreads), kThreads, 0, s->stream>>>(
             (float2 *)s->amps, nwork, ins, bit(q0) | bit(q1), (float)c, (float)sn);
     else

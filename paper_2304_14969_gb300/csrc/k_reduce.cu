@@ -110,52 +110,102 @@ __global__ void k_red_norm(const typename V2T<R>::T *__restrict__ a, uint64_t N,
     block_write<1>(acc, partial);
 }
 
-// ---- P(q = 1): partial[0] = sum over bit q = 1, partial[1] = total
+// ---- P(q = 1): partial[0] = sum over bit q = 1, partial[1] = total.
+// complex64: 16-byte loads (amplitude pairs 2i, 2i+1), consecutive lanes on
+// consecutive pairs, four loads in flight; runs of 8 terms in FP32.
 template <typename R>
 __global__ void k_red_prob1(const typename V2T<R>::T *__restrict__ a, uint64_t N, uint64_t qb, double *partial)
 {
     double acc[2] = {0, 0};
-    uint64_t stride = (uint64_t)gridDim.x * blockDim.x * 8;
-    for (uint64_t base = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) * 8; base < N; base += stride) {
-        R one = 0, all = 0;
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (uint64_t)gridDim.x * blockDim.x;
+    if constexpr (sizeof(R) == 4) {
+        const float4 *a4 = (const float4 *)a;
+        const uint64_t N4 = N / 2;
+        uint64_t i = tid;
+        for (; i + 3 * nt < N4; i += 4 * nt) {
+            float4 v[4];
 #pragma unroll
-        for (int j = 0; j < 8; j++) {
-            uint64_t i = base + j;
-            if (i < N) {
-                auto v = a[i];
-                R p = v.x * v.x + v.y * v.y;
-                all += p;
-                one += (i & qb) ? p : R(0);
+            for (int j = 0; j < 4; j++) v[j] = a4[i + j * nt];
+            float one = 0.f, all = 0.f;
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const uint64_t e = 2 * (i + j * nt);
+                const float p0 = v[j].x * v[j].x + v[j].y * v[j].y, p1 = v[j].z * v[j].z + v[j].w * v[j].w;
+                all += p0 + p1;
+                one += ((e & qb) ? p0 : 0.f) + (((e + 1) & qb) ? p1 : 0.f);
             }
+            acc[0] += (double)one;
+            acc[1] += (double)all;
         }
-        acc[0] += (double)one;
-        acc[1] += (double)all;
+        for (; i < N4; i += nt) {
+            const float4 v = a4[i];
+            const uint64_t e = 2 * i;
+            const float p0 = v.x * v.x + v.y * v.y, p1 = v.z * v.z + v.w * v.w;
+            acc[1] += (double)(p0 + p1);
+            acc[0] += (double)(((e & qb) ? p0 : 0.f) + (((e + 1) & qb) ? p1 : 0.f));
+        }
+        if ((N & 1) && tid == 0) {
+            const auto v = a[N - 1];
+            const double p = (double)v.x * v.x + (double)v.y * v.y;
+            acc[1] += p;
+            if ((N - 1) & qb) acc[0] += p;
+        }
+    } else {
+        for (uint64_t i = tid; i < N; i += nt) {
+            const auto v = a[i];
+            const double p = v.x * v.x + v.y * v.y;
+            acc[1] += p;
+            if (i & qb) acc[0] += p;
+        }
     }
     block_write<2>(acc, partial);
 }
 
-// ---- <a|b> = sum conj(a_i) b_i
+// ---- <a|b> = sum conj(a_i) b_i (complex64: as above, two streams)
 template <typename R>
 __global__ void k_red_inner(const typename V2T<R>::T *__restrict__ a, const typename V2T<R>::T *__restrict__ b,
                             uint64_t N, double *partial)
 {
     double acc[2] = {0, 0};
-    uint64_t stride = (uint64_t)gridDim.x * blockDim.x * 8;
-    for (uint64_t base = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) * 8; base < N; base += stride) {
-        R re = 0, im = 0;
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (uint64_t)gridDim.x * blockDim.x;
+    if constexpr (sizeof(R) == 4) {
+        const float4 *a4 = (const float4 *)a, *b4 = (const float4 *)b;
+        const uint64_t N4 = N / 2;
+        uint64_t i = tid;
+        for (; i + 1 * nt < N4; i += 2 * nt) {
+            float4 x[2], y[2];
 #pragma unroll
-        for (int j = 0; j < 8; j++) {
-            if (base + j < N) {
-                auto x = a[base + j];
-                auto y = b[base + j];
-                re = fma(x.x, y.x, re);
-                re = fma(x.y, y.y, re);
-                im = fma(x.x, y.y, im);
-                im = fma(-x.y, y.x, im);
+            for (int j = 0; j < 2; j++) {
+                x[j] = a4[i + j * nt];
+                y[j] = b4[i + j * nt];
             }
+            float re = 0.f, im = 0.f;
+#pragma unroll
+            for (int j = 0; j < 2; j++) {
+                re = fmaf(x[j].x, y[j].x, fmaf(x[j].y, y[j].y, re));
+                re = fmaf(x[j].z, y[j].z, fmaf(x[j].w, y[j].w, re));
+                im = fmaf(x[j].x, y[j].y, fmaf(-x[j].y, y[j].x, im));
+                im = fmaf(x[j].z, y[j].w, fmaf(-x[j].w, y[j].z, im));
+            }
+            acc[0] += (double)re;
+            acc[1] += (double)im;
         }
-        acc[0] += (double)re;
-        acc[1] += (double)im;
+        for (; i < N4; i += nt) {
+            const float4 x = a4[i], y = b4[i];
+            acc[0] += (double)(x.x * y.x + x.y * y.y + x.z * y.z + x.w * y.w);
+            acc[1] += (double)(x.x * y.y - x.y * y.x + x.z * y.w - x.w * y.z);
+        }
+        if ((N & 1) && tid == 0) {
+            const auto x = a[N - 1], y = b[N - 1];
+            acc[0] += (double)x.x * y.x + (double)x.y * y.y;
+            acc[1] += (double)x.x * y.y - (double)x.y * y.x;
+        }
+    } else {
+        for (uint64_t i = tid; i < N; i += nt) {
+            const auto x = a[i], y = b[i];
+            acc[0] += x.x * y.x + x.y * y.y;
+            acc[1] += x.x * y.y - x.y * y.x;
+        }
     }
     block_write<2>(acc, partial);
 }
@@ -275,6 +325,119 @@ __global__ void k_red_bloch_tile(const typename V2T<R>::T *__restrict__ a, TileS
     if ((threadIdx.x & 31) == 0) atomicAdd(&bacc[0], tot);
     __syncthreads();
     for (int m = threadIdx.x; m < kTileRow; m += blockDim.x) partial[(size_t)blockIdx.x * kTileRow + m] = bacc[m];
+}
+
+// Compensated accumulator: FP32 (hi, lo) pair kept with TwoSum (Knuth), so
+// that thousands of per-tile runs add up to near-FP64 accuracy without the
+// FP64 pipe; FP64 for complex128 kets.
+template <typename R> struct CAcc;
+template <> struct CAcc<float> {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add(float x)
+    {
+        const float s = hi + x, bp = s - hi;
+        lo += (hi - (s - bp)) + (x - bp);
+        hi = s;
+    }
+    __device__ __forceinline__ double get() const { return (double)hi + (double)lo; }
+};
+template <> struct CAcc<double> {
+    double hi = 0.0;
+    __device__ __forceinline__ void add(double x) { hi += x; }
+    __device__ __forceinline__ double get() const { return hi; }
+};
+
+// Bloch sums of the 12 tile qubits of every tile (t = 12, c = 4: tile qubits
+// 0..3 and eight high ones), same partial-row format as k_red_bloch_tile.
+// A thread holds 16 amplitudes in registers: first the 16 consecutive ones
+// of its run (register bits = tile bits 0..3, one contiguous 128-byte
+// (complex64) load), then, read back from an XOR-swizzled shared-memory copy
+// of the tile, those with register bits = tile bits 4..7 and 8..11. Every
+// tile qubit's pair sums are taken in registers: sum over bit = 1 of |psi|^2,
+// and S = sum over bit = 0 of conj(psi_i) psi_{i + 2^q}; runs of 8 terms in
+// the ket's precision, added into compensated accumulators.
+template <typename R>
+__global__ void __launch_bounds__(256, 1)
+    k_red_bloch_reg(const typename V2T<R>::T *__restrict__ a, const __grid_constant__ TileSpec ts, double *partial)
+{
+    using V = typename V2T<R>::T;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    V *tile = (V *)smraw;
+    __shared__ double red[8][37];
+    const int th = threadIdx.x, lane = th & 31, warp = th >> 5;
+    auto swz = [](uint32_t e) { return e ^ (((e >> 4) ^ (e >> 8)) & 15u); };
+    // offset of this thread's run: th's bits on tile qubits 4..11
+    uint64_t hoff = 0;
+#pragma unroll
+    for (int b = 0; b < 8; b++)
+        if ((th >> b) & 1) hoff |= 1ull << ts.tq[4 + b];
+    CAcc<R> acc[37];   // [0] total, then (s1, sr, si) of tile qubit j at 1 + 3 j
+    const uint64_t ntiles = 1ull << (ts.n - 12);
+    // the next tile's run is loaded while this one is summed
+    V nxt[16];
+    if (blockIdx.x < ntiles) {
+        const V *src = a + (tile_expand((uint64_t)blockIdx.x << 4, ts.ins) | hoff);
+#pragma unroll
+        for (int r = 0; r < 16; r++) nxt[r] = src[r];
+    }
+    for (uint64_t tid = blockIdx.x; tid < ntiles; tid += gridDim.x) {
+        V v[16];
+#pragma unroll
+        for (int r = 0; r < 16; r++) v[r] = nxt[r];
+        if (tid + gridDim.x < ntiles) {
+            const V *src = a + (tile_expand((tid + gridDim.x) << 4, ts.ins) | hoff);
+#pragma unroll
+            for (int r = 0; r < 16; r++) nxt[r] = src[r];
+        }
+        auto sums = [&](int j0) {
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                R s1 = 0, sr = 0, si = 0;
+#pragma unroll
+                for (int r = 0; r < 16; r++) {
+                    if (r & (1 << j)) continue;
+                    const V x = v[r], y = v[r | (1 << j)];
+                    s1 = fma(y.x, y.x, fma(y.y, y.y, s1));
+                    sr = fma(x.x, y.x, fma(x.y, y.y, sr));
+                    si = fma(x.x, y.y, fma(-x.y, y.x, si));
+                }
+                acc[1 + 3 * (j0 + j)].add(s1);
+                acc[2 + 3 * (j0 + j)].add(sr);
+                acc[3 + 3 * (j0 + j)].add(si);
+            }
+        };
+        {
+            R tot = 0;
+#pragma unroll
+            for (int r = 0; r < 16; r++) tot = fma(v[r].x, v[r].x, fma(v[r].y, v[r].y, tot));
+            acc[0].add(tot);
+        }
+        sums(0);
+        __syncthreads();   // the previous tile's reads are done
+#pragma unroll
+        for (int r = 0; r < 16; r++) tile[swz(((uint32_t)th << 4) | r)] = v[r];
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < 16; r++) v[r] = tile[swz((th & 15) | (r << 4) | ((th >> 4) << 8))];
+        sums(4);
+#pragma unroll
+        for (int r = 0; r < 16; r++) v[r] = tile[swz(th | (r << 8))];
+        sums(8);
+    }
+    // block reduction of the 37 sums (FP64) into this CTA's partial row
+#pragma unroll
+    for (int m = 0; m < 37; m++) {
+        double x = acc[m].get();
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) red[warp][m] = x;
+    }
+    __syncthreads();
+    for (int m = th; m < kTileRow; m += blockDim.x) {
+        double x = 0;
+        if (m < 37)
+            for (int w = 0; w < (int)(blockDim.x >> 5); w++) x += red[w][m];
+        partial[(size_t)blockIdx.x * kTileRow + m] = x;
+    }
 }
 
 template <typename R>
@@ -420,7 +583,7 @@ __global__ void k_bloch_scatter(const double *__restrict__ comb, TileSpec ts, in
 qsim_status bloch_sums_device(const void *amps, qsim_dtype dt, int n, cudaStream_t stream, Scratch &sc,
                               double *d_out, int *passes)
 {
-    int t = std::min(n, dt == QSIM_C64 ? 12 : 11);
+    int t = std::min(n, 12);
     int c = std::min(t, 4);
     QS_TRY(ensure_scratch(sc, (size_t)kMaxRedBlocks * 64 + 64));
     int next_high = c, np = 0;
@@ -440,12 +603,29 @@ qsim_status bloch_sums_device(const void *amps, qsim_dtype dt, int n, cudaStream
         ts.ins.npos = t - c;
         for (int j = 0; j < t - c; j++) ts.ins.pos[j] = high[j];
         uint64_t ntiles = 1ull << (n - t);
-        int blocks = (int)std::min<uint64_t>(ntiles, kMaxRedBlocks);
-        size_t smem = ((size_t)1 << t) * (dt == QSIM_C64 ? 8 : 16);
-        if (dt == QSIM_C64)
-            k_red_bloch_tile<float><<<blocks, kRedThreads, smem, stream>>>((const float2 *)amps, ts, sc.d);
-        else
-            k_red_bloch_tile<double><<<blocks, kRedThreads, smem, stream>>>((const double2 *)amps, ts, sc.d);
+        int blocks;
+        if (t == 12 && c == 4) {
+            // register-resident tile pass (256 threads x 16 amplitudes)
+            const size_t smem = (size_t)4096 * (dt == QSIM_C64 ? 8 : 16);
+            static bool attr = false;
+            if (!attr) {
+                cudaFuncSetAttribute(k_red_bloch_reg<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536);
+                cudaFuncSetAttribute(k_red_bloch_reg<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 32768);
+                attr = true;
+            }
+            blocks = (int)std::min<uint64_t>(ntiles, (uint64_t)num_sms());
+            if (dt == QSIM_C64)
+                k_red_bloch_reg<float><<<blocks, 256, smem, stream>>>((const float2 *)amps, ts, sc.d);
+            else
+                k_red_bloch_reg<double><<<blocks, 256, smem, stream>>>((const double2 *)amps, ts, sc.d);
+        } else {
+            blocks = (int)std::min<uint64_t>(ntiles, kMaxRedBlocks);
+            size_t smem = ((size_t)1 << t) * (dt == QSIM_C64 ? 8 : 16);
+            if (dt == QSIM_C64)
+                k_red_bloch_tile<float><<<blocks, kRedThreads, smem, stream>>>((const float2 *)amps, ts, sc.d);
+            else
+                k_red_bloch_tile<double><<<blocks, kRedThreads, smem, stream>>>((const double2 *)amps, ts, sc.d);
+        }
         QS_CUDA(cudaGetLastError());
         double *comb = sc.d + (size_t)kMaxRedBlocks * 64;
         k_red_final<kTileRow><<<1, 256, 0, stream>>>(sc.d, blocks, comb);
