@@ -297,16 +297,35 @@ def main():
         peaks = json.load(open(pp))
     peak = peaks.get("hbm_gbs", 6800.0)
 
-    # ---- end to end through the public API with pinned host buffers
-    e2e_ms = []
-    for k in range(max(3, min(args.steps, 5))):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        Q.qsim_upload(st.h, C.c_void_p(host_in.data_ptr()))
-        plans[0].execute(st)
-        Q.qsim_download(st.h, C.c_void_p(host_out.data_ptr()))
-        e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    e2e_val = job_value(world, ng * N, max_over_ranks(float(np.median(e2e_ms)), world))
+    # ---- end to end through the public API with pinned host buffers: every
+    # step uploads its input ket, runs the QFT and downloads the result in
+    # logical order; two kets on two streams, so one step's download
+    # overlaps the next one's upload and transform (the host link is full
+    # duplex). Wall-clock over all steps, after both streams drained.
+    st2 = Q.State(n, Q.QSIM_C64, stream=torch.cuda.Stream().cuda_stream)
+    host_out2 = torch.empty(N, dtype=torch.complex64).pin_memory()
+    kets, outs = (st, st2), (host_out, host_out2)
+    e2e_steps = max(4, min(args.steps, 12))
+
+    def e2e_step(k):
+        s_ = kets[k % 2]
+        Q.qsim_upload(s_.h, C.c_void_p(host_in.data_ptr()))
+        plans[0].execute(s_)
+        Q.qsim_download_async(s_.h, C.c_void_p(outs[k % 2].data_ptr()))
+
+    for k in range(2):
+        e2e_step(k)
+    for s_ in kets:
+        Q.qsim_synchronize(s_.h)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(e2e_steps):
+        e2e_step(k)
+    for s_ in kets:
+        Q.qsim_synchronize(s_.h)
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
+    st2.close()
+    e2e_val = job_value(world, ng * N, max_over_ranks(e2e_ms, world))
 
     extras = {}
     if rank == 0 and not args.no_extras:
@@ -327,7 +346,8 @@ def main():
                      "frac": achieved / peak, "traffic": traffic_from_profiles("k_tc_pipe"),
                      "kernel": "k_tc_pipe", "alg_bytes_per_launch": alg_bytes,
                      "launch_ms": launch_ms, "peak_source": "measured hbm_gbs" if peaks else "fallback"},
-        "e2e": {"value": e2e_val, "unit": "updates/s", "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 8 * N},
+        "e2e": {"value": e2e_val, "unit": "updates/s", "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 8 * N,
+                "ms_per_step": e2e_ms, "pipeline": "2 kets on 2 streams: upload, QFT, download in logical order"},
         "gpu_launches": args.steps * npass,   # timed steps (the kernel-timing loop is outside the step region)
         "clocks": clk,
         "cpu_baseline": cpu,

@@ -139,11 +139,21 @@ qsim_status qsim_destroy(qsim_state *s);
 qsim_status qsim_set_basis(qsim_state *s, uint64_t x);
 
 /* Copies 2^n amplitudes of the state's dtype from host memory (logical
- * index order); the map becomes the identity. */
+ * index order); the map becomes the identity. Stream-ordered: from
+ * page-locked host memory the copy is asynchronous, and the buffer must not
+ * change until the stream has passed it (e.g. qsim_synchronize); from
+ * pageable memory the call returns once the data has been staged. */
 qsim_status qsim_upload(qsim_state *s, const void *host_amps);
 
 /* Copies the state to host memory in logical index order (synchronises). */
 qsim_status qsim_download(qsim_state *s, void *host_amps);
+
+/* Stream-ordered form of qsim_download: queues the copy (and the permutation
+ * into logical order, through a stream-ordered temporary, when the map is
+ * not the identity) and returns. host_amps should be page-locked; it holds
+ * the result once the stream has passed the copy (qsim_synchronize). Lets a
+ * caller overlap one ket's download with another's upload and gates. */
+qsim_status qsim_download_async(qsim_state *s, void *host_amps);
 
 /* Device address of the amplitudes (physical order) and the current map:
  * l2p[q] = physical bit holding logical qubit q (host array of n). */

@@ -141,16 +141,14 @@ qsim_status qsim_upload(qsim_state *s, const void *host_amps)
     return QSIM_OK;
 }
 
-qsim_status qsim_download(qsim_state *s, void *host_amps)
+qsim_status qsim_download_async(qsim_state *s, void *host_amps)
 {
     clear_error();
     QS_TRY(check_state(s));
     if (!host_amps) return fail(QSIM_E_INVAL, "host_amps is NULL");
     if (is_identity(s)) {
         QS_CUDA(cudaMemcpyAsync(host_amps, s->amps, s->amp_bytes(), cudaMemcpyDeviceToHost, s->stream));
-        err_fetch(s);
-        QS_CUDA(cudaStreamSynchronize(s->stream));
-        return err_check(s);
+        return QSIM_OK;
     }
     // physical bit p holds logical qubit L with l2p[L] = p; logical order puts it at bit L
     std::vector<int> to(s->n);
@@ -162,6 +160,12 @@ qsim_status qsim_download(qsim_state *s, void *host_amps)
         e = cudaMemcpyAsync(host_amps, tmp, s->amp_bytes(), cudaMemcpyDeviceToHost, s->stream);
     cudaFreeAsync(tmp, s->stream);
     if (e != cudaSuccess) return cuda_fail(e, "download");
+    return QSIM_OK;
+}
+
+qsim_status qsim_download(qsim_state *s, void *host_amps)
+{
+    QS_TRY(qsim_download_async(s, host_amps));
     err_fetch(s);
     QS_CUDA(cudaStreamSynchronize(s->stream));
     return err_check(s);

@@ -100,6 +100,7 @@ def _sig(L):
         "qsim_qubit_map": [P, P],
         "qsim_materialize": [P],
         "qsim_synchronize": [P],
+        "qsim_download_async": [P, P],
         "qsim_plan_execute_norm": [P, P, P],
         "qsim_selftest_wait_timeout": [P, C.c_int64],
         "qsim_apply_gate": [P, P, i32, P, i32, u64],
@@ -180,6 +181,7 @@ def _wrap(name):
 
 for _n in ["qsim_create", "qsim_wrap", "qsim_destroy", "qsim_set_basis", "qsim_upload", "qsim_download",
            "qsim_device_ptr", "qsim_qubit_map", "qsim_materialize", "qsim_synchronize", "qsim_selftest_wait_timeout", "qsim_plan_execute_norm",
+           "qsim_download_async",
            "qsim_apply_gate",
            "qsim_apply_cphase", "qsim_apply_2q", "qsim_apply_swap", "qsim_apply_fused", "qsim_run_circuit",
            "qsim_plan_create", "qsim_plan_create_for_state", "qsim_plan_destroy", "qsim_plan_info", "qsim_plan_execute", "qsim_norm",

@@ -294,3 +294,23 @@ def test_relabel_download_is_exact_permutation(Q, dt, n):
         y = st.download().astype(np.complex128)
         st.close()
         assert np.array_equal(y, ref)
+
+
+def test_download_async_matches_download(Q):
+    """qsim_download_async (stream-ordered, pinned host buffer) gives the
+    same logical-order ket as qsim_download, also from a permuted layout."""
+    import ctypes as C
+    import torch
+    n = 18
+    x = W.gaussian_state(n, 7)
+    g = W.qft_circuit(n)
+    st = Q.State(n, 0)
+    st.upload(x)
+    st.run(Q.Circuit(n, g), mode=1, relabel=1)
+    assert not np.array_equal(st.qubit_map(), np.arange(n))
+    ref = st.download()
+    pinned = torch.zeros(1 << n, dtype=torch.complex64).pin_memory()
+    Q.qsim_download_async(st.h, C.c_void_p(pinned.data_ptr()))
+    Q.qsim_synchronize(st.h)
+    assert np.array_equal(pinned.numpy(), ref)
+    st.close()
