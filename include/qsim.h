@@ -52,8 +52,18 @@ typedef enum { QSIM_C64 = 0, QSIM_C128 = 1 } qsim_dtype;
  * NATIVE: SIMT FMA in the state's precision.
  * 3XTF32: tensor-core products a_hi*b_hi + a_hi*b_lo + a_lo*b_hi of TF32
  *         parts, FP32 accumulation (complex64 states only).
- * BF16X3: the same three-product split with BF16 parts. */
-typedef enum { QSIM_PREC_NATIVE = 0, QSIM_PREC_3XTF32 = 1, QSIM_PREC_BF16X3 = 2 } qsim_prec;
+ * BF16X3: the same three-product split with BF16 parts (complex64 states).
+ * BF16X6: complex128 states: amplitudes rounded to FP32, each operand split
+ *         into three BF16 slices (x ~ x0 + x1 + x2, 24 bits), the six slice
+ *         products x_i*y_j with i + j <= 2 accumulated in FP32, results
+ *         widened to FP64 (exactly); n >= 13. Per-block error ~1e-7
+ *         relative, against ~1e-5 for BF16X3. */
+typedef enum {
+    QSIM_PREC_NATIVE = 0,
+    QSIM_PREC_3XTF32 = 1,
+    QSIM_PREC_BF16X3 = 2,
+    QSIM_PREC_BF16X6 = 3
+} qsim_prec;
 
 typedef enum {
     QSIM_OK = 0,
@@ -204,8 +214,9 @@ qsim_status qsim_apply_swap(qsim_state *s, int q0, int q1, int relabel);
  * row-major) applied on qubits[0..k-1], where qubits[b] is bit b of U's
  * row/column index (Table I "coalesced gates with a single traversal").
  * prec selects SIMT (NATIVE, k <= 7) or the tensor-core split precisions;
- * the tensor-core forms need a complex64 state, n >= 6 and k <= 6 (smaller
- * blocks are padded with identity qubits); k = 7 returns
+ * the tensor-core forms take k <= 6 (smaller blocks are padded with
+ * identity qubits) and a complex64 state with n >= 6 (3XTF32, BF16X3) or a
+ * complex128 state with n >= 13 (BF16X6); other pairings and k = 7 return
  * QSIM_E_UNSUPPORTED. */
 qsim_status qsim_apply_fused(qsim_state *s, int k, const int *qubits, const double *u,
                              qsim_prec prec);

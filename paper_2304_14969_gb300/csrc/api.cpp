@@ -299,7 +299,8 @@ qsim_status qsim_apply_fused(qsim_state *s, int k, const int *qubits, const doub
         QS_CUDA(launch_fused_simt(s, k, phys, m.data()));
         return QSIM_OK;
     }
-    if (prec != QSIM_PREC_3XTF32 && prec != QSIM_PREC_BF16X3) return fail(QSIM_E_INVAL, "unknown prec %d", prec);
+    if (prec != QSIM_PREC_3XTF32 && prec != QSIM_PREC_BF16X3 && prec != QSIM_PREC_BF16X6)
+        return fail(QSIM_E_INVAL, "unknown prec %d", prec);
     return apply_fused_tc(s, k, phys, m.data(), prec);
 }
 

@@ -86,7 +86,7 @@ qsim_status plan_upload(qsim_plan *P)
         if (bytes) memcpy(buf.data() + off, src, bytes);
         return off;
     };
-    const bool pipe = !P->tc_A.empty() && tc_pipe_eligible(P->n, (qsim_prec)P->prec);
+    const bool pipe = !P->tc_A.empty() && tc_pipe_eligible(P->n, P->dt, (qsim_prec)P->prec);
     std::vector<size_t> gt(P->tc_A.size(), 0);
     for (size_t i = 0; i < P->tc_A.size(); i++) {
         if (P->tc_pd_off[i].empty()) continue;
@@ -123,7 +123,7 @@ qsim_status plan_upload(qsim_plan *P)
         P->tc_pipe.resize(P->tc_A.size());
         for (size_t i = 0; i < P->tc_A.size(); i++) {
             const void *g = P->tc_pd_off[i].empty() ? nullptr : (const void *)((unsigned char *)P->dmem + gt[i]);
-            QS_TRY(tc_pipe_prepare(P->n, P->tc_spec[i], g, P->tc_pipe[i]));
+            QS_TRY(tc_pipe_prepare(P->n, P->tc_spec[i], g, P->tc_pipe[i], P->dt == QSIM_C128));
         }
     }
     return QSIM_OK;
@@ -189,9 +189,16 @@ static qsim_status plan_create_impl(const qsim_circuit *c, qsim_dtype dt, const 
     qsim_plan *P = new qsim_plan();
     qsim_status st;
     if (opts && opts->prec != QSIM_PREC_NATIVE) {
-        if (opts->prec != QSIM_PREC_3XTF32 && opts->prec != QSIM_PREC_BF16X3) st = fail(QSIM_E_INVAL, "unknown prec");
-        else if (dt != QSIM_C64) st = fail(QSIM_E_UNSUPPORTED, "tensor-core plans take complex64 kets");
-        else st = plan_build_tc(c, opts, start, P);
+        if (opts->prec != QSIM_PREC_3XTF32 && opts->prec != QSIM_PREC_BF16X3 && opts->prec != QSIM_PREC_BF16X6)
+            st = fail(QSIM_E_INVAL, "unknown prec");
+        else if (dt == QSIM_C64 && opts->prec == QSIM_PREC_BF16X6)
+            st = fail(QSIM_E_UNSUPPORTED, "BF16X6 plans take complex128 kets");
+        else if (dt == QSIM_C128 && !tc_pipe_eligible(c->n, dt, (qsim_prec)opts->prec))
+            st = fail(QSIM_E_UNSUPPORTED, "complex128 tensor-core plans take BF16X6 and n >= 13");
+        else {
+            st = plan_build_tc(c, opts, start, P);
+            P->dt = dt;
+        }
     } else {
         st = plan_build(c, dt, opts, start, P);
     }
@@ -306,8 +313,8 @@ qsim_status qsim_plan_execute_norm(qsim_state *s, const qsim_plan *p, double *no
 {
     clear_error();
     if (!norm) return fail(QSIM_E_INVAL, "norm is NULL");
-    const bool fused = p && !p->steps.empty() && p->steps.back().kind == 3 && !p->tc_pipe.empty() &&
-                       s && s->dt == QSIM_C64;
+    if (p && !p->dmem && (!p->passes.empty() || !p->tc_A.empty())) QS_TRY(plan_upload(const_cast<qsim_plan *>(p)));
+    const bool fused = p && !p->steps.empty() && p->steps.back().kind == 3 && !p->tc_pipe.empty() && s;
     if (!fused) {
         QS_TRY(plan_execute_impl(s, p, nullptr));
         return qsim_norm(s, norm);

@@ -258,50 +258,49 @@ __global__ void __launch_bounds__(kTcThreads, PREC == 1 ? 1 : 2) k_tc_block(floa
 
 // Host side: pads the block to 6 qubits (identity on the highest unused
 // qubits, which keeps the low qubits outside the block so consecutive groups
-// are consecutive amplitudes), forms A = [[Re U, -Im U], [Im U, Re U]]
-// interleaved, and splits it into hi / lo parts in the kernel's byte layout.
+// are consecutive amplitudes), orders the 6 block bits by qubit (U permuted
+// to match: the block's low qubits are its low index bits, its high qubits
+// the high ones), forms A = [[Re U, -Im U], [Im U, Re U]] interleaved, and
+// splits it into parts in the kernel's byte layout: TF32 hi / lo (3XTF32),
+// BF16 hi / lo (BF16X3), or three BF16 slices of the FP64 value (BF16X6).
 qsim_status tc_build(int n, int k, const int *phys, const cd *u, qsim_prec prec, std::vector<unsigned char> &A,
                      TcSpec &ts)
 {
     if (k > 6) return fail(QSIM_E_UNSUPPORTED, "tensor-core blocks take k <= 6 (M = 128)");
     if (n < 6) return fail(QSIM_E_UNSUPPORTED, "tensor-core blocks need n >= 6");
-    // block bits in ascending qubit order (u permuted to match): the
-    // block's low qubits are then its low index bits
-    int q[6];
+    int q0[6];
     uint64_t used = 0;
-    int order[6];
-    for (int b = 0; b < k; b++) order[b] = b;
-    std::sort(order, order + k, [&](int x, int y) { return phys[x] < phys[y]; });
     for (int b = 0; b < k; b++) {
-        q[b] = phys[order[b]];
+        q0[b] = phys[b];
         used |= bit(phys[b]);
-    }
-    std::vector<cd> us((size_t)(1 << k) << k);
-    {
-        const int D = 1 << k;
-        auto old_index = [&](int r) {
-            int o = 0;
-            for (int j = 0; j < k; j++)
-                if ((r >> j) & 1) o |= 1 << order[j];
-            return o;
-        };
-        for (int r = 0; r < D; r++)
-            for (int c = 0; c < D; c++) us[(size_t)r * D + c] = u[(size_t)old_index(r) * D + old_index(c)];
-        u = us.data();
     }
     int kk = k;
     for (int p = n - 1; p >= 0 && kk < 6; p--)
         if (!(used & bit(p))) {
-            q[kk++] = p;
+            q0[kk++] = p;
             used |= bit(p);
         }
+    // new bit b <-> old bit order[b], ascending qubits
+    int order[6], q[6];
+    for (int b = 0; b < 6; b++) order[b] = b;
+    std::sort(order, order + 6, [&](int x, int y) { return q0[x] < q0[y]; });
+    for (int b = 0; b < 6; b++) q[b] = q0[order[b]];
+    auto old_index = [&](int r) {
+        int o = 0;
+        for (int j = 0; j < 6; j++)
+            if ((r >> j) & 1) o |= 1 << order[j];
+        return o;
+    };
     const int D = 1 << k;
     const int es = prec == QSIM_PREC_3XTF32 ? 4 : 2;
+    const int nparts = prec == QSIM_PREC_BF16X6 ? 3 : 2;
     const size_t abytes = (size_t)kTcRows * kTcRows * es;
-    A.assign(2 * abytes, 0);
+    A.assign((size_t)nparts * abytes, 0);
     for (int r = 0; r < 64; r++)
         for (int c = 0; c < 64; c++) {
-            cd v = ((r >> k) == (c >> k)) ? u[(r & (D - 1)) * D + (c & (D - 1))] : cd(0.0);
+            // padded 64 x 64 block in the old bit order: identity on bits >= k
+            const int ro = old_index(r), co = old_index(c);
+            cd v = ((ro >> k) == (co >> k)) ? u[(ro & (D - 1)) * D + (co & (D - 1))] : cd(0.0);
             double e[2][2] = {{v.real(), -v.imag()}, {v.imag(), v.real()}};
             for (int ri = 0; ri < 2; ri++)
                 for (int ci = 0; ci < 2; ci++) {
@@ -318,6 +317,14 @@ qsim_status tc_build(int n, int k, const int *phys, const cd *u, qsim_prec prec,
                         float lo = x - hf;
                         memcpy(A.data() + off, &h, 4);
                         memcpy(A.data() + abytes + off, &lo, 4);
+                    } else if (nparts == 3) {
+                        // slices of the FP64 value: each takes the remainder of the ones before
+                        double rem = e[ri][ci];
+                        for (int sl = 0; sl < 3; sl++) {
+                            __nv_bfloat16 h = __float2bfloat16_rn((float)rem);
+                            rem -= (double)__bfloat162float(h);
+                            memcpy(A.data() + (size_t)sl * abytes + off, &h, 2);
+                        }
                     } else {
                         __nv_bfloat16 h = __float2bfloat16_rn(x);
                         float hf = __bfloat162float(h);
@@ -327,11 +334,9 @@ qsim_status tc_build(int n, int k, const int *phys, const cd *u, qsim_prec prec,
                     }
                 }
         }
-    std::vector<int> pos(q, q + 6);
-    std::sort(pos.begin(), pos.end());
     for (int b = 0; b < 6; b++) ts.q[b] = q[b];
     ts.ins.npos = 6;
-    for (int b = 0; b < 6; b++) ts.ins.pos[b] = pos[b];
+    for (int b = 0; b < 6; b++) ts.ins.pos[b] = q[b];
     ts.pd_off = nullptr;
     ts.pd_bit = nullptr;
     ts.pd_tw = nullptr;
@@ -373,7 +378,10 @@ cudaError_t tc_launch(qsim_state *s, const TcSpec &ts, const unsigned char *dA, 
 
 qsim_status apply_fused_tc(qsim_state *s, int k, const int *phys, const cd *u, qsim_prec prec)
 {
-    if (s->dt != QSIM_C64) return fail(QSIM_E_UNSUPPORTED, "tensor-core blocks take complex64 kets");
+    if (s->dt == QSIM_C64 && prec == QSIM_PREC_BF16X6)
+        return fail(QSIM_E_UNSUPPORTED, "BF16X6 blocks take complex128 kets");
+    if (s->dt == QSIM_C128 && !tc_pipe_eligible(s->n, s->dt, prec))
+        return fail(QSIM_E_UNSUPPORTED, "complex128 kets take BF16X6 tensor-core blocks with n >= 13");
     std::vector<unsigned char> A;
     TcSpec ts;
     QS_TRY(tc_build(s->n, k, phys, u, prec, A, ts));
@@ -384,9 +392,9 @@ qsim_status apply_fused_tc(qsim_state *s, int k, const int *phys, const cd *u, q
     QS_CUDA(cudaMemsetAsync(derr, 0, sizeof(int), s->stream));
     QS_CUDA(cudaMemcpyAsync(dA, A.data(), A.size(), cudaMemcpyHostToDevice, s->stream));
     cudaError_t e;
-    if (tc_pipe_eligible(s->n, prec)) {
+    if (tc_pipe_eligible(s->n, s->dt, prec)) {
         TcPipeHost H;
-        qsim_status st = tc_pipe_prepare(s->n, ts, nullptr, H);
+        qsim_status st = tc_pipe_prepare(s->n, ts, nullptr, H, s->dt == QSIM_C128);
         e = st == QSIM_OK ? tc_pipe_launch(s, H, dA, derr) : cudaErrorInvalidValue;
     } else {
         e = tc_launch(s, ts, dA, prec, derr);

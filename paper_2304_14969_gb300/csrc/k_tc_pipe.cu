@@ -20,11 +20,23 @@
 //            consecutive groups, so stores are coalesced when the low
 //            qubits are outside the block).
 //
-// Stage s is reloaded once the MMAs that read it have completed; TMEM
-// accumulator b is reused once the write-back of the tile before has read
-// it. Every wait is bounded; a wait that gives up sets the error word and
-// every role leaves its loop (loads still in flight are waited for, with a
-// bound, before the CTA exits).
+// Stage s is reloaded once the converters have read it; TMEM accumulator b
+// is reused once the write-back of the tile before has read it. Every wait
+// is bounded; a wait that gives up sets the error word and every role
+// leaves its loop (loads still in flight are waited for, with a bound,
+// before the CTA exits).
+//
+// Complex128 kets (W = true, BF16X6): the tile is the same 128 x 64
+// amplitudes but 128 KB, so it is loaded as four 32 KB quarter tiles (one
+// per value of the tile's two highest qubits) into a ring of three stages;
+// the four converter warps whose amplitudes lie in a quarter read it. A
+// converter rounds each FP64 amplitude to FP32 (integer arithmetic on the
+// IEEE encodings: FP64 instructions are scarce on this part), applies the
+// phases in FP32 and writes three BF16 slices (24 bits) into the one TMEM
+// A buffer (3 x 64 columns; two accumulators take the other 256). The MMA
+// warp issues the six slice products a_i u_j with i + j <= 2, smallest
+// first; the write-back widens FP32 to FP64 exactly and stores 16 bytes
+// per amplitude. Shared memory: U slices 96 KB + 3 x 32 KB stages.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -45,10 +57,48 @@ constexpr int kPConv = 32 * kPConvWarps;
 constexpr int kPEpiWarps = 4;                // write-back warps (18 .. 21), one per TMEM lane quarter
 constexpr int kPEpi = 32 * kPEpiWarps;
 constexpr int kPThreads = 64 + kPConv + kPEpi;
-constexpr uint32_t kPStage = 65536;          // one tile of complex64
-constexpr uint32_t kPHalf = 32768;           // hi or lo BF16 operand of a tile (128 x 128)
-constexpr uint32_t kPU = 65536;              // U hi + lo
-constexpr size_t kPSmem = kPU + 2 * (size_t)kPStage + 1024;
+constexpr uint32_t kPHalf = 32768;           // one BF16 operand part of 128 x 128
+// per amplitude width: stage bytes, stages, U parts, loads per tile
+template <bool W> struct PipeCfg {
+    static constexpr uint32_t kStage = W ? 32768u : 65536u;   // a quarter tile of complex128 / a tile of complex64
+    static constexpr int kNStage = W ? 3 : 2;
+    static constexpr int kParts = W ? 3 : 2;                   // BF16 parts of U (and of A)
+    static constexpr uint32_t kU = kParts * kPHalf;
+    static constexpr int kQ = W ? 4 : 1;                       // loads per tile
+    // full / free barrier pairs: load m signals full[m % kNBar]. Complex128
+    // gives each quarter its own pair (load m is quarter m % 4), so every
+    // waiter sees a barrier's completions one by one in order; a barrier
+    // shared by loads of different quarters would be waited on for its
+    // second completion before its first (a parity wait cannot tell them
+    // apart).
+    static constexpr int kNBar = W ? 4 : 2;
+    static constexpr size_t kSmem = kU + (size_t)kNStage * kStage + 1024;
+};
+static_assert(PipeCfg<false>::kSmem == PipeCfg<true>::kSmem, "one shared-memory size for both widths");
+constexpr size_t kPSmem = PipeCfg<false>::kSmem;
+
+// IEEE binary64 -> binary32, round to nearest (ties away from zero), on the
+// encodings: magnitudes below 2^-126 become signed zero, at or above 2^128
+// infinity.
+__device__ __forceinline__ float f64_to_f32_rn(double x)
+{
+    const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+    const uint32_t e = (hi >> 20) & 0x7ffu, sg = hi & 0x80000000u;
+    uint32_t f = sg | ((e - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+    f += (lo >> 28) & 1u;   // a carry into the exponent field is the correct rounding
+    f = e > 896u ? f : sg;
+    return __uint_as_float(e < 1151u ? f : (sg | 0x7f800000u));
+}
+
+// IEEE binary32 -> binary64 (exact) on the encodings; binary32 subnormals
+// (below 2^-126) become signed zero.
+__device__ __forceinline__ double f32_to_f64(uint32_t f)
+{
+    const uint32_t e = (f >> 23) & 0xffu;
+    const uint32_t hi = (f & 0x80000000u) | (e ? (((e + 896u) << 20) | ((f >> 3) & 0xfffffu)) : 0u);
+    const uint32_t lo = e ? (f << 29) : 0u;
+    return __hiloint2double((int)hi, (int)lo);
+}
 
 
 __device__ __forceinline__ uint64_t tile_base(const TcPipeArgs &P, uint64_t t)
@@ -68,18 +118,33 @@ __device__ __forceinline__ void turns_sincos(uint64_t tt, float &s, float &c)
     sincospif(2.0f * f, &s, &c);
 }
 
+// TMEM column of the A part and index of the U part of product p: complex64
+// a0 u0, a0 u1, a1 u0 (parts at +0, +64); complex128 a1 u1, a0 u2, a2 u0,
+// a0 u1, a1 u0, a0 u0 (slices at +0, +64, +128; the smallest first)
+template <bool W>
+__device__ __forceinline__ uint32_t prod_a(int p)
+{
+    return W ? (p == 0 || p == 4 ? 64u : p == 2 ? 128u : 0u) : (p == 2 ? 64u : 0u);
+}
+template <bool W>
+__device__ __forceinline__ uint32_t prod_u(int p)
+{
+    return W ? (p == 0 || p == 3 ? 1u : p == 1 ? 2u : 0u) : (p == 1 ? 1u : 0u);
+}
+
 // G = false: one block over one ket, CTAs stride over its tiles (the
-// tensor map, geometry, ket and U come as parameters). G = true: grouped
-// (batched circuits): CTA i takes work entry i, a range of tiles of the
-// block that descs[works[i].desc] describes, and stamps the circuit's first
-// load and last store with %globaltimer.
-template <bool G>
+// tensor map, geometry, ket and U come as parameters). G = true (complex64
+// only): grouped (batched circuits): CTA i takes work entry i, a range of
+// tiles of the block that descs[works[i].desc] describes, and stamps the
+// circuit's first load and last store with %globaltimer. W: complex128 ket.
+template <bool G, bool W>
 __global__ void __launch_bounds__(kPThreads, 1)
     k_tc_pipe(const __grid_constant__ CUtensorMap tmap_param, const __grid_constant__ TcPipeArgs P_param,
-              float2 *__restrict__ a_param, const unsigned char *__restrict__ Ug_param, int *err,
+              void *__restrict__ a_param, const unsigned char *__restrict__ Ug_param, int *err,
               const TcBatchDesc *__restrict__ descs, const TcWork *__restrict__ works, unsigned long long *t0s,
               unsigned long long *t1s, double *norm_out)
 {
+    using Cfg = PipeCfg<W>;
     extern __shared__ unsigned char sm_dyn[];
     __shared__ __align__(16) TcPipeArgs s_P;
     const TcBatchDesc *desc = G ? &descs[works[blockIdx.x].desc] : nullptr;
@@ -91,15 +156,15 @@ __global__ void __launch_bounds__(kPThreads, 1)
     __syncthreads();
     const TcPipeArgs &P = s_P;
     const void *tmap = G ? (const void *)desc->tmap : (const void *)&tmap_param;
-    float2 *__restrict__ a = G ? desc->amps : a_param;
+    void *__restrict__ a = G ? (void *)desc->amps : a_param;
     const unsigned char *__restrict__ Ug = G ? desc->U : Ug_param;
     const uint64_t wtile0 = G ? works[blockIdx.x].tile0 : 0, wntiles = G ? works[blockIdx.x].ntiles : 0;
     // tile of this CTA's j-th iteration
     auto tile_of = [&](uint64_t j) -> uint64_t { return G ? wtile0 + j : blockIdx.x + j * gridDim.x; };
     unsigned char *smb = (unsigned char *)(((uintptr_t)sm_dyn + 1023) & ~(uintptr_t)1023);
-    unsigned char *Us = smb;                              // U operand (N x K): hi [0, 32K), lo [32K, 64K)
-    unsigned char *St = smb + kPU;                        // raw stages 0 and 1
-    __shared__ __align__(8) uint64_t bar_full[2], bar_sfree[2], bar_aready[2], bar_mma[2], bar_accf[2];
+    unsigned char *Us = smb;                              // U operand (N x K): kParts parts of 32 KB
+    unsigned char *St = smb + Cfg::kU;                    // raw stages
+    __shared__ __align__(8) uint64_t bar_full[4], bar_sfree[4], bar_aready[2], bar_mma[2], bar_accf[2];
     __shared__ uint32_t s_tmem;
     __shared__ int s_abort;
     __shared__ uint16_t s_posL[64];
@@ -121,18 +186,21 @@ __global__ void __launch_bounds__(kPThreads, 1)
     {
         const int4 *src = (const int4 *)Ug;
         int4 *dst = (int4 *)Us;
-        for (uint32_t i = tid; i < kPU / 16; i += kPThreads) dst[i] = src[i];
+        for (uint32_t i = tid; i < Cfg::kU / 16; i += kPThreads) dst[i] = src[i];
     }
     if (tid == 0) {
         s_abort = 0;
-        for (int s = 0; s < 2; s++) {
+        for (int s = 0; s < Cfg::kNBar; s++) {
             // with deferred phases the producer arrives a second time once the
             // tile factors are written
             mbar_init(smem_addr(&bar_full[s]), has_pd ? 2 : 1);
-            mbar_init(smem_addr(&bar_sfree[s]), kPConv);
-            mbar_init(smem_addr(&bar_aready[s]), kPConv);
-            mbar_init(smem_addr(&bar_mma[s]), 1);
-            mbar_init(smem_addr(&bar_accf[s]), kPEpi);
+            // a complex128 quarter tile is read by the four warps it belongs to
+            mbar_init(smem_addr(&bar_sfree[s]), W ? kPConv / 4 : kPConv);
+        }
+        for (int b = 0; b < 2; b++) {
+            mbar_init(smem_addr(&bar_aready[b]), kPConv);
+            mbar_init(smem_addr(&bar_mma[b]), 1);
+            mbar_init(smem_addr(&bar_accf[b]), kPEpi);
         }
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
@@ -145,8 +213,9 @@ __global__ void __launch_bounds__(kPThreads, 1)
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
-    // TMEM columns: accumulators [0, 128) and [128, 256); A operands (hi, lo:
-    // 64 + 64 columns, BF16 pairs) [256, 384) and [384, 512)
+    // TMEM columns: accumulators [0, 128) and [128, 256); complex64: A
+    // operands (hi, lo: 64 + 64 columns, BF16 pairs) [256, 384) and
+    // [384, 512); complex128: one A operand (three slices) [256, 448)
     const uint32_t tmem = s_tmem;
     volatile int *abort_flag = &s_abort;
     auto give_up = [&]() {
@@ -159,49 +228,62 @@ __global__ void __launch_bounds__(kPThreads, 1)
 
     if (warp == 0) {
         // ---------------- TMA producer (lane 0) and tile factors of the
-        // deferred phases (lanes 0..5): stage s is reloaded once the
-        // converters have read the tile two before
-        uint64_t issued = 0;
-        for (uint64_t j = 0; j < J; j++) {
-            const int s = (int)(j & 1);
-            int stop = 0;
-            if (lane == 0) {
-                const bool ok = j < 2 ||
-                                mbar_wait_or_abort(smem_addr(&bar_sfree[s]), (uint32_t)(((j - 2) >> 1) & 1), abort_flag);
-                if (!ok) give_up();
-                stop = !ok || *abort_flag;
-            }
-            if (__shfl_sync(0xffffffffu, stop, 0)) break;
+        // deferred phases (lanes 0..5): load m goes to stage m mod kNStage,
+        // once the converters have read load m - kNStage, and signals
+        // full[m mod kNBar]
+        uint32_t m = 0;   // loads issued
+        bool quit = false;
+        for (uint64_t j = 0; j < J && !quit; j++) {
             const uint64_t t = tile_of(j);
-            const uint32_t fb = smem_addr(&bar_full[s]);
-            if (lane == 0) {
-                const uint64_t base = tile_base(P, t);
-                int c[5];
-#pragma unroll
-                for (int d = 0; d < 5; d++) c[d] = (int)((base >> P.dim_lo[d]) & ((1ull << P.dim_bits[d]) - 1));
-                mbar_arrive_expect_tx(fb, P.box_bytes * (uint32_t)P.nload);
-                const uint32_t dst = smem_addr(St + (size_t)s * kPStage);
-                for (int v = 0; v < P.nload; v++)
-                    tma_load_5d(dst + (uint32_t)v * P.box_bytes, tmap, fb, c[0], c[1], c[2], c[3], c[4] + P.xoff[v]);
-            }
-            if (has_pd) {
-                if (lane < 6) {
-                    uint64_t tt = 0;
-                    for (int i = 0; i < P.ntb; i++)
-                        if ((t >> i) & 1) tt += s_tturn[lane * 24 + i];
-                    float sn, cs;
-                    turns_sincos(tt, sn, cs);
-                    s_E[j & 3][lane] = make_float2(cs, sn);
+            const uint64_t base = tile_base(P, t);
+            for (int q = 0; q < Cfg::kQ; q++, m++) {
+                const int s = (int)(m % Cfg::kNStage);
+                int stop = 0;
+                if (lane == 0) {
+                    const uint32_t r = m - Cfg::kNStage;   // the load stage s held before
+                    const bool ok = m < (uint32_t)Cfg::kNStage ||
+                                    mbar_wait_or_abort(smem_addr(&bar_sfree[r % Cfg::kNBar]), (r / Cfg::kNBar) & 1u,
+                                                       abort_flag);
+                    if (!ok) give_up();
+                    stop = !ok || *abort_flag;
                 }
-                __syncwarp();
-                if (lane == 0) mbar_arrive(fb);
+                quit = __shfl_sync(0xffffffffu, stop, 0) != 0;
+                if (quit) break;
+                const uint32_t fb = smem_addr(&bar_full[m % Cfg::kNBar]);
+                if (lane == 0) {
+                    uint64_t bq = base;
+                    if (W) bq |= ((uint64_t)(q & 1) << P.tpos[11]) | ((uint64_t)(q >> 1) << P.tpos[12]);
+                    int c[5];
+#pragma unroll
+                    for (int d = 0; d < 5; d++) c[d] = (int)((bq >> P.dim_lo[d]) & ((1ull << P.dim_bits[d]) - 1));
+                    if (W) c[0] <<= 1;   // dimension 0 counts the 8-byte halves of an amplitude
+                    mbar_arrive_expect_tx(fb, P.box_bytes * (uint32_t)P.nload);
+                    const uint32_t dst = smem_addr(St + (size_t)s * Cfg::kStage);
+                    for (int v = 0; v < P.nload; v++)
+                        tma_load_5d(dst + (uint32_t)v * P.box_bytes, tmap, fb, c[0], c[1], c[2], c[3], c[4] + P.xoff[v]);
+                }
+                if (has_pd) {
+                    if (q == 0) {
+                        if (lane < 6) {
+                            uint64_t tt = 0;
+                            for (int i = 0; i < P.ntb; i++)
+                                if ((t >> i) & 1) tt += s_tturn[lane * 24 + i];
+                            float sn, cs;
+                            turns_sincos(tt, sn, cs);
+                            s_E[j & 3][lane] = make_float2(cs, sn);
+                        }
+                        __syncwarp();
+                    }
+                    if (lane == 0) mbar_arrive(fb);
+                }
             }
-            issued = j + 1;
         }
-        // loads still in flight (only after an abort) land before the CTA exits
+        // loads still in flight (only after an abort) land before the CTA
+        // exits; the loads before them have been read, so these waits see
+        // each barrier's completions in order
         if (lane == 0)
-            for (uint64_t j = issued >= 2 ? issued - 2 : 0; j < issued; j++)
-                mbar_wait(smem_addr(&bar_full[j & 1]), (uint32_t)((j >> 1) & 1));
+            for (uint32_t x = m >= (uint32_t)Cfg::kNStage ? m - Cfg::kNStage : 0; x < m; x++)
+                mbar_wait(smem_addr(&bar_full[x % Cfg::kNBar]), (x / Cfg::kNBar) & 1u);
     } else if (warp == 1) {
         // ---------------- MMA issue: D[g][n] = sum_k A[g][k] U[n][k], A in TMEM
         if (lane == 0) {
@@ -211,7 +293,9 @@ __global__ void __launch_bounds__(kPThreads, 1)
             uint64_t issued = 0;
             for (uint64_t j = 0; j < J && !*abort_flag; j++) {
                 const int b = (int)(j & 1);
-                if (!mbar_wait_or_abort(smem_addr(&bar_aready[b]), (uint32_t)((j >> 1) & 1), abort_flag)) {
+                // complex64: A operand b, its (j >> 1)-th fill; complex128: the one A operand, its j-th
+                if (!mbar_wait_or_abort(smem_addr(&bar_aready[W ? 0 : b]),
+                                        W ? (uint32_t)(j & 1) : (uint32_t)((j >> 1) & 1), abort_flag)) {
                     give_up();
                     break;
                 }
@@ -222,12 +306,12 @@ __global__ void __launch_bounds__(kPThreads, 1)
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 const uint32_t d = tmem + (uint32_t)b * 128u;
-                const uint32_t ah = tmem + 256u + (uint32_t)b * 128u, al = ah + 64u;
-                const uint32_t uh = smem_addr(Us), ul = uh + kPHalf;
+                const uint32_t a0 = tmem + 256u + (W ? 0u : (uint32_t)b * 128u);
+                const uint32_t u0 = smem_addr(Us);
                 uint32_t accum = 0;
-#pragma unroll 1
-                for (int part = 0; part < 3; part++) {
-                    const uint32_t abase = part == 2 ? al : ah, bbase = part == 1 ? ul : uh;
+#pragma unroll
+                for (int p = 0; p < (W ? 6 : 3); p++) {
+                    const uint32_t abase = a0 + prod_a<W>(p), bbase = u0 + prod_u<W>(p) * kPHalf;
 #pragma unroll
                     for (int kk = 0; kk < 8; kk++) {
                         // K step of 16 BF16 = 8 TMEM columns of A, two core matrices of U
@@ -245,37 +329,68 @@ __global__ void __launch_bounds__(kPThreads, 1)
     } else if (warp < 2 + kPConvWarps) {
         // ---------------- convert (warps 2..17). A thread owns one group (its
         // TMEM lane) and 16 of its 64 amplitudes, l = 16 part + i. The stage
-        // is released as soon as it has been read: with two stages, the time
-        // a landed tile waits to be read is what bounds the load pipeline.
+        // is released as soon as it has been read: the time a landed tile
+        // waits to be read is what bounds the load pipeline.
         const int ct = tid - 64, cw = ct >> 5;
         const int quarter = warp & 3, part = cw >> 2;
         const int g = 32 * quarter + lane;
         const uint32_t lane_off = (uint32_t)(32 * quarter) << 16;
-        const uint32_t offG = 8u * P.posG[g];
-        const int rot = P.rot_bits ? (lane >> (4 - P.rot_bits)) & ((1 << P.rot_bits) - 1) : 0;
+        const int rot = P.rot_bits ? (lane >> (P.rot_shift - P.rot_bits)) & ((1 << P.rot_bits) - 1) : 0;
+        // complex128: the quarter tile holding this thread's amplitudes (the
+        // bits of tpos[11], tpos[12] among its group and part bits)
+        int qi = 0;
+        if (W) {
+#pragma unroll
+            for (int i = 0; i < 2; i++) {
+                const int code = P.qsel[i];
+                qi |= (code < 2 ? (quarter >> code) & 1 : (part >> (code - 2)) & 1) << i;
+            }
+        }
         // in-stage byte offsets of this thread's reads (the same for every tile)
+        constexpr uint32_t kEsz = W ? 16u : 8u, kEmask = W ? 0x7ffu : 0x1fffu;
         uint32_t offL[16];
 #pragma unroll
-        for (int i = 0; i < 16; i++) offL[i] = offG + 8u * s_posL[16 * part + (i ^ rot)];
+        for (int i = 0; i < 16; i++) offL[i] = kEsz * ((uint32_t)(P.posG[g] | s_posL[16 * part + (i ^ rot)]) & kEmask);
 
         for (uint64_t j = 0; j < J; j++) {
-            const int s = (int)(j & 1), b = (int)(j & 1);
-            const bool ok = mbar_wait_or_abort(smem_addr(&bar_full[s]), (uint32_t)((j >> 1) & 1), abort_flag);
-            // one decision for all converter threads (none may be left at a barrier)
-            if (named_bar_or(1, kPConv, !ok || *abort_flag)) {
-                give_up();
-                break;
-            }
-            const unsigned char *stage = St + (size_t)s * kPStage;
+            const int b = (int)(j & 1);
+            const uint32_t m = W ? (uint32_t)(4 * j + qi) : (uint32_t)j;   // the load this thread reads
+            const int s = (int)(m % Cfg::kNStage), fbi = (int)(m % Cfg::kNBar);
+            const bool ok = mbar_wait_or_abort(smem_addr(&bar_full[fbi]), (m / Cfg::kNBar) & 1u, abort_flag);
+            const unsigned char *stage = St + (size_t)s * Cfg::kStage;
             float2 v[16];
-            // Block qubits among qubits 0..3 (block bits 0..rot_bits-1) would put
-            // the 16 lanes of a half-warp on one bank: each lane reads its
-            // amplitudes in an order XOR-rotated by its own lane bits, so every
-            // read instruction covers 16 distinct banks; v[] is put back in
-            // order below.
+            bool qbad = false;
+            // Block qubits among the lowest rot_shift qubits (block bits
+            // 0..rot_bits-1) would put the lanes sharing a shared-memory row
+            // on one bank group: each lane reads its amplitudes in an order
+            // XOR-rotated by its own lane bits, so every read instruction
+            // covers distinct banks; v[] is put back in order below.
+            if (!W) {
+                // one decision for all converter threads (none may be left at a barrier)
+                if (named_bar_or(1, kPConv, !ok || *abort_flag)) {
+                    give_up();
+                    break;
+                }
 #pragma unroll
-            for (int i = 0; i < 16; i++) v[i] = *(const float2 *)(stage + offL[i]);
-            mbar_arrive(smem_addr(&bar_sfree[s]));   // the stage may be reloaded
+                for (int i = 0; i < 16; i++) v[i] = *(const float2 *)(stage + offL[i]);
+                mbar_arrive(smem_addr(&bar_sfree[fbi]));   // the stage may be reloaded
+            } else {
+                // one decision per quarter tile (its four warps): the quarters
+                // land one after another, and a quarter's stage must be released
+                // before the next quarters can load
+                qbad = named_bar_or(3 + qi, kPConv / 4, !ok || *abort_flag);
+                if (!qbad) {
+#pragma unroll
+                    for (int i = 0; i < 16; i++) {
+                        const double2 x = *(const double2 *)(stage + offL[i]);
+                        v[i] = make_float2(f64_to_f32_rn(x.x), f64_to_f32_rn(x.y));
+                    }
+                    mbar_arrive(smem_addr(&bar_sfree[fbi]));
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 16; i++) v[i] = make_float2(0.f, 0.f);
+                }
+            }
 #pragma unroll
             for (int bb = 0; bb < 4; bb++) {
                 if (bb < P.rot_bits) {
@@ -295,9 +410,9 @@ __global__ void __launch_bounds__(kPThreads, 1)
                 float er[6], ei[6];
 #pragma unroll
                 for (int bb = 0; bb < 6; bb++) {
-                    const float2 E = s_E[j & 3][bb], G = s_gfac[g * 6 + bb];
-                    er[bb] = E.x * G.x - E.y * G.y;
-                    ei[bb] = E.x * G.y + E.y * G.x;
+                    const float2 E = s_E[j & 3][bb], F = s_gfac[g * 6 + bb];
+                    er[bb] = E.x * F.x - E.y * F.y;
+                    ei[bb] = E.x * F.y + E.y * F.x;
                 }
                 float fr = 1.f, fi = 0.f;
                 if (part & 1) {
@@ -316,9 +431,9 @@ __global__ void __launch_bounds__(kPThreads, 1)
 #pragma unroll
                 for (int bb = 0; bb < 4; bb++) {
 #pragma unroll
-                    for (int m = 0; m < (1 << bb); m++) {
-                        tr[m + (1 << bb)] = tr[m] * er[bb] - ti[m] * ei[bb];
-                        ti[m + (1 << bb)] = tr[m] * ei[bb] + ti[m] * er[bb];
+                    for (int mm = 0; mm < (1 << bb); mm++) {
+                        tr[mm + (1 << bb)] = tr[mm] * er[bb] - ti[mm] * ei[bb];
+                        ti[mm + (1 << bb)] = tr[mm] * ei[bb] + ti[mm] * er[bb];
                     }
                 }
 #pragma unroll
@@ -328,32 +443,58 @@ __global__ void __launch_bounds__(kPThreads, 1)
                     v[i].x = xr;
                 }
             }
-            // BF16 hi / lo split into A operand b (TMEM)
-            uint32_t hi[16], lo[16];
+            if (!W) {
+                // BF16 hi / lo split into A operand b (TMEM)
+                uint32_t hi[16], lo[16];
 #pragma unroll
-            for (int i = 0; i < 16; i++) {
-                const __nv_bfloat162 h = __floats2bfloat162_rn(v[i].x, v[i].y);
-                const float2 hf = __bfloat1622float2(h);
-                const __nv_bfloat162 l2 = __floats2bfloat162_rn(v[i].x - hf.x, v[i].y - hf.y);
-                hi[i] = *(const uint32_t *)&h;
-                lo[i] = *(const uint32_t *)&l2;
-            }
-            if (j >= 2) {
-                // A operand b was last read by the MMAs of tile j - 2
-                const bool ok2 =
-                    mbar_wait_or_abort(smem_addr(&bar_mma[b]), (uint32_t)(((j - 2) >> 1) & 1), abort_flag);
+                for (int i = 0; i < 16; i++) {
+                    const __nv_bfloat162 h = __floats2bfloat162_rn(v[i].x, v[i].y);
+                    const float2 hf = __bfloat1622float2(h);
+                    const __nv_bfloat162 l2 = __floats2bfloat162_rn(v[i].x - hf.x, v[i].y - hf.y);
+                    hi[i] = *(const uint32_t *)&h;
+                    lo[i] = *(const uint32_t *)&l2;
+                }
+                if (j >= 2) {
+                    // A operand b was last read by the MMAs of tile j - 2
+                    const bool ok2 =
+                        mbar_wait_or_abort(smem_addr(&bar_mma[b]), (uint32_t)(((j - 2) >> 1) & 1), abort_flag);
+                    if (named_bar_or(1, kPConv, !ok2 || *abort_flag)) {
+                        give_up();
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;");
+                }
+                const uint32_t acol = tmem + lane_off + 256u + (uint32_t)b * 128u + (uint32_t)(16 * part);
+                tmem_st16(acol, hi);
+                tmem_st16(acol + 64u, lo);
+            } else {
+                // the one A operand was last read by the MMAs of tile j - 1
+                const bool ok2 = !qbad && (j == 0 || mbar_wait_or_abort(smem_addr(&bar_mma[(j - 1) & 1]),
+                                                                        (uint32_t)(((j - 1) >> 1) & 1), abort_flag));
                 if (named_bar_or(1, kPConv, !ok2 || *abort_flag)) {
                     give_up();
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;");
+                // three BF16 slices, each of the remainder of the ones before
+                const uint32_t acol = tmem + lane_off + 256u + (uint32_t)(16 * part);
+#pragma unroll
+                for (int sl = 0; sl < 3; sl++) {
+                    uint32_t pk[16];
+#pragma unroll
+                    for (int i = 0; i < 16; i++) {
+                        const __nv_bfloat162 h = __floats2bfloat162_rn(v[i].x, v[i].y);
+                        const float2 hf = __bfloat1622float2(h);
+                        v[i].x -= hf.x;
+                        v[i].y -= hf.y;
+                        pk[i] = *(const uint32_t *)&h;
+                    }
+                    tmem_st16(acol + 64u * (uint32_t)sl, pk);
+                }
             }
-            const uint32_t acol = tmem + lane_off + 256u + (uint32_t)b * 128u + (uint32_t)(16 * part);
-            tmem_st16(acol, hi);
-            tmem_st16(acol + 64u, lo);
             tmem_wait_st();
             asm volatile("tcgen05.fence::before_thread_sync;");
-            mbar_arrive(smem_addr(&bar_aready[b]));
+            mbar_arrive(smem_addr(&bar_aready[W ? 0 : b]));
         }
     } else {
         // ---------------- write back (warps 18..21): TMEM lane = group,
@@ -372,7 +513,6 @@ __global__ void __launch_bounds__(kPThreads, 1)
             }
             asm volatile("tcgen05.fence::after_thread_sync;");
             const uint64_t base = tile_base(P, tile_of(j));
-            float2 *dstg = a + (base + spG);
 #pragma unroll 1
             for (int c0 = 0; c0 < 128; c0 += 32) {
                 uint32_t r[32];
@@ -385,14 +525,21 @@ __global__ void __launch_bounds__(kPThreads, 1)
                     nacc += (double)run;
                 }
                 const int l0 = c0 / 2;
-                if (P.vec2) {
+                if (W) {
+                    double2 *dstg = (double2 *)a + (base + spG);
+#pragma unroll
+                    for (int i = 0; i < 16; i++)
+                        dstg[s_spL[l0 + i]] = make_double2(f32_to_f64(r[2 * i]), f32_to_f64(r[2 * i + 1]));
+                } else if (P.vec2) {
                     // amplitudes l, l + 1 adjacent: one 16-byte store per pair
+                    float2 *dstg = (float2 *)a + (base + spG);
 #pragma unroll
                     for (int i = 0; i < 16; i += 2)
                         *(float4 *)(dstg + s_spL[l0 + i]) =
                             make_float4(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1]),
                                         __uint_as_float(r[2 * i + 2]), __uint_as_float(r[2 * i + 3]));
                 } else {
+                    float2 *dstg = (float2 *)a + (base + spG);
 #pragma unroll
                     for (int i = 0; i < 16; i++)
                         dstg[s_spL[l0 + i]] = make_float2(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1]));
@@ -460,8 +607,9 @@ static void tc_pipe_attrs()
 {
     static std::once_flag once;
     std::call_once(once, []() {
-        cudaFuncSetAttribute(k_tc_pipe<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPSmem);
-        cudaFuncSetAttribute(k_tc_pipe<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPSmem);
+        cudaFuncSetAttribute(k_tc_pipe<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPSmem);
+        cudaFuncSetAttribute(k_tc_pipe<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPSmem);
+        cudaFuncSetAttribute(k_tc_pipe<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPSmem);
     });
 }
 
@@ -471,8 +619,13 @@ cudaError_t tc_pipe_launch(qsim_state *s, const TcPipeHost &H, const unsigned ch
     if (tc_pipe_encode(H, s->amps, (unsigned char *)&tm) != QSIM_OK) return cudaErrorInvalidValue;
     tc_pipe_attrs();
     const int grid = (int)std::min<uint64_t>(H.args.ntiles, (uint64_t)num_sms());
-    k_tc_pipe<false><<<grid, kPThreads, kPSmem, s->stream>>>(tm, H.args, (float2 *)s->amps, dU, derr, nullptr, nullptr,
-                                                              nullptr, nullptr, norm_out);
+    if (H.args.wide != (s->dt == QSIM_C128)) return cudaErrorInvalidValue;
+    if (H.args.wide)
+        k_tc_pipe<false, true><<<grid, kPThreads, kPSmem, s->stream>>>(tm, H.args, s->amps, dU, derr, nullptr,
+                                                                        nullptr, nullptr, nullptr, norm_out);
+    else
+        k_tc_pipe<false, false><<<grid, kPThreads, kPSmem, s->stream>>>(tm, H.args, s->amps, dU, derr, nullptr,
+                                                                         nullptr, nullptr, nullptr, norm_out);
     return cudaGetLastError();
 }
 
@@ -485,7 +638,8 @@ cudaError_t tc_pipe_launch_grouped(const TcBatchDesc *descs, const TcWork *works
     memset(&tm, 0, sizeof tm);
     TcPipeArgs none;
     memset(&none, 0, sizeof none);
-    k_tc_pipe<true><<<nwork, kPThreads, kPSmem, st>>>(tm, none, nullptr, nullptr, err, descs, works, t0, t1, nullptr);
+    k_tc_pipe<true, false><<<nwork, kPThreads, kPSmem, st>>>(tm, none, nullptr, nullptr, err, descs, works, t0, t1,
+                                                              nullptr);
     return cudaGetLastError();
 }
 

@@ -95,14 +95,15 @@ qsim_status tc_build(int n, int k, const int *phys, const cd *u, qsim_prec prec,
                      TcSpec &ts);
 cudaError_t tc_launch(qsim_state *s, const TcSpec &ts, const unsigned char *dA, qsim_prec prec, int *derr);
 
-// Pipelined BF16x3 block kernel (n >= 13): tile geometry and tables, built
-// on the host per block (k_tc_pipe.cu).
+// Pipelined block kernel (BF16X3 on complex64, BF16X6 on complex128;
+// n >= 13): tile geometry and tables, built on the host per block
+// (k_tc_pipe.cu).
 struct TcPipeArgs {
     uint64_t ntiles;
     int tpos[13];            // tile qubits, ascending (tile index bits go to the other positions)
     int dim_lo[5];           // lowest qubit of each tensor dimension
     int dim_bits[5];         // qubits covered by each tensor dimension (coordinate width)
-    int nload;               // boxes per tile
+    int nload;               // boxes per tile (per quarter tile when wide)
     int xoff[4];             // coordinate offset along dimension 4 of box v
     uint32_t box_bytes;
     uint16_t posL[64];       // in-stage element index of block index l
@@ -112,6 +113,13 @@ struct TcPipeArgs {
     int ntb;                 // tile-index bits (n - 13)
     int rot_bits;            // block qubits among qubits 0..3 (= block index bits 0..rot_bits-1)
     int vec2;                // qubit 0 is block bit 0: amplitudes l, l + 1 (l even) are adjacent
+    int rot_shift;           // lanes sharing a shared-memory row: 2^rot_shift (4: 8-byte, 3: 16-byte amplitudes)
+    // complex128 kets (wide = 1): a tile is loaded as four quarter tiles,
+    // one per value of its two highest qubits tpos[11], tpos[12]; qsel[i]
+    // names the converter bit that carries tpos[11 + i] (0, 1: group bits
+    // 5, 6 = TMEM lane quarter bits; 2, 3: block bits 4, 5 = part bits)
+    int wide;
+    int qsel[2];
     // deferred phases (NULL if none): exp(2 pi i T_b) of block bit b for a
     // group is the product of a tile factor, from the turns tturn[b][i] of
     // the tile-index bits i, and the group factor gfac[g][b]
@@ -125,8 +133,9 @@ struct TcPipeHost {
     uint32_t box[5], estr[5];
     int freeq[7];
 };
-bool tc_pipe_eligible(int n, qsim_prec prec);
-qsim_status tc_pipe_prepare(int n, const TcSpec &ts, const void *pd_tables_dev, TcPipeHost &H);
+// complex64 with BF16X3, or complex128 with BF16X6; n >= 13
+bool tc_pipe_eligible(int n, qsim_dtype dt, qsim_prec prec);
+qsim_status tc_pipe_prepare(int n, const TcSpec &ts, const void *pd_tables_dev, TcPipeHost &H, bool wide = false);
 // Deferred-phase tables of a block (tturn then gfac, kTcPipeTableBytes).
 const size_t kTcPipeTableBytes = 6 * 24 * 8 + 128 * 6 * 8;
 void tc_pipe_tables(int n, const TcSpec &ts, const std::vector<int32_t> &off, const std::vector<int32_t> &pbit,
@@ -141,7 +150,7 @@ cudaError_t tc_pipe_launch(qsim_state *s, const TcPipeHost &H, const unsigned ch
 struct alignas(64) TcBatchDesc {
     unsigned char tmap[128];     // tensor map of the block over the circuit's ket
     TcPipeArgs args;
-    const unsigned char *U;      // BF16 hi / lo operand of the block (64 KB, device)
+    const unsigned char *U;      // BF16 hi / lo operand of the block (64 KB, device; complex64 kets only)
     float2 *amps;                // the circuit's ket (device)
     int circ;                    // circuit index (latency stamps)
 };

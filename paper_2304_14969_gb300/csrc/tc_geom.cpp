@@ -10,7 +10,10 @@
 
 namespace qs {
 
-bool tc_pipe_eligible(int n, qsim_prec prec) { return prec == QSIM_PREC_BF16X3 && n >= 13; }
+bool tc_pipe_eligible(int n, qsim_dtype dt, qsim_prec prec)
+{
+    return n >= 13 && ((dt == QSIM_C64 && prec == QSIM_PREC_BF16X3) || (dt == QSIM_C128 && prec == QSIM_PREC_BF16X6));
+}
 
 // Tile geometry of a block: tile qubits T = the block's 6 qubits and the 7
 // lowest qubits outside it; the tensor map views the ket as up to 5
@@ -18,7 +21,12 @@ bool tc_pipe_eligible(int n, qsim_prec prec) { return prec == QSIM_PREC_BF16X3 &
 // dimension) plus the non-tile qubits above it, so a box is exactly the
 // tile's amplitudes with the tile base's bits as coordinates. Runs beyond
 // the fifth become extra boxes along dimension 4.
-qsim_status tc_pipe_prepare(int n, const TcSpec &ts, const void *pd_tables_dev, TcPipeHost &H)
+//
+// wide (complex128, 16-byte amplitudes): the box is a quarter tile, the
+// tile qubits below its two highest (tpos[11], tpos[12]), which become
+// coordinates; dimension 0 counts 8-byte halves, so its run is at most 7
+// qubits (a box dimension spans at most 256 elements).
+qsim_status tc_pipe_prepare(int n, const TcSpec &ts, const void *pd_tables_dev, TcPipeHost &H, bool wide)
 {
     if (n < 13 || n > 36) return fail(QSIM_E_UNSUPPORTED, "pipelined tensor-core blocks need 13 <= n <= 36");
     uint64_t blk = 0;
@@ -29,10 +37,14 @@ qsim_status tc_pipe_prepare(int n, const TcSpec &ts, const void *pd_tables_dev, 
     std::vector<int> T;
     for (int p = 0; p < n; p++)
         if ((blk & bit(p)) || std::find(freeq.begin(), freeq.end(), p) != freeq.end()) T.push_back(p);
-    // chunks of consecutive tile qubits, at most 8 each
+    const int es = wide ? 16 : 8;                   // bytes per amplitude
+    const int nbox = wide ? 11 : 13;                 // tile qubits a box covers
+    // chunks of consecutive box qubits, at most 8 each (7 for dimension 0 when wide)
     std::vector<std::pair<int, int>> ch;   // (first qubit, length)
-    for (int p : T) {
-        if (!ch.empty() && ch.back().first + ch.back().second == p && ch.back().second < 8)
+    for (int j = 0; j < nbox; j++) {
+        const int p = T[j];
+        const int cap = (wide && ch.size() == 1) ? 7 : 8;
+        if (!ch.empty() && ch.back().first + ch.back().second == p && ch.back().second < cap)
             ch.back().second++;
         else
             ch.push_back({p, 1});
@@ -51,8 +63,8 @@ qsim_status tc_pipe_prepare(int n, const TcSpec &ts, const void *pd_tables_dev, 
             const int hi = (d + 1 < nd) ? ch[d + 1].first : n;
             A.dim_lo[d] = lo;
             A.dim_bits[d] = hi - lo;
-            gdim[d] = 1ull << (hi - lo);
-            box[d] = 1u << ch[d].second;
+            gdim[d] = (d == 0 && wide ? 2ull : 1ull) << (hi - lo);
+            box[d] = (d == 0 && wide ? 2u : 1u) << ch[d].second;
             boxbits += ch[d].second;
         } else {
             A.dim_lo[d] = n;
@@ -60,13 +72,13 @@ qsim_status tc_pipe_prepare(int n, const TcSpec &ts, const void *pd_tables_dev, 
             gdim[d] = 1;
             box[d] = 1;
         }
-        if (d >= 1) gstr[d - 1] = (d < nd) ? (uint64_t)8 << A.dim_lo[d] : (uint64_t)8 << n;
+        if (d >= 1) gstr[d - 1] = (uint64_t)es << ((d < nd) ? A.dim_lo[d] : n);
     }
     // extra boxes enumerate the qubits of chunks 5.. (inside dimension 4)
     std::vector<int> xq;
     for (size_t c = 5; c < ch.size(); c++)
         for (int i = 0; i < ch[c].second; i++) xq.push_back(ch[c].first + i);
-    if ((int)xq.size() > 2 || boxbits + (int)xq.size() != 13)
+    if ((int)xq.size() > 2 || boxbits + (int)xq.size() != nbox)
         return fail(QSIM_E_UNSUPPORTED, "tensor-core tile geometry not covered (%d extra qubits)", (int)xq.size());
     A.nload = 1 << xq.size();
     for (int v = 0; v < A.nload; v++) {
@@ -75,7 +87,7 @@ qsim_status tc_pipe_prepare(int n, const TcSpec &ts, const void *pd_tables_dev, 
             if ((v >> i) & 1) off |= 1 << (xq[i] - A.dim_lo[4]);
         A.xoff[v] = off;
     }
-    A.box_bytes = (uint32_t)(8u << boxbits);
+    A.box_bytes = (uint32_t)es << boxbits;
     auto rank = [&](int q) { return (int)(std::find(T.begin(), T.end(), q) - T.begin()); };
     for (int l = 0; l < 64; l++) {
         int r = 0;
@@ -100,13 +112,31 @@ qsim_status tc_pipe_prepare(int n, const TcSpec &ts, const void *pd_tables_dev, 
         A.spG[g] = o;
     }
     A.ntb = n - 13;
-    // tile qubits 0..3 are the in-stage bits 0..3 (the tile holds qubits
-    // 0..3: each is a block qubit or one of the lowest outside ones)
+    // tile qubits 0..rot_shift-1 are the in-stage bits 0..rot_shift-1 (the
+    // tile holds the lowest qubits: each is a block qubit or one of the
+    // lowest outside ones); one shared-memory row holds 2^rot_shift amplitudes
+    A.rot_shift = wide ? 3 : 4;
     A.rot_bits = 0;
-    for (int b = 0; b < 6; b++) A.rot_bits += ts.q[b] < 4;
-    for (int b = 0; b < A.rot_bits; b++)
-        if (ts.q[b] >= 4) return fail(QSIM_E_UNSUPPORTED, "tensor-core block bits not in ascending qubit order");
-    A.vec2 = ts.q[0] == 0;
+    for (int b = 0; b < 6; b++) A.rot_bits += ts.q[b] < A.rot_shift;
+    for (int b = 1; b < 6; b++)
+        if (ts.q[b] <= ts.q[b - 1])
+            return fail(QSIM_E_UNSUPPORTED, "tensor-core block bits not in ascending qubit order");
+    A.vec2 = !wide && ts.q[0] == 0;
+    A.wide = wide;
+    if (wide) {
+        // the two highest tile qubits are the two highest block qubits (block
+        // bits 4, 5) or the two highest outside ones (group bits 5, 6)
+        for (int i = 0; i < 2; i++) {
+            const int p = T[11 + i];
+            int code = -1;
+            for (int b = 4; b < 6; b++)
+                if (ts.q[b] == p) code = 2 + (b - 4);
+            for (int f = 5; f < 7; f++)
+                if (freeq[f] == p) code = f - 5;
+            if (code < 0) return fail(QSIM_E_UNSUPPORTED, "quarter-tile qubit %d not a high block or group bit", p);
+            A.qsel[i] = code;
+        }
+    }
     A.tturn = pd_tables_dev ? (const uint64_t *)pd_tables_dev : nullptr;
     A.gfac = pd_tables_dev ? (const float2 *)((const unsigned char *)pd_tables_dev + 6 * 24 * 8) : nullptr;
     H.rank = 5;

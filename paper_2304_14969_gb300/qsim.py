@@ -22,7 +22,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libqsim.so")
 
 QSIM_C64, QSIM_C128 = 0, 1
-QSIM_PREC_NATIVE, QSIM_PREC_3XTF32, QSIM_PREC_BF16X3 = 0, 1, 2
+QSIM_PREC_NATIVE, QSIM_PREC_3XTF32, QSIM_PREC_BF16X3, QSIM_PREC_BF16X6 = 0, 1, 2, 3
 QSIM_MODE_PER_GATE, QSIM_MODE_FUSED = 0, 1
 QSIM_SCHED_EXHAUSTIVE, QSIM_SCHED_MLP, QSIM_SCHED_FORCED = 0, 1, 2
 STATUS = {0: "QSIM_OK", 1: "QSIM_E_INVAL", 2: "QSIM_E_NOMEM", 3: "QSIM_E_CUDA", 4: "QSIM_E_TIMEOUT",

@@ -161,16 +161,17 @@ extern "C" int emu_tc_run(const qsim_circuit *c, int prec, const int *start_l2p,
 // extents, dims[15..19] global extents, dims[20..23] byte strides of
 // dimensions 1..4, dims[24] boxes per tile, dims[25..28] dimension-4
 // offsets of the boxes, dims[29] box bytes, dims[30] rotated low block bits,
-// dims[31] paired stores; tpos[13] tile qubits. q6 ascending (as tc_build
-// orders a block).
-extern "C" int emu_tc_geometry(int n, const int *q6, int64_t *dims, int *tpos, int *posL, int *posG, uint64_t *spL,
-                               uint64_t *spG)
+// dims[31] paired stores, dims[32] rotation shift, dims[33] wide,
+// dims[34..35] quarter-tile bit codes; tpos[13] tile qubits. q6 ascending
+// (as tc_build orders a block). wide: complex128 geometry (quarter tiles).
+extern "C" int emu_tc_geometry(int n, const int *q6, int wide, int64_t *dims, int *tpos, int *posL, int *posG,
+                               uint64_t *spL, uint64_t *spG)
 {
     TcSpec ts;
     memset(&ts, 0, sizeof ts);
     for (int b = 0; b < 6; b++) ts.q[b] = q6[b];
     TcPipeHost H;
-    qsim_status st = tc_pipe_prepare(n, ts, nullptr, H);
+    qsim_status st = tc_pipe_prepare(n, ts, nullptr, H, wide != 0);
     if (st != QSIM_OK) return (int)st;
     const TcPipeArgs &A = H.args;
     for (int d = 0; d < 5; d++) {
@@ -185,6 +186,10 @@ extern "C" int emu_tc_geometry(int n, const int *q6, int64_t *dims, int *tpos, i
     dims[29] = A.box_bytes;
     dims[30] = A.rot_bits;
     dims[31] = A.vec2;
+    dims[32] = A.rot_shift;
+    dims[33] = A.wide;
+    dims[34] = A.qsel[0];
+    dims[35] = A.qsel[1];
     for (int j = 0; j < 13; j++) tpos[j] = A.tpos[j];
     for (int l = 0; l < 64; l++) {
         posL[l] = A.posL[l];

@@ -114,35 +114,47 @@ def tile_base(tpos, t):
     return base
 
 
-@pytest.mark.parametrize("seed", range(40))
-def test_tc_pipe_tile_geometry(emu, seed):
-    """The pipelined tensor-core kernel loads a tile (the block's 6 qubits and
-    the 7 lowest others) with up to four 5-D TMA boxes. Replaying the box
-    semantics (element (i0..i4) of box v sits at sum_d (c_d + i_d) * stride_d,
-    c_4 shifted by the box's offset; the boxes land one after another in
-    shared memory, dimension 0 fastest) must give every amplitude of the tile
-    exactly once, at the in-stage index posL[l] | posG[g] the kernel reads,
-    with all coordinates inside the tensor."""
-    rng = np.random.default_rng(seed)
-    n = int(rng.integers(13, 31))
+def block_qubits(rng, seed, n):
     if seed % 4 == 0:
-        q6 = sorted(int(v) for v in rng.choice(n, 6, replace=False))
+        q6 = [int(v) for v in rng.choice(n, 6, replace=False)]
     elif seed % 4 == 1:
         q6 = [int(v) for v in rng.choice(np.arange(0, n, 2), 6, replace=False)]
     elif seed % 4 == 2:
         q6 = [n - 1 - i for i in range(6)]
     else:
-        q6 = [int(v) for v in rng.choice(n, 6, replace=False)]
-    q6 = sorted(q6)                # tc_build orders block bits by qubit
-    dims = (C.c_int64 * 32)()
+        q6 = [int(v) for v in rng.choice(min(n, 9), 6, replace=False)]
+    return sorted(q6)                # tc_build orders block bits by qubit
+
+
+@pytest.mark.parametrize("wide", [0, 1])
+@pytest.mark.parametrize("seed", range(40))
+def test_tc_pipe_tile_geometry(emu, seed, wide):
+    """The pipelined tensor-core kernel loads a tile (the block's 6 qubits and
+    the 7 lowest others) with up to four 5-D TMA boxes of 8-byte elements.
+    Replaying the box semantics (element (i0..i4) of box v sits at sum_d
+    (c_d + i_d) * stride_d, c_4 shifted by the box's offset; the boxes land
+    one after another in shared memory, dimension 0 fastest) must give every
+    amplitude of the tile exactly once, at the in-stage index posL[l] |
+    posG[g] the kernel reads, with all coordinates inside the tensor. For
+    complex128 (wide) a load is a quarter tile: the tile's two highest qubits
+    are fixed by the load's index, dimension 0 counts the two 8-byte halves
+    of an amplitude, and the in-stage index keeps the low 11 bits."""
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(13, 31))
+    q6 = block_qubits(rng, seed, n)
+    dims = (C.c_int64 * 40)()
     tpos = (C.c_int * 13)()
     posL, posG = (C.c_int * 64)(), (C.c_int * 128)()
     spL, spG = (C.c_uint64 * 64)(), (C.c_uint64 * 128)()
-    rc = emu.emu_tc_geometry(n, (C.c_int * 6)(*q6), dims, tpos, posL, posG, spL, spG)
+    rc = emu.emu_tc_geometry(n, (C.c_int * 6)(*q6), wide, dims, tpos, posL, posG, spL, spG)
     assert rc == 0
     d = list(dims)
     lo, bits, box, gdim, gstr = d[0:5], d[5:10], d[10:15], d[15:20], d[20:24]
     nload, xoff, box_bytes = d[24], d[25:29], d[29]
+    rot_bits, vec2, rot_shift, dwide, qsel = d[30], d[31], d[32], d[33], d[34:36]
+    es = 16 if wide else 8                  # bytes per amplitude
+    hpa = es // 8                           # 8-byte elements per amplitude
+    assert dwide == wide and rot_shift == (3 if wide else 4)
     tp = list(tpos)
     assert sorted(tp) == tp and set(q6) <= set(tp)
     free = [p for p in range(n) if p not in q6][:7]
@@ -152,42 +164,68 @@ def test_tc_pipe_tile_geometry(emu, seed):
         assert strides[k] == strides[k - 1] * gdim[k - 1]
         assert strides[k] % 16 == 0 and strides[k] < 2 ** 40
     assert all(1 <= b <= 256 for b in box) and box[0] * 8 % 16 == 0
-    assert box_bytes == 8 * int(np.prod(box)) and box_bytes * nload == 65536
+    assert gdim[0] * 8 == es << bits[0]
+    nq = 4 if wide else 1                   # loads per tile
+    stage_elems = 8192 * es // 8 // nq      # 8-byte elements per load
+    assert box_bytes == 8 * int(np.prod(box)) and box_bytes * nload == stage_elems * 8
+    emask = (1 << 11) - 1 if wide else (1 << 13) - 1
+    # the quarter of (g, l): its bits at tp[11], tp[12]; the kernel derives
+    # it from qsel (0, 1: group bits 5, 6; 2, 3: block bits 4, 5)
+    def quarter_of(g, l):
+        x = spG[g] | spL[l]
+        return ((x >> tp[11]) & 1) | (((x >> tp[12]) & 1) << 1)
+
+    def quarter_from_qsel(g, l):
+        q = 0
+        for i, code in enumerate(qsel):
+            q |= (((g >> (5 + code)) & 1) if code < 2 else ((l >> (2 + code)) & 1)) << i
+        return q
+
+    if wide:
+        for g in range(0, 128, 9):
+            for l in range(0, 64, 5):
+                assert quarter_of(g, l) == quarter_from_qsel(g, l)
     ntiles = 1 << (n - 13)
     for t in {0, ntiles - 1, int(rng.integers(0, ntiles))}:
         base = tile_base(tp, t)
         assert all(not (base >> p) & 1 for p in tp)
-        c = [(base >> lo[k]) & ((1 << bits[k]) - 1) for k in range(5)]
-        stage = np.full(8192, -1, dtype=np.int64)
-        for v in range(nload):
-            cc = list(c)
-            cc[4] += xoff[v]
-            for k in range(5):
-                assert 0 <= cc[k] and cc[k] + box[k] <= gdim[k]
-            idx = np.zeros(1, dtype=np.int64)
-            for k in range(5):       # box elements, dimension 0 fastest
-                off = (cc[k] + np.arange(box[k], dtype=np.int64)) * (strides[k] // 8)
-                idx = (idx[None, :] + off[:, None]).reshape(-1)
-            stage[v * (box_bytes // 8):(v + 1) * (box_bytes // 8)] = idx
-        want = np.array([base + spL[l] + spG[g] for g in range(128) for l in range(64)], dtype=np.int64)
-        pos = np.array([posL[l] | posG[g] for g in range(128) for l in range(64)])
-        assert np.array_equal(np.sort(pos), np.arange(8192))
-        assert np.array_equal(stage[pos], want)
+        for q in range(nq):
+            bq = base | (((q & 1) << tp[11]) | ((q >> 1) << tp[12]) if wide else 0)
+            c = [(bq >> lo[k]) & ((1 << bits[k]) - 1) for k in range(5)]
+            c[0] *= hpa
+            stage = np.full(stage_elems, -1, dtype=np.int64)
+            for v in range(nload):
+                cc = list(c)
+                cc[4] += xoff[v]
+                for k in range(5):
+                    assert 0 <= cc[k] and cc[k] + box[k] <= gdim[k]
+                idx = np.zeros(1, dtype=np.int64)
+                for k in range(5):       # box elements, dimension 0 fastest
+                    off = (cc[k] + np.arange(box[k], dtype=np.int64)) * (strides[k] // 8)
+                    idx = (idx[None, :] + off[:, None]).reshape(-1)
+                stage[v * (box_bytes // 8):(v + 1) * (box_bytes // 8)] = idx
+            gl = [(g, l) for g in range(128) for l in range(64) if not wide or quarter_of(g, l) == q]
+            assert len(gl) == 8192 // nq
+            want = np.array([base + spL[l] + spG[g] for g, l in gl], dtype=np.int64)
+            pos = np.array([(posL[l] | posG[g]) & emask for g, l in gl])
+            assert np.array_equal(np.sort(pos), np.arange(8192 // nq))
+            for h in range(hpa):         # each 8-byte half of the amplitude
+                assert np.array_equal(stage[pos * hpa + h], want * hpa + h)
     # converter reads: lane (group g = 32 quarter + lane) reads block index
-    # 16 part + (i ^ rot(lane)) at instruction i; each half-warp's 16 lanes
-    # must hit 16 distinct 8-byte slots of a 128-byte bank row
-    rot_bits, vec2 = d[30], d[31]
-    assert rot_bits == sum(q < 4 for q in q6) and vec2 == (q6[0] == 0)
+    # 16 part + (i ^ rot(lane)) at instruction i; the 2^rot_shift lanes that
+    # share a 128-byte shared-memory row must hit distinct slots of it
+    row = 1 << rot_shift
+    assert rot_bits == sum(q < rot_shift for q in q6) and vec2 == (not wide and q6[0] == 0)
     for quarter in range(4):
         for part in range(4):
             for i in range(16):
-                for hw in range(2):
+                for hw in range(32 // row):
                     slots = set()
-                    for lane in range(16 * hw, 16 * hw + 16):
-                        rot = (lane >> (4 - rot_bits)) & ((1 << rot_bits) - 1) if rot_bits else 0
+                    for lane in range(row * hw, row * hw + row):
+                        rot = (lane >> (rot_shift - rot_bits)) & ((1 << rot_bits) - 1) if rot_bits else 0
                         g, l = 32 * quarter + lane, 16 * part + (i ^ rot)
-                        slots.add((posG[g] | posL[l]) % 16)
-                    assert len(slots) == 16, (q6, quarter, part, i, hw)
+                        slots.add(((posG[g] | posL[l]) & emask) % row)
+                    assert len(slots) == row, (q6, quarter, part, i, hw)
     if vec2:
         assert all(spL[l + 1] == spL[l] + 1 for l in range(0, 64, 2))
 
