@@ -42,8 +42,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip the per-gate FP64, grid and CPU legs")
     ap.add_argument("--workload", default="qft27",
-                    help="qft27 (default: the 27-qubit QFT on tensor-core blocks) or {qft,grid}<n>_{tc,simt} (one "
-                         "circuit on tensor-core blocks or fused SIMT passes; profiling workloads)")
+                    help="qft27 (default: the 27-qubit QFT on tensor-core blocks) or {qft,grid}<n>_{tc,tc128,simt} "
+                         "(one circuit on complex64 or complex128 tensor-core blocks or fused SIMT passes; "
+                         "profiling workloads)")
     return ap.parse_args()
 
 
@@ -389,19 +390,21 @@ def run_grid_tc(args):
     fam = "qft" if args.workload.startswith("qft") else "grid"
     n = int(args.workload[len(fam):].split("_")[0])
     simt = args.workload.endswith("_simt")
-    prec_kw = {} if simt else {"prec": Q.QSIM_PREC_BF16X3}
+    c128 = args.workload.endswith("_tc128")
+    dt, es = (Q.QSIM_C128, 16) if c128 else (Q.QSIM_C64, 8)
+    prec_kw = {} if simt else {"prec": Q.QSIM_PREC_BF16X6 if c128 else Q.QSIM_PREC_BF16X3}
     if fam == "grid":
         rows, cols = W.grid_shape(n)
         g = W.grid_rcs_circuit(rows, cols, 10, seed=0, n=n)
     else:
         g = W.qft_circuit(n)
     circ = Q.Circuit(n, g)
-    st = Q.State(n, Q.QSIM_C64)
+    st = Q.State(n, dt)
     # plans for both qubit maps the state alternates between (a QFT with
     # relabelled swaps leaves the ket bit-reversed), so no step permutes
-    plans = [Q.Plan(circ, dtype=Q.QSIM_C64, state=st, **prec_kw)]
+    plans = [Q.Plan(circ, dtype=dt, state=st, **prec_kw)]
     plans[0].execute(st)
-    plans.append(Q.Plan(circ, dtype=Q.QSIM_C64, state=st, **prec_kw))
+    plans.append(Q.Plan(circ, dtype=dt, state=st, **prec_kw))
     k = 1
     for _ in range(args.warmup):
         plans[k % 2].execute(st)
@@ -424,10 +427,53 @@ def run_grid_tc(args):
                       "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                       "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                       "data": "synthetic",
-                      "config": {"workload": f"{fam}{n}_c64_" + ("fused_simt" if simt else "tc_bf16x3"),
+                      "config": {"workload": f"{fam}{n}_" + ("c128_tc_bf16x6" if c128 else "c64_fused_simt" if simt
+                                                             else "c64_tc_bf16x3"),
                                  "n_qubits": n, "gates": len(g), "launches_per_step": nb},
                       "roofline": {"bound": "hbm", "kernel": "k_fused_pass" if simt else "k_tc_pipe",
-                                   "achieved": 2 * 8 * N / (ms / nb * 1e-3) / 1e9}}))
+                                   "achieved": 2 * es * N / (ms / nb * 1e-3) / 1e9}}))
+
+
+def c128_tc_leg(Q, C, torch, circ, x, n, ng, sref, peaks, fused_ms, per_gate_ms, reps=6):
+    """Complex128 ket through BF16X6 tensor-core blocks: device time (two
+    plans alternated, as the QFT leaves the ket bit-reversed), HBM rate per
+    block, and infidelity against sref, the per-gate FP64 result of the same
+    circuit on the same input (x, or |0...0> when x is None)."""
+    N = 1 << n
+    st = Q.State(n, Q.QSIM_C128)
+    if x is None:
+        Q.qsim_set_basis(st.h, 0)
+    else:
+        st.upload(x)
+    tps = [Q.Plan(circ, dtype=Q.QSIM_C128, prec=Q.QSIM_PREC_BF16X6, state=st)]
+    tps[0].execute(st)
+    ip = (C.c_double * 2)()
+    na, nb = C.c_double(), C.c_double()
+    Q.qsim_inner_product(sref.h, st.h, ip)
+    Q.qsim_norm(sref.h, C.byref(na))
+    Q.qsim_norm(st.h, C.byref(nb))
+    infid = 1.0 - (ip[0] ** 2 + ip[1] ** 2) / (na.value * nb.value)
+    tps.append(Q.Plan(circ, dtype=Q.QSIM_C128, prec=Q.QSIM_PREC_BF16X6, state=st))
+    tps[1].execute(st)
+    a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    Q.qsim_synchronize(st.h)
+    torch.cuda.synchronize()
+    a.record()
+    for r in range(reps):
+        tps[r % 2].execute(st)
+    z.record()
+    Q.qsim_synchronize(st.h)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(z) / reps
+    nbk = tps[0].info()["passes"]
+    achieved = 2 * 16 * N / (ms / nbk * 1e-3) / 1e9
+    st.close()
+    r = {"updates_per_s": ng * N / (ms * 1e-3), "ms": ms, "blocks": nbk, "kernel": "k_tc_pipe (complex128)",
+         "hbm_gbs_per_block": achieved, "frac_of_hbm": achieved / peaks.get("hbm_gbs", 6800.0),
+         "infidelity_vs_per_gate_fp64": infid, "speedup_vs_per_gate_fp64": per_gate_ms / ms}
+    if fused_ms:
+        r["speedup_vs_fused_fp64"] = fused_ms / ms
+    return r
 
 
 def extra_legs(Q, W, C, torch, circ, x, n, ng):
@@ -448,7 +494,10 @@ def extra_legs(Q, W, C, torch, circ, x, n, ng):
     Q.qsim_synchronize(s128.h)
     pg = time.perf_counter() - t0
     out["per_gate_fp64"] = {"updates_per_s": ng * N / pg, "ms": pg * 1e3, "dtype": "c128"}
-    s128.close()
+    peaks = {}
+    pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pp):
+        peaks = json.load(open(pp))
     # fused c128
     s = Q.State(n, Q.QSIM_C128)
     s.upload(x)
@@ -463,6 +512,12 @@ def extra_legs(Q, W, C, torch, circ, x, n, ng):
     out["fused_fp64"] = {"updates_per_s": ng * N / f128, "ms": f128 * 1e3, "dtype": "c128",
                          "passes": p.info()["passes"]}
     s.close()
+    # the same QFT on complex128 tensor-core blocks (BF16X6: three BF16
+    # slices per operand, six products, FP32 accumulation), against the
+    # per-gate FP64 result
+    out["qft27_c128_tc_bf16x6"] = c128_tc_leg(Q, C, torch, circ, x, n, ng, s128, peaks, out["fused_fp64"]["ms"],
+                                              out["per_gate_fp64"]["ms"])
+    s128.close()
     # the same QFT as fused SIMT passes (complex64, 2^13-amplitude tiles)
     ssim = Q.State(n, Q.QSIM_C64)
     ssim.upload(x)
@@ -614,6 +669,7 @@ def extra_legs(Q, W, C, torch, circ, x, n, ng):
     out["grid30_per_gate_fp64"] = {"updates_per_s": len(g) * (1 << 30) / pg, "ms": pg * 1e3, "dtype": "c128"}
     best = min(out[k]["ms"] for k in out if k.startswith("grid30_c64"))
     out["grid30_speedup_vs_per_gate_fp64"] = pg * 1e3 / best
+    out["grid30_c128_tc_bf16x6"] = c128_tc_leg(Q, C, torch, gc, None, 30, len(g), s128, peaks, None, pg * 1e3)
     s128.close()
     out["rows"] = rows_leg(Q, W, C, torch)
     out["batch512"] = batch_leg(Q, W, C)

@@ -28,8 +28,9 @@
 //
 // Complex128 kets (W = true, BF16X6): the tile is the same 128 x 64
 // amplitudes but 128 KB, so it is loaded as four 32 KB quarter tiles (one
-// per value of the tile's two highest qubits) into a ring of three stages;
-// the four converter warps whose amplitudes lie in a quarter read it. A
+// per value of the block's two highest qubits) into a ring of three stages;
+// the four converter warps whose amplitudes lie in a quarter (one part, one
+// warp per SM sub-partition) read it. A
 // converter rounds each FP64 amplitude to FP32 (integer arithmetic on the
 // IEEE encodings: FP64 instructions are scarce on this part), applies the
 // phases in FP32 and writes three BF16 slices (24 bits) into the one TMEM
@@ -78,26 +79,25 @@ static_assert(PipeCfg<false>::kSmem == PipeCfg<true>::kSmem, "one shared-memory 
 constexpr size_t kPSmem = PipeCfg<false>::kSmem;
 
 // IEEE binary64 -> binary32, round to nearest (ties away from zero), on the
-// encodings: magnitudes below 2^-126 become signed zero, at or above 2^128
-// infinity.
+// encodings, for magnitudes below 2^128 (amplitudes); magnitudes below
+// 2^-126 become signed zero. Shifting the double's top 35 bits left by 3
+// leaves its low 9 exponent bits above the 23 mantissa bits; the exponent
+// bias differs by 896 = 384 (mod 512), so one subtraction rebiases them.
 __device__ __forceinline__ float f64_to_f32_rn(double x)
 {
     const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
-    const uint32_t e = (hi >> 20) & 0x7ffu, sg = hi & 0x80000000u;
-    uint32_t f = sg | ((e - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
-    f += (lo >> 28) & 1u;   // a carry into the exponent field is the correct rounding
-    f = e > 896u ? f : sg;
-    return __uint_as_float(e < 1151u ? f : (sg | 0x7f800000u));
+    const uint32_t t = __funnelshift_l(lo, hi, 3) - (384u << 23) + ((lo >> 28) & 1u);
+    const uint32_t f = (t & 0x7fffffffu) | (hi & 0x80000000u);
+    return __uint_as_float(((hi >> 20) & 0x7ffu) > 896u ? f : (hi & 0x80000000u));
 }
 
 // IEEE binary32 -> binary64 (exact) on the encodings; binary32 subnormals
 // (below 2^-126) become signed zero.
 __device__ __forceinline__ double f32_to_f64(uint32_t f)
 {
-    const uint32_t e = (f >> 23) & 0xffu;
-    const uint32_t hi = (f & 0x80000000u) | (e ? (((e + 896u) << 20) | ((f >> 3) & 0xfffffu)) : 0u);
-    const uint32_t lo = e ? (f << 29) : 0u;
-    return __hiloint2double((int)hi, (int)lo);
+    const uint32_t hi = (((f & 0x7fffffffu) >> 3) + (896u << 20)) | (f & 0x80000000u);
+    const bool nz = (f & 0x7f800000u) != 0u;
+    return __hiloint2double((int)(nz ? hi : (f & 0x80000000u)), (int)(nz ? (f << 29) : 0u));
 }
 
 
@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
     __shared__ uint16_t s_posL[64];
     __shared__ uint64_t s_spL[64];
     __shared__ uint64_t s_tturn[6 * 24];
-    __shared__ float2 s_gfac[128 * 6];
+    __shared__ float2 s_gfac[6 * 128];       // [b][g]: a warp's lanes read consecutive entries
     __shared__ float2 s_E[4][6];             // tile factors of the deferred phases (tile j in slot j & 3)
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
         s_spL[i] = P.spL[i];
     }
     if (has_pd) {
-        for (int i = tid; i < 128 * 6; i += kPThreads) s_gfac[i] = P.gfac[i];
+        for (int i = tid; i < 128 * 6; i += kPThreads) s_gfac[(i % 6) * 128 + i / 6] = P.gfac[i];
         for (int i = tid; i < 6 * 24; i += kPThreads) s_tturn[i] = P.tturn[i];
     }
     {
@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
                 const uint32_t fb = smem_addr(&bar_full[m % Cfg::kNBar]);
                 if (lane == 0) {
                     uint64_t bq = base;
-                    if (W) bq |= ((uint64_t)(q & 1) << P.tpos[11]) | ((uint64_t)(q >> 1) << P.tpos[12]);
+                    if (W) bq |= ((uint64_t)(q & 1) << P.qpos[0]) | ((uint64_t)(q >> 1) << P.qpos[1]);
                     int c[5];
 #pragma unroll
                     for (int d = 0; d < 5; d++) c[d] = (int)((bq >> P.dim_lo[d]) & ((1ull << P.dim_bits[d]) - 1));
@@ -336,27 +336,28 @@ __global__ void __launch_bounds__(kPThreads, 1)
         const int g = 32 * quarter + lane;
         const uint32_t lane_off = (uint32_t)(32 * quarter) << 16;
         const int rot = P.rot_bits ? (lane >> (P.rot_shift - P.rot_bits)) & ((1 << P.rot_bits) - 1) : 0;
-        // complex128: the quarter tile holding this thread's amplitudes (the
-        // bits of tpos[11], tpos[12] among its group and part bits)
-        int qi = 0;
-        if (W) {
+        // complex128: this thread's amplitudes lie in quarter tile `part`
+        // (block bits 4, 5); the part's warp of lane quarter 0 polls its barriers
+        const int qi = W ? part : 0;
+        const bool qlead = !W || quarter == 0;
+        // in-stage byte offset of this thread's i-th read: the group's part,
+        // plus the block bits 0..3 of i ^ rot (posL is linear in l's bits);
+        // the 16 offsets are XORs of five per-thread values
+        constexpr uint32_t kEsz = W ? 16u : 8u;
+        uint32_t pb[4];
 #pragma unroll
-            for (int i = 0; i < 2; i++) {
-                const int code = P.qsel[i];
-                qi |= (code < 2 ? (quarter >> code) & 1 : (part >> (code - 2)) & 1) << i;
-            }
-        }
-        // in-stage byte offsets of this thread's reads (the same for every tile)
-        constexpr uint32_t kEsz = W ? 16u : 8u, kEmask = W ? 0x7ffu : 0x1fffu;
-        uint32_t offL[16];
-#pragma unroll
-        for (int i = 0; i < 16; i++) offL[i] = kEsz * ((uint32_t)(P.posG[g] | s_posL[16 * part + (i ^ rot)]) & kEmask);
+        for (int k = 0; k < 4; k++) pb[k] = kEsz * s_posL[1 << k];
+        const uint32_t obase = kEsz * (uint32_t)(P.posG[g] | s_posL[16 * part] | s_posL[rot]);
+        auto off_of = [&](int i) -> uint32_t {
+            return obase ^ ((i & 1) ? pb[0] : 0u) ^ ((i & 2) ? pb[1] : 0u) ^ ((i & 4) ? pb[2] : 0u) ^
+                   ((i & 8) ? pb[3] : 0u);
+        };
 
         for (uint64_t j = 0; j < J; j++) {
             const int b = (int)(j & 1);
             const uint32_t m = W ? (uint32_t)(4 * j + qi) : (uint32_t)j;   // the load this thread reads
             const int s = (int)(m % Cfg::kNStage), fbi = (int)(m % Cfg::kNBar);
-            const bool ok = mbar_wait_or_abort(smem_addr(&bar_full[fbi]), (m / Cfg::kNBar) & 1u, abort_flag);
+            const uint32_t fbar = smem_addr(&bar_full[fbi]), fpar = (m / Cfg::kNBar) & 1u;
             const unsigned char *stage = St + (size_t)s * Cfg::kStage;
             float2 v[16];
             bool qbad = false;
@@ -366,27 +367,33 @@ __global__ void __launch_bounds__(kPThreads, 1)
             // XOR-rotated by its own lane bits, so every read instruction
             // covers distinct banks; v[] is put back in order below.
             if (!W) {
-                // one decision for all converter threads (none may be left at a barrier)
+                // converter warp 0 polls; one decision for all converter
+                // threads (none may be left at a barrier); every thread then
+                // observes the completed phase itself
+                const bool ok = cw != 0 || mbar_wait_or_abort(fbar, fpar, abort_flag);
                 if (named_bar_or(1, kPConv, !ok || *abort_flag)) {
                     give_up();
                     break;
                 }
+                (void)mbar_try_wait(fbar, fpar);
 #pragma unroll
-                for (int i = 0; i < 16; i++) v[i] = *(const float2 *)(stage + offL[i]);
+                for (int i = 0; i < 16; i++) v[i] = *(const float2 *)(stage + off_of(i));
                 mbar_arrive(smem_addr(&bar_sfree[fbi]));   // the stage may be reloaded
             } else {
                 // one decision per quarter tile (its four warps): the quarters
                 // land one after another, and a quarter's stage must be released
                 // before the next quarters can load
+                const bool ok = !qlead || mbar_wait_or_abort(fbar, fpar, abort_flag);
                 qbad = named_bar_or(3 + qi, kPConv / 4, !ok || *abort_flag);
                 if (!qbad) {
+                    (void)mbar_try_wait(fbar, fpar);
 #pragma unroll
                     for (int i = 0; i < 16; i++) {
-                        const double2 x = *(const double2 *)(stage + offL[i]);
+                        const double2 x = *(const double2 *)(stage + off_of(i));
                         v[i] = make_float2(f64_to_f32_rn(x.x), f64_to_f32_rn(x.y));
                     }
                     mbar_arrive(smem_addr(&bar_sfree[fbi]));
-                } else {
+            } else {
 #pragma unroll
                     for (int i = 0; i < 16; i++) v[i] = make_float2(0.f, 0.f);
                 }
@@ -410,7 +417,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
                 float er[6], ei[6];
 #pragma unroll
                 for (int bb = 0; bb < 6; bb++) {
-                    const float2 E = s_E[j & 3][bb], F = s_gfac[g * 6 + bb];
+                    const float2 E = s_E[j & 3][bb], F = s_gfac[bb * 128 + g];
                     er[bb] = E.x * F.x - E.y * F.y;
                     ei[bb] = E.x * F.y + E.y * F.x;
                 }
@@ -455,13 +462,14 @@ __global__ void __launch_bounds__(kPThreads, 1)
                     lo[i] = *(const uint32_t *)&l2;
                 }
                 if (j >= 2) {
-                    // A operand b was last read by the MMAs of tile j - 2
-                    const bool ok2 =
-                        mbar_wait_or_abort(smem_addr(&bar_mma[b]), (uint32_t)(((j - 2) >> 1) & 1), abort_flag);
+                    // A operand b was last read by the MMAs of tile j - 2 (converter warp 0 polls)
+                    const uint32_t mb = smem_addr(&bar_mma[b]), mp = (uint32_t)(((j - 2) >> 1) & 1);
+                    const bool ok2 = cw != 0 || mbar_wait_or_abort(mb, mp, abort_flag);
                     if (named_bar_or(1, kPConv, !ok2 || *abort_flag)) {
                         give_up();
                         break;
                     }
+                    (void)mbar_try_wait(mb, mp);
                     asm volatile("tcgen05.fence::after_thread_sync;");
                 }
                 const uint32_t acol = tmem + lane_off + 256u + (uint32_t)b * 128u + (uint32_t)(16 * part);
@@ -469,12 +477,14 @@ __global__ void __launch_bounds__(kPThreads, 1)
                 tmem_st16(acol + 64u, lo);
             } else {
                 // the one A operand was last read by the MMAs of tile j - 1
-                const bool ok2 = !qbad && (j == 0 || mbar_wait_or_abort(smem_addr(&bar_mma[(j - 1) & 1]),
-                                                                        (uint32_t)(((j - 1) >> 1) & 1), abort_flag));
+                // (converter warp 0 polls)
+                const uint32_t mb = smem_addr(&bar_mma[(j - 1) & 1]), mp = (uint32_t)(((j - 1) >> 1) & 1);
+                const bool ok2 = !qbad && (j == 0 || cw != 0 || mbar_wait_or_abort(mb, mp, abort_flag));
                 if (named_bar_or(1, kPConv, !ok2 || *abort_flag)) {
                     give_up();
                     break;
                 }
+                if (j >= 1) (void)mbar_try_wait(mb, mp);
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 // three BF16 slices, each of the remainder of the ones before
                 const uint32_t acol = tmem + lane_off + 256u + (uint32_t)(16 * part);
@@ -506,11 +516,13 @@ __global__ void __launch_bounds__(kPThreads, 1)
         double nacc = 0;   // sum of |amplitude|^2 written (norm_out): FP32 runs of 16, FP64 across runs
         for (uint64_t j = 0; j < J; j++) {
             const int b = (int)(j & 1);
-            const bool ok = mbar_wait_or_abort(smem_addr(&bar_mma[b]), (uint32_t)((j >> 1) & 1), abort_flag);
+            const uint32_t mb = smem_addr(&bar_mma[b]), mp = (uint32_t)((j >> 1) & 1);
+            const bool ok = warp != 2 + kPConvWarps || mbar_wait_or_abort(mb, mp, abort_flag);   // one warp polls
             if (named_bar_or(2, kPEpi, !ok || *abort_flag)) {
                 give_up();
                 break;
             }
+            (void)mbar_try_wait(mb, mp);
             asm volatile("tcgen05.fence::after_thread_sync;");
             const uint64_t base = tile_base(P, tile_of(j));
 #pragma unroll 1

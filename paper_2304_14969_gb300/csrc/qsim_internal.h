@@ -106,7 +106,7 @@ struct TcPipeArgs {
     int nload;               // boxes per tile (per quarter tile when wide)
     int xoff[4];             // coordinate offset along dimension 4 of box v
     uint32_t box_bytes;
-    uint16_t posL[64];       // in-stage element index of block index l
+    uint16_t posL[64];       // in-stage element index of block index l (wide: within its quarter tile)
     uint16_t posG[128];      // in-stage element index of group g
     uint64_t spL[64];        // amplitude offset of block index l
     uint64_t spG[128];       // amplitude offset of group g
@@ -115,11 +115,11 @@ struct TcPipeArgs {
     int vec2;                // qubit 0 is block bit 0: amplitudes l, l + 1 (l even) are adjacent
     int rot_shift;           // lanes sharing a shared-memory row: 2^rot_shift (4: 8-byte, 3: 16-byte amplitudes)
     // complex128 kets (wide = 1): a tile is loaded as four quarter tiles,
-    // one per value of its two highest qubits tpos[11], tpos[12]; qsel[i]
-    // names the converter bit that carries tpos[11 + i] (0, 1: group bits
-    // 5, 6 = TMEM lane quarter bits; 2, 3: block bits 4, 5 = part bits)
+    // one per value of block bits 4, 5 (qubits qpos[0], qpos[1]), so that
+    // each quarter is read by the converter warps of one part, one on each
+    // SM sub-partition; posL / posG then rank the other 11 tile qubits
     int wide;
-    int qsel[2];
+    int qpos[2];
     // deferred phases (NULL if none): exp(2 pi i T_b) of block bit b for a
     // group is the product of a tile factor, from the turns tturn[b][i] of
     // the tile-index bits i, and the group factor gfac[g][b]

@@ -23,9 +23,9 @@ bool tc_pipe_eligible(int n, qsim_dtype dt, qsim_prec prec)
 // the fifth become extra boxes along dimension 4.
 //
 // wide (complex128, 16-byte amplitudes): the box is a quarter tile, the
-// tile qubits below its two highest (tpos[11], tpos[12]), which become
-// coordinates; dimension 0 counts 8-byte halves, so its run is at most 7
-// qubits (a box dimension spans at most 256 elements).
+// tile qubits other than the block's two highest (block bits 4, 5), which
+// become coordinates; dimension 0 counts 8-byte halves, so its run is at
+// most 7 qubits (a box dimension spans at most 256 elements).
 qsim_status tc_pipe_prepare(int n, const TcSpec &ts, const void *pd_tables_dev, TcPipeHost &H, bool wide)
 {
     if (n < 13 || n > 36) return fail(QSIM_E_UNSUPPORTED, "pipelined tensor-core blocks need 13 <= n <= 36");
@@ -39,10 +39,13 @@ qsim_status tc_pipe_prepare(int n, const TcSpec &ts, const void *pd_tables_dev, 
         if ((blk & bit(p)) || std::find(freeq.begin(), freeq.end(), p) != freeq.end()) T.push_back(p);
     const int es = wide ? 16 : 8;                   // bytes per amplitude
     const int nbox = wide ? 11 : 13;                 // tile qubits a box covers
+    std::vector<int> Tb;                             // box qubits, ascending
+    for (int p : T)
+        if (!wide || (p != ts.q[4] && p != ts.q[5])) Tb.push_back(p);
     // chunks of consecutive box qubits, at most 8 each (7 for dimension 0 when wide)
     std::vector<std::pair<int, int>> ch;   // (first qubit, length)
     for (int j = 0; j < nbox; j++) {
-        const int p = T[j];
+        const int p = Tb[j];
         const int cap = (wide && ch.size() == 1) ? 7 : 8;
         if (!ch.empty() && ch.back().first + ch.back().second == p && ch.back().second < cap)
             ch.back().second++;
@@ -88,13 +91,18 @@ qsim_status tc_pipe_prepare(int n, const TcSpec &ts, const void *pd_tables_dev, 
         A.xoff[v] = off;
     }
     A.box_bytes = (uint32_t)es << boxbits;
-    auto rank = [&](int q) { return (int)(std::find(T.begin(), T.end(), q) - T.begin()); };
+    // in-stage element index: rank among the box qubits (the quarter qubits
+    // of a wide tile add nothing)
+    auto rank_bit = [&](int q) {
+        const auto it = std::find(Tb.begin(), Tb.end(), q);
+        return it == Tb.end() ? 0 : 1 << (int)(it - Tb.begin());
+    };
     for (int l = 0; l < 64; l++) {
         int r = 0;
         uint64_t o = 0;
         for (int b = 0; b < 6; b++)
             if ((l >> b) & 1) {
-                r |= 1 << rank(ts.q[b]);
+                r |= rank_bit(ts.q[b]);
                 o |= bit(ts.q[b]);
             }
         A.posL[l] = (uint16_t)r;
@@ -105,7 +113,7 @@ qsim_status tc_pipe_prepare(int n, const TcSpec &ts, const void *pd_tables_dev, 
         uint64_t o = 0;
         for (int f = 0; f < 7; f++)
             if ((g >> f) & 1) {
-                r |= 1 << rank(freeq[f]);
+                r |= rank_bit(freeq[f]);
                 o |= bit(freeq[f]);
             }
         A.posG[g] = (uint16_t)r;
@@ -123,20 +131,8 @@ qsim_status tc_pipe_prepare(int n, const TcSpec &ts, const void *pd_tables_dev, 
             return fail(QSIM_E_UNSUPPORTED, "tensor-core block bits not in ascending qubit order");
     A.vec2 = !wide && ts.q[0] == 0;
     A.wide = wide;
-    if (wide) {
-        // the two highest tile qubits are the two highest block qubits (block
-        // bits 4, 5) or the two highest outside ones (group bits 5, 6)
-        for (int i = 0; i < 2; i++) {
-            const int p = T[11 + i];
-            int code = -1;
-            for (int b = 4; b < 6; b++)
-                if (ts.q[b] == p) code = 2 + (b - 4);
-            for (int f = 5; f < 7; f++)
-                if (freeq[f] == p) code = f - 5;
-            if (code < 0) return fail(QSIM_E_UNSUPPORTED, "quarter-tile qubit %d not a high block or group bit", p);
-            A.qsel[i] = code;
-        }
-    }
+    A.qpos[0] = wide ? ts.q[4] : 0;
+    A.qpos[1] = wide ? ts.q[5] : 0;
     A.tturn = pd_tables_dev ? (const uint64_t *)pd_tables_dev : nullptr;
     A.gfac = pd_tables_dev ? (const float2 *)((const unsigned char *)pd_tables_dev + 6 * 24 * 8) : nullptr;
     H.rank = 5;

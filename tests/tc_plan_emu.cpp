@@ -162,7 +162,7 @@ extern "C" int emu_tc_run(const qsim_circuit *c, int prec, const int *start_l2p,
 // dimensions 1..4, dims[24] boxes per tile, dims[25..28] dimension-4
 // offsets of the boxes, dims[29] box bytes, dims[30] rotated low block bits,
 // dims[31] paired stores, dims[32] rotation shift, dims[33] wide,
-// dims[34..35] quarter-tile bit codes; tpos[13] tile qubits. q6 ascending
+// dims[34..35] quarter-tile qubits; tpos[13] tile qubits. q6 ascending
 // (as tc_build orders a block). wide: complex128 geometry (quarter tiles).
 extern "C" int emu_tc_geometry(int n, const int *q6, int wide, int64_t *dims, int *tpos, int *posL, int *posG,
                                uint64_t *spL, uint64_t *spG)
@@ -188,8 +188,8 @@ extern "C" int emu_tc_geometry(int n, const int *q6, int wide, int64_t *dims, in
     dims[31] = A.vec2;
     dims[32] = A.rot_shift;
     dims[33] = A.wide;
-    dims[34] = A.qsel[0];
-    dims[35] = A.qsel[1];
+    dims[34] = A.qpos[0];
+    dims[35] = A.qpos[1];
     for (int j = 0; j < 13; j++) tpos[j] = A.tpos[j];
     for (int l = 0; l < 64; l++) {
         posL[l] = A.posL[l];
@@ -217,4 +217,30 @@ extern "C" int emu_tc_tables(int n, const int *q6, const int32_t *off, const int
     tc_pipe_tables(n, ts, o, pb, t, blob);
     memcpy(out, blob.data(), blob.size());
     return (int)blob.size();
+}
+
+// Builds the tensor-core plan of c (from start_l2p, NULL = identity) and
+// writes each block's six physical qubits (as tc_build received them) to
+// q_out[6 * b ..] and its number of deferred-phase partners to npd[b];
+// returns the number of blocks (at most cap), or -status.
+extern "C" int emu_tc_plan_blocks(const qsim_circuit *c, const int *start_l2p, int cap, int *q_out, int *npd)
+{
+    g_blocks.clear();
+    qsim_run_opts o;
+    memset(&o, 0, sizeof o);
+    o.mode = QSIM_MODE_FUSED;
+    o.prec = QSIM_PREC_BF16X3;
+    o.relabel_swaps = 1;
+    qsim_plan P;
+    qsim_status st = plan_build_tc(c, &o, start_l2p, &P);
+    if (st != QSIM_OK) return -(int)st;
+    int nb = 0;
+    for (const PlanStep &s : P.steps) {
+        if (s.kind != 3 || nb >= cap) continue;
+        const EmuBlock &B = g_blocks[s.pass];
+        for (int x = 0; x < 6; x++) q_out[6 * nb + x] = B.q[x];
+        npd[nb] = P.tc_pd_bit[s.pass].size();
+        nb++;
+    }
+    return nb;
 }

@@ -136,9 +136,10 @@ def test_tc_pipe_tile_geometry(emu, seed, wide):
     one after another in shared memory, dimension 0 fastest) must give every
     amplitude of the tile exactly once, at the in-stage index posL[l] |
     posG[g] the kernel reads, with all coordinates inside the tensor. For
-    complex128 (wide) a load is a quarter tile: the tile's two highest qubits
-    are fixed by the load's index, dimension 0 counts the two 8-byte halves
-    of an amplitude, and the in-stage index keeps the low 11 bits."""
+    complex128 (wide) a load is a quarter tile: the block's two highest
+    qubits (block bits 4, 5: the converter's part) are fixed by the load's
+    index, dimension 0 counts the two 8-byte halves of an amplitude, and the
+    in-stage index ranks the other 11 tile qubits."""
     rng = np.random.default_rng(seed)
     n = int(rng.integers(13, 31))
     q6 = block_qubits(rng, seed, n)
@@ -151,7 +152,7 @@ def test_tc_pipe_tile_geometry(emu, seed, wide):
     d = list(dims)
     lo, bits, box, gdim, gstr = d[0:5], d[5:10], d[10:15], d[15:20], d[20:24]
     nload, xoff, box_bytes = d[24], d[25:29], d[29]
-    rot_bits, vec2, rot_shift, dwide, qsel = d[30], d[31], d[32], d[33], d[34:36]
+    rot_bits, vec2, rot_shift, dwide, qpos = d[30], d[31], d[32], d[33], d[34:36]
     es = 16 if wide else 8                  # bytes per amplitude
     hpa = es // 8                           # 8-byte elements per amplitude
     assert dwide == wide and rot_shift == (3 if wide else 4)
@@ -168,29 +169,23 @@ def test_tc_pipe_tile_geometry(emu, seed, wide):
     nq = 4 if wide else 1                   # loads per tile
     stage_elems = 8192 * es // 8 // nq      # 8-byte elements per load
     assert box_bytes == 8 * int(np.prod(box)) and box_bytes * nload == stage_elems * 8
-    emask = (1 << 11) - 1 if wide else (1 << 13) - 1
-    # the quarter of (g, l): its bits at tp[11], tp[12]; the kernel derives
-    # it from qsel (0, 1: group bits 5, 6; 2, 3: block bits 4, 5)
+    # the quarter of (g, l): its bits at the quarter qubits, which are block
+    # bits 4, 5, i.e. the converter's part l >> 4
     def quarter_of(g, l):
         x = spG[g] | spL[l]
-        return ((x >> tp[11]) & 1) | (((x >> tp[12]) & 1) << 1)
-
-    def quarter_from_qsel(g, l):
-        q = 0
-        for i, code in enumerate(qsel):
-            q |= (((g >> (5 + code)) & 1) if code < 2 else ((l >> (2 + code)) & 1)) << i
-        return q
+        return ((x >> qpos[0]) & 1) | (((x >> qpos[1]) & 1) << 1)
 
     if wide:
+        assert list(qpos) == q6[4:6]
         for g in range(0, 128, 9):
             for l in range(0, 64, 5):
-                assert quarter_of(g, l) == quarter_from_qsel(g, l)
+                assert quarter_of(g, l) == l >> 4
     ntiles = 1 << (n - 13)
     for t in {0, ntiles - 1, int(rng.integers(0, ntiles))}:
         base = tile_base(tp, t)
         assert all(not (base >> p) & 1 for p in tp)
         for q in range(nq):
-            bq = base | (((q & 1) << tp[11]) | ((q >> 1) << tp[12]) if wide else 0)
+            bq = base | (((q & 1) << qpos[0]) | ((q >> 1) << qpos[1]) if wide else 0)
             c = [(bq >> lo[k]) & ((1 << bits[k]) - 1) for k in range(5)]
             c[0] *= hpa
             stage = np.full(stage_elems, -1, dtype=np.int64)
@@ -207,7 +202,7 @@ def test_tc_pipe_tile_geometry(emu, seed, wide):
             gl = [(g, l) for g in range(128) for l in range(64) if not wide or quarter_of(g, l) == q]
             assert len(gl) == 8192 // nq
             want = np.array([base + spL[l] + spG[g] for g, l in gl], dtype=np.int64)
-            pos = np.array([(posL[l] | posG[g]) & emask for g, l in gl])
+            pos = np.array([posL[l] | posG[g] for g, l in gl])
             assert np.array_equal(np.sort(pos), np.arange(8192 // nq))
             for h in range(hpa):         # each 8-byte half of the amplitude
                 assert np.array_equal(stage[pos * hpa + h], want * hpa + h)
@@ -224,10 +219,30 @@ def test_tc_pipe_tile_geometry(emu, seed, wide):
                     for lane in range(row * hw, row * hw + row):
                         rot = (lane >> (rot_shift - rot_bits)) & ((1 << rot_bits) - 1) if rot_bits else 0
                         g, l = 32 * quarter + lane, 16 * part + (i ^ rot)
-                        slots.add(((posG[g] | posL[l]) & emask) % row)
+                        slots.add((posG[g] | posL[l]) % row)
                     assert len(slots) == row, (q6, quarter, part, i, hw)
     if vec2:
         assert all(spL[l + 1] == spL[l] + 1 for l in range(0, 64, 2))
+
+
+@pytest.mark.parametrize("wide", [0, 1])
+def test_tc_pipe_geometry_always_covered(emu, wide):
+    """Every block the planner can emit has a tile geometry (at most five
+    tensor dimensions plus two extra-box qubits): all 6-qubit blocks among
+    qubits 0..13 at n = 20, and random blocks at n = 13..36."""
+    import itertools
+    dims = (C.c_int64 * 40)()
+    tpos = (C.c_int * 13)()
+    posL, posG = (C.c_int * 64)(), (C.c_int * 128)()
+    spL, spG = (C.c_uint64 * 64)(), (C.c_uint64 * 128)()
+    cases = [(20, list(q)) for q in itertools.combinations(range(14), 6)]
+    rng = np.random.default_rng(7)
+    for _ in range(3000):
+        n = int(rng.integers(13, 37))
+        cases.append((n, sorted(int(v) for v in rng.choice(n, 6, replace=False))))
+    for n, q6 in cases:
+        rc = emu.emu_tc_geometry(n, (C.c_int * 6)(*q6), wide, dims, tpos, posL, posG, spL, spG)
+        assert rc == 0, (n, q6, wide)
 
 
 @pytest.mark.parametrize("seed", range(12))
