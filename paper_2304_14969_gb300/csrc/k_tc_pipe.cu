@@ -137,10 +137,13 @@ __device__ __forceinline__ uint32_t prod_u(int p)
 // only): grouped (batched circuits): CTA i takes work entry i, a range of
 // tiles of the block that descs[works[i].desc] describes, and stamps the
 // circuit's first load and last store with %globaltimer. W: complex128 ket.
+template <bool W> struct AmpOf { using T = float2; };
+template <> struct AmpOf<true> { using T = double2; };
+
 template <bool G, bool W>
 __global__ void __launch_bounds__(kPThreads, 1)
     k_tc_pipe(const __grid_constant__ CUtensorMap tmap_param, const __grid_constant__ TcPipeArgs P_param,
-              void *__restrict__ a_param, const unsigned char *__restrict__ Ug_param, int *err,
+              typename AmpOf<W>::T *__restrict__ a_param, const unsigned char *__restrict__ Ug_param, int *err,
               const TcBatchDesc *__restrict__ descs, const TcWork *__restrict__ works, unsigned long long *t0s,
               unsigned long long *t1s, double *norm_out)
 {
@@ -156,7 +159,9 @@ __global__ void __launch_bounds__(kPThreads, 1)
     __syncthreads();
     const TcPipeArgs &P = s_P;
     const void *tmap = G ? (const void *)desc->tmap : (const void *)&tmap_param;
-    void *__restrict__ a = G ? (void *)desc->amps : a_param;
+    // the ket (typed and restrict-qualified: its stores may not alias the
+    // shared-memory tables the write-back reads)
+    typename AmpOf<W>::T *__restrict__ a = G ? (typename AmpOf<W>::T *)desc->amps : a_param;
     const unsigned char *__restrict__ Ug = G ? desc->U : Ug_param;
     const uint64_t wtile0 = G ? works[blockIdx.x].tile0 : 0, wntiles = G ? works[blockIdx.x].ntiles : 0;
     // tile of this CTA's j-th iteration
@@ -228,62 +233,108 @@ __global__ void __launch_bounds__(kPThreads, 1)
 
     if (warp == 0) {
         // ---------------- TMA producer (lane 0) and tile factors of the
-        // deferred phases (lanes 0..5): load m goes to stage m mod kNStage,
-        // once the converters have read load m - kNStage, and signals
-        // full[m mod kNBar]
-        uint32_t m = 0;   // loads issued
-        bool quit = false;
-        for (uint64_t j = 0; j < J && !quit; j++) {
-            const uint64_t t = tile_of(j);
-            const uint64_t base = tile_base(P, t);
-            for (int q = 0; q < Cfg::kQ; q++, m++) {
-                const int s = (int)(m % Cfg::kNStage);
+        // deferred phases (lanes 0..5)
+        if constexpr (!W) {
+            // complex64: tile j goes to stage j & 1 once the converters have
+            // read tile j - 2
+            uint64_t issued = 0;
+            for (uint64_t j = 0; j < J; j++) {
+                const int s = (int)(j & 1);
                 int stop = 0;
                 if (lane == 0) {
-                    const uint32_t r = m - Cfg::kNStage;   // the load stage s held before
-                    const bool ok = m < (uint32_t)Cfg::kNStage ||
-                                    mbar_wait_or_abort(smem_addr(&bar_sfree[r % Cfg::kNBar]), (r / Cfg::kNBar) & 1u,
-                                                       abort_flag);
+                    const bool ok = j < 2 || mbar_wait_or_abort(smem_addr(&bar_sfree[s]),
+                                                                (uint32_t)(((j - 2) >> 1) & 1), abort_flag);
                     if (!ok) give_up();
                     stop = !ok || *abort_flag;
                 }
-                quit = __shfl_sync(0xffffffffu, stop, 0) != 0;
-                if (quit) break;
-                const uint32_t fb = smem_addr(&bar_full[m % Cfg::kNBar]);
+                if (__shfl_sync(0xffffffffu, stop, 0)) break;
+                const uint64_t t = tile_of(j);
+                const uint32_t fb = smem_addr(&bar_full[s]);
                 if (lane == 0) {
-                    uint64_t bq = base;
-                    if (W) bq |= ((uint64_t)(q & 1) << P.qpos[0]) | ((uint64_t)(q >> 1) << P.qpos[1]);
+                    const uint64_t base = tile_base(P, t);
                     int c[5];
 #pragma unroll
-                    for (int d = 0; d < 5; d++) c[d] = (int)((bq >> P.dim_lo[d]) & ((1ull << P.dim_bits[d]) - 1));
-                    if (W) c[0] <<= 1;   // dimension 0 counts the 8-byte halves of an amplitude
+                    for (int d = 0; d < 5; d++) c[d] = (int)((base >> P.dim_lo[d]) & ((1ull << P.dim_bits[d]) - 1));
                     mbar_arrive_expect_tx(fb, P.box_bytes * (uint32_t)P.nload);
                     const uint32_t dst = smem_addr(St + (size_t)s * Cfg::kStage);
                     for (int v = 0; v < P.nload; v++)
                         tma_load_5d(dst + (uint32_t)v * P.box_bytes, tmap, fb, c[0], c[1], c[2], c[3], c[4] + P.xoff[v]);
                 }
                 if (has_pd) {
-                    if (q == 0) {
-                        if (lane < 6) {
-                            uint64_t tt = 0;
-                            for (int i = 0; i < P.ntb; i++)
-                                if ((t >> i) & 1) tt += s_tturn[lane * 24 + i];
-                            float sn, cs;
-                            turns_sincos(tt, sn, cs);
-                            s_E[j & 3][lane] = make_float2(cs, sn);
-                        }
-                        __syncwarp();
+                    if (lane < 6) {
+                        uint64_t tt = 0;
+                        for (int i = 0; i < P.ntb; i++)
+                            if ((t >> i) & 1) tt += s_tturn[lane * 24 + i];
+                        float sn, cs;
+                        turns_sincos(tt, sn, cs);
+                        s_E[j & 3][lane] = make_float2(cs, sn);
                     }
+                    __syncwarp();
                     if (lane == 0) mbar_arrive(fb);
                 }
+                issued = j + 1;
             }
+            // loads still in flight (only after an abort) land before the CTA exits
+            if (lane == 0)
+                for (uint64_t j = issued >= 2 ? issued - 2 : 0; j < issued; j++)
+                    mbar_wait(smem_addr(&bar_full[j & 1]), (uint32_t)((j >> 1) & 1));
+        } else {
+            // complex128: load m (quarter m & 3 of tile m >> 2) goes to stage
+            // m mod kNStage once the converters have read load m - kNStage,
+            // and signals full[m mod kNBar]
+            uint32_t m = 0;   // loads issued
+            bool quit = false;
+            for (uint64_t j = 0; j < J && !quit; j++) {
+                const uint64_t t = tile_of(j);
+                for (int q = 0; q < Cfg::kQ; q++, m++) {
+                    const int s = (int)(m % Cfg::kNStage);
+                    int stop = 0;
+                    if (lane == 0) {
+                        const uint32_t r = m - Cfg::kNStage;   // the load stage s held before
+                        const bool ok = m < (uint32_t)Cfg::kNStage ||
+                                        mbar_wait_or_abort(smem_addr(&bar_sfree[r % Cfg::kNBar]), (r / Cfg::kNBar) & 1u,
+                                                           abort_flag);
+                        if (!ok) give_up();
+                        stop = !ok || *abort_flag;
+                    }
+                    quit = __shfl_sync(0xffffffffu, stop, 0) != 0;
+                    if (quit) break;
+                    const uint32_t fb = smem_addr(&bar_full[m % Cfg::kNBar]);
+                    if (lane == 0) {
+                        const uint64_t bq = tile_base(P, t) | ((uint64_t)(q & 1) << P.qpos[0]) |
+                                            ((uint64_t)(q >> 1) << P.qpos[1]);
+                        int c[5];
+#pragma unroll
+                        for (int d = 0; d < 5; d++) c[d] = (int)((bq >> P.dim_lo[d]) & ((1ull << P.dim_bits[d]) - 1));
+                        c[0] <<= 1;   // dimension 0 counts the 8-byte halves of an amplitude
+                        mbar_arrive_expect_tx(fb, P.box_bytes * (uint32_t)P.nload);
+                        const uint32_t dst = smem_addr(St + (size_t)s * Cfg::kStage);
+                        for (int v = 0; v < P.nload; v++)
+                            tma_load_5d(dst + (uint32_t)v * P.box_bytes, tmap, fb, c[0], c[1], c[2], c[3], c[4] + P.xoff[v]);
+                    }
+                    if (has_pd) {
+                        if (q == 0) {
+                            if (lane < 6) {
+                                uint64_t tt = 0;
+                                for (int i = 0; i < P.ntb; i++)
+                                    if ((t >> i) & 1) tt += s_tturn[lane * 24 + i];
+                                float sn, cs;
+                                turns_sincos(tt, sn, cs);
+                                s_E[j & 3][lane] = make_float2(cs, sn);
+                            }
+                            __syncwarp();
+                        }
+                        if (lane == 0) mbar_arrive(fb);
+                    }
+                }
+            }
+            // loads still in flight (only after an abort) land before the CTA
+            // exits; the loads before them have been read, so these waits see
+            // each barrier's completions in order
+            if (lane == 0)
+                for (uint32_t x = m >= (uint32_t)Cfg::kNStage ? m - Cfg::kNStage : 0; x < m; x++)
+                    mbar_wait(smem_addr(&bar_full[x % Cfg::kNBar]), (x / Cfg::kNBar) & 1u);
         }
-        // loads still in flight (only after an abort) land before the CTA
-        // exits; the loads before them have been read, so these waits see
-        // each barrier's completions in order
-        if (lane == 0)
-            for (uint32_t x = m >= (uint32_t)Cfg::kNStage ? m - Cfg::kNStage : 0; x < m; x++)
-                mbar_wait(smem_addr(&bar_full[x % Cfg::kNBar]), (x / Cfg::kNBar) & 1u);
     } else if (warp == 1) {
         // ---------------- MMA issue: D[g][n] = sum_k A[g][k] U[n][k], A in TMEM
         if (lane == 0) {
@@ -340,18 +391,11 @@ __global__ void __launch_bounds__(kPThreads, 1)
         // (block bits 4, 5); the part's warp of lane quarter 0 polls its barriers
         const int qi = W ? part : 0;
         const bool qlead = !W || quarter == 0;
-        // in-stage byte offset of this thread's i-th read: the group's part,
-        // plus the block bits 0..3 of i ^ rot (posL is linear in l's bits);
-        // the 16 offsets are XORs of five per-thread values
+        // in-stage byte offsets of this thread's reads (the same for every tile)
         constexpr uint32_t kEsz = W ? 16u : 8u;
-        uint32_t pb[4];
+        uint32_t offL[16];
 #pragma unroll
-        for (int k = 0; k < 4; k++) pb[k] = kEsz * s_posL[1 << k];
-        const uint32_t obase = kEsz * (uint32_t)(P.posG[g] | s_posL[16 * part] | s_posL[rot]);
-        auto off_of = [&](int i) -> uint32_t {
-            return obase ^ ((i & 1) ? pb[0] : 0u) ^ ((i & 2) ? pb[1] : 0u) ^ ((i & 4) ? pb[2] : 0u) ^
-                   ((i & 8) ? pb[3] : 0u);
-        };
+        for (int i = 0; i < 16; i++) offL[i] = kEsz * ((uint32_t)P.posG[g] + s_posL[16 * part + (i ^ rot)]);
 
         for (uint64_t j = 0; j < J; j++) {
             const int b = (int)(j & 1);
@@ -367,17 +411,14 @@ __global__ void __launch_bounds__(kPThreads, 1)
             // XOR-rotated by its own lane bits, so every read instruction
             // covers distinct banks; v[] is put back in order below.
             if (!W) {
-                // converter warp 0 polls; one decision for all converter
-                // threads (none may be left at a barrier); every thread then
-                // observes the completed phase itself
-                const bool ok = cw != 0 || mbar_wait_or_abort(fbar, fpar, abort_flag);
+                // one decision for all converter threads (none may be left at a barrier)
+                const bool ok = mbar_wait_or_abort(fbar, fpar, abort_flag);
                 if (named_bar_or(1, kPConv, !ok || *abort_flag)) {
                     give_up();
                     break;
                 }
-                (void)mbar_try_wait(fbar, fpar);
 #pragma unroll
-                for (int i = 0; i < 16; i++) v[i] = *(const float2 *)(stage + off_of(i));
+                for (int i = 0; i < 16; i++) v[i] = *(const float2 *)(stage + offL[i]);
                 mbar_arrive(smem_addr(&bar_sfree[fbi]));   // the stage may be reloaded
             } else {
                 // one decision per quarter tile (its four warps): the quarters
@@ -389,7 +430,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
                     (void)mbar_try_wait(fbar, fpar);
 #pragma unroll
                     for (int i = 0; i < 16; i++) {
-                        const double2 x = *(const double2 *)(stage + off_of(i));
+                        const double2 x = *(const double2 *)(stage + offL[i]);
                         v[i] = make_float2(f64_to_f32_rn(x.x), f64_to_f32_rn(x.y));
                     }
                     mbar_arrive(smem_addr(&bar_sfree[fbi]));
@@ -462,14 +503,13 @@ __global__ void __launch_bounds__(kPThreads, 1)
                     lo[i] = *(const uint32_t *)&l2;
                 }
                 if (j >= 2) {
-                    // A operand b was last read by the MMAs of tile j - 2 (converter warp 0 polls)
+                    // A operand b was last read by the MMAs of tile j - 2
                     const uint32_t mb = smem_addr(&bar_mma[b]), mp = (uint32_t)(((j - 2) >> 1) & 1);
-                    const bool ok2 = cw != 0 || mbar_wait_or_abort(mb, mp, abort_flag);
+                    const bool ok2 = mbar_wait_or_abort(mb, mp, abort_flag);
                     if (named_bar_or(1, kPConv, !ok2 || *abort_flag)) {
                         give_up();
                         break;
                     }
-                    (void)mbar_try_wait(mb, mp);
                     asm volatile("tcgen05.fence::after_thread_sync;");
                 }
                 const uint32_t acol = tmem + lane_off + 256u + (uint32_t)b * 128u + (uint32_t)(16 * part);
@@ -517,12 +557,11 @@ __global__ void __launch_bounds__(kPThreads, 1)
         for (uint64_t j = 0; j < J; j++) {
             const int b = (int)(j & 1);
             const uint32_t mb = smem_addr(&bar_mma[b]), mp = (uint32_t)((j >> 1) & 1);
-            const bool ok = warp != 2 + kPConvWarps || mbar_wait_or_abort(mb, mp, abort_flag);   // one warp polls
+            const bool ok = mbar_wait_or_abort(mb, mp, abort_flag);
             if (named_bar_or(2, kPEpi, !ok || *abort_flag)) {
                 give_up();
                 break;
             }
-            (void)mbar_try_wait(mb, mp);
             asm volatile("tcgen05.fence::after_thread_sync;");
             const uint64_t base = tile_base(P, tile_of(j));
 #pragma unroll 1
@@ -537,24 +576,25 @@ __global__ void __launch_bounds__(kPThreads, 1)
                     nacc += (double)run;
                 }
                 const int l0 = c0 / 2;
-                if (W) {
-                    double2 *dstg = (double2 *)a + (base + spG);
+                auto *dstg = a + (base + spG);
+                if constexpr (W) {
 #pragma unroll
                     for (int i = 0; i < 16; i++)
                         dstg[s_spL[l0 + i]] = make_double2(f32_to_f64(r[2 * i]), f32_to_f64(r[2 * i + 1]));
-                } else if (P.vec2) {
-                    // amplitudes l, l + 1 adjacent: one 16-byte store per pair
-                    float2 *dstg = (float2 *)a + (base + spG);
-#pragma unroll
-                    for (int i = 0; i < 16; i += 2)
-                        *(float4 *)(dstg + s_spL[l0 + i]) =
-                            make_float4(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1]),
-                                        __uint_as_float(r[2 * i + 2]), __uint_as_float(r[2 * i + 3]));
                 } else {
-                    float2 *dstg = (float2 *)a + (base + spG);
+                    if (P.vec2) {
+                        // amplitudes l, l + 1 adjacent: one 16-byte store per pair
 #pragma unroll
-                    for (int i = 0; i < 16; i++)
-                        dstg[s_spL[l0 + i]] = make_float2(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1]));
+                        for (int i = 0; i < 16; i += 2)
+                            *(float4 *)(dstg + s_spL[l0 + i]) =
+                                make_float4(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1]),
+                                            __uint_as_float(r[2 * i + 2]), __uint_as_float(r[2 * i + 3]));
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 16; i++)
+                            dstg[s_spL[l0 + i]] =
+                                make_float2(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1]));
+                    }
                 }
             }
             asm volatile("tcgen05.fence::before_thread_sync;");
@@ -633,10 +673,10 @@ cudaError_t tc_pipe_launch(qsim_state *s, const TcPipeHost &H, const unsigned ch
     const int grid = (int)std::min<uint64_t>(H.args.ntiles, (uint64_t)num_sms());
     if (H.args.wide != (s->dt == QSIM_C128)) return cudaErrorInvalidValue;
     if (H.args.wide)
-        k_tc_pipe<false, true><<<grid, kPThreads, kPSmem, s->stream>>>(tm, H.args, s->amps, dU, derr, nullptr,
+        k_tc_pipe<false, true><<<grid, kPThreads, kPSmem, s->stream>>>(tm, H.args, (double2 *)s->amps, dU, derr, nullptr,
                                                                         nullptr, nullptr, nullptr, norm_out);
     else
-        k_tc_pipe<false, false><<<grid, kPThreads, kPSmem, s->stream>>>(tm, H.args, s->amps, dU, derr, nullptr,
+        k_tc_pipe<false, false><<<grid, kPThreads, kPSmem, s->stream>>>(tm, H.args, (float2 *)s->amps, dU, derr, nullptr,
                                                                          nullptr, nullptr, nullptr, norm_out);
     return cudaGetLastError();
 }
