@@ -470,7 +470,11 @@ def c128_tc_leg(Q, C, torch, circ, x, n, ng, sref, peaks, fused_ms, per_gate_ms,
     st.close()
     r = {"updates_per_s": ng * N / (ms * 1e-3), "ms": ms, "blocks": nbk, "kernel": "k_tc_pipe (complex128)",
          "hbm_gbs_per_block": achieved, "frac_of_hbm": achieved / peaks.get("hbm_gbs", 6800.0),
-         "infidelity_vs_per_gate_fp64": infid, "speedup_vs_per_gate_fp64": per_gate_ms / ms}
+         "infidelity_vs_per_gate_fp64": infid, "speedup_vs_per_gate_fp64": per_gate_ms / ms,
+         "alg_bytes_per_block": 2 * 16 * N}
+    if n == 27 and circ.n == 27:
+        # ncu DRAM traffic per launch of the QFT-27 blocks (profiles/traffic.json)
+        r["traffic_per_block"] = traffic_from_profiles("k_tc_pipe_c128")
     if fused_ms:
         r["speedup_vs_fused_fp64"] = fused_ms / ms
     return r

@@ -1,0 +1,191 @@
+"""Barrier protocol of the pipelined tensor-core kernel (k_tc_pipe.cu),
+modelled on the CPU with random interleavings of its roles.
+
+The model follows the kernel's roles and mbarrier waits: the TMA producer
+(load m into stage m mod S, signalling full[m mod B] after waiting for the
+free barrier of the load the stage held before), the converters (complex64:
+one group reading tile j; complex128: four quarter groups, quarter q of tile
+j is load 4j + q, plus the all-converter barrier before the A operand is
+rewritten), the MMA issuer and the write-back. A parity wait passes when the
+barrier's current phase parity differs from the one waited for, as
+mbarrier.try_wait.parity does. Every interleaving must read each load from
+its stage after it landed and before the stage is reloaded, and finish.
+With the stage ring's barriers shared between quarters (B = S = 3) the model
+reproduces the race the per-quarter barriers remove. The model must be kept
+in step with the kernel by hand."""
+import random
+
+import pytest
+
+
+class Bar:
+    def __init__(self, count):
+        self.count = count
+        self.pend = count
+        self.tx = 0
+        self.phase = 0
+
+    def _check(self):
+        assert self.pend >= 0 and self.tx >= 0, "barrier underflow"
+        if self.pend == 0 and self.tx == 0:
+            self.phase += 1
+            self.pend = self.count
+
+    def arrive(self):
+        self.pend -= 1
+        self._check()
+
+    def expect_tx(self, b):
+        self.tx += b
+        self.pend -= 1
+        self._check()
+
+    def complete_tx(self, b):
+        self.tx -= b
+        self._check()
+
+    def done(self, parity):
+        return (self.phase & 1) != parity
+
+
+def run(wide, J, pd, seed, nbar=None):
+    rng = random.Random(seed)
+    NS, NB, Q = (3, 4, 4) if wide else (2, 2, 1)
+    if nbar:
+        NB = nbar
+    NG = 4 if wide else 1
+    full = [Bar(2 if pd else 1) for _ in range(NB)]
+    sfree = [Bar(1) for _ in range(NB)]       # a group's threads act as one arrival
+    aready = [Bar(NG) for _ in range(2)]
+    mma = [Bar(1) for _ in range(2)]
+    accf = [Bar(1) for _ in range(2)]
+    stage = [None] * NS                        # (load, landed)
+    read = set()
+    inflight = []
+    acc = [None, None]
+    abuf = {}
+    written = []
+
+    def producer():
+        m = 0
+        for j in range(J):
+            for q in range(Q):
+                s = m % NS
+                if m >= NS:
+                    r = m - NS
+                    while not sfree[r % NB].done((r // NB) & 1):
+                        yield
+                    assert r in read, ("stage reloaded before it was read", m, r)
+                assert stage[s] is None or stage[s][0] in read, "stage overwritten"
+                stage[s] = (m, False)
+                full[m % NB].expect_tx(1)
+                inflight.append((s, m, m % NB))
+                if pd:
+                    full[m % NB].arrive()
+                m += 1
+                yield
+
+    def tma():
+        while True:
+            if inflight and rng.random() < 0.5:
+                k = rng.randrange(len(inflight)) if rng.random() < 0.2 else 0
+                s, m, b = inflight.pop(k)
+                assert stage[s][0] == m
+                stage[s] = (m, True)
+                full[b].complete_tx(1)
+            yield
+
+    bar1 = {"cnt": 0, "gen": 0}
+
+    def barrier_all(n):
+        g = bar1["gen"]
+        bar1["cnt"] += 1
+        if bar1["cnt"] == n:
+            bar1["cnt"] = 0
+            bar1["gen"] += 1
+        while bar1["gen"] == g:
+            yield
+
+    def converter(qi):
+        for j in range(J):
+            b = j & 1
+            m = 4 * j + qi if wide else j
+            while not full[m % NB].done((m // NB) & 1):
+                yield
+            assert stage[m % NS] == (m, True), ("read before the load landed", j, qi, stage[m % NS], m)
+            read.add(m)
+            sfree[m % NB].arrive()
+            yield
+            if wide:
+                if j >= 1:
+                    while not mma[(j - 1) & 1].done(((j - 1) >> 1) & 1):
+                        yield
+                yield from barrier_all(NG)
+                ab = 0
+            else:
+                if j >= 2:
+                    while not mma[b].done(((j - 2) >> 1) & 1):
+                        yield
+                ab = b
+            assert abuf.get((ab, qi), (-1, True))[1], "A operand rewritten before the MMAs read it"
+            abuf[(ab, qi)] = (j, False)
+            aready[ab].arrive()
+
+    def mma_issuer():
+        for j in range(J):
+            b = j & 1
+            ab = 0 if wide else b
+            while not aready[ab].done((j & 1) if wide else ((j >> 1) & 1)):
+                yield
+            if j >= 2:
+                while not accf[b].done(((j - 2) >> 1) & 1):
+                    yield
+            for qi in range(NG):
+                assert abuf[(ab, qi)][0] == j, "MMA read another tile's A operand"
+            assert acc[b] is None, "accumulator still being written back"
+            acc[b] = j
+            yield
+            for qi in range(NG):
+                abuf[(ab, qi)] = (j, True)
+            mma[b].arrive()
+
+    def write_back():
+        for j in range(J):
+            b = j & 1
+            while not mma[b].done((j >> 1) & 1):
+                yield
+            assert acc[b] == j
+            written.append(j)
+            acc[b] = None
+            accf[b].arrive()
+            yield
+
+    alive = [producer(), mma_issuer(), write_back()] + [converter(q) for q in range(NG)]
+    t = tma()
+    steps = 0
+    while alive:
+        steps += 1
+        assert steps < 200000, "no progress (deadlock)"
+        if rng.random() < 0.3:
+            next(t)
+        a = rng.choice(alive)
+        try:
+            next(a)
+        except StopIteration:
+            alive.remove(a)
+    assert written == list(range(J)) and not inflight
+
+
+@pytest.mark.parametrize("wide", [False, True])
+@pytest.mark.parametrize("pd", [False, True])
+def test_protocol_random_interleavings(wide, pd):
+    for seed in range(600):
+        run(wide, 1 + seed % 7, pd, seed)
+
+
+def test_shared_stage_barriers_race():
+    """Quarters sharing the ring's barriers (three for four quarters): some
+    interleaving reads a quarter before its load landed."""
+    with pytest.raises(AssertionError, match="read before the load landed"):
+        for seed in range(600):
+            run(True, 1 + seed % 7, False, seed, nbar=3)
