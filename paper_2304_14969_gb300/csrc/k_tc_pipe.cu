@@ -78,6 +78,15 @@ template <bool W> struct PipeCfg {
 static_assert(PipeCfg<false>::kSmem == PipeCfg<true>::kSmem, "one shared-memory size for both widths");
 constexpr size_t kPSmem = PipeCfg<false>::kSmem;
 
+// One 32-byte global store (sm_100 and later; p 32-byte aligned).
+__device__ __forceinline__ void st_global_256(void *p, uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t a4,
+                                              uint32_t a5, uint32_t a6, uint32_t a7)
+{
+    asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "r"(a0), "r"(a1), "r"(a2),
+                 "r"(a3), "r"(a4), "r"(a5), "r"(a6), "r"(a7)
+                 : "memory");
+}
+
 // IEEE binary64 -> binary32, round to nearest (ties away from zero), on the
 // encodings, for magnitudes below 2^128 (amplitudes); magnitudes below
 // 2^-126 become signed zero. Shifting the double's top 35 bits left by 3
@@ -578,11 +587,18 @@ __global__ void __launch_bounds__(kPThreads, 1)
                 const int l0 = c0 / 2;
                 auto *dstg = a + (base + spG);
                 if constexpr (W) {
+                    // (32-byte pair stores measured 0.4 % slower here)
 #pragma unroll
                     for (int i = 0; i < 16; i++)
                         dstg[s_spL[l0 + i]] = make_double2(f32_to_f64(r[2 * i]), f32_to_f64(r[2 * i + 1]));
                 } else {
-                    if (P.vec2) {
+                    if (P.vecw >= 2) {
+                        // amplitudes l .. l + 3 adjacent: one 32-byte store per quad
+#pragma unroll
+                        for (int i = 0; i < 16; i += 4)
+                            st_global_256(dstg + s_spL[l0 + i], r[2 * i], r[2 * i + 1], r[2 * i + 2], r[2 * i + 3],
+                                          r[2 * i + 4], r[2 * i + 5], r[2 * i + 6], r[2 * i + 7]);
+                    } else if (P.vecw == 1) {
                         // amplitudes l, l + 1 adjacent: one 16-byte store per pair
 #pragma unroll
                         for (int i = 0; i < 16; i += 2)

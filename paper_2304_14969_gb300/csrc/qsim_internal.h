@@ -112,7 +112,8 @@ struct TcPipeArgs {
     uint64_t spG[128];       // amplitude offset of group g
     int ntb;                 // tile-index bits (n - 13)
     int rot_bits;            // block qubits among qubits 0..3 (= block index bits 0..rot_bits-1)
-    int vec2;                // qubit 0 is block bit 0: amplitudes l, l + 1 (l even) are adjacent
+    int vecw;                // complex64: the lowest qubits are block bits 0..vecw-1, so a thread's
+                             // amplitudes come in runs of 2^vecw adjacent ones (stored 16 or 32 bytes at a time)
     int rot_shift;           // lanes sharing a shared-memory row: 2^rot_shift (4: 8-byte, 3: 16-byte amplitudes)
     // complex128 kets (wide = 1): a tile is loaded as four quarter tiles,
     // one per value of block bits 4, 5 (qubits qpos[0], qpos[1]), so that

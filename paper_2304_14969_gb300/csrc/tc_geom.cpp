@@ -129,7 +129,7 @@ qsim_status tc_pipe_prepare(int n, const TcSpec &ts, const void *pd_tables_dev, 
     for (int b = 1; b < 6; b++)
         if (ts.q[b] <= ts.q[b - 1])
             return fail(QSIM_E_UNSUPPORTED, "tensor-core block bits not in ascending qubit order");
-    A.vec2 = !wide && ts.q[0] == 0;
+    A.vecw = (wide || ts.q[0] != 0) ? 0 : ts.q[1] != 1 ? 1 : 2;   // complex64 only
     A.wide = wide;
     A.qpos[0] = wide ? ts.q[4] : 0;
     A.qpos[1] = wide ? ts.q[5] : 0;

@@ -161,7 +161,7 @@ extern "C" int emu_tc_run(const qsim_circuit *c, int prec, const int *start_l2p,
 // extents, dims[15..19] global extents, dims[20..23] byte strides of
 // dimensions 1..4, dims[24] boxes per tile, dims[25..28] dimension-4
 // offsets of the boxes, dims[29] box bytes, dims[30] rotated low block bits,
-// dims[31] paired stores, dims[32] rotation shift, dims[33] wide,
+// dims[31] log2 of the write-back's store runs, dims[32] rotation shift, dims[33] wide,
 // dims[34..35] quarter-tile qubits; tpos[13] tile qubits. q6 ascending
 // (as tc_build orders a block). wide: complex128 geometry (quarter tiles).
 extern "C" int emu_tc_geometry(int n, const int *q6, int wide, int64_t *dims, int *tpos, int *posL, int *posG,
@@ -185,7 +185,7 @@ extern "C" int emu_tc_geometry(int n, const int *q6, int wide, int64_t *dims, in
     for (int v = 0; v < 4; v++) dims[25 + v] = A.xoff[v];
     dims[29] = A.box_bytes;
     dims[30] = A.rot_bits;
-    dims[31] = A.vec2;
+    dims[31] = A.vecw;
     dims[32] = A.rot_shift;
     dims[33] = A.wide;
     dims[34] = A.qpos[0];

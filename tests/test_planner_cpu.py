@@ -152,7 +152,7 @@ def test_tc_pipe_tile_geometry(emu, seed, wide):
     d = list(dims)
     lo, bits, box, gdim, gstr = d[0:5], d[5:10], d[10:15], d[15:20], d[20:24]
     nload, xoff, box_bytes = d[24], d[25:29], d[29]
-    rot_bits, vec2, rot_shift, dwide, qpos = d[30], d[31], d[32], d[33], d[34:36]
+    rot_bits, vecw, rot_shift, dwide, qpos = d[30], d[31], d[32], d[33], d[34:36]
     es = 16 if wide else 8                  # bytes per amplitude
     hpa = es // 8                           # 8-byte elements per amplitude
     assert dwide == wide and rot_shift == (3 if wide else 4)
@@ -210,7 +210,12 @@ def test_tc_pipe_tile_geometry(emu, seed, wide):
     # 16 part + (i ^ rot(lane)) at instruction i; the 2^rot_shift lanes that
     # share a 128-byte shared-memory row must hit distinct slots of it
     row = 1 << rot_shift
-    assert rot_bits == sum(q < rot_shift for q in q6) and vec2 == (not wide and q6[0] == 0)
+    assert rot_bits == sum(q < rot_shift for q in q6)
+    # store runs: 2^vecw adjacent amplitudes, at most 32 bytes, aligned
+    run = 0
+    while run < len(q6) and q6[run] == run:
+        run += 1
+    assert vecw == (0 if wide else min(run, 2))
     for quarter in range(4):
         for part in range(4):
             for i in range(16):
@@ -221,8 +226,10 @@ def test_tc_pipe_tile_geometry(emu, seed, wide):
                         g, l = 32 * quarter + lane, 16 * part + (i ^ rot)
                         slots.add((posG[g] | posL[l]) % row)
                     assert len(slots) == row, (q6, quarter, part, i, hw)
-    if vec2:
-        assert all(spL[l + 1] == spL[l] + 1 for l in range(0, 64, 2))
+    w = 1 << vecw
+    for l in range(0, 64, w):
+        assert all(spL[l + i] == spL[l] + i for i in range(w)) and spL[l] % w == 0
+    assert all(spG[g] % w == 0 for g in range(128))
 
 
 @pytest.mark.parametrize("wide", [0, 1])
