@@ -42,9 +42,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip the per-gate FP64, grid and CPU legs")
     ap.add_argument("--workload", default="qft27",
-                    help="qft27 (default: the 27-qubit QFT on tensor-core blocks) or {qft,grid}<n>_{tc,tc128,simt} "
+                    help="qft27 (default: the 27-qubit QFT on tensor-core blocks), {qft,grid}<n>_{tc,tc128,simt} "
                          "(one circuit on complex64 or complex128 tensor-core blocks or fused SIMT passes; "
-                         "profiling workloads)")
+                         "profiling workloads), or appendix_a (the paper's fidelity-model validation in full)")
     return ap.parse_args()
 
 
@@ -207,6 +207,9 @@ def main():
         return
     if args.warmup < 3:
         args.warmup = 3
+    if args.workload == "appendix_a":
+        run_appendix_a()
+        return
     if args.workload != "qft27":
         run_grid_tc(args)
         return
@@ -686,6 +689,7 @@ def extra_legs(Q, W, C, torch, circ, x, n, ng):
     # exhaustive-mode traces of 20-qubit circuits of the same family)
     h = train_proposal_mlp(Q, W, C)
     out["approx54_paper_family_mlp"] = approx_leg(Q, W, pf, budget_gib=80.0, mlp=h)
+    out["appendix_a_validation"] = appa_leg(Q, W, C, seeds=10, time_cap_s=60.0)
     Q.qsim_mlp_destroy(h)
     return out
 
@@ -846,6 +850,64 @@ def approx_leg(Q, W, g, budget_gib=80.0, time_cap_s=40.0, p_start=1.0, mlp=None)
             "min_p": done[-1]["p"] if done else None, "F_at_min_p": done[-1]["F"] if done else None,
             "seconds_total": sum(x["seconds"] for x in done),
             "bloch_passes_total": sum(x["bloch_passes"] for x in done), "runs": runs}
+
+
+# App. A of the paper: RMSE of the fidelity model against the exact fidelity,
+# per width x depth set (its Table II, 100 circuits per set there)
+APPA_SETS = ((6, 6), (12, 6), (18, 6), (12, 12), (18, 12), (18, 18), (15, 15), (19, 10))
+APPA_PAPER_RMSE = {(6, 6): 0.067, (12, 6): 0.054, (18, 6): 0.044, (12, 12): 0.039, (18, 12): 0.025,
+                   (18, 18): 0.018, (15, 15): 0.024, (19, 10): 0.025}
+
+
+def appa_leg(Q, W, C, seeds=3, time_cap_s=90.0):
+    """For each set: `seeds` circuits of the paper's family (width w on a
+    grid of ceil(sqrt(w)) columns), p = 0, 0.025, ..., 1; F model of the
+    approximate run (complex128) against F_exact = |<psi_approx|psi_exact>|^2
+    with psi_exact from the per-gate FP64 path. Seeds are added round-robin
+    over the sets until the time cap."""
+    t0 = time.perf_counter()
+    res = {s: [] for s in APPA_SETS}
+    ps = [round(0.025 * i, 3) for i in range(41)]
+    for seed in range(seeds):
+        for (w, d) in APPA_SETS:
+            if time.perf_counter() - t0 > time_cap_s:
+                break
+            rows, cols = W.grid_shape(w)
+            g = W.paper_random_circuit(rows, cols, d, seed=1000 * w + d * 10 + seed, n=w)
+            se = Q.State(w, Q.QSIM_C128)
+            se.run(Q.Circuit(w, g), mode=Q.QSIM_MODE_PER_GATE)
+            ex = se.download()
+            se.close()
+            for p in ps:
+                r, st, _, _ = Q.approx_run(w, g, p, dtype=Q.QSIM_C128, want_state=True)
+                fe = abs(np.vdot(st, ex)) ** 2 / (np.vdot(st, st).real * np.vdot(ex, ex).real)
+                res[(w, d)].append((r.fidelity_model, float(fe)))
+    out = {"sets": [], "p_grid": "0..1 step 0.025", "dtype": "c128", "seconds": time.perf_counter() - t0}
+    allr = []
+    for (w, d), obs in res.items():
+        if not obs:
+            continue
+        r2 = [(a - b) ** 2 for a, b in obs]
+        allr += r2
+        out["sets"].append({"width": w, "depth": d, "circuits": len(obs) // len(ps), "observations": len(obs),
+                            "rmse": float(np.sqrt(np.mean(r2))), "mean_F": float(np.mean([a for a, _ in obs])),
+                            "mean_F_exact": float(np.mean([b for _, b in obs])),
+                            "paper_rmse_100_circuits": APPA_PAPER_RMSE[(w, d)]})
+    out["observations"] = len(allr)
+    out["rmse_overall"] = float(np.sqrt(np.mean(allr))) if allr else None
+    out["paper_rmse_overall"] = 0.039
+    return out
+
+
+def run_appendix_a():
+    """The paper's App. A protocol in full: 100 circuits per width x depth
+    set, 41 values of p each (32,800 observations); one JSON line."""
+    import ctypes as C
+    from paper_2304_14969_gb300 import build, qsim as Q
+    from paper_2304_14969_gb300 import workloads as W
+    build.build()
+    Q.lib()
+    print(json.dumps({"workload": "appendix_a_validation", **appa_leg(Q, W, C, seeds=100, time_cap_s=1e9)}))
 
 
 def train_proposal_mlp(Q, W, C):

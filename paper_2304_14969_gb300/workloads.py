@@ -163,12 +163,13 @@ def grid_shape(n: int) -> tuple:
 
 
 def paper_random_circuit(rows: int, cols: int, layers: int, seed: int,
-                         patterns: str = "ABCDCDAB") -> list:
+                         patterns: str = "ABCDCDAB", n: Optional[int] = None) -> list:
     """The paper's random family (Sec. III.C): U(theta, phi, lambda) on every
     qubit with theta in [0, 4 pi), phi, lambda in [0, 2 pi), then on every
     coupler of the layer's pattern one gate drawn from CX, CY, CZ, AX, AY,
-    AZ with a random choice of which end is the control."""
-    nq = rows * cols
+    AZ with a random choice of which end is the control. n < rows * cols
+    keeps the first n grid sites (couplers touching the others are dropped)."""
+    nq = rows * cols if n is None else n
     rng = np.random.default_rng(seed)
     g = []
     for layer in range(layers):
@@ -178,6 +179,8 @@ def paper_random_circuit(rows: int, cols: int, layers: int, seed: int,
             la = float(rng.uniform(0.0, 2.0 * math.pi))
             g.append(Gate("u3", (q,), (th, ph, la)))
         for a, b in grid_couplers(rows, cols, patterns[layer % len(patterns)]):
+            if a >= nq or b >= nq:
+                continue
             pauli = ("x", "y", "z")[int(rng.integers(0, 3))]
             cval = int(rng.integers(0, 2))
             if int(rng.integers(0, 2)):

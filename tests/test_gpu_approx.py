@@ -137,3 +137,29 @@ def test_54_qubit_grid_runs(Q, p):
     if st == 0:
         assert 0 < r.fidelity_model <= 1
         assert r.peak_bytes <= 64 * 2 ** 30
+
+
+def test_appendix_a_observables(Q):
+    """App. A quantities on one 6x6 circuit of the paper's family (complex128):
+    over p = 0, 0.025, ..., 1 both fidelities lie in [0, 1], p = 0 is exact
+    (F = F_exact = 1), F_exact is taken against the per-gate FP64 result, and
+    the model tracks it (the paper's RMSE for its 6x6 set is 6.7 %; the bound
+    here is loose, for one circuit)."""
+    w, d = 6, 6
+    rows, cols = W.grid_shape(w)
+    g = W.paper_random_circuit(rows, cols, d, seed=66, n=w)
+    se = Q.State(w, 1)
+    se.run(Q.Circuit(w, g), mode=0)
+    ex = se.download()
+    se.close()
+    assert fid(ex, oracle.apply_circuit(W.basis_state(w, 0), g)) > 1 - 1e-12
+    r2 = []
+    for i in range(41):
+        p = round(0.025 * i, 3)
+        r, st, _, _ = Q.approx_run(w, g, p, dtype=1, want_state=True)
+        fe = abs(np.vdot(st, ex)) ** 2 / (np.vdot(st, st).real * np.vdot(ex, ex).real)
+        assert -1e-12 <= r.fidelity_model <= 1 + 1e-12 and -1e-12 <= fe <= 1 + 1e-12
+        if p == 0.0:
+            assert r.fidelity_model == 1.0 and fe > 1 - 1e-12
+        r2.append((r.fidelity_model - fe) ** 2)
+    assert np.sqrt(np.mean(r2)) < 0.25
