@@ -690,6 +690,7 @@ def extra_legs(Q, W, C, torch, circ, x, n, ng):
     h = train_proposal_mlp(Q, W, C)
     out["approx54_paper_family_mlp"] = approx_leg(Q, W, pf, budget_gib=80.0, mlp=h)
     out["appendix_a_validation"] = appa_leg(Q, W, C, seeds=10, time_cap_s=60.0)
+    out["qft54_zero_factorized"] = qft_zero_factorized_leg(Q, W)
     Q.qsim_mlp_destroy(h)
     return out
 
@@ -897,6 +898,16 @@ def appa_leg(Q, W, C, seeds=3, time_cap_s=90.0):
     out["rmse_overall"] = float(np.sqrt(np.mean(allr))) if allr else None
     out["paper_rmse_overall"] = 0.039
     return out
+
+
+def qft_zero_factorized_leg(Q, W, n=54):
+    """QFT of |0...0> on 54 qubits through the approximate mode with p = 0
+    (exact separation only): the ket stays factorised (2-qubit subsystems at
+    most), where a state vector would take 2^54 x 16 bytes."""
+    r, _, _, _ = Q.approx_run(n, W.qft_circuit(n), 0.0, dtype=Q.QSIM_C128, tau=1e-13)
+    return {"qubits": n, "gates": len(W.qft_circuit(n)), "seconds": r.seconds, "F": r.fidelity_model,
+            "rounds": r.n_rounds, "exact_separations": r.n_exact, "max_subsystem_qubits": r.max_subsystem_qubits,
+            "peak_bytes": r.peak_bytes, "state_vector_bytes": 16 * 2 ** n}
 
 
 def run_appendix_a():

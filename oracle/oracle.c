@@ -439,7 +439,7 @@ void orc_sdrp_project(cplx *psi, int n, int q, const double r[3])
  * SWAP, which only exchanges the two qubits' memberships; after a merge,
  * every qubit of the merged subsystem is checked in ascending global id,
  * one after the other, while that subsystem still holds two or more
- * qubits. A check computes r and eps = (1 - |r|)/2; eps <= p/2 rounds
+ * qubits. A check computes r and eps = (1 - |r|)/2; eps <= p/2 (p > 0) rounds
  * (F <- F (1 - eps), Eq. fid_model); otherwise eps <= tau separates the
  * qubit exactly without touching F; otherwise the qubit stays. A rounded
  * or separated qubit becomes a subsystem of its own.
@@ -498,7 +498,7 @@ int orc_sdrp_run(cplx *psi, int n, const orc_gate *g, int ng, double p, double t
             double len = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
             double eps = (1.0 - len) / 2.0;
             int action = 0;
-            if (eps <= p / 2.0) action = 1;
+            if (p > 0.0 && eps <= p / 2.0) action = 1;   /* p = 0: exact simulation, nothing rounds */
             else if (eps <= tau) action = 2;
             if (action) {
                 orc_sdrp_project(psi, n, q, r);

@@ -135,7 +135,7 @@ __global__ void k_decide(const double *__restrict__ sums, const int *__restrict_
         out->r[k][0] = r0;
         out->r[k][1] = r1;
         out->r[k][2] = r2;
-        int act = eps <= p / 2.0 ? 1 : (eps <= tau ? 2 : 0);
+        int act = (p > 0.0 && eps <= p / 2.0) ? 1 : (eps <= tau ? 2 : 0);   // p = 0 rounds nothing
         if (act) {
             double th = 0.0, ph = 0.0;
             if (len >= 1e-15) {

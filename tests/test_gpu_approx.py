@@ -163,3 +163,19 @@ def test_appendix_a_observables(Q):
             assert r.fidelity_model == 1.0 and fe > 1 - 1e-12
         r2.append((r.fidelity_model - fe) ** 2)
     assert np.sqrt(np.mean(r2)) < 0.25
+
+
+def test_qft_on_zero_state_stays_factorized(Q):
+    """QFT of |0...0> in the approximate mode with p = 0 (exact separation
+    only, tau = 1e-13): every controlled phase acts on a control still in
+    |0>, so after each merge both qubits separate again (Sec. II.A
+    factorisation); the ket stays a product of single-qubit factors and the
+    expanded result is the closed form of Eq. (dft) for x = 0, the uniform
+    superposition, with F = 1."""
+    n = 20
+    r, st, _, _ = Q.approx_run(n, W.qft_circuit(n), 0.0, dtype=1, tau=1e-13, want_state=True)
+    assert r.fidelity_model == 1.0 and r.n_rounds == 0
+    assert r.max_subsystem_qubits <= 2
+    assert r.n_exact > 0
+    ref = np.full(1 << n, 2.0 ** (-n / 2), dtype=np.complex128)
+    assert fid(st, ref) > 1 - 1e-12
