@@ -355,7 +355,8 @@ typedef struct {
 } qsim_approx_result;
 
 /* Runs circuit c from |0...0> with SDRP rounding at threshold p in [0, 1]
- * (Eq. sdrp: round when eps <= p/2) on a factorised ket: a list of
+ * (Eq. sdrp: round when eps <= p/2; p = 0 rounds nothing, only exact
+ * separations with eps <= tau happen) on a factorised ket: a list of
  * subsystem kets, composed when a two-qubit gate spans two of them
  * (Sec. II.A) and split when a check rounds or separates a qubit. Returns
  * QSIM_E_BUDGET (with result filled up to that gate) when the kets would

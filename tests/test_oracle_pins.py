@@ -310,6 +310,18 @@ def test_sdrp_p0_is_exact():
     assert abs(oracle.fidelity(psi, exact) - 1) < 1e-12
 
 
+def test_sdrp_p0_separates_exactly_without_rounding():
+    """QFT of |0...0> at p = 0: every controlled phase meets a control in |0>,
+    so the checks find eps exactly 0; with p = 0 nothing rounds (exact
+    simulation), each such check is an exact separation (action 2), and the
+    result is the closed form of Eq. (dft) for x = 0."""
+    n = 8
+    psi, F, nr, log = oracle.sdrp_run(n, W.qft_circuit(n), p=0.0, tau=1e-13)
+    assert F == 1.0 and nr == 0
+    assert len(log) > 0 and set(int(a) for a in log["action"]) <= {0, 2} and (log["action"] == 2).any()
+    assert abs(oracle.fidelity(psi, np.full(1 << n, 2.0 ** (-n / 2), dtype=np.complex128)) - 1) < 1e-12
+
+
 def test_sdrp_single_projection_fidelity_is_exact():
     """With exactly one rounding, F = 1 - eps equals F_exact (Sec. III.B)."""
     n = 5
