@@ -782,145 +782,145 @@ namespace qs {
 // index) when no earlier gate of the block acted on q (so the term may move
 // to the block's start), and o is then kept out of the block. SWAPs are
 // relabels. Every block is one pass of the tensor-core kernel.
-qsim_status plan_build_tc(const qsim_circuit *cir, const qsim_run_opts *opts, const int *start_l2p, qsim_plan *P)
-{
-    const int n = cir->n;
-    if (n < 6) return fail(QSIM_E_UNSUPPORTED, "tensor-core plans need n >= 6");
-    P->n = n;
-    P->dt = QSIM_C64;
-    P->prec = opts->prec;
-    P->ngates = cir->ngates;
-    {
-        std::vector<int> l2p(n);
-        for (int q = 0; q < n; q++) l2p[q] = start_l2p ? start_l2p[q] : q;
-        P->start_l2p = l2p;
-    }
-    std::vector<Item> items;
-    classify_gates(cir, start_l2p, true, items, P->final_l2p, P->nswaps);
+//
+// Which qubits a block gets: the first-fit sweep lets the earliest gates
+// decide, which on 2-D circuits often closes a block after gates of one
+// layer. The sweep can also be restricted to a candidate qubit set; the
+// candidates are the sets grown from each of the first dense gates (the
+// gate's qubits plus those of the following gates that overlap and fit).
+// Per block the candidate taking the most dense gates wins (sweeps without
+// matrices decide). The plan is built with per-block choice when a full
+// matrix-free sweep shows it needs fewer blocks than first fit, else with
+// first fit, so no circuit gets more blocks than before.
+namespace {
+
+struct TcSweep {
+    int n;
     std::vector<Term> pending;
     cd gphase = 1.0;
-    auto item_qubits = [](const Item *it, std::vector<int> &v) {
-        v.clear();
-        if (it->kind == 2) {
-            v.push_back(it->gate.q0);
-            for (int j = 0; j < it->gate.ncontrols; j++) v.push_back(it->gate.controls[j]);
-        } else if (it->kind == 1) {
-            for (const Term &tm : it->terms) {
-                if (std::find(v.begin(), v.end(), tm.a) == v.end()) v.push_back(tm.a);
-                if (tm.b >= 0 && std::find(v.begin(), v.end(), tm.b) == v.end()) v.push_back(tm.b);
-            }
-        } else {
-            for (int k = 0; k < it->nq; k++) v.push_back(it->q[k]);
+    // one block's outcome
+    std::vector<int> Q;                                        // block qubits, block bit b <-> Q[b]
+    std::vector<cd> U;
+    std::vector<char> outside;
+    std::vector<std::pair<int, std::pair<int, double>>> pre;   // (block qubit, (outside qubit, angle))
+    std::vector<const Item *> left;
+    int ng = 0;
+};
+
+void item_qubits(const Item *it, std::vector<int> &v)
+{
+    v.clear();
+    if (it->kind == 2) {
+        v.push_back(it->gate.q0);
+        for (int j = 0; j < it->gate.ncontrols; j++) v.push_back(it->gate.controls[j]);
+    } else if (it->kind == 1) {
+        for (const Term &tm : it->terms) {
+            if (std::find(v.begin(), v.end(), tm.a) == v.end()) v.push_back(tm.a);
+            if (tm.b >= 0 && std::find(v.begin(), v.end(), tm.b) == v.end()) v.push_back(tm.b);
         }
-    };
-    auto flush_pergate = [&]() {
-        for (const Term &tm : pending) {
-            PlanStep st;
-            st.kind = 1;
-            memset(&st.gate, 0, sizeof st.gate);
-            if (tm.b < 0) {
-                st.gate.kind = QSIM_G_PHASE;
-                st.gate.q0 = tm.a;
-                st.mat = {1.0, 0.0, 0.0, std::polar(1.0, tm.th)};
-            } else {
-                st.gate.kind = QSIM_G_CP;
-                st.gate.q0 = tm.a;
-                st.gate.q1 = tm.b;
-                st.gate.params[0] = tm.th;
-            }
-            P->steps.push_back(st);
-            P->npergate++;
-        }
-        pending.clear();
-    };
-    std::vector<const Item *> rem;
-    for (auto &it : items) rem.push_back(&it);
+    } else {
+        for (int k = 0; k < it->nq; k++) v.push_back(it->q[k]);
+    }
+}
+
+// One block of the sweep over rem (state in S: pending terms, global phase;
+// results in S.Q / U / pre / outside / left / ng). allow != 0 restricts the
+// block to those qubits; dry skips the matrices.
+void tc_sweep_block(TcSweep &S, const std::vector<const Item *> &rem, uint64_t allow, bool dry)
+{
+    const int n = S.n;
+    S.Q.clear();
+    S.U.assign(1, 1.0);
+    S.outside.assign(n, 0);
+    S.pre.clear();
+    S.left.clear();
+    S.ng = 0;
+    std::vector<char> blocked(n, 0), touched(n, 0);
     std::vector<int> qv;
-    while (!rem.empty()) {
-        std::vector<int> Q;                   // block qubits, block bit b <-> Q[b]
-        std::vector<cd> U(1, 1.0);
-        std::vector<char> blocked(n, 0), touched(n, 0), outside(n, 0);
-        std::vector<std::pair<int, std::pair<int, double>>> pre;   // (block qubit, (outside qubit, angle))
-        std::vector<const Item *> left;
-        int ng = 0;
-        for (const Item *it : rem) {
-            item_qubits(it, qv);
-            bool blk = false;
-            for (int q : qv) blk = blk || blocked[q];
-            if (!blk && it->kind == 1) {
-                for (const Term &tm : it->terms) pending.push_back(tm);
-                gphase *= it->gphase;
-                continue;
+    std::vector<int> &Q = S.Q;
+    std::vector<cd> &U = S.U;
+    for (const Item *it : rem) {
+        item_qubits(it, qv);
+        bool blk = false;
+        for (int q : qv) blk = blk || blocked[q];
+        if (!blk && it->kind == 1) {
+            for (const Term &tm : it->terms) S.pending.push_back(tm);
+            S.gphase *= it->gphase;
+            continue;
+        }
+        bool fits = !blk && it->kind == 0;
+        std::vector<int> nq = Q;
+        if (fits) {
+            for (int q : qv) {
+                if (S.outside[q]) fits = false;
+                if (allow && !(allow & bit(q))) fits = false;
+                if (std::find(nq.begin(), nq.end(), q) == nq.end()) nq.push_back(q);
             }
-            bool fits = !blk && it->kind == 0;
-            std::vector<int> nq = Q;
-            if (fits) {
-                for (int q : qv) {
-                    if (outside[q]) fits = false;
-                    if (std::find(nq.begin(), nq.end(), q) == nq.end()) nq.push_back(q);
+            if (nq.size() > 6) fits = false;
+        }
+        // pending terms this gate must see first
+        std::vector<Term> keep, fold, hoist;
+        if (fits) {
+            auto in_op = [&](int q) { return std::find(qv.begin(), qv.end(), q) != qv.end(); };
+            auto in_blk = [&](int q) { return std::find(nq.begin(), nq.end(), q) != nq.end(); };
+            for (const Term &tm : S.pending) {
+                bool t = in_op(tm.a) || (tm.b >= 0 && in_op(tm.b));
+                if (!t) {
+                    keep.push_back(tm);
+                    continue;
                 }
-                if (nq.size() > 6) fits = false;
-            }
-            // pending terms this gate must see first
-            std::vector<Term> keep, fold, hoist;
-            if (fits) {
-                auto in_op = [&](int q) { return std::find(qv.begin(), qv.end(), q) != qv.end(); };
-                auto in_blk = [&](int q) { return std::find(nq.begin(), nq.end(), q) != nq.end(); };
-                for (const Term &tm : pending) {
-                    bool t = in_op(tm.a) || (tm.b >= 0 && in_op(tm.b));
-                    if (!t) {
-                        keep.push_back(tm);
-                        continue;
-                    }
-                    if (tm.b < 0 || (in_blk(tm.a) && in_blk(tm.b))) {
-                        fold.push_back(tm);
-                        continue;
-                    }
-                    int q = in_blk(tm.a) ? tm.a : tm.b;
-                    if (touched[q]) {
-                        fits = false;
-                        break;
-                    }
-                    hoist.push_back(tm);
+                if (tm.b < 0 || (in_blk(tm.a) && in_blk(tm.b))) {
+                    fold.push_back(tm);
+                    continue;
                 }
+                int q = in_blk(tm.a) ? tm.a : tm.b;
+                if (touched[q]) {
+                    fits = false;
+                    break;
+                }
+                hoist.push_back(tm);
             }
-            if (!fits) {
-                for (int q : qv) blocked[q] = 1;
-                left.push_back(it);
-                continue;
-            }
-            pending.swap(keep);
-            // extend U to nq (new qubits become higher block bits)
-            int od = 1 << Q.size(), nd = 1 << nq.size();
-            if (nd != od) {
+        }
+        if (!fits) {
+            for (int q : qv) blocked[q] = 1;
+            S.left.push_back(it);
+            continue;
+        }
+        S.pending.swap(keep);
+        // extend U to nq (new qubits become higher block bits)
+        int od = 1 << Q.size(), nd = 1 << nq.size();
+        if (nd != od) {
+            if (!dry) {
                 std::vector<cd> V((size_t)nd * nd, 0.0);
                 for (int r = 0; r < nd; r++)
                     for (int c = 0; c < nd; c++)
                         if ((r / od) == (c / od)) V[(size_t)r * nd + c] = U[(size_t)(r % od) * od + (c % od)];
                 U.swap(V);
-                Q = nq;
             }
-            auto bpos = [&](int q) { return (int)(std::find(Q.begin(), Q.end(), q) - Q.begin()); };
-            // folded terms: a diagonal on the block, applied now
-            if (!fold.empty()) {
-                for (int r = 0; r < nd; r++) {
-                    double ang = 0;
-                    for (const Term &tm : fold) {
-                        bool ba = (r >> bpos(tm.a)) & 1;
-                        bool bb = tm.b < 0 ? true : (bool)((r >> bpos(tm.b)) & 1);
-                        if (ba && bb) ang += tm.th;
-                    }
-                    cd f = std::polar(1.0, ang);
-                    for (int c = 0; c < nd; c++) U[(size_t)r * nd + c] *= f;
+            Q = nq;
+        }
+        auto bpos = [&](int q) { return (int)(std::find(Q.begin(), Q.end(), q) - Q.begin()); };
+        // folded terms: a diagonal on the block, applied now
+        if (!fold.empty() && !dry) {
+            for (int r = 0; r < nd; r++) {
+                double ang = 0;
+                for (const Term &tm : fold) {
+                    bool ba = (r >> bpos(tm.a)) & 1;
+                    bool bb = tm.b < 0 ? true : (bool)((r >> bpos(tm.b)) & 1);
+                    if (ba && bb) ang += tm.th;
                 }
+                cd f = std::polar(1.0, ang);
+                for (int c = 0; c < nd; c++) U[(size_t)r * nd + c] *= f;
             }
-            for (const Term &tm : hoist) {
-                int q = std::find(Q.begin(), Q.end(), tm.a) != Q.end() ? tm.a : tm.b;
-                int o = q == tm.a ? tm.b : tm.a;
-                pre.push_back({q, {o, tm.th}});
-                outside[o] = 1;
-            }
-            // the gate
+        }
+        for (const Term &tm : hoist) {
+            int q = std::find(Q.begin(), Q.end(), tm.a) != Q.end() ? tm.a : tm.b;
+            int o = q == tm.a ? tm.b : tm.a;
+            S.pre.push_back({q, {o, tm.th}});
+            S.outside[o] = 1;
+        }
+        // the gate
+        if (!dry) {
             int gd = 1 << it->nq, gmask = 0;
             int pos[2];
             for (int k = 0; k < it->nq; k++) {
@@ -941,9 +941,144 @@ qsim_status plan_build_tc(const qsim_circuit *cir, const qsim_run_opts *opts, co
                     for (int c = 0; c < nd; c++) W[(size_t)r * nd + c] += a * U[(size_t)x * nd + c];
                 }
             U.swap(W);
-            for (int k = 0; k < it->nq; k++) touched[it->q[k]] = 1;
-            ng++;
         }
+        for (int k = 0; k < it->nq; k++) touched[it->q[k]] = 1;
+        S.ng++;
+    }
+}
+
+// Candidate qubit sets for the next block: grown from each of the first kMaxSeeds dense items.
+std::vector<uint64_t> tc_candidates(const std::vector<const Item *> &rem)
+{
+    const int kMaxSeeds = 48;
+    std::vector<uint64_t> out;
+    int seeds = 0;
+    for (size_t s = 0; s < rem.size() && seeds < kMaxSeeds; s++) {
+        if (rem[s]->kind != 0) continue;
+        seeds++;
+        uint64_t m = 0;
+        int cnt = 0;
+        for (int k = 0; k < rem[s]->nq; k++)
+            if (!(m & bit(rem[s]->q[k]))) {
+                m |= bit(rem[s]->q[k]);
+                cnt++;
+            }
+        for (size_t i = 0; i < rem.size() && cnt < 6; i++) {
+            const Item *it = rem[i];
+            if (it->kind != 0) continue;
+            uint64_t mi = 0;
+            int ci = 0;
+            for (int k = 0; k < it->nq; k++)
+                if (!(mi & bit(it->q[k]))) {
+                    mi |= bit(it->q[k]);
+                    ci++;
+                }
+            if (!(mi & m)) continue;
+            int add = 0;
+            for (int k = 0; k < it->nq; k++) add += !(m & bit(it->q[k])) && (mi & bit(it->q[k]));
+            if (cnt + add > 6) continue;
+            m |= mi;
+            cnt += add;
+        }
+        if (std::find(out.begin(), out.end(), m) == out.end()) out.push_back(m);
+    }
+    return out;
+}
+
+// The restriction for the next block: 0 (first fit) unless a candidate set
+// takes more dense items in a matrix-free sweep.
+uint64_t tc_choose(const TcSweep &S0, const std::vector<const Item *> &rem)
+{
+    TcSweep T = S0;
+    tc_sweep_block(T, rem, 0, true);
+    int best = T.ng;
+    uint64_t pick = 0;
+    for (uint64_t m : tc_candidates(rem)) {
+        TcSweep C = S0;
+        tc_sweep_block(C, rem, m, true);
+        if (C.ng > best) {
+            best = C.ng;
+            pick = m;
+        }
+    }
+    return pick;
+}
+
+// Blocks of a matrix-free sweep of the whole circuit (choose: per-block choice).
+int tc_count_blocks(int n, const std::vector<Item> &items, bool choose)
+{
+    TcSweep S;
+    S.n = n;
+    std::vector<const Item *> rem;
+    for (auto &it : items) rem.push_back(&it);
+    int blocks = 0;
+    while (!rem.empty()) {
+        const uint64_t allow = choose ? tc_choose(S, rem) : 0;
+        tc_sweep_block(S, rem, allow, true);
+        if (S.ng == 0) {
+            if (S.left.empty()) break;
+            S.pending.clear();   // flushed per gate before the barrier
+            S.left.erase(S.left.begin());
+            rem = S.left;
+            continue;
+        }
+        blocks++;
+        rem = S.left;
+    }
+    return blocks;
+}
+
+}  // namespace
+
+qsim_status plan_build_tc(const qsim_circuit *cir, const qsim_run_opts *opts, const int *start_l2p, qsim_plan *P)
+{
+    const int n = cir->n;
+    if (n < 6) return fail(QSIM_E_UNSUPPORTED, "tensor-core plans need n >= 6");
+    P->n = n;
+    P->dt = QSIM_C64;
+    P->prec = opts->prec;
+    P->ngates = cir->ngates;
+    {
+        std::vector<int> l2p(n);
+        for (int q = 0; q < n; q++) l2p[q] = start_l2p ? start_l2p[q] : q;
+        P->start_l2p = l2p;
+    }
+    std::vector<Item> items;
+    classify_gates(cir, start_l2p, true, items, P->final_l2p, P->nswaps);
+    const bool choose = tc_count_blocks(n, items, true) < tc_count_blocks(n, items, false);
+    TcSweep S;
+    S.n = n;
+    auto flush_pergate = [&]() {
+        for (const Term &tm : S.pending) {
+            PlanStep st;
+            st.kind = 1;
+            memset(&st.gate, 0, sizeof st.gate);
+            if (tm.b < 0) {
+                st.gate.kind = QSIM_G_PHASE;
+                st.gate.q0 = tm.a;
+                st.mat = {1.0, 0.0, 0.0, std::polar(1.0, tm.th)};
+            } else {
+                st.gate.kind = QSIM_G_CP;
+                st.gate.q0 = tm.a;
+                st.gate.q1 = tm.b;
+                st.gate.params[0] = tm.th;
+            }
+            P->steps.push_back(st);
+            P->npergate++;
+        }
+        S.pending.clear();
+    };
+    std::vector<const Item *> rem;
+    for (auto &it : items) rem.push_back(&it);
+    while (!rem.empty()) {
+        const uint64_t allow = choose ? tc_choose(S, rem) : 0;
+        tc_sweep_block(S, rem, allow, false);
+        std::vector<int> &Q = S.Q;
+        std::vector<cd> &U = S.U;
+        auto &pre = S.pre;
+        auto &outside = S.outside;
+        std::vector<const Item *> left = S.left;
+        const int ng = S.ng;
         if (ng == 0) {
             if (left.empty()) {
                 rem.clear();
@@ -963,9 +1098,9 @@ qsim_status plan_build_tc(const qsim_circuit *cir, const qsim_run_opts *opts, co
             continue;
         }
         // the global phase gathered so far rides on this block
-        if (std::abs(gphase - cd(1.0)) > 1e-15) {
-            for (auto &x : U) x *= gphase;
-            gphase = 1.0;
+        if (std::abs(S.gphase - cd(1.0)) > 1e-15) {
+            for (auto &x : U) x *= S.gphase;
+            S.gphase = 1.0;
         }
         // pad the block to six qubits here (the kernel reads a pre-diagonal
         // partner's bit from the group index, where padded bits are 0):
@@ -1032,10 +1167,10 @@ qsim_status plan_build_tc(const qsim_circuit *cir, const qsim_run_opts *opts, co
         P->ndense += ng;
         rem = left;
     }
-    if (std::abs(gphase - cd(1.0)) > 1e-15) {
+    if (std::abs(S.gphase - cd(1.0)) > 1e-15) {
         PlanStep st;
         st.kind = 2;
-        st.phase = gphase;
+        st.phase = S.gphase;
         P->steps.push_back(st);
     }
     flush_pergate();
