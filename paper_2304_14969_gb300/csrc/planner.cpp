@@ -947,11 +947,49 @@ void tc_sweep_block(TcSweep &S, const std::vector<const Item *> &rem, uint64_t a
     }
 }
 
-// Candidate qubit sets for the next block: grown from each of the first kMaxSeeds dense items.
-std::vector<uint64_t> tc_candidates(const std::vector<const Item *> &rem)
+// Candidate qubit sets for the next block, from each of the first
+// kMaxSeeds dense items: (1) the item's qubits plus those of the following
+// items that overlap and fit; (2) for a two-qubit item, its qubits grown one
+// qubit at a time by the qubit with the most dense two-qubit gates to the
+// set among the next kWindow ones (compact clusters of the interaction
+// graph, e.g. patches of a 2-D grid).
+std::vector<uint64_t> tc_candidates(const std::vector<const Item *> &rem, int n)
 {
-    const int kMaxSeeds = 48;
+    const int kMaxSeeds = 48, kWindow = 400;
     std::vector<uint64_t> out;
+    std::vector<int> w((size_t)n * n, 0);
+    {
+        int cnt = 0;
+        for (size_t i = 0; i < rem.size() && cnt < kWindow; i++) {
+            const Item *it = rem[i];
+            if (it->kind != 0 || it->nq != 2) continue;
+            w[(size_t)it->q[0] * n + it->q[1]]++;
+            w[(size_t)it->q[1] * n + it->q[0]]++;
+            cnt++;
+        }
+    }
+    int gseeds = 0;
+    for (size_t s = 0; s < rem.size() && gseeds < kMaxSeeds; s++) {
+        if (rem[s]->kind != 0 || rem[s]->nq != 2) continue;
+        gseeds++;
+        uint64_t m = bit(rem[s]->q[0]) | bit(rem[s]->q[1]);
+        for (int size = 2; size < 6; size++) {
+            int best = -1, bw = 0;
+            for (int q = 0; q < n; q++) {
+                if (m & bit(q)) continue;
+                int ww = 0;
+                for (int x = 0; x < n; x++)
+                    if (m & bit(x)) ww += w[(size_t)q * n + x];
+                if (ww > bw) {
+                    bw = ww;
+                    best = q;
+                }
+            }
+            if (best < 0) break;
+            m |= bit(best);
+        }
+        if (std::find(out.begin(), out.end(), m) == out.end()) out.push_back(m);
+    }
     int seeds = 0;
     for (size_t s = 0; s < rem.size() && seeds < kMaxSeeds; s++) {
         if (rem[s]->kind != 0) continue;
@@ -993,7 +1031,7 @@ uint64_t tc_choose(const TcSweep &S0, const std::vector<const Item *> &rem)
     tc_sweep_block(T, rem, 0, true);
     int best = T.ng;
     uint64_t pick = 0;
-    for (uint64_t m : tc_candidates(rem)) {
+    for (uint64_t m : tc_candidates(rem, S0.n)) {
         TcSweep C = S0;
         tc_sweep_block(C, rem, m, true);
         if (C.ng > best) {

@@ -87,6 +87,25 @@ def test_tc_plan_from_permuted_map(emu, name):
         assert infid(y, ref) <= 1e-12
 
 
+@pytest.mark.parametrize("case", ["grid", "paper"])
+def test_tc_plan_candidate_sets_on_grids(emu, case):
+    """On 2-D circuits the planner picks each block's qubits among candidate
+    sets (interaction-graph clusters), which a first-fit sweep would not: a
+    4x5 grid circuit of 8 layers takes at most 12 blocks (first fit: 16) and
+    the paper-family 4x5 circuit at most 13; the result still matches the
+    oracle from a Gaussian ket and from a permuted start map."""
+    n = 20
+    g = W.grid_rcs_circuit(4, 5, 8, seed=2) if case == "grid" else W.paper_random_circuit(4, 5, 8, seed=9)
+    x = W.gaussian_state(n, 21)
+    ref = oracle.apply_circuit(x, g)
+    y, info = run(emu, n, g, x)
+    assert info[0] <= (12 if case == "grid" else 13)
+    assert infid(y, ref) <= 1e-12 and np.max(np.abs(y - ref)) <= 1e-12
+    start = [int(v) for v in np.random.default_rng(5).permutation(n)]
+    y, _ = run(emu, n, g, x, start=start)
+    assert infid(y, ref) <= 1e-12
+
+
 def test_tc_plan_qft_block_count(emu):
     """QFT-16: controlled phases deferred into the Hadamards' blocks; the
     whole transform takes three six-qubit blocks and no per-gate step."""
