@@ -41,6 +41,34 @@ def emu():
     return lib
 
 
+@pytest.fixture(scope="module")
+def femu():
+    """CPU emulation of fused SIMT plans (tests/fused_plan_emu.cpp)."""
+    out = os.path.join(HERE, "_build", "libfusedemu.so")
+    os.makedirs(os.path.dirname(out), exist_ok=True)
+    srcs = [os.path.join(HERE, "fused_plan_emu.cpp"), os.path.join(CSRC, "planner.cpp"), os.path.join(CSRC, "gates.cpp"),
+            os.path.join(CSRC, "tc_geom.cpp")]
+    cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-I", os.path.join(ROOT, "include"), "-I", CSRC,
+           "-I", os.path.join(CUDA, "include"), "-o", out] + srcs + \
+          ["-L", os.path.join(CUDA, "lib64"), "-lcudart", "-Wl,-rpath," + os.path.join(CUDA, "lib64")]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        pytest.fail("building the fused-plan emulator failed:\n" + r.stderr[-3000:])
+    lib = C.CDLL(out)
+    lib.emu_fused_run.restype = C.c_int
+    return lib
+
+
+def run_fused(lib, n, gates, x, dt, tile=0, start=None):
+    c = Q.Circuit(n, gates)
+    y = np.ascontiguousarray(x.astype(np.complex128)).copy()
+    info = (C.c_int64 * 4)()
+    sp = (C.c_int * n)(*start) if start is not None else None
+    rc = lib.emu_fused_run(c.ptr(), dt, tile, sp, y.ctypes.data_as(C.c_void_p), info)
+    assert rc == 0, rc
+    return y, list(info)
+
+
 def run(lib, n, gates, x, start=None, prec=1):
     c = Q.Circuit(n, gates)
     y = np.ascontiguousarray(x.astype(np.complex128)).copy()
@@ -73,6 +101,45 @@ def test_tc_plan_matches_oracle(emu, name):
     assert info[0] >= 1
     assert infid(y, ref) <= 1e-12
     assert np.max(np.abs(y - ref)) <= 1e-12
+
+
+FUSED_CASES = {
+    "qft14": lambda: (14, W.qft_circuit(14), W.gaussian_state(14, 1)),
+    "iqft12": lambda: (12, W.inverse_circuit(W.qft_circuit(12)), W.gaussian_state(12, 2)),
+    "grid16": lambda: (16, W.grid_rcs_circuit(4, 4, 8, seed=3), W.gaussian_state(16, 3)),
+    "paper15": lambda: (15, W.paper_random_circuit(3, 5, 6, seed=4), W.gaussian_state(15, 4)),
+    "random13": lambda: (13, W.random_1q_circuit(13, 250, 7), W.gaussian_state(13, 7)),
+}
+
+
+@pytest.mark.parametrize("dt", [0, 1])
+@pytest.mark.parametrize("name", sorted(FUSED_CASES))
+def test_fused_plan_matches_oracle(femu, name, dt):
+    """Fused SIMT plans (passes of on-chip tiles, deferred phases, register
+    transposes), applied on the CPU with the kernel's semantics for the
+    staged constant block, against the oracle: infidelity <= 1e-12 for
+    complex128 plans (FP64 coefficients), <= 1e-6 for complex64 ones (FP32
+    coefficients)."""
+    n, g, x = FUSED_CASES[name]()
+    ref = oracle.apply_circuit(x, g)
+    y, info = run_fused(femu, n, g, x, dt)
+    assert info[0] >= 1
+    assert infid(y, ref) <= (1e-12 if dt else 1e-6)
+
+
+@pytest.mark.parametrize("tile", [9, 10, 11, 12])
+def test_fused_plan_tile_sizes_and_start_maps(femu, tile):
+    """Smaller tiles (more passes, more deferred phases from outside the
+    tile) and a permuted start map."""
+    n, g, x = FUSED_CASES["grid16"]()
+    ref = oracle.apply_circuit(x, g)
+    start = [int(v) for v in np.random.default_rng(tile).permutation(n)]
+    for dt in (0, 1):
+        y, info = run_fused(femu, n, g, x, dt, tile=tile, start=start)
+        assert infid(y, ref) <= (1e-12 if dt else 1e-6)
+    n, g, x = FUSED_CASES["qft14"]()
+    y, _ = run_fused(femu, n, g, x, 1, tile=tile, start=list(range(n))[::-1])
+    assert infid(y, oracle.apply_circuit(x, g)) <= 1e-12
 
 
 @pytest.mark.parametrize("name", ["qft16", "random14", "grid20"])
