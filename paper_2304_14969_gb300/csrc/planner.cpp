@@ -668,15 +668,19 @@ qsim_status plan_build(const qsim_circuit *cir, qsim_dtype dt, const qsim_run_op
         }
         B.pending.clear();
     };
-    std::vector<int> qv;
-    while (!rem.empty()) {
-        // grow the tile in circuit order
-        std::vector<int> tile;  // high qubits
+    // One pass's sweep over rm: the tile's high qubits grow in circuit order
+    // (allow != 0: only from allow), diagonal items run wherever they are not
+    // blocked. Returns the dense items taken.
+    auto pass_sweep = [&](const std::vector<const Item *> &rm, uint64_t allow, std::vector<int> &tile,
+                          std::vector<const Item *> &exec, std::vector<const Item *> &left) {
+        tile.clear();
+        exec.clear();
+        left.clear();
         std::vector<char> in_tile(n, 0), blocked(n, 0);
         for (int b = 0; b < c; b++) in_tile[b] = 1;
-        std::vector<const Item *> exec, left;
-        int ndense = 0;
-        for (const Item *it : rem) {
+        int nd = 0;
+        std::vector<int> qv;
+        for (const Item *it : rm) {
             item_qubits(it, qv);
             bool blk = false;
             for (int q : qv) blk = blk || blocked[q];
@@ -686,21 +690,125 @@ qsim_status plan_build(const qsim_circuit *cir, qsim_dtype dt, const qsim_run_op
             }
             if (!blk && it->kind == 0) {
                 int need = 0;
-                for (int q : qv) need += !in_tile[q];
-                if ((int)tile.size() + need <= t - c) {
+                bool ok = true;
+                for (int q : qv)
+                    if (!in_tile[q]) {
+                        need++;
+                        if (allow && !(allow & bit(q))) ok = false;
+                    }
+                if (ok && (int)tile.size() + need <= t - c) {
                     for (int q : qv)
                         if (!in_tile[q]) {
                             in_tile[q] = 1;
                             tile.push_back(q);
                         }
                     exec.push_back(it);
-                    ndense++;
+                    nd++;
                     continue;
                 }
             }
             for (int q : qv) blocked[q] = 1;
             left.push_back(it);
         }
+        return nd;
+    };
+    // Candidate high-qubit sets for the next pass (as for tensor-core blocks:
+    // sets grown from each of the first dense items, by overlap in circuit
+    // order and by interaction-graph weight to the set and the low qubits);
+    // the candidate whose sweep takes the most dense items wins.
+    auto pass_choose = [&](const std::vector<const Item *> &rm) -> uint64_t {
+        const int kMaxSeeds = 48, kWindow = 400, hq = t - c;
+        std::vector<int> w((size_t)n * n, 0);
+        int cnt = 0;
+        for (size_t i = 0; i < rm.size() && cnt < kWindow; i++) {
+            const Item *it = rm[i];
+            if (it->kind != 0 || it->nq != 2) continue;
+            w[(size_t)it->q[0] * n + it->q[1]]++;
+            w[(size_t)it->q[1] * n + it->q[0]]++;
+            cnt++;
+        }
+        const uint64_t low = bit(c) - 1;
+        std::vector<uint64_t> cands;
+        auto add = [&](uint64_t m) {
+            if (m && std::find(cands.begin(), cands.end(), m) == cands.end()) cands.push_back(m);
+        };
+        int seeds = 0;
+        for (size_t s0 = 0; s0 < rm.size() && seeds < kMaxSeeds; s0++) {
+            const Item *sd = rm[s0];
+            if (sd->kind != 0) continue;
+            seeds++;
+            uint64_t m0 = 0;
+            for (int k = 0; k < sd->nq; k++) m0 |= bit(sd->q[k]);
+            m0 &= ~low;
+            // (1) overlap growth in circuit order
+            uint64_t m = m0;
+            for (size_t i = 0; i < rm.size() && __builtin_popcountll(m) < hq; i++) {
+                const Item *it = rm[i];
+                if (it->kind != 0) continue;
+                uint64_t mi = 0;
+                for (int k = 0; k < it->nq; k++) mi |= bit(it->q[k]);
+                if (!(mi & (m | low))) continue;
+                if (__builtin_popcountll(m | (mi & ~low)) <= hq) m |= mi & ~low;
+            }
+            add(m);
+            // (2) interaction-graph growth
+            m = m0;
+            while (__builtin_popcountll(m) < hq) {
+                int best = -1, bw = 0;
+                for (int q = c; q < n; q++) {
+                    if (m & bit(q)) continue;
+                    int ww = 0;
+                    for (int x = 0; x < n; x++)
+                        if ((m | low) & bit(x)) ww += w[(size_t)q * n + x];
+                    if (ww > bw) {
+                        bw = ww;
+                        best = q;
+                    }
+                }
+                if (best < 0) break;
+                m |= bit(best);
+            }
+            add(m);
+        }
+        std::vector<int> tl;
+        std::vector<const Item *> ex, lf;
+        int best = pass_sweep(rm, 0, tl, ex, lf);
+        uint64_t pick = 0;
+        for (uint64_t m : cands) {
+            const int nd = pass_sweep(rm, m, tl, ex, lf);
+            if (nd > best) {
+                best = nd;
+                pick = m;
+            }
+        }
+        return pick;
+    };
+    // passes of a whole sweep (choose: per-pass choice), without building them
+    auto count_passes = [&](bool choose) {
+        std::vector<const Item *> rm = rem, ex, lf;
+        std::vector<int> tl;
+        int np = 0;
+        while (!rm.empty()) {
+            const int nd = pass_sweep(rm, choose ? pass_choose(rm) : 0, tl, ex, lf);
+            if (nd == 0) {
+                if (lf.empty()) break;
+                lf.erase(lf.begin());
+                rm = lf;
+                continue;
+            }
+            np++;
+            rm = lf;
+        }
+        return np;
+    };
+    const bool choose = count_passes(true) < count_passes(false);
+    while (!rem.empty()) {
+        std::vector<int> tile;  // high qubits
+        std::vector<const Item *> exec, left;
+        const int ndense = pass_sweep(rem, choose ? pass_choose(rem) : 0, tile, exec, left);
+        std::vector<char> in_tile(n, 0);
+        for (int b = 0; b < c; b++) in_tile[b] = 1;
+        for (int q : tile) in_tile[q] = 1;
         if (ndense == 0) {
             // only diagonal items and barriers remain runnable: fold the
             // diagonal ones, then run the first barrier per gate

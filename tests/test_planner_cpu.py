@@ -109,6 +109,9 @@ FUSED_CASES = {
     "grid16": lambda: (16, W.grid_rcs_circuit(4, 4, 8, seed=3), W.gaussian_state(16, 3)),
     "paper15": lambda: (15, W.paper_random_circuit(3, 5, 6, seed=4), W.gaussian_state(15, 4)),
     "random13": lambda: (13, W.random_1q_circuit(13, 250, 7), W.gaussian_state(13, 7)),
+    # 2-D circuits whose passes take their high qubits from candidate sets
+    "grid20": lambda: (20, W.grid_rcs_circuit(4, 5, 10, seed=1), W.gaussian_state(20, 5)),
+    "paper20": lambda: (20, W.paper_random_circuit(4, 5, 9, seed=2), W.gaussian_state(20, 5)),
 }
 
 
