@@ -125,6 +125,18 @@ def test_fused_grid_vs_oracle(Q, rows, cols, layers):
     assert infid(y, ref) <= 1e-12
 
 
+@pytest.mark.parametrize("dt", [0, 1])
+def test_fused_paper_family_vs_oracle(Q, dt):
+    """The paper's random family (U3 + C/A-Pauli couplers, diagonal CZ/AZ
+    deferred) on a 4x5 grid, 9 layers: passes whose high qubits come from
+    candidate sets, against the oracle."""
+    n = 20
+    g = W.paper_random_circuit(4, 5, 9, seed=2)
+    x = W.gaussian_state(n, 5)
+    ref = oracle.apply_circuit(x, g)
+    assert infid(run_gpu(Q, n, g, x, dt, mode=1), ref) <= TOL_INF[dt]
+
+
 def test_fused_tile_sizes(Q):
     n = 16
     x = W.gaussian_state(n, 3)
