@@ -134,18 +134,51 @@ class ClockSampler:
 
 # ------------------------------------------------------------ CPU oracle
 
-def oracle_sample(n_gates=16, n=N_QUBITS, seed=0):
-    """The FP64 CPU oracle on the first n_gates gates of the 27-qubit QFT
-    (single thread), in updates/s."""
+def cpu_model():
+    """Host CPU model name (from /proc/cpuinfo; Arm hosts may list no name)."""
+    try:
+        names, parts = [], []
+        for ln in open("/proc/cpuinfo"):
+            k, _, v = ln.partition(":")
+            k = k.strip().lower()
+            if k in ("model name", "cpu model"):
+                names.append(v.strip())
+            elif k == "cpu part":
+                parts.append(v.strip())
+        if names:
+            return names[0]
+        if parts:
+            return f"Arm CPU part {parts[0]}"
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+_ORACLE_INPUTS = {}
+
+
+def oracle_sample(n_gates=16, n=N_QUBITS, seed=0, all_cores=False):
+    """The FP64 CPU oracle on the first n_gates gates of the 27-qubit QFT on a
+    Gaussian ket: the one-thread build, or the all-core build (the same C
+    loops with OpenMP pragmas). Returns (updates/s, seconds, gates, threads)."""
     import oracle
     from paper_2304_14969_gb300 import workloads as W
     g = W.qft_circuit(n)[:n_gates]
-    x = W.gaussian_state(n, seed)
-    oracle.lib()
-    t0 = time.perf_counter()
-    oracle.apply_circuit(x, g)
-    dt = time.perf_counter() - t0
-    return len(g) * (1 << n) / dt, dt, len(g)
+    key = (n, seed)
+    if key not in _ORACLE_INPUTS:
+        _ORACLE_INPUTS.clear()
+        _ORACLE_INPUTS[key] = W.gaussian_state(n, seed)
+    x = _ORACLE_INPUTS[key]
+    oracle.use_all_cores(all_cores)
+    try:
+        threads = oracle.threads()
+        t0 = time.perf_counter()
+        oracle.apply_circuit(x, g)
+        dt = time.perf_counter() - t0
+    finally:
+        oracle.use_all_cores(False)
+    return len(g) * (1 << n) / dt, dt, len(g), threads
 
 
 def main_config(world, blocks=5):
@@ -158,24 +191,30 @@ def main_config(world, blocks=5):
 
 
 def run_reference(args):
+    """The reference arm: the FP64 CPU oracle (all-core build) on the host's
+    cores, each step the first 16 gates of the 27-qubit QFT on the same
+    Gaussian ket, in the same metric."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     vals, secs = [], []
+    ng, threads = 16, 1
     for i in range(args.warmup + args.steps):
-        v, dt, ng = oracle_sample(n_gates=4)
+        v, dt, ng, threads = oracle_sample(n_gates=16, all_cores=True)
         if i >= args.warmup:
             vals.append(v)
             secs.append(dt)
     value = float(np.median(vals))
+    sample = (f"first {ng} gates of the 27-qubit QFT on a Gaussian ket per step, FP64 oracle (all-core build, "
+              f"{threads} threads, {cpu_model()}, nproc {os.cpu_count()})")
     line = {
         "impl": "reference", "metric": "amplitude-gate updates/s", "value": value, "unit": "updates/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * float(np.median(secs)), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": dict(main_config(1), sample="first 4 gates of the 27-qubit QFT per step (FP64 oracle)"),
-        "cpu_baseline": {"value": value, "unit": "updates/s", "cores": 1, "kind": "oracle",
-                         "sample": "first 4 gates of the 27-qubit QFT per step, FP64, one thread"},
+        "config": dict(main_config(1), sample=sample),
+        "cpu_baseline": {"value": value, "unit": "updates/s", "cores": threads, "kind": "oracle", "sample": sample,
+                         "cpu_model": cpu_model(), "nproc": os.cpu_count()},
         "e2e": {"value": value, "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -330,17 +369,26 @@ def main():
     e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
     st2.close()
     e2e_val = job_value(world, ng * N, max_over_ranks(e2e_ms, world))
+    phases = e2e_phases(Q, C, torch, plans[0], st, stream, host_in, host_out)
+    parity = headline_parity(Q, W, plans, st, n)
 
     extras = {}
     if rank == 0 and not args.no_extras:
-        extras = extra_legs(Q, W, C, torch, circ, x, n, ng)
+        extras = extra_legs(Q, W, C, torch, circ, x, n, ng, plans)
     if rank != 0:
         return
     cpu = {}
     if not args.no_extras:
-        v, dt, k = oracle_sample()
-        cpu = {"value": v, "unit": "updates/s", "cores": 1, "kind": "oracle",
-               "sample": f"first {k} gates of the 27-qubit QFT on a Gaussian ket, FP64, one thread ({dt:.1f} s)"}
+        # the oracle as it stands on the host's cores (all-core build), and
+        # its one-thread build beside it
+        v, dt, k, thr = oracle_sample(n_gates=64, all_cores=True)
+        v1, dt1, k1, _ = oracle_sample(n_gates=8)
+        cpu = {"value": v, "unit": "updates/s", "cores": thr, "kind": "oracle",
+               "sample": f"first {k} gates of the 27-qubit QFT on a Gaussian ket, FP64 oracle, all-core build "
+                         f"({thr} threads, {dt:.1f} s)",
+               "cpu_model": cpu_model(), "nproc": os.cpu_count(),
+               "one_thread": {"value": v1, "unit": "updates/s", "cores": 1,
+                              "sample": f"first {k1} gates, one-thread build ({dt1:.1f} s)"}}
     line = {
         "metric": "amplitude-gate updates/s", "value": value, "unit": "updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -351,7 +399,9 @@ def main():
                      "kernel": "k_tc_pipe", "alg_bytes_per_launch": alg_bytes,
                      "launch_ms": launch_ms, "peak_source": "measured hbm_gbs" if peaks else "fallback"},
         "e2e": {"value": e2e_val, "unit": "updates/s", "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 8 * N,
-                "ms_per_step": e2e_ms, "pipeline": "2 kets on 2 streams: upload, QFT, download in logical order"},
+                "ms_per_step": e2e_ms, "pipeline": "2 kets on 2 streams: upload, QFT, download in logical order",
+                "phases_one_stream": phases},
+        "infidelity": parity,
         "gpu_launches": args.steps * npass,   # timed steps (the kernel-timing loop is outside the step region)
         "clocks": clk,
         "cpu_baseline": cpu,
@@ -362,6 +412,69 @@ def main():
         line["speedup_vs_per_gate_fp64"] = extras["per_gate_fp64"]["ms"] / float(np.mean(pass_ms))
     print(json.dumps(line))
     st.close()
+
+
+def _chunked_fidelity(y, ref_fn, N, chunk=1 << 24):
+    """1 - |<y|ref>|^2 / (<y|y><ref|ref>) in FP64, with ref produced chunk by
+    chunk by ref_fn(start, stop) (keeps host memory small at 2^27)."""
+    ip = 0j
+    ny = nr = 0.0
+    for a in range(0, N, chunk):
+        b = min(N, a + chunk)
+        yy = y[a:b].astype(np.complex128)
+        rr = ref_fn(a, b)
+        ip += np.vdot(yy, rr)
+        ny += float(np.vdot(yy, yy).real)
+        nr += float(np.vdot(rr, rr).real)
+    return 1.0 - abs(ip) ** 2 / (ny * nr)
+
+
+def headline_parity(Q, W, plans, st, n):
+    """The timed path's error, measured beside the headline: the bench's two
+    plans applied to a basis ket |x>, every output of the first against
+    Eq. (dft)'s closed form y_k = 2^(-n/2) exp(2 pi i x k / 2^n), the second
+    (the QFT applied again) against QFT^2 |x> = |-x mod 2^n>."""
+    N = 1 << n
+    x = W.basis_index(n, 27)
+    Q.qsim_set_basis(st.h, x)
+    n0 = plans[0].execute_norm(st)
+    y = st.download()
+
+    def cf(a, b):
+        ks = np.arange(a, b, dtype=np.int64)
+        return np.exp(2j * np.pi * ((x * ks) % N).astype(np.float64) / N) / np.sqrt(N)
+
+    f0 = _chunked_fidelity(y, cf, N)
+    n1 = plans[1].execute_norm(st)
+    y = st.download().astype(np.complex128)
+    j = (N - x) % N
+    f1 = 1.0 - abs(y[j]) ** 2 / float(np.vdot(y, y).real)
+    return {"input": f"basis |x>, x = {x}", "infidelity_first_plan_vs_closed_form": f0,
+            "infidelity_second_plan_vs_closed_form": f1, "fused_norms": [n0, n1], "bound": 1e-6,
+            "within_bound": bool(f0 <= 1e-6 and f1 <= 1e-6)}
+
+
+def e2e_phases(Q, C, torch, plan, st, stream, host_in, host_out, reps=4):
+    """Device time of each phase of one end-to-end step on one stream (CUDA
+    events): upload of the input ket from pinned memory, the plan, the
+    download in logical order (permutation and copy to pinned memory)."""
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    acc = np.zeros(3)
+    for r in range(reps + 1):
+        ev[0].record(stream)
+        Q.qsim_upload(st.h, C.c_void_p(host_in.data_ptr()))
+        ev[1].record(stream)
+        plan.execute(st)
+        ev[2].record(stream)
+        Q.qsim_download_async(st.h, C.c_void_p(host_out.data_ptr()))
+        ev[3].record(stream)
+        Q.qsim_synchronize(st.h)
+        if r:
+            acc += [ev[k].elapsed_time(ev[k + 1]) for k in range(3)]
+    acc /= reps
+    gb = host_in.numel() * host_in.element_size() / 1e9
+    return {"upload_ms": acc[0], "plan_ms": acc[1], "download_ms": acc[2], "upload_gbs": gb / (acc[0] * 1e-3),
+            "download_gbs": gb / (acc[2] * 1e-3)}
 
 
 def time_plan(Q, C, plan, st, reps):
@@ -483,7 +596,7 @@ def c128_tc_leg(Q, C, torch, circ, x, n, ng, sref, peaks, fused_ms, per_gate_ms,
     return r
 
 
-def extra_legs(Q, W, C, torch, circ, x, n, ng):
+def extra_legs(Q, W, C, torch, circ, x, n, ng, plans):
     out = {}
     N = 1 << n
     # plain per-gate FP64 path on the same circuit
@@ -501,6 +614,16 @@ def extra_legs(Q, W, C, torch, circ, x, n, ng):
     Q.qsim_synchronize(s128.h)
     pg = time.perf_counter() - t0
     out["per_gate_fp64"] = {"updates_per_s": ng * N / pg, "ms": pg * 1e3, "dtype": "c128"}
+    # the headline path (first plan of the timed steps) on the same Gaussian
+    # input, against the per-gate FP64 result: the infidelity of the speedup
+    ref = s128.download()
+    sh = Q.State(n, Q.QSIM_C64)
+    sh.upload(x)
+    plans[0].execute_norm(sh)
+    yh = sh.download()
+    sh.close()
+    out["per_gate_fp64"]["infidelity_of_headline_path"] = _chunked_fidelity(yh, lambda a, b: ref[a:b], N)
+    del ref, yh
     peaks = {}
     pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(pp):

@@ -8,7 +8,12 @@ no arithmetic of the method.
 
 The arithmetic lives in ``oracle.c`` (single-threaded C, ``double complex``),
 compiled here with gcc into ``oracle/_build/liboracle.so``. This module only
-marshals numpy arrays into it. Paper sections followed (arXiv 2304.14969):
+marshals numpy arrays into it. The same file compiled with ``-fopenmp``
+(``liboracle_mt.so``, the only difference being its ``omp`` pragmas) runs the
+index loops on all host cores; ``use_all_cores(True)`` routes the calls below
+to it (large parity cases and the all-core CPU baseline). The one-thread build
+stays the default and is the one the pins check; the all-core build is checked
+against it. Paper sections followed (arXiv 2304.14969):
 Sec. II (gate-by-gate Schroedinger evolution), Eq. (dft) (QFT definition),
 Sec. III.A (SDRP check and projection), Eq. (fid_model) and Eq. (fid_exact).
 """
@@ -24,8 +29,10 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
 _OUT = os.path.join(_HERE, "_build", "liboracle.so")
+_OUT_MT = os.path.join(_HERE, "_build", "liboracle_mt.so")
 _lock = threading.Lock()
-_lib = None
+_libs = {}
+_all_cores = False
 
 # The oracle's own gate numbering (mirrors the enum in oracle.c).
 KIND = {
@@ -47,44 +54,68 @@ DECISION_DTYPE = np.dtype([
 ], align=True)
 
 
+def _compile(out: str, extra, force: bool) -> str:
+    with _lock:
+        if (not force and os.path.exists(out)
+                and os.path.getmtime(out) >= os.path.getmtime(_SRC)):
+            return out
+        os.makedirs(os.path.dirname(out), exist_ok=True)
+        tmp = out + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared",
+                               "-fno-fast-math", *extra, "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, out)
+        return out
+
+
 def build(force: bool = False) -> str:
     """Compile oracle.c with gcc (no fast-math: the compensated sums need
-    IEEE semantics). Returns the path of the shared library."""
-    with _lock:
-        if (not force and os.path.exists(_OUT)
-                and os.path.getmtime(_OUT) >= os.path.getmtime(_SRC)):
-            return _OUT
-        os.makedirs(os.path.dirname(_OUT), exist_ok=True)
-        tmp = _OUT + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared",
-                               "-fno-fast-math", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _OUT)
-        return _OUT
+    IEEE semantics), one-thread and all-core builds. Returns the path of the
+    one-thread library."""
+    _compile(_OUT_MT, ["-fopenmp"], force)
+    return _compile(_OUT, [], force)
+
+
+def use_all_cores(flag: bool = True) -> None:
+    """Routes the calls of this module to the all-core build (True) or the
+    one-thread build (False, the default)."""
+    global _all_cores
+    _all_cores = bool(flag)
+
+
+def threads() -> int:
+    """Threads the selected build runs its index loops on."""
+    return int(lib().orc_threads())
+
+
+def _load(path):
+    L = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    i32, f64, u64 = ctypes.c_int, ctypes.c_double, ctypes.c_uint64
+    L.orc_threads.restype = i32
+    L.orc_gate_matrix.argtypes = [P, P]
+    L.orc_apply_circuit.argtypes = [P, i32, P, i32]
+    L.orc_apply_kq.argtypes = [P, i32, i32, P, P]
+    L.orc_dense_circuit.argtypes = [i32, P, i32, P]
+    L.orc_norm2.argtypes = [P, i32]
+    L.orc_norm2.restype = f64
+    L.orc_probs.argtypes = [P, i32, P]
+    L.orc_prob1.argtypes = [P, i32, i32]
+    L.orc_prob1.restype = f64
+    L.orc_inner.argtypes = [P, P, i32, P]
+    L.orc_bloch.argtypes = [P, i32, i32, P]
+    L.orc_dft_sample.argtypes = [P, i32, u64, P]
+    L.orc_sdrp_project.argtypes = [P, i32, i32, P]
+    L.orc_sdrp_run.argtypes = [P, i32, P, i32, f64, f64, P, i32, P, P, P, i32]
+    L.orc_sdrp_run.restype = i32
+    return L
 
 
 def lib():
-    global _lib
-    if _lib is None:
-        L = ctypes.CDLL(build())
-        P = ctypes.c_void_p
-        i32, f64, u64 = ctypes.c_int, ctypes.c_double, ctypes.c_uint64
-        L.orc_gate_matrix.argtypes = [P, P]
-        L.orc_apply_circuit.argtypes = [P, i32, P, i32]
-        L.orc_apply_kq.argtypes = [P, i32, i32, P, P]
-        L.orc_dense_circuit.argtypes = [i32, P, i32, P]
-        L.orc_norm2.argtypes = [P, i32]
-        L.orc_norm2.restype = f64
-        L.orc_probs.argtypes = [P, i32, P]
-        L.orc_prob1.argtypes = [P, i32, i32]
-        L.orc_prob1.restype = f64
-        L.orc_inner.argtypes = [P, P, i32, P]
-        L.orc_bloch.argtypes = [P, i32, i32, P]
-        L.orc_dft_sample.argtypes = [P, i32, u64, P]
-        L.orc_sdrp_project.argtypes = [P, i32, i32, P]
-        L.orc_sdrp_run.argtypes = [P, i32, P, i32, f64, f64, P, i32, P, P, P, i32]
-        L.orc_sdrp_run.restype = i32
-        _lib = L
-    return _lib
+    key = "mt" if _all_cores else "st"
+    if key not in _libs:
+        path = build()
+        _libs[key] = _load(_OUT_MT if _all_cores else path)
+    return _libs[key]
 
 
 def _ptr(a: np.ndarray):

@@ -5,6 +5,12 @@ logits. Parameter vector layout: W1[H][nfeat], b1[H], W2[H][H], b2[H],
 W3[H], b3. numpy matrix products serve as the primitive; the backward pass
 is the chain rule written out layer by layer. Pinned by central finite
 differences in tests/test_oracle_mlp.py.
+
+The optimiser step is Adam as published (Kingma and Ba, "Adam: A Method for
+Stochastic Optimization", ICLR 2015, Algorithm 1), in FP64: exponential
+moving averages of the gradient and of its square, each divided by its
+bias correction, and a step of lr times their ratio. Pinned by hand-computed
+first and second steps in tests/test_oracle_mlp.py.
 """
 import numpy as np
 
@@ -63,3 +69,30 @@ def loss_grad(theta, X, y, nf, H):
     gb1 = dz1.sum(axis=0)
     g = np.concatenate([gW1.ravel(), gb1, gW2.ravel(), gb2, gW3, [gb3]])
     return L, g
+
+
+def adam_step(theta, m, v, g, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam update at step t >= 1 (Kingma and Ba 2015, Algorithm 1).
+    Returns the new (theta, m, v); the inputs are not modified."""
+    theta = np.asarray(theta, dtype=np.float64)
+    g = np.asarray(g, dtype=np.float64)
+    m = beta1 * np.asarray(m, dtype=np.float64) + (1.0 - beta1) * g
+    v = beta2 * np.asarray(v, dtype=np.float64) + (1.0 - beta2) * g * g
+    m_hat = m / (1.0 - beta1 ** t)
+    v_hat = v / (1.0 - beta2 ** t)
+    return theta - lr * m_hat / (np.sqrt(v_hat) + eps), m, v
+
+
+def train(theta, X, y, nf, H, lr, steps):
+    """`steps` Adam steps of the mean BCE loss on (X, y) from theta, moments
+    starting at zero. Returns (theta, losses), losses[t] at the start of
+    step t + 1."""
+    theta = np.asarray(theta, dtype=np.float64).copy()
+    m = np.zeros_like(theta)
+    v = np.zeros_like(theta)
+    losses = []
+    for t in range(1, steps + 1):
+        L, g = loss_grad(theta, X, y, nf, H)
+        losses.append(L)
+        theta, m, v = adam_step(theta, m, v, g, t, lr)
+    return theta, losses

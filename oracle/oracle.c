@@ -24,6 +24,14 @@
  *  - Sec. III.B, Eq. (fid_exact): F_exact = |<psi_approx|psi_exact>|^2.
  *  - Sec. III.C: the U(theta, phi, lambda) single-qubit gate.
  *
+ * All-core build: the same file compiled with -fopenmp (liboracle_mt.so)
+ * splits the iterations of the index loops across the host's threads; the
+ * only differences are the "omp" pragmas below. Element-wise loops give
+ * bit-identical results; each thread keeps its own compensated partial sums,
+ * merged (compensated) at the end, so sums agree with the one-thread build
+ * to within the compensated sums' error. The one-thread build is the
+ * oracle the pins check; the all-core build is checked against it.
+ *
  * Pins: every function here is checked by the CPU tests against closed
  * forms, library routines (numpy FFT, numpy kron-built matrices), brute
  * force on tiny inputs and identities; see tests/test_oracle_*.py.
@@ -85,6 +93,27 @@ static void nsum_add(nsum *a, double x)
 }
 
 static double nsum_get(const nsum *a) { return a->s + a->c; }
+
+#ifdef _OPENMP
+#include <omp.h>
+/* Merges a thread's partial sum into another (all-core build only). */
+static void nsum_merge(nsum *out, const nsum *in)
+{
+    nsum_add(out, in->s);
+    nsum_add(out, in->c);
+}
+#pragma omp declare reduction(nplus : nsum : nsum_merge(&omp_out, &omp_in)) initializer(omp_priv = (nsum){ 0, 0 })
+#endif
+
+/* Threads the index loops use: 1 in the one-thread build. */
+int orc_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 /* ------------------------------------------------------- gate matrices */
 
@@ -185,6 +214,9 @@ static int controls_hold(const orc_gate *g, uint64_t i)
 void orc_apply_1q(cplx *psi, int n, const cplx *u, int t, const orc_gate *ctl)
 {
     uint64_t N = (uint64_t)1 << n, bt = (uint64_t)1 << t;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
     for (uint64_t i = 0; i < N; i++) {
         if (i & bt) continue;
         if (ctl && !controls_hold(ctl, i)) continue;
@@ -198,6 +230,9 @@ void orc_apply_1q(cplx *psi, int n, const cplx *u, int t, const orc_gate *ctl)
 void orc_apply_2q(cplx *psi, int n, const cplx *u, int q0, int q1)
 {
     uint64_t N = (uint64_t)1 << n, b0 = (uint64_t)1 << q0, b1 = (uint64_t)1 << q1;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
     for (uint64_t i = 0; i < N; i++) {
         if ((i & b0) || (i & b1)) continue;
         uint64_t idx[4] = { i, i | b0, i | b1, i | b0 | b1 };
@@ -211,16 +246,20 @@ void orc_apply_2q(cplx *psi, int n, const cplx *u, int q0, int q1)
     }
 }
 
-/* psi <- U psi with U of size 2^k x 2^k on qubits[0..k-1]; qubits[b] is
- * bit b of U's row/column index. Gather, multiply, scatter. */
+/* psi <- U psi with U of size 2^k x 2^k on qubits[0..k-1] (k <= 8); qubits[b]
+ * is bit b of U's row/column index. Gather, multiply, scatter. */
 void orc_apply_kq(cplx *psi, int n, int k, const int *qubits, const cplx *u)
 {
+    if (k < 1 || k > 8) return;
     uint64_t N = (uint64_t)1 << n, D = (uint64_t)1 << k, mask = 0;
     for (int b = 0; b < k; b++) mask |= (uint64_t)1 << qubits[b];
-    uint64_t *idx = malloc(D * sizeof(uint64_t));
-    cplx *v = malloc(D * sizeof(cplx)), *w = malloc(D * sizeof(cplx));
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
     for (uint64_t i = 0; i < N; i++) {
         if (i & mask) continue;
+        uint64_t idx[256];
+        cplx v[256], w[256];
         for (uint64_t l = 0; l < D; l++) {
             uint64_t j = i;
             for (int b = 0; b < k; b++)
@@ -234,7 +273,6 @@ void orc_apply_kq(cplx *psi, int n, int k, const int *qubits, const cplx *u)
         }
         for (uint64_t l = 0; l < D; l++) psi[idx[l]] = w[l];
     }
-    free(idx); free(v); free(w);
 }
 
 /* Applies one gate record. Returns 0 on success, -1 on an unknown kind. */
@@ -317,6 +355,9 @@ double orc_norm2(const cplx *psi, int n)
 {
     uint64_t N = (uint64_t)1 << n;
     nsum s = { 0, 0 };
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) reduction(nplus : s)
+#endif
     for (uint64_t i = 0; i < N; i++) nsum_add(&s, creal(psi[i]) * creal(psi[i]) + cimag(psi[i]) * cimag(psi[i]));
     return nsum_get(&s);
 }
@@ -324,6 +365,9 @@ double orc_norm2(const cplx *psi, int n)
 void orc_probs(const cplx *psi, int n, double *p)
 {
     uint64_t N = (uint64_t)1 << n;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
     for (uint64_t i = 0; i < N; i++) p[i] = creal(psi[i]) * creal(psi[i]) + cimag(psi[i]) * cimag(psi[i]);
 }
 
@@ -332,6 +376,9 @@ double orc_prob1(const cplx *psi, int n, int q)
 {
     uint64_t N = (uint64_t)1 << n;
     nsum one = { 0, 0 }, all = { 0, 0 };
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) reduction(nplus : one, all)
+#endif
     for (uint64_t i = 0; i < N; i++) {
         double a = creal(psi[i]) * creal(psi[i]) + cimag(psi[i]) * cimag(psi[i]);
         nsum_add(&all, a);
@@ -345,6 +392,9 @@ void orc_inner(const cplx *a, const cplx *b, int n, double out[2])
 {
     uint64_t N = (uint64_t)1 << n;
     nsum re = { 0, 0 }, im = { 0, 0 };
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) reduction(nplus : re, im)
+#endif
     for (uint64_t i = 0; i < N; i++) {
         cplx z = conj(a[i]) * b[i];
         nsum_add(&re, creal(z));
@@ -363,6 +413,9 @@ void orc_bloch(const cplx *psi, int n, int q, double r[3])
 {
     uint64_t N = (uint64_t)1 << n, bq = (uint64_t)1 << q;
     nsum r00 = { 0, 0 }, r11 = { 0, 0 }, sre = { 0, 0 }, sim = { 0, 0 };
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) reduction(nplus : r00, r11, sre, sim)
+#endif
     for (uint64_t i = 0; i < N; i++) {
         if (i & bq) continue;
         cplx a = psi[i], b = psi[i | bq];
@@ -387,6 +440,9 @@ void orc_dft_sample(const cplx *x, int n, uint64_t j, double out[2])
 {
     uint64_t N = (uint64_t)1 << n;
     nsum re = { 0, 0 }, im = { 0, 0 };
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) reduction(nplus : re, im)
+#endif
     for (uint64_t k = 0; k < N; k++) {
         uint64_t m = (j * k) & (N - 1);
         double ang = 2.0 * M_PI * (double)m / (double)N;
@@ -423,9 +479,15 @@ void orc_sdrp_project(cplx *psi, int n, int q, const double r[3])
     cplx Vd[4] = { conj(V[0]), conj(V[2]), conj(V[1]), conj(V[3]) };
     uint64_t N = (uint64_t)1 << n, bq = (uint64_t)1 << q;
     orc_apply_1q(psi, n, V, q, NULL);                 /* step 2: rotate */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
     for (uint64_t i = 0; i < N; i++)                  /* step 3: post-select |0> */
         if (i & bq) psi[i] = 0;
     double s = sqrt(orc_norm2(psi, n));
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
     for (uint64_t i = 0; i < N; i++) psi[i] /= s;
     orc_apply_1q(psi, n, Vd, q, NULL);                /* step 4: rotate back */
 }

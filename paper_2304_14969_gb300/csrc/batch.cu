@@ -534,11 +534,11 @@ qsim_status qsim_batch_create(const qsim_circuit *const *cs, int count, const qs
     size_t lin_bytes = ((size_t)max_lin * 16 + 15) & ~(size_t)15;
     b->stage_off = (int)(kBatchTile + lin_bytes);
     b->smem = kBatchTile + lin_bytes + max_stage;
-    if (b->smem > 220 * 1024) {
+    if (b->smem > kFusedSmemCap) {
         batch_free(b);
         return fail(QSIM_E_UNSUPPORTED, "batch pass constants too large for shared memory");
     }
-    cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedSmemCap);
     int occ = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch, kBatchThreads, b->smem);
     if (occ < 1) occ = 1;

@@ -133,12 +133,12 @@ template <typename R, int RB, int NT, int MINB>
 cudaError_t launch_pass_t(void *amps, const FPassDev &d, cudaStream_t st)
 {
     using V = typename FV<R>::T;
-    size_t smem = ((size_t)sizeof(V) << d.t) + (((size_t)d.nlin * 16 + 15) & ~(size_t)15) + d.stage_bytes;
-    if (smem > 220 * 1024) return cudaErrorInvalidValue;
+    const size_t smem = fused_pass_smem(d, sizeof(V) == 8 ? QSIM_C64 : QSIM_C128);
+    if (smem > kFusedSmemCap) return cudaErrorInvalidValue;
     auto kern = k_fused_pass<R, RB, NT, MINB>;
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedSmemCap);
         attr = true;
     }
     uint64_t ntiles = 1ull << (d.n - d.t);

@@ -73,6 +73,16 @@ struct FPassDev {
     InsSpec ins;             // sorted hq for tile-id expansion
 };
 
+// Dynamic shared memory of one fused-pass CTA: the tile, the per-tile
+// factors of partners outside the tile, the pass's constant block; a pass
+// needing more than kFusedSmemCap is refused when the plan is built.
+constexpr size_t kFusedSmemCap = 220 * 1024;
+inline size_t fused_pass_smem(const FPassDev &d, qsim_dtype dt)
+{
+    const size_t amp = dt == QSIM_C64 ? 8 : 16;
+    return (amp << d.t) + (((size_t)d.nlin * 16 + 15) & ~(size_t)15) + (size_t)d.stage_bytes;
+}
+
 // Host-side plan
 struct PlanPass {
     FPassDev dev;            // stage pointer filled at upload

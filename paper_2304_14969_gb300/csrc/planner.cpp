@@ -783,13 +783,17 @@ qsim_status plan_build(const qsim_circuit *cir, qsim_dtype dt, const qsim_run_op
         }
         return pick;
     };
-    // passes of a whole sweep (choose: per-pass choice), without building them
-    auto count_passes = [&](bool choose) {
+    // passes of a whole sweep (choose: per-pass choice), without building
+    // them; masks receives the high-qubit set chosen at each step of the
+    // sweep, which the build loop below repeats step for step
+    auto count_passes = [&](bool choose, std::vector<uint64_t> *masks) {
         std::vector<const Item *> rm = rem, ex, lf;
         std::vector<int> tl;
         int np = 0;
         while (!rm.empty()) {
-            const int nd = pass_sweep(rm, choose ? pass_choose(rm) : 0, tl, ex, lf);
+            const uint64_t m = choose ? pass_choose(rm) : 0;
+            if (masks) masks->push_back(m);
+            const int nd = pass_sweep(rm, m, tl, ex, lf);
             if (nd == 0) {
                 if (lf.empty()) break;
                 lf.erase(lf.begin());
@@ -801,11 +805,15 @@ qsim_status plan_build(const qsim_circuit *cir, qsim_dtype dt, const qsim_run_op
         }
         return np;
     };
-    const bool choose = count_passes(true) < count_passes(false);
+    std::vector<uint64_t> chosen;
+    const bool choose = count_passes(true, &chosen) < count_passes(false, nullptr);
+    size_t step_i = 0;
     while (!rem.empty()) {
         std::vector<int> tile;  // high qubits
         std::vector<const Item *> exec, left;
-        const int ndense = pass_sweep(rem, choose ? pass_choose(rem) : 0, tile, exec, left);
+        const uint64_t mask = choose && step_i < chosen.size() ? chosen[step_i] : 0;
+        step_i++;
+        const int ndense = pass_sweep(rem, mask, tile, exec, left);
         std::vector<char> in_tile(n, 0);
         for (int b = 0; b < c; b++) in_tile[b] = 1;
         for (int q : tile) in_tile[q] = 1;
@@ -870,6 +878,14 @@ qsim_status plan_build(const qsim_circuit *cir, qsim_dtype dt, const qsim_run_op
         ps.tw_end = last ? (int)P->tw.size() : P->passes[i + 1].tw_begin;
         ps.ext_end = last ? (int)P->ext_bit.size() : P->passes[i + 1].ext_begin;
         B.finalize(ps);
+        // the pass kernel stages tile, per-tile partner factors and the
+        // constant block in shared memory: refuse at plan time a pass that
+        // could not launch
+        const size_t need = fused_pass_smem(ps.dev, dt);
+        if (need > kFusedSmemCap)
+            return fail(QSIM_E_UNSUPPORTED,
+                        "fused pass %zu needs %zu bytes of shared memory (at most %zu); plan with fewer tile qubits",
+                        i, need, kFusedSmemCap);
     }
     return QSIM_OK;
 }

@@ -1,6 +1,8 @@
 """Proposal MLP kernels against the FP64 reference (oracle/mlp.py):
 gradients of the GPU's fused forward/backward kernel, BF16 vs FP32
-inference, and an Adam training run that lowers the loss."""
+inference, Adam steps against the FP64 Adam of the reference (Kingma and
+Ba 2015, Algorithm 1) with the BF16 copies refreshed from the FP32 masters,
+and an Adam training run that lowers the loss."""
 import ctypes as C
 
 import numpy as np
@@ -65,6 +67,70 @@ def test_bf16_inference_close_to_fp32(Q):
     assert np.max(np.abs(out32 - zref)) <= 1e-4 * max(1.0, np.max(np.abs(zref)))
     # BF16 weights: 8 significant bits, FP32 accumulation
     assert np.max(np.abs(out16 - zref)) <= 3e-2 * max(1.0, np.max(np.abs(zref)))
+    Q.qsim_mlp_destroy(h)
+
+
+def bf16_round(a):
+    """FP32 -> BF16 (round to nearest, ties to even) -> FP32, on the encodings."""
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) >> 16 << 16
+    return u.astype(np.uint32).view(np.float32)
+
+
+def test_adam_steps_match_reference(Q):
+    """Three qsim_mlp_train_step calls against three FP64 Adam steps of the
+    reference from the same FP32 parameters, element by element. Where the
+    reference gradient is well above FP32 accumulation error in every step,
+    each parameter agrees within 1e-3 lr (the update is lr m_hat /
+    (sqrt(v_hat) + eps), so a relative gradient error d moves it by about
+    d lr); elsewhere within Adam's step bound (a sign of a near-zero sum may
+    differ). A dropped bias correction would move the first step by 3.2 lr
+    instead of lr and fail both. Afterwards inference with the BF16 copies
+    equals the FP64 forward pass at the masters rounded to BF16, so the
+    copies were refreshed by the step."""
+    nf, H, rows, lr, steps = 12, 64, 512, 1e-2, 3
+    h, npar = make(Q, nf, H, 11)
+    rng = np.random.default_rng(12)
+    X = rng.normal(0, 1, (rows, nf)).astype(np.float32)
+    y = (X[:, 1] - 0.3 * X[:, 4] > 0.1).astype(np.float32)
+    theta0 = np.zeros(npar, dtype=np.float32)
+    Q.qsim_mlp_get_params(h, fptr(theta0))
+    loss = C.c_float()
+    gpu_losses = []
+    for _ in range(steps):
+        Q.qsim_mlp_train_step(h, fptr(X), fptr(y), rows, C.c_float(lr), C.byref(loss))
+        gpu_losses.append(loss.value)
+    theta = np.zeros(npar, dtype=np.float32)
+    Q.qsim_mlp_get_params(h, fptr(theta))
+    X64, y64 = X.astype(np.float64), y.astype(np.float64)
+    ref, ref_losses = M.train(theta0.astype(np.float64), X64, y64, nf, H, lr, steps)
+    # gradients of the reference along its own trajectory
+    t = theta0.astype(np.float64)
+    m = np.zeros(npar)
+    v = np.zeros(npar)
+    gmin = np.full(npar, np.inf)
+    gmax = 0.0
+    for k in range(1, steps + 1):
+        _, g = M.loss_grad(t, X64, y64, nf, H)
+        gmin = np.minimum(gmin, np.abs(g))
+        gmax = max(gmax, float(np.max(np.abs(g))))
+        t, m, v = M.adam_step(t, m, v, g, k, lr)
+    assert np.max(np.abs(t - ref)) == 0.0
+    assert np.max(np.abs(np.array(gpu_losses) - np.array(ref_losses))) <= 1e-5
+    firm = gmin >= 1e-2 * gmax
+    assert firm.mean() > 0.3
+    d = np.abs(theta.astype(np.float64) - ref)
+    assert np.max(d[firm]) <= 1e-3 * lr + 1e-6 * np.max(np.abs(ref)), np.max(d[firm])
+    # Adam's step bound lr (1 - beta1) / sqrt(1 - beta2) per step, for each side
+    assert np.max(d) <= 2 * steps * lr * 0.1 / np.sqrt(0.001) + 1e-6
+    # BF16 copies: inference with them is the forward pass at the rounded masters
+    out16 = np.zeros(rows, dtype=np.float32)
+    Q.qsim_mlp_infer(h, fptr(X), rows, 1, fptr(out16))
+    z16, _ = M.forward(bf16_round(theta).astype(np.float64), X64, nf, H)
+    zold, _ = M.forward(bf16_round(theta0).astype(np.float64), X64, nf, H)
+    err = np.max(np.abs(out16 - z16))
+    assert err <= 1e-4 * max(1.0, np.max(np.abs(z16)))
+    assert np.max(np.abs(out16 - zold)) > 10 * err + 1e-6
     Q.qsim_mlp_destroy(h)
 
 

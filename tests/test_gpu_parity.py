@@ -128,8 +128,11 @@ def test_fused_grid_vs_oracle(Q, rows, cols, layers):
 @pytest.mark.parametrize("dt", [0, 1])
 def test_fused_paper_family_vs_oracle(Q, dt):
     """The paper's random family (U3 + C/A-Pauli couplers, diagonal CZ/AZ
-    deferred) on a 4x5 grid, 9 layers: passes whose high qubits come from
-    candidate sets, against the oracle."""
+    deferred) on a 4x5 grid, 9 layers, against the oracle. For complex128
+    the plan's passes take their high qubits from candidate sets (7 passes
+    instead of 9 with first-fit tiles); the complex64 plan gets 6 passes
+    either way, so complex64 candidate passes run in the 4x6 grid case of
+    test_fused_grid_vs_oracle instead."""
     n = 20
     g = W.paper_random_circuit(4, 5, 9, seed=2)
     x = W.gaussian_state(n, 5)

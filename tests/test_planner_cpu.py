@@ -378,3 +378,28 @@ def test_tc_pipe_phase_tables(emu, seed):
             tt = sum(int(tturn[b, i]) for i in range(n - 13) if (t >> i) & 1) % 2 ** 64
             f = np.exp(2j * np.pi * tt / 2 ** 64) * complex(gfac[gi, b, 0], gfac[gi, b, 1])
             assert abs(f - np.exp(2j * np.pi * direct / 2 ** 64)) < 1e-6
+
+
+# Passes of fused SIMT plans and blocks of tensor-core plans (plan only, no
+# GPU): the per-pass / per-block choice among candidate high-qubit sets gives
+# these counts; first-fit tiles give grid20 9 / 11, paper20 6 / 9, grid30
+# 17 / 21 passes (complex64 / complex128) and 30 tensor-core blocks on grid30.
+# A regression that turns the choice off, or plans more passes, fails here.
+PASS_COUNTS = {
+    "grid20": (lambda: (20, W.grid_rcs_circuit(4, 5, 10, seed=1)), 7, 10, 15),
+    "paper20": (lambda: (20, W.paper_random_circuit(4, 5, 9, seed=2)), 6, 7, 15),
+    "grid30": (lambda: (30, W.grid_rcs_circuit(5, 6, 10, seed=0)), 14, 17, 22),
+    "paper30": (lambda: (30, W.paper_random_circuit(5, 6, 10, seed=0)), 13, 15, 24),
+    "qft27": (lambda: (27, W.qft_circuit(27)), 3, 4, 5),
+}
+
+
+@pytest.mark.parametrize("name", sorted(PASS_COUNTS))
+def test_plan_pass_counts(name):
+    mk, c64, c128, tc = PASS_COUNTS[name]
+    n, g = mk()
+    Q.lib()
+    circ = Q.Circuit(n, g)
+    assert Q.Plan(circ, dtype=Q.QSIM_C64).info()["passes"] == c64
+    assert Q.Plan(circ, dtype=Q.QSIM_C128).info()["passes"] == c128
+    assert Q.Plan(circ, dtype=Q.QSIM_C64, prec=Q.QSIM_PREC_BF16X3).info()["passes"] == tc
