@@ -42,8 +42,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip the per-gate FP64, grid and CPU legs")
     ap.add_argument("--workload", default="qft27",
-                    help="qft27 (default: the 27-qubit QFT on tensor-core blocks), {qft,grid}<n>_{tc,tc128,simt} "
-                         "(one circuit on complex64 or complex128 tensor-core blocks or fused SIMT passes; "
+                    help="qft27 (default: the 27-qubit QFT on tensor-core blocks), {qft,grid}<n>_{tc,tf32,tc128,simt} "
+                         "(one circuit on complex64 BF16x3 or 3xTF32, or complex128, tensor-core blocks, or fused "
+                         "SIMT passes; "
                          "profiling workloads), or appendix_a (the paper's fidelity-model validation in full)")
     return ap.parse_args()
 
@@ -135,7 +136,16 @@ class ClockSampler:
 # ------------------------------------------------------------ CPU oracle
 
 def cpu_model():
-    """Host CPU model name (from /proc/cpuinfo; Arm hosts may list no name)."""
+    """Host CPU model name (lscpu's, else /proc/cpuinfo's; Arm hosts may list
+    only a part number there)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            k, _, v = ln.partition(":")
+            if k.strip().lower() == "model name" and v.strip():
+                return v.strip()
+    except Exception:
+        pass
     try:
         names, parts = [], []
         for ln in open("/proc/cpuinfo"):
@@ -342,32 +352,42 @@ def main():
 
     # ---- end to end through the public API with pinned host buffers: every
     # step uploads its input ket, runs the QFT and downloads the result in
-    # logical order; two kets on two streams, so one step's download
-    # overlaps the next one's upload and transform (the host link is full
-    # duplex). Wall-clock over all steps, after both streams drained.
-    st2 = Q.State(n, Q.QSIM_C64, stream=torch.cuda.Stream().cuda_stream)
-    host_out2 = torch.empty(N, dtype=torch.complex64).pin_memory()
-    kets, outs = (st, st2), (host_out, host_out2)
-    e2e_steps = max(4, min(args.steps, 12))
+    # logical order; `depth` kets on as many streams, so one step's download
+    # overlaps the next ones' uploads and transforms (the host link carries
+    # both directions at once). Wall-clock over all steps, after every
+    # stream drained; the pipeline depth (2 or 3) with the lower time is
+    # reported, both are recorded.
+    e2e_steps = max(6, min(args.steps, 12))
+    extra_kets = [Q.State(n, Q.QSIM_C64, stream=torch.cuda.Stream().cuda_stream) for _ in range(2)]
+    extra_outs = [torch.empty(N, dtype=torch.complex64).pin_memory() for _ in range(2)]
+    kets_all, outs_all = [st] + extra_kets, [host_out] + extra_outs
 
-    def e2e_step(k):
-        s_ = kets[k % 2]
-        Q.qsim_upload(s_.h, C.c_void_p(host_in.data_ptr()))
-        plans[0].execute(s_)
-        Q.qsim_download_async(s_.h, C.c_void_p(outs[k % 2].data_ptr()))
+    def e2e_run(depth):
+        kets, outs = kets_all[:depth], outs_all[:depth]
 
-    for k in range(2):
-        e2e_step(k)
-    for s_ in kets:
-        Q.qsim_synchronize(s_.h)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for k in range(e2e_steps):
-        e2e_step(k)
-    for s_ in kets:
-        Q.qsim_synchronize(s_.h)
-    e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
-    st2.close()
+        def e2e_step(k):
+            s_ = kets[k % depth]
+            Q.qsim_upload(s_.h, C.c_void_p(host_in.data_ptr()))
+            plans[0].execute(s_)
+            Q.qsim_download_async(s_.h, C.c_void_p(outs[k % depth].data_ptr()))
+
+        for k in range(depth):
+            e2e_step(k)
+        for s_ in kets:
+            Q.qsim_synchronize(s_.h)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(e2e_steps):
+            e2e_step(k)
+        for s_ in kets:
+            Q.qsim_synchronize(s_.h)
+        return (time.perf_counter() - t0) * 1e3 / e2e_steps
+
+    e2e_by_depth = {d: e2e_run(d) for d in (2, 3)}
+    e2e_depth = min(e2e_by_depth, key=e2e_by_depth.get)
+    e2e_ms = e2e_by_depth[e2e_depth]
+    for s_ in extra_kets:
+        s_.close()
     e2e_val = job_value(world, ng * N, max_over_ranks(e2e_ms, world))
     phases = e2e_phases(Q, C, torch, plans[0], st, stream, host_in, host_out)
     parity = headline_parity(Q, W, plans, st, n)
@@ -399,8 +419,9 @@ def main():
                      "kernel": "k_tc_pipe", "alg_bytes_per_launch": alg_bytes,
                      "launch_ms": launch_ms, "peak_source": "measured hbm_gbs" if peaks else "fallback"},
         "e2e": {"value": e2e_val, "unit": "updates/s", "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 8 * N,
-                "ms_per_step": e2e_ms, "pipeline": "2 kets on 2 streams: upload, QFT, download in logical order",
-                "phases_one_stream": phases},
+                "ms_per_step": e2e_ms,
+                "pipeline": f"{e2e_depth} kets on {e2e_depth} streams: upload, QFT, download in logical order",
+                "ms_per_step_by_depth": e2e_by_depth, "phases_one_stream": phases},
         "infidelity": parity,
         "gpu_launches": args.steps * npass,   # timed steps (the kernel-timing loop is outside the step region)
         "clocks": clk,
@@ -507,8 +528,10 @@ def run_grid_tc(args):
     n = int(args.workload[len(fam):].split("_")[0])
     simt = args.workload.endswith("_simt")
     c128 = args.workload.endswith("_tc128")
+    tf32 = args.workload.endswith("_tf32")
     dt, es = (Q.QSIM_C128, 16) if c128 else (Q.QSIM_C64, 8)
-    prec_kw = {} if simt else {"prec": Q.QSIM_PREC_BF16X6 if c128 else Q.QSIM_PREC_BF16X3}
+    prec_kw = {} if simt else {"prec": Q.QSIM_PREC_BF16X6 if c128 else Q.QSIM_PREC_3XTF32 if tf32
+                               else Q.QSIM_PREC_BF16X3}
     if fam == "grid":
         rows, cols = W.grid_shape(n)
         g = W.grid_rcs_circuit(rows, cols, 10, seed=0, n=n)
@@ -544,7 +567,7 @@ def run_grid_tc(args):
                       "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                       "data": "synthetic",
                       "config": {"workload": f"{fam}{n}_" + ("c128_tc_bf16x6" if c128 else "c64_fused_simt" if simt
-                                                             else "c64_tc_bf16x3"),
+                                                             else "c64_tc_3xtf32" if tf32 else "c64_tc_bf16x3"),
                                  "n_qubits": n, "gates": len(g), "launches_per_step": nb},
                       "roofline": {"bound": "hbm", "kernel": "k_fused_pass" if simt else "k_tc_pipe",
                                    "achieved": 2 * es * N / (ms / nb * 1e-3) / 1e9}}))
@@ -740,7 +763,7 @@ def extra_legs(Q, W, C, torch, circ, x, n, ng, plans):
         nbk = tps[0].info()["passes"]
         achieved = 2 * 8 * N / (ms / nbk * 1e-3) / 1e9
         out[f"qft27_c64_tc_{name}"] = {"updates_per_s": ng * N / (ms * 1e-3), "ms": ms, "blocks": nbk,
-                                       "kernel": "k_tc_pipe" if name == "bf16x3" else "k_tc_block", "hbm_gbs_per_block": achieved,
+                                       "kernel": "k_tc_pipe" if name == "bf16x3" else "k_tc_pipe (3xTF32)", "hbm_gbs_per_block": achieved,
                                        "frac_of_hbm": achieved / peaks.get("hbm_gbs", 6800.0),
                                        "infidelity_vs_simt": 1.0 - (ip[0] ** 2 + ip[1] ** 2) / (na.value * nb.value)}
         stc.close()
@@ -783,7 +806,7 @@ def extra_legs(Q, W, C, torch, circ, x, n, ng, plans):
         Q.qsim_norm(st2.h, C.byref(nb2))
         out[f"grid30_c64_tc_{name}"] = {
             "updates_per_s": len(g) * (1 << 30) / (ms * 1e-3), "ms": ms, "blocks": nb,
-            "kernel": "k_tc_pipe" if name == "bf16x3" else "k_tc_block", "hbm_gbs_per_block": achieved,
+            "kernel": "k_tc_pipe" if name == "bf16x3" else "k_tc_pipe (3xTF32)", "hbm_gbs_per_block": achieved,
             "frac_of_hbm": achieved / peaks.get("hbm_gbs", 6800.0),
             "infidelity_vs_simt": 1.0 - (ip[0] ** 2 + ip[1] ** 2) / (na.value * nb2.value)}
         st2.close()
@@ -810,7 +833,8 @@ def extra_legs(Q, W, C, torch, circ, x, n, ng, plans):
     out["approx54_paper_family_full_hbm"] = approx_leg(Q, W, pf, budget_gib=240.0, p_start=0.45, time_cap_s=60.0)
     # the same sweep with the learned proposal schedule (MLP trained here on
     # exhaustive-mode traces of 20-qubit circuits of the same family)
-    h = train_proposal_mlp(Q, W, C)
+    h, out["mlp_training"] = train_proposal_mlp(Q, W, C)
+    out["mlp_gain_20_28_qubits"] = mlp_gain_leg(Q, W, h)
     out["approx54_paper_family_mlp"] = approx_leg(Q, W, pf, budget_gib=80.0, mlp=h)
     out["appendix_a_validation"] = appa_leg(Q, W, C, seeds=10, time_cap_s=60.0)
     out["qft54_zero_factorized"] = qft_zero_factorized_leg(Q, W)
@@ -1026,11 +1050,17 @@ def appa_leg(Q, W, C, seeds=3, time_cap_s=90.0):
 def qft_zero_factorized_leg(Q, W, n=54):
     """QFT of |0...0> on 54 qubits through the approximate mode with p = 0
     (exact separation only): the ket stays factorised (2-qubit subsystems at
-    most), where a state vector would take 2^54 x 16 bytes."""
-    r, _, _, _ = Q.approx_run(n, W.qft_circuit(n), 0.0, dtype=Q.QSIM_C128, tau=1e-13)
-    return {"qubits": n, "gates": len(W.qft_circuit(n)), "seconds": r.seconds, "F": r.fidelity_model,
-            "rounds": r.n_rounds, "exact_separations": r.n_exact, "max_subsystem_qubits": r.max_subsystem_qubits,
-            "peak_bytes": r.peak_bytes, "state_vector_bytes": 16 * 2 ** n}
+    most), where a state vector would take 2^54 x 16 bytes. Also with the
+    unobservable optimisation (Sec. II.B): every controlled phase meets a
+    qubit in |0> and is removed, so nothing is ever composed."""
+    out = {}
+    for unobs in (0, 1):
+        r, _, _, _ = Q.approx_run(n, W.qft_circuit(n), 0.0, dtype=Q.QSIM_C128, tau=1e-13, unobservable=unobs)
+        out["unobservable_on" if unobs else "unobservable_off"] = {
+            "seconds": r.seconds, "F": r.fidelity_model, "rounds": r.n_rounds, "exact_separations": r.n_exact,
+            "checks": r.n_checks, "gates_removed_or_reduced": r.n_unobservable,
+            "max_subsystem_qubits": r.max_subsystem_qubits, "peak_bytes": r.peak_bytes}
+    return {"qubits": n, "gates": len(W.qft_circuit(n)), "state_vector_bytes": 16 * 2 ** n, **out}
 
 
 def run_appendix_a():
@@ -1046,24 +1076,63 @@ def run_appendix_a():
 
 def train_proposal_mlp(Q, W, C):
     """Proposal MLP (12 -> 64 -> 64 -> 1) trained on the GPU on traces of the
-    exhaustive approximate mode: 4x5 paper-family circuits (U3 + C/A Pauli),
-    7 layers, p from 0.3 to 0.7."""
+    exhaustive approximate mode: paper-family circuits (U3 + C/A Pauli) on
+    4x5, 4x6, 5x5 and 4x7 grids (20 to 28 qubits), 7 layers, p from 0.3 to
+    0.7. Returns (handle, training summary)."""
     X, Y = [], []
-    for seed in range(6):
-        g = W.paper_random_circuit(4, 5, 7, seed=200 + seed)
-        for p in (0.3, 0.35, 0.4, 0.45, 0.5, 0.55, 0.6, 0.65, 0.7):
-            _, _, (f, l), _ = Q.approx_run(20, g, p, trace_cap=20000)
-            X.append(f)
-            Y.append(l)
+    t0 = time.perf_counter()
+    shapes = ((4, 5), (4, 6), (5, 5), (4, 7))
+    for si, (rows, cols) in enumerate(shapes):
+        for seed in range(3 if rows * cols < 28 else 2):
+            g = W.paper_random_circuit(rows, cols, 7, seed=200 + 10 * si + seed)
+            for p in (0.3, 0.4, 0.5, 0.6, 0.7):
+                _, _, (f, l), _ = Q.approx_run(rows * cols, g, p, trace_cap=20000)
+                X.append(f)
+                Y.append(l)
+    t_traces = time.perf_counter() - t0
     X = np.ascontiguousarray(np.concatenate(X), dtype=np.float32)
     Y = np.ascontiguousarray(np.concatenate(Y), dtype=np.float32)
     h = C.c_void_p()
     Q.qsim_mlp_create(12, 64, 7, C.byref(h))
     loss = C.c_float()
     fp = lambda a: a.ctypes.data_as(C.POINTER(C.c_float))
+    t0 = time.perf_counter()
+    first = None
     for _ in range(400):
         Q.qsim_mlp_train_step(h, fp(X), fp(Y), len(X), C.c_float(3e-3), C.byref(loss))
-    return h
+        first = loss.value if first is None else first
+    t_train = time.perf_counter() - t0
+    return h, {"qubits": [r * c for r, c in shapes], "trace_rows": int(len(X)), "positive_fraction": float(Y.mean()),
+               "traces_seconds": t_traces, "train_steps": 400, "train_seconds": t_train, "loss_first": first,
+               "loss_last": loss.value}
+
+
+def mlp_gain_leg(Q, W, h):
+    """The learned schedule against the exhaustive one on held-out
+    paper-family circuits of 20, 24 and 28 qubits (7 layers), at equal p:
+    wall time, Bloch reductions, roundings and F model of each (summed over
+    the circuits)."""
+    out = []
+    for rows, cols in ((4, 5), (4, 6), (4, 7)):
+        n = rows * cols
+        gs = [W.paper_random_circuit(rows, cols, 7, seed=900 + s) for s in range(2)]
+        for p in (0.4, 0.6):
+            row = {"qubits": n, "p": p}
+            for name, kw in (("exhaustive", {}), ("mlp", {"schedule": Q.QSIM_SCHED_MLP, "mlp": h, "top_m": 4,
+                                                          "fallback_every": 8})):
+                sec = passes = rounds = 0
+                logF = 0.0
+                for g in gs:
+                    r, _, _, _ = Q.approx_run(n, g, p, **kw)
+                    sec += r.seconds
+                    passes += r.n_bloch_passes
+                    rounds += r.n_rounds
+                    logF += float(np.log(max(r.fidelity_model, 1e-300)))
+                row[name] = {"seconds": sec, "bloch_passes": passes, "rounds": rounds,
+                             "F_geomean": float(np.exp(logF / len(gs)))}
+            row["wall_time_gain"] = row["exhaustive"]["seconds"] / max(row["mlp"]["seconds"], 1e-12)
+            out.append(row)
+    return out
 
 
 if __name__ == "__main__":

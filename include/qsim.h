@@ -159,10 +159,14 @@ qsim_status qsim_upload(qsim_state *s, const void *host_amps);
 qsim_status qsim_download(qsim_state *s, void *host_amps);
 
 /* Stream-ordered form of qsim_download: queues the copy (and the permutation
- * into logical order, through a stream-ordered temporary, when the map is
- * not the identity) and returns. host_amps should be page-locked; it holds
- * the result once the stream has passed the copy (qsim_synchronize). Lets a
- * caller overlap one ket's download with another's upload and gates. */
+ * into logical order when the map is not the identity) and returns.
+ * host_amps should be page-locked; it holds the result once the stream has
+ * passed the copy (qsim_synchronize). Lets a caller overlap one ket's
+ * download with another's upload and gates. The permutation goes through a
+ * second ket-sized device buffer that a state of at most 8 GiB allocates at
+ * its first permutation and keeps until qsim_destroy (so kets pipelined on
+ * different streams never wait for one another's temporaries); larger kets
+ * take a stream-ordered temporary per call. */
 qsim_status qsim_download_async(qsim_state *s, void *host_amps);
 
 /* Device address of the amplitudes (physical order) and the current map:
@@ -300,7 +304,8 @@ qsim_status qsim_bloch_all(qsim_state *s, double *r);
 /* ------------------------------------------------- approximate mode */
 
 /* One SDRP decision (Sec. III.A step 2). action: 0 kept, 1 rounded
- * (eps <= p/2), 2 exact separation (eps <= tau). */
+ * (eps <= p/2), 2 exact separation (eps <= tau). reserved: 0 for a
+ * one-qubit check; 1 + the second qubit for a two-qubit check (opts->pairs). */
 typedef struct {
     int32_t gate;
     int32_t qubit;
@@ -338,6 +343,25 @@ typedef struct {
     int32_t *trace_labels;      /* host, optional: 1 if that check rounded */
     int64_t trace_cap;
     void *stream;               /* cudaStream_t to run on (NULL: default) */
+    int32_t unobservable;       /* 1: Sec. II.B unobservable optimisation (Table I, "eliminates
+                                   Z-basis eigenstate controls"): before a controlled one-qubit
+                                   gate or a controlled phase, a control (either qubit of a CP)
+                                   that is a one-qubit subsystem whose probability of the other
+                                   value is at most tau is projected onto that Z eigenstate (as
+                                   an exact separation: F unchanged); a control holding the
+                                   value the gate waits for is dropped, one holding the other
+                                   value removes the gate. A gate left acting on one qubit is
+                                   applied locally: nothing is composed and no check runs.
+                                   0: off */
+    int32_t pairs;              /* 1: two-qubit-subsystem SDRP (Sec. III.A, the rounding generalised
+                                   to a subsystem of two qubits): after the one-qubit checks of a
+                                   gate coupling exactly two qubits (a, b) still in one subsystem of
+                                   three or more qubits, the pair's reduced density matrix rho_ab
+                                   (FP64) gives eps = 1 - (its largest eigenvalue); eps <= p/2
+                                   rounds (F <- F (1 - eps)) and eps <= tau separates exactly,
+                                   projecting onto the top eigenvector, which becomes a two-qubit
+                                   subsystem. Its log entry: qubit a, reserved 1 + b, r the three
+                                   largest eigenvalues. 0: off */
 } qsim_approx_opts;
 
 typedef struct {
@@ -352,6 +376,7 @@ typedef struct {
     int64_t n_trace;            /* trace rows produced (may exceed trace_cap) */
     int32_t max_subsystem_qubits;
     int32_t budget_gate;        /* gate index where the budget was hit, or -1 */
+    int64_t n_unobservable;     /* gates removed or reduced by the unobservable optimisation */
 } qsim_approx_result;
 
 /* Runs circuit c from |0...0> with SDRP rounding at threshold p in [0, 1]

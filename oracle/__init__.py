@@ -105,7 +105,10 @@ def _load(path):
     L.orc_bloch.argtypes = [P, i32, i32, P]
     L.orc_dft_sample.argtypes = [P, i32, u64, P]
     L.orc_sdrp_project.argtypes = [P, i32, i32, P]
-    L.orc_sdrp_run.argtypes = [P, i32, P, i32, f64, f64, P, i32, P, P, P, i32]
+    L.orc_sdrp_run.argtypes = [P, i32, P, i32, f64, f64, P, i32, P, i32, i32, P, P, P, P, i32]
+    L.orc_rho2.argtypes = [P, i32, i32, i32, P]
+    L.orc_herm4_eig.argtypes = [P, P, P]
+    L.orc_sdrp_project2.argtypes = [P, i32, i32, i32, P]
     L.orc_sdrp_run.restype = i32
     return L
 
@@ -236,10 +239,18 @@ def sdrp_project(psi, q, r):
     return out
 
 
-def sdrp_run(n: int, gates, p: float, tau: float, force=None, psi0=None):
+def sdrp_run(n: int, gates, p: float, tau: float, force=None, psi0=None, force_actions=None,
+             unobservable=False, stats=None, pairs=False):
     """Runs the circuit from |0...0> (or psi0, a product state) with SDRP
     rounding on the full state vector. Returns (psi, F, nround, log) where
-    log is a structured array of decisions (gate, qubit, action, eps, r)."""
+    log is a structured array of decisions (gate, qubit, action, eps, r).
+    force: (gate, qubit) checks to run instead of the exhaustive schedule;
+    force_actions (with force): the decision of each forced check (0 keep,
+    1 round, 2 separate exactly, -1 decide by eps). unobservable: Sec.
+    II.B's elimination of Z-eigenstate controls (stats["unobservable"]
+    receives the number of gates removed or reduced, when stats is a dict).
+    pairs: the two-qubit-subsystem check after each gate coupling two
+    qubits (log entries with pad = 1 + the pair's second qubit)."""
     psi = np.zeros(1 << n, dtype=np.complex128) if psi0 is None else psi0.astype(np.complex128).copy()
     if psi0 is None:
         psi[0] = 1.0
@@ -253,8 +264,44 @@ def sdrp_run(n: int, gates, p: float, tau: float, force=None, psi0=None):
         fptr, nf = _ptr(f), f.shape[0]
     else:
         f, fptr, nf = None, None, 0
+    aptr = None
+    if force_actions is not None:
+        if f is None:
+            raise ValueError("force_actions needs force")
+        acts = np.ascontiguousarray(np.asarray(force_actions, dtype=np.int32).reshape(-1))
+        if acts.size != nf:
+            raise ValueError("one action per forced check")
+        aptr = _ptr(acts)
+    nu = ctypes.c_int(0)
     nlog = lib().orc_sdrp_run(_ptr(psi), n, _ptr(rec), len(rec), float(p), float(tau),
-                              fptr, nf, ctypes.byref(F), ctypes.byref(nr), _ptr(log), cap)
+                              fptr, nf, aptr, int(bool(unobservable)), int(bool(pairs)), ctypes.byref(F),
+                              ctypes.byref(nr),
+                              ctypes.byref(nu), _ptr(log), cap)
+    if stats is not None:
+        stats["unobservable"] = nu.value
     if nlog < 0:
         raise ValueError("unknown gate kind")
     return psi, F.value, nr.value, log[: min(nlog, cap)].copy()
+
+
+def rho2(psi, qa, qb):
+    """Normalised reduced density matrix of the pair (qa: bit 0, qb: bit 1)."""
+    out = np.zeros(16, dtype=np.complex128)
+    lib().orc_rho2(_ptr(psi), _nq(psi), qa, qb, _ptr(out))
+    return out.reshape(4, 4)
+
+
+def herm4_eig(H):
+    """(eigenvalues ascending, eigenvectors as columns) of a Hermitian 4 x 4."""
+    Hc = np.ascontiguousarray(H, dtype=np.complex128)
+    w = np.zeros(4)
+    v = np.zeros(16, dtype=np.complex128)
+    lib().orc_herm4_eig(_ptr(Hc), _ptr(w), _ptr(v))
+    return w, v.reshape(4, 4)
+
+
+def sdrp_project2(psi, qa, qb, phi):
+    out = psi.copy()
+    ph = np.ascontiguousarray(phi, dtype=np.complex128)
+    lib().orc_sdrp_project2(_ptr(out), _nq(out), qa, qb, _ptr(ph))
+    return out

@@ -492,6 +492,142 @@ void orc_sdrp_project(cplx *psi, int n, int q, const double r[3])
     orc_apply_1q(psi, n, Vd, q, NULL);                /* step 4: rotate back */
 }
 
+/* ------------------------------------------- two-qubit subsystems (SDRP) */
+
+/* Reduced density matrix of the pair (qa, qb) of psi, normalised:
+ * rho[x * 4 + y] = sum over the other qubits of psi[.. x ..] conj(psi[.. y ..])
+ * / <psi|psi>, where x = bit qa + 2 bit qb of the index. */
+void orc_rho2(const cplx *psi, int n, int qa, int qb, cplx rho[16])
+{
+    uint64_t N = (uint64_t)1 << n, ba = (uint64_t)1 << qa, bb = (uint64_t)1 << qb;
+    nsum re[16], im[16];
+    for (int k = 0; k < 16; k++) { re[k].s = re[k].c = 0; im[k].s = im[k].c = 0; }
+    for (uint64_t i = 0; i < N; i++) {
+        if ((i & ba) || (i & bb)) continue;
+        uint64_t idx[4] = { i, i | ba, i | bb, i | ba | bb };
+        for (int x = 0; x < 4; x++)
+            for (int y = 0; y < 4; y++) {
+                cplx z = psi[idx[x]] * conj(psi[idx[y]]);
+                nsum_add(&re[x * 4 + y], creal(z));
+                nsum_add(&im[x * 4 + y], cimag(z));
+            }
+    }
+    double tr = nsum_get(&re[0]) + nsum_get(&re[5]) + nsum_get(&re[10]) + nsum_get(&re[15]);
+    for (int k = 0; k < 16; k++) rho[k] = (nsum_get(&re[k]) + I * nsum_get(&im[k])) / tr;
+}
+
+/* Eigenvalues (ascending in w[0..3]) and unit eigenvectors (columns of
+ * vec, vec[r * 4 + c] = component r of vector c) of a Hermitian 4 x 4 H.
+ * The cyclic Jacobi method (Jacobi 1846; see Golub and Van Loan, Matrix
+ * Computations, Sec. 8.5) runs on the real symmetric 8 x 8 embedding
+ * M = [[Re H, -Im H], [Im H, Re H]]: each eigenvalue of H appears twice
+ * in M, and an eigenvector (x, y) of M gives the eigenvector x + i y of H. */
+void orc_herm4_eig(const cplx H[16], double w[4], cplx vec[16])
+{
+    double A[8][8], V[8][8];
+    for (int r = 0; r < 4; r++)
+        for (int c = 0; c < 4; c++) {
+            A[r][c] = creal(H[r * 4 + c]);
+            A[r][c + 4] = -cimag(H[r * 4 + c]);
+            A[r + 4][c] = cimag(H[r * 4 + c]);
+            A[r + 4][c + 4] = creal(H[r * 4 + c]);
+        }
+    for (int r = 0; r < 8; r++)
+        for (int c = 0; c < 8; c++) V[r][c] = r == c ? 1.0 : 0.0;
+    for (int sweep = 0; sweep < 100; sweep++) {
+        double off = 0, diag = 0;
+        for (int p = 0; p < 8; p++) {
+            diag += A[p][p] * A[p][p];
+            for (int q = p + 1; q < 8; q++) off += A[p][q] * A[p][q];
+        }
+        if (off <= 1e-34 * diag || off == 0.0) break;
+        for (int p = 0; p < 8; p++)
+            for (int q = p + 1; q < 8; q++) {
+                if (A[p][q] == 0.0) continue;
+                /* rotation J (J_pp = J_qq = c, J_pq = s, J_qp = -s) with
+                 * (J^T A J)_pq = 0: t = tan(theta) is the smaller root of
+                 * t^2 + 2 tau t - 1 = 0, tau = (A_qq - A_pp) / (2 A_pq) */
+                double tau = (A[q][q] - A[p][p]) / (2.0 * A[p][q]);
+                double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(tau * tau + 1.0));
+                double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
+                for (int k = 0; k < 8; k++) {   /* A <- A J */
+                    double akp = A[k][p], akq = A[k][q];
+                    A[k][p] = c * akp - sn * akq;
+                    A[k][q] = sn * akp + c * akq;
+                }
+                for (int k = 0; k < 8; k++) {   /* A <- J^T A */
+                    double apk = A[p][k], aqk = A[q][k];
+                    A[p][k] = c * apk - sn * aqk;
+                    A[q][k] = sn * apk + c * aqk;
+                }
+                for (int k = 0; k < 8; k++) {   /* V <- V J */
+                    double vkp = V[k][p], vkq = V[k][q];
+                    V[k][p] = c * vkp - sn * vkq;
+                    V[k][q] = sn * vkp + c * vkq;
+                }
+            }
+    }
+    /* the 8 eigenvalues in ascending order; each of H's comes twice: take
+     * every other one, with the eigenvector of the first of each pair */
+    int ord[8];
+    for (int k = 0; k < 8; k++) ord[k] = k;
+    for (int a = 0; a < 8; a++)
+        for (int b = a + 1; b < 8; b++)
+            if (A[ord[b]][ord[b]] < A[ord[a]][ord[a]]) { int t = ord[a]; ord[a] = ord[b]; ord[b] = t; }
+    for (int e = 0; e < 4; e++) {
+        int k = ord[2 * e];
+        w[e] = 0.5 * (A[ord[2 * e]][ord[2 * e]] + A[ord[2 * e + 1]][ord[2 * e + 1]]);
+        double nrm = 0;
+        for (int r = 0; r < 4; r++) nrm += V[r][k] * V[r][k] + V[r + 4][k] * V[r + 4][k];
+        nrm = sqrt(nrm);
+        for (int r = 0; r < 4; r++) vec[r * 4 + e] = (V[r][k] + I * V[r + 4][k]) / nrm;
+    }
+}
+
+/* The SDRP projection generalised to the pair (qa, qb): psi <- (|phi><phi|
+ * on the pair, identity on the rest) psi, renormalised by the computed norm
+ * (phi: four amplitudes, index bit qa + 2 bit qb). */
+void orc_sdrp_project2(cplx *psi, int n, int qa, int qb, const cplx phi[4])
+{
+    uint64_t N = (uint64_t)1 << n, ba = (uint64_t)1 << qa, bb = (uint64_t)1 << qb;
+    for (uint64_t i = 0; i < N; i++) {
+        if ((i & ba) || (i & bb)) continue;
+        uint64_t idx[4] = { i, i | ba, i | bb, i | ba | bb };
+        cplx ov = 0;
+        for (int x = 0; x < 4; x++) ov += conj(phi[x]) * psi[idx[x]];
+        for (int x = 0; x < 4; x++) psi[idx[x]] = phi[x] * ov;
+    }
+    double s = sqrt(orc_norm2(psi, n));
+    for (uint64_t i = 0; i < N; i++) psi[i] /= s;
+}
+
+/* Projects qubit q onto the Z eigenstate |v> (post-selects bit q = v and
+ * renormalises by the computed norm). */
+void orc_project_z(cplx *psi, int n, int q, int v)
+{
+    uint64_t N = (uint64_t)1 << n, bq = (uint64_t)1 << q;
+    for (uint64_t i = 0; i < N; i++)
+        if (((i & bq) != 0) != (v != 0)) psi[i] = 0;
+    double s = sqrt(orc_norm2(psi, n));
+    for (uint64_t i = 0; i < N; i++) psi[i] /= s;
+}
+
+/* Sec. II.B (unobservable optimisations, Table I "eliminates Z-basis
+ * eigenstate controls"): the Z-eigenstate value of qubit q if it is a
+ * subsystem of its own and its probability of the other value is at most
+ * tau (returns 0 or 1, the eigenvalue's bit), else -1. A nonzero
+ * probability of the other value is projected away first. */
+static int z_eigen(cplx *psi, int n, const int *sys, int q, double tau)
+{
+    int members = 0;
+    for (int x = 0; x < n; x++) members += sys[x] == sys[q];
+    if (members != 1) return -1;
+    double p1 = orc_prob1(psi, n, q);
+    int v = p1 <= tau ? 0 : (1.0 - p1 <= tau ? 1 : -1);
+    if (v >= 0 && (v == 0 ? p1 : 1.0 - p1) != 0.0) orc_project_z(psi, n, q, v);
+    return v;
+}
+
 /* Runs a circuit with SDRP rounding on the full state vector (no
  * factorisation). psi must hold a product state on entry (normally
  * |0...0>); every qubit starts in its own subsystem.
@@ -508,22 +644,78 @@ void orc_sdrp_project(cplx *psi, int n, int q, const double r[3])
  *
  * force (optional, nforce entries): when given, only the listed
  * (gate, qubit) checks run, in the listed order, instead of the
- * exhaustive schedule.
+ * exhaustive schedule. force_action (optional, nforce entries, only with
+ * force): entry j >= 0 replaces the decision of check j (0 keep, 1 round,
+ * 2 separate exactly) while r and eps are still computed and logged; -1
+ * decides by eps as above. This replays another run's decisions, so that a
+ * decision taken the other way at a near-tie (eps within rounding of p/2
+ * or tau) does not hide the rest of the trajectory from the comparison.
+ *
+ * unobservable != 0 applies Sec. II.B's rule before each controlled
+ * one-qubit gate and each controlled phase: a control (either qubit of a
+ * CP) that is a one-qubit subsystem in a Z eigenstate, to within tau, is
+ * first projected onto that eigenstate (fidelity >= 1 - tau, not entered
+ * into F, as an exact separation); a control holding the value the gate
+ * waits for is dropped, one holding the other value removes the gate. The
+ * gate is still applied to the full vector, where it now acts exactly as
+ * its reduced form; only the qubits it still couples merge, so a gate
+ * reduced to a local one merges nothing and triggers no checks.
+ * *nunobs_out (optional) counts the gates removed or reduced.
+ *
+ * pairs != 0 adds a two-qubit check after the one-qubit checks of a gate
+ * that couples exactly two qubits (a, b): if a and b are still in one
+ * subsystem of three or more qubits, rho of the pair gives eps = 1 -
+ * (largest eigenvalue), the rounding error of the pair's dominant Schmidt
+ * branch; eps <= p/2 rounds (F <- F (1 - eps)) and eps <= tau separates
+ * exactly, projecting onto that branch's pair state, after which the pair is
+ * a subsystem of its own. Its log entry has qubit a, pad 1 + b, and r the
+ * three largest eigenvalues in descending order.
  *
  * Returns the number of decisions written to log (capped at logcap). */
 int orc_sdrp_run(cplx *psi, int n, const orc_gate *g, int ng, double p, double tau,
-                 const int32_t *force, int nforce,
-                 double *F_out, int *nround_out, orc_decision *log, int logcap)
+                 const int32_t *force, int nforce, const int32_t *force_action, int unobservable, int pairs,
+                 double *F_out, int *nround_out, int *nunobs_out, orc_decision *log, int logcap)
 {
     int sys[64];
     int nextsys = n;
     for (int q = 0; q < n; q++) sys[q] = q;
     double F = 1.0;
-    int nround = 0, nlog = 0, fpos = 0;
+    int nround = 0, nlog = 0, fpos = 0, nunobs = 0;
 
     for (int k = 0; k < ng; k++) {
         const orc_gate *gk = &g[k];
+        /* qubits the gate still couples after the unobservable rule */
+        int keep_q[ORC_MAXCTRL + 2], nkeep = -1, removed = 0;
+        if (unobservable && (gk->kind == OG_CP || (gk->nctrl > 0 && gk->kind < OG_CP))) {
+            nkeep = 0;
+            if (gk->kind == OG_CP) {
+                /* diag(1,1,1,e^{i theta}) is symmetric: either qubit may act as the control */
+                int e0 = z_eigen(psi, n, sys, gk->q[0], tau);
+                int e1 = e0 < 0 ? z_eigen(psi, n, sys, gk->q[1], tau) : -1;
+                if (e0 >= 0 || e1 >= 0) {
+                    int v = e0 >= 0 ? e0 : e1;
+                    if (v == 0) removed = 1;
+                    else keep_q[nkeep++] = e0 >= 0 ? gk->q[1] : gk->q[0];
+                } else {
+                    keep_q[nkeep++] = gk->q[0];
+                    keep_q[nkeep++] = gk->q[1];
+                }
+            } else {
+                keep_q[nkeep++] = gk->q[0];
+                for (int j = 0; j < gk->nctrl; j++) {
+                    int e = z_eigen(psi, n, sys, gk->ctrl[j], tau);
+                    if (e < 0) {
+                        keep_q[nkeep++] = gk->ctrl[j];
+                        continue;
+                    }
+                    if (e != gk->cval[j]) removed = 1;
+                }
+            }
+            const int orig = gk->kind == OG_CP ? 2 : 1 + gk->nctrl;   /* qubits the gate couples as written */
+            if (removed || nkeep < orig) nunobs++;
+        }
         if (orc_apply_gate(psi, n, gk)) return -1;
+        if (nkeep >= 0 && (removed || nkeep < 2)) continue;   /* removed or local: nothing merges */
         if (gk->kind == OG_SWAP) {
             /* a SWAP entangles nothing: the two qubits trade subsystems */
             int t = sys[gk->q[0]];
@@ -539,17 +731,29 @@ int orc_sdrp_run(cplx *psi, int n, const orc_gate *g, int ng, double p, double t
         if (!two) continue;
         /* merge subsystems of every qubit the gate touches */
         int keep = sys[a], drop = sys[b];
-        for (int q = 0; q < n; q++) if (sys[q] == drop) sys[q] = keep;
-        for (int j = 1; j < gk->nctrl; j++) {
-            int dj = sys[gk->ctrl[j]];
-            for (int q = 0; q < n; q++) if (sys[q] == dj) sys[q] = keep;
+        if (nkeep >= 2) {
+            /* merge only the qubits the reduced gate still couples */
+            keep = sys[keep_q[0]];
+            for (int j = 1; j < nkeep; j++) {
+                int dj = sys[keep_q[j]];
+                for (int q = 0; q < n; q++) if (sys[q] == dj) sys[q] = keep;
+            }
+        } else {
+            for (int q = 0; q < n; q++) if (sys[q] == drop) sys[q] = keep;
+            for (int j = 1; j < gk->nctrl; j++) {
+                int dj = sys[gk->ctrl[j]];
+                for (int q = 0; q < n; q++) if (sys[q] == dj) sys[q] = keep;
+            }
         }
 
-        int cand[64], ncand = 0;
+        int cand[64], cact[64], ncand = 0;
         if (force) {
-            while (fpos < nforce && force[2 * fpos] == k) cand[ncand++] = force[2 * fpos++ + 1];
+            while (fpos < nforce && force[2 * fpos] == k) {
+                cact[ncand] = force_action ? force_action[fpos] : -1;
+                cand[ncand++] = force[2 * fpos++ + 1];
+            }
         } else {
-            for (int q = 0; q < n; q++) if (sys[q] == keep) cand[ncand++] = q;
+            for (int q = 0; q < n; q++) if (sys[q] == keep) { cact[ncand] = -1; cand[ncand++] = q; }
         }
         for (int c = 0; c < ncand; c++) {
             int q = cand[c], members = 0;
@@ -562,6 +766,7 @@ int orc_sdrp_run(cplx *psi, int n, const orc_gate *g, int ng, double p, double t
             int action = 0;
             if (p > 0.0 && eps <= p / 2.0) action = 1;   /* p = 0: exact simulation, nothing rounds */
             else if (eps <= tau) action = 2;
+            if (cact[c] >= 0) action = cact[c];
             if (action) {
                 orc_sdrp_project(psi, n, q, r);
                 if (action == 1) { F *= (1.0 - eps); nround++; }
@@ -574,8 +779,45 @@ int orc_sdrp_run(cplx *psi, int n, const orc_gate *g, int ng, double p, double t
             }
             nlog++;
         }
+        if (pairs) {
+            /* the two qubits the gate couples (after the unobservable rule) */
+            int pa = -1, pb = -1;
+            if (nkeep >= 0) {
+                if (nkeep == 2) { pa = keep_q[0]; pb = keep_q[1]; }
+            } else if (d == 4) {
+                pa = gk->q[0]; pb = gk->q[1];
+            } else if (gk->nctrl == 1) {
+                pa = gk->q[0]; pb = gk->ctrl[0];
+            }
+            int members = 0;
+            if (pa >= 0 && sys[pa] == sys[pb])
+                for (int x = 0; x < n; x++) members += sys[x] == sys[pa];
+            if (members >= 3) {
+                cplx rho[16], vec[16], phi[4];
+                double w[4];
+                orc_rho2(psi, n, pa, pb, rho);
+                orc_herm4_eig(rho, w, vec);
+                double eps = 1.0 - w[3];
+                int action = 0;
+                if (p > 0.0 && eps <= p / 2.0) action = 1;
+                else if (eps <= tau) action = 2;
+                if (action) {
+                    for (int x = 0; x < 4; x++) phi[x] = vec[x * 4 + 3];
+                    orc_sdrp_project2(psi, n, pa, pb, phi);
+                    if (action == 1) { F *= (1.0 - eps); nround++; }
+                    sys[pa] = sys[pb] = nextsys++;
+                }
+                if (nlog < logcap) {
+                    log[nlog].gate = k; log[nlog].qubit = pa; log[nlog].action = action;
+                    log[nlog].pad = 1 + pb; log[nlog].eps = eps;
+                    log[nlog].r[0] = w[3]; log[nlog].r[1] = w[2]; log[nlog].r[2] = w[1];
+                }
+                nlog++;
+            }
+        }
     }
     *F_out = F;
     *nround_out = nround;
+    if (nunobs_out) *nunobs_out = nunobs;
     return nlog;
 }

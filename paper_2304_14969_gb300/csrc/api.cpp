@@ -54,16 +54,42 @@ qsim_status make_state(int n, qsim_dtype dt, void *stream, qsim_state **out)
 }  // namespace
 
 namespace qs {
+// Kets up to this size keep their permutation buffer (a stream-ordered
+// temporary taken from the shared pool per call would make a second state's
+// stream wait for the first's frees, serialising pipelined kets).
+static const size_t kPermKeepBytes = (size_t)8 << 30;
+
+// A ket-sized device buffer for a permutation of s: the state's kept buffer,
+// or (*temporary set) a stream-ordered temporary the caller frees after use.
+static qsim_status perm_buffer(qsim_state *s, void **buf, bool *temporary)
+{
+    *temporary = false;
+    if (s->perm) {
+        *buf = s->perm;
+        return QSIM_OK;
+    }
+    if (s->amp_bytes() <= kPermKeepBytes && cudaMalloc(&s->perm, s->amp_bytes()) == cudaSuccess) {
+        *buf = s->perm;
+        return QSIM_OK;
+    }
+    cudaGetLastError();   // a failed keep falls back to a temporary
+    s->perm = nullptr;
+    cudaError_t e = cudaMallocAsync(buf, s->amp_bytes(), s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync (permutation buffer)");
+    *temporary = true;
+    return QSIM_OK;
+}
+
 // Moves the amplitudes so that physical bit p ends up at new_pos[p].
 qsim_status permute_state(qsim_state *s, const std::vector<int> &new_pos)
 {
     void *tmp = nullptr;
-    cudaError_t e = cudaMallocAsync(&tmp, s->amp_bytes(), s->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync (permutation buffer)");
-    e = launch_permute(s->amps, tmp, s->dt, s->n, new_pos.data(), s->stream);
+    bool temporary = false;
+    QS_TRY(perm_buffer(s, &tmp, &temporary));
+    cudaError_t e = launch_permute(s->amps, tmp, s->dt, s->n, new_pos.data(), s->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(s->amps, tmp, s->amp_bytes(), cudaMemcpyDeviceToDevice, s->stream);
-    cudaFreeAsync(tmp, s->stream);
+    if (temporary) cudaFreeAsync(tmp, s->stream);
     if (e != cudaSuccess) return cuda_fail(e, "permute");
     return QSIM_OK;
 }
@@ -114,6 +140,7 @@ qsim_status qsim_destroy(qsim_state *s)
     if (s->stream) cudaStreamSynchronize(s->stream);
     else cudaDeviceSynchronize();
     if (s->owned && s->amps) cudaFree(s->amps);
+    if (s->perm) cudaFree(s->perm);
     if (s->d_err) cudaFree(s->d_err);
     if (s->h_err) cudaFreeHost(s->h_err);
     free_scratch(s->red);
@@ -154,11 +181,12 @@ qsim_status qsim_download_async(qsim_state *s, void *host_amps)
     std::vector<int> to(s->n);
     for (int L = 0; L < s->n; L++) to[s->l2p[L]] = L;
     void *tmp = nullptr;
-    QS_CUDA(cudaMallocAsync(&tmp, s->amp_bytes(), s->stream));
+    bool temporary = false;
+    QS_TRY(perm_buffer(s, &tmp, &temporary));
     cudaError_t e = launch_permute(s->amps, tmp, s->dt, s->n, to.data(), s->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(host_amps, tmp, s->amp_bytes(), cudaMemcpyDeviceToHost, s->stream);
-    cudaFreeAsync(tmp, s->stream);
+    if (temporary) cudaFreeAsync(tmp, s->stream);
     if (e != cudaSuccess) return cuda_fail(e, "download");
     return QSIM_OK;
 }

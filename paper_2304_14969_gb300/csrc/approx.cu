@@ -15,6 +15,24 @@
 // FP64 renormalisation) and becomes a one-qubit subsystem holding |phi>.
 // F <- F (1 - eps) for each rounding (Eq. fid_model). Candidates after the
 // rounded one are checked again on the new, smaller subsystem.
+//
+// Optionally (opts->unobservable, Sec. II.B and Table I) a controlled gate
+// whose control is a one-qubit subsystem in a Z eigenstate is removed or
+// reduced before anything is composed: the control's two amplitudes are
+// read back, a probability of the other value of at most tau projects it
+// onto the eigenstate, and the gate then drops that control (value as
+// required) or is removed (value opposite); a controlled phase may use
+// either qubit as the control. A gate left on one qubit runs locally and
+// entangles nothing, so no check follows it.
+//
+// Optionally (opts->pairs) the rounding also acts on two-qubit subsystems:
+// after the one-qubit checks of a gate coupling exactly two qubits a, b
+// that still share a subsystem of three or more qubits, one FP64 reduction
+// gives the pair's 4 x 4 reduced density matrix, a complex Jacobi
+// iteration on the host its eigenvalues, and eps = 1 - lambda_max decides
+// (eps <= p/2 rounds, eps <= tau separates exactly): the subsystem is
+// projected onto the top eigenvector |phi> of the pair, which becomes a
+// two-qubit subsystem holding |phi>.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -104,6 +122,152 @@ __global__ void k_put2(typename AV<R>::T *__restrict__ d, double a0r, double a0i
     d[1].y = (R)a1i;
 }
 
+// The 16 FP64 sums of a pair's reduced density matrix (unnormalised) over
+// the quads of a subsystem ket (pair bits ba, bb): |a_x|^2 for x = 0..3,
+// then Re and Im of a_x conj(a_y) for the six x < y, x = bit ba + 2 bit bb.
+// One row of 16 partial sums per CTA.
+constexpr int kRhoThreads = 128;
+template <typename R>
+__global__ void __launch_bounds__(kRhoThreads) k_rho2(const typename AV<R>::T *__restrict__ a, int ba, int bb,
+                                                       uint64_t nquads, double *__restrict__ part)
+{
+    double acc[16];
+#pragma unroll
+    for (int k = 0; k < 16; k++) acc[k] = 0.0;
+    const int lo = ba < bb ? ba : bb, hi = ba < bb ? bb : ba;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nquads; j += stride) {
+        // insert zero bits at lo, then hi
+        uint64_t i = ((j >> lo) << (lo + 1)) | (j & ((1ull << lo) - 1));
+        i = ((i >> hi) << (hi + 1)) | (i & ((1ull << hi) - 1));
+        double xr[4], xi[4];
+#pragma unroll
+        for (int x = 0; x < 4; x++) {
+            const auto v = a[i | ((uint64_t)(x & 1) << ba) | ((uint64_t)(x >> 1) << bb)];
+            xr[x] = (double)v.x;
+            xi[x] = (double)v.y;
+        }
+#pragma unroll
+        for (int x = 0; x < 4; x++) acc[x] += xr[x] * xr[x] + xi[x] * xi[x];
+        int k = 4;
+#pragma unroll
+        for (int x = 0; x < 4; x++)
+#pragma unroll
+            for (int y = x + 1; y < 4; y++) {
+                // a_x conj(a_y)
+                acc[k++] += xr[x] * xr[y] + xi[x] * xi[y];
+                acc[k++] += xi[x] * xr[y] - xr[x] * xi[y];
+            }
+    }
+    __shared__ double sh[kRhoThreads / 32][16];
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+        double v = acc[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 16) {
+        double v = 0;
+        for (int w = 0; w < kRhoThreads / 32; w++) v += sh[w][threadIdx.x];
+        part[(size_t)blockIdx.x * 16 + threadIdx.x] = v;
+    }
+}
+
+// dst[j] = sum_x conj(phi_x) src[j with the pair bits (ba, bb) = x]: the
+// subsystem ket projected onto <phi| of the pair (m - 2 qubits out).
+template <typename R>
+__global__ void k_project2(const typename AV<R>::T *__restrict__ src, int ba, int bb, uint64_t nout,
+                           const double4 ph01, const double4 ph23, typename AV<R>::T *__restrict__ dst)
+{
+    const double pr[4] = {ph01.x, ph01.z, ph23.x, ph23.z}, pi[4] = {ph01.y, ph01.w, ph23.y, ph23.w};
+    const int lo = ba < bb ? ba : bb, hi = ba < bb ? bb : ba;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nout; j += stride) {
+        uint64_t i = ((j >> lo) << (lo + 1)) | (j & ((1ull << lo) - 1));
+        i = ((i >> hi) << (hi + 1)) | (i & ((1ull << hi) - 1));
+        double orr = 0, oi = 0;
+#pragma unroll
+        for (int x = 0; x < 4; x++) {
+            const auto v = src[i | ((uint64_t)(x & 1) << ba) | ((uint64_t)(x >> 1) << bb)];
+            // conj(phi_x) v
+            orr += pr[x] * (double)v.x + pi[x] * (double)v.y;
+            oi += pr[x] * (double)v.y - pi[x] * (double)v.x;
+        }
+        typename AV<R>::T o;
+        o.x = (R)orr;
+        o.y = (R)oi;
+        dst[j] = o;
+    }
+}
+
+template <typename R>
+__global__ void k_put4(typename AV<R>::T *__restrict__ d, const double4 ph01, const double4 ph23)
+{
+    d[0].x = (R)ph01.x;
+    d[0].y = (R)ph01.y;
+    d[1].x = (R)ph01.z;
+    d[1].y = (R)ph01.w;
+    d[2].x = (R)ph23.x;
+    d[2].y = (R)ph23.y;
+    d[3].x = (R)ph23.z;
+    d[3].y = (R)ph23.w;
+}
+
+// Eigenvalues (ascending) and unit eigenvectors (columns) of a Hermitian
+// 4 x 4 by cyclic complex Jacobi rotations: for the entry h_pq = r e^{i f},
+// G = [[c, s e^{i f}], [-s e^{-i f}, c]] on (p, q), with t = s / c the
+// smaller root of t^2 + 2 tau t - 1 = 0, tau = (h_qq - h_pp) / (2 r), makes
+// (G^H H G)_pq = 0; V accumulates the G.
+static void herm4_jacobi(cd H[4][4], double w[4], cd V[4][4])
+{
+    for (int r = 0; r < 4; r++)
+        for (int c = 0; c < 4; c++) V[r][c] = r == c ? 1.0 : 0.0;
+    for (int sweep = 0; sweep < 60; sweep++) {
+        double off = 0, dg = 0;
+        for (int p = 0; p < 4; p++) {
+            dg += std::norm(H[p][p]);
+            for (int q = p + 1; q < 4; q++) off += std::norm(H[p][q]);
+        }
+        if (off == 0.0 || off <= 1e-34 * dg) break;
+        for (int p = 0; p < 4; p++)
+            for (int q = p + 1; q < 4; q++) {
+                const double r = std::abs(H[p][q]);
+                if (r == 0.0) continue;
+                const cd e = H[p][q] / r;   // e^{i f}
+                const double tau = (H[q][q].real() - H[p][p].real()) / (2.0 * r);
+                const double t = (tau >= 0 ? 1.0 : -1.0) / (std::fabs(tau) + std::sqrt(tau * tau + 1.0));
+                const double c = 1.0 / std::sqrt(t * t + 1.0), sn = t * c;
+                const cd gpq = sn * e, gqp = -sn * std::conj(e);
+                for (int k = 0; k < 4; k++) {   // H <- H G
+                    const cd hp = H[k][p], hq = H[k][q];
+                    H[k][p] = c * hp + gqp * hq;
+                    H[k][q] = gpq * hp + c * hq;
+                }
+                for (int k = 0; k < 4; k++) {   // H <- G^H H
+                    const cd hp = H[p][k], hq = H[q][k];
+                    H[p][k] = c * hp + std::conj(gqp) * hq;
+                    H[q][k] = std::conj(gpq) * hp + c * hq;
+                }
+                for (int k = 0; k < 4; k++) {   // V <- V G
+                    const cd vp = V[k][p], vq = V[k][q];
+                    V[k][p] = c * vp + gqp * vq;
+                    V[k][q] = gpq * vp + c * vq;
+                }
+            }
+    }
+    int ord[4] = {0, 1, 2, 3};
+    std::sort(ord, ord + 4, [&](int x, int y) { return H[x][x].real() < H[y][y].real(); });
+    cd Vs[4][4];
+    for (int e = 0; e < 4; e++) {
+        w[e] = H[ord[e]][ord[e]].real();
+        for (int r = 0; r < 4; r++) Vs[r][e] = V[r][ord[e]];
+    }
+    for (int r = 0; r < 4; r++)
+        for (int c = 0; c < 4; c++) V[r][c] = Vs[r][c];
+}
+
 struct Decide {
     int32_t first;       // index into the candidate list of the first acted-on qubit, or ncand
     int32_t action;      // 1 rounded, 2 exact, 0 none
@@ -178,6 +342,7 @@ struct Run {
     double *d_sums = nullptr;
     int *d_cand = nullptr;
     Decide *d_dec = nullptr, *h_dec = nullptr;
+    double *h_amp2 = nullptr;   // pinned: two amplitudes of a one-qubit factor (re, im each)
     int64_t bloch_passes = 0;
 
     ~Run()
@@ -189,6 +354,7 @@ struct Run {
         if (d_cand) cudaFree(d_cand);
         if (d_dec) cudaFree(d_dec);
         if (h_dec) cudaFreeHost(h_dec);
+        if (h_amp2) cudaFreeHost(h_amp2);
         free_scratch(sc);
     }
 
@@ -253,6 +419,125 @@ struct Run {
         C.d = nullptr;
         for (int q : A.qs) sys_of[q] = i;
         subs[j].reset();
+        return QSIM_OK;
+    }
+
+    // Z-eigenstate value of qubit q (0 or 1) if it is a one-qubit subsystem
+    // whose probability of the other value is at most tau, else -1; an
+    // eigenstate within tau is made exact (the factor projected onto it,
+    // keeping its phase).
+    qsim_status z_eigen(int q, double tau, int *out)
+    {
+        *out = -1;
+        Sub &S = *subs[sys_of[q]];
+        if (S.qs.size() != 1) return QSIM_OK;
+        if (dt == QSIM_C64) {
+            float f[4];
+            QS_CUDA(cudaMemcpyAsync(f, S.d, sizeof f, cudaMemcpyDeviceToHost, st));
+            QS_CUDA(cudaStreamSynchronize(st));
+            for (int i = 0; i < 4; i++) h_amp2[i] = f[i];
+        } else {
+            QS_CUDA(cudaMemcpyAsync(h_amp2, S.d, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+            QS_CUDA(cudaStreamSynchronize(st));
+        }
+        const double a2 = h_amp2[0] * h_amp2[0] + h_amp2[1] * h_amp2[1];
+        const double b2 = h_amp2[2] * h_amp2[2] + h_amp2[3] * h_amp2[3];
+        const double p1 = b2 / (a2 + b2);
+        if (p1 <= tau) *out = 0;
+        else if (1.0 - p1 <= tau) *out = 1;
+        else return QSIM_OK;
+        if (*out == 0 && b2 != 0.0) {
+            const double ra = std::sqrt(a2);
+            if (dt == QSIM_C64) k_put2<float><<<1, 1, 0, st>>>((float2 *)S.d, h_amp2[0] / ra, h_amp2[1] / ra, 0, 0);
+            else k_put2<double><<<1, 1, 0, st>>>((double2 *)S.d, h_amp2[0] / ra, h_amp2[1] / ra, 0, 0);
+            QS_CUDA(cudaGetLastError());
+        } else if (*out == 1 && a2 != 0.0) {
+            const double rb = std::sqrt(b2);
+            if (dt == QSIM_C64) k_put2<float><<<1, 1, 0, st>>>((float2 *)S.d, 0, 0, h_amp2[2] / rb, h_amp2[3] / rb);
+            else k_put2<double><<<1, 1, 0, st>>>((double2 *)S.d, 0, 0, h_amp2[2] / rb, h_amp2[3] / rb);
+            QS_CUDA(cudaGetLastError());
+        }
+        return QSIM_OK;
+    }
+
+    // reduced density matrix of the pair (qubits qa, qb) of subsystem i,
+    // normalised, rho[x][y] with x = bit qa + 2 bit qb (FP64)
+    qsim_status pair_rho(int i, int qa, int qb, cd rho[4][4])
+    {
+        Sub &S = *subs[i];
+        const int m = (int)S.qs.size();
+        const int ba = local(S, qa), bb = local(S, qb);
+        const uint64_t nquads = 1ull << (m - 2);
+        const int grid = (int)std::min<uint64_t>((nquads + kRhoThreads - 1) / kRhoThreads, 256);
+        QS_TRY(ensure_scratch(sc, (size_t)grid * 16 + 64));
+        if (dt == QSIM_C64)
+            k_rho2<float><<<grid, kRhoThreads, 0, st>>>((const float2 *)S.d, ba, bb, nquads, sc.d);
+        else
+            k_rho2<double><<<grid, kRhoThreads, 0, st>>>((const double2 *)S.d, ba, bb, nquads, sc.d);
+        QS_CUDA(cudaGetLastError());
+        std::vector<double> part((size_t)grid * 16);
+        QS_CUDA(cudaMemcpyAsync(part.data(), sc.d, part.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+        QS_CUDA(cudaStreamSynchronize(st));
+        double v[16] = {0};
+        for (int b = 0; b < grid; b++)
+            for (int k = 0; k < 16; k++) v[k] += part[(size_t)b * 16 + k];
+        const double tr = v[0] + v[1] + v[2] + v[3];
+        if (!(tr > 0)) return fail(QSIM_E_CUDA, "pair check on a ket of zero norm");
+        for (int x = 0; x < 4; x++) rho[x][x] = v[x] / tr;
+        int k = 4;
+        for (int x = 0; x < 4; x++)
+            for (int y = x + 1; y < 4; y++) {
+                rho[x][y] = cd(v[k], v[k + 1]) / tr;
+                rho[y][x] = std::conj(rho[x][y]);
+                k += 2;
+            }
+        bloch_passes++;
+        return QSIM_OK;
+    }
+
+    // projects the pair (qa, qb) of subsystem i onto phi (index bit qa + 2
+    // bit qb) and splits it off as a two-qubit subsystem
+    qsim_status split2(int i, int qa, int qb, const cd phi[4])
+    {
+        Sub &S = *subs[i];
+        const int m = (int)S.qs.size();
+        const int ba = local(S, qa), bb = local(S, qb);
+        Sub R;
+        for (int b = 0; b < m; b++)
+            if (b != ba && b != bb) R.qs.push_back(S.qs[b]);
+        QS_TRY(alloc(R, m - 2));
+        const uint64_t nout = 1ull << (m - 2);
+        const int grid = default_grid(nout, 256);
+        const double4 p01 = make_double4(phi[0].real(), phi[0].imag(), phi[1].real(), phi[1].imag());
+        const double4 p23 = make_double4(phi[2].real(), phi[2].imag(), phi[3].real(), phi[3].imag());
+        if (dt == QSIM_C64)
+            k_project2<float><<<grid, 256, 0, st>>>((const float2 *)S.d, ba, bb, nout, p01, p23, (float2 *)R.d);
+        else
+            k_project2<double><<<grid, 256, 0, st>>>((const double2 *)S.d, ba, bb, nout, p01, p23, (double2 *)R.d);
+        QS_CUDA(cudaGetLastError());
+        release(S);
+        S = R;
+        R.d = nullptr;
+        for (int q : S.qs) sys_of[q] = i;
+        // renormalise by the computed FP64 norm (Sec. III.A step 3)
+        qsim_state v = view(S);
+        v.red = sc;
+        double nrm = 0;
+        qsim_status stt = reduce_norm(&v, &nrm);
+        sc = v.red;
+        v.red = Scratch();
+        QS_TRY(stt);
+        if (!(nrm > 0)) return fail(QSIM_E_CUDA, "projected ket has zero norm");
+        QS_CUDA(launch_scale(S.d, dt, nout, 1.0 / std::sqrt(nrm), st));
+        // the pair's new subsystem holds |phi> (local bit 0 = qa, 1 = qb)
+        auto F = std::make_unique<Sub>();
+        F->qs = {qa, qb};
+        QS_TRY(alloc(*F, 2));
+        if (dt == QSIM_C64) k_put4<float><<<1, 1, 0, st>>>((float2 *)F->d, p01, p23);
+        else k_put4<double><<<1, 1, 0, st>>>((double2 *)F->d, p01, p23);
+        QS_CUDA(cudaGetLastError());
+        subs.push_back(std::move(F));
+        sys_of[qa] = sys_of[qb] = (int)subs.size() - 1;
         return QSIM_OK;
     }
 
@@ -341,6 +626,7 @@ extern "C" qsim_status qsim_approx_run(const qsim_circuit *c, double p, const qs
     QS_CUDA(cudaMalloc(&R.d_cand, sizeof(int) * 64));
     QS_CUDA(cudaMalloc(&R.d_dec, sizeof(Decide)));
     QS_CUDA(cudaMallocHost(&R.h_dec, sizeof(Decide)));
+    QS_CUDA(cudaMallocHost(&R.h_amp2, 4 * sizeof(double)));
     for (int q = 0; q < n; q++) {
         auto s = std::make_unique<Sub>();
         s->qs = {q};
@@ -365,7 +651,7 @@ extern "C" qsim_status qsim_approx_run(const qsim_circuit *c, double p, const qs
     } free_mlp{d_feat, d_logit};
     int64_t n_ent = 0, ntrace = 0;
     double F = 1.0;
-    int64_t nlog = 0, nround = 0, nexact = 0, nchecks = 0;
+    int64_t nlog = 0, nround = 0, nexact = 0, nchecks = 0, nunobs = 0;
     int maxsub = 1, fpos = 0;
     qsim_status status = QSIM_OK;
     for (int k = 0; k < c->ngates && status == QSIM_OK; k++) {
@@ -382,10 +668,54 @@ extern "C" qsim_status qsim_approx_run(const qsim_circuit *c, double p, const qs
             R.sys_of[b] = ia;
             continue;
         }
+        // Sec. II.B: Z-eigenstate controls removed, or the gate removed
+        qsim_gate gr = g;       // the gate as reduced
+        bool removed = false;
+        if (o.unobservable && (g.kind == QSIM_G_CP || (d == 2 && g.ncontrols > 0))) {
+            bool reduced = false;
+            if (g.kind == QSIM_G_CP) {
+                int e0 = -1, e1 = -1;
+                QS_TRY(R.z_eigen(g.q0, tau, &e0));
+                if (e0 < 0) QS_TRY(R.z_eigen(g.q1, tau, &e1));
+                if (e0 >= 0 || e1 >= 0) {
+                    reduced = true;
+                    const int v = e0 >= 0 ? e0 : e1;
+                    if (v == 0) {
+                        removed = true;
+                    } else {
+                        // CP with one qubit in |1>: the phase diag(1, e^{i theta}) on the other
+                        gr.kind = QSIM_G_PHASE;
+                        gr.q0 = e0 >= 0 ? g.q1 : g.q0;
+                        gr.q1 = -1;
+                        gr.ncontrols = 0;
+                        d = gate_matrix(gr, c->matrices, c->nmatrix_doubles, m);
+                    }
+                }
+            } else {
+                gr.ncontrols = 0;
+                gr.control_values = 0;
+                for (int j = 0; j < g.ncontrols; j++) {
+                    int e = -1;
+                    QS_TRY(R.z_eigen(g.controls[j], tau, &e));
+                    if (e < 0) {
+                        if ((g.control_values >> j) & 1) gr.control_values |= 1u << gr.ncontrols;
+                        gr.controls[gr.ncontrols++] = g.controls[j];
+                        continue;
+                    }
+                    reduced = true;
+                    if (e != (int)((g.control_values >> j) & 1)) removed = true;
+                }
+            }
+            if (reduced) nunobs++;
+        }
+        if (removed) {
+            hist[g.q0].g1++;
+            continue;
+        }
         std::vector<int> touched;
-        touched.push_back(g.q0);
-        if (d == 4) touched.push_back(g.q1);
-        for (int j = 0; j < g.ncontrols; j++) touched.push_back(g.controls[j]);
+        touched.push_back(gr.q0);
+        if (d == 4) touched.push_back(gr.q1);
+        for (int j = 0; j < gr.ncontrols; j++) touched.push_back(gr.controls[j]);
         int si = R.sys_of[touched[0]];
         for (size_t j = 1; j < touched.size() && status == QSIM_OK; j++) {
             int sj = R.sys_of[touched[j]];
@@ -400,19 +730,19 @@ extern "C" qsim_status qsim_approx_run(const qsim_circuit *c, double p, const qs
         qsim_state v = R.view(S);
         if (d == 2) {
             uint64_t cmask = 0, cval = 0;
-            for (int j = 0; j < g.ncontrols; j++) {
-                uint64_t bb = bit(R.local(S, g.controls[j]));
+            for (int j = 0; j < gr.ncontrols; j++) {
+                uint64_t bb = bit(R.local(S, gr.controls[j]));
                 cmask |= bb;
-                if ((g.control_values >> j) & 1) cval |= bb;
+                if ((gr.control_values >> j) & 1) cval |= bb;
             }
-            QS_CUDA(launch_gate1(&v, m, R.local(S, g.q0), cmask, cval));
-        } else if (g.kind == QSIM_G_CP) {
-            QS_CUDA(launch_cphase(&v, R.local(S, g.q0), R.local(S, g.q1), g.params[0]));
+            QS_CUDA(launch_gate1(&v, m, R.local(S, gr.q0), cmask, cval));
+        } else if (gr.kind == QSIM_G_CP) {
+            QS_CUDA(launch_cphase(&v, R.local(S, gr.q0), R.local(S, gr.q1), gr.params[0]));
         } else {
-            QS_CUDA(launch_gate2(&v, m, R.local(S, g.q0), R.local(S, g.q1)));
+            QS_CUDA(launch_gate2(&v, m, R.local(S, gr.q0), R.local(S, gr.q1)));
         }
         if (touched.size() < 2) {
-            hist[g.q0].g1++;
+            hist[gr.q0].g1++;
             continue;
         }
         for (int q : touched) hist[q].g2++;
@@ -527,6 +857,44 @@ extern "C" qsim_status qsim_approx_run(const qsim_circuit *c, double p, const qs
             QS_TRY(R.split(sidx, R.local(Sq, qa), phi));
             ci += D.examined;
         }
+        // ---- two-qubit-subsystem check of the gate's pair (opts->pairs)
+        if (o.pairs && touched.size() == 2) {
+            const int qa = touched[0], qb = touched[1];
+            const int sp = R.sys_of[qa];
+            if (sp == R.sys_of[qb] && R.subs[sp]->qs.size() >= 3) {
+                cd rho[4][4], V[4][4];
+                double w[4];
+                QS_TRY(R.pair_rho(sp, qa, qb, rho));
+                herm4_jacobi(rho, w, V);
+                const double eps = 1.0 - w[3];
+                int act = 0;
+                if (p > 0.0 && eps <= p / 2.0) act = 1;
+                else if (eps <= tau) act = 2;
+                if (o.log && nlog < o.log_cap) {
+                    qsim_decision &L = o.log[nlog];
+                    L.gate = k;
+                    L.qubit = qa;
+                    L.action = act;
+                    L.reserved = 1 + qb;
+                    L.eps = eps;
+                    L.r[0] = w[3];
+                    L.r[1] = w[2];
+                    L.r[2] = w[1];
+                }
+                nlog++;
+                nchecks++;
+                if (act) {
+                    if (act == 1) {
+                        F *= (1.0 - eps);
+                        nround++;
+                    } else {
+                        nexact++;
+                    }
+                    cd phi[4] = {V[0][3], V[1][3], V[2][3], V[3][3]};
+                    QS_TRY(R.split2(sp, qa, qb, phi));
+                }
+            }
+        }
     }
     res->fidelity_model = F;
     res->n_rounds = nround;
@@ -537,6 +905,7 @@ extern "C" qsim_status qsim_approx_run(const qsim_circuit *c, double p, const qs
     res->n_log = nlog;
     res->n_trace = ntrace;
     res->max_subsystem_qubits = maxsub;
+    res->n_unobservable = nunobs;
     if (status != QSIM_OK) {
         res->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         return status;

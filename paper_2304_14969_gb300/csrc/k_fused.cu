@@ -123,7 +123,7 @@ qsim_status plan_upload(qsim_plan *P)
         P->tc_pipe.resize(P->tc_A.size());
         for (size_t i = 0; i < P->tc_A.size(); i++) {
             const void *g = P->tc_pd_off[i].empty() ? nullptr : (const void *)((unsigned char *)P->dmem + gt[i]);
-            QS_TRY(tc_pipe_prepare(P->n, P->tc_spec[i], g, P->tc_pipe[i], P->dt == QSIM_C128));
+            QS_TRY(tc_pipe_prepare(P->n, P->tc_spec[i], g, P->tc_pipe[i], tc_pipe_kind(P->dt, (qsim_prec)P->prec)));
         }
     }
     return QSIM_OK;

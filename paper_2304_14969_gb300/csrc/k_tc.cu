@@ -394,7 +394,7 @@ qsim_status apply_fused_tc(qsim_state *s, int k, const int *phys, const cd *u, q
     cudaError_t e;
     if (tc_pipe_eligible(s->n, s->dt, prec)) {
         TcPipeHost H;
-        qsim_status st = tc_pipe_prepare(s->n, ts, nullptr, H, s->dt == QSIM_C128);
+        qsim_status st = tc_pipe_prepare(s->n, ts, nullptr, H, tc_pipe_kind(s->dt, prec));
         e = st == QSIM_OK ? tc_pipe_launch(s, H, dA, derr) : cudaErrorInvalidValue;
     } else {
         e = tc_launch(s, ts, dA, prec, derr);

@@ -38,6 +38,15 @@
 // warp issues the six slice products a_i u_j with i + j <= 2, smallest
 // first; the write-back widens FP32 to FP64 exactly and stores 16 bytes
 // per amplitude. Shared memory: U slices 96 KB + 3 x 32 KB stages.
+//
+// Complex64 kets with 3xTF32 (KD = 2): TF32 parts take twice the bytes of
+// BF16 ones, so U (hi, lo) fills 128 KB of shared memory and one A operand
+// (hi, lo: 2 x 128 columns) sits in TMEM beside the two accumulators. The
+// tile then comes as four 16 KB quarter tiles (the complex128 scheme: one
+// per value of block bits 4, 5, read by the converter warps of one part)
+// into a ring of five stages (eight full / free barrier pairs). A converter splits each amplitude x into
+// hi = x rounded to TF32 and lo = x - hi (exact in FP32); the MMA warp issues
+// a_hi u_hi, a_hi u_lo, a_lo u_hi as kind::tf32 (K = 8 per instruction).
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -60,23 +69,29 @@ constexpr int kPEpi = 32 * kPEpiWarps;
 constexpr int kPThreads = 64 + kPConv + kPEpi;
 constexpr uint32_t kPHalf = 32768;           // one BF16 operand part of 128 x 128
 // per amplitude width: stage bytes, stages, U parts, loads per tile
-template <bool W> struct PipeCfg {
-    static constexpr uint32_t kStage = W ? 32768u : 65536u;   // a quarter tile of complex128 / a tile of complex64
-    static constexpr int kNStage = W ? 3 : 2;
-    static constexpr int kParts = W ? 3 : 2;                   // BF16 parts of U (and of A)
-    static constexpr uint32_t kU = kParts * kPHalf;
-    static constexpr int kQ = W ? 4 : 1;                       // loads per tile
-    // full / free barrier pairs: load m signals full[m % kNBar]. Complex128
-    // gives each quarter its own pair (load m is quarter m % 4), so every
-    // waiter sees a barrier's completions one by one in order; a barrier
-    // shared by loads of different quarters would be waited on for its
-    // second completion before its first (a parity wait cannot tell them
-    // apart).
-    static constexpr int kNBar = W ? 4 : 2;
+// KD: 0 complex64 BF16x3 (whole tiles), 1 complex128 BF16X6 (quarter
+// tiles), 2 complex64 3xTF32 (quarter tiles)
+template <int KD> struct PipeCfg {
+    static constexpr bool W = KD == 1, TF = KD == 2, QT = KD != 0;
+    // a tile of complex64 / a quarter tile of complex128 / of complex64
+    static constexpr uint32_t kStage = W ? 32768u : TF ? 16384u : 65536u;
+    static constexpr int kNStage = W ? 3 : TF ? 5 : 2;
+    static constexpr int kParts = W ? 3 : 2;                   // parts of U (and of A)
+    static constexpr uint32_t kPart = TF ? 2 * kPHalf : kPHalf;   // bytes of one part of U
+    static constexpr uint32_t kU = kParts * kPart;
+    static constexpr int kQ = QT ? 4 : 1;                      // loads per tile
+    // full / free barrier pairs: load m signals full[m % kNBar]. Quarter
+    // tiles give each quarter its own pair (load m is quarter m % 4; with
+    // five stages, two pairs per quarter by tile parity), so every waiter
+    // sees a barrier's completions one by one in order: a barrier shared by
+    // loads of different quarters would be waited on for its second
+    // completion before its first (a parity wait cannot tell them apart),
+    // and fewer pairs than stages let the producer's wait for a stage find
+    // its barrier two completions on. With kNBar >= kNStage, issuing load
+    // m + kNBar implies load m was read.
+    static constexpr int kNBar = TF ? 8 : QT ? 4 : 2;
     static constexpr size_t kSmem = kU + (size_t)kNStage * kStage + 1024;
 };
-static_assert(PipeCfg<false>::kSmem == PipeCfg<true>::kSmem, "one shared-memory size for both widths");
-constexpr size_t kPSmem = PipeCfg<false>::kSmem;
 
 // One 32-byte global store (sm_100 and later; p 32-byte aligned).
 __device__ __forceinline__ void st_global_256(void *p, uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t a4,
@@ -149,14 +164,15 @@ __device__ __forceinline__ uint32_t prod_u(int p)
 template <bool W> struct AmpOf { using T = float2; };
 template <> struct AmpOf<true> { using T = double2; };
 
-template <bool G, bool W>
+template <bool G, int KD>
 __global__ void __launch_bounds__(kPThreads, 1)
     k_tc_pipe(const __grid_constant__ CUtensorMap tmap_param, const __grid_constant__ TcPipeArgs P_param,
-              typename AmpOf<W>::T *__restrict__ a_param, const unsigned char *__restrict__ Ug_param, int *err,
+              typename AmpOf<KD == 1>::T *__restrict__ a_param, const unsigned char *__restrict__ Ug_param, int *err,
               const TcBatchDesc *__restrict__ descs, const TcWork *__restrict__ works, unsigned long long *t0s,
               unsigned long long *t1s, double *norm_out)
 {
-    using Cfg = PipeCfg<W>;
+    using Cfg = PipeCfg<KD>;
+    constexpr bool W = Cfg::W, TF = Cfg::TF, QT = Cfg::QT;
     extern __shared__ unsigned char sm_dyn[];
     __shared__ __align__(16) TcPipeArgs s_P;
     const TcBatchDesc *desc = G ? &descs[works[blockIdx.x].desc] : nullptr;
@@ -178,7 +194,8 @@ __global__ void __launch_bounds__(kPThreads, 1)
     unsigned char *smb = (unsigned char *)(((uintptr_t)sm_dyn + 1023) & ~(uintptr_t)1023);
     unsigned char *Us = smb;                              // U operand (N x K): kParts parts of 32 KB
     unsigned char *St = smb + Cfg::kU;                    // raw stages
-    __shared__ __align__(8) uint64_t bar_full[4], bar_sfree[4], bar_aready[2], bar_mma[2], bar_accf[2];
+    __shared__ __align__(8) uint64_t bar_full[8], bar_sfree[8], bar_aready[2], bar_mma[2], bar_accf[2];
+    static_assert(Cfg::kNBar <= 8 && Cfg::kNBar >= Cfg::kNStage, "barrier pairs per stage ring");
     __shared__ uint32_t s_tmem;
     __shared__ int s_abort;
     __shared__ uint16_t s_posL[64];
@@ -209,7 +226,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
             // tile factors are written
             mbar_init(smem_addr(&bar_full[s]), has_pd ? 2 : 1);
             // a complex128 quarter tile is read by the four warps it belongs to
-            mbar_init(smem_addr(&bar_sfree[s]), W ? kPConv / 4 : kPConv);
+            mbar_init(smem_addr(&bar_sfree[s]), QT ? kPConv / 4 : kPConv);
         }
         for (int b = 0; b < 2; b++) {
             mbar_init(smem_addr(&bar_aready[b]), kPConv);
@@ -243,8 +260,8 @@ __global__ void __launch_bounds__(kPThreads, 1)
     if (warp == 0) {
         // ---------------- TMA producer (lane 0) and tile factors of the
         // deferred phases (lanes 0..5)
-        if constexpr (!W) {
-            // complex64: tile j goes to stage j & 1 once the converters have
+        if constexpr (!QT) {
+            // whole tiles: tile j goes to stage j & 1 once the converters have
             // read tile j - 2
             uint64_t issued = 0;
             for (uint64_t j = 0; j < J; j++) {
@@ -288,9 +305,9 @@ __global__ void __launch_bounds__(kPThreads, 1)
                 for (uint64_t j = issued >= 2 ? issued - 2 : 0; j < issued; j++)
                     mbar_wait(smem_addr(&bar_full[j & 1]), (uint32_t)((j >> 1) & 1));
         } else {
-            // complex128: load m (quarter m & 3 of tile m >> 2) goes to stage
-            // m mod kNStage once the converters have read load m - kNStage,
-            // and signals full[m mod kNBar]
+            // quarter tiles: load m (quarter m & 3 of tile m >> 2) goes to
+            // stage m mod kNStage once the converters have read load
+            // m - kNStage, and signals full[m mod kNBar]
             uint32_t m = 0;   // loads issued
             bool quit = false;
             for (uint64_t j = 0; j < J && !quit; j++) {
@@ -315,7 +332,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
                         int c[5];
 #pragma unroll
                         for (int d = 0; d < 5; d++) c[d] = (int)((bq >> P.dim_lo[d]) & ((1ull << P.dim_bits[d]) - 1));
-                        c[0] <<= 1;   // dimension 0 counts the 8-byte halves of an amplitude
+                        if (W) c[0] <<= 1;   // dimension 0 counts the 8-byte halves of an amplitude
                         mbar_arrive_expect_tx(fb, P.box_bytes * (uint32_t)P.nload);
                         const uint32_t dst = smem_addr(St + (size_t)s * Cfg::kStage);
                         for (int v = 0; v < P.nload; v++)
@@ -347,15 +364,19 @@ __global__ void __launch_bounds__(kPThreads, 1)
     } else if (warp == 1) {
         // ---------------- MMA issue: D[g][n] = sum_k A[g][k] U[n][k], A in TMEM
         if (lane == 0) {
-            const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(128 >> 3) << 17) |
+            // instruction descriptor: FP32 accumulator, A and B BF16 (kind::f16)
+            // or TF32 (kind::tf32), both K-major, N = 128, M = 128
+            const uint32_t ab = TF ? 2u : 1u;
+            const uint32_t idesc = (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(128 >> 3) << 17) |
                                    ((uint32_t)(128 >> 4) << 24);
-            const uint32_t SBO = 2048u;
+            // U part: 8-row groups of core matrices SBO bytes apart (K = 128 elements per row)
+            const uint32_t SBO = TF ? 4096u : 2048u;
             uint64_t issued = 0;
             for (uint64_t j = 0; j < J && !*abort_flag; j++) {
                 const int b = (int)(j & 1);
-                // complex64: A operand b, its (j >> 1)-th fill; complex128: the one A operand, its j-th
-                if (!mbar_wait_or_abort(smem_addr(&bar_aready[W ? 0 : b]),
-                                        W ? (uint32_t)(j & 1) : (uint32_t)((j >> 1) & 1), abort_flag)) {
+                // whole tiles: A operand b, its (j >> 1)-th fill; quarter tiles: the one A operand, its j-th
+                if (!mbar_wait_or_abort(smem_addr(&bar_aready[QT ? 0 : b]),
+                                        QT ? (uint32_t)(j & 1) : (uint32_t)((j >> 1) & 1), abort_flag)) {
                     give_up();
                     break;
                 }
@@ -366,18 +387,33 @@ __global__ void __launch_bounds__(kPThreads, 1)
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 const uint32_t d = tmem + (uint32_t)b * 128u;
-                const uint32_t a0 = tmem + 256u + (W ? 0u : (uint32_t)b * 128u);
+                const uint32_t a0 = tmem + 256u + (QT ? 0u : (uint32_t)b * 128u);
                 const uint32_t u0 = smem_addr(Us);
                 uint32_t accum = 0;
+                if constexpr (TF) {
+                    // a_hi u_hi, a_hi u_lo, a_lo u_hi; A hi at +0, lo at +128 columns
 #pragma unroll
-                for (int p = 0; p < (W ? 6 : 3); p++) {
-                    const uint32_t abase = a0 + prod_a<W>(p), bbase = u0 + prod_u<W>(p) * kPHalf;
+                    for (int p = 0; p < 3; p++) {
+                        const uint32_t abase = a0 + (p == 2 ? 128u : 0u), bbase = u0 + (p == 1 ? Cfg::kPart : 0u);
 #pragma unroll
-                    for (int kk = 0; kk < 8; kk++) {
-                        // K step of 16 BF16 = 8 TMEM columns of A, two core matrices of U
-                        mma_issue_tmem_a(d, abase + (uint32_t)kk * 8u, smem_desc(bbase + (uint32_t)kk * 256u, 128u, SBO),
-                                         idesc, accum);
-                        accum = 1;
+                        for (int kk = 0; kk < 16; kk++) {
+                            // K step of 8 TF32 = 8 TMEM columns of A, two core matrices of U
+                            mma_issue_tmem_a_tf32(d, abase + (uint32_t)kk * 8u,
+                                                  smem_desc(bbase + (uint32_t)kk * 256u, 128u, SBO), idesc, accum);
+                            accum = 1;
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int p = 0; p < (W ? 6 : 3); p++) {
+                        const uint32_t abase = a0 + prod_a<W>(p), bbase = u0 + prod_u<W>(p) * kPHalf;
+#pragma unroll
+                        for (int kk = 0; kk < 8; kk++) {
+                            // K step of 16 BF16 = 8 TMEM columns of A, two core matrices of U
+                            mma_issue_tmem_a(d, abase + (uint32_t)kk * 8u,
+                                             smem_desc(bbase + (uint32_t)kk * 256u, 128u, SBO), idesc, accum);
+                            accum = 1;
+                        }
                     }
                 }
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -396,19 +432,24 @@ __global__ void __launch_bounds__(kPThreads, 1)
         const int g = 32 * quarter + lane;
         const uint32_t lane_off = (uint32_t)(32 * quarter) << 16;
         const int rot = P.rot_bits ? (lane >> (P.rot_shift - P.rot_bits)) & ((1 << P.rot_bits) - 1) : 0;
-        // complex128: this thread's amplitudes lie in quarter tile `part`
+        // quarter tiles: this thread's amplitudes lie in quarter tile `part`
         // (block bits 4, 5); the part's warp of lane quarter 0 polls its barriers
-        const int qi = W ? part : 0;
-        const bool qlead = !W || quarter == 0;
-        // in-stage byte offsets of this thread's reads (the same for every tile)
+        const int qi = QT ? part : 0;
+        const bool qlead = !QT || quarter == 0;
+        // in-stage byte offsets of this thread's reads (the same for every
+        // tile): held in registers, except for TF32, whose split keeps 64
+        // registers live and which reads them from shared memory instead
         constexpr uint32_t kEsz = W ? 16u : 8u;
-        uint32_t offL[16];
+        const uint32_t offG = kEsz * (uint32_t)P.posG[g];
+        uint32_t offL[TF ? 1 : 16];
+        if constexpr (!TF) {
 #pragma unroll
-        for (int i = 0; i < 16; i++) offL[i] = kEsz * ((uint32_t)P.posG[g] + s_posL[16 * part + (i ^ rot)]);
+            for (int i = 0; i < 16; i++) offL[i] = offG + kEsz * s_posL[16 * part + (i ^ rot)];
+        }
 
         for (uint64_t j = 0; j < J; j++) {
             const int b = (int)(j & 1);
-            const uint32_t m = W ? (uint32_t)(4 * j + qi) : (uint32_t)j;   // the load this thread reads
+            const uint32_t m = QT ? (uint32_t)(4 * j + qi) : (uint32_t)j;   // the load this thread reads
             const int s = (int)(m % Cfg::kNStage), fbi = (int)(m % Cfg::kNBar);
             const uint32_t fbar = smem_addr(&bar_full[fbi]), fpar = (m / Cfg::kNBar) & 1u;
             const unsigned char *stage = St + (size_t)s * Cfg::kStage;
@@ -419,7 +460,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
             // on one bank group: each lane reads its amplitudes in an order
             // XOR-rotated by its own lane bits, so every read instruction
             // covers distinct banks; v[] is put back in order below.
-            if (!W) {
+            if (!QT) {
                 // one decision for all converter threads (none may be left at a barrier)
                 const bool ok = mbar_wait_or_abort(fbar, fpar, abort_flag);
                 if (named_bar_or(1, kPConv, !ok || *abort_flag)) {
@@ -437,10 +478,16 @@ __global__ void __launch_bounds__(kPThreads, 1)
                 qbad = named_bar_or(3 + qi, kPConv / 4, !ok || *abort_flag);
                 if (!qbad) {
                     (void)mbar_try_wait(fbar, fpar);
+                    if constexpr (W) {
 #pragma unroll
-                    for (int i = 0; i < 16; i++) {
-                        const double2 x = *(const double2 *)(stage + offL[i]);
-                        v[i] = make_float2(f64_to_f32_rn(x.x), f64_to_f32_rn(x.y));
+                        for (int i = 0; i < 16; i++) {
+                            const double2 x = *(const double2 *)(stage + offL[i]);
+                            v[i] = make_float2(f64_to_f32_rn(x.x), f64_to_f32_rn(x.y));
+                        }
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 16; i++)
+                            v[i] = *(const float2 *)(stage + offG + kEsz * s_posL[16 * part + (i ^ rot)]);
                     }
                     mbar_arrive(smem_addr(&bar_sfree[fbi]));
             } else {
@@ -500,7 +547,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
                     v[i].x = xr;
                 }
             }
-            if (!W) {
+            if constexpr (!QT) {
                 // BF16 hi / lo split into A operand b (TMEM)
                 uint32_t hi[16], lo[16];
 #pragma unroll
@@ -525,6 +572,25 @@ __global__ void __launch_bounds__(kPThreads, 1)
                 tmem_st16(acol, hi);
                 tmem_st16(acol + 64u, lo);
             } else {
+                // TF32: split before waiting for the MMAs (the split overlaps
+                // them; only the TMEM stores wait): hi = x rounded to TF32
+                // (to nearest, ties away), lo = x - hi (exact in FP32), kept
+                // in v; K index 2 l + ri of l = 16 part + i is column
+                // 32 part + 2 i + ri of the part
+                uint32_t hi0[16], hi1[16];
+                if constexpr (TF) {
+#pragma unroll
+                    for (int i = 0; i < 8; i++) {
+                        const uint32_t a0 = f32_to_tf32_rna(v[i].x), a1 = f32_to_tf32_rna(v[i].y);
+                        const uint32_t b0 = f32_to_tf32_rna(v[8 + i].x), b1 = f32_to_tf32_rna(v[8 + i].y);
+                        hi0[2 * i] = a0;
+                        hi0[2 * i + 1] = a1;
+                        hi1[2 * i] = b0;
+                        hi1[2 * i + 1] = b1;
+                        v[i] = make_float2(v[i].x - __uint_as_float(a0), v[i].y - __uint_as_float(a1));
+                        v[8 + i] = make_float2(v[8 + i].x - __uint_as_float(b0), v[8 + i].y - __uint_as_float(b1));
+                    }
+                }
                 // the one A operand was last read by the MMAs of tile j - 1
                 // (converter warp 0 polls)
                 const uint32_t mb = smem_addr(&bar_mma[(j - 1) & 1]), mp = (uint32_t)(((j - 1) >> 1) & 1);
@@ -535,25 +601,42 @@ __global__ void __launch_bounds__(kPThreads, 1)
                 }
                 if (j >= 1) (void)mbar_try_wait(mb, mp);
                 asm volatile("tcgen05.fence::after_thread_sync;");
-                // three BF16 slices, each of the remainder of the ones before
-                const uint32_t acol = tmem + lane_off + 256u + (uint32_t)(16 * part);
+                if constexpr (W) {
+                    // three BF16 slices, each of the remainder of the ones before
+                    const uint32_t acol = tmem + lane_off + 256u + (uint32_t)(16 * part);
 #pragma unroll
-                for (int sl = 0; sl < 3; sl++) {
-                    uint32_t pk[16];
+                    for (int sl = 0; sl < 3; sl++) {
+                        uint32_t pk[16];
 #pragma unroll
-                    for (int i = 0; i < 16; i++) {
-                        const __nv_bfloat162 h = __floats2bfloat162_rn(v[i].x, v[i].y);
-                        const float2 hf = __bfloat1622float2(h);
-                        v[i].x -= hf.x;
-                        v[i].y -= hf.y;
-                        pk[i] = *(const uint32_t *)&h;
+                        for (int i = 0; i < 16; i++) {
+                            const __nv_bfloat162 h = __floats2bfloat162_rn(v[i].x, v[i].y);
+                            const float2 hf = __bfloat1622float2(h);
+                            v[i].x -= hf.x;
+                            v[i].y -= hf.y;
+                            pk[i] = *(const uint32_t *)&h;
+                        }
+                        tmem_st16(acol + 64u * (uint32_t)sl, pk);
                     }
-                    tmem_st16(acol + 64u * (uint32_t)sl, pk);
+                } else {
+                    // hi at +0, lo at +128 columns
+                    const uint32_t acol = tmem + lane_off + 256u + (uint32_t)(32 * part);
+                    uint32_t lo0[16], lo1[16];
+#pragma unroll
+                    for (int i = 0; i < 8; i++) {
+                        lo0[2 * i] = __float_as_uint(v[i].x);
+                        lo0[2 * i + 1] = __float_as_uint(v[i].y);
+                        lo1[2 * i] = __float_as_uint(v[8 + i].x);
+                        lo1[2 * i + 1] = __float_as_uint(v[8 + i].y);
+                    }
+                    tmem_st16(acol, hi0);
+                    tmem_st16(acol + 16u, hi1);
+                    tmem_st16(acol + 128u, lo0);
+                    tmem_st16(acol + 144u, lo1);
                 }
             }
             tmem_wait_st();
             asm volatile("tcgen05.fence::before_thread_sync;");
-            mbar_arrive(smem_addr(&bar_aready[W ? 0 : b]));
+            mbar_arrive(smem_addr(&bar_aready[QT ? 0 : b]));
         }
     } else {
         // ---------------- write back (warps 18..21): TMEM lane = group,
@@ -675,9 +758,10 @@ static void tc_pipe_attrs()
 {
     static std::once_flag once;
     std::call_once(once, []() {
-        cudaFuncSetAttribute(k_tc_pipe<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPSmem);
-        cudaFuncSetAttribute(k_tc_pipe<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPSmem);
-        cudaFuncSetAttribute(k_tc_pipe<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPSmem);
+        cudaFuncSetAttribute(k_tc_pipe<false, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PipeCfg<0>::kSmem);
+        cudaFuncSetAttribute(k_tc_pipe<false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PipeCfg<1>::kSmem);
+        cudaFuncSetAttribute(k_tc_pipe<false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PipeCfg<2>::kSmem);
+        cudaFuncSetAttribute(k_tc_pipe<true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PipeCfg<0>::kSmem);
     });
 }
 
@@ -687,13 +771,17 @@ cudaError_t tc_pipe_launch(qsim_state *s, const TcPipeHost &H, const unsigned ch
     if (tc_pipe_encode(H, s->amps, (unsigned char *)&tm) != QSIM_OK) return cudaErrorInvalidValue;
     tc_pipe_attrs();
     const int grid = (int)std::min<uint64_t>(H.args.ntiles, (uint64_t)num_sms());
-    if (H.args.wide != (s->dt == QSIM_C128)) return cudaErrorInvalidValue;
-    if (H.args.wide)
-        k_tc_pipe<false, true><<<grid, kPThreads, kPSmem, s->stream>>>(tm, H.args, (double2 *)s->amps, dU, derr, nullptr,
-                                                                        nullptr, nullptr, nullptr, norm_out);
+    const int kind = H.args.kind;
+    if ((kind == 1) != (s->dt == QSIM_C128)) return cudaErrorInvalidValue;
+    if (kind == 1)
+        k_tc_pipe<false, 1><<<grid, kPThreads, PipeCfg<1>::kSmem, s->stream>>>(
+            tm, H.args, (double2 *)s->amps, dU, derr, nullptr, nullptr, nullptr, nullptr, norm_out);
+    else if (kind == 2)
+        k_tc_pipe<false, 2><<<grid, kPThreads, PipeCfg<2>::kSmem, s->stream>>>(
+            tm, H.args, (float2 *)s->amps, dU, derr, nullptr, nullptr, nullptr, nullptr, norm_out);
     else
-        k_tc_pipe<false, false><<<grid, kPThreads, kPSmem, s->stream>>>(tm, H.args, (float2 *)s->amps, dU, derr, nullptr,
-                                                                         nullptr, nullptr, nullptr, norm_out);
+        k_tc_pipe<false, 0><<<grid, kPThreads, PipeCfg<0>::kSmem, s->stream>>>(
+            tm, H.args, (float2 *)s->amps, dU, derr, nullptr, nullptr, nullptr, nullptr, norm_out);
     return cudaGetLastError();
 }
 
@@ -706,8 +794,8 @@ cudaError_t tc_pipe_launch_grouped(const TcBatchDesc *descs, const TcWork *works
     memset(&tm, 0, sizeof tm);
     TcPipeArgs none;
     memset(&none, 0, sizeof none);
-    k_tc_pipe<true, false><<<nwork, kPThreads, kPSmem, st>>>(tm, none, nullptr, nullptr, err, descs, works, t0, t1,
-                                                              nullptr);
+    k_tc_pipe<true, 0><<<nwork, kPThreads, PipeCfg<0>::kSmem, st>>>(tm, none, nullptr, nullptr, err, descs, works, t0,
+                                                                     t1, nullptr);
     return cudaGetLastError();
 }
 

@@ -66,6 +66,11 @@ struct qsim_state {
     // allocated on first use, read at the next call that synchronises
     int *d_err = nullptr;
     int *h_err = nullptr;
+    // a second ket-sized buffer for permutations (downloads of a relabelled
+    // ket, materialisation), allocated at the first permutation of a ket of
+    // at most 8 GiB and kept until destroy; larger kets take a
+    // stream-ordered temporary per permutation instead
+    void *perm = nullptr;
     size_t amp_bytes() const { return (size_t)(dt == QSIM_C64 ? 8 : 16) << n; }
     uint64_t N() const { return (uint64_t)1 << n; }
 };
@@ -121,6 +126,8 @@ struct TcPipeArgs {
     // SM sub-partition; posL / posG then rank the other 11 tile qubits
     int wide;
     int qpos[2];
+    int kind;                // 0: complex64 BF16X3 whole tiles, 1: complex128 BF16X6, 2: complex64 3XTF32
+                             // (quarter tiles of 8-byte amplitudes, TF32 operands)
     // deferred phases (NULL if none): exp(2 pi i T_b) of block bit b for a
     // group is the product of a tile factor, from the turns tturn[b][i] of
     // the tile-index bits i, and the group factor gfac[g][b]
@@ -134,9 +141,11 @@ struct TcPipeHost {
     uint32_t box[5], estr[5];
     int freeq[7];
 };
-// complex64 with BF16X3, or complex128 with BF16X6; n >= 13
+// complex64 with BF16X3 or 3XTF32, or complex128 with BF16X6; n >= 13
 bool tc_pipe_eligible(int n, qsim_dtype dt, qsim_prec prec);
-qsim_status tc_pipe_prepare(int n, const TcSpec &ts, const void *pd_tables_dev, TcPipeHost &H, bool wide = false);
+// kernel variant (TcPipeArgs::kind) of an eligible pairing
+int tc_pipe_kind(qsim_dtype dt, qsim_prec prec);
+qsim_status tc_pipe_prepare(int n, const TcSpec &ts, const void *pd_tables_dev, TcPipeHost &H, int kind = 0);
 // Deferred-phase tables of a block (tturn then gfac, kTcPipeTableBytes).
 const size_t kTcPipeTableBytes = 6 * 24 * 8 + 128 * 6 * 8;
 void tc_pipe_tables(int n, const TcSpec &ts, const std::vector<int32_t> &off, const std::vector<int32_t> &pbit,

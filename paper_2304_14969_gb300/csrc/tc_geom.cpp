@@ -12,7 +12,13 @@ namespace qs {
 
 bool tc_pipe_eligible(int n, qsim_dtype dt, qsim_prec prec)
 {
-    return n >= 13 && ((dt == QSIM_C64 && prec == QSIM_PREC_BF16X3) || (dt == QSIM_C128 && prec == QSIM_PREC_BF16X6));
+    return n >= 13 && ((dt == QSIM_C64 && (prec == QSIM_PREC_BF16X3 || prec == QSIM_PREC_3XTF32)) ||
+                       (dt == QSIM_C128 && prec == QSIM_PREC_BF16X6));
+}
+
+int tc_pipe_kind(qsim_dtype dt, qsim_prec prec)
+{
+    return dt == QSIM_C128 ? 1 : prec == QSIM_PREC_3XTF32 ? 2 : 0;
 }
 
 // Tile geometry of a block: tile qubits T = the block's 6 qubits and the 7
@@ -22,12 +28,16 @@ bool tc_pipe_eligible(int n, qsim_dtype dt, qsim_prec prec)
 // tile's amplitudes with the tile base's bits as coordinates. Runs beyond
 // the fifth become extra boxes along dimension 4.
 //
-// wide (complex128, 16-byte amplitudes): the box is a quarter tile, the
-// tile qubits other than the block's two highest (block bits 4, 5), which
-// become coordinates; dimension 0 counts 8-byte halves, so its run is at
-// most 7 qubits (a box dimension spans at most 256 elements).
-qsim_status tc_pipe_prepare(int n, const TcSpec &ts, const void *pd_tables_dev, TcPipeHost &H, bool wide)
+// kind 1 (complex128, 16-byte amplitudes) and kind 2 (complex64 with TF32
+// operands): the box is a quarter tile, the tile qubits other than the
+// block's two highest (block bits 4, 5), which become coordinates. For
+// complex128 dimension 0 counts 8-byte halves, so its run is at most 7
+// qubits (a box dimension spans at most 256 elements).
+qsim_status tc_pipe_prepare(int n, const TcSpec &ts, const void *pd_tables_dev, TcPipeHost &H, int kind)
 {
+    if (kind < 0 || kind > 2) return fail(QSIM_E_INVAL, "unknown tensor-core kernel variant %d", kind);
+    const bool wide = kind == 1;          // 16-byte amplitudes (halves along dimension 0)
+    const bool quarters = kind != 0;      // quarter-tile boxes
     if (n < 13 || n > 36) return fail(QSIM_E_UNSUPPORTED, "pipelined tensor-core blocks need 13 <= n <= 36");
     uint64_t blk = 0;
     for (int b = 0; b < 6; b++) blk |= bit(ts.q[b]);
@@ -38,10 +48,10 @@ qsim_status tc_pipe_prepare(int n, const TcSpec &ts, const void *pd_tables_dev, 
     for (int p = 0; p < n; p++)
         if ((blk & bit(p)) || std::find(freeq.begin(), freeq.end(), p) != freeq.end()) T.push_back(p);
     const int es = wide ? 16 : 8;                   // bytes per amplitude
-    const int nbox = wide ? 11 : 13;                 // tile qubits a box covers
+    const int nbox = quarters ? 11 : 13;             // tile qubits a box covers
     std::vector<int> Tb;                             // box qubits, ascending
     for (int p : T)
-        if (!wide || (p != ts.q[4] && p != ts.q[5])) Tb.push_back(p);
+        if (!quarters || (p != ts.q[4] && p != ts.q[5])) Tb.push_back(p);
     // chunks of consecutive box qubits, at most 8 each (7 for dimension 0 when wide)
     std::vector<std::pair<int, int>> ch;   // (first qubit, length)
     for (int j = 0; j < nbox; j++) {
@@ -92,7 +102,7 @@ qsim_status tc_pipe_prepare(int n, const TcSpec &ts, const void *pd_tables_dev, 
     }
     A.box_bytes = (uint32_t)es << boxbits;
     // in-stage element index: rank among the box qubits (the quarter qubits
-    // of a wide tile add nothing)
+    // of a quarter-tile box add nothing)
     auto rank_bit = [&](int q) {
         const auto it = std::find(Tb.begin(), Tb.end(), q);
         return it == Tb.end() ? 0 : 1 << (int)(it - Tb.begin());
@@ -131,8 +141,9 @@ qsim_status tc_pipe_prepare(int n, const TcSpec &ts, const void *pd_tables_dev, 
             return fail(QSIM_E_UNSUPPORTED, "tensor-core block bits not in ascending qubit order");
     A.vecw = (wide || ts.q[0] != 0) ? 0 : ts.q[1] != 1 ? 1 : 2;   // complex64 only
     A.wide = wide;
-    A.qpos[0] = wide ? ts.q[4] : 0;
-    A.qpos[1] = wide ? ts.q[5] : 0;
+    A.kind = kind;
+    A.qpos[0] = quarters ? ts.q[4] : 0;
+    A.qpos[1] = quarters ? ts.q[5] : 0;
     A.tturn = pd_tables_dev ? (const uint64_t *)pd_tables_dev : nullptr;
     A.gfac = pd_tables_dev ? (const float2 *)((const unsigned char *)pd_tables_dev + 6 * 24 * 8) : nullptr;
     H.rank = 5;

@@ -66,6 +66,24 @@ __device__ __forceinline__ void mma_issue_tmem_a(uint32_t tmem_d, uint32_t tmem_
                  "r"(tmem_a), "l"(bdesc), "r"(idesc), "r"(accum));
 }
 
+// The same with kind::tf32 (TF32 inputs: one 32-bit TMEM column per A element).
+__device__ __forceinline__ void mma_issue_tmem_a_tf32(uint32_t tmem_d, uint32_t tmem_a, uint64_t bdesc,
+                                                      uint32_t idesc, uint32_t accum)
+{
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+                 "r"(tmem_a), "l"(bdesc), "r"(idesc), "r"(accum));
+}
+
+// x rounded to TF32 (10 mantissa bits, to nearest, ties away from zero), as
+// the bits of an FP32 value whose low 13 mantissa bits are zero.
+__device__ __forceinline__ uint32_t f32_to_tf32_rna(float x)
+{
+    uint32_t h;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+    return h;
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t parity)
 {
     uint32_t done;

@@ -66,14 +66,15 @@ class qsim_approx_opts(C.Structure):
                 ("exhaustive_from", C.c_int32), ("mlp", C.c_void_p), ("force", C.POINTER(C.c_int32)), ("nforce", C.c_int32),
                 ("log_cap", C.c_int32), ("log", C.POINTER(qsim_decision)), ("state_out", C.c_void_p),
                 ("trace_features", C.POINTER(C.c_float)), ("trace_labels", C.POINTER(C.c_int32)),
-                ("trace_cap", C.c_int64), ("stream", C.c_void_p)]
+                ("trace_cap", C.c_int64), ("stream", C.c_void_p), ("unobservable", C.c_int32),
+                ("pairs", C.c_int32)]
 
 
 class qsim_approx_result(C.Structure):
     _fields_ = [("fidelity_model", C.c_double), ("seconds", C.c_double), ("n_rounds", C.c_int64),
                 ("n_exact", C.c_int64), ("n_checks", C.c_int64), ("n_bloch_passes", C.c_int64),
                 ("peak_bytes", C.c_int64), ("n_log", C.c_int64), ("n_trace", C.c_int64),
-                ("max_subsystem_qubits", C.c_int32), ("budget_gate", C.c_int32)]
+                ("max_subsystem_qubits", C.c_int32), ("budget_gate", C.c_int32), ("n_unobservable", C.c_int64)]
 
 
 class qsim_batch_opts(C.Structure):
@@ -369,7 +370,8 @@ def u2(m) -> np.ndarray:
 
 
 def approx_run(n, gates, p, dtype=QSIM_C64, tau=0.0, budget=0.0, schedule=QSIM_SCHED_EXHAUSTIVE, mlp=None,
-               top_m=4, fallback_every=0, exhaustive_from=0, want_state=False, trace_cap=0, log_cap=0):
+               top_m=4, fallback_every=0, exhaustive_from=0, want_state=False, trace_cap=0, log_cap=0,
+               unobservable=0, pairs=0):
     """qsim_approx_run on a list of workloads.Gate; returns (result, state or
     None, (features, labels) or None, decisions list)."""
     circ = Circuit(n, gates)
@@ -381,6 +383,8 @@ def approx_run(n, gates, p, dtype=QSIM_C64, tau=0.0, budget=0.0, schedule=QSIM_S
     o.top_m = top_m
     o.fallback_every = fallback_every
     o.exhaustive_from = exhaustive_from
+    o.unobservable = int(unobservable)
+    o.pairs = int(pairs)
     if mlp is not None:
         o.mlp = mlp
     state = None

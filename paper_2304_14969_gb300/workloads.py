@@ -288,3 +288,36 @@ def random_1q_circuit(n: int, ngates: int, seed: int, with_controls: bool = True
             b = int(rng.choice(others))
             g.append(Gate("mat2", (q, b), matrix=random_unitary(2, int(rng.integers(0, 2**31)))))
     return g
+
+
+def sparse_control_circuit(n: int, ngates: int, seed: int) -> list:
+    """Controlled gates on a ket that stays close to the computational basis
+    (a workload for the unobservable optimisation of Sec. II.B): a seeded
+    mix of X and T on single qubits, an occasional H or U3, CX / anti-CX,
+    two-control X, CZ (a controlled phase of pi) and controlled phases of
+    random angle on random qubits. Many controls are then Z eigenstates."""
+    rng = np.random.default_rng(seed)
+    g = []
+    for _ in range(ngates):
+        r = float(rng.uniform())
+        q = int(rng.integers(0, n))
+        others = [x for x in range(n) if x != q]
+        if r < 0.20:
+            g.append(Gate("x", (q,)))
+        elif r < 0.28:
+            g.append(Gate("t", (q,)))
+        elif r < 0.34:
+            g.append(Gate("h", (q,)))
+        elif r < 0.38:
+            g.append(Gate("u3", (q,), tuple(float(v) for v in rng.uniform(0, 2 * math.pi, 3))))
+        elif r < 0.62:
+            c = int(rng.choice(others))
+            g.append(Gate("x", (q,), (), (c,), (int(rng.integers(0, 2)),)))
+        elif r < 0.72 and n >= 3:
+            cs = tuple(int(x) for x in rng.choice(others, size=2, replace=False))
+            g.append(Gate("x", (q,), (), cs, (1, int(rng.integers(0, 2)))))
+        elif r < 0.86:
+            g.append(Gate("cp", (q, int(rng.choice(others))), (math.pi,)))
+        else:
+            g.append(Gate("cp", (q, int(rng.choice(others))), (float(rng.uniform(0, 2 * math.pi)),)))
+    return g

@@ -162,16 +162,17 @@ extern "C" int emu_tc_run(const qsim_circuit *c, int prec, const int *start_l2p,
 // dimensions 1..4, dims[24] boxes per tile, dims[25..28] dimension-4
 // offsets of the boxes, dims[29] box bytes, dims[30] rotated low block bits,
 // dims[31] log2 of the write-back's store runs, dims[32] rotation shift, dims[33] wide,
-// dims[34..35] quarter-tile qubits; tpos[13] tile qubits. q6 ascending
-// (as tc_build orders a block). wide: complex128 geometry (quarter tiles).
-extern "C" int emu_tc_geometry(int n, const int *q6, int wide, int64_t *dims, int *tpos, int *posL, int *posG,
+// dims[34..35] quarter-tile qubits, dims[36] kernel variant; tpos[13] tile
+// qubits. q6 ascending (as tc_build orders a block). kind: 0 complex64
+// whole tiles, 1 complex128 quarter tiles, 2 complex64 quarter tiles (TF32).
+extern "C" int emu_tc_geometry(int n, const int *q6, int kind, int64_t *dims, int *tpos, int *posL, int *posG,
                                uint64_t *spL, uint64_t *spG)
 {
     TcSpec ts;
     memset(&ts, 0, sizeof ts);
     for (int b = 0; b < 6; b++) ts.q[b] = q6[b];
     TcPipeHost H;
-    qsim_status st = tc_pipe_prepare(n, ts, nullptr, H, wide != 0);
+    qsim_status st = tc_pipe_prepare(n, ts, nullptr, H, kind);
     if (st != QSIM_OK) return (int)st;
     const TcPipeArgs &A = H.args;
     for (int d = 0; d < 5; d++) {
@@ -190,6 +191,7 @@ extern "C" int emu_tc_geometry(int n, const int *q6, int wide, int64_t *dims, in
     dims[33] = A.wide;
     dims[34] = A.qpos[0];
     dims[35] = A.qpos[1];
+    dims[36] = A.kind;
     for (int j = 0; j < 13; j++) tpos[j] = A.tpos[j];
     for (int l = 0; l < 64; l++) {
         posL[l] = A.posL[l];

@@ -2,9 +2,11 @@
 GPU run against the oracle's full-state-vector run of the same algorithm.
 
 complex128: identical decision log, F within 1e-12, expanded state within
-infidelity 1e-10 of the oracle's. complex64: decisions may differ only where
-the oracle's eps lies within 1e-5 of p/2 (a tie in FP32); such cases are
-checked by replaying the GPU's checks through the oracle."""
+infidelity 1e-10 of the oracle's, up to the 24-28-qubit grid and paper-family
+circuits of the approximate-mode configuration. complex64: decisions may
+differ only where the oracle's eps lies within 1e-5 of p/2 or tau (a tie in
+FP32); the rest of the trajectory is then checked by replaying the GPU's
+checks and decisions through the oracle."""
 import ctypes as C
 
 import numpy as np
@@ -24,7 +26,7 @@ def Q():
     return qsim
 
 
-def gpu_approx(Q, n, gates, p, dt, tau, want_state=True, budget=0.0, force=None):
+def gpu_approx(Q, n, gates, p, dt, tau, want_state=True, budget=0.0, force=None, unobservable=0, pairs=0):
     circ = Q.Circuit(n, gates)
     cap = 64 * len(gates) + 64
     log = (Q.qsim_decision * cap)()
@@ -35,6 +37,8 @@ def gpu_approx(Q, n, gates, p, dt, tau, want_state=True, budget=0.0, force=None)
     o.budget_bytes = budget
     o.log = log
     o.log_cap = cap
+    o.unobservable = unobservable
+    o.pairs = pairs
     if force is not None:
         f = np.ascontiguousarray(np.asarray(force, dtype=np.int32).reshape(-1))
         o.schedule = Q.QSIM_SCHED_FORCED
@@ -44,7 +48,8 @@ def gpu_approx(Q, n, gates, p, dt, tau, want_state=True, budget=0.0, force=None)
         o.state_out = out.ctypes.data_as(C.c_void_p)
     r = Q.qsim_approx_result()
     st = Q.lib().qsim_approx_run(circ.ptr(), float(p), C.byref(o), C.byref(r))
-    entries = [(log[i].gate, log[i].qubit, log[i].action, log[i].eps) for i in range(min(r.n_log, cap))]
+    entries = [(log[i].gate, log[i].qubit, log[i].action, log[i].eps, log[i].reserved)
+               for i in range(min(r.n_log, cap))]
     return st, r, entries, out
 
 
@@ -82,7 +87,8 @@ def test_approx_paper_family_c128(Q, p):
     st, r, log, psi = gpu_approx(Q, n, g, p, 1, 1e-13)
     assert st == 0
     opsi, oF, onr, olog = oracle.sdrp_run(n, g, p, 1e-13)
-    assert len(log) == len(olog)
+    assert [(e[0], e[1], e[2]) for e in log] == [(int(a), int(b), int(c)) for a, b, c in
+                                                 zip(olog["gate"], olog["qubit"], olog["action"])]
     assert abs(r.fidelity_model - oF) < 1e-12
     assert fid(psi, opsi) > 1 - 1e-10
 
@@ -100,9 +106,180 @@ def test_approx_c64_with_ties(Q, p):
     mism = [i for i, e in enumerate(log) if e[2] != olog["action"][i]]
     for i in mism:   # only ties near the threshold may differ
         assert abs(olog["eps"][i] - p / 2) < 1e-5 or abs(olog["eps"][i] - tau) < 1e-5
+    # the whole trajectory, ties included: the oracle replays the GPU's checks
+    # with the GPU's decisions
+    rpsi, rF, rnr, rlog = oracle.sdrp_run(n, g, p, tau, force=force, force_actions=[e[2] for e in log])
+    assert rnr == r.n_rounds
+    assert np.max(np.abs(rlog["eps"] - np.array([e[3] for e in log]))) < 1e-5
+    assert abs(r.fidelity_model - rF) < 1e-5
+    assert fid(psi, rpsi) > 1 - 1e-5
     if not mism:
         assert abs(r.fidelity_model - oF) < 1e-5
         assert fid(psi, opsi) > 1 - 1e-5
+
+
+# The approximate-mode configuration's sizes (4x6 = 24, 5x5 = 25 and 4x7 = 28
+# qubits, 7 layers) on the grid family (fSim couplers) and the paper's family
+# (U3 + C/A-Pauli couplers), at thresholds where checks round selectively
+# and where every check rounds. The oracle runs its all-core build.
+CONFIG_CASES = [
+    ("grid", 5, 5, 0.65), ("grid", 5, 5, 0.72), ("grid", 5, 5, 1.0), ("grid", 4, 6, 1.0),
+    ("paper", 4, 6, 0.05), ("paper", 4, 6, 0.2), ("paper", 4, 6, 0.5),
+    ("grid", 4, 7, 1.0), ("paper", 4, 7, 0.5),
+]
+
+
+@pytest.mark.parametrize("fam,rows,cols,p", CONFIG_CASES)
+def test_approx_config_sizes_c128(Q, fam, rows, cols, p):
+    n = rows * cols
+    g = (W.grid_rcs_circuit(rows, cols, 7, seed=3) if fam == "grid"
+         else W.paper_random_circuit(rows, cols, 7, seed=3))
+    tau = 1e-13
+    st, r, log, psi = gpu_approx(Q, n, g, p, 1, tau)
+    assert st == 0
+    oracle.use_all_cores(True)
+    try:
+        opsi, oF, onr, olog = oracle.sdrp_run(n, g, p, tau)
+    finally:
+        oracle.use_all_cores(False)
+    assert onr > 0
+    assert [(e[0], e[1], e[2]) for e in log] == [(int(a), int(b), int(c)) for a, b, c in
+                                                 zip(olog["gate"], olog["qubit"], olog["action"])]
+    assert np.max(np.abs(np.array([e[3] for e in log]) - olog["eps"])) < 1e-10
+    assert abs(r.fidelity_model - oF) < 1e-12
+    assert r.n_rounds == onr
+    assert fid(psi, opsi) > 1 - 1e-10
+
+
+# Sec. II.B unobservable optimisation (Z-eigenstate controls removed, the gate
+# removed or run locally) against the oracle's run with the same rule.
+UNOBS_CASES = {
+    "qft16_zero": lambda: (16, W.qft_circuit(16)),
+    "sparse16_s0": lambda: (16, W.sparse_control_circuit(16, 120, 0)),
+    "sparse16_s1": lambda: (16, W.sparse_control_circuit(16, 120, 1)),
+    "sparse20_s2": lambda: (20, W.sparse_control_circuit(20, 200, 2)),
+}
+
+
+@pytest.mark.parametrize("p", [0.0, 0.3])
+@pytest.mark.parametrize("name", sorted(UNOBS_CASES))
+def test_unobservable_c128_matches_oracle(Q, name, p):
+    """complex128: the same gates reduced (count), the same decision log, F
+    within 1e-12 and the expanded state within 1e-10 of the oracle's."""
+    n, g = UNOBS_CASES[name]()
+    tau = 1e-13
+    st, r, log, psi = gpu_approx(Q, n, g, p, 1, tau, unobservable=1)
+    assert st == 0
+    stats = {}
+    opsi, oF, onr, olog = oracle.sdrp_run(n, g, p, tau, unobservable=True, stats=stats)
+    assert r.n_unobservable == stats["unobservable"] > 0
+    assert [(e[0], e[1], e[2]) for e in log] == [(int(a), int(b), int(c)) for a, b, c in
+                                                 zip(olog["gate"], olog["qubit"], olog["action"])]
+    assert abs(r.fidelity_model - oF) < 1e-12
+    assert r.n_rounds == onr
+    assert fid(psi, opsi) > 1 - 1e-10
+    if name == "qft16_zero":
+        # every controlled phase meets a qubit in |0>: nothing is composed
+        assert r.n_unobservable == 120 and len(log) == 0 and r.max_subsystem_qubits == 1
+        assert fid(psi, np.full(1 << n, 2.0 ** (-n / 2))) > 1 - 1e-12
+
+
+def test_unobservable_c64_matches_oracle(Q):
+    n, g = UNOBS_CASES["sparse16_s1"]()
+    tau = 1e-6
+    st, r, log, psi = gpu_approx(Q, n, g, 0.3, 0, tau, unobservable=1)
+    assert st == 0
+    stats = {}
+    force = [(e[0], e[1]) for e in log]
+    opsi, oF, onr, olog = oracle.sdrp_run(n, g, 0.3, tau, unobservable=True, stats=stats, force=force,
+                                          force_actions=[e[2] for e in log])
+    assert r.n_unobservable == stats["unobservable"]
+    assert abs(r.fidelity_model - oF) < 1e-5
+    assert fid(psi, opsi) > 1 - 1e-5
+
+
+def test_unobservable_off_is_unchanged(Q):
+    """With the option off the run is the plain exhaustive one (no gate
+    reduced), as before the option existed."""
+    n, g = UNOBS_CASES["sparse16_s0"]()
+    st, r, log, psi = gpu_approx(Q, n, g, 0.3, 1, 1e-13)
+    assert st == 0 and r.n_unobservable == 0
+    opsi, oF, onr, olog = oracle.sdrp_run(n, g, 0.3, 1e-13)
+    assert len(log) == len(olog) and abs(r.fidelity_model - oF) < 1e-12
+
+
+def pair_weak_circuit(delta=0.2):
+    """Bell pairs (0, 1) and (2, 3), a weak controlled U3(delta) from qubit 1
+    to qubit 2, then a CZ on (0, 1)."""
+    return [W.Gate("h", (0,)), W.Gate("x", (1,), (), (0,), (1,)), W.Gate("h", (2,)), W.Gate("x", (3,), (), (2,), (1,)),
+            W.Gate("u3", (2,), (delta, 0.0, 0.0), (1,), (1,)), W.Gate("cp", (0, 1), (np.pi,))]
+
+
+def pair_chain_circuit(npairs=6, delta=0.25):
+    """Bell pairs (2i, 2i + 1), weak controlled U3(delta) between
+    neighbouring pairs (2i + 1 -> 2i + 2), then a CZ on every pair."""
+    g = []
+    for i in range(npairs):
+        g += [W.Gate("h", (2 * i,)), W.Gate("x", (2 * i + 1,), (), (2 * i,), (1,))]
+    for i in range(npairs - 1):
+        g.append(W.Gate("u3", (2 * i + 2,), (delta * (1 + 0.1 * i), 0.3 * i, 0.0), (2 * i + 1,), (1,)))
+    for i in range(npairs):
+        g.append(W.Gate("cp", (2 * i, 2 * i + 1), (np.pi,)))
+    return g
+
+
+PAIR_CASES = [
+    ("weak4", 0.1), ("weak4", 0.0), ("chain12", 0.1), ("chain12", 0.02), ("grid12", 0.3), ("grid12", 0.0),
+    ("paper12", 0.05), ("paper12", 0.2), ("paper20", 0.1),
+]
+
+
+@pytest.mark.parametrize("name,p", PAIR_CASES)
+def test_pairs_c128_matches_oracle(Q, name, p):
+    """Two-qubit-subsystem SDRP (opts->pairs) against the oracle's run with
+    pair checks: identical decision log including the pair entries (qubit a,
+    reserved 1 + b), F within 1e-12, expanded state within 1e-10."""
+    if name == "weak4":
+        n, g = 4, pair_weak_circuit()
+    elif name == "chain12":
+        n, g = 12, pair_chain_circuit()
+    elif name == "grid12":
+        n, g = 12, W.grid_rcs_circuit(3, 4, 6, seed=3)
+    elif name == "paper12":
+        n, g = 12, W.paper_random_circuit(3, 4, 5, seed=11)
+    else:
+        n, g = 20, W.paper_random_circuit(4, 5, 6, seed=12)
+    tau = 1e-13
+    st, r, log, psi = gpu_approx(Q, n, g, p, 1, tau, pairs=1)
+    assert st == 0
+    opsi, oF, onr, olog = oracle.sdrp_run(n, g, p, tau, pairs=True)
+    assert [(e[0], e[1], e[2], e[4]) for e in log] == [
+        (int(a), int(b), int(c), int(d)) for a, b, c, d in zip(olog["gate"], olog["qubit"], olog["action"], olog["pad"])]
+    assert any(e[4] > 0 for e in log)
+    assert np.max(np.abs(np.array([e[3] for e in log]) - olog["eps"])) < 1e-10
+    assert abs(r.fidelity_model - oF) < 1e-12
+    assert r.n_rounds == onr
+    assert fid(psi, opsi) > 1 - 1e-10
+    if name == "weak4" and p == 0.1:
+        # one pair rounding, nothing else: F is exact (Sec. III.B)
+        assert r.n_rounds == 1 and [e[4] for e in log if e[2] == 1] == [2]
+        exact = oracle.apply_circuit(W.basis_state(n, 0), g)
+        assert abs(r.fidelity_model - fid(psi, exact)) < 1e-12
+
+
+def test_pairs_c64_matches_oracle(Q):
+    n, g = 12, W.grid_rcs_circuit(3, 4, 6, seed=3)
+    st, r, log, psi = gpu_approx(Q, n, g, 0.6, 0, 1e-6, pairs=1)
+    assert st == 0
+    opsi, oF, onr, olog = oracle.sdrp_run(n, g, 0.6, 1e-6, pairs=True)
+    same = [(e[0], e[1], e[2], e[4]) for e in log] == [
+        (int(a), int(b), int(c), int(d)) for a, b, c, d in zip(olog["gate"], olog["qubit"], olog["action"], olog["pad"])]
+    if same:
+        assert abs(r.fidelity_model - oF) < 1e-5
+        assert fid(psi, opsi) > 1 - 1e-5
+    else:   # a near-tie decided the other way in FP32: eps within 1e-5 of p/2 or tau
+        k = next(i for i, (e, a) in enumerate(zip(log, olog["action"])) if e[2] != a)
+        assert abs(olog["eps"][k] - 0.3) < 1e-5 or abs(olog["eps"][k] - 1e-6) < 1e-5
 
 
 def test_single_rounding_model_is_exact(Q):

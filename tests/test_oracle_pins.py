@@ -365,6 +365,191 @@ def test_sdrp_threshold_inclusive_and_log_consistent():
     assert np.max(np.abs(psi2 - psi)) == 0
 
 
+def test_sdrp_forced_actions():
+    """Replaying another run's decisions (the near-tie reading of Sec. III.A
+    checks): forcing the natural decisions is bit-identical to the natural
+    run; forcing a single rounding where eps > p/2 gives F = 1 - eps and a
+    state at exactly that fidelity to the exact one (Sec. III.B, the
+    per-projection fidelity); forcing a keep leaves the exact state."""
+    n = 9
+    g = W.paper_random_circuit(3, 3, 3, seed=4)
+    psi, F, nr, log = oracle.sdrp_run(n, g, p=0.3, tau=1e-13)
+    force = np.stack([log["gate"], log["qubit"]], axis=1)
+    psi2, F2, nr2, log2 = oracle.sdrp_run(n, g, p=0.3, tau=1e-13, force=force, force_actions=log["action"])
+    assert F2 == F and nr2 == nr and np.max(np.abs(psi2 - psi)) == 0
+    exact = oracle.apply_circuit(W.basis_state(n, 0), g)
+    # one forced check that would not round at p = 0.3
+    j = int(np.flatnonzero((log["action"] == 0) & (log["eps"] > 0.2))[0])
+    one = force[j:j + 1]
+    psi3, F3, nr3, log3 = oracle.sdrp_run(n, g, p=0.3, tau=1e-13, force=one, force_actions=[1])
+    assert nr3 == 1 and log3["action"][0] == 1
+    eps = log3["eps"][0]
+    assert abs(F3 - (1 - eps)) < 1e-15
+    assert abs(oracle.fidelity(psi3, exact) - (1 - eps)) < 1e-12
+    # one forced keep of a check that would round
+    k = int(np.flatnonzero(log["action"] == 1)[0])
+    psi4, F4, nr4, _ = oracle.sdrp_run(n, g, p=0.3, tau=1e-13, force=force[k:k + 1], force_actions=[0])
+    assert F4 == 1.0 and nr4 == 0
+    assert np.max(np.abs(psi4 - exact)) == 0
+
+
+def _cx(c, t, v=1):
+    return W.Gate("x", (t,), (), (c,), (v,))
+
+
+def test_unobservable_definition_on_basis_input():
+    """Sec. II.B: a transformation is unobservable when |<psi0|C'^dag C|psi0>|^2
+    = 1. On a basis input every control is a Z eigenstate: CX with control
+    |1> acts as a local X, with control |0> (or an anti-control in |1>) as
+    nothing, a CP with either qubit in |0> as nothing and with one in |1> as
+    a phase on the other. Every gate is reduced, nothing merges, no check
+    runs, and the state equals the gate-by-gate result exactly."""
+    n = 6
+    g = [W.Gate("x", (0,)), W.Gate("x", (3,)),
+         _cx(0, 1), _cx(1, 2), _cx(4, 5), _cx(0, 4, 0), _cx(2, 5, 0),
+         W.Gate("cp", (0, 3), (0.7,)), W.Gate("cp", (4, 1), (0.3,)), W.Gate("cp", (5, 2), (1.1,)),
+         W.Gate("x", (5,), (), (0, 3), (1, 1))]
+    st = {}
+    psi, F, nr, log = oracle.sdrp_run(n, g, p=0.5, tau=1e-13, unobservable=True, stats=st)
+    assert len(log) == 0 and F == 1.0 and nr == 0
+    assert st["unobservable"] == 9
+    ex = oracle.apply_circuit(W.basis_state(n, 0), g)
+    assert np.max(np.abs(psi - ex)) == 0
+    # without the rule every one of those gates merges and checks
+    _, _, _, log0 = oracle.sdrp_run(n, g, p=0.5, tau=1e-13)
+    assert len(log0) > 0
+
+
+def test_unobservable_qft_of_zero_state():
+    """QFT of |0...0> (Sec. II.E): every controlled phase meets a qubit still
+    in |0>, so the rule removes all n(n-1)/2 of them; no subsystem is ever
+    composed and the result is the closed form of Eq. (dft) for x = 0."""
+    n = 10
+    g = W.qft_circuit(n)
+    st = {}
+    psi, F, nr, log = oracle.sdrp_run(n, g, p=0.0, tau=1e-13, unobservable=True, stats=st)
+    assert st["unobservable"] == n * (n - 1) // 2 and len(log) == 0 and F == 1.0
+    assert np.max(np.abs(psi - 2.0 ** (-n / 2))) < 1e-14
+
+
+def test_unobservable_partial_and_near_eigenstate():
+    """A two-control X with one control in |1> drops that control and merges
+    only the target with the other control (checks run on those two alone);
+    a control within tau of |0> (U3 with theta = 1e-8: P(1) = sin^2(5e-9),
+    below tau = 1e-13) is projected onto |0> first: the state then has
+    fidelity 1 - P(1) with the exact one, and F is unchanged."""
+    n = 4
+    g = [W.Gate("x", (1,)), W.Gate("h", (2,)), W.Gate("x", (0,), (), (1, 2), (1, 1))]
+    psi, F, nr, log = oracle.sdrp_run(n, g, p=0.0, tau=1e-13, unobservable=True)
+    assert sorted(set(int(q) for q in log["qubit"])) == [0, 2]
+    assert np.max(np.abs(psi - oracle.apply_circuit(W.basis_state(n, 0), g))) == 0
+    th = 1e-8
+    g = [W.Gate("u3", (0,), (th, 0.0, 0.0)), W.Gate("h", (1,)), _cx(0, 1)]
+    st = {}
+    psi, F, nr, log = oracle.sdrp_run(2, g, p=0.0, tau=1e-13, unobservable=True, stats=st)
+    ex = oracle.apply_circuit(W.basis_state(2, 0), g)
+    assert st["unobservable"] == 1 and F == 1.0 and len(log) == 0
+    assert abs(oracle.fidelity(psi, ex) - (1 - np.sin(th / 2) ** 2)) < 1e-15
+    assert abs(psi[1]) < 1e-300 and abs(psi[3]) < 1e-300   # qubit 0 exactly |0>
+
+
+def test_rho2_against_partial_trace():
+    """The pair's reduced density matrix against numpy's partial trace of
+    |psi><psi| (reshape and einsum), a pair in either bit order."""
+    n = 7
+    psi = W.gaussian_state(n, 41)
+    for qa, qb in ((1, 4), (5, 0), (6, 2)):
+        T = psi.reshape([2] * n)            # axis k = qubit n - 1 - k
+        ax = [n - 1 - qa, n - 1 - qb]
+        rest = [k for k in range(n) if k not in ax]
+        M = np.transpose(T, ax[::-1] + rest).reshape(4, -1)   # row index = b_qa + 2 b_qb
+        want = M @ M.conj().T
+        got = oracle.rho2(psi, qa, qb)
+        assert np.max(np.abs(got - want / np.trace(want).real)) < 1e-14
+
+
+def test_herm4_eig_against_numpy():
+    rng = np.random.default_rng(5)
+    for _ in range(20):
+        A = rng.normal(size=(4, 4)) + 1j * rng.normal(size=(4, 4))
+        H = A + A.conj().T
+        w, V = oracle.herm4_eig(H)
+        wn = np.linalg.eigvalsh(H)
+        assert np.max(np.abs(w - wn)) < 1e-12 * np.max(np.abs(wn))
+        for e in range(4):
+            v = V[:, e]
+            assert abs(np.vdot(v, v).real - 1) < 1e-12
+            assert np.max(np.abs(H @ v - w[e] * v)) < 1e-11 * np.max(np.abs(wn))
+
+
+def test_pair_projection_fidelity_and_purity():
+    """Sec. III.B's per-projection fidelity for the pair: projecting onto the
+    top eigenvector of rho_pair keeps fidelity lambda_max = 1 - eps with the
+    input, leaves the pair pure (rho_pair of rank one) and the norm 1."""
+    n = 8
+    psi = W.gaussian_state(n, 43)
+    w, V = oracle.herm4_eig(oracle.rho2(psi, 2, 6))
+    out = oracle.sdrp_project2(psi, 2, 6, V[:, 3])
+    assert abs(oracle.fidelity(out, psi) - w[3]) < 1e-13
+    assert abs(oracle.norm2(out) - 1) < 1e-13
+    w2, _ = oracle.herm4_eig(oracle.rho2(out, 2, 6))
+    assert abs(w2[3] - 1) < 1e-12 and np.max(np.abs(w2[:3])) < 1e-12
+
+
+def test_pair_check_separates_a_bell_pair():
+    """Two Bell pairs (0, 1) and (2, 3), joined into one subsystem by a
+    gate that entangles nothing new (CP of angle 0 on qubits 1, 2), then a
+    CZ on (0, 1): each single qubit has eps = 1/2, so no one-qubit check
+    acts, yet the pair (0, 1) is separable from the rest, eps_pair = 0, and
+    the pair check splits it off exactly (only reachable with two-qubit
+    subsystems)."""
+    n = 4
+    g = [W.Gate("h", (0,)), W.Gate("x", (1,), (), (0,), (1,)), W.Gate("h", (2,)), W.Gate("x", (3,), (), (2,), (1,)),
+         W.Gate("cp", (1, 2), (0.0,)), W.Gate("cp", (0, 1), (np.pi,))]
+    psi, F, nr, log = oracle.sdrp_run(n, g, p=0.0, tau=1e-13, pairs=True)
+    pair = [e for e in log if e["pad"] > 0]
+    last = [e for e in pair if int(e["gate"]) == 5]
+    assert len(last) == 1
+    e = last[0]
+    assert e["action"] == 2 and e["eps"] < 1e-13 and (int(e["qubit"]), int(e["pad"]) - 1) == (0, 1)
+    # the pair (1, 2) after gate 4 is not separable: two halves of different Bell pairs
+    e4 = [e for e in pair if int(e["gate"]) == 4][0]
+    assert e4["action"] == 0 and abs(e4["eps"] - 0.75) < 1e-12
+    assert abs(oracle.fidelity(psi, oracle.apply_circuit(W.basis_state(n, 0), g)) - 1) < 1e-12
+    # every one-qubit check kept (eps = 1/2)
+    assert all(abs(e["eps"] - 0.5) < 1e-12 and e["action"] == 0 for e in log if e["pad"] == 0)
+
+
+def pair_weak_circuit(delta=0.2):
+    """Bell pairs (0, 1) and (2, 3), a weak controlled rotation U3(delta) from
+    qubit 1 to qubit 2, then a CZ on (0, 1): every single qubit stays close to
+    maximally mixed, while the pair (0, 1) is only weakly entangled with
+    (2, 3)."""
+    return [W.Gate("h", (0,)), W.Gate("x", (1,), (), (0,), (1,)), W.Gate("h", (2,)), W.Gate("x", (3,), (), (2,), (1,)),
+            W.Gate("u3", (2,), (delta, 0.0, 0.0), (1,), (1,)), W.Gate("cp", (0, 1), (np.pi,))]
+
+
+def test_pair_rounding_model():
+    """Exactly one rounding, of the pair (0, 1) at the CZ: F = 1 - eps_pair
+    equals the exact fidelity (Sec. III.B); eps_pair equals the smaller
+    Schmidt weight of the (0, 1) | (2, 3) cut computed by numpy's SVD; pairs
+    off reproduces the plain run bit for bit."""
+    n = 4
+    g = pair_weak_circuit()
+    exact = oracle.apply_circuit(W.basis_state(n, 0), g)
+    psi, F, nr, log = oracle.sdrp_run(n, g, p=0.1, tau=1e-13, pairs=True)
+    rounded = [e for e in log if e["action"] == 1]
+    assert len(rounded) == 1 and rounded[0]["pad"] == 2 and int(rounded[0]["qubit"]) == 0
+    M = exact.reshape(4, 4).T          # rows: index bits 0-1 (pair), columns: bits 2-3
+    sv = np.linalg.svd(M, compute_uv=False) ** 2
+    assert abs(rounded[0]["eps"] - (1 - sv[0])) < 1e-13
+    assert abs(F - (1 - rounded[0]["eps"])) < 1e-15
+    assert abs(F - oracle.fidelity(psi, exact)) < 1e-12
+    base = oracle.sdrp_run(n, g, p=0.1, tau=1e-13)
+    off = oracle.sdrp_run(n, g, p=0.1, tau=1e-13, pairs=False)
+    assert np.max(np.abs(base[0] - off[0])) == 0 and len(base[3]) == len(off[3])
+
+
 def test_p_grid_count():
     """Appendix A: 8 width x depth sets x 100 circuits x 41 values of p on
     [0, 1] in steps of 0.025 = 32,800 observations."""

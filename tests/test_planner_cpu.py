@@ -215,9 +215,9 @@ def block_qubits(rng, seed, n):
     return sorted(q6)                # tc_build orders block bits by qubit
 
 
-@pytest.mark.parametrize("wide", [0, 1])
+@pytest.mark.parametrize("kind", [0, 1, 2])
 @pytest.mark.parametrize("seed", range(40))
-def test_tc_pipe_tile_geometry(emu, seed, wide):
+def test_tc_pipe_tile_geometry(emu, seed, kind):
     """The pipelined tensor-core kernel loads a tile (the block's 6 qubits and
     the 7 lowest others) with up to four 5-D TMA boxes of 8-byte elements.
     Replaying the box semantics (element (i0..i4) of box v sits at sum_d
@@ -225,10 +225,13 @@ def test_tc_pipe_tile_geometry(emu, seed, wide):
     one after another in shared memory, dimension 0 fastest) must give every
     amplitude of the tile exactly once, at the in-stage index posL[l] |
     posG[g] the kernel reads, with all coordinates inside the tensor. For
-    complex128 (wide) a load is a quarter tile: the block's two highest
-    qubits (block bits 4, 5: the converter's part) are fixed by the load's
-    index, dimension 0 counts the two 8-byte halves of an amplitude, and the
-    in-stage index ranks the other 11 tile qubits."""
+    complex128 (kind 1) and for complex64 with TF32 operands (kind 2) a load
+    is a quarter tile: the block's two highest qubits (block bits 4, 5: the
+    converter's part) are fixed by the load's index and the in-stage index
+    ranks the other 11 tile qubits; for complex128 dimension 0 counts the
+    two 8-byte halves of an amplitude."""
+    wide = kind == 1
+    quarters = kind != 0
     rng = np.random.default_rng(seed)
     n = int(rng.integers(13, 31))
     q6 = block_qubits(rng, seed, n)
@@ -236,9 +239,10 @@ def test_tc_pipe_tile_geometry(emu, seed, wide):
     tpos = (C.c_int * 13)()
     posL, posG = (C.c_int * 64)(), (C.c_int * 128)()
     spL, spG = (C.c_uint64 * 64)(), (C.c_uint64 * 128)()
-    rc = emu.emu_tc_geometry(n, (C.c_int * 6)(*q6), wide, dims, tpos, posL, posG, spL, spG)
+    rc = emu.emu_tc_geometry(n, (C.c_int * 6)(*q6), kind, dims, tpos, posL, posG, spL, spG)
     assert rc == 0
     d = list(dims)
+    assert d[36] == kind
     lo, bits, box, gdim, gstr = d[0:5], d[5:10], d[10:15], d[15:20], d[20:24]
     nload, xoff, box_bytes = d[24], d[25:29], d[29]
     rot_bits, vecw, rot_shift, dwide, qpos = d[30], d[31], d[32], d[33], d[34:36]
@@ -255,7 +259,7 @@ def test_tc_pipe_tile_geometry(emu, seed, wide):
         assert strides[k] % 16 == 0 and strides[k] < 2 ** 40
     assert all(1 <= b <= 256 for b in box) and box[0] * 8 % 16 == 0
     assert gdim[0] * 8 == es << bits[0]
-    nq = 4 if wide else 1                   # loads per tile
+    nq = 4 if quarters else 1               # loads per tile
     stage_elems = 8192 * es // 8 // nq      # 8-byte elements per load
     assert box_bytes == 8 * int(np.prod(box)) and box_bytes * nload == stage_elems * 8
     # the quarter of (g, l): its bits at the quarter qubits, which are block
@@ -264,7 +268,7 @@ def test_tc_pipe_tile_geometry(emu, seed, wide):
         x = spG[g] | spL[l]
         return ((x >> qpos[0]) & 1) | (((x >> qpos[1]) & 1) << 1)
 
-    if wide:
+    if quarters:
         assert list(qpos) == q6[4:6]
         for g in range(0, 128, 9):
             for l in range(0, 64, 5):
@@ -274,7 +278,7 @@ def test_tc_pipe_tile_geometry(emu, seed, wide):
         base = tile_base(tp, t)
         assert all(not (base >> p) & 1 for p in tp)
         for q in range(nq):
-            bq = base | (((q & 1) << qpos[0]) | ((q >> 1) << qpos[1]) if wide else 0)
+            bq = base | (((q & 1) << qpos[0]) | ((q >> 1) << qpos[1]) if quarters else 0)
             c = [(bq >> lo[k]) & ((1 << bits[k]) - 1) for k in range(5)]
             c[0] *= hpa
             stage = np.full(stage_elems, -1, dtype=np.int64)
@@ -288,7 +292,7 @@ def test_tc_pipe_tile_geometry(emu, seed, wide):
                     off = (cc[k] + np.arange(box[k], dtype=np.int64)) * (strides[k] // 8)
                     idx = (idx[None, :] + off[:, None]).reshape(-1)
                 stage[v * (box_bytes // 8):(v + 1) * (box_bytes // 8)] = idx
-            gl = [(g, l) for g in range(128) for l in range(64) if not wide or quarter_of(g, l) == q]
+            gl = [(g, l) for g in range(128) for l in range(64) if not quarters or quarter_of(g, l) == q]
             assert len(gl) == 8192 // nq
             want = np.array([base + spL[l] + spG[g] for g, l in gl], dtype=np.int64)
             pos = np.array([posL[l] | posG[g] for g, l in gl])
@@ -321,8 +325,8 @@ def test_tc_pipe_tile_geometry(emu, seed, wide):
     assert all(spG[g] % w == 0 for g in range(128))
 
 
-@pytest.mark.parametrize("wide", [0, 1])
-def test_tc_pipe_geometry_always_covered(emu, wide):
+@pytest.mark.parametrize("kind", [0, 1, 2])
+def test_tc_pipe_geometry_always_covered(emu, kind):
     """Every block the planner can emit has a tile geometry (at most five
     tensor dimensions plus two extra-box qubits): all 6-qubit blocks among
     qubits 0..13 at n = 20, and random blocks at n = 13..36."""
@@ -337,8 +341,8 @@ def test_tc_pipe_geometry_always_covered(emu, wide):
         n = int(rng.integers(13, 37))
         cases.append((n, sorted(int(v) for v in rng.choice(n, 6, replace=False))))
     for n, q6 in cases:
-        rc = emu.emu_tc_geometry(n, (C.c_int * 6)(*q6), wide, dims, tpos, posL, posG, spL, spG)
-        assert rc == 0, (n, q6, wide)
+        rc = emu.emu_tc_geometry(n, (C.c_int * 6)(*q6), kind, dims, tpos, posL, posG, spL, spG)
+        assert rc == 0, (n, q6, kind)
 
 
 @pytest.mark.parametrize("seed", range(12))

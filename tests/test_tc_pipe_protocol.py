@@ -4,9 +4,10 @@ modelled on the CPU with random interleavings of its roles.
 The model follows the kernel's roles and mbarrier waits: the TMA producer
 (load m into stage m mod S, signalling full[m mod B] after waiting for the
 free barrier of the load the stage held before), the converters (complex64:
-one group reading tile j; complex128: four quarter groups, quarter q of tile
-j is load 4j + q, plus the all-converter barrier before the A operand is
-rewritten), the MMA issuer and the write-back. A parity wait passes when the
+one group reading tile j; complex128 and complex64 with TF32 operands: four
+quarter groups, quarter q of tile j is load 4j + q, plus the all-converter
+barrier before the A operand is rewritten), the MMA issuer and the
+write-back. A parity wait passes when the
 barrier's current phase parity differs from the one waited for, as
 mbarrier.try_wait.parity does. Every interleaving must read each load from
 its stage after it landed and before the stage is reloaded, and finish.
@@ -48,11 +49,13 @@ class Bar:
         return (self.phase & 1) != parity
 
 
-def run(wide, J, pd, seed, nbar=None):
+def run(wide, J, pd, seed, nbar=None, nstage=None):
     rng = random.Random(seed)
     NS, NB, Q = (3, 4, 4) if wide else (2, 2, 1)
     if nbar:
         NB = nbar
+    if nstage:
+        NS = nstage
     NG = 4 if wide else 1
     full = [Bar(2 if pd else 1) for _ in range(NB)]
     sfree = [Bar(1) for _ in range(NB)]       # a group's threads act as one arrival
@@ -181,6 +184,28 @@ def run(wide, J, pd, seed, nbar=None):
 def test_protocol_random_interleavings(wide, pd):
     for seed in range(600):
         run(wide, 1 + seed % 7, pd, seed)
+
+
+@pytest.mark.parametrize("pd", [False, True])
+def test_protocol_quarter_tiles_five_stages(pd):
+    """Complex64 with TF32 operands: quarter tiles (as complex128) in a ring
+    of five stages with eight barrier pairs (two per quarter, by tile
+    parity), one A operand. With at least as many pairs as stages, issuing
+    load m + B implies load m was read (the producer waited for its stage at
+    load m + S), so no waiter can see a barrier complete twice."""
+    for seed in range(600):
+        run(True, 1 + seed % 7, pd, seed, nstage=5, nbar=8)
+
+
+def test_more_stages_than_barrier_pairs_fails():
+    """Five stages on four barrier pairs: the producer's wait for load
+    m - 5's stage can find the barrier already past load m - 1 as well (two
+    completions, one parity), and loads can be issued onto a barrier whose
+    previous phase has not completed: some interleaving deadlocks or
+    underflows a barrier."""
+    with pytest.raises(AssertionError, match="barrier underflow|deadlock|read before the load landed"):
+        for seed in range(600):
+            run(True, 1 + seed % 7, False, seed, nstage=5, nbar=4)
 
 
 def test_shared_stage_barriers_race():
