@@ -45,6 +45,7 @@ def parse():
                     help="qft27 (default: the 27-qubit QFT on tensor-core blocks), {qft,grid}<n>_{tc,tf32,tc128,simt} "
                          "(one circuit on complex64 BF16x3 or 3xTF32, or complex128, tensor-core blocks, or fused "
                          "SIMT passes; "
+                         "gates27: the per-gate kernels on a 27-qubit complex64 ket, low and high qubits; "
                          "profiling workloads), or appendix_a (the paper's fidelity-model validation in full)")
     return ap.parse_args()
 
@@ -258,6 +259,9 @@ def main():
         args.warmup = 3
     if args.workload == "appendix_a":
         run_appendix_a()
+        return
+    if args.workload == "gates27":
+        run_gates(args)
         return
     if args.workload != "qft27":
         run_grid_tc(args)
@@ -513,6 +517,64 @@ def time_plan(Q, C, plan, st, reps):
     Q.qsim_synchronize(st.h)
     torch.cuda.synchronize()
     return a.elapsed_time(z) / reps
+
+
+def run_gates(args):
+    """Per-gate kernels (A2-A4) on a 27-qubit complex64 ket (1 GiB, larger
+    than L2), each case on high and on low qubits (where a 32-byte sector
+    holds 4 amplitudes and a gate touching every other run of them reads
+    whole sectors anyway): device time per call (CUDA events), algorithmic
+    bytes and GB/s. The profiling workload for their DRAM traffic."""
+    import ctypes as C
+    import torch
+    from paper_2304_14969_gb300 import build, qsim as Q
+    build.build()
+    Q.lib()
+    n = N_QUBITS
+    N = 1 << n
+    B = 8
+    st = Q.State(n, Q.QSIM_C64)
+    Q.qsim_set_basis(st.h, 12345)
+    h = np.ascontiguousarray(np.array([1, 0, 1, 0, 1, 0, -1, 0], dtype=np.float64) / np.sqrt(2))
+    x = np.ascontiguousarray(np.array([0, 0, 1, 0, 1, 0, 0, 0], dtype=np.float64))
+    fsim = np.zeros((4, 4), dtype=np.complex128)
+    fsim[0, 0] = 1
+    fsim[1, 2] = fsim[2, 1] = -1j
+    fsim[3, 3] = np.exp(-1j * np.pi / 6)
+    f2 = np.ascontiguousarray(fsim.ravel().view(np.float64))
+    ctl = (C.c_int * 1)(5)
+    hp = h.ctypes.data_as(C.c_void_p)
+    cases = [
+        ("H q20", lambda: Q.qsim_apply_gate(st.h, hp, 20, None, 0, 0), 2 * B * N),
+        ("H q1", lambda: Q.qsim_apply_gate(st.h, hp, 1, None, 0, 0), 2 * B * N),
+        ("CX c5 t20", lambda: Q.qsim_apply_gate(st.h, x.ctypes.data_as(C.c_void_p), 20, ctl, 1, 1), B * N),
+        ("CP q3 q22", lambda: Q.qsim_apply_cphase(st.h, 3, 22, 0.3), 2 * B * N // 4),
+        ("CP q0 q1", lambda: Q.qsim_apply_cphase(st.h, 0, 1, 0.3), 2 * B * N // 4),
+        ("CP q20 q24", lambda: Q.qsim_apply_cphase(st.h, 20, 24, 0.3), 2 * B * N // 4),
+        ("fSim q7 q19", lambda: Q.qsim_apply_2q(st.h, f2.ctypes.data_as(C.c_void_p), 7, 19), 2 * B * N),
+    ]
+    peaks = {}
+    pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pp):
+        peaks = json.load(open(pp))
+    peak = peaks.get("hbm_gbs", 6800.0)
+    out = {}
+    for name, fn, by in cases:
+        for _ in range(args.warmup):
+            fn()
+        Q.qsim_synchronize(st.h)
+        torch.cuda.synchronize()
+        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(args.steps):
+            fn()
+        z.record()
+        Q.qsim_synchronize(st.h)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(z) / args.steps
+        out[name] = {"ms": ms, "alg_bytes": by, "gbs": by / (ms * 1e-3) / 1e9, "frac_of_hbm": by / (ms * 1e-3) / 1e9 / peak}
+    st.close()
+    print(json.dumps({"workload": "gates27", "n_qubits": n, "ket_bytes": B * N, "steps": args.steps, "cases": out}))
 
 
 def run_grid_tc(args):
@@ -1111,12 +1173,14 @@ def mlp_gain_leg(Q, W, h):
     """The learned schedule against the exhaustive one on held-out
     paper-family circuits of 20, 24 and 28 qubits (7 layers), at equal p:
     wall time, Bloch reductions, roundings and F model of each (summed over
-    the circuits)."""
+    the circuits). An MLP round scores, selects and checks on the device
+    with one host synchronisation, as an exhaustive round does, and skips
+    the Bloch reductions when nothing is proposed."""
     out = []
     for rows, cols in ((4, 5), (4, 6), (4, 7)):
         n = rows * cols
         gs = [W.paper_random_circuit(rows, cols, 7, seed=900 + s) for s in range(2)]
-        for p in (0.4, 0.6):
+        for p in (0.2, 0.4, 0.6):
             row = {"qubits": n, "p": p}
             for name, kw in (("exhaustive", {}), ("mlp", {"schedule": Q.QSIM_SCHED_MLP, "mlp": h, "top_m": 4,
                                                           "fallback_every": 8})):

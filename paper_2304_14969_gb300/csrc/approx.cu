@@ -175,13 +175,18 @@ __global__ void __launch_bounds__(kRhoThreads) k_rho2(const typename AV<R>::T *_
     }
 }
 
+// Four complex amplitudes of a pair state (index bit a + 2 bit b).
+struct Pair4 {
+    double re[4], im[4];
+};
+
 // dst[j] = sum_x conj(phi_x) src[j with the pair bits (ba, bb) = x]: the
 // subsystem ket projected onto <phi| of the pair (m - 2 qubits out).
 template <typename R>
-__global__ void k_project2(const typename AV<R>::T *__restrict__ src, int ba, int bb, uint64_t nout,
-                           const double4 ph01, const double4 ph23, typename AV<R>::T *__restrict__ dst)
+__global__ void k_project2(const typename AV<R>::T *__restrict__ src, int ba, int bb, uint64_t nout, const Pair4 ph,
+                           typename AV<R>::T *__restrict__ dst)
 {
-    const double pr[4] = {ph01.x, ph01.z, ph23.x, ph23.z}, pi[4] = {ph01.y, ph01.w, ph23.y, ph23.w};
+    const double *pr = ph.re, *pi = ph.im;
     const int lo = ba < bb ? ba : bb, hi = ba < bb ? bb : ba;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nout; j += stride) {
@@ -203,16 +208,12 @@ __global__ void k_project2(const typename AV<R>::T *__restrict__ src, int ba, in
 }
 
 template <typename R>
-__global__ void k_put4(typename AV<R>::T *__restrict__ d, const double4 ph01, const double4 ph23)
+__global__ void k_put4(typename AV<R>::T *__restrict__ d, const Pair4 ph)
 {
-    d[0].x = (R)ph01.x;
-    d[0].y = (R)ph01.y;
-    d[1].x = (R)ph01.z;
-    d[1].y = (R)ph01.w;
-    d[2].x = (R)ph23.x;
-    d[2].y = (R)ph23.y;
-    d[3].x = (R)ph23.z;
-    d[3].y = (R)ph23.w;
+    for (int x = 0; x < 4; x++) {
+        d[x].x = (R)ph.re[x];
+        d[x].y = (R)ph.im[x];
+    }
 }
 
 // Eigenvalues (ascending) and unit eigenvectors (columns) of a Hermitian
@@ -276,6 +277,9 @@ struct Decide {
     double eps[64];
     double r[64][3];
     double phi[4];       // |phi> of the acted-on qubit (re0, im0, re1, im1)
+    int32_t nsel;        // MLP rounds: candidates the network proposed (rows of the scored list)
+    int32_t pad2;
+    int32_t sel[64];
 };
 
 // Sec. III.A step 2 in FP64 on the device: for candidates in order, r from
@@ -283,9 +287,10 @@ struct Decide {
 // eps <= tau (exact separation). |phi> = (cos(th/2), e^{i ph} sin(th/2)),
 // th = acos(r_z/|r|), ph = atan2(r_y, r_x); +z when |r| < 1e-15.
 __global__ void k_decide(const double *__restrict__ sums, const int *__restrict__ cand, int ncand, double p,
-                         double tau, Decide *__restrict__ out)
+                         double tau, Decide *__restrict__ out, const int *__restrict__ d_ncand)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (d_ncand) ncand = *d_ncand;
     out->first = ncand;
     out->action = 0;
     int k = 0;
@@ -321,6 +326,36 @@ __global__ void k_decide(const double *__restrict__ sums, const int *__restrict_
     out->examined = k;
 }
 
+// Proposal step of an MLP check round, on the device so that the round
+// needs one host synchronisation, as an exhaustive one: of the `rows`
+// scored qubits (ascending ids, local bits loc[]), those with logit > 0,
+// the top_m by logit (ties to the lower row), in ascending order: their
+// local bits go to cand[], their count to *ncand (0: the round's Bloch
+// passes and decisions do nothing), their rows to out->sel.
+__global__ void k_mlp_select(const float *__restrict__ logit, const int *__restrict__ loc, int rows, int top_m,
+                             int *__restrict__ cand, int *__restrict__ ncand, Decide *__restrict__ out)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    uint64_t chosen = 0;
+    int nsel = 0;
+    while (nsel < top_m) {
+        int best = -1;
+        for (int i = 0; i < rows; i++)
+            if (!((chosen >> i) & 1) && logit[i] > 0.f && (best < 0 || logit[i] > logit[best])) best = i;
+        if (best < 0) break;
+        chosen |= 1ull << best;
+        nsel++;
+    }
+    int k = 0;
+    for (int i = 0; i < rows; i++)
+        if ((chosen >> i) & 1) {
+            out->sel[k] = i;
+            cand[k++] = loc[i];
+        }
+    out->nsel = k;
+    *ncand = k;
+}
+
 namespace {
 
 struct Sub {
@@ -341,6 +376,7 @@ struct Run {
     Scratch sc;
     double *d_sums = nullptr;
     int *d_cand = nullptr;
+    int *d_loc = nullptr;       // MLP rounds: local bits of the scored qubits, then the count
     Decide *d_dec = nullptr, *h_dec = nullptr;
     double *h_amp2 = nullptr;   // pinned: two amplitudes of a one-qubit factor (re, im each)
     int64_t bloch_passes = 0;
@@ -352,6 +388,7 @@ struct Run {
             if (s && s->d) cudaFree(s->d);
         if (d_sums) cudaFree(d_sums);
         if (d_cand) cudaFree(d_cand);
+        if (d_loc) cudaFree(d_loc);
         if (d_dec) cudaFree(d_dec);
         if (h_dec) cudaFreeHost(h_dec);
         if (h_amp2) cudaFreeHost(h_amp2);
@@ -508,12 +545,15 @@ struct Run {
         QS_TRY(alloc(R, m - 2));
         const uint64_t nout = 1ull << (m - 2);
         const int grid = default_grid(nout, 256);
-        const double4 p01 = make_double4(phi[0].real(), phi[0].imag(), phi[1].real(), phi[1].imag());
-        const double4 p23 = make_double4(phi[2].real(), phi[2].imag(), phi[3].real(), phi[3].imag());
+        Pair4 ph;
+        for (int x = 0; x < 4; x++) {
+            ph.re[x] = phi[x].real();
+            ph.im[x] = phi[x].imag();
+        }
         if (dt == QSIM_C64)
-            k_project2<float><<<grid, 256, 0, st>>>((const float2 *)S.d, ba, bb, nout, p01, p23, (float2 *)R.d);
+            k_project2<float><<<grid, 256, 0, st>>>((const float2 *)S.d, ba, bb, nout, ph, (float2 *)R.d);
         else
-            k_project2<double><<<grid, 256, 0, st>>>((const double2 *)S.d, ba, bb, nout, p01, p23, (double2 *)R.d);
+            k_project2<double><<<grid, 256, 0, st>>>((const double2 *)S.d, ba, bb, nout, ph, (double2 *)R.d);
         QS_CUDA(cudaGetLastError());
         release(S);
         S = R;
@@ -533,8 +573,8 @@ struct Run {
         auto F = std::make_unique<Sub>();
         F->qs = {qa, qb};
         QS_TRY(alloc(*F, 2));
-        if (dt == QSIM_C64) k_put4<float><<<1, 1, 0, st>>>((float2 *)F->d, p01, p23);
-        else k_put4<double><<<1, 1, 0, st>>>((double2 *)F->d, p01, p23);
+        if (dt == QSIM_C64) k_put4<float><<<1, 1, 0, st>>>((float2 *)F->d, ph);
+        else k_put4<double><<<1, 1, 0, st>>>((double2 *)F->d, ph);
         QS_CUDA(cudaGetLastError());
         subs.push_back(std::move(F));
         sys_of[qa] = sys_of[qb] = (int)subs.size() - 1;
@@ -624,6 +664,7 @@ extern "C" qsim_status qsim_approx_run(const qsim_circuit *c, double p, const qs
     R.sys_of.resize(n);
     QS_CUDA(cudaMalloc(&R.d_sums, 4 * sizeof(double) * 64));
     QS_CUDA(cudaMalloc(&R.d_cand, sizeof(int) * 64));
+    QS_CUDA(cudaMalloc(&R.d_loc, sizeof(int) * 65));
     QS_CUDA(cudaMalloc(&R.d_dec, sizeof(Decide)));
     QS_CUDA(cudaMallocHost(&R.h_dec, sizeof(Decide)));
     QS_CUDA(cudaMallocHost(&R.h_amp2, 4 * sizeof(double)));
@@ -756,29 +797,9 @@ extern "C" qsim_status qsim_approx_run(const qsim_circuit *c, double p, const qs
             cand = R.subs[si]->qs;
             std::sort(cand.begin(), cand.end());
         }
-        if (o.schedule == QSIM_SCHED_MLP && cand.size() >= 2 &&
-            !(o.fallback_every > 0 && n_ent % o.fallback_every == 0) &&
-            !(o.exhaustive_from > 0 && (int)cand.size() >= o.exhaustive_from)) {
-            // score every qubit of the subsystem, keep the top_m predicted
-            // to round (logit > 0), check them in ascending qubit order
-            int rows = (int)std::min<size_t>(cand.size(), 64);
-            hfeat.assign((size_t)rows * kFeat, 0.f);
-            hlogit.assign(rows, 0.f);
-            int msz = (int)R.subs[si]->qs.size();
-            for (int i = 0; i < rows; i++) features(hist[cand[i]], k, msz, n, p, &hfeat[(size_t)i * kFeat]);
-            QS_CUDA(cudaMemcpyAsync(d_feat, hfeat.data(), sizeof(float) * hfeat.size(), cudaMemcpyHostToDevice, R.st));
-            QS_TRY(mlp_infer_device(o.mlp, d_feat, rows, d_logit, R.st));
-            QS_CUDA(cudaMemcpyAsync(hlogit.data(), d_logit, sizeof(float) * rows, cudaMemcpyDeviceToHost, R.st));
-            QS_CUDA(cudaStreamSynchronize(R.st));
-            std::vector<std::pair<float, int>> sc;
-            for (int i = 0; i < rows; i++)
-                if (hlogit[i] > 0.f) sc.push_back({-hlogit[i], cand[i]});
-            std::sort(sc.begin(), sc.end());
-            if ((int)sc.size() > o.top_m) sc.resize(o.top_m);
-            cand.clear();
-            for (auto &x : sc) cand.push_back(x.second);
-            std::sort(cand.begin(), cand.end());
-        }
+        const bool mlp_round = o.schedule == QSIM_SCHED_MLP && cand.size() >= 2 &&
+                               !(o.fallback_every > 0 && n_ent % o.fallback_every == 0) &&
+                               !(o.exhaustive_from > 0 && (int)cand.size() >= o.exhaustive_from);
         // trace rows: features of the candidates before this check round
         std::vector<float> tf;
         if (o.trace_features && o.schedule != QSIM_SCHED_MLP) {
@@ -786,29 +807,8 @@ extern "C" qsim_status qsim_approx_run(const qsim_circuit *c, double p, const qs
             int msz = (int)R.subs[si]->qs.size();
             for (size_t i = 0; i < cand.size(); i++) features(hist[cand[i]], k, msz, n, p, &tf[i * kFeat]);
         }
-        size_t ci = 0;
-        while (ci < cand.size()) {
-            // skip candidates whose subsystem is a single qubit now
-            int q = cand[ci];
-            Sub &Sq = *R.subs[R.sys_of[q]];
-            if (Sq.qs.size() < 2) {
-                ci++;
-                continue;
-            }
-            int sidx = R.sys_of[q];
-            // the run of following candidates in the same subsystem
-            std::vector<int> loc;
-            size_t cj = ci;
-            while (cj < cand.size() && R.sys_of[cand[cj]] == sidx && loc.size() < 64) loc.push_back(R.local(Sq, cand[cj++]));
-            int passes = 0;
-            QS_TRY(bloch_sums_device(Sq.d, R.dt, (int)Sq.qs.size(), R.st, R.sc, R.d_sums, &passes));
-            R.bloch_passes += passes;
-            QS_CUDA(cudaMemcpyAsync(R.d_cand, loc.data(), sizeof(int) * loc.size(), cudaMemcpyHostToDevice, R.st));
-            k_decide<<<1, 1, 0, R.st>>>(R.d_sums, R.d_cand, (int)loc.size(), p, tau, R.d_dec);
-            QS_CUDA(cudaGetLastError());
-            QS_CUDA(cudaMemcpyAsync(R.h_dec, R.d_dec, sizeof(Decide), cudaMemcpyDeviceToHost, R.st));
-            QS_CUDA(cudaStreamSynchronize(R.st));
-            const Decide &D = *R.h_dec;
+        // the decisions of one check round (D) on candidates cand[ci ..]
+        auto consume = [&](const Decide &D, size_t ci, int sidx, Sub &Sq) -> qsim_status {
             for (int e = 0; e < D.examined; e++) {
                 int qq = cand[ci + e];
                 int act = (e == D.first) ? D.action : 0;
@@ -842,10 +842,7 @@ extern "C" qsim_status qsim_approx_run(const qsim_circuit *c, double p, const qs
                 nlog++;
                 nchecks++;
             }
-            if (D.action == 0) {
-                ci += D.examined;
-                continue;
-            }
+            if (D.action == 0) return QSIM_OK;
             double phi[4] = {D.phi[0], D.phi[1], D.phi[2], D.phi[3]};
             int qa = cand[ci + D.first];
             if (D.action == 1) {
@@ -855,6 +852,66 @@ extern "C" qsim_status qsim_approx_run(const qsim_circuit *c, double p, const qs
                 nexact++;
             }
             QS_TRY(R.split(sidx, R.local(Sq, qa), phi));
+            return QSIM_OK;
+        };
+        size_t ci = 0;
+        if (mlp_round) {
+            // score every qubit of the subsystem (up to 64, ascending), let the
+            // device keep the top_m predicted to round (logit > 0) and check
+            // them: one host synchronisation for the whole round
+            std::vector<int> rows_q = cand;
+            if (rows_q.size() > 64) rows_q.resize(64);
+            const int rows = (int)rows_q.size();
+            Sub &S0 = *R.subs[si];
+            hfeat.assign((size_t)rows * kFeat, 0.f);
+            std::vector<int> loc_all(rows);
+            for (int i = 0; i < rows; i++) {
+                features(hist[rows_q[i]], k, (int)S0.qs.size(), n, p, &hfeat[(size_t)i * kFeat]);
+                loc_all[i] = R.local(S0, rows_q[i]);
+            }
+            QS_CUDA(cudaMemcpyAsync(d_feat, hfeat.data(), sizeof(float) * hfeat.size(), cudaMemcpyHostToDevice, R.st));
+            QS_CUDA(cudaMemcpyAsync(R.d_loc, loc_all.data(), sizeof(int) * rows, cudaMemcpyHostToDevice, R.st));
+            QS_TRY(mlp_infer_device(o.mlp, d_feat, rows, d_logit, R.st));
+            k_mlp_select<<<1, 1, 0, R.st>>>(d_logit, R.d_loc, rows, o.top_m, R.d_cand, R.d_loc + 64, R.d_dec);
+            QS_CUDA(cudaGetLastError());
+            int passes = 0;
+            QS_TRY(bloch_sums_device(S0.d, R.dt, (int)S0.qs.size(), R.st, R.sc, R.d_loc + 64, R.d_sums, &passes));
+            k_decide<<<1, 1, 0, R.st>>>(R.d_sums, R.d_cand, 0, p, tau, R.d_dec, R.d_loc + 64);
+            QS_CUDA(cudaGetLastError());
+            QS_CUDA(cudaMemcpyAsync(R.h_dec, R.d_dec, sizeof(Decide), cudaMemcpyDeviceToHost, R.st));
+            QS_CUDA(cudaStreamSynchronize(R.st));
+            const Decide &D = *R.h_dec;
+            cand.clear();
+            for (int i = 0; i < D.nsel; i++) cand.push_back(rows_q[D.sel[i]]);
+            if (D.nsel > 0) {
+                R.bloch_passes += passes;
+                QS_TRY(consume(D, 0, si, S0));
+                ci = D.examined;
+            }
+        }
+        while (ci < cand.size()) {
+            // skip candidates whose subsystem is a single qubit now
+            int q = cand[ci];
+            Sub &Sq = *R.subs[R.sys_of[q]];
+            if (Sq.qs.size() < 2) {
+                ci++;
+                continue;
+            }
+            int sidx = R.sys_of[q];
+            // the run of following candidates in the same subsystem
+            std::vector<int> loc;
+            size_t cj = ci;
+            while (cj < cand.size() && R.sys_of[cand[cj]] == sidx && loc.size() < 64) loc.push_back(R.local(Sq, cand[cj++]));
+            int passes = 0;
+            QS_TRY(bloch_sums_device(Sq.d, R.dt, (int)Sq.qs.size(), R.st, R.sc, nullptr, R.d_sums, &passes));
+            R.bloch_passes += passes;
+            QS_CUDA(cudaMemcpyAsync(R.d_cand, loc.data(), sizeof(int) * loc.size(), cudaMemcpyHostToDevice, R.st));
+            k_decide<<<1, 1, 0, R.st>>>(R.d_sums, R.d_cand, (int)loc.size(), p, tau, R.d_dec, nullptr);
+            QS_CUDA(cudaGetLastError());
+            QS_CUDA(cudaMemcpyAsync(R.h_dec, R.d_dec, sizeof(Decide), cudaMemcpyDeviceToHost, R.st));
+            QS_CUDA(cudaStreamSynchronize(R.st));
+            const Decide &D = *R.h_dec;
+            QS_TRY(consume(D, ci, sidx, Sq));
             ci += D.examined;
         }
         // ---- two-qubit-subsystem check of the gate's pair (opts->pairs)

@@ -265,8 +265,10 @@ __device__ __forceinline__ uint64_t tile_expand(uint64_t w, const InsSpec &ins)
 }
 
 template <typename R>
-__global__ void k_red_bloch_tile(const typename V2T<R>::T *__restrict__ a, TileSpec ts, double *partial)
+__global__ void k_red_bloch_tile(const typename V2T<R>::T *__restrict__ a, TileSpec ts, double *partial,
+                                 const int *__restrict__ gate)
 {
+    if (gate && *gate == 0) return;   // nothing to check (the sums are not read)
     extern __shared__ __align__(16) unsigned char smraw[];
     typename V2T<R>::T *tile = (typename V2T<R>::T *)smraw;
     const int t = ts.t, c = ts.c;
@@ -358,8 +360,10 @@ template <> struct CAcc<double> {
 // the ket's precision, added into compensated accumulators.
 template <typename R>
 __global__ void __launch_bounds__(256, 1)
-    k_red_bloch_reg(const typename V2T<R>::T *__restrict__ a, const __grid_constant__ TileSpec ts, double *partial)
+    k_red_bloch_reg(const typename V2T<R>::T *__restrict__ a, const __grid_constant__ TileSpec ts, double *partial,
+                    const int *__restrict__ gate)
 {
+    if (gate && *gate == 0) return;   // nothing to check (the sums are not read)
     using V = typename V2T<R>::T;
     extern __shared__ __align__(16) unsigned char smraw[];
     V *tile = (V *)smraw;
@@ -580,7 +584,7 @@ __global__ void k_bloch_scatter(const double *__restrict__ comb, TileSpec ts, in
 // Bloch sums of all n qubits of a ket into d_out[4n] (device), without a
 // host sync: ceil((n - c)/(t - c)) tiled passes, each covering the c low
 // qubits and t - c new high qubits.
-qsim_status bloch_sums_device(const void *amps, qsim_dtype dt, int n, cudaStream_t stream, Scratch &sc,
+qsim_status bloch_sums_device(const void *amps, qsim_dtype dt, int n, cudaStream_t stream, Scratch &sc, const int *d_gate,
                               double *d_out, int *passes)
 {
     int t = std::min(n, 12);
@@ -615,16 +619,17 @@ qsim_status bloch_sums_device(const void *amps, qsim_dtype dt, int n, cudaStream
             }
             blocks = (int)std::min<uint64_t>(ntiles, (uint64_t)num_sms());
             if (dt == QSIM_C64)
-                k_red_bloch_reg<float><<<blocks, 256, smem, stream>>>((const float2 *)amps, ts, sc.d);
+                k_red_bloch_reg<float><<<blocks, 256, smem, stream>>>((const float2 *)amps, ts, sc.d, d_gate);
             else
-                k_red_bloch_reg<double><<<blocks, 256, smem, stream>>>((const double2 *)amps, ts, sc.d);
+                k_red_bloch_reg<double><<<blocks, 256, smem, stream>>>((const double2 *)amps, ts, sc.d, d_gate);
         } else {
             blocks = (int)std::min<uint64_t>(ntiles, kMaxRedBlocks);
             size_t smem = ((size_t)1 << t) * (dt == QSIM_C64 ? 8 : 16);
             if (dt == QSIM_C64)
-                k_red_bloch_tile<float><<<blocks, kRedThreads, smem, stream>>>((const float2 *)amps, ts, sc.d);
+                k_red_bloch_tile<float><<<blocks, kRedThreads, smem, stream>>>((const float2 *)amps, ts, sc.d, d_gate);
             else
-                k_red_bloch_tile<double><<<blocks, kRedThreads, smem, stream>>>((const double2 *)amps, ts, sc.d);
+                k_red_bloch_tile<double><<<blocks, kRedThreads, smem, stream>>>((const double2 *)amps, ts, sc.d,
+                                                                                 d_gate);
         }
         QS_CUDA(cudaGetLastError());
         double *comb = sc.d + (size_t)kMaxRedBlocks * 64;
@@ -645,7 +650,7 @@ qsim_status reduce_bloch_all(qsim_state *s, double *sums)
     QS_TRY(ensure_red(s));
     double *d = nullptr;
     QS_CUDA(cudaMallocAsync((void **)&d, 4 * sizeof(double) * s->n, s->stream));
-    qsim_status st = bloch_sums_device(s->amps, s->dt, s->n, s->stream, s->red, d, nullptr);
+    qsim_status st = bloch_sums_device(s->amps, s->dt, s->n, s->stream, s->red, nullptr, d, nullptr);
     if (st == QSIM_OK) {
         cudaError_t e = cudaMemcpyAsync(sums, d, 4 * sizeof(double) * s->n, cudaMemcpyDeviceToHost, s->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);

@@ -199,8 +199,10 @@ qsim_status reduce_inner(qsim_state *a, qsim_state *b, double out[2]);
 qsim_status reduce_bloch(qsim_state *s, int phys_q, double out4[4]);
 qsim_status reduce_bloch_all(qsim_state *s, double *sums /* 4 per physical qubit */);
 qsim_status probs_to_device(qsim_state *s, double *d_out);
+// d_gate (device, optional): when it holds 0 the tiled passes return at once
+// (a check round with no candidate: the sums are then not read).
 qsim_status bloch_sums_device(const void *amps, qsim_dtype dt, int n, cudaStream_t stream, Scratch &sc,
-                              double *d_out, int *passes);
+                              const int *d_gate, double *d_out, int *passes);
 
 // Generic device buffers ("raw" kets used by approx mode).
 qsim_status ensure_scratch(Scratch &sc, size_t doubles);

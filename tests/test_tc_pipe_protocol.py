@@ -49,8 +49,17 @@ class Bar:
         return (self.phase & 1) != parity
 
 
-def run(wide, J, pd, seed, nbar=None, nstage=None):
+def run(wide, J, pd, seed, nbar=None, nstage=None, lenient=None):
+    """One random interleaving. lenient (a list) records stage violations
+    (an early read, a stage reloaded or overwritten before it was read)
+    instead of failing on them, so that the run goes on to show what the
+    barriers do next; barrier underflow and deadlock still fail."""
     rng = random.Random(seed)
+
+    def violation(kind, info):
+        if lenient is None:
+            raise AssertionError(kind, info)
+        lenient.append(kind)
     NS, NB, Q = (3, 4, 4) if wide else (2, 2, 1)
     if nbar:
         NB = nbar
@@ -78,8 +87,10 @@ def run(wide, J, pd, seed, nbar=None, nstage=None):
                     r = m - NS
                     while not sfree[r % NB].done((r // NB) & 1):
                         yield
-                    assert r in read, ("stage reloaded before it was read", m, r)
-                assert stage[s] is None or stage[s][0] in read, "stage overwritten"
+                    if r not in read:
+                        violation("stage reloaded before it was read", (m, r))
+                if not (stage[s] is None or stage[s][0] in read):
+                    violation("stage overwritten", m)
                 stage[s] = (m, False)
                 full[m % NB].expect_tx(1)
                 inflight.append((s, m, m % NB))
@@ -115,7 +126,8 @@ def run(wide, J, pd, seed, nbar=None, nstage=None):
             m = 4 * j + qi if wide else j
             while not full[m % NB].done((m // NB) & 1):
                 yield
-            assert stage[m % NS] == (m, True), ("read before the load landed", j, qi, stage[m % NS], m)
+            if stage[m % NS] != (m, True):
+                violation("read before the load landed", (j, qi, stage[m % NS], m))
             read.add(m)
             sfree[m % NB].arrive()
             yield
@@ -195,6 +207,26 @@ def test_protocol_quarter_tiles_five_stages(pd):
     load m + S), so no waiter can see a barrier complete twice."""
     for seed in range(600):
         run(True, 1 + seed % 7, pd, seed, nstage=5, nbar=8)
+
+
+def test_shared_stage_barriers_underflow():
+    """What the shared-barrier layout does after such an early read: some
+    interleavings reload a stage whose load was never read and then complete
+    a load's bytes on a barrier phase that has already completed (barrier
+    underflow: an mbarrier over-arrived, undefined in PTX, with a bulk copy
+    still writing the stage). The first complex128 runs of the kernel with
+    that layout returned wrong amplitudes and then a launch failure."""
+    found = False
+    for seed in range(2000):
+        rec = []
+        try:
+            run(True, 1 + seed % 7, False, seed, nbar=3, lenient=rec)
+        except AssertionError as e:
+            if str(e.args[0]).startswith("barrier underflow"):
+                assert rec, "underflow without an earlier stage violation"
+                found = True
+                break
+    assert found
 
 
 def test_more_stages_than_barrier_pairs_fails():
