@@ -498,8 +498,34 @@ def e2e_phases(Q, C, torch, plan, st, stream, host_in, host_out, reps=4):
             acc += [ev[k].elapsed_time(ev[k + 1]) for k in range(3)]
     acc /= reps
     gb = host_in.numel() * host_in.element_size() / 1e9
+    # the host link itself: a 1 GiB copy each way alone and both at once on
+    # two streams (copy engines, pinned buffers), the floor of an e2e step
+    dev_a = torch.empty_like(host_in, device="cuda")
+    dev_b = torch.empty_like(host_in, device="cuda")
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def link(h2d, d2h):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        if h2d:
+            with torch.cuda.stream(s1):
+                dev_a.copy_(host_in, non_blocking=True)
+        if d2h:
+            with torch.cuda.stream(s2):
+                host_out.copy_(dev_b, non_blocking=True)
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) * 1e3
+
+    for _ in range(2):
+        link(True, True)
+    h2d_ms = min(link(True, False) for _ in range(3))
+    d2h_ms = min(link(False, True) for _ in range(3))
+    both_ms = min(link(True, True) for _ in range(3))
+    del dev_a, dev_b
     return {"upload_ms": acc[0], "plan_ms": acc[1], "download_ms": acc[2], "upload_gbs": gb / (acc[0] * 1e-3),
-            "download_gbs": gb / (acc[2] * 1e-3)}
+            "download_gbs": gb / (acc[2] * 1e-3),
+            "link": {"h2d_ms": h2d_ms, "d2h_ms": d2h_ms, "both_ms": both_ms, "h2d_gbs": gb / (h2d_ms * 1e-3),
+                     "d2h_gbs": gb / (d2h_ms * 1e-3), "both_gbs_total": 2 * gb / (both_ms * 1e-3)}}
 
 
 def time_plan(Q, C, plan, st, reps):
@@ -520,8 +546,9 @@ def time_plan(Q, C, plan, st, reps):
 
 
 def run_gates(args):
-    """Per-gate kernels (A2-A4) on a 27-qubit complex64 ket (1 GiB, larger
-    than L2), each case on high and on low qubits (where a 32-byte sector
+    """Per-gate kernels (A2-A4) and the all-qubit Bloch reduction (A11) on a
+    27-qubit complex64 ket (1 GiB, larger than L2), each gate on high and on
+    low qubits (where a 32-byte sector
     holds 4 amplitudes and a gate touching every other run of them reads
     whole sectors anyway): device time per call (CUDA events), algorithmic
     bytes and GB/s. The profiling workload for their DRAM traffic."""
@@ -544,6 +571,7 @@ def run_gates(args):
     f2 = np.ascontiguousarray(fsim.ravel().view(np.float64))
     ctl = (C.c_int * 1)(5)
     hp = h.ctypes.data_as(C.c_void_p)
+    r3 = np.zeros(3 * n)
     cases = [
         ("H q20", lambda: Q.qsim_apply_gate(st.h, hp, 20, None, 0, 0), 2 * B * N),
         ("H q1", lambda: Q.qsim_apply_gate(st.h, hp, 1, None, 0, 0), 2 * B * N),
@@ -552,6 +580,8 @@ def run_gates(args):
         ("CP q0 q1", lambda: Q.qsim_apply_cphase(st.h, 0, 1, 0.3), 2 * B * N // 4),
         ("CP q20 q24", lambda: Q.qsim_apply_cphase(st.h, 20, 24, 0.3), 2 * B * N // 4),
         ("fSim q7 q19", lambda: Q.qsim_apply_2q(st.h, f2.ctypes.data_as(C.c_void_p), 7, 19), 2 * B * N),
+        # all 27 Bloch vectors: three tiled passes, each one read of the ket (synchronises)
+        ("Bloch all", lambda: Q.qsim_bloch_all(st.h, r3.ctypes.data_as(C.c_void_p)), 3 * B * N),
     ]
     peaks = {}
     pp = os.path.join(ROOT, "MEASURED_PEAKS.json")

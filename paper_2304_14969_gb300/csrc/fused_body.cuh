@@ -59,6 +59,24 @@ __device__ __forceinline__ void op_g1f(V (&v)[NR], const R *__restrict__ u, R fr
             if (x & (1 << J)) continue;
             const int xr = ((x >> (J + 1)) << J) | (x & ((1 << J) - 1));
             V p = v[x], q = v[x | (1 << J)];
+            if constexpr (UF == U_HAD && PR != PRE_NONE) {
+                // butterfly with the prefactor F folded in: o0 = p + F q in four
+                // FMAs, o1 = p - F q = 2 p - o0 in two
+                R Fr = D[2 * xr], Fi = D[2 * xr + 1];
+                if constexpr (PR == PRE_FD) {
+                    const R dr = Fr;
+                    Fr = fr * dr - fi * Fi;
+                    Fi = fr * Fi + fi * dr;
+                }
+                V o0, o1;
+                o0.x = fma(Fr, q.x, fma(-Fi, q.y, p.x));
+                o0.y = fma(Fr, q.y, fma(Fi, q.x, p.y));
+                o1.x = fma((R)2, p.x, -o0.x);
+                o1.y = fma((R)2, p.y, -o0.y);
+                v[x] = o0;
+                v[x | (1 << J)] = o1;
+                continue;
+            }
             if constexpr (PR == PRE_D) {
                 q = cmul(q, D[2 * xr], D[2 * xr + 1]);
             } else if constexpr (PR == PRE_FD) {

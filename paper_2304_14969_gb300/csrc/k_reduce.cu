@@ -357,11 +357,13 @@ template <> struct CAcc<double> {
 // of the tile, those with register bits = tile bits 4..7 and 8..11. Every
 // tile qubit's pair sums are taken in registers: sum over bit = 1 of |psi|^2,
 // and S = sum over bit = 0 of conj(psi_i) psi_{i + 2^q}; runs of 8 terms in
-// the ket's precision, added into compensated accumulators.
+// the ket's precision, added into compensated accumulators. low = 0 skips
+// the low qubits' sums (an earlier pass over the same ket has them). A
+// complex64 run is read 16 bytes (two amplitudes) at a time.
 template <typename R>
 __global__ void __launch_bounds__(256, 1)
     k_red_bloch_reg(const typename V2T<R>::T *__restrict__ a, const __grid_constant__ TileSpec ts, double *partial,
-                    const int *__restrict__ gate)
+                    const int *__restrict__ gate, int low)
 {
     if (gate && *gate == 0) return;   // nothing to check (the sums are not read)
     using V = typename V2T<R>::T;
@@ -379,20 +381,27 @@ __global__ void __launch_bounds__(256, 1)
     const uint64_t ntiles = 1ull << (ts.n - 12);
     // the next tile's run is loaded while this one is summed
     V nxt[16];
-    if (blockIdx.x < ntiles) {
-        const V *src = a + (tile_expand((uint64_t)blockIdx.x << 4, ts.ins) | hoff);
+    auto load_run = [&](uint64_t t) {
+        const V *src = a + (tile_expand(t << 4, ts.ins) | hoff);
+        if constexpr (sizeof(V) == 8) {
+            const float4 *s4 = (const float4 *)src;
 #pragma unroll
-        for (int r = 0; r < 16; r++) nxt[r] = src[r];
-    }
+            for (int r = 0; r < 8; r++) {
+                const float4 w = s4[r];
+                nxt[2 * r] = make_float2(w.x, w.y);
+                nxt[2 * r + 1] = make_float2(w.z, w.w);
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < 16; r++) nxt[r] = src[r];
+        }
+    };
+    if (blockIdx.x < ntiles) load_run(blockIdx.x);
     for (uint64_t tid = blockIdx.x; tid < ntiles; tid += gridDim.x) {
         V v[16];
 #pragma unroll
         for (int r = 0; r < 16; r++) v[r] = nxt[r];
-        if (tid + gridDim.x < ntiles) {
-            const V *src = a + (tile_expand((tid + gridDim.x) << 4, ts.ins) | hoff);
-#pragma unroll
-            for (int r = 0; r < 16; r++) nxt[r] = src[r];
-        }
+        if (tid + gridDim.x < ntiles) load_run(tid + gridDim.x);
         auto sums = [&](int j0) {
 #pragma unroll
             for (int j = 0; j < 4; j++) {
@@ -416,7 +425,7 @@ __global__ void __launch_bounds__(256, 1)
             for (int r = 0; r < 16; r++) tot = fma(v[r].x, v[r].x, fma(v[r].y, v[r].y, tot));
             acc[0].add(tot);
         }
-        sums(0);
+        if (low) sums(0);
         __syncthreads();   // the previous tile's reads are done
 #pragma unroll
         for (int r = 0; r < 16; r++) tile[swz(((uint32_t)th << 4) | r)] = v[r];
@@ -568,12 +577,14 @@ qsim_status reduce_bloch(qsim_state *s, int q, double out4[4])
 // Writes, for every tile qubit j of a finished tiled pass, the four sums
 // [sum_{bit0}|psi|^2, sum_{bit1}|psi|^2, Re S, Im S] of qubit tq[j] into
 // out[4*tq[j] ..] (device), from the FP64 combine of the partial rows.
-__global__ void k_bloch_scatter(const double *__restrict__ comb, TileSpec ts, int first_new, double *__restrict__ out)
+__global__ void k_bloch_scatter(const double *__restrict__ comb, TileSpec ts, int first_new, int low,
+                                double *__restrict__ out)
 {
     int j = threadIdx.x;
     if (j >= ts.t) return;
     int q = ts.tq[j];
     if (q < first_new && j >= ts.c) return;   // covered by an earlier pass
+    if (j < ts.c && !low) return;             // the low qubits: the first pass has them
     double total = comb[0], one = comb[1 + 3 * j];
     out[4 * q + 0] = total - one;
     out[4 * q + 1] = one;
@@ -619,9 +630,10 @@ qsim_status bloch_sums_device(const void *amps, qsim_dtype dt, int n, cudaStream
             }
             blocks = (int)std::min<uint64_t>(ntiles, (uint64_t)num_sms());
             if (dt == QSIM_C64)
-                k_red_bloch_reg<float><<<blocks, 256, smem, stream>>>((const float2 *)amps, ts, sc.d, d_gate);
+                k_red_bloch_reg<float><<<blocks, 256, smem, stream>>>((const float2 *)amps, ts, sc.d, d_gate, np == 0);
             else
-                k_red_bloch_reg<double><<<blocks, 256, smem, stream>>>((const double2 *)amps, ts, sc.d, d_gate);
+                k_red_bloch_reg<double><<<blocks, 256, smem, stream>>>((const double2 *)amps, ts, sc.d, d_gate,
+                                                                        np == 0);
         } else {
             blocks = (int)std::min<uint64_t>(ntiles, kMaxRedBlocks);
             size_t smem = ((size_t)1 << t) * (dt == QSIM_C64 ? 8 : 16);
@@ -634,7 +646,8 @@ qsim_status bloch_sums_device(const void *amps, qsim_dtype dt, int n, cudaStream
         QS_CUDA(cudaGetLastError());
         double *comb = sc.d + (size_t)kMaxRedBlocks * 64;
         k_red_final<kTileRow><<<1, 256, 0, stream>>>(sc.d, blocks, comb);
-        k_bloch_scatter<<<1, 32, 0, stream>>>(comb, ts, np == 0 ? 0 : first_new, d_out);
+        k_bloch_scatter<<<1, 32, 0, stream>>>(comb, ts, np == 0 ? 0 : first_new,
+                                              (t == 12 && c == 4) ? (np == 0) : 1, d_out);
         QS_CUDA(cudaGetLastError());
         np++;
         next_high += t - c;
