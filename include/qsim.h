@@ -125,7 +125,8 @@ typedef struct {
     int32_t prec;           /* qsim_prec of fused blocks (fused mode) */
     int32_t tile_qubits;    /* fused: qubits per on-chip tile t (default 13/12 for c64/c128) */
     int32_t low_qubits;     /* fused: low physical qubits kept in every tile (default 5/4) */
-    int32_t max_block;      /* fused: largest dense block k (default 3 SIMT, 6 tensor) */
+    int32_t max_block;      /* tensor-core plans: 7 fuses blocks of up to 7 qubits (complex64,
+                               BF16X3, n >= 14, else QSIM_E_UNSUPPORTED); any other value: 6 */
     int32_t relabel_swaps;  /* 1: SWAP changes the qubit map instead of moving data */
     int32_t reserved[6];
 } qsim_run_opts;
@@ -220,8 +221,8 @@ qsim_status qsim_apply_swap(qsim_state *s, int q0, int q1, int relabel);
  * prec selects SIMT (NATIVE, k <= 7) or the tensor-core split precisions;
  * the tensor-core forms take k <= 6 (smaller blocks are padded with
  * identity qubits) and a complex64 state with n >= 6 (3XTF32, BF16X3) or a
- * complex128 state with n >= 13 (BF16X6); other pairings and k = 7 return
- * QSIM_E_UNSUPPORTED. */
+ * complex128 state with n >= 13 (BF16X6), or k = 7 with BF16X3 on a
+ * complex64 state with n >= 14; other pairings return QSIM_E_UNSUPPORTED. */
 qsim_status qsim_apply_fused(qsim_state *s, int k, const int *qubits, const double *u,
                              qsim_prec prec);
 

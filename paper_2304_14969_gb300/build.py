@@ -33,7 +33,7 @@ def sources() -> list:
 
 
 def _deps_mtime() -> float:
-    files = sources() + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
+    files = sources() + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     files.append(os.path.join(ROOT, "include", "qsim.h"))
     return max(os.path.getmtime(f) for f in files)
 

@@ -86,7 +86,8 @@ qsim_status plan_upload(qsim_plan *P)
         if (bytes) memcpy(buf.data() + off, src, bytes);
         return off;
     };
-    const bool pipe = !P->tc_A.empty() && tc_pipe_eligible(P->n, P->dt, (qsim_prec)P->prec);
+    const int kb = P->tc_spec.empty() ? 6 : P->tc_spec[0].kb;   // every block of a plan has the same size
+    const bool pipe = !P->tc_A.empty() && tc_pipe_eligible(P->n, P->dt, (qsim_prec)P->prec, kb);
     std::vector<size_t> gt(P->tc_A.size(), 0);
     for (size_t i = 0; i < P->tc_A.size(); i++) {
         if (P->tc_pd_off[i].empty()) continue;
@@ -123,7 +124,7 @@ qsim_status plan_upload(qsim_plan *P)
         P->tc_pipe.resize(P->tc_A.size());
         for (size_t i = 0; i < P->tc_A.size(); i++) {
             const void *g = P->tc_pd_off[i].empty() ? nullptr : (const void *)((unsigned char *)P->dmem + gt[i]);
-            QS_TRY(tc_pipe_prepare(P->n, P->tc_spec[i], g, P->tc_pipe[i], tc_pipe_kind(P->dt, (qsim_prec)P->prec)));
+            QS_TRY(tc_pipe_prepare(P->n, P->tc_spec[i], g, P->tc_pipe[i], tc_pipe_kind(P->dt, (qsim_prec)P->prec, kb)));
         }
     }
     return QSIM_OK;
@@ -195,6 +196,8 @@ static qsim_status plan_create_impl(const qsim_circuit *c, qsim_dtype dt, const 
             st = fail(QSIM_E_UNSUPPORTED, "BF16X6 plans take complex128 kets");
         else if (dt == QSIM_C128 && !tc_pipe_eligible(c->n, dt, (qsim_prec)opts->prec))
             st = fail(QSIM_E_UNSUPPORTED, "complex128 tensor-core plans take BF16X6 and n >= 13");
+        else if (opts->max_block == 7 && !tc_pipe_eligible(c->n, dt, (qsim_prec)opts->prec, 7))
+            st = fail(QSIM_E_UNSUPPORTED, "7-qubit tensor-core plans take complex64 kets, BF16X3 and n >= 14");
         else {
             st = plan_build_tc(c, opts, start, P);
             P->dt = dt;

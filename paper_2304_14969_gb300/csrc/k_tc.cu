@@ -263,10 +263,73 @@ __global__ void __launch_bounds__(kTcThreads, PREC == 1 ? 1 : 2) k_tc_block(floa
 // the high ones), forms A = [[Re U, -Im U], [Im U, Re U]] interleaved, and
 // splits it into parts in the kernel's byte layout: TF32 hi / lo (3XTF32),
 // BF16 hi / lo (BF16X3), or three BF16 slices of the FP64 value (BF16X6).
-qsim_status tc_build(int n, int k, const int *phys, const cd *u, qsim_prec prec, std::vector<unsigned char> &A,
-                     TcSpec &ts)
+//
+// kb = 7 (the 7-qubit kernel, complex64 BF16X3): the block is padded to 7
+// qubits the same way and packed as two BF16 levels (hi, then lo), each a
+// 256 x 128 matrix in the same layout (K = input index l) whose rows are the
+// 64-row blocks Re U[0..63], Im U[0..63], Re U[64..127], Im U[64..127]. The
+// kernel forms the real and imaginary outputs from these and the signed
+// parts of the amplitudes, so the real embedding's duplicated blocks are
+// never stored.
+static qsim_status tc_build7(int n, int k, const int *phys, const cd *u, qsim_prec prec,
+                             std::vector<unsigned char> &A, TcSpec &ts)
 {
-    if (k > 6) return fail(QSIM_E_UNSUPPORTED, "tensor-core blocks take k <= 6 (M = 128)");
+    if (prec != QSIM_PREC_BF16X3) return fail(QSIM_E_UNSUPPORTED, "7-qubit tensor-core blocks take BF16X3");
+    if (k > 7) return fail(QSIM_E_UNSUPPORTED, "tensor-core blocks take k <= 7");
+    if (n < 14) return fail(QSIM_E_UNSUPPORTED, "7-qubit tensor-core blocks need n >= 14");
+    int q0[7];
+    uint64_t used = 0;
+    for (int b = 0; b < k; b++) {
+        q0[b] = phys[b];
+        used |= bit(phys[b]);
+    }
+    int kk = k;
+    for (int p = n - 1; p >= 0 && kk < 7; p--)
+        if (!(used & bit(p))) {
+            q0[kk++] = p;
+            used |= bit(p);
+        }
+    int order[7], q[7];
+    for (int b = 0; b < 7; b++) order[b] = b;
+    std::sort(order, order + 7, [&](int x, int y) { return q0[x] < q0[y]; });
+    for (int b = 0; b < 7; b++) q[b] = q0[order[b]];
+    auto old_index = [&](int r) {
+        int o = 0;
+        for (int j = 0; j < 7; j++)
+            if ((r >> j) & 1) o |= 1 << order[j];
+        return o;
+    };
+    const int D = 1 << k;
+    const size_t level = (size_t)2 * kTcRows * kTcRows * 2;   // 256 rows x 128 K of BF16
+    A.assign(2 * level, 0);
+    for (int r = 0; r < 128; r++)
+        for (int c = 0; c < 128; c++) {
+            const int ro = old_index(r), co = old_index(c);
+            const cd v = ((ro >> k) == (co >> k)) ? u[(ro & (D - 1)) * D + (co & (D - 1))] : cd(0.0);
+            const float x[2] = {(float)v.real(), (float)v.imag()};
+            for (int ri = 0; ri < 2; ri++) {
+                const uint32_t off = canon_off(128 * (r >> 6) + 64 * ri + (r & 63), c, 2);
+                const __nv_bfloat16 h = __float2bfloat16_rn(x[ri]);
+                const __nv_bfloat16 lo = __float2bfloat16_rn(x[ri] - __bfloat162float(h));
+                memcpy(A.data() + off, &h, 2);
+                memcpy(A.data() + level + off, &lo, 2);
+            }
+        }
+    for (int b = 0; b < 7; b++) ts.q[b] = q[b];
+    ts.kb = 7;
+    ts.ins.npos = 7;
+    for (int b = 0; b < 7; b++) ts.ins.pos[b] = q[b];
+    ts.pd_off = nullptr;
+    ts.pd_bit = nullptr;
+    ts.pd_tw = nullptr;
+    return QSIM_OK;
+}
+
+qsim_status tc_build(int n, int k, const int *phys, const cd *u, qsim_prec prec, std::vector<unsigned char> &A,
+                     TcSpec &ts, int kb)
+{
+    if (kb == 7) return tc_build7(n, k, phys, u, prec, A, ts);
+    if (k > 6) return fail(QSIM_E_UNSUPPORTED, "tensor-core blocks of 7 qubits take complex64 kets with BF16X3");
     if (n < 6) return fail(QSIM_E_UNSUPPORTED, "tensor-core blocks need n >= 6");
     int q0[6];
     uint64_t used = 0;
@@ -335,6 +398,7 @@ qsim_status tc_build(int n, int k, const int *phys, const cd *u, qsim_prec prec,
                 }
         }
     for (int b = 0; b < 6; b++) ts.q[b] = q[b];
+    ts.kb = 6;
     ts.ins.npos = 6;
     for (int b = 0; b < 6; b++) ts.ins.pos[b] = q[b];
     ts.pd_off = nullptr;
@@ -382,9 +446,12 @@ qsim_status apply_fused_tc(qsim_state *s, int k, const int *phys, const cd *u, q
         return fail(QSIM_E_UNSUPPORTED, "BF16X6 blocks take complex128 kets");
     if (s->dt == QSIM_C128 && !tc_pipe_eligible(s->n, s->dt, prec))
         return fail(QSIM_E_UNSUPPORTED, "complex128 kets take BF16X6 tensor-core blocks with n >= 13");
+    const int kb = k == 7 ? 7 : 6;
+    if (kb == 7 && !tc_pipe_eligible(s->n, s->dt, prec, 7))
+        return fail(QSIM_E_UNSUPPORTED, "7-qubit tensor-core blocks take complex64 kets, BF16X3 and n >= 14");
     std::vector<unsigned char> A;
     TcSpec ts;
-    QS_TRY(tc_build(s->n, k, phys, u, prec, A, ts));
+    QS_TRY(tc_build(s->n, k, phys, u, prec, A, ts, kb));
     unsigned char *dA = nullptr;
     int *derr = nullptr;
     QS_CUDA(cudaMallocAsync((void **)&dA, A.size(), s->stream));
@@ -392,9 +459,9 @@ qsim_status apply_fused_tc(qsim_state *s, int k, const int *phys, const cd *u, q
     QS_CUDA(cudaMemsetAsync(derr, 0, sizeof(int), s->stream));
     QS_CUDA(cudaMemcpyAsync(dA, A.data(), A.size(), cudaMemcpyHostToDevice, s->stream));
     cudaError_t e;
-    if (tc_pipe_eligible(s->n, s->dt, prec)) {
+    if (tc_pipe_eligible(s->n, s->dt, prec, kb)) {
         TcPipeHost H;
-        qsim_status st = tc_pipe_prepare(s->n, ts, nullptr, H, tc_pipe_kind(s->dt, prec));
+        qsim_status st = tc_pipe_prepare(s->n, ts, nullptr, H, tc_pipe_kind(s->dt, prec, kb));
         e = st == QSIM_OK ? tc_pipe_launch(s, H, dA, derr) : cudaErrorInvalidValue;
     } else {
         e = tc_launch(s, ts, dA, prec, derr);

@@ -56,6 +56,7 @@
 #include <mutex>
 
 #include "qsim_internal.h"
+#include "tc_pipe_dev.cuh"
 #include "tc_ptx.cuh"
 
 namespace qs {
@@ -93,15 +94,6 @@ template <int KD> struct PipeCfg {
     static constexpr size_t kSmem = kU + (size_t)kNStage * kStage + 1024;
 };
 
-// One 32-byte global store (sm_100 and later; p 32-byte aligned).
-__device__ __forceinline__ void st_global_256(void *p, uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t a4,
-                                              uint32_t a5, uint32_t a6, uint32_t a7)
-{
-    asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "r"(a0), "r"(a1), "r"(a2),
-                 "r"(a3), "r"(a4), "r"(a5), "r"(a6), "r"(a7)
-                 : "memory");
-}
-
 // IEEE binary64 -> binary32, round to nearest (ties away from zero), on the
 // encodings, for magnitudes below 2^128 (amplitudes); magnitudes below
 // 2^-126 become signed zero. Shifting the double's top 35 bits left by 3
@@ -124,23 +116,6 @@ __device__ __forceinline__ double f32_to_f64(uint32_t f)
     return __hiloint2double((int)(nz ? hi : (f & 0x80000000u)), (int)(nz ? (f << 29) : 0u));
 }
 
-
-__device__ __forceinline__ uint64_t tile_base(const TcPipeArgs &P, uint64_t t)
-{
-    uint64_t base = t;
-#pragma unroll
-    for (int j = 0; j < 13; j++) {
-        const int p = P.tpos[j];
-        base = ((base >> p) << (p + 1)) | (base & ((1ull << p) - 1));
-    }
-    return base;
-}
-
-__device__ __forceinline__ void turns_sincos(uint64_t tt, float &s, float &c)
-{
-    const float f = (float)(int64_t)tt * 5.42101086242752217e-20f;   // turns in [-0.5, 0.5)
-    sincospif(2.0f * f, &s, &c);
-}
 
 // TMEM column of the A part and index of the U part of product p: complex64
 // a0 u0, a0 u1, a1 u0 (parts at +0, +64); complex128 a1 u1, a0 u2, a2 u0,
@@ -277,7 +252,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
                 const uint64_t t = tile_of(j);
                 const uint32_t fb = smem_addr(&bar_full[s]);
                 if (lane == 0) {
-                    const uint64_t base = tile_base(P, t);
+                    const uint64_t base = tile_base<13>(P, t);
                     int c[5];
 #pragma unroll
                     for (int d = 0; d < 5; d++) c[d] = (int)((base >> P.dim_lo[d]) & ((1ull << P.dim_bits[d]) - 1));
@@ -327,7 +302,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
                     if (quit) break;
                     const uint32_t fb = smem_addr(&bar_full[m % Cfg::kNBar]);
                     if (lane == 0) {
-                        const uint64_t bq = tile_base(P, t) | ((uint64_t)(q & 1) << P.qpos[0]) |
+                        const uint64_t bq = tile_base<13>(P, t) | ((uint64_t)(q & 1) << P.qpos[0]) |
                                             ((uint64_t)(q >> 1) << P.qpos[1]);
                         int c[5];
 #pragma unroll
@@ -655,7 +630,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;");
-            const uint64_t base = tile_base(P, tile_of(j));
+            const uint64_t base = tile_base<13>(P, tile_of(j));
 #pragma unroll 1
             for (int c0 = 0; c0 < 128; c0 += 32) {
                 uint32_t r[32];
@@ -773,6 +748,7 @@ cudaError_t tc_pipe_launch(qsim_state *s, const TcPipeHost &H, const unsigned ch
     const int grid = (int)std::min<uint64_t>(H.args.ntiles, (uint64_t)num_sms());
     const int kind = H.args.kind;
     if ((kind == 1) != (s->dt == QSIM_C128)) return cudaErrorInvalidValue;
+    if (kind == 3) return tc_pipe7_launch(s, H, dU, derr, norm_out);
     if (kind == 1)
         k_tc_pipe<false, 1><<<grid, kPThreads, PipeCfg<1>::kSmem, s->stream>>>(
             tm, H.args, (double2 *)s->amps, dU, derr, nullptr, nullptr, nullptr, nullptr, norm_out);

@@ -895,7 +895,7 @@ qsim_status plan_build(const qsim_circuit *cir, qsim_dtype dt, const qsim_run_op
 namespace qs {
 
 // Tensor-core plans: dense gates are fused into blocks of at most 6 qubits
-// by the commutation-aware sweep of the fused passes (a gate joins the
+// (7 with the 7-qubit kernel) by the commutation-aware sweep of the fused passes (a gate joins the
 // current block when its qubits fit and no earlier gate left for later
 // shares a qubit with it). Diagonal gates never block: as in the fused
 // passes they become pending phase terms and are applied right before the
@@ -920,6 +920,7 @@ namespace {
 
 struct TcSweep {
     int n;
+    int kb = 6;                                                // block size limit (6, or 7 for the 7-qubit kernel)
     std::vector<Term> pending;
     cd gphase = 1.0;
     // one block's outcome
@@ -980,7 +981,7 @@ void tc_sweep_block(TcSweep &S, const std::vector<const Item *> &rem, uint64_t a
                 if (allow && !(allow & bit(q))) fits = false;
                 if (std::find(nq.begin(), nq.end(), q) == nq.end()) nq.push_back(q);
             }
-            if (nq.size() > 6) fits = false;
+            if ((int)nq.size() > S.kb) fits = false;
         }
         // pending terms this gate must see first
         std::vector<Term> keep, fold, hoist;
@@ -1077,7 +1078,7 @@ void tc_sweep_block(TcSweep &S, const std::vector<const Item *> &rem, uint64_t a
 // qubit at a time by the qubit with the most dense two-qubit gates to the
 // set among the next kWindow ones (compact clusters of the interaction
 // graph, e.g. patches of a 2-D grid).
-std::vector<uint64_t> tc_candidates(const std::vector<const Item *> &rem, int n)
+std::vector<uint64_t> tc_candidates(const std::vector<const Item *> &rem, int n, int kb)
 {
     const int kMaxSeeds = 48, kWindow = 400;
     std::vector<uint64_t> out;
@@ -1097,7 +1098,7 @@ std::vector<uint64_t> tc_candidates(const std::vector<const Item *> &rem, int n)
         if (rem[s]->kind != 0 || rem[s]->nq != 2) continue;
         gseeds++;
         uint64_t m = bit(rem[s]->q[0]) | bit(rem[s]->q[1]);
-        for (int size = 2; size < 6; size++) {
+        for (int size = 2; size < kb; size++) {
             int best = -1, bw = 0;
             for (int q = 0; q < n; q++) {
                 if (m & bit(q)) continue;
@@ -1125,7 +1126,7 @@ std::vector<uint64_t> tc_candidates(const std::vector<const Item *> &rem, int n)
                 m |= bit(rem[s]->q[k]);
                 cnt++;
             }
-        for (size_t i = 0; i < rem.size() && cnt < 6; i++) {
+        for (size_t i = 0; i < rem.size() && cnt < kb; i++) {
             const Item *it = rem[i];
             if (it->kind != 0) continue;
             uint64_t mi = 0;
@@ -1138,7 +1139,7 @@ std::vector<uint64_t> tc_candidates(const std::vector<const Item *> &rem, int n)
             if (!(mi & m)) continue;
             int add = 0;
             for (int k = 0; k < it->nq; k++) add += !(m & bit(it->q[k])) && (mi & bit(it->q[k]));
-            if (cnt + add > 6) continue;
+            if (cnt + add > kb) continue;
             m |= mi;
             cnt += add;
         }
@@ -1155,7 +1156,7 @@ uint64_t tc_choose(const TcSweep &S0, const std::vector<const Item *> &rem)
     tc_sweep_block(T, rem, 0, true);
     int best = T.ng;
     uint64_t pick = 0;
-    for (uint64_t m : tc_candidates(rem, S0.n)) {
+    for (uint64_t m : tc_candidates(rem, S0.n, S0.kb)) {
         TcSweep C = S0;
         tc_sweep_block(C, rem, m, true);
         if (C.ng > best) {
@@ -1167,10 +1168,11 @@ uint64_t tc_choose(const TcSweep &S0, const std::vector<const Item *> &rem)
 }
 
 // Blocks of a matrix-free sweep of the whole circuit (choose: per-block choice).
-int tc_count_blocks(int n, const std::vector<Item> &items, bool choose)
+int tc_count_blocks(int n, int kb, const std::vector<Item> &items, bool choose)
 {
     TcSweep S;
     S.n = n;
+    S.kb = kb;
     std::vector<const Item *> rem;
     for (auto &it : items) rem.push_back(&it);
     int blocks = 0;
@@ -1205,11 +1207,17 @@ qsim_status plan_build_tc(const qsim_circuit *cir, const qsim_run_opts *opts, co
         for (int q = 0; q < n; q++) l2p[q] = start_l2p ? start_l2p[q] : q;
         P->start_l2p = l2p;
     }
+    // block size: 6 (blocks of fewer qubits are padded to 6), or 7 when
+    // max_block asks for it (the 7-qubit kernel: complex64, BF16X3, n >= 14)
+    const int kb = opts->max_block == 7 ? 7 : 6;
+    if (kb == 7 && (opts->prec != QSIM_PREC_BF16X3 || n < 14))
+        return fail(QSIM_E_UNSUPPORTED, "7-qubit tensor-core blocks take BF16X3 and n >= 14");
     std::vector<Item> items;
     classify_gates(cir, start_l2p, true, items, P->final_l2p, P->nswaps);
-    const bool choose = tc_count_blocks(n, items, true) < tc_count_blocks(n, items, false);
+    const bool choose = tc_count_blocks(n, kb, items, true) < tc_count_blocks(n, kb, items, false);
     TcSweep S;
     S.n = n;
+    S.kb = kb;
     auto flush_pergate = [&]() {
         for (const Term &tm : S.pending) {
             PlanStep st;
@@ -1264,14 +1272,14 @@ qsim_status plan_build_tc(const qsim_circuit *cir, const qsim_run_opts *opts, co
             for (auto &x : U) x *= S.gphase;
             S.gphase = 1.0;
         }
-        // pad the block to six qubits here (the kernel reads a pre-diagonal
+        // pad the block to kb qubits here (the kernel reads a pre-diagonal
         // partner's bit from the group index, where padded bits are 0):
         // highest free qubits that are no partner first, then partners,
         // whose terms then act inside the block as a diagonal before U
         {
             std::vector<int> pad;
             for (int pass = 0; pass < 2; pass++)
-                for (int p = n - 1; p >= 0 && Q.size() + pad.size() < 6; p--)
+                for (int p = n - 1; p >= 0 && (int)(Q.size() + pad.size()) < kb; p--)
                     if (std::find(Q.begin(), Q.end(), p) == Q.end() &&
                         std::find(pad.begin(), pad.end(), p) == pad.end() && (bool)outside[p] == (pass == 1))
                         pad.push_back(p);
@@ -1303,11 +1311,11 @@ qsim_status plan_build_tc(const qsim_circuit *cir, const qsim_run_opts *opts, co
         }
         TcSpec ts;
         std::vector<unsigned char> A;
-        QS_TRY(tc_build(n, (int)Q.size(), Q.data(), U.data(), (qsim_prec)opts->prec, A, ts));
+        QS_TRY(tc_build(n, (int)Q.size(), Q.data(), U.data(), (qsim_prec)opts->prec, A, ts, kb));
         // pre-diagonal partner lists per block bit, in tc_build's bit order
-        std::vector<int32_t> off(7, 0), pb;
+        std::vector<int32_t> off(kb + 1, 0), pb;
         std::vector<uint64_t> ptw;
-        for (int b = 0; b < 6; b++) {
+        for (int b = 0; b < kb; b++) {
             off[b] = (int32_t)pb.size();
             if (b < (int)Q.size())
                 for (auto &x : pre)
@@ -1316,7 +1324,7 @@ qsim_status plan_build_tc(const qsim_circuit *cir, const qsim_run_opts *opts, co
                         ptw.push_back(to_turns(x.second.second));
                     }
         }
-        off[6] = (int32_t)pb.size();
+        off[kb] = (int32_t)pb.size();
         P->tc_spec.push_back(ts);
         P->tc_A.push_back(std::move(A));
         P->tc_pd_off.push_back(pre.empty() ? std::vector<int32_t>() : off);

@@ -83,10 +83,11 @@ struct InsSpec {
     int pos[12] = {0};  // ascending
 };
 
-// Tensor-core block (k <= 6, padded to 6): physical bit of block bit b and
-// the sorted block qubits for group expansion.
+// Tensor-core block (k <= 6 padded to 6, or k = 7): physical bit of block
+// bit b (ascending) and the sorted block qubits for group expansion.
 struct TcSpec {
-    int q[6];
+    int q[7];
+    int kb = 6;              // block bits: 6, or 7 (complex64 BF16X3 blocks of the 7-qubit kernel)
     InsSpec ins;
     // optional pre-diagonal: the amplitude with block index l in the group
     // whose outside bits are G is multiplied by exp(2 pi i sum_b l_b T_b(G))
@@ -96,8 +97,10 @@ struct TcSpec {
     const int32_t *pd_bit;
     const uint64_t *pd_tw;
 };
+// kb = 7: the block is padded to seven qubits and packed for the 7-qubit
+// kernel (complex64 BF16X3 only).
 qsim_status tc_build(int n, int k, const int *phys, const cd *u, qsim_prec prec, std::vector<unsigned char> &A,
-                     TcSpec &ts);
+                     TcSpec &ts, int kb = 6);
 cudaError_t tc_launch(qsim_state *s, const TcSpec &ts, const unsigned char *dA, qsim_prec prec, int *derr);
 
 // Pipelined block kernel (BF16X3 on complex64, BF16X6 on complex128;
@@ -105,17 +108,17 @@ cudaError_t tc_launch(qsim_state *s, const TcSpec &ts, const unsigned char *dA, 
 // (k_tc_pipe.cu).
 struct TcPipeArgs {
     uint64_t ntiles;
-    int tpos[13];            // tile qubits, ascending (tile index bits go to the other positions)
+    int tpos[14];            // tile qubits, ascending (tile index bits go to the other positions)
     int dim_lo[5];           // lowest qubit of each tensor dimension
     int dim_bits[5];         // qubits covered by each tensor dimension (coordinate width)
     int nload;               // boxes per tile (per quarter tile when wide)
     int xoff[4];             // coordinate offset along dimension 4 of box v
     uint32_t box_bytes;
-    uint16_t posL[64];       // in-stage element index of block index l (wide: within its quarter tile)
+    uint16_t posL[128];      // in-stage element index of block index l (split loads: within its load)
     uint16_t posG[128];      // in-stage element index of group g
-    uint64_t spL[64];        // amplitude offset of block index l
+    uint64_t spL[128];       // amplitude offset of block index l
     uint64_t spG[128];       // amplitude offset of group g
-    int ntb;                 // tile-index bits (n - 13)
+    int ntb;                 // tile-index bits (n - 13, or n - 14 for 7-qubit blocks)
     int rot_bits;            // block qubits among qubits 0..3 (= block index bits 0..rot_bits-1)
     int vecw;                // complex64: the lowest qubits are block bits 0..vecw-1, so a thread's
                              // amplitudes come in runs of 2^vecw adjacent ones (stored 16 or 32 bytes at a time)
@@ -125,14 +128,16 @@ struct TcPipeArgs {
     // each quarter is read by the converter warps of one part, one on each
     // SM sub-partition; posL / posG then rank the other 11 tile qubits
     int wide;
-    int qpos[2];
+    int qpos[3];             // block qubits 4, 5 (and 6) whose values select a split load
     int kind;                // 0: complex64 BF16X3 whole tiles, 1: complex128 BF16X6, 2: complex64 3XTF32
-                             // (quarter tiles of 8-byte amplitudes, TF32 operands)
+                             // (quarter tiles of 8-byte amplitudes, TF32 operands), 3: complex64 BF16X3
+                             // 7-qubit blocks (tiles of 14 qubits in eighths, one per value of block bits 4..6)
+    int kb;                  // block bits (6, or 7 for kind 3)
     // deferred phases (NULL if none): exp(2 pi i T_b) of block bit b for a
     // group is the product of a tile factor, from the turns tturn[b][i] of
     // the tile-index bits i, and the group factor gfac[g][b]
-    const uint64_t *tturn;   // [6][24]
-    const float2 *gfac;      // [128][6]
+    const uint64_t *tturn;   // [kb][24]
+    const float2 *gfac;      // [128][kb]
 };
 struct TcPipeHost {
     TcPipeArgs args;
@@ -142,18 +147,24 @@ struct TcPipeHost {
     int freeq[7];
 };
 // complex64 with BF16X3 or 3XTF32, or complex128 with BF16X6; n >= 13
-bool tc_pipe_eligible(int n, qsim_dtype dt, qsim_prec prec);
+// (kb = 7: complex64 with BF16X3 and n >= 14)
+bool tc_pipe_eligible(int n, qsim_dtype dt, qsim_prec prec, int kb = 6);
 // kernel variant (TcPipeArgs::kind) of an eligible pairing
-int tc_pipe_kind(qsim_dtype dt, qsim_prec prec);
+int tc_pipe_kind(qsim_dtype dt, qsim_prec prec, int kb = 6);
 qsim_status tc_pipe_prepare(int n, const TcSpec &ts, const void *pd_tables_dev, TcPipeHost &H, int kind = 0);
-// Deferred-phase tables of a block (tturn then gfac, kTcPipeTableBytes).
-const size_t kTcPipeTableBytes = 6 * 24 * 8 + 128 * 6 * 8;
+// Deferred-phase tables of a block (tturn then gfac: tc_pipe_table_bytes(kb)
+// bytes; kTcPipeTableBytes is the larger of the two sizes).
+inline size_t tc_pipe_table_bytes(int kb) { return (size_t)kb * 24 * 8 + 128 * (size_t)kb * 8; }
+const size_t kTcPipeTableBytes = 7 * 24 * 8 + 128 * 7 * 8;
 void tc_pipe_tables(int n, const TcSpec &ts, const std::vector<int32_t> &off, const std::vector<int32_t> &pbit,
                     const std::vector<uint64_t> &tw, std::vector<unsigned char> &out);
 // norm_out (device, optional): the kernel adds the sum of |amplitude|^2 of
 // everything it writes (FP64 accumulation); the caller zeroes it first.
 cudaError_t tc_pipe_launch(qsim_state *s, const TcPipeHost &H, const unsigned char *dU, int *derr,
                            double *norm_out = nullptr);
+// The 7-qubit variant (kind 3, k_tc_pipe7.cu); tc_pipe_launch forwards to it.
+cudaError_t tc_pipe7_launch(qsim_state *s, const TcPipeHost &H, const unsigned char *dU, int *derr,
+                            double *norm_out);
 
 // Grouped launches of the pipelined kernel (batched circuits): one CTA per
 // work entry = a range of tiles of one block of one circuit.

@@ -283,8 +283,8 @@ class State:
         qsim_download(self.h, out.ctypes.data_as(C.c_void_p))
         return out
 
-    def run(self, circ: Circuit, mode=QSIM_MODE_PER_GATE, relabel=0, prec=QSIM_PREC_NATIVE, tile=0):
-        o = qsim_run_opts(mode=mode, prec=prec, tile_qubits=tile, relabel_swaps=relabel)
+    def run(self, circ: Circuit, mode=QSIM_MODE_PER_GATE, relabel=0, prec=QSIM_PREC_NATIVE, tile=0, max_block=0):
+        o = qsim_run_opts(mode=mode, prec=prec, tile_qubits=tile, max_block=max_block, relabel_swaps=relabel)
         qsim_run_circuit(self.h, circ.ptr(), C.byref(o))
 
     def norm(self):
@@ -326,9 +326,9 @@ class State:
 class Plan:
     """Fused plan; with `state` it starts from that state's current qubit map."""
 
-    def __init__(self, circ: Circuit, dtype=QSIM_C64, prec=QSIM_PREC_NATIVE, tile=0, state=None):
+    def __init__(self, circ: Circuit, dtype=QSIM_C64, prec=QSIM_PREC_NATIVE, tile=0, state=None, max_block=0):
         self.circ = circ
-        o = qsim_run_opts(mode=QSIM_MODE_FUSED, prec=prec, tile_qubits=tile, relabel_swaps=1)
+        o = qsim_run_opts(mode=QSIM_MODE_FUSED, prec=prec, tile_qubits=tile, max_block=max_block, relabel_swaps=1)
         h = C.c_void_p()
         if state is None:
             qsim_plan_create(circ.ptr(), dtype, C.byref(o), C.byref(h))

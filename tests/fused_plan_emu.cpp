@@ -19,7 +19,7 @@
 namespace qs {
 qsim_status plan_build(const qsim_circuit *, qsim_dtype, const qsim_run_opts *, const int *, qsim_plan *);
 // the tensor-core planner is linked in but not used here
-qsim_status tc_build(int, int, const int *, const cd *, qsim_prec, std::vector<unsigned char> &, TcSpec &)
+qsim_status tc_build(int, int, const int *, const cd *, qsim_prec, std::vector<unsigned char> &, TcSpec &, int)
 {
     return QSIM_E_UNSUPPORTED;
 }

@@ -17,29 +17,32 @@ namespace qs {
 qsim_status plan_build_tc(const qsim_circuit *, const qsim_run_opts *, const int *, qsim_plan *);
 
 struct EmuBlock {
-    int k;
-    int q[6];
+    int k, kb;
+    int q[7];
     std::vector<cd> U;
 };
 static std::vector<EmuBlock> g_blocks;
 
-qsim_status tc_build(int n, int k, const int *phys, const cd *u, qsim_prec, std::vector<unsigned char> &, TcSpec &ts)
+qsim_status tc_build(int n, int k, const int *phys, const cd *u, qsim_prec, std::vector<unsigned char> &, TcSpec &ts,
+                     int kb)
 {
     EmuBlock b;
     b.k = k;
+    b.kb = kb;
     uint64_t used = 0;
     for (int j = 0; j < k; j++) {
         b.q[j] = phys[j];
         used |= 1ull << phys[j];
     }
     int kk = k;
-    for (int p = n - 1; p >= 0 && kk < 6; p--)
+    for (int p = n - 1; p >= 0 && kk < kb; p--)
         if (!((used >> p) & 1)) {
             b.q[kk++] = p;
             used |= 1ull << p;
         }
     b.U.assign(u, u + (size_t)(1 << k) * (1 << k));
-    for (int j = 0; j < 6; j++) ts.q[j] = b.q[j];
+    for (int j = 0; j < kb; j++) ts.q[j] = b.q[j];
+    ts.kb = kb;
     g_blocks.push_back(b);
     return QSIM_OK;
 }
@@ -49,15 +52,18 @@ using namespace qs;
 
 // psi_io: 2^n interleaved complex doubles in logical order (in and out).
 // start_l2p: logical -> physical map the plan starts from (NULL = identity).
-// info[0..2]: blocks, per-gate steps, qubits tc_build padded (0 when the
-// planner pads every block itself).
-extern "C" int emu_tc_run(const qsim_circuit *c, int prec, const int *start_l2p, double *psi_io, int64_t info[3])
+// max_block: the plan option (7: 7-qubit blocks). info[0..2]: blocks,
+// per-gate steps, qubits tc_build padded (0 when the planner pads every
+// block itself).
+extern "C" int emu_tc_run(const qsim_circuit *c, int prec, const int *start_l2p, int max_block, double *psi_io,
+                          int64_t info[3])
 {
     g_blocks.clear();
     qsim_run_opts o;
     memset(&o, 0, sizeof o);
     o.mode = QSIM_MODE_FUSED;
     o.prec = prec;
+    o.max_block = max_block;
     o.relabel_swaps = 1;
     qsim_plan P;
     qsim_status st = plan_build_tc(c, &o, start_l2p, &P);
@@ -75,9 +81,10 @@ extern "C" int emu_tc_run(const qsim_circuit *c, int prec, const int *start_l2p,
     for (const PlanStep &s : P.steps) {
         if (s.kind == 3) {
             const EmuBlock &B = g_blocks[s.pass];
-            padded += 6 - B.k;
+            const int kb = B.kb, KB = 1 << kb;
+            padded += kb - B.k;
             uint64_t m6 = 0;
-            for (int x = 0; x < 6; x++) m6 |= 1ull << B.q[x];
+            for (int x = 0; x < kb; x++) m6 |= 1ull << B.q[x];
             const std::vector<int32_t> &off = P.tc_pd_off[s.pass];
             const std::vector<int32_t> &pb = P.tc_pd_bit[s.pass];
             const std::vector<uint64_t> &tw = P.tc_pd_tw[s.pass];
@@ -85,15 +92,15 @@ extern "C" int emu_tc_run(const qsim_circuit *c, int prec, const int *start_l2p,
             std::vector<cd> v(D), w(D);
             for (uint64_t base = 0; base < N; base++) {
                 if (base & m6) continue;
-                for (int hi = 0; hi < 64 / D; hi++) {
+                for (int hi = 0; hi < KB / D; hi++) {
                     for (int l = 0; l < D; l++) {
                         int row = l | (hi * D);
                         uint64_t idx = base;
-                        for (int x = 0; x < 6; x++)
+                        for (int x = 0; x < kb; x++)
                             if ((row >> x) & 1) idx |= 1ull << B.q[x];
                         cd f = a[idx];
                         if (!off.empty())
-                            for (int bb = 0; bb < 6; bb++)
+                            for (int bb = 0; bb < kb; bb++)
                                 if ((row >> bb) & 1)
                                     for (int z = off[bb]; z < off[bb + 1]; z++)
                                         if ((base >> pb[z]) & 1)
@@ -107,7 +114,7 @@ extern "C" int emu_tc_run(const qsim_circuit *c, int prec, const int *start_l2p,
                     for (int l = 0; l < D; l++) {
                         int row = l | (hi * D);
                         uint64_t idx = base;
-                        for (int x = 0; x < 6; x++)
+                        for (int x = 0; x < kb; x++)
                             if ((row >> x) & 1) idx |= 1ull << B.q[x];
                         a[idx] = w[l];
                     }
@@ -156,21 +163,26 @@ extern "C" int emu_tc_run(const qsim_circuit *c, int prec, const int *start_l2p,
     return 0;
 }
 
-// Tile geometry of the pipelined tensor-core kernel for block qubits q6:
+// Tile geometry of the pipelined tensor-core kernel for block qubits qk (6,
+// or 7 for kind 3):
 // dims[0..4] lowest qubit, dims[5..9] coordinate bits, dims[10..14] box
 // extents, dims[15..19] global extents, dims[20..23] byte strides of
 // dimensions 1..4, dims[24] boxes per tile, dims[25..28] dimension-4
 // offsets of the boxes, dims[29] box bytes, dims[30] rotated low block bits,
 // dims[31] log2 of the write-back's store runs, dims[32] rotation shift, dims[33] wide,
-// dims[34..35] quarter-tile qubits, dims[36] kernel variant; tpos[13] tile
-// qubits. q6 ascending (as tc_build orders a block). kind: 0 complex64
-// whole tiles, 1 complex128 quarter tiles, 2 complex64 quarter tiles (TF32).
+// dims[34..35] quarter-tile qubits, dims[36] kernel variant, dims[37] the
+// third load-select qubit (kind 3), dims[38] block bits; tpos[13 or 14]
+// tile qubits; posL / spL 2^kb entries. qk ascending (as tc_build orders a
+// block). kind: 0 complex64 whole tiles, 1 complex128 quarter tiles, 2
+// complex64 quarter tiles (TF32), 3 complex64 7-qubit blocks (eighth tiles).
 extern "C" int emu_tc_geometry(int n, const int *q6, int kind, int64_t *dims, int *tpos, int *posL, int *posG,
                                uint64_t *spL, uint64_t *spG)
 {
+    const int kb = kind == 3 ? 7 : 6;
     TcSpec ts;
     memset(&ts, 0, sizeof ts);
-    for (int b = 0; b < 6; b++) ts.q[b] = q6[b];
+    for (int b = 0; b < kb; b++) ts.q[b] = q6[b];
+    ts.kb = kb;
     TcPipeHost H;
     qsim_status st = tc_pipe_prepare(n, ts, nullptr, H, kind);
     if (st != QSIM_OK) return (int)st;
@@ -192,8 +204,10 @@ extern "C" int emu_tc_geometry(int n, const int *q6, int kind, int64_t *dims, in
     dims[34] = A.qpos[0];
     dims[35] = A.qpos[1];
     dims[36] = A.kind;
-    for (int j = 0; j < 13; j++) tpos[j] = A.tpos[j];
-    for (int l = 0; l < 64; l++) {
+    dims[37] = A.qpos[2];
+    dims[38] = A.kb;
+    for (int j = 0; j < kb + 7; j++) tpos[j] = A.tpos[j];
+    for (int l = 0; l < (1 << kb); l++) {
         posL[l] = A.posL[l];
         spL[l] = A.spL[l];
     }
@@ -204,17 +218,18 @@ extern "C" int emu_tc_geometry(int n, const int *q6, int kind, int64_t *dims, in
     return 0;
 }
 
-// Deferred-phase tables of the pipelined kernel for block qubits q6 and
-// partner lists (off[7], pbit, tw): out = tturn[6][24] (uint64) followed by
-// gfac[128][6] (float2).
-extern "C" int emu_tc_tables(int n, const int *q6, const int32_t *off, const int32_t *pbit, const uint64_t *tw,
-                             unsigned char *out)
+// Deferred-phase tables of the pipelined kernel for kb (6 or 7) block
+// qubits q6 and partner lists (off[kb + 1], pbit, tw): out = tturn[kb][24]
+// (uint64) followed by gfac[128][kb] (float2).
+extern "C" int emu_tc_tables(int n, int kb, const int *q6, const int32_t *off, const int32_t *pbit,
+                             const uint64_t *tw, unsigned char *out)
 {
     TcSpec ts;
     memset(&ts, 0, sizeof ts);
-    for (int b = 0; b < 6; b++) ts.q[b] = q6[b];
-    std::vector<int32_t> o(off, off + 7), pb(pbit, pbit + off[6]);
-    std::vector<uint64_t> t(tw, tw + off[6]);
+    for (int b = 0; b < kb; b++) ts.q[b] = q6[b];
+    ts.kb = kb;
+    std::vector<int32_t> o(off, off + kb + 1), pb(pbit, pbit + off[kb]);
+    std::vector<uint64_t> t(tw, tw + off[kb]);
     std::vector<unsigned char> blob;
     tc_pipe_tables(n, ts, o, pb, t, blob);
     memcpy(out, blob.data(), blob.size());

@@ -63,15 +63,21 @@ def closed_form(x, n):
     return np.exp(2j * np.pi * ((x * ks) % N).astype(np.float64) / N) / np.sqrt(N)
 
 
-def test_qft27_bench_sequence_basis_closed_form(Q):
+# block sizes of the benchmark's tensor-core plans: 6-qubit blocks (five
+# passes of k_tc_pipe) and 7-qubit blocks (four passes of k_tc_pipe7)
+BLOCKS = {0: 5, 7: 4}
+
+
+@pytest.mark.parametrize("max_block", sorted(BLOCKS))
+def test_qft27_bench_sequence_basis_closed_form(Q, max_block):
     n = N_QUBITS
     N = 1 << n
     x = W.basis_index(n, 27)
     st, dev, _ = bench_state(Q, n)
     Q.qsim_set_basis(st.h, x)
     circ = Q.Circuit(n, W.qft_circuit(n))
-    p0 = Q.Plan(circ, dtype=Q.QSIM_C64, prec=Q.QSIM_PREC_BF16X3, state=st)
-    assert p0.info()["passes"] == 5
+    p0 = Q.Plan(circ, dtype=Q.QSIM_C64, prec=Q.QSIM_PREC_BF16X3, state=st, max_block=max_block)
+    assert p0.info()["passes"] == BLOCKS[max_block]
     nf = p0.execute_norm(st)
     assert abs(nf - 1.0) <= 1e-5
     y = st.download()
@@ -80,7 +86,7 @@ def test_qft27_bench_sequence_basis_closed_form(Q):
     assert np.max(np.abs(y - ref)) <= 1e-3 / np.sqrt(N)
     del ref
     # the second plan of the bench, from the bit-reversed map the first left
-    p1 = Q.Plan(circ, dtype=Q.QSIM_C64, prec=Q.QSIM_PREC_BF16X3, state=st)
+    p1 = Q.Plan(circ, dtype=Q.QSIM_C64, prec=Q.QSIM_PREC_BF16X3, state=st, max_block=max_block)
     nf = p1.execute_norm(st)
     assert abs(nf - 1.0) <= 1e-5
     assert list(st.qubit_map()) == list(range(n))
@@ -93,7 +99,24 @@ def test_qft27_bench_sequence_basis_closed_form(Q):
     del dev
 
 
-def test_qft27_bench_sequence_gaussian_vs_oracle(Q):
+_REF = {}
+
+
+def oracle_qft27(x, g):
+    """The oracle's QFT of the Gaussian input and its probabilities (all-core
+    build), computed once for both block sizes."""
+    if "ref" not in _REF:
+        oracle.use_all_cores(True)
+        try:
+            _REF["ref"] = oracle.apply_circuit(x, g)
+            _REF["pref"] = oracle.probs(_REF["ref"])
+        finally:
+            oracle.use_all_cores(False)
+    return _REF["ref"], _REF["pref"]
+
+
+@pytest.mark.parametrize("max_block", sorted(BLOCKS))
+def test_qft27_bench_sequence_gaussian_vs_oracle(Q, max_block):
     import torch
     n = N_QUBITS
     N = 1 << n
@@ -103,17 +126,13 @@ def test_qft27_bench_sequence_gaussian_vs_oracle(Q):
     host_in = torch.from_numpy(x.astype(np.complex64)).pin_memory()
     Q.qsim_upload(st.h, C.c_void_p(host_in.data_ptr()))
     circ = Q.Circuit(n, g)
-    p0 = Q.Plan(circ, dtype=Q.QSIM_C64, prec=Q.QSIM_PREC_BF16X3, state=st)
+    p0 = Q.Plan(circ, dtype=Q.QSIM_C64, prec=Q.QSIM_PREC_BF16X3, state=st, max_block=max_block)
+    assert p0.info()["passes"] == BLOCKS[max_block]
     nf = p0.execute_norm(st)
     assert abs(nf - 1.0) <= 1e-5
     y = st.download()
     probs = st.probs()
-    oracle.use_all_cores(True)
-    try:
-        ref = oracle.apply_circuit(x, g)
-        pref = oracle.probs(ref)
-    finally:
-        oracle.use_all_cores(False)
+    ref, pref = oracle_qft27(x, g)
     f = infid(y, ref)
     assert f <= 1e-6, f
     # probabilities in logical index order: the library's FP64 squares of its
@@ -128,7 +147,7 @@ def test_qft27_bench_sequence_gaussian_vs_oracle(Q):
         assert int(np.argmax(probs)) == int(top[1])
     del ref, pref, probs, mine, y64
     # second plan: QFT^2 x = x[-j mod N] exactly
-    p1 = Q.Plan(circ, dtype=Q.QSIM_C64, prec=Q.QSIM_PREC_BF16X3, state=st)
+    p1 = Q.Plan(circ, dtype=Q.QSIM_C64, prec=Q.QSIM_PREC_BF16X3, state=st, max_block=max_block)
     nf = p1.execute_norm(st)
     assert abs(nf - 1.0) <= 1e-5
     y2 = st.download()

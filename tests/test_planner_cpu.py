@@ -69,12 +69,12 @@ def run_fused(lib, n, gates, x, dt, tile=0, start=None):
     return y, list(info)
 
 
-def run(lib, n, gates, x, start=None, prec=1):
+def run(lib, n, gates, x, start=None, prec=1, max_block=0):
     c = Q.Circuit(n, gates)
     y = np.ascontiguousarray(x.astype(np.complex128)).copy()
     info = (C.c_int64 * 3)()
     sp = (C.c_int * n)(*start) if start is not None else None
-    rc = lib.emu_tc_run(c.ptr(), prec, sp, y.ctypes.data_as(C.c_void_p), info)
+    rc = lib.emu_tc_run(c.ptr(), prec, sp, max_block, y.ctypes.data_as(C.c_void_p), info)
     assert rc == 0, rc
     return y, list(info)
 
@@ -176,6 +176,37 @@ def test_tc_plan_candidate_sets_on_grids(emu, case):
     assert infid(y, ref) <= 1e-12
 
 
+@pytest.mark.parametrize("name", ["grid20", "paper16", "random14", "qft16"])
+def test_tc_plan7_matches_oracle(emu, name):
+    """Plans of 7-qubit blocks (max_block = 7, the 7-qubit kernel): the same
+    sweep with blocks of up to 7 qubits, padded to 7. Applied as the kernel
+    interprets them (deferred phases from the group index, then the
+    128 x 128 block), they must give the oracle's state, from the identity
+    map and from a permuted one, with no more blocks than 6-qubit plans."""
+    n, g, x = CASES[name]()
+    ref = oracle.apply_circuit(x, g)
+    y, info = run(emu, n, g, x, prec=2, max_block=7)
+    _, info6 = run(emu, n, g, x, prec=2)
+    assert info[0] <= info6[0]
+    assert infid(y, ref) <= 1e-12 and np.max(np.abs(y - ref)) <= 1e-12
+    start = [int(v) for v in np.random.default_rng(9).permutation(n)]
+    y, _ = run(emu, n, g, x, start=start, prec=2, max_block=7)
+    assert infid(y, ref) <= 1e-12 and np.max(np.abs(y - ref)) <= 1e-12
+
+
+def test_tc_plan7_refused_outside_its_kernel():
+    """7-qubit blocks exist for complex64 kets with BF16X3 and n >= 14 only;
+    other requests fail at plan creation (no silent fallback to 6)."""
+    Q.lib()
+    c = Q.Circuit(16, W.qft_circuit(16))
+    for dt, prec in [(Q.QSIM_C128, Q.QSIM_PREC_BF16X6), (Q.QSIM_C64, Q.QSIM_PREC_3XTF32)]:
+        with pytest.raises(Q.QsimError):
+            Q.Plan(c, dtype=dt, prec=prec, max_block=7)
+    with pytest.raises(Q.QsimError):
+        Q.Plan(Q.Circuit(13, W.qft_circuit(13)), dtype=Q.QSIM_C64, prec=Q.QSIM_PREC_BF16X3, max_block=7)
+    assert Q.Plan(c, dtype=Q.QSIM_C64, prec=Q.QSIM_PREC_BF16X3, max_block=7).info()["passes"] == 3
+
+
 def test_tc_plan_qft_block_count(emu):
     """QFT-16: controlled phases deferred into the Hadamards' blocks; the
     whole transform takes three six-qubit blocks and no per-gate step."""
@@ -203,19 +234,29 @@ def tile_base(tpos, t):
     return base
 
 
-def block_qubits(rng, seed, n):
+def block_qubits(rng, seed, n, kb=6):
     if seed % 4 == 0:
-        q6 = [int(v) for v in rng.choice(n, 6, replace=False)]
+        q6 = [int(v) for v in rng.choice(n, kb, replace=False)]
     elif seed % 4 == 1:
-        q6 = [int(v) for v in rng.choice(np.arange(0, n, 2), 6, replace=False)]
+        q6 = [int(v) for v in rng.choice(np.arange(0, n, 2), kb, replace=False)]
     elif seed % 4 == 2:
-        q6 = [n - 1 - i for i in range(6)]
+        q6 = [n - 1 - i for i in range(kb)]
     else:
-        q6 = [int(v) for v in rng.choice(min(n, 9), 6, replace=False)]
+        q6 = [int(v) for v in rng.choice(min(n, kb + 3), kb, replace=False)]
     return sorted(q6)                # tc_build orders block bits by qubit
 
 
-@pytest.mark.parametrize("kind", [0, 1, 2])
+def geometry(emu, n, qk, kind):
+    kb = 7 if kind == 3 else 6
+    dims = (C.c_int64 * 40)()
+    tpos = (C.c_int * 14)()
+    posL, posG = (C.c_int * 128)(), (C.c_int * 128)()
+    spL, spG = (C.c_uint64 * 128)(), (C.c_uint64 * 128)()
+    rc = emu.emu_tc_geometry(n, (C.c_int * kb)(*qk), kind, dims, tpos, posL, posG, spL, spG)
+    return rc, list(dims), list(tpos)[:kb + 7], list(posL)[:1 << kb], list(posG), list(spL)[:1 << kb], list(spG)
+
+
+@pytest.mark.parametrize("kind", [0, 1, 2, 3])
 @pytest.mark.parametrize("seed", range(40))
 def test_tc_pipe_tile_geometry(emu, seed, kind):
     """The pipelined tensor-core kernel loads a tile (the block's 6 qubits and
@@ -229,27 +270,26 @@ def test_tc_pipe_tile_geometry(emu, seed, kind):
     is a quarter tile: the block's two highest qubits (block bits 4, 5: the
     converter's part) are fixed by the load's index and the in-stage index
     ranks the other 11 tile qubits; for complex128 dimension 0 counts the
-    two 8-byte halves of an amplitude."""
+    two 8-byte halves of an amplitude. 7-qubit blocks (kind 3): the tile has
+    14 qubits and a load is an eighth of it, block bits 4, 5, 6 fixed by the
+    load's index (the A chunk l >> 4 the converters write)."""
     wide = kind == 1
-    quarters = kind != 0
+    split = kind != 0
+    kb = 7 if kind == 3 else 6
+    ntq = kb + 7
     rng = np.random.default_rng(seed)
-    n = int(rng.integers(13, 31))
-    q6 = block_qubits(rng, seed, n)
-    dims = (C.c_int64 * 40)()
-    tpos = (C.c_int * 13)()
-    posL, posG = (C.c_int * 64)(), (C.c_int * 128)()
-    spL, spG = (C.c_uint64 * 64)(), (C.c_uint64 * 128)()
-    rc = emu.emu_tc_geometry(n, (C.c_int * 6)(*q6), kind, dims, tpos, posL, posG, spL, spG)
+    n = int(rng.integers(ntq, 31))
+    q6 = block_qubits(rng, seed, n, kb)
+    rc, d, tp, posL, posG, spL, spG = geometry(emu, n, q6, kind)
     assert rc == 0
-    d = list(dims)
-    assert d[36] == kind
+    assert d[36] == kind and d[38] == kb
     lo, bits, box, gdim, gstr = d[0:5], d[5:10], d[10:15], d[15:20], d[20:24]
     nload, xoff, box_bytes = d[24], d[25:29], d[29]
-    rot_bits, vecw, rot_shift, dwide, qpos = d[30], d[31], d[32], d[33], d[34:36]
+    rot_bits, vecw, rot_shift, dwide = d[30], d[31], d[32], d[33]
+    qpos = d[34:36] + [d[37]]
     es = 16 if wide else 8                  # bytes per amplitude
     hpa = es // 8                           # 8-byte elements per amplitude
     assert dwide == wide and rot_shift == (3 if wide else 4)
-    tp = list(tpos)
     assert sorted(tp) == tp and set(q6) <= set(tp)
     free = [p for p in range(n) if p not in q6][:7]
     assert sorted(set(q6) | set(free)) == tp
@@ -259,26 +299,30 @@ def test_tc_pipe_tile_geometry(emu, seed, kind):
         assert strides[k] % 16 == 0 and strides[k] < 2 ** 40
     assert all(1 <= b <= 256 for b in box) and box[0] * 8 % 16 == 0
     assert gdim[0] * 8 == es << bits[0]
-    nq = 4 if quarters else 1               # loads per tile
-    stage_elems = 8192 * es // 8 // nq      # 8-byte elements per load
+    nsel = kb - 4 if split else 0           # block bits that select a load
+    nq = 1 << nsel                          # loads per tile
+    tile = 1 << ntq                         # amplitudes per tile
+    stage_elems = tile * es // 8 // nq      # 8-byte elements per load
     assert box_bytes == 8 * int(np.prod(box)) and box_bytes * nload == stage_elems * 8
-    # the quarter of (g, l): its bits at the quarter qubits, which are block
-    # bits 4, 5, i.e. the converter's part l >> 4
-    def quarter_of(g, l):
-        x = spG[g] | spL[l]
-        return ((x >> qpos[0]) & 1) | (((x >> qpos[1]) & 1) << 1)
+    assert stage_elems * 8 <= (16384 if kind in (2, 3) else 32768 if wide else 65536)
 
-    if quarters:
-        assert list(qpos) == q6[4:6]
+    # the load of (g, l): its bits at the load-select qubits, which are block
+    # bits 4.., i.e. l >> 4
+    def load_of(g, l):
+        x = spG[g] | spL[l]
+        return sum(((x >> qpos[i]) & 1) << i for i in range(nsel))
+
+    if split:
+        assert qpos[:nsel] == q6[4:kb]
         for g in range(0, 128, 9):
-            for l in range(0, 64, 5):
-                assert quarter_of(g, l) == l >> 4
-    ntiles = 1 << (n - 13)
+            for l in range(0, 1 << kb, 5):
+                assert load_of(g, l) == l >> 4
+    ntiles = 1 << (n - ntq)
     for t in {0, ntiles - 1, int(rng.integers(0, ntiles))}:
         base = tile_base(tp, t)
         assert all(not (base >> p) & 1 for p in tp)
         for q in range(nq):
-            bq = base | (((q & 1) << qpos[0]) | ((q >> 1) << qpos[1]) if quarters else 0)
+            bq = base | sum(((q >> i) & 1) << qpos[i] for i in range(nsel))
             c = [(bq >> lo[k]) & ((1 << bits[k]) - 1) for k in range(5)]
             c[0] *= hpa
             stage = np.full(stage_elems, -1, dtype=np.int64)
@@ -292,11 +336,11 @@ def test_tc_pipe_tile_geometry(emu, seed, kind):
                     off = (cc[k] + np.arange(box[k], dtype=np.int64)) * (strides[k] // 8)
                     idx = (idx[None, :] + off[:, None]).reshape(-1)
                 stage[v * (box_bytes // 8):(v + 1) * (box_bytes // 8)] = idx
-            gl = [(g, l) for g in range(128) for l in range(64) if not quarters or quarter_of(g, l) == q]
-            assert len(gl) == 8192 // nq
+            gl = [(g, l) for g in range(128) for l in range(1 << kb) if not split or load_of(g, l) == q]
+            assert len(gl) == tile // nq
             want = np.array([base + spL[l] + spG[g] for g, l in gl], dtype=np.int64)
             pos = np.array([posL[l] | posG[g] for g, l in gl])
-            assert np.array_equal(np.sort(pos), np.arange(8192 // nq))
+            assert np.array_equal(np.sort(pos), np.arange(tile // nq))
             for h in range(hpa):         # each 8-byte half of the amplitude
                 assert np.array_equal(stage[pos * hpa + h], want * hpa + h)
     # converter reads: lane (group g = 32 quarter + lane) reads block index
@@ -310,7 +354,7 @@ def test_tc_pipe_tile_geometry(emu, seed, kind):
         run += 1
     assert vecw == (0 if wide else min(run, 2))
     for quarter in range(4):
-        for part in range(4):
+        for part in range(1 << (kb - 4)):
             for i in range(16):
                 for hw in range(32 // row):
                     slots = set()
@@ -320,66 +364,69 @@ def test_tc_pipe_tile_geometry(emu, seed, kind):
                         slots.add((posG[g] | posL[l]) % row)
                     assert len(slots) == row, (q6, quarter, part, i, hw)
     w = 1 << vecw
-    for l in range(0, 64, w):
+    for l in range(0, 1 << kb, w):
         assert all(spL[l + i] == spL[l] + i for i in range(w)) and spL[l] % w == 0
     assert all(spG[g] % w == 0 for g in range(128))
 
 
-@pytest.mark.parametrize("kind", [0, 1, 2])
+@pytest.mark.parametrize("kind", [0, 1, 2, 3])
 def test_tc_pipe_geometry_always_covered(emu, kind):
     """Every block the planner can emit has a tile geometry (at most five
-    tensor dimensions plus two extra-box qubits): all 6-qubit blocks among
-    qubits 0..13 at n = 20, and random blocks at n = 13..36."""
+    tensor dimensions plus two extra-box qubits): all blocks among qubits
+    0..13 (0..14 for 7-qubit blocks) at n = 20, and random blocks at n up to
+    36."""
     import itertools
-    dims = (C.c_int64 * 40)()
-    tpos = (C.c_int * 13)()
-    posL, posG = (C.c_int * 64)(), (C.c_int * 128)()
-    spL, spG = (C.c_uint64 * 64)(), (C.c_uint64 * 128)()
-    cases = [(20, list(q)) for q in itertools.combinations(range(14), 6)]
+    kb = 7 if kind == 3 else 6
+    cases = [(20, list(q)) for q in itertools.combinations(range(kb + 8), kb)]
     rng = np.random.default_rng(7)
     for _ in range(3000):
-        n = int(rng.integers(13, 37))
-        cases.append((n, sorted(int(v) for v in rng.choice(n, 6, replace=False))))
+        n = int(rng.integers(kb + 7, 37))
+        cases.append((n, sorted(int(v) for v in rng.choice(n, kb, replace=False))))
     for n, q6 in cases:
-        rc = emu.emu_tc_geometry(n, (C.c_int * 6)(*q6), kind, dims, tpos, posL, posG, spL, spG)
+        rc = geometry(emu, n, q6, kind)[0]
         assert rc == 0, (n, q6, kind)
 
 
+@pytest.mark.parametrize("kb", [6, 7])
 @pytest.mark.parametrize("seed", range(12))
-def test_tc_pipe_phase_tables(emu, seed):
-    """Deferred phases in the pipelined kernel: block bit b of the amplitude
+def test_tc_pipe_phase_tables(emu, seed, kb):
+    """Deferred phases in the pipelined kernels: block bit b of the amplitude
     with index x is multiplied by exp(2 pi i T_b(x)), T_b(x) = sum of the
     turns of b's partners whose bit is set in x. The kernel forms it as
     (tile factor from tturn[b][tile-index bits]) x gfac[g][b]; for random
-    partner lists and amplitudes that product must equal the direct sum."""
+    partner lists and amplitudes that product must equal the direct sum
+    (kb = 6 or 7 block bits; the tile is the block and the 7 lowest other
+    qubits)."""
     rng = np.random.default_rng(100 + seed)
-    n = int(rng.integers(13, 29))
-    q6 = [int(v) for v in rng.choice(n, 6, replace=False)]
+    ntq = kb + 7
+    n = int(rng.integers(ntq, 29))
+    q6 = [int(v) for v in rng.choice(n, kb, replace=False)]
     outside = [p for p in range(n) if p not in q6]
     off, pbit, tw = [0], [], []
-    for b in range(6):
+    for b in range(kb):
         k = int(rng.integers(0, min(12, len(outside)) + 1))
         for p in rng.choice(outside, k, replace=False):
             pbit.append(int(p))
             tw.append(int(rng.integers(0, 2 ** 63)) * 2 + int(rng.integers(0, 2)))
         off.append(len(pbit))
-    out = np.zeros(6 * 24 * 8 + 128 * 6 * 8, dtype=np.uint8)
-    rc = emu.emu_tc_tables(n, (C.c_int * 6)(*q6), (C.c_int32 * 7)(*off), (C.c_int32 * max(1, len(pbit)))(*pbit),
-                           (C.c_uint64 * max(1, len(tw)))(*tw), out.ctypes.data_as(C.c_void_p))
+    out = np.zeros(kb * 24 * 8 + 128 * kb * 8, dtype=np.uint8)
+    rc = emu.emu_tc_tables(n, kb, (C.c_int * kb)(*q6), (C.c_int32 * (kb + 1))(*off),
+                           (C.c_int32 * max(1, len(pbit)))(*pbit), (C.c_uint64 * max(1, len(tw)))(*tw),
+                           out.ctypes.data_as(C.c_void_p))
     assert rc == out.size
-    tturn = out[:6 * 24 * 8].view(np.uint64).reshape(6, 24)
-    gfac = out[6 * 24 * 8:].view(np.float32).reshape(128, 6, 2)
+    tturn = out[:kb * 24 * 8].view(np.uint64).reshape(kb, 24)
+    gfac = out[kb * 24 * 8:].view(np.float32).reshape(128, kb, 2)
     free = [p for p in range(n) if p not in q6][:7]
     tile = sorted(q6 + free)
     tbits = [p for p in range(n) if p not in tile]
     for _ in range(20):
-        t = int(rng.integers(0, 1 << (n - 13)))
+        t = int(rng.integers(0, 1 << (n - ntq)))
         gi = int(rng.integers(0, 128))
-        x = sum(1 << tbits[i] for i in range(n - 13) if (t >> i) & 1)
+        x = sum(1 << tbits[i] for i in range(n - ntq) if (t >> i) & 1)
         x |= sum(1 << free[f] for f in range(7) if (gi >> f) & 1)
-        for b in range(6):
+        for b in range(kb):
             direct = sum(tw[e] for e in range(off[b], off[b + 1]) if (x >> pbit[e]) & 1) % 2 ** 64
-            tt = sum(int(tturn[b, i]) for i in range(n - 13) if (t >> i) & 1) % 2 ** 64
+            tt = sum(int(tturn[b, i]) for i in range(n - ntq) if (t >> i) & 1) % 2 ** 64
             f = np.exp(2j * np.pi * tt / 2 ** 64) * complex(gfac[gi, b, 0], gfac[gi, b, 1])
             assert abs(f - np.exp(2j * np.pi * direct / 2 ** 64)) < 1e-6
 
@@ -388,22 +435,24 @@ def test_tc_pipe_phase_tables(emu, seed):
 # GPU): the per-pass / per-block choice among candidate high-qubit sets gives
 # these counts; first-fit tiles give grid20 9 / 11, paper20 6 / 9, grid30
 # 17 / 21 passes (complex64 / complex128) and 30 tensor-core blocks on grid30.
+# The last column is 7-qubit blocks (max_block = 7).
 # A regression that turns the choice off, or plans more passes, fails here.
 PASS_COUNTS = {
-    "grid20": (lambda: (20, W.grid_rcs_circuit(4, 5, 10, seed=1)), 7, 10, 15),
-    "paper20": (lambda: (20, W.paper_random_circuit(4, 5, 9, seed=2)), 6, 7, 15),
-    "grid30": (lambda: (30, W.grid_rcs_circuit(5, 6, 10, seed=0)), 14, 17, 22),
-    "paper30": (lambda: (30, W.paper_random_circuit(5, 6, 10, seed=0)), 13, 15, 24),
-    "qft27": (lambda: (27, W.qft_circuit(27)), 3, 4, 5),
+    "grid20": (lambda: (20, W.grid_rcs_circuit(4, 5, 10, seed=1)), 7, 10, 15, 11),
+    "paper20": (lambda: (20, W.paper_random_circuit(4, 5, 9, seed=2)), 6, 7, 15, 11),
+    "grid30": (lambda: (30, W.grid_rcs_circuit(5, 6, 10, seed=0)), 14, 17, 22, 20),
+    "paper30": (lambda: (30, W.paper_random_circuit(5, 6, 10, seed=0)), 13, 15, 24, 22),
+    "qft27": (lambda: (27, W.qft_circuit(27)), 3, 4, 5, 4),
 }
 
 
 @pytest.mark.parametrize("name", sorted(PASS_COUNTS))
 def test_plan_pass_counts(name):
-    mk, c64, c128, tc = PASS_COUNTS[name]
+    mk, c64, c128, tc, tc7 = PASS_COUNTS[name]
     n, g = mk()
     Q.lib()
     circ = Q.Circuit(n, g)
     assert Q.Plan(circ, dtype=Q.QSIM_C64).info()["passes"] == c64
     assert Q.Plan(circ, dtype=Q.QSIM_C128).info()["passes"] == c128
     assert Q.Plan(circ, dtype=Q.QSIM_C64, prec=Q.QSIM_PREC_BF16X3).info()["passes"] == tc
+    assert Q.Plan(circ, dtype=Q.QSIM_C64, prec=Q.QSIM_PREC_BF16X3, max_block=7).info()["passes"] == tc7

@@ -246,3 +246,147 @@ def test_shared_stage_barriers_race():
     with pytest.raises(AssertionError, match="read before the load landed"):
         for seed in range(600):
             run(True, 1 + seed % 7, False, seed, nbar=3)
+
+
+def run7(J, pd, seed, nstage=5, nbar=8, nslot_e=4):
+    """One random interleaving of the 7-qubit kernel (k_tc_pipe7.cu): load m =
+    8 j + e (eighth e of tile j) into stage m mod S after the free barrier of
+    load m - S, signalling full[m mod B]; converter part p reads eighths p
+    and p + 4 of each tile, and writes A chunk c once afree[c] shows that the
+    MMAs of the previous tile's second half have read it; the MMA issuer
+    takes output half h of tile j into slot h once the write-back has read
+    slot h of tile j - 1 (accf[h]), waiting for aready[c] per chunk in the
+    first half and arriving at afree[c] after each chunk of the second; the
+    write-back reads slot 0, then slot 1. With deferred phases the producer
+    writes tile j's factors into slot j mod 4 before its second arrival on
+    full[0], and the converters of tile j read that slot."""
+    rng = random.Random(seed)
+    NS, NB = nstage, nbar
+    full = [Bar(2 if pd else 1) for _ in range(NB)]
+    sfree = [Bar(1) for _ in range(NB)]       # a part's four warps act as one arrival
+    aready = [Bar(1) for _ in range(8)]
+    afree = [Bar(1) for _ in range(8)]
+    mma = [Bar(1) for _ in range(2)]
+    accf = [Bar(1) for _ in range(2)]
+    stage = [None] * NS
+    read = set()
+    inflight = []
+    slot = [None, None]
+    achunk = [None] * 8                        # (tile, read by both halves)
+    sE = [None] * nslot_e
+    written = []
+
+    def producer():
+        m = 0
+        for j in range(J):
+            for e in range(8):
+                s = m % NS
+                if m >= NS:
+                    r = m - NS
+                    while not sfree[r % NB].done((r // NB) & 1):
+                        yield
+                    assert r in read, ("stage reloaded before it was read", m, r)
+                assert stage[s] is None or stage[s][0] in read, ("stage overwritten", m)
+                stage[s] = (m, False)
+                full[m % NB].expect_tx(1)
+                inflight.append((s, m, m % NB))
+                if pd:
+                    if e == 0:
+                        sE[j % nslot_e] = j
+                    yield
+                    full[m % NB].arrive()
+                m += 1
+                yield
+
+    def tma():
+        while True:
+            if inflight and rng.random() < 0.5:
+                k = rng.randrange(len(inflight)) if rng.random() < 0.2 else 0
+                s, m, b = inflight.pop(k)
+                assert stage[s][0] == m
+                stage[s] = (m, True)
+                full[b].complete_tx(1)
+            yield
+
+    def converter(p):
+        for j in range(J):
+            for hh in range(2):
+                c = p + 4 * hh
+                m = 8 * j + c
+                while not full[m % NB].done((m // NB) & 1):
+                    yield
+                assert stage[m % NS] == (m, True), ("read before the load landed", j, c)
+                if pd:
+                    assert sE[j % nslot_e] == j, ("tile factors overwritten", j, c)
+                read.add(m)
+                sfree[m % NB].arrive()
+                yield
+                if j >= 1:
+                    while not afree[c].done((j - 1) & 1):
+                        yield
+                assert achunk[c] is None or achunk[c] == (j - 1, True), ("A chunk rewritten before both halves read it",
+                                                                         j, c, achunk[c])
+                achunk[c] = (j, False)
+                yield
+                aready[c].arrive()
+
+    def mma_issuer():
+        for j in range(J):
+            for h in range(2):
+                if j >= 1:
+                    while not accf[h].done((j - 1) & 1):
+                        yield
+                assert slot[h] is None, "slot still being written back"
+                for c in range(8):
+                    if h == 0:
+                        while not aready[c].done(j & 1):
+                            yield
+                    assert achunk[c] == (j, False), ("MMA read another tile's A chunk", j, h, c, achunk[c])
+                    yield
+                    if h == 1:
+                        achunk[c] = (j, True)
+                        afree[c].arrive()
+                slot[h] = j
+                mma[h].arrive()
+
+    def write_back():
+        for j in range(J):
+            for h in range(2):
+                while not mma[h].done(j & 1):
+                    yield
+                assert slot[h] == j
+                yield
+                slot[h] = None
+                written.append((j, h))
+                accf[h].arrive()
+
+    alive = [producer(), mma_issuer(), write_back()] + [converter(p) for p in range(4)]
+    t = tma()
+    steps = 0
+    while alive:
+        steps += 1
+        assert steps < 400000, "no progress (deadlock)"
+        if rng.random() < 0.3:
+            next(t)
+        a = rng.choice(alive)
+        try:
+            next(a)
+        except StopIteration:
+            alive.remove(a)
+    assert written == [(j, h) for j in range(J) for h in range(2)] and not inflight
+
+
+@pytest.mark.parametrize("pd", [False, True])
+def test_protocol7_random_interleavings(pd):
+    """The 7-qubit kernel's protocol: five stages on eight barrier pairs (one
+    per eighth), per-chunk A barriers and two output slots."""
+    for seed in range(500):
+        run7(1 + seed % 6, pd, seed)
+
+
+def test_protocol7_needs_a_pair_per_eighth():
+    """With fewer barrier pairs than stages (five stages, four pairs) some
+    interleaving of the 7-qubit kernel's ring fails."""
+    with pytest.raises(AssertionError):
+        for seed in range(500):
+            run7(1 + seed % 6, False, seed, nbar=4)
