@@ -1,17 +1,20 @@
-"""Benchmark: exact QFT on 27 qubits (complex64 ket, fused passes) through
-the C-ABI library, in amplitude-gate updates per second.
+"""Benchmark: exact QFT on 27 qubits (complex64 ket) through the C-ABI
+library, in amplitude-gate updates per second.
 
 One step = the whole hot path over one ket: the 391-gate QFT (H, controlled
-phases, qubit-reversal swaps) applied to a seeded Gaussian 27-qubit ket by
-the fused SIMT passes, followed by the FP64 norm reduction of the result.
-updates/s = gates x 2^n / step time. The ket (1 GiB) is larger than L2, so
-no flush is needed between steps.
+phases, qubit-reversal swaps) applied to a seeded Gaussian 27-qubit ket as
+fused dense blocks on the tensor cores (BF16x3 split, FP32 accumulation;
+blocks of up to 7 qubits by default, --block 6 for the 6-qubit kernel),
+followed by the FP64 norm of the result taken by the last block's
+write-back. updates/s = gates x 2^n / step time. The ket (1 GiB) is larger
+than L2, so no flush is needed between steps.
 
 Also reported on the same box: the plain per-gate FP64 (complex128) path on
-the same circuit (the in-run GPU baseline), the 30-qubit 5x6 grid random
-circuit (10 layers) on the fused complex64 path, the roofline of the fused
-pass kernel against the measured HBM copy bandwidth, the end-to-end number
-with host buffers, and the FP64 CPU oracle on a bounded sample.
+the same circuit (the in-run GPU baseline), fused SIMT and FP64 passes, the
+other block sizes and splits, the 30-qubit 5x6 grid random circuit (10
+layers), the roofline of the dominant kernel against the measured HBM copy
+bandwidth, the end-to-end number with host buffers, and the FP64 CPU oracle
+on a bounded sample.
 
 --impl reference times the CPU oracle instead (the oracle is the reference
 for this build: there is no reference implementation to install).
@@ -41,10 +44,12 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip the per-gate FP64, grid and CPU legs")
+    ap.add_argument("--block", type=int, default=7, choices=[6, 7],
+                    help="largest tensor-core block of the timed plans (7: the 7-qubit kernel, 6: k_tc_pipe)")
     ap.add_argument("--workload", default="qft27",
-                    help="qft27 (default: the 27-qubit QFT on tensor-core blocks), {qft,grid}<n>_{tc,tf32,tc128,simt} "
-                         "(one circuit on complex64 BF16x3 or 3xTF32, or complex128, tensor-core blocks, or fused "
-                         "SIMT passes; "
+                    help="qft27 (default: the 27-qubit QFT on tensor-core blocks), "
+                         "{qft,grid}<n>_{tc,tc7,tf32,tc128,simt} (one circuit on complex64 BF16x3 6- or 7-qubit, "
+                         "or 3xTF32, or complex128, tensor-core blocks, or fused SIMT passes; "
                          "gates27: the per-gate kernels on a 27-qubit complex64 ket, low and high qubits; "
                          "profiling workloads), or appendix_a (the paper's fidelity-model validation in full)")
     return ap.parse_args()
@@ -192,11 +197,12 @@ def oracle_sample(n_gates=16, n=N_QUBITS, seed=0, all_cores=False):
     return len(g) * (1 << n) / dt, dt, len(g), threads
 
 
-def main_config(world, blocks=5):
+def main_config(world, blocks=4, block=7):
     """The workload both arms report (the 27-qubit QFT on a Gaussian
     complex64 ket, on tensor-core blocks in this implementation)."""
     return {"workload": "qft27_gaussian_c64_tc_bf16x3", "n_qubits": N_QUBITS, "gates": 391, "blocks": blocks,
-            "path": "fused <=6-qubit blocks on tensor cores (BF16x3 split, FP32 accumulation)",
+            "max_block": block,
+            "path": f"fused <={block}-qubit blocks on tensor cores (BF16x3 split, FP32 accumulation)",
             "ket_bytes": 8 << N_QUBITS, "l2": "ket (1 GiB) larger than L2",
             "parallelism": "replicas" if world > 1 else "single"}
 
@@ -294,11 +300,14 @@ def main():
     # The QFT leaves the ket bit-reversed (its swaps are relabels, Table I);
     # a second plan starts from that layout, so consecutive steps alternate
     # between the two plans and no step moves data for the relabel.
-    # Fused blocks of <= 6 qubits on the tensor cores (BF16x3 split, FP32
-    # accumulation in TMEM, controlled phases deferred into per-group phases).
-    plans = [Q.Plan(circ, dtype=Q.QSIM_C64, prec=Q.QSIM_PREC_BF16X3, state=st)]
+    # Fused blocks of <= 7 (or 6) qubits on the tensor cores (BF16x3 split,
+    # FP32 accumulation in TMEM, controlled phases deferred into per-group
+    # phases).
+    mb = 7 if args.block == 7 else 0
+    kernel = "k_tc_pipe7" if args.block == 7 else "k_tc_pipe"
+    plans = [Q.Plan(circ, dtype=Q.QSIM_C64, prec=Q.QSIM_PREC_BF16X3, state=st, max_block=mb)]
     plans[0].execute(st)
-    plans.append(Q.Plan(circ, dtype=Q.QSIM_C64, prec=Q.QSIM_PREC_BF16X3, state=st))
+    plans.append(Q.Plan(circ, dtype=Q.QSIM_C64, prec=Q.QSIM_PREC_BF16X3, state=st, max_block=mb))
     plans[1].execute(st)
     info = plans[0].info()
     nrm = C.c_double()
@@ -417,10 +426,10 @@ def main():
         "metric": "amplitude-gate updates/s", "value": value, "unit": "updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": main_config(world, npass),
+        "config": main_config(world, npass, args.block),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic_from_profiles("k_tc_pipe"),
-                     "kernel": "k_tc_pipe", "alg_bytes_per_launch": alg_bytes,
+                     "frac": achieved / peak, "traffic": traffic_from_profiles(kernel),
+                     "kernel": kernel, "alg_bytes_per_launch": alg_bytes,
                      "launch_ms": launch_ms, "peak_source": "measured hbm_gbs" if peaks else "fallback"},
         "e2e": {"value": e2e_val, "unit": "updates/s", "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 8 * N,
                 "ms_per_step": e2e_ms,
@@ -619,11 +628,14 @@ def run_grid_tc(args):
     fam = "qft" if args.workload.startswith("qft") else "grid"
     n = int(args.workload[len(fam):].split("_")[0])
     simt = args.workload.endswith("_simt")
+    k7 = args.workload.endswith("_tc7")
     c128 = args.workload.endswith("_tc128")
     tf32 = args.workload.endswith("_tf32")
     dt, es = (Q.QSIM_C128, 16) if c128 else (Q.QSIM_C64, 8)
     prec_kw = {} if simt else {"prec": Q.QSIM_PREC_BF16X6 if c128 else Q.QSIM_PREC_3XTF32 if tf32
                                else Q.QSIM_PREC_BF16X3}
+    if k7:
+        prec_kw["max_block"] = 7
     if fam == "grid":
         rows, cols = W.grid_shape(n)
         g = W.grid_rcs_circuit(rows, cols, 10, seed=0, n=n)
@@ -659,9 +671,11 @@ def run_grid_tc(args):
                       "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                       "data": "synthetic",
                       "config": {"workload": f"{fam}{n}_" + ("c128_tc_bf16x6" if c128 else "c64_fused_simt" if simt
-                                                             else "c64_tc_3xtf32" if tf32 else "c64_tc_bf16x3"),
+                                                             else "c64_tc_3xtf32" if tf32 else
+                                                             "c64_tc_bf16x3_k7" if k7 else "c64_tc_bf16x3"),
                                  "n_qubits": n, "gates": len(g), "launches_per_step": nb},
-                      "roofline": {"bound": "hbm", "kernel": "k_fused_pass" if simt else "k_tc_pipe",
+                      "roofline": {"bound": "hbm", "kernel": "k_fused_pass" if simt else
+                                   "k_tc_pipe7" if k7 else "k_tc_pipe",
                                    "achieved": 2 * es * N / (ms / nb * 1e-3) / 1e9}}))
 
 
@@ -786,14 +800,15 @@ def extra_legs(Q, W, C, torch, circ, x, n, ng, plans):
     ssim.close()
     # larger QFTs on tensor-core blocks (complex64, 8 GiB and 64 GiB kets,
     # basis-state input prepared on the device)
-    for nn in (30, 33):
+    for nn, mbk in ((30, 0), (30, 7), (33, 0)):
+        key = f"qft{nn}_c64_tc_bf16x3" + ("_k7" if mbk else "")
         try:
             cc = Q.Circuit(nn, W.qft_circuit(nn))
             sb = Q.State(nn, Q.QSIM_C64)
             Q.qsim_set_basis(sb.h, 1)
-            bps = [Q.Plan(cc, dtype=Q.QSIM_C64, prec=Q.QSIM_PREC_BF16X3, state=sb)]
+            bps = [Q.Plan(cc, dtype=Q.QSIM_C64, prec=Q.QSIM_PREC_BF16X3, state=sb, max_block=mbk)]
             bps[0].execute(sb)
-            bps.append(Q.Plan(cc, dtype=Q.QSIM_C64, prec=Q.QSIM_PREC_BF16X3, state=sb))
+            bps.append(Q.Plan(cc, dtype=Q.QSIM_C64, prec=Q.QSIM_PREC_BF16X3, state=sb, max_block=mbk))
             bps[1].execute(sb)
             reps = 6 if nn == 30 else 2
             a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -810,14 +825,15 @@ def extra_legs(Q, W, C, torch, circ, x, n, ng, plans):
             nrm = C.c_double()
             Q.qsim_norm(sb.h, C.byref(nrm))
             ngg = len(cc.gates)
-            out[f"qft{nn}_c64_tc_bf16x3"] = {
-                "updates_per_s": ngg * (1 << nn) / (ms * 1e-3), "ms": ms, "blocks": nb_, "kernel": "k_tc_pipe",
+            out[key] = {
+                "updates_per_s": ngg * (1 << nn) / (ms * 1e-3), "ms": ms, "blocks": nb_,
+                "kernel": "k_tc_pipe7" if mbk else "k_tc_pipe",
                 "hbm_gbs_per_block": 2 * 8 * (1 << nn) / (ms / nb_ * 1e-3) / 1e9,
                 "ket_gib": 8 * (1 << nn) / 2 ** 30, "norm": nrm.value}
             sb.close()
             del bps
         except Exception as e:   # e.g. not enough device memory on a smaller part
-            out[f"qft{nn}_c64_tc_bf16x3"] = {"error": str(e)[:200]}
+            out[key] = {"error": str(e)[:200]}
     # the same QFT on tensor-core blocks (deferred phases as per-group
     # pre-diagonals), agreement with the fused SIMT result
     peaks = {}
@@ -827,10 +843,11 @@ def extra_legs(Q, W, C, torch, circ, x, n, ng, plans):
     sref = Q.State(n, Q.QSIM_C64)
     sref.upload(x)
     Q.Plan(circ, dtype=Q.QSIM_C64, state=sref).execute(sref)
-    for prec, name in ((Q.QSIM_PREC_BF16X3, "bf16x3"), (Q.QSIM_PREC_3XTF32, "3xtf32")):
+    for prec, name, mbk in ((Q.QSIM_PREC_BF16X3, "bf16x3", 0), (Q.QSIM_PREC_BF16X3, "bf16x3_k7", 7),
+                            (Q.QSIM_PREC_3XTF32, "3xtf32", 0)):
         stc = Q.State(n, Q.QSIM_C64)
         stc.upload(x)
-        tp = Q.Plan(circ, dtype=Q.QSIM_C64, prec=prec, state=stc)
+        tp = Q.Plan(circ, dtype=Q.QSIM_C64, prec=prec, state=stc, max_block=mbk)
         tp.execute(stc)
         ip = (C.c_double * 2)()
         na, nb = C.c_double(), C.c_double()
@@ -838,9 +855,9 @@ def extra_legs(Q, W, C, torch, circ, x, n, ng, plans):
         Q.qsim_norm(sref.h, C.byref(na))
         Q.qsim_norm(stc.h, C.byref(nb))
         # timing: alternate the two layouts as in the main leg
-        tps = [Q.Plan(circ, dtype=Q.QSIM_C64, prec=prec, state=stc)]
+        tps = [Q.Plan(circ, dtype=Q.QSIM_C64, prec=prec, state=stc, max_block=mbk)]
         tps[0].execute(stc)
-        tps.append(Q.Plan(circ, dtype=Q.QSIM_C64, prec=prec, state=stc))
+        tps.append(Q.Plan(circ, dtype=Q.QSIM_C64, prec=prec, state=stc, max_block=mbk))
         tps[1].execute(stc)
         a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         Q.qsim_synchronize(stc.h)
@@ -854,8 +871,9 @@ def extra_legs(Q, W, C, torch, circ, x, n, ng, plans):
         ms = a.elapsed_time(z) / 6
         nbk = tps[0].info()["passes"]
         achieved = 2 * 8 * N / (ms / nbk * 1e-3) / 1e9
+        kn = {"bf16x3": "k_tc_pipe", "bf16x3_k7": "k_tc_pipe7", "3xtf32": "k_tc_pipe (3xTF32)"}[name]
         out[f"qft27_c64_tc_{name}"] = {"updates_per_s": ng * N / (ms * 1e-3), "ms": ms, "blocks": nbk,
-                                       "kernel": "k_tc_pipe" if name == "bf16x3" else "k_tc_pipe (3xTF32)", "hbm_gbs_per_block": achieved,
+                                       "kernel": kn, "hbm_gbs_per_block": achieved,
                                        "frac_of_hbm": achieved / peaks.get("hbm_gbs", 6800.0),
                                        "infidelity_vs_simt": 1.0 - (ip[0] ** 2 + ip[1] ** 2) / (na.value * nb.value)}
         stc.close()
@@ -880,8 +898,9 @@ def extra_legs(Q, W, C, torch, circ, x, n, ng, plans):
     pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(pp):
         peaks = json.load(open(pp))
-    for prec, name in ((Q.QSIM_PREC_BF16X3, "bf16x3"), (Q.QSIM_PREC_3XTF32, "3xtf32")):
-        tp = Q.Plan(gc, dtype=Q.QSIM_C64, prec=prec)
+    for prec, name, mbk in ((Q.QSIM_PREC_BF16X3, "bf16x3", 0), (Q.QSIM_PREC_BF16X3, "bf16x3_k7", 7),
+                            (Q.QSIM_PREC_3XTF32, "3xtf32", 0)):
+        tp = Q.Plan(gc, dtype=Q.QSIM_C64, prec=prec, max_block=mbk)
         st2 = Q.State(30, Q.QSIM_C64)
         ms = time_plan(Q, C, tp, st2, 3)
         nb = tp.info()["passes"]
@@ -898,7 +917,8 @@ def extra_legs(Q, W, C, torch, circ, x, n, ng, plans):
         Q.qsim_norm(st2.h, C.byref(nb2))
         out[f"grid30_c64_tc_{name}"] = {
             "updates_per_s": len(g) * (1 << 30) / (ms * 1e-3), "ms": ms, "blocks": nb,
-            "kernel": "k_tc_pipe" if name == "bf16x3" else "k_tc_pipe (3xTF32)", "hbm_gbs_per_block": achieved,
+            "kernel": {"bf16x3": "k_tc_pipe", "bf16x3_k7": "k_tc_pipe7", "3xtf32": "k_tc_pipe (3xTF32)"}[name],
+            "hbm_gbs_per_block": achieved,
             "frac_of_hbm": achieved / peaks.get("hbm_gbs", 6800.0),
             "infidelity_vs_simt": 1.0 - (ip[0] ** 2 + ip[1] ** 2) / (na.value * nb2.value)}
         st2.close()
