@@ -4,7 +4,7 @@ library, in amplitude-gate updates per second.
 One step = the whole hot path over one ket: the 391-gate QFT (H, controlled
 phases, qubit-reversal swaps) applied to a seeded Gaussian 27-qubit ket as
 fused dense blocks on the tensor cores (BF16x3 split, FP32 accumulation;
-blocks of up to 7 qubits by default, --block 6 for the 6-qubit kernel),
+blocks of up to 6 qubits by default, --block 7 for the 7-qubit kernel),
 followed by the FP64 norm of the result taken by the last block's
 write-back. updates/s = gates x 2^n / step time. The ket (1 GiB) is larger
 than L2, so no flush is needed between steps.
@@ -44,8 +44,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip the per-gate FP64, grid and CPU legs")
-    ap.add_argument("--block", type=int, default=7, choices=[6, 7],
-                    help="largest tensor-core block of the timed plans (7: the 7-qubit kernel, 6: k_tc_pipe)")
+    ap.add_argument("--block", type=int, default=6, choices=[6, 7],
+                    help="largest tensor-core block of the timed plans (6: k_tc_pipe, 7: the 7-qubit kernel)")
     ap.add_argument("--workload", default="qft27",
                     help="qft27 (default: the 27-qubit QFT on tensor-core blocks), "
                          "{qft,grid}<n>_{tc,tc7,tf32,tc128,simt} (one circuit on complex64 BF16x3 6- or 7-qubit, "
@@ -197,7 +197,7 @@ def oracle_sample(n_gates=16, n=N_QUBITS, seed=0, all_cores=False):
     return len(g) * (1 << n) / dt, dt, len(g), threads
 
 
-def main_config(world, blocks=4, block=7):
+def main_config(world, blocks=5, block=6):
     """The workload both arms report (the 27-qubit QFT on a Gaussian
     complex64 ket, on tensor-core blocks in this implementation)."""
     return {"workload": "qft27_gaussian_c64_tc_bf16x3", "n_qubits": N_QUBITS, "gates": 391, "blocks": blocks,
@@ -300,7 +300,7 @@ def main():
     # The QFT leaves the ket bit-reversed (its swaps are relabels, Table I);
     # a second plan starts from that layout, so consecutive steps alternate
     # between the two plans and no step moves data for the relabel.
-    # Fused blocks of <= 7 (or 6) qubits on the tensor cores (BF16x3 split,
+    # Fused blocks of <= 6 (or 7) qubits on the tensor cores (BF16x3 split,
     # FP32 accumulation in TMEM, controlled phases deferred into per-group
     # phases).
     mb = 7 if args.block == 7 else 0
