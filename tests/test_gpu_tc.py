@@ -174,17 +174,20 @@ def test_tc_qft27_full_size_sampled(Q, prec):
     assert num / den <= 1e-6
 
 
-def test_tc_qft30_basis_closed_form(Q):
-    """30-qubit QFT (8 GiB complex64 ket) on tensor-core blocks, BF16x3, from a
-    basis state |x>: Eq. (dft) gives every output in closed form,
-    y_k = 2^(-n/2) exp(2 pi i x k / 2^n). Checked on 4096 sampled outputs
-    (relative squared error <= 1e-6) and on the FP64 norm."""
+@pytest.mark.parametrize("max_block", [0, 7])
+def test_tc_qft30_basis_closed_form(Q, max_block):
+    """30-qubit QFT (8 GiB complex64 ket) on tensor-core blocks, BF16x3, 6- and
+    7-qubit blocks, from a basis state |x>: Eq. (dft) gives every output in
+    closed form, y_k = 2^(-n/2) exp(2 pi i x k / 2^n). Checked on the whole
+    state (infidelity <= 1e-6, the closed form computed chunk by chunk), on
+    4096 sampled outputs (relative squared error <= 1e-6) and on the FP64
+    norm."""
     n = 30
     N = 1 << n
     x = 0x2A5F3B1D % N
     st = Q.State(n, 0)
     Q.qsim_set_basis(st.h, x)
-    st.run(Q.Circuit(n, W.qft_circuit(n)), mode=1, prec=2, relabel=1)
+    st.run(Q.Circuit(n, W.qft_circuit(n)), mode=1, prec=2, relabel=1, max_block=max_block)
     assert abs(st.norm() - 1.0) < 1e-5
     y = st.download()
     st.close()
@@ -193,6 +196,14 @@ def test_tc_qft30_basis_closed_form(Q):
     ref = np.exp(2j * np.pi * ((x * ks) % N).astype(np.float64) / N) / np.sqrt(N)
     got = y[ks].astype(np.complex128)
     assert np.sum(np.abs(got - ref) ** 2) / np.sum(np.abs(ref) ** 2) <= 1e-6
+    ip, ny = 0j, 0.0
+    for a in range(0, N, 1 << 24):
+        k = np.arange(a, a + (1 << 24), dtype=np.int64)
+        rr = np.exp(2j * np.pi * ((x * k) % N).astype(np.float64) / N) / np.sqrt(N)
+        yy = y[a:a + (1 << 24)].astype(np.complex128)
+        ip += np.vdot(yy, rr)
+        ny += float(np.vdot(yy, yy).real)
+    assert 1.0 - abs(ip) ** 2 / ny <= 1e-6
 
 
 @pytest.mark.parametrize("which", ["qft16", "grid20", "simt_qft16"])
