@@ -169,7 +169,8 @@ __global__ void __launch_bounds__(kPThreads, 1)
     unsigned char *smb = (unsigned char *)(((uintptr_t)sm_dyn + 1023) & ~(uintptr_t)1023);
     unsigned char *Us = smb;                              // U operand (N x K): kParts parts of 32 KB
     unsigned char *St = smb + Cfg::kU;                    // raw stages
-    __shared__ __align__(8) uint64_t bar_full[8], bar_sfree[8], bar_aready[2], bar_mma[2], bar_accf[2];
+    __shared__ __align__(8) uint64_t bar_full[8], bar_sfree[8], bar_aready[2], bar_mma[2], bar_accf[2], bar_lofree,
+        bar_loready, bar_fin;
     static_assert(Cfg::kNBar <= 8 && Cfg::kNBar >= Cfg::kNStage, "barrier pairs per stage ring");
     __shared__ uint32_t s_tmem;
     __shared__ int s_abort;
@@ -203,6 +204,11 @@ __global__ void __launch_bounds__(kPThreads, 1)
             // a complex128 quarter tile is read by the four warps it belongs to
             mbar_init(smem_addr(&bar_sfree[s]), QT ? kPConv / 4 : kPConv);
         }
+        // 3xTF32: the lo half of the one A operand has its own handshake
+        // (lo free after the tile's first product, lo ready from the converters)
+        mbar_init(smem_addr(&bar_lofree), 1);
+        mbar_init(smem_addr(&bar_loready), kPConv);
+        mbar_init(smem_addr(&bar_fin), 1);
         for (int b = 0; b < 2; b++) {
             mbar_init(smem_addr(&bar_aready[b]), kPConv);
             mbar_init(smem_addr(&bar_mma[b]), 1);
@@ -346,8 +352,58 @@ __global__ void __launch_bounds__(kPThreads, 1)
                                    ((uint32_t)(128 >> 4) << 24);
             // U part: 8-row groups of core matrices SBO bytes apart (K = 128 elements per row)
             const uint32_t SBO = TF ? 4096u : 2048u;
+            if constexpr (TF) {
+                // a_lo u_hi first, then a commit that lets the converters write the
+                // next tile's lo parts while a_hi u_hi and a_hi u_lo run; A hi at +0,
+                // lo at +128 columns
+                const uint32_t a0 = tmem + 256u, u0 = smem_addr(Us);
+                bool any = false;
+                for (uint64_t j = 0; j < J && !*abort_flag; j++) {
+                    const int b = (int)(j & 1);
+                    if (j >= 2 &&
+                        !mbar_wait_or_abort(smem_addr(&bar_accf[b]), (uint32_t)(((j - 2) >> 1) & 1), abort_flag)) {
+                        give_up();
+                        break;
+                    }
+                    if (!mbar_wait_or_abort(smem_addr(&bar_loready), (uint32_t)(j & 1), abort_flag)) {
+                        give_up();
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;");
+                    const uint32_t d = tmem + (uint32_t)b * 128u;
+#pragma unroll
+                    for (int kk = 0; kk < 16; kk++)
+                        mma_issue_tmem_a_tf32(d, a0 + 128u + (uint32_t)kk * 8u,
+                                              smem_desc(u0 + (uint32_t)kk * 256u, 128u, SBO), idesc, kk ? 1u : 0u);
+                    any = true;
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                        smem_addr(&bar_lofree)));
+                    if (!mbar_wait_or_abort(smem_addr(&bar_aready[0]), (uint32_t)(j & 1), abort_flag)) {
+                        give_up();
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;");
+#pragma unroll
+                    for (int p = 0; p < 2; p++) {
+#pragma unroll
+                        for (int kk = 0; kk < 16; kk++)
+                            mma_issue_tmem_a_tf32(d, a0 + (uint32_t)kk * 8u,
+                                                  smem_desc(u0 + (uint32_t)p * Cfg::kPart + (uint32_t)kk * 256u, 128u,
+                                                            SBO),
+                                                  idesc, 1u);
+                    }
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                        smem_addr(&bar_mma[b])));
+                }
+                // every issued MMA completes before TMEM is released
+                if (any) {
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                        smem_addr(&bar_fin)));
+                    mbar_wait(smem_addr(&bar_fin), 0u);
+                }
+            }
             uint64_t issued = 0;
-            for (uint64_t j = 0; j < J && !*abort_flag; j++) {
+            for (uint64_t j = 0; j < J && !*abort_flag && !TF; j++) {
                 const int b = (int)(j & 1);
                 // whole tiles: A operand b, its (j >> 1)-th fill; quarter tiles: the one A operand, its j-th
                 if (!mbar_wait_or_abort(smem_addr(&bar_aready[QT ? 0 : b]),
@@ -365,30 +421,15 @@ __global__ void __launch_bounds__(kPThreads, 1)
                 const uint32_t a0 = tmem + 256u + (QT ? 0u : (uint32_t)b * 128u);
                 const uint32_t u0 = smem_addr(Us);
                 uint32_t accum = 0;
-                if constexpr (TF) {
-                    // a_hi u_hi, a_hi u_lo, a_lo u_hi; A hi at +0, lo at +128 columns
 #pragma unroll
-                    for (int p = 0; p < 3; p++) {
-                        const uint32_t abase = a0 + (p == 2 ? 128u : 0u), bbase = u0 + (p == 1 ? Cfg::kPart : 0u);
+                for (int p = 0; p < (W ? 6 : 3); p++) {
+                    const uint32_t abase = a0 + prod_a<W>(p), bbase = u0 + prod_u<W>(p) * kPHalf;
 #pragma unroll
-                        for (int kk = 0; kk < 16; kk++) {
-                            // K step of 8 TF32 = 8 TMEM columns of A, two core matrices of U
-                            mma_issue_tmem_a_tf32(d, abase + (uint32_t)kk * 8u,
-                                                  smem_desc(bbase + (uint32_t)kk * 256u, 128u, SBO), idesc, accum);
-                            accum = 1;
-                        }
-                    }
-                } else {
-#pragma unroll
-                    for (int p = 0; p < (W ? 6 : 3); p++) {
-                        const uint32_t abase = a0 + prod_a<W>(p), bbase = u0 + prod_u<W>(p) * kPHalf;
-#pragma unroll
-                        for (int kk = 0; kk < 8; kk++) {
-                            // K step of 16 BF16 = 8 TMEM columns of A, two core matrices of U
-                            mma_issue_tmem_a(d, abase + (uint32_t)kk * 8u,
-                                             smem_desc(bbase + (uint32_t)kk * 256u, 128u, SBO), idesc, accum);
-                            accum = 1;
-                        }
+                    for (int kk = 0; kk < 8; kk++) {
+                        // K step of 16 BF16 = 8 TMEM columns of A, two core matrices of U
+                        mma_issue_tmem_a(d, abase + (uint32_t)kk * 8u,
+                                         smem_desc(bbase + (uint32_t)kk * 256u, 128u, SBO), idesc, accum);
+                        accum = 1;
                     }
                 }
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -566,6 +607,47 @@ __global__ void __launch_bounds__(kPThreads, 1)
                         v[8 + i] = make_float2(v[8 + i].x - __uint_as_float(b0), v[8 + i].y - __uint_as_float(b1));
                     }
                 }
+                if constexpr (TF) {
+                    // lo parts first: their columns were last read by tile j - 1's
+                    // first product (lo free); then the hi parts, once tile j - 1's
+                    // MMAs are done (converter warp 0 polls)
+                    const uint32_t acol = tmem + lane_off + 256u + (uint32_t)(32 * part);
+                    uint32_t lo0[16], lo1[16];
+#pragma unroll
+                    for (int i = 0; i < 8; i++) {
+                        lo0[2 * i] = __float_as_uint(v[i].x);
+                        lo0[2 * i + 1] = __float_as_uint(v[i].y);
+                        lo1[2 * i] = __float_as_uint(v[8 + i].x);
+                        lo1[2 * i + 1] = __float_as_uint(v[8 + i].y);
+                    }
+                    const uint32_t lf = smem_addr(&bar_lofree), lp = (uint32_t)((j - 1) & 1);
+                    const bool okl = !qbad && (j == 0 || cw != 0 || mbar_wait_or_abort(lf, lp, abort_flag));
+                    if (named_bar_or(1, kPConv, !okl || *abort_flag)) {
+                        give_up();
+                        break;
+                    }
+                    if (j >= 1) (void)mbar_try_wait(lf, lp);
+                    asm volatile("tcgen05.fence::after_thread_sync;");
+                    tmem_st16(acol + 128u, lo0);
+                    tmem_st16(acol + 144u, lo1);
+                    tmem_wait_st();
+                    asm volatile("tcgen05.fence::before_thread_sync;");
+                    mbar_arrive(smem_addr(&bar_loready));
+                    const uint32_t hb = smem_addr(&bar_mma[(j - 1) & 1]), hp = (uint32_t)(((j - 1) >> 1) & 1);
+                    const bool okh = j == 0 || cw != 0 || mbar_wait_or_abort(hb, hp, abort_flag);
+                    if (named_bar_or(1, kPConv, !okh || *abort_flag)) {
+                        give_up();
+                        break;
+                    }
+                    if (j >= 1) (void)mbar_try_wait(hb, hp);
+                    asm volatile("tcgen05.fence::after_thread_sync;");
+                    tmem_st16(acol, hi0);
+                    tmem_st16(acol + 16u, hi1);
+                    tmem_wait_st();
+                    asm volatile("tcgen05.fence::before_thread_sync;");
+                    mbar_arrive(smem_addr(&bar_aready[0]));
+                    continue;
+                }
                 // the one A operand was last read by the MMAs of tile j - 1
                 // (converter warp 0 polls)
                 const uint32_t mb = smem_addr(&bar_mma[(j - 1) & 1]), mp = (uint32_t)(((j - 1) >> 1) & 1);
@@ -592,21 +674,6 @@ __global__ void __launch_bounds__(kPThreads, 1)
                         }
                         tmem_st16(acol + 64u * (uint32_t)sl, pk);
                     }
-                } else {
-                    // hi at +0, lo at +128 columns
-                    const uint32_t acol = tmem + lane_off + 256u + (uint32_t)(32 * part);
-                    uint32_t lo0[16], lo1[16];
-#pragma unroll
-                    for (int i = 0; i < 8; i++) {
-                        lo0[2 * i] = __float_as_uint(v[i].x);
-                        lo0[2 * i + 1] = __float_as_uint(v[i].y);
-                        lo1[2 * i] = __float_as_uint(v[8 + i].x);
-                        lo1[2 * i + 1] = __float_as_uint(v[8 + i].y);
-                    }
-                    tmem_st16(acol, hi0);
-                    tmem_st16(acol + 16u, hi1);
-                    tmem_st16(acol + 128u, lo0);
-                    tmem_st16(acol + 144u, lo1);
                 }
             }
             tmem_wait_st();

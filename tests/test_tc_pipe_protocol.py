@@ -390,3 +390,99 @@ def test_protocol7_needs_a_pair_per_eighth():
     with pytest.raises(AssertionError):
         for seed in range(500):
             run7(1 + seed % 6, False, seed, nbar=4)
+
+
+def run_tf_split(J, pd, seed, shared_lo=False):
+    """The 3xTF32 variant's A handshake in two halves: the MMA issuer takes
+    a_lo u_hi first and commits (lo free), then a_hi u_hi and a_hi u_lo and
+    commits (the whole tile done); the converters (one group: the quarters
+    are read as in `run`, the A stores follow an all-converter barrier) write
+    tile j's lo parts once tile j - 1's lo product is done and signal lo
+    ready, then its hi parts once tile j - 1's MMAs are done and signal hi
+    ready; the MMA waits lo ready before the lo product and hi ready before
+    the others. shared_lo: the lo parts wait only for the whole previous
+    tile (the one-handshake layout)."""
+    rng = random.Random(seed)
+    lofree, loready, hiready = Bar(1), Bar(1), Bar(1)
+    mma = [Bar(1) for _ in range(2)]
+    accf = [Bar(1) for _ in range(2)]
+    a_lo = [None, True]       # (tile, read) of the one A operand's lo and hi regions
+    a_hi = [None, True]
+    acc = [None, None]
+    written = []
+    state = {"lo_read": -1, "hi_read": -1}
+
+    def converters():
+        for j in range(J):
+            yield                                        # quarters read, phases, split
+            if j >= 1:
+                if shared_lo:
+                    while not mma[(j - 1) & 1].done(((j - 1) >> 1) & 1):
+                        yield
+                else:
+                    while not lofree.done((j - 1) & 1):
+                        yield
+            assert state["lo_read"] == j - 1, ("lo rewritten before the MMAs read it", j)
+            a_lo[0] = j
+            yield
+            loready.arrive()
+            if j >= 1:
+                while not mma[(j - 1) & 1].done(((j - 1) >> 1) & 1):
+                    yield
+            assert state["hi_read"] == j - 1, ("hi rewritten before the MMAs read it", j)
+            a_hi[0] = j
+            yield
+            hiready.arrive()
+
+    def mma_issuer():
+        for j in range(J):
+            b = j & 1
+            if j >= 2:
+                while not accf[b].done(((j - 2) >> 1) & 1):
+                    yield
+            assert acc[b] is None, "accumulator still being written back"
+            while not loready.done(j & 1):
+                yield
+            assert a_lo[0] == j, ("lo product read another tile's lo parts", j)
+            yield
+            state["lo_read"] = j
+            lofree.arrive()
+            while not hiready.done(j & 1):
+                yield
+            assert a_hi[0] == j, ("hi products read another tile's hi parts", j)
+            yield
+            state["hi_read"] = j
+            acc[b] = j
+            mma[b].arrive()
+
+    def write_back():
+        for j in range(J):
+            b = j & 1
+            while not mma[b].done((j >> 1) & 1):
+                yield
+            assert acc[b] == j
+            yield
+            acc[b] = None
+            written.append(j)
+            accf[b].arrive()
+
+    alive = [converters(), mma_issuer(), write_back()]
+    steps = 0
+    while alive:
+        steps += 1
+        assert steps < 200000, "no progress (deadlock)"
+        a = rng.choice(alive)
+        try:
+            next(a)
+        except StopIteration:
+            alive.remove(a)
+    assert written == list(range(J))
+
+
+@pytest.mark.parametrize("shared_lo", [False, True])
+def test_protocol_tf32_lo_hi_handshake(shared_lo):
+    """The two-half A handshake of the 3xTF32 variant: every interleaving
+    writes each half of the one A operand only after the MMAs that read its
+    previous contents are done, and finishes."""
+    for seed in range(800):
+        run_tf_split(1 + seed % 9, False, seed, shared_lo=shared_lo)
