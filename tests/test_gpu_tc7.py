@@ -116,3 +116,17 @@ def test_tc7_plan_vs_oracle(Q, name):
     y64 = y.astype(np.complex128)
     assert abs(nf - np.vdot(y64, y64).real) <= 1e-6
     assert abs(nf - np.vdot(x, x).real) <= 1e-4 * np.vdot(x, x).real
+
+
+@pytest.mark.parametrize("dt,prec", [(0, 1), (1, 3), (1, 2)])
+def test_tc7_rejects_other_pairings(Q, dt, prec):
+    """7-qubit tensor-core blocks exist for complex64 kets with BF16x3 only:
+    3xTF32 on complex64 and every complex128 precision are refused on the
+    host, before any launch."""
+    st = Q.State(16, dt)
+    qa = (C.c_int * 7)(*range(7))
+    u = np.ascontiguousarray(np.eye(128, dtype=np.complex128).ravel().view(np.float64))
+    with pytest.raises(Q.QsimError) as e:
+        Q.qsim_apply_fused(st.h, 7, qa, u.ctypes.data_as(C.c_void_p), prec)
+    assert e.value.status == 6
+    st.close()
