@@ -1013,7 +1013,9 @@ def rows_leg(Q, W, C, torch, n=27):
         out[name] = {"ms": ms, "bytes": by, "gbs": by / (ms * 1e-3) / 1e9, "frac_of_hbm": by / (ms * 1e-3) / 1e9 / peak}
     # A11: Bloch vectors of all 27 qubits (tiled passes over the ket)
     ms = timed(lambda: Q.qsim_bloch_all(st.h, r3), reps=3)
-    out["A11 Bloch vectors, all 27 qubits"] = {"ms": ms}
+    by = 3 * B * N   # three tiled passes, one read of the ket each
+    out["A11 Bloch vectors, all 27 qubits"] = {"ms": ms, "bytes": by, "gbs": by / (ms * 1e-3) / 1e9,
+                                               "frac_of_hbm": by / (ms * 1e-3) / 1e9 / peak}
     st.close()
     other.close()
     # A19 / A20: proposal MLP (12 -> 64 -> 64 -> 1)

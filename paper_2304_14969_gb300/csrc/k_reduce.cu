@@ -49,21 +49,15 @@ template <int M>
 __global__ void __launch_bounds__(256) k_red_final(const double *__restrict__ partial, int rows,
                                                    double *__restrict__ out)
 {
-    // one CTA of 256 threads; per column m each thread adds every 256th row,
-    // then a warp-shuffle and shared-memory tree adds the 256 sums (FP64)
-    __shared__ double sh[8];
-    for (int m = 0; m < M; m++) {
+    // one CTA of 256 threads; warp w adds the columns m = w, w + 8, ...: each
+    // lane adds every 32nd row, then a warp-shuffle tree adds the 32 lanes
+    // (FP64; no block-wide barrier, so the columns proceed in parallel)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int m = warp; m < M; m += nw) {
         double v = 0;
-        for (int r = threadIdx.x; r < rows; r += blockDim.x) v += partial[(size_t)r * M + m];
+        for (int r = lane; r < rows; r += 32) v += partial[(size_t)r * M + m];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double t = 0;
-            for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += sh[w];
-            out[m] = t;
-        }
-        __syncthreads();
+        if (lane == 0) out[m] = v;
     }
 }
 
@@ -351,104 +345,212 @@ template <> struct CAcc<double> {
 
 // Bloch sums of the 12 tile qubits of every tile (t = 12, c = 4: tile qubits
 // 0..3 and eight high ones), same partial-row format as k_red_bloch_tile.
-// A thread holds 16 amplitudes in registers: first the 16 consecutive ones
-// of its run (register bits = tile bits 0..3, one contiguous 128-byte
-// (complex64) load), then, read back from an XOR-swizzled shared-memory copy
-// of the tile, those with register bits = tile bits 4..7 and 8..11. Every
-// tile qubit's pair sums are taken in registers: sum over bit = 1 of |psi|^2,
-// and S = sum over bit = 0 of conj(psi_i) psi_{i + 2^q}; runs of 8 terms in
-// the ket's precision, added into compensated accumulators. low = 0 skips
-// the low qubits' sums (an earlier pass over the same ket has them). A
-// complex64 run is read 16 bytes (two amplitudes) at a time.
+//
+// Tiles stream through a ring of kBlochStages shared-memory stages filled by
+// 16-byte cp.async copies, so kBlochStages - 1 tiles are in flight while one
+// is summed and registers hold only the accumulators and one slice of 16
+// amplitudes. A stage keeps a tile as 256 runs of 16 consecutive amplitudes
+// (tile bits 0..3); run r sits at byte r * (16 B + 16): the 16-byte pad
+// staggers the runs across the shared-memory banks, which makes the copies
+// and the three read patterns below free of bank conflicts. The copies of a
+// warp cover whole runs (one 128- or 256-byte line each).
+//
+// Thread th then takes three slices of 16 amplitudes: its own run (register
+// bits = tile bits 0..3, tile bits 4..11 = th), then those with register
+// bits = tile bits 4..7 and 8..11. Each slice gives, for its four tile
+// qubits, S = sum over bit = 0 of conj(psi_i) psi_{i + 2^q}, in runs of 8
+// terms in the ket's precision added into compensated accumulators. The
+// first slice also gives the run total |psi|^2 and, for LOW, the sums over
+// bit = 1 of |psi|^2 of the tile qubits 0..3. That sum for a high tile qubit
+// 4 + b is the sum of the run totals of the threads whose bit b is set, so
+// it is formed once, in the block reduction. LOW = false skips the low
+// qubits (an earlier pass over the same ket has them).
+static const int kBlochStages = 3;
+
 template <typename R>
-__global__ void __launch_bounds__(256, 1)
-    k_red_bloch_reg(const typename V2T<R>::T *__restrict__ a, const __grid_constant__ TileSpec ts, double *partial,
-                    const int *__restrict__ gate, int low)
+struct BlochGeom {
+    static constexpr int kB = 2 * (int)sizeof(R);   // bytes per amplitude
+    static constexpr int kRun = 16 * kB;             // bytes of a run
+    static constexpr int kRunPad = kRun + 16;        // stage stride of a run
+    static constexpr int kStage = 256 * kRunPad;     // bytes of a stage
+    static constexpr int kGran = kRun / 16;          // 16-byte granules per run
+    static constexpr int kSmem = kBlochStages * kStage;
+};
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+template <typename R, bool LOW>
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
+    k_red_bloch_pipe(const typename V2T<R>::T *__restrict__ a, const __grid_constant__ TileSpec ts,
+                     double *partial, const int *__restrict__ gate)
 {
     if (gate && *gate == 0) return;   // nothing to check (the sums are not read)
     using V = typename V2T<R>::T;
+    using G = BlochGeom<R>;
     extern __shared__ __align__(16) unsigned char smraw[];
-    V *tile = (V *)smraw;
-    __shared__ double red[8][37];
+    __shared__ uint64_t hh[16];   // ket offset of the run-index bits above the ones a thread fixes
     const int th = threadIdx.x, lane = th & 31, warp = th >> 5;
-    auto swz = [](uint32_t e) { return e ^ (((e >> 4) ^ (e >> 8)) & 15u); };
-    // offset of this thread's run: th's bits on tile qubits 4..11
-    uint64_t hoff = 0;
-#pragma unroll
-    for (int b = 0; b < 8; b++)
-        if ((th >> b) & 1) hoff |= 1ull << ts.tq[4 + b];
-    CAcc<R> acc[37];   // [0] total, then (s1, sr, si) of tile qubit j at 1 + 3 j
+    // copy k of thread th moves granule th % kGran of run k * (256 / kGran) + th / kGran
+    constexpr int kLoBits = G::kGran == 8 ? 5 : 4;   // run-index bits fixed by th
+    if (th < G::kGran) {
+        uint64_t h = 0;
+        for (int b = 0; b < 8 - kLoBits; b++)
+            if ((th >> b) & 1) h |= 1ull << ts.tq[4 + kLoBits + b];
+        hh[th] = h * (uint64_t)G::kB;
+    }
+    uint64_t hlo = 0;
+    for (int b = 0; b < kLoBits; b++)
+        if (((th / G::kGran) >> b) & 1) hlo |= 1ull << ts.tq[4 + b];
+    const unsigned char *src0 = (const unsigned char *)a + hlo * G::kB + (th % G::kGran) * 16;
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smraw);
+    const uint32_t dst0 = sbase + (th / G::kGran) * G::kRunPad + (th % G::kGran) * 16;
+    constexpr uint32_t kDstStep = (256 / G::kGran) * G::kRunPad;
+    __syncthreads();
+
     const uint64_t ntiles = 1ull << (ts.n - 12);
-    // the next tile's run is loaded while this one is summed
-    V nxt[16];
-    auto load_run = [&](uint64_t t) {
-        const V *src = a + (tile_expand(t << 4, ts.ins) | hoff);
-        if constexpr (sizeof(V) == 8) {
-            const float4 *s4 = (const float4 *)src;
+    const uint64_t cnt = ntiles > blockIdx.x ? (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+    // ket index of the next tile to issue: the tile id's bits deposited into the
+    // non-tile bit positions (mask M); the next id of this CTA is gridDim.x on,
+    // added with carries running through the tile positions (set to one)
+    uint64_t nonTile = ((1ull << ts.n) - 1) & ~0xfull;
+    for (int j = 0; j < 8; j++) nonTile &= ~(1ull << ts.tq[4 + j]);
+    const uint64_t step = tile_expand((uint64_t)gridDim.x << 4, ts.ins);
+    uint64_t nextBase = tile_expand((uint64_t)blockIdx.x << 4, ts.ins);
+    auto issue = [&](uint64_t i) {
+        const uint64_t base = nextBase * G::kB;
+        nextBase = ((nextBase | ~nonTile) + step) & nonTile;
+        const uint32_t d = dst0 + (uint32_t)(i % kBlochStages) * G::kStage;
 #pragma unroll
-            for (int r = 0; r < 8; r++) {
-                const float4 w = s4[r];
-                nxt[2 * r] = make_float2(w.x, w.y);
-                nxt[2 * r + 1] = make_float2(w.z, w.w);
+        for (int k = 0; k < G::kGran; k++) cp_async16(d + k * kDstStep, src0 + base + hh[k]);
+    };
+#pragma unroll
+    for (int s = 0; s < kBlochStages - 1; s++) {
+        if (s < cnt) issue(s);
+        cp_async_commit();
+    }
+
+    CAcc<R> aT;                       // run totals
+    CAcc<R> aS1[LOW ? 4 : 1];         // sum over bit = 1 of |psi|^2, tile qubits 0..3
+    CAcc<R> aR[LOW ? 12 : 8], aI[LOW ? 12 : 8];   // Re S, Im S (index j - 4 without LOW)
+    constexpr int kOff = LOW ? 0 : 4;
+    // without LOW the run sums of an even tile are held and added together with
+    // the next tile's (runs of 16 terms), which halves the compensated adds
+    R hR[LOW ? 1 : 8], hI[LOW ? 1 : 8];
+    bool hold = false, paired = false;
+    V v[16];
+    auto pair_sums = [&](int j0) {
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            R sr = 0, si = 0;
+#pragma unroll
+            for (int r = 0; r < 16; r++) {
+                if (r & (1 << j)) continue;
+                const V x = v[r], y = v[r | (1 << j)];
+                sr = fma(x.x, y.x, fma(x.y, y.y, sr));
+                si = fma(x.x, y.y, fma(-x.y, y.x, si));
+            }
+            const int k = j0 + j - kOff;
+            if constexpr (LOW) {
+                aR[k].add(sr);
+                aI[k].add(si);
+            } else if (hold) {
+                hR[k] = sr;
+                hI[k] = si;
+            } else {
+                aR[k].add(paired ? hR[k] + sr : sr);
+                aI[k].add(paired ? hI[k] + si : si);
+            }
+        }
+    };
+    const uint32_t offA = (uint32_t)th * G::kRunPad;
+    const uint32_t offB = (uint32_t)(th >> 4) * 16 * G::kRunPad + (th & 15) * G::kB;
+    const uint32_t offC = (uint32_t)(th >> 4) * G::kRunPad + (th & 15) * G::kB;
+
+    for (uint64_t i = 0; i < cnt; i++) {
+        cp_async_wait<kBlochStages - 2>();   // this thread's copies of tile i have landed
+        __syncthreads();                     // everyone's have, and tile i - 1 is read
+        if (i + kBlochStages - 1 < cnt) issue(i + kBlochStages - 1);
+        cp_async_commit();
+        const unsigned char *st = smraw + (size_t)(i % kBlochStages) * G::kStage;
+        hold = !(i & 1) && i + 1 < cnt;
+        paired = (i & 1);
+        // slice 1: own run
+        if constexpr (sizeof(R) == 4) {
+#pragma unroll
+            for (int g = 0; g < 8; g++) {
+                const float4 w = *(const float4 *)(st + offA + g * 16);
+                v[2 * g] = make_float2(w.x, w.y);
+                v[2 * g + 1] = make_float2(w.z, w.w);
             }
         } else {
 #pragma unroll
-            for (int r = 0; r < 16; r++) nxt[r] = src[r];
+            for (int r = 0; r < 16; r++) v[r] = *(const V *)(st + offA + r * 16);
         }
-    };
-    if (blockIdx.x < ntiles) load_run(blockIdx.x);
-    for (uint64_t tid = blockIdx.x; tid < ntiles; tid += gridDim.x) {
-        V v[16];
-#pragma unroll
-        for (int r = 0; r < 16; r++) v[r] = nxt[r];
-        if (tid + gridDim.x < ntiles) load_run(tid + gridDim.x);
-        auto sums = [&](int j0) {
-#pragma unroll
-            for (int j = 0; j < 4; j++) {
-                R s1 = 0, sr = 0, si = 0;
-#pragma unroll
-                for (int r = 0; r < 16; r++) {
-                    if (r & (1 << j)) continue;
-                    const V x = v[r], y = v[r | (1 << j)];
-                    s1 = fma(y.x, y.x, fma(y.y, y.y, s1));
-                    sr = fma(x.x, y.x, fma(x.y, y.y, sr));
-                    si = fma(x.x, y.y, fma(-x.y, y.x, si));
-                }
-                acc[1 + 3 * (j0 + j)].add(s1);
-                acc[2 + 3 * (j0 + j)].add(sr);
-                acc[3 + 3 * (j0 + j)].add(si);
-            }
-        };
         {
+            R p[16];
+#pragma unroll
+            for (int r = 0; r < 16; r++) p[r] = fma(v[r].x, v[r].x, v[r].y * v[r].y);
             R tot = 0;
 #pragma unroll
-            for (int r = 0; r < 16; r++) tot = fma(v[r].x, v[r].x, fma(v[r].y, v[r].y, tot));
-            acc[0].add(tot);
+            for (int r = 0; r < 16; r++) tot += p[r];
+            aT.add(tot);
+            if constexpr (LOW) {
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    R s1 = 0;
+#pragma unroll
+                    for (int r = 0; r < 16; r++)
+                        if (r & (1 << j)) s1 += p[r];
+                    aS1[j].add(s1);
+                }
+            }
         }
-        if (low) sums(0);
-        __syncthreads();   // the previous tile's reads are done
+        if constexpr (LOW) pair_sums(0);
+        // slice 2: register bits = tile bits 4..7
 #pragma unroll
-        for (int r = 0; r < 16; r++) tile[swz(((uint32_t)th << 4) | r)] = v[r];
-        __syncthreads();
+        for (int r = 0; r < 16; r++) v[r] = *(const V *)(st + offB + r * G::kRunPad);
+        pair_sums(4);
+        // slice 3: register bits = tile bits 8..11
 #pragma unroll
-        for (int r = 0; r < 16; r++) v[r] = tile[swz((th & 15) | (r << 4) | ((th >> 4) << 8))];
-        sums(4);
-#pragma unroll
-        for (int r = 0; r < 16; r++) v[r] = tile[swz(th | (r << 8))];
-        sums(8);
+        for (int r = 0; r < 16; r++) v[r] = *(const V *)(st + offC + r * 16 * G::kRunPad);
+        pair_sums(8);
     }
-    // block reduction of the 37 sums (FP64) into this CTA's partial row
-#pragma unroll
-    for (int m = 0; m < 37; m++) {
-        double x = acc[m].get();
+    cp_async_wait<0>();
+    __syncthreads();   // the stages are free: the block reduction uses them
+
+    // block reduction (FP64) into this CTA's partial row
+    double *red = (double *)smraw;   // [8 warps][kTileRow]
+    const double tot = aT.get();
+    auto put = [&](int m, double x) {
         for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-        if (lane == 0) red[warp][m] = x;
+        if (lane == 0) red[warp * kTileRow + m] = x;
+    };
+    put(0, tot);
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        put(1 + 3 * j, LOW ? aS1[LOW ? j : 0].get() : 0.0);
+        put(2 + 3 * j, LOW ? aR[LOW ? j : 0].get() : 0.0);
+        put(3 + 3 * j, LOW ? aI[LOW ? j : 0].get() : 0.0);
+    }
+#pragma unroll
+    for (int j = 4; j < 12; j++) {
+        put(1 + 3 * j, ((th >> (j - 4)) & 1) ? tot : 0.0);
+        put(2 + 3 * j, aR[j - kOff].get());
+        put(3 + 3 * j, aI[j - kOff].get());
     }
     __syncthreads();
     for (int m = th; m < kTileRow; m += blockDim.x) {
         double x = 0;
         if (m < 37)
-            for (int w = 0; w < (int)(blockDim.x >> 5); w++) x += red[w][m];
+            for (int w = 0; w < (int)(blockDim.x >> 5); w++) x += red[w * kTileRow + m];
         partial[(size_t)blockIdx.x * kTileRow + m] = x;
     }
 }
@@ -620,20 +722,39 @@ qsim_status bloch_sums_device(const void *amps, qsim_dtype dt, int n, cudaStream
         uint64_t ntiles = 1ull << (n - t);
         int blocks;
         if (t == 12 && c == 4) {
-            // register-resident tile pass (256 threads x 16 amplitudes)
-            const size_t smem = (size_t)4096 * (dt == QSIM_C64 ? 8 : 16);
+            // pipelined tile pass (256 threads x 16 amplitudes, cp.async stage ring);
+            // complex64: two CTAs per SM, complex128: one
             static bool attr = false;
             if (!attr) {
-                cudaFuncSetAttribute(k_red_bloch_reg<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536);
-                cudaFuncSetAttribute(k_red_bloch_reg<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 32768);
+                cudaFuncSetAttribute(k_red_bloch_pipe<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     BlochGeom<float>::kSmem);
+                cudaFuncSetAttribute(k_red_bloch_pipe<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     BlochGeom<float>::kSmem);
+                cudaFuncSetAttribute(k_red_bloch_pipe<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     BlochGeom<double>::kSmem);
+                cudaFuncSetAttribute(k_red_bloch_pipe<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     BlochGeom<double>::kSmem);
                 attr = true;
             }
-            blocks = (int)std::min<uint64_t>(ntiles, (uint64_t)num_sms());
-            if (dt == QSIM_C64)
-                k_red_bloch_reg<float><<<blocks, 256, smem, stream>>>((const float2 *)amps, ts, sc.d, d_gate, np == 0);
-            else
-                k_red_bloch_reg<double><<<blocks, 256, smem, stream>>>((const double2 *)amps, ts, sc.d, d_gate,
-                                                                        np == 0);
+            const bool low = np == 0;
+            if (dt == QSIM_C64) {
+                blocks = (int)std::min<uint64_t>(ntiles, 2 * (uint64_t)num_sms());
+                const size_t smem = BlochGeom<float>::kSmem;
+                if (low)
+                    k_red_bloch_pipe<float, true><<<blocks, 256, smem, stream>>>((const float2 *)amps, ts, sc.d, d_gate);
+                else
+                    k_red_bloch_pipe<float, false><<<blocks, 256, smem, stream>>>((const float2 *)amps, ts, sc.d,
+                                                                                   d_gate);
+            } else {
+                blocks = (int)std::min<uint64_t>(ntiles, (uint64_t)num_sms());
+                const size_t smem = BlochGeom<double>::kSmem;
+                if (low)
+                    k_red_bloch_pipe<double, true><<<blocks, 256, smem, stream>>>((const double2 *)amps, ts, sc.d,
+                                                                                   d_gate);
+                else
+                    k_red_bloch_pipe<double, false><<<blocks, 256, smem, stream>>>((const double2 *)amps, ts, sc.d,
+                                                                                    d_gate);
+            }
         } else {
             blocks = (int)std::min<uint64_t>(ntiles, kMaxRedBlocks);
             size_t smem = ((size_t)1 << t) * (dt == QSIM_C64 ? 8 : 16);

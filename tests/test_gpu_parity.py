@@ -226,14 +226,18 @@ def test_reductions_vs_oracle(Q, dt):
     other.close()
 
 
-def test_bloch_all_large(Q):
-    n = 22
-    x = W.gaussian_state(n, 2)
-    st = Q.State(n, 0)
+@pytest.mark.parametrize("dt,n", [(0, 12), (0, 13), (1, 13), (0, 22), (1, 20), (0, 24), (1, 23)])
+def test_bloch_all_large(Q, dt, n):
+    """All-qubit Bloch sums (Sec. III.A step 1) of a Gaussian ket, every qubit
+    against the oracle: one tile (n = 12), one tile per CTA (13), and several
+    tiles per CTA, so that the stage ring of the tiled pass wraps (20-24)."""
+    x = W.gaussian_state(n, 2 + n)
+    st = Q.State(n, dt)
     st.upload(x)
     r = st.bloch_all()
-    for q in (0, 5, 11, 17, 21):
-        assert np.max(np.abs(r[q] - oracle.bloch(x, q))) <= 2e-6
+    tol = 1e-13 if dt else 2e-6
+    for q in range(n):
+        assert np.max(np.abs(r[q] - oracle.bloch(x, q))) <= tol, q
     st.close()
 
 
