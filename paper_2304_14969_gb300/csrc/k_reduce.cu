@@ -246,6 +246,7 @@ struct TileSpec {
     int n, t, c;
     int tq[16];       // tile qubits, tq[0..c-1] = 0..c-1, rest ascending
     InsSpec ins;      // high tile qubits to insert when expanding a tile id
+    uint32_t wmask;   // tile qubits whose sums this pass reports
 };
 
 __device__ __forceinline__ uint64_t tile_expand(uint64_t w, const InsSpec &ins)
@@ -343,6 +344,78 @@ template <> struct CAcc<double> {
     __device__ __forceinline__ double get() const { return hi; }
 };
 
+// A pair of values of the ket's precision handled together: for FP32 one
+// 64-bit register pair and the packed FP32x2 instructions (one instruction
+// for two multiply-adds), for FP64 two scalars.
+struct PkF {
+    unsigned long long u;
+};
+struct PkD {
+    double x, y;
+};
+template <typename R> struct PkT;
+template <> struct PkT<float> { using T = PkF; };
+template <> struct PkT<double> { using T = PkD; };
+
+__device__ __forceinline__ PkF pk(float a, float b)
+{
+    PkF r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r.u) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ PkD pk(double a, double b) { return PkD{a, b}; }
+__device__ __forceinline__ float2 upk(PkF p)
+{
+    float a, b;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(p.u));
+    return make_float2(a, b);
+}
+__device__ __forceinline__ double2 upk(PkD p) { return make_double2(p.x, p.y); }
+__device__ __forceinline__ PkF fma2(PkF a, PkF b, PkF c)
+{
+    PkF r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.u) : "l"(a.u), "l"(b.u), "l"(c.u));
+    return r;
+}
+__device__ __forceinline__ PkD fma2(PkD a, PkD b, PkD c) { return PkD{fma(a.x, b.x, c.x), fma(a.y, b.y, c.y)}; }
+__device__ __forceinline__ PkF add2(PkF a, PkF b)
+{
+    PkF r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.u) : "l"(a.u), "l"(b.u));
+    return r;
+}
+__device__ __forceinline__ PkD add2(PkD a, PkD b) { return PkD{a.x + b.x, a.y + b.y}; }
+__device__ __forceinline__ PkF sub2(PkF a, PkF b)
+{
+    PkF r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r.u) : "l"(a.u), "l"(b.u));
+    return r;
+}
+__device__ __forceinline__ PkD sub2(PkD a, PkD b) { return PkD{a.x - b.x, a.y - b.y}; }
+
+// CAcc for a pair: TwoSum on both halves at once (FP32x2), plain FP64 sums
+// for complex128 kets.
+template <typename R> struct CAcc2;
+template <> struct CAcc2<float> {
+    PkF hi = pk(0.f, 0.f), lo = pk(0.f, 0.f);
+    __device__ __forceinline__ void add(PkF x)
+    {
+        const PkF s = add2(hi, x), bp = sub2(s, hi);
+        lo = add2(lo, add2(sub2(hi, sub2(s, bp)), sub2(x, bp)));
+        hi = s;
+    }
+    __device__ __forceinline__ double2 get() const
+    {
+        const float2 h = upk(hi), l = upk(lo);
+        return make_double2((double)h.x + (double)l.x, (double)h.y + (double)l.y);
+    }
+};
+template <> struct CAcc2<double> {
+    PkD hi = PkD{0.0, 0.0};
+    __device__ __forceinline__ void add(PkD x) { hi = add2(hi, x); }
+    __device__ __forceinline__ double2 get() const { return upk(hi); }
+};
+
 // Bloch sums of the 12 tile qubits of every tile (t = 12, c = 4: tile qubits
 // 0..3 and eight high ones), same partial-row format as k_red_bloch_tile.
 //
@@ -437,36 +510,41 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
         cp_async_commit();
     }
 
+    using P = typename PkT<R>::T;
     CAcc<R> aT;                       // run totals
     CAcc<R> aS1[LOW ? 4 : 1];         // sum over bit = 1 of |psi|^2, tile qubits 0..3
-    CAcc<R> aR[LOW ? 12 : 8], aI[LOW ? 12 : 8];   // Re S, Im S (index j - 4 without LOW)
+    CAcc2<R> aS[LOW ? 12 : 8];        // (Re S, Im S) of tile qubit j (index j - 4 without LOW)
     constexpr int kOff = LOW ? 0 : 4;
     // without LOW the run sums of an even tile are held and added together with
     // the next tile's (runs of 16 terms), which halves the compensated adds
-    R hR[LOW ? 1 : 8], hI[LOW ? 1 : 8];
+    P hS[LOW ? 1 : 8];
     bool hold = false, paired = false;
     V v[16];
+    // S_j = sum over pairs of conj(x) y = (x.x y.x + x.y y.y) + i (x.x y.y - x.y y.x):
+    // two packed products per pair, x (.) y and x (.) (y.y, y.x), split at the end
     auto pair_sums = [&](int j0) {
+        P ys[16];
+#pragma unroll
+        for (int r = 1; r < 16; r++) ys[r] = pk(v[r].y, v[r].x);
 #pragma unroll
         for (int j = 0; j < 4; j++) {
-            R sr = 0, si = 0;
+            P q1 = pk((R)0, (R)0), q2 = pk((R)0, (R)0);
 #pragma unroll
             for (int r = 0; r < 16; r++) {
                 if (r & (1 << j)) continue;
-                const V x = v[r], y = v[r | (1 << j)];
-                sr = fma(x.x, y.x, fma(x.y, y.y, sr));
-                si = fma(x.x, y.y, fma(-x.y, y.x, si));
+                const P x = pk(v[r].x, v[r].y), y = pk(v[r | (1 << j)].x, v[r | (1 << j)].y);
+                q1 = fma2(x, y, q1);
+                q2 = fma2(x, ys[r | (1 << j)], q2);
             }
+            const auto a1 = upk(q1), a2 = upk(q2);
+            const P sri = pk(a1.x + a1.y, a2.x - a2.y);
             const int k = j0 + j - kOff;
             if constexpr (LOW) {
-                aR[k].add(sr);
-                aI[k].add(si);
+                aS[k].add(sri);
             } else if (hold) {
-                hR[k] = sr;
-                hI[k] = si;
+                hS[k] = sri;
             } else {
-                aR[k].add(paired ? hR[k] + sr : sr);
-                aI[k].add(paired ? hI[k] + si : si);
+                aS[k].add(paired ? add2(hS[k], sri) : sri);
             }
         }
     };
@@ -495,14 +573,14 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
             for (int r = 0; r < 16; r++) v[r] = *(const V *)(st + offA + r * 16);
         }
         {
-            R p[16];
-#pragma unroll
-            for (int r = 0; r < 16; r++) p[r] = fma(v[r].x, v[r].x, v[r].y * v[r].y);
-            R tot = 0;
-#pragma unroll
-            for (int r = 0; r < 16; r++) tot += p[r];
-            aT.add(tot);
             if constexpr (LOW) {
+                R p[16];
+#pragma unroll
+                for (int r = 0; r < 16; r++) p[r] = fma(v[r].x, v[r].x, v[r].y * v[r].y);
+                R tot = 0;
+#pragma unroll
+                for (int r = 0; r < 16; r++) tot += p[r];
+                aT.add(tot);
 #pragma unroll
                 for (int j = 0; j < 4; j++) {
                     R s1 = 0;
@@ -511,6 +589,15 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
                         if (r & (1 << j)) s1 += p[r];
                     aS1[j].add(s1);
                 }
+            } else {
+                P t2 = pk((R)0, (R)0);
+#pragma unroll
+                for (int r = 0; r < 16; r++) {
+                    const P x = pk(v[r].x, v[r].y);
+                    t2 = fma2(x, x, t2);
+                }
+                const auto tt = upk(t2);
+                aT.add(tt.x + tt.y);
             }
         }
         if constexpr (LOW) pair_sums(0);
@@ -536,15 +623,17 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
     put(0, tot);
 #pragma unroll
     for (int j = 0; j < 4; j++) {
+        const double2 sj = LOW ? aS[LOW ? j : 0].get() : make_double2(0.0, 0.0);
         put(1 + 3 * j, LOW ? aS1[LOW ? j : 0].get() : 0.0);
-        put(2 + 3 * j, LOW ? aR[LOW ? j : 0].get() : 0.0);
-        put(3 + 3 * j, LOW ? aI[LOW ? j : 0].get() : 0.0);
+        put(2 + 3 * j, sj.x);
+        put(3 + 3 * j, sj.y);
     }
 #pragma unroll
     for (int j = 4; j < 12; j++) {
+        const double2 sj = aS[j - kOff].get();
         put(1 + 3 * j, ((th >> (j - 4)) & 1) ? tot : 0.0);
-        put(2 + 3 * j, aR[j - kOff].get());
-        put(3 + 3 * j, aI[j - kOff].get());
+        put(2 + 3 * j, sj.x);
+        put(3 + 3 * j, sj.y);
     }
     __syncthreads();
     for (int m = th; m < kTileRow; m += blockDim.x) {
@@ -676,17 +765,15 @@ qsim_status reduce_bloch(qsim_state *s, int q, double out4[4])
     return QSIM_OK;
 }
 
-// Writes, for every tile qubit j of a finished tiled pass, the four sums
+// Writes, for every tile qubit j of a finished tiled pass that the pass
+// reports (bit j of ts.wmask), the four sums
 // [sum_{bit0}|psi|^2, sum_{bit1}|psi|^2, Re S, Im S] of qubit tq[j] into
 // out[4*tq[j] ..] (device), from the FP64 combine of the partial rows.
-__global__ void k_bloch_scatter(const double *__restrict__ comb, TileSpec ts, int first_new, int low,
-                                double *__restrict__ out)
+__global__ void k_bloch_scatter(const double *__restrict__ comb, TileSpec ts, double *__restrict__ out)
 {
     int j = threadIdx.x;
-    if (j >= ts.t) return;
+    if (j >= ts.t || !((ts.wmask >> j) & 1)) return;
     int q = ts.tq[j];
-    if (q < first_new && j >= ts.c) return;   // covered by an earlier pass
-    if (j < ts.c && !low) return;             // the low qubits: the first pass has them
     double total = comb[0], one = comb[1 + 3 * j];
     out[4 * q + 0] = total - one;
     out[4 * q + 1] = one;
@@ -695,33 +782,56 @@ __global__ void k_bloch_scatter(const double *__restrict__ comb, TileSpec ts, in
 }
 
 // Bloch sums of all n qubits of a ket into d_out[4n] (device), without a
-// host sync: ceil((n - c)/(t - c)) tiled passes, each covering the c low
-// qubits and t - c new high qubits.
+// host sync. n < 12: one pass with every qubit in the tile. n >= 12: P =
+// ceil((n - 4)/8) passes of 12 tile qubits, the 4 lowest (reported by the
+// first pass) and 8 high ones; high qubit number i (ascending) goes to pass
+// i mod P, so that every pass holds a few of the highest qubits and a tile's
+// runs spread over few memory pages; a pass with fewer than 8 of its own
+// fills its tile with low high qubits of other passes (not reported).
 qsim_status bloch_sums_device(const void *amps, qsim_dtype dt, int n, cudaStream_t stream, Scratch &sc, const int *d_gate,
                               double *d_out, int *passes)
 {
-    int t = std::min(n, 12);
-    int c = std::min(t, 4);
     QS_TRY(ensure_scratch(sc, (size_t)kMaxRedBlocks * 64 + 64));
-    int next_high = c, np = 0;
-    while (true) {
+    std::vector<TileSpec> specs;
+    if (n < 12) {
         TileSpec ts;
         ts.n = n;
-        ts.t = t;
-        ts.c = c;
-        for (int j = 0; j < c; j++) ts.tq[j] = j;
-        std::vector<int> high;
-        for (int q = next_high; q < n && (int)high.size() < t - c; q++) high.push_back(q);
-        int first_new = next_high;
-        for (int q = n - 1; (int)high.size() < t - c && q >= c; q--)
-            if (std::find(high.begin(), high.end(), q) == high.end()) high.push_back(q);
-        std::sort(high.begin(), high.end());
-        for (int j = 0; j < t - c; j++) ts.tq[c + j] = high[j];
-        ts.ins.npos = t - c;
-        for (int j = 0; j < t - c; j++) ts.ins.pos[j] = high[j];
-        uint64_t ntiles = 1ull << (n - t);
+        ts.t = n;
+        ts.c = std::min(n, 4);
+        for (int j = 0; j < n; j++) ts.tq[j] = j;
+        ts.ins.npos = n - ts.c;
+        for (int j = 0; j < n - ts.c; j++) ts.ins.pos[j] = ts.c + j;
+        ts.wmask = (1u << n) - 1;
+        specs.push_back(ts);
+    } else {
+        const int h = n - 4, P = (h + 7) / 8;
+        for (int p = 0; p < P; p++) {
+            std::vector<int> own, high;
+            for (int i = p; i < h; i += P) own.push_back(4 + i);
+            high = own;
+            for (int q = 4; q < n && (int)high.size() < 8; q++)
+                if (std::find(high.begin(), high.end(), q) == high.end()) high.push_back(q);
+            std::sort(high.begin(), high.end());
+            TileSpec ts;
+            ts.n = n;
+            ts.t = 12;
+            ts.c = 4;
+            for (int j = 0; j < 4; j++) ts.tq[j] = j;
+            ts.wmask = p == 0 ? 0xfu : 0u;
+            for (int j = 0; j < 8; j++) {
+                ts.tq[4 + j] = high[j];
+                ts.ins.pos[j] = high[j];
+                if (std::find(own.begin(), own.end(), high[j]) != own.end()) ts.wmask |= 1u << (4 + j);
+            }
+            ts.ins.npos = 8;
+            specs.push_back(ts);
+        }
+    }
+    int np = 0;
+    for (const TileSpec &ts : specs) {
+        const uint64_t ntiles = 1ull << (n - ts.t);
         int blocks;
-        if (t == 12 && c == 4) {
+        if (ts.t == 12) {
             // pipelined tile pass (256 threads x 16 amplitudes, cp.async stage ring);
             // complex64: two CTAs per SM, complex128: one
             static bool attr = false;
@@ -757,7 +867,7 @@ qsim_status bloch_sums_device(const void *amps, qsim_dtype dt, int n, cudaStream
             }
         } else {
             blocks = (int)std::min<uint64_t>(ntiles, kMaxRedBlocks);
-            size_t smem = ((size_t)1 << t) * (dt == QSIM_C64 ? 8 : 16);
+            size_t smem = ((size_t)1 << ts.t) * (dt == QSIM_C64 ? 8 : 16);
             if (dt == QSIM_C64)
                 k_red_bloch_tile<float><<<blocks, kRedThreads, smem, stream>>>((const float2 *)amps, ts, sc.d, d_gate);
             else
@@ -767,12 +877,9 @@ qsim_status bloch_sums_device(const void *amps, qsim_dtype dt, int n, cudaStream
         QS_CUDA(cudaGetLastError());
         double *comb = sc.d + (size_t)kMaxRedBlocks * 64;
         k_red_final<kTileRow><<<1, 256, 0, stream>>>(sc.d, blocks, comb);
-        k_bloch_scatter<<<1, 32, 0, stream>>>(comb, ts, np == 0 ? 0 : first_new,
-                                              (t == 12 && c == 4) ? (np == 0) : 1, d_out);
+        k_bloch_scatter<<<1, 32, 0, stream>>>(comb, ts, d_out);
         QS_CUDA(cudaGetLastError());
         np++;
-        next_high += t - c;
-        if (next_high >= n || t == n) break;
     }
     if (passes) *passes = np;
     return QSIM_OK;

@@ -58,7 +58,8 @@ def stage_image(B, n, high, tid):
 
 
 CASES = [(12, list(range(4, 12))), (27, list(range(4, 12))), (27, list(range(12, 20))),
-         (27, list(range(19, 27))), (20, [4, 7, 9, 11, 13, 15, 17, 19])]
+         (27, list(range(19, 27))), (20, [4, 7, 9, 11, 13, 15, 17, 19]),
+         (27, [4, 7, 10, 13, 16, 19, 22, 25]), (27, [4, 6, 9, 12, 15, 18, 21, 24])]
 
 
 @pytest.mark.parametrize("B", [8, 16])
@@ -129,7 +130,7 @@ def test_no_bank_conflicts(B):
 
 @pytest.mark.parametrize("n,high,grid", [(27, list(range(4, 12)), 304), (27, list(range(19, 27)), 304),
                                          (24, [4, 7, 9, 11, 13, 15, 17, 23], 152), (13, list(range(4, 12)), 152),
-                                         (12, list(range(4, 12)), 304)])
+                                         (12, list(range(4, 12)), 304), (27, [5, 8, 11, 14, 17, 20, 23, 26], 304)])
 def test_tile_base_masked_add(n, high, grid):
     nontile = ((1 << n) - 1) & ~0xF
     for q in high:
