@@ -463,7 +463,8 @@ template <int N> __device__ __forceinline__ void cp_async_wait()
 template <typename R, bool LOW>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
     k_red_bloch_pipe(const typename V2T<R>::T *__restrict__ a, const __grid_constant__ TileSpec ts,
-                     double *partial, const int *__restrict__ gate)
+                     double *partial, const int *__restrict__ gate, double *__restrict__ out,
+                     unsigned *__restrict__ ticket)
 {
     if (gate && *gate == 0) return;   // nothing to check (the sums are not read)
     using V = typename V2T<R>::T;
@@ -642,6 +643,34 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
             for (int w = 0; w < (int)(blockDim.x >> 5); w++) x += red[w * kTileRow + m];
         partial[(size_t)blockIdx.x * kTileRow + m] = x;
     }
+
+    // The last CTA to finish adds the rows of all CTAs (FP64, in the same
+    // order as k_red_final) and writes the pass's sums of the tile qubits it
+    // reports: [sum_{bit0}|psi|^2, sum_{bit1}|psi|^2, Re S, Im S] of qubit
+    // tq[j] at out[4 tq[j]]. The ticket wraps back to 0 with the last CTA.
+    __threadfence();
+    __syncthreads();
+    __shared__ unsigned s_last;
+    if (th == 0) s_last = atomicInc(ticket, gridDim.x - 1) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    double *comb = red;   // the block rows above have been consumed
+    for (int m = warp; m < 37; m += (int)(blockDim.x >> 5)) {
+        double x = 0;
+        for (int r = lane; r < (int)gridDim.x; r += 32) x += __ldcg(&partial[(size_t)r * kTileRow + m]);
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) comb[m] = x;
+    }
+    __syncthreads();
+    if (th < 12 && ((ts.wmask >> th) & 1)) {
+        const int q = ts.tq[th];
+        const double total = comb[0], one = comb[1 + 3 * th];
+        out[4 * q + 0] = total - one;
+        out[4 * q + 1] = one;
+        out[4 * q + 2] = comb[2 + 3 * th];
+        out[4 * q + 3] = comb[3 + 3 * th];
+    }
 }
 
 template <typename R>
@@ -661,8 +690,12 @@ qsim_status ensure_scratch(Scratch &sc, size_t doubles)
 {
     if (sc.cap >= doubles) return QSIM_OK;
     free_scratch(sc);
-    QS_CUDA(cudaMalloc(&sc.d, doubles * sizeof(double)));
+    // one more slot past the capacity holds the tiled Bloch pass's ticket,
+    // which no other user of the scratch writes; it starts at 0
+    QS_CUDA(cudaMalloc(&sc.d, (doubles + 1) * sizeof(double)));
     QS_CUDA(cudaMallocHost(&sc.h, 64 * sizeof(double)));
+    const double zero = 0.0;
+    QS_CUDA(cudaMemcpy(sc.d + doubles, &zero, sizeof(double), cudaMemcpyHostToDevice));
     sc.cap = doubles;
     return QSIM_OK;
 }
@@ -847,24 +880,29 @@ qsim_status bloch_sums_device(const void *amps, qsim_dtype dt, int n, cudaStream
                 attr = true;
             }
             const bool low = np == 0;
+            unsigned *ticket = (unsigned *)(sc.d + sc.cap);
             if (dt == QSIM_C64) {
                 blocks = (int)std::min<uint64_t>(ntiles, 2 * (uint64_t)num_sms());
                 const size_t smem = BlochGeom<float>::kSmem;
                 if (low)
-                    k_red_bloch_pipe<float, true><<<blocks, 256, smem, stream>>>((const float2 *)amps, ts, sc.d, d_gate);
+                    k_red_bloch_pipe<float, true><<<blocks, 256, smem, stream>>>((const float2 *)amps, ts, sc.d, d_gate,
+                                                                                  d_out, ticket);
                 else
                     k_red_bloch_pipe<float, false><<<blocks, 256, smem, stream>>>((const float2 *)amps, ts, sc.d,
-                                                                                   d_gate);
+                                                                                   d_gate, d_out, ticket);
             } else {
                 blocks = (int)std::min<uint64_t>(ntiles, (uint64_t)num_sms());
                 const size_t smem = BlochGeom<double>::kSmem;
                 if (low)
                     k_red_bloch_pipe<double, true><<<blocks, 256, smem, stream>>>((const double2 *)amps, ts, sc.d,
-                                                                                   d_gate);
+                                                                                   d_gate, d_out, ticket);
                 else
                     k_red_bloch_pipe<double, false><<<blocks, 256, smem, stream>>>((const double2 *)amps, ts, sc.d,
-                                                                                    d_gate);
+                                                                                    d_gate, d_out, ticket);
             }
+            QS_CUDA(cudaGetLastError());
+            np++;
+            continue;   // the pass's last CTA has combined the rows and written the sums
         } else {
             blocks = (int)std::min<uint64_t>(ntiles, kMaxRedBlocks);
             size_t smem = ((size_t)1 << ts.t) * (dt == QSIM_C64 ? 8 : 16);
@@ -888,17 +926,14 @@ qsim_status bloch_sums_device(const void *amps, qsim_dtype dt, int n, cudaStream
 // Host copy of the per-physical-qubit Bloch sums (synchronises).
 qsim_status reduce_bloch_all(qsim_state *s, double *sums)
 {
-    QS_TRY(ensure_red(s));
-    double *d = nullptr;
-    QS_CUDA(cudaMallocAsync((void **)&d, 4 * sizeof(double) * s->n, s->stream));
-    qsim_status st = bloch_sums_device(s->amps, s->dt, s->n, s->stream, s->red, nullptr, d, nullptr);
-    if (st == QSIM_OK) {
-        cudaError_t e = cudaMemcpyAsync(sums, d, 4 * sizeof(double) * s->n, cudaMemcpyDeviceToHost, s->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-        if (e != cudaSuccess) st = cuda_fail(e, "bloch sums");
-    }
-    cudaFreeAsync(d, s->stream);
-    return st;
+    // the 4n sums go to the state's scratch, past the partial rows and the combine row
+    const size_t at = (size_t)kMaxRedBlocks * 64 + 64;
+    QS_TRY(ensure_scratch(s->red, at + 4 * (size_t)s->n));
+    double *d = s->red.d + at;
+    QS_TRY(bloch_sums_device(s->amps, s->dt, s->n, s->stream, s->red, nullptr, d, nullptr));
+    QS_CUDA(cudaMemcpyAsync(sums, d, 4 * sizeof(double) * s->n, cudaMemcpyDeviceToHost, s->stream));
+    QS_CUDA(cudaStreamSynchronize(s->stream));
+    return QSIM_OK;
 }
 
 qsim_status probs_to_device(qsim_state *s, double *d_out)
