@@ -6,9 +6,12 @@ slices are read, and how the tile base advances. Checked: every copy stays
 inside its stage and the ket, the copies of a tile cover the stage exactly
 once, each stage position then holds the amplitude the read patterns expect,
 the reads of a warp phase hit distinct shared-memory banks, and the
-masked-add advance of the tile base equals the bit insertion it replaces."""
+masked-add advance of the tile base equals the bit insertion it replaces.
+The passes' plan (which qubits each pass tiles and reports) and the sums the
+passes form from their slices are emulated in FP64 against the oracle."""
 import random
 
+import numpy as np
 import pytest
 
 M64 = (1 << 64) - 1
@@ -143,3 +146,90 @@ def test_tile_base_masked_add(n, high, grid):
             assert nb == tile_expand((b + i * grid) << 4, high)
             nb = ((nb | (~nontile & M64)) + step) & M64 & nontile
             i += 1
+
+
+def pass_specs(n):
+    """The tiled passes of the all-qubit Bloch sums for n >= 12 qubits, as the
+    host side of csrc/k_reduce.cu plans them: 12 tile qubits (0..3 and 8 high
+    ones), high qubit number i to pass i mod P, fillers from the lowest high
+    qubits of other passes, and the mask of tile qubits the pass reports."""
+    h = n - 4
+    P = (h + 7) // 8
+    specs = []
+    for p in range(P):
+        own = [4 + i for i in range(p, h, P)]
+        high = list(own)
+        q = 4
+        while len(high) < 8:
+            if q not in high:
+                high.append(q)
+            q += 1
+        high.sort()
+        wmask = (0xF if p == 0 else 0) | sum(1 << (4 + j) for j, q in enumerate(high) if q in own)
+        specs.append(([0, 1, 2, 3] + high, wmask))
+    return specs
+
+
+def emulate_bloch_all(psi):
+    """The kernel's sums in FP64, tile by tile: thread th of a tile holds its
+    run (tile bits 0..3, tile bits 4..11 = th), then the slices with register
+    bits = tile bits 4..7 and 8..11; S_j from the register pairs of the slice
+    that holds tile bit j; Z sums of the high tile qubits from the threads'
+    run totals."""
+    n = int(np.log2(psi.size))
+    out = np.zeros((n, 4))
+    seen = np.zeros(n, dtype=int)
+    for tq, wmask in pass_specs(n):
+        rest = [q for q in range(n) if q not in tq]
+        comb = np.zeros(1 + 3 * 12)
+        for tid in range(1 << len(rest)):
+            base = sum(((tid >> k) & 1) << q for k, q in enumerate(rest))
+            tile = np.array([psi[base + sum(((e >> j) & 1) << tq[j] for j in range(12))] for e in range(4096)])
+            runs = tile.reshape(256, 16)                       # [th][r]
+            tot_th = (np.abs(runs) ** 2).sum(axis=1)
+            comb[0] += tot_th.sum()
+            for j in range(4):                                  # slice 1: own run, pairs in r bit j
+                r0 = [r for r in range(16) if not (r >> j) & 1]
+                x, y = runs[:, r0], runs[:, [r | (1 << j) for r in r0]]
+                comb[1 + 3 * j] += (np.abs(y) ** 2).sum()
+                s = (np.conj(x) * y).sum()
+                comb[2 + 3 * j] += s.real
+                comb[3 + 3 * j] += s.imag
+            for b in range(8):                                  # Z of tile bit 4 + b from run totals
+                comb[1 + 3 * (4 + b)] += tot_th[[th for th in range(256) if (th >> b) & 1]].sum()
+            for j in range(4, 12):                              # slices 2 and 3: pairs in tile bit j
+                e0 = [e for e in range(4096) if not (e >> j) & 1]
+                s = (np.conj(tile[e0]) * tile[[e | (1 << j) for e in e0]]).sum()
+                comb[2 + 3 * j] += s.real
+                comb[3 + 3 * j] += s.imag
+        for j in range(12):
+            if (wmask >> j) & 1:
+                q = tq[j]
+                seen[q] += 1
+                out[q] = [comb[0] - comb[1 + 3 * j], comb[1 + 3 * j], comb[2 + 3 * j], comb[3 + 3 * j]]
+    assert (seen == 1).all()   # every qubit reported by exactly one pass
+    return out
+
+
+@pytest.mark.parametrize("n", [12, 13, 14])
+def test_pass_plan_and_sums_match_the_oracle(n):
+    """Every qubit is reported by one pass, and the sums the passes form give
+    the oracle's Bloch vectors (r = (2 Re S, 2 Im S, p0 - p1) / (p0 + p1))."""
+    import oracle
+    rng = np.random.default_rng(n)
+    psi = rng.normal(size=1 << n) + 1j * rng.normal(size=1 << n)
+    sums = emulate_bloch_all(psi)
+    for q in range(n):
+        p0, p1, sr, si = sums[q]
+        r = np.array([2 * sr, 2 * si, p0 - p1]) / (p0 + p1)
+        assert np.max(np.abs(r - oracle.bloch(psi, q))) <= 1e-12, q
+
+
+@pytest.mark.parametrize("n", [12, 13, 20, 27, 34])
+def test_pass_plan_covers_every_qubit_once(n):
+    specs = pass_specs(n)
+    assert len(specs) == (n - 4 + 7) // 8
+    rep = [q for tq, m in specs for j, q in enumerate(tq) if (m >> j) & 1]
+    assert sorted(rep) == list(range(n))
+    for tq, m in specs:
+        assert len(set(tq)) == 12 and max(tq) < n
