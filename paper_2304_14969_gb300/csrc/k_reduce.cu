@@ -437,7 +437,9 @@ template <> struct CAcc2<double> {
 // bit = 1 of |psi|^2 of the tile qubits 0..3. That sum for a high tile qubit
 // 4 + b is the sum of the run totals of the threads whose bit b is set, so
 // it is formed once, in the block reduction. LOW = false skips the low
-// qubits (an earlier pass over the same ket has them).
+// qubits (an earlier pass over the same ket has them). Each CTA writes one
+// partial row; the last CTA to finish adds the rows and writes the sums of
+// the qubits the pass reports.
 static const int kBlochStages = 3;
 
 template <typename R>
