@@ -259,9 +259,44 @@ __device__ __forceinline__ uint64_t tile_expand(uint64_t w, const InsSpec &ins)
     return w;
 }
 
+// End of a tiled Bloch pass, called by every thread of every CTA after the
+// CTA's partial row (kTileRow doubles, ncol of them used) is written: the
+// last CTA to finish (ticket, which wraps back to 0 with it) adds the rows in
+// FP64 and writes [sum_{bit0}|psi|^2, sum_{bit1}|psi|^2, Re S, Im S] of qubit
+// tq[j] at out[4 tq[j]] for every tile qubit j the pass reports (ts.wmask).
+__device__ __forceinline__ void bloch_last_cta(const double *partial, int ncol, const TileSpec &ts,
+                                               double *__restrict__ out, unsigned *__restrict__ ticket)
+{
+    __shared__ unsigned s_last;
+    __shared__ double comb[kTileRow];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicInc(ticket, gridDim.x - 1) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    for (int m = warp; m < ncol; m += nw) {
+        double x = 0;
+        for (int r = lane; r < (int)gridDim.x; r += 32) x += __ldcg(&partial[(size_t)r * kTileRow + m]);
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) comb[m] = x;
+    }
+    __syncthreads();
+    const int j = threadIdx.x;
+    if (j < ts.t && ((ts.wmask >> j) & 1)) {
+        const int q = ts.tq[j];
+        const double total = comb[0], one = comb[1 + 3 * j];
+        out[4 * q + 0] = total - one;
+        out[4 * q + 1] = one;
+        out[4 * q + 2] = comb[2 + 3 * j];
+        out[4 * q + 3] = comb[3 + 3 * j];
+    }
+}
+
 template <typename R>
 __global__ void k_red_bloch_tile(const typename V2T<R>::T *__restrict__ a, TileSpec ts, double *partial,
-                                 const int *__restrict__ gate)
+                                 const int *__restrict__ gate, double *__restrict__ out, unsigned *__restrict__ ticket)
 {
     if (gate && *gate == 0) return;   // nothing to check (the sums are not read)
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -322,6 +357,7 @@ __global__ void k_red_bloch_tile(const typename V2T<R>::T *__restrict__ a, TileS
     if ((threadIdx.x & 31) == 0) atomicAdd(&bacc[0], tot);
     __syncthreads();
     for (int m = threadIdx.x; m < kTileRow; m += blockDim.x) partial[(size_t)blockIdx.x * kTileRow + m] = bacc[m];
+    bloch_last_cta(partial, 1 + 3 * t, ts, out, ticket);
 }
 
 // Compensated accumulator: FP32 (hi, lo) pair kept with TwoSum (Knuth), so
@@ -646,33 +682,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
         partial[(size_t)blockIdx.x * kTileRow + m] = x;
     }
 
-    // The last CTA to finish adds the rows of all CTAs (FP64, in the same
-    // order as k_red_final) and writes the pass's sums of the tile qubits it
-    // reports: [sum_{bit0}|psi|^2, sum_{bit1}|psi|^2, Re S, Im S] of qubit
-    // tq[j] at out[4 tq[j]]. The ticket wraps back to 0 with the last CTA.
-    __threadfence();
-    __syncthreads();
-    __shared__ unsigned s_last;
-    if (th == 0) s_last = atomicInc(ticket, gridDim.x - 1) == gridDim.x - 1;
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    double *comb = red;   // the block rows above have been consumed
-    for (int m = warp; m < 37; m += (int)(blockDim.x >> 5)) {
-        double x = 0;
-        for (int r = lane; r < (int)gridDim.x; r += 32) x += __ldcg(&partial[(size_t)r * kTileRow + m]);
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-        if (lane == 0) comb[m] = x;
-    }
-    __syncthreads();
-    if (th < 12 && ((ts.wmask >> th) & 1)) {
-        const int q = ts.tq[th];
-        const double total = comb[0], one = comb[1 + 3 * th];
-        out[4 * q + 0] = total - one;
-        out[4 * q + 1] = one;
-        out[4 * q + 2] = comb[2 + 3 * th];
-        out[4 * q + 3] = comb[3 + 3 * th];
-    }
+    bloch_last_cta(partial, 37, ts, out, ticket);
 }
 
 template <typename R>
@@ -800,22 +810,6 @@ qsim_status reduce_bloch(qsim_state *s, int q, double out4[4])
     return QSIM_OK;
 }
 
-// Writes, for every tile qubit j of a finished tiled pass that the pass
-// reports (bit j of ts.wmask), the four sums
-// [sum_{bit0}|psi|^2, sum_{bit1}|psi|^2, Re S, Im S] of qubit tq[j] into
-// out[4*tq[j] ..] (device), from the FP64 combine of the partial rows.
-__global__ void k_bloch_scatter(const double *__restrict__ comb, TileSpec ts, double *__restrict__ out)
-{
-    int j = threadIdx.x;
-    if (j >= ts.t || !((ts.wmask >> j) & 1)) return;
-    int q = ts.tq[j];
-    double total = comb[0], one = comb[1 + 3 * j];
-    out[4 * q + 0] = total - one;
-    out[4 * q + 1] = one;
-    out[4 * q + 2] = comb[2 + 3 * j];
-    out[4 * q + 3] = comb[3 + 3 * j];
-}
-
 // Bloch sums of all n qubits of a ket into d_out[4n] (device), without a
 // host sync. n < 12: one pass with every qubit in the tile. n >= 12: P =
 // ceil((n - 4)/8) passes of 12 tile qubits, the 4 lowest (reported by the
@@ -863,6 +857,7 @@ qsim_status bloch_sums_device(const void *amps, qsim_dtype dt, int n, cudaStream
         }
     }
     int np = 0;
+    unsigned *ticket = (unsigned *)(sc.d + sc.cap);   // see ensure_scratch
     for (const TileSpec &ts : specs) {
         const uint64_t ntiles = 1ull << (n - ts.t);
         int blocks;
@@ -882,7 +877,6 @@ qsim_status bloch_sums_device(const void *amps, qsim_dtype dt, int n, cudaStream
                 attr = true;
             }
             const bool low = np == 0;
-            unsigned *ticket = (unsigned *)(sc.d + sc.cap);
             if (dt == QSIM_C64) {
                 blocks = (int)std::min<uint64_t>(ntiles, 2 * (uint64_t)num_sms());
                 const size_t smem = BlochGeom<float>::kSmem;
@@ -902,22 +896,16 @@ qsim_status bloch_sums_device(const void *amps, qsim_dtype dt, int n, cudaStream
                     k_red_bloch_pipe<double, false><<<blocks, 256, smem, stream>>>((const double2 *)amps, ts, sc.d,
                                                                                     d_gate, d_out, ticket);
             }
-            QS_CUDA(cudaGetLastError());
-            np++;
-            continue;   // the pass's last CTA has combined the rows and written the sums
         } else {
             blocks = (int)std::min<uint64_t>(ntiles, kMaxRedBlocks);
             size_t smem = ((size_t)1 << ts.t) * (dt == QSIM_C64 ? 8 : 16);
             if (dt == QSIM_C64)
-                k_red_bloch_tile<float><<<blocks, kRedThreads, smem, stream>>>((const float2 *)amps, ts, sc.d, d_gate);
+                k_red_bloch_tile<float><<<blocks, kRedThreads, smem, stream>>>((const float2 *)amps, ts, sc.d, d_gate,
+                                                                               d_out, ticket);
             else
                 k_red_bloch_tile<double><<<blocks, kRedThreads, smem, stream>>>((const double2 *)amps, ts, sc.d,
-                                                                                 d_gate);
+                                                                                 d_gate, d_out, ticket);
         }
-        QS_CUDA(cudaGetLastError());
-        double *comb = sc.d + (size_t)kMaxRedBlocks * 64;
-        k_red_final<kTileRow><<<1, 256, 0, stream>>>(sc.d, blocks, comb);
-        k_bloch_scatter<<<1, 32, 0, stream>>>(comb, ts, d_out);
         QS_CUDA(cudaGetLastError());
         np++;
     }
