@@ -530,7 +530,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1)
     const uint64_t ntiles = 1ull << (ts.n - 12);
     const uint64_t cnt = ntiles > blockIdx.x ? (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
     // ket index of the next tile to issue: the tile id's bits deposited into the
-    // non-tile bit positions (mask M); the next id of this CTA is gridDim.x on,
+    // non-tile bit positions (nonTile); the next id of this CTA is gridDim.x on,
     // added with carries running through the tile positions (set to one)
     uint64_t nonTile = ((1ull << ts.n) - 1) & ~0xfull;
     for (int j = 0; j < 8; j++) nonTile &= ~(1ull << ts.tq[4 + j]);
