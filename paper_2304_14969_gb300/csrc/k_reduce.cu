@@ -302,7 +302,7 @@ __global__ void k_red_bloch_tile(const typename V2T<R>::T *__restrict__ a, TileS
     extern __shared__ __align__(16) unsigned char smraw[];
     typename V2T<R>::T *tile = (typename V2T<R>::T *)smraw;
     const int t = ts.t, c = ts.c;
-    const uint64_t T = 1ull << t, runs = T >> c, runlen = 1ull << c;
+    const uint64_t T = 1ull << t, runlen = 1ull << c;
     const uint64_t ntiles = 1ull << (ts.n - t);
     __shared__ double bacc[kTileRow];
     for (int m = threadIdx.x; m < kTileRow; m += blockDim.x) bacc[m] = 0;
