@@ -282,7 +282,6 @@ __device__ __forceinline__ void fused_tile(typename FV<R>::T *__restrict__ a, co
     using V = typename FV<R>::T;
     constexpr int NR = 1 << RB;
     V *sm = (V *)smraw;
-    const uint64_t *tw = (const uint64_t *)(stg + P.off_tw);
     const R *cf = (const R *)(stg + P.off_cf);
     const FOp *ops = (const FOp *)(stg + P.off_ops);
     const FMap *maps = (const FMap *)(stg + P.off_maps);
